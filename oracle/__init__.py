@@ -1,0 +1,173 @@
+"""FP64 CPU oracle: Python entry points over ``tdks_oracle.c``.
+
+TEST INFRASTRUCTURE ONLY.  The tests, the smoke check and the benchmark's CPU baseline
+are the only callers; the product library never imports this package.  The oracle is
+compiled with gcc (``build()``) into ``oracle/_build/liboracle.so``.
+
+Every array argument uses the host layout of the seeded inputs: orbitals complex128
+[n_k, nz, ny, nx, n_orb]; fields float64 [nz, ny, nx].
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tdks_oracle.c")
+_OUT = os.path.join(_HERE, "_build", "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
+    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
+        tmp = _OUT + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                               "-D_GNU_SOURCE", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _OUT)
+    return _OUT
+
+
+class _Sys(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("h", ctypes.c_double), ("fd_order", ctypes.c_int), ("bc", ctypes.c_int),
+        ("n_orb", ctypes.c_int), ("n_k", ctypes.c_int),
+        ("kpts", ctypes.c_void_p), ("kw", ctypes.c_void_p), ("vloc", ctypes.c_void_p),
+        ("xc", ctypes.c_int), ("occ", ctypes.c_double), ("gauge", ctypes.c_int),
+        ("pol", ctypes.c_double * 3), ("amp", ctypes.c_double), ("omega", ctypes.c_double),
+        ("envelope", ctypes.c_int), ("t_total", ctypes.c_double),
+        ("n_atoms", ctypes.c_int), ("pos", ctypes.c_void_p), ("D", ctypes.c_void_p),
+        ("r_c", ctypes.c_double), ("r_cut", ctypes.c_double),
+    ]
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        P, D, I = ctypes.c_void_p, ctypes.c_double, ctypes.c_int
+        S = ctypes.POINTER(_Sys)
+        _lib.oracle_fd_laplacian_weights.argtypes = [I, P]
+        _lib.oracle_fd_gradient_weights.argtypes = [I, P]
+        _lib.oracle_field.argtypes = [S, D, P, P]
+        _lib.oracle_density.argtypes = [S, P, P]
+        _lib.oracle_lda_x.argtypes = [S, P, P]
+        _lib.oracle_lda_x.restype = D
+        _lib.oracle_apply_H.argtypes = [S, D, P, P, P]
+        _lib.oracle_taylor_substep.argtypes = [S, D, D, P]
+        _lib.oracle_observables.argtypes = [S, D, D, P, P]
+        _lib.oracle_propagate.argtypes = [S, D, D, I, I, P, P]
+        _lib.oracle_sphere_count.argtypes = [S, I]
+        _lib.oracle_sphere_count.restype = I
+    return _lib
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+class System:
+    """An oracle view of one problem.  Holds contiguous copies of the inputs so the C
+    struct's pointers stay valid for the object's lifetime."""
+
+    def __init__(self, spec, inputs, *, xc=None, gauge=None, projectors=None, vloc=None):
+        self.spec = spec
+        self.N = spec.n_points
+        self.vloc = np.ascontiguousarray(inputs.vloc if vloc is None else vloc, dtype=np.float64)
+        self.kpts = np.ascontiguousarray(inputs.kpts, dtype=np.float64)
+        self.kw = np.ascontiguousarray(inputs.kw, dtype=np.float64)
+        self.pos = np.ascontiguousarray(inputs.pos, dtype=np.float64).reshape(-1, 3)
+        self.D = np.ascontiguousarray(inputs.D, dtype=np.float64).reshape(-1, 4)
+        use_proj = spec.projectors if projectors is None else projectors
+        s = _Sys()
+        s.nx, s.ny, s.nz, s.h = spec.nx, spec.ny, spec.nz, spec.h
+        s.fd_order, s.bc, s.n_orb = spec.fd_order, spec.bc, spec.n_orb
+        s.n_k = self.kpts.shape[0]
+        s.kpts, s.kw, s.vloc = _ptr(self.kpts), _ptr(self.kw), _ptr(self.vloc)
+        s.xc = spec.xc if xc is None else xc
+        s.occ = spec.occ
+        s.gauge = spec.gauge if gauge is None else gauge
+        s.pol = (ctypes.c_double * 3)(*spec.pol)
+        s.amp, s.omega, s.envelope, s.t_total = spec.amp, spec.omega, spec.envelope, spec.t_total
+        s.n_atoms = self.pos.shape[0] if use_proj else 0
+        s.pos, s.D = _ptr(self.pos), _ptr(self.D)
+        s.r_c, s.r_cut = spec.r_c, spec.r_cut
+        self._s = s
+        self.lib = _load()
+        self.shape = (s.n_k, spec.nz, spec.ny, spec.nx, spec.n_orb)
+
+    @property
+    def ref(self):
+        return ctypes.byref(self._s)
+
+    def _psi(self, psi) -> np.ndarray:
+        a = np.ascontiguousarray(psi, dtype=np.complex128)
+        assert a.shape == self.shape, (a.shape, self.shape)
+        return a
+
+    def field(self, t):
+        E, A = np.zeros(3), np.zeros(3)
+        self.lib.oracle_field(self.ref, t, _ptr(E), _ptr(A))
+        return E, A
+
+    def density(self, psi) -> np.ndarray:
+        psi = self._psi(psi)
+        n = np.empty(self.N)
+        self.lib.oracle_density(self.ref, _ptr(psi), _ptr(n))
+        return n.reshape(self.spec.nz, self.spec.ny, self.spec.nx)
+
+    def lda_x(self, n):
+        n = np.ascontiguousarray(n, dtype=np.float64)
+        vx = np.empty_like(n)
+        ex = self.lib.oracle_lda_x(self.ref, _ptr(n), _ptr(vx))
+        return ex, vx
+
+    def apply_H(self, psi, t=0.0, vx=None) -> np.ndarray:
+        """H[vx, t] psi.  vx=None applies no exchange term; pass vx explicitly (e.g. from
+        ``vx_of(psi_state)``) to apply the Hamiltonian of a given state's density."""
+        psi = self._psi(psi)
+        out = np.empty_like(psi)
+        vptr = None
+        if vx is not None:
+            vx = np.ascontiguousarray(vx, dtype=np.float64)
+            vptr = _ptr(vx)
+        self.lib.oracle_apply_H(self.ref, t, vptr, _ptr(psi), _ptr(out))
+        return out
+
+    def vx_of(self, psi):
+        if self._s.xc != 1:
+            return None
+        return self.lda_x(self.density(psi))[1]
+
+    def taylor_substep(self, psi, t, dt) -> np.ndarray:
+        psi = self._psi(psi).copy()
+        self.lib.oracle_taylor_substep(self.ref, t, dt, _ptr(psi))
+        return psi
+
+    def observables(self, psi, t_state, t_field) -> np.ndarray:
+        psi = self._psi(psi)
+        obs = np.empty(8)
+        self.lib.oracle_observables(self.ref, t_state, t_field, _ptr(psi), _ptr(obs))
+        return obs
+
+    def propagate(self, psi, t0, dt, n_steps, substeps, record=True):
+        psi = self._psi(psi).copy()
+        obs = np.empty((n_steps, 8)) if record else None
+        self.lib.oracle_propagate(self.ref, t0, dt, n_steps, substeps, _ptr(psi),
+                                  _ptr(obs) if record else None)
+        return psi, obs
+
+    def sphere_count(self, a: int) -> int:
+        return self.lib.oracle_sphere_count(self.ref, a)
+
+
+def fd_weights(M: int):
+    lib = _load()
+    c, d = np.zeros(M + 1), np.zeros(M + 1)
+    lib.oracle_fd_laplacian_weights(M, _ptr(c))
+    lib.oracle_fd_gradient_weights(M, _ptr(d))
+    return c, d

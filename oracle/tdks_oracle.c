@@ -1,0 +1,452 @@
+/*
+ * FP64 CPU oracle for real-time TDDFT propagation on a uniform 3D grid.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the benchmark's CPU
+ * baseline may load this file's library.  It shares no code, header, table or helper
+ * with the CUDA library; the two meet only in the seeded inputs.
+ *
+ * What it computes follows the paper's statement of the problem (arXiv:1912.07921):
+ *   - the TDKS system  dphi_i/dt = -i H[n(t), t] phi_i,  phi(t0) = phi^0
+ *     (Sec. "New propagators for real-time TDDFT", first three equations);
+ *   - the adiabatic approximation: the exchange potential depends on the current
+ *     density only (same section);
+ *   - the high-order finite-difference Laplacian and gradient on the real-space grid
+ *     (Sec. "Maxwell ... coupling", discretisation paragraph; Sec. "Periodic systems");
+ *   - the LDA exchange energy E_x = int n e_x(n) (Sec. "Local domains", LDA equation);
+ *   - the time-dependent dipole d(t) = int r n(r,t) dr (Sec. "Local domains");
+ *   - the macroscopic current J = -(i/Omega) int sum_i phi_i [H, r] phi_i
+ *     (Sec. "Conductivities", eqn. current_density), local part;
+ *   - the velocity-gauge field E = -dA/dt (same section);
+ *   - closed-shell occupations f_i = 2 (Sec. "t-SURFF", closed shells).
+ * The exponential is a 4th-order Taylor series with H frozen over a (sub-)step; the
+ * paper does not print this propagator, so the oracle takes the readings listed at each
+ * function.  Everything is plain loops in double precision; OpenMP only splits the
+ * outermost independent loop.
+ *
+ * Layout: orbitals are complex doubles, index [k][z][y][x][orb] (state index innermost,
+ * Sec. "Memory layout").  Parity with the paper itself is unpinned: the paper prints no
+ * number for this path.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef double complex cplx;
+
+typedef struct {
+  int nx, ny, nz;
+  double h;
+  int fd_order;       /* 2M: 4 or 8 */
+  int bc;             /* 0: psi = 0 outside the box; 1: Bloch-twisted periodic cell */
+  int n_orb;
+  int n_k;
+  const double *kpts; /* [n_k][3] */
+  const double *kw;   /* [n_k] */
+  const double *vloc; /* [nz][ny][nx] */
+  int xc;             /* 0: none; 1: LDA exchange */
+  double occ;         /* occupation of every orbital */
+  int gauge;          /* 0: no field; 1: length gauge E(t).r; 2: velocity gauge A(t) */
+  double pol[3];
+  double amp, omega;
+  int envelope;       /* 0: none; 1: sin^2(pi t / t_total) on [0, t_total] */
+  double t_total;
+  int n_atoms;
+  const double *pos;  /* [n_atoms][3] */
+  const double *D;    /* [n_atoms][4] */
+  double r_c, r_cut;
+} oracle_sys;
+
+static long npts(const oracle_sys *s) { return (long)s->nx * s->ny * s->nz; }
+
+/* --------------------------------------------------------------------------------
+ * Finite-difference weights.  Central differences of order 2M on a uniform grid; the
+ * paper takes its weights from its Ref. (PRB 78, 075109) without printing them.  Closed
+ * forms: second derivative c_m = 2(-1)^(m+1) (M!)^2 / (m^2 (M-m)! (M+m)!),
+ * c_0 = -2 sum c_m; first derivative d_m = (-1)^(m+1) (M!)^2 / (m (M-m)! (M+m)!).
+ * ------------------------------------------------------------------------------ */
+static double fact(int n) { double f = 1.0; for (int i = 2; i <= n; i++) f *= i; return f; }
+
+void oracle_fd_laplacian_weights(int M, double *c) {
+  double s = 0.0;
+  for (int m = 1; m <= M; m++) {
+    double sign = (m % 2 == 1) ? 1.0 : -1.0;
+    c[m] = 2.0 * sign * fact(M) * fact(M) / ((double)m * m * fact(M - m) * fact(M + m));
+    s += c[m];
+  }
+  c[0] = -2.0 * s;
+}
+
+void oracle_fd_gradient_weights(int M, double *d) {
+  d[0] = 0.0;
+  for (int m = 1; m <= M; m++) {
+    double sign = (m % 2 == 1) ? 1.0 : -1.0;
+    d[m] = sign * fact(M) * fact(M) / ((double)m * fact(M - m) * fact(M + m));
+  }
+}
+
+/* Grid coordinates: centred box for finite systems, cell from the origin for solids. */
+static double coord(const oracle_sys *s, int axis, int i) {
+  int n = axis == 0 ? s->nx : (axis == 1 ? s->ny : s->nz);
+  if (s->bc == 0) return ((double)i - 0.5 * (double)(n - 1)) * s->h;
+  return (double)i * s->h;
+}
+
+/* --------------------------------------------------------------------------------
+ * External field.  Length gauge: E(t) = amp env(t) sin(omega t) pol, coupling +E.r
+ * (electron charge -1).  Velocity gauge: A(t) = amp env(t) sin(omega t) pol and
+ * E = -dA/dt (Sec. "Conductivities"; c absorbed into A).
+ * ------------------------------------------------------------------------------ */
+static double envelope(const oracle_sys *s, double t, double *denv) {
+  if (s->envelope == 1) {
+    if (t < 0.0 || t > s->t_total) { *denv = 0.0; return 0.0; }
+    double a = M_PI * t / s->t_total;
+    *denv = 2.0 * sin(a) * cos(a) * M_PI / s->t_total;
+    return sin(a) * sin(a);
+  }
+  *denv = 0.0;
+  return 1.0;
+}
+
+void oracle_field(const oracle_sys *s, double t, double *E, double *A) {
+  double denv, env = envelope(s, t, &denv);
+  double f = s->amp * env * sin(s->omega * t);
+  double df = s->amp * (denv * sin(s->omega * t) + env * s->omega * cos(s->omega * t));
+  for (int a = 0; a < 3; a++) {
+    E[a] = 0.0;
+    A[a] = 0.0;
+    if (s->gauge == 1) E[a] = f * s->pol[a];
+    if (s->gauge == 2) { A[a] = f * s->pol[a]; E[a] = -df * s->pol[a]; }
+  }
+}
+
+/* --------------------------------------------------------------------------------
+ * Boundary extension.  Value of orbital (k, o) at integer grid position (ix, iy, iz),
+ * which may lie outside the box: zero for finite systems; for a periodic cell the
+ * Bloch condition psi(r + L e_a) = exp(i k_a L_a) psi(r) folds it back.
+ * ------------------------------------------------------------------------------ */
+static cplx fetch(const oracle_sys *s, const cplx *psi, int k, int o, int ix, int iy, int iz) {
+  int n[3] = {s->nx, s->ny, s->nz};
+  int i[3] = {ix, iy, iz};
+  cplx phase = 1.0;
+  for (int a = 0; a < 3; a++) {
+    if (i[a] >= 0 && i[a] < n[a]) continue;
+    if (s->bc == 0) return 0.0;
+    int w = (int)floor((double)i[a] / (double)n[a]);
+    i[a] -= w * n[a];
+    double L = n[a] * s->h;
+    phase *= cexp(I * s->kpts[3 * k + a] * L * (double)w);
+  }
+  long p = ((long)i[2] * s->ny + i[1]) * s->nx + i[0];
+  return phase * psi[((long)k * npts(s) + p) * s->n_orb + o];
+}
+
+/* --------------------------------------------------------------------------------
+ * Density n(r) = sum_k w_k sum_i f_i |phi_ik(r)|^2  (TDKS density; f_i = occ).
+ * ------------------------------------------------------------------------------ */
+void oracle_density(const oracle_sys *s, const cplx *psi, double *n) {
+  long N = npts(s);
+#pragma omp parallel for
+  for (long p = 0; p < N; p++) {
+    double acc = 0.0;
+    for (int k = 0; k < s->n_k; k++)
+      for (int o = 0; o < s->n_orb; o++) {
+        cplx v = psi[((long)k * N + p) * s->n_orb + o];
+        acc += s->kw[k] * s->occ * (creal(v) * creal(v) + cimag(v) * cimag(v));
+      }
+    n[p] = acc;
+  }
+}
+
+/* --------------------------------------------------------------------------------
+ * LDA exchange, spin-unpolarised: e_x(n) = -(3/4)(3 n / pi)^(1/3) per particle,
+ * v_x = d(n e_x)/dn = -(3 n / pi)^(1/3);  E_x = sum_r n e_x(n) h^3.
+ * ------------------------------------------------------------------------------ */
+double oracle_lda_x(const oracle_sys *s, const double *n, double *vx) {
+  long N = npts(s);
+  double h3 = s->h * s->h * s->h, ex = 0.0;
+  for (long p = 0; p < N; p++) {
+    double c = cbrt(3.0 * n[p] / M_PI);
+    if (vx) vx[p] = -c;
+    ex += n[p] * (-0.75 * c) * h3;
+  }
+  return ex;
+}
+
+/* --------------------------------------------------------------------------------
+ * Kleinman-Bylander projectors.  The paper uses norm-conserving pseudopotentials with
+ * non-local parts but prints no projector formula, so these are synthetic:
+ *   beta_a1 = g(d), beta_a2..4 = (d_x, d_y, d_z) g(d),  g = exp(-|d|^2 / (2 r_c^2)),
+ *   d = r - R_a, support |d| <= r_cut,   V_NL = sum_aj |beta_aj> D_aj <beta_aj|.
+ * In a Bloch cell the sphere points are unwrapped positions u = cell point + T and carry
+ * exp(i k.T); in the velocity gauge beta is dressed by exp(-i A.d) so that V_NL is the
+ * gauge transform exp(-iA.r) V_NL exp(iA.r) and stays Hermitian.
+ * ------------------------------------------------------------------------------ */
+typedef struct {
+  long cell;      /* flat cell index */
+  double d[3];    /* u - R_a */
+  double T[3];    /* lattice translation u - cell position */
+} sphere_pt;
+
+static int sphere_points(const oracle_sys *s, int a, sphere_pt **out) {
+  int n[3] = {s->nx, s->ny, s->nz};
+  int lo[3], hi[3];
+  const double *R = s->pos + 3 * a;
+  for (int ax = 0; ax < 3; ax++) {
+    if (s->bc == 0) { lo[ax] = 0; hi[ax] = n[ax] - 1; }
+    else {
+      lo[ax] = (int)floor((R[ax] - s->r_cut) / s->h) - 1;
+      hi[ax] = (int)ceil((R[ax] + s->r_cut) / s->h) + 1;
+    }
+  }
+  long cap = (long)(hi[0] - lo[0] + 1) * (hi[1] - lo[1] + 1) * (hi[2] - lo[2] + 1);
+  sphere_pt *pts = (sphere_pt *)malloc(sizeof(sphere_pt) * (size_t)cap);
+  int cnt = 0;
+  for (int iz = lo[2]; iz <= hi[2]; iz++)
+    for (int iy = lo[1]; iy <= hi[1]; iy++)
+      for (int ix = lo[0]; ix <= hi[0]; ix++) {
+        int ii[3] = {ix, iy, iz}, cc[3];
+        double u[3], d[3], r2 = 0.0;
+        for (int ax = 0; ax < 3; ax++) {
+          if (s->bc == 0) u[ax] = coord(s, ax, ii[ax]);
+          else u[ax] = (double)ii[ax] * s->h;
+          d[ax] = u[ax] - R[ax];
+          r2 += d[ax] * d[ax];
+        }
+        if (r2 > s->r_cut * s->r_cut) continue;
+        sphere_pt *q = &pts[cnt++];
+        for (int ax = 0; ax < 3; ax++) {
+          int w = (int)floor((double)ii[ax] / (double)n[ax]);
+          cc[ax] = ii[ax] - w * n[ax];
+          q->T[ax] = (double)(w * n[ax]) * s->h;
+          q->d[ax] = d[ax];
+        }
+        q->cell = ((long)cc[2] * s->ny + cc[1]) * s->nx + cc[0];
+      }
+  *out = pts;
+  return cnt;
+}
+
+static void beta_values(const oracle_sys *s, const double *d, double *b) {
+  double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+  double g = exp(-r2 / (2.0 * s->r_c * s->r_c));
+  b[0] = g;
+  b[1] = d[0] * g;
+  b[2] = d[1] * g;
+  b[3] = d[2] * g;
+}
+
+/* Number of grid points in the projector sphere of atom a (for tests). */
+int oracle_sphere_count(const oracle_sys *s, int a) {
+  sphere_pt *p;
+  int c = sphere_points(s, a, &p);
+  free(p);
+  return c;
+}
+
+/* --------------------------------------------------------------------------------
+ * H psi for every orbital and k-point.  H = -1/2 Lap_h + V_loc + v_x + E(t).r
+ * (length gauge) or H = 1/2 (-i grad_h + A(t))^2 + V_loc + v_x (velocity gauge),
+ * plus V_NL.  vx may be NULL (no exchange term).  The field is taken at time t.
+ * ------------------------------------------------------------------------------ */
+void oracle_apply_H(const oracle_sys *s, double t, const double *vx, const cplx *in, cplx *out) {
+  int M = s->fd_order / 2;
+  double c[5], d[5];
+  oracle_fd_laplacian_weights(M, c);
+  oracle_fd_gradient_weights(M, d);
+  double E[3], A[3];
+  oracle_field(s, t, E, A);
+  double h = s->h, h2 = h * h, h3 = h * h * h;
+  long N = npts(s);
+  int B = s->n_orb;
+  double A2 = A[0] * A[0] + A[1] * A[1] + A[2] * A[2];
+
+  /* local part: kinetic stencil, potential, field */
+#pragma omp parallel for collapse(2)
+  for (int k = 0; k < s->n_k; k++)
+    for (int iz = 0; iz < s->nz; iz++)
+      for (int iy = 0; iy < s->ny; iy++)
+        for (int ix = 0; ix < s->nx; ix++) {
+          long p = ((long)iz * s->ny + iy) * s->nx + ix;
+          double v = s->vloc[p] + (vx ? vx[p] : 0.0);
+          if (s->gauge == 1)
+            v += E[0] * coord(s, 0, ix) + E[1] * coord(s, 1, iy) + E[2] * coord(s, 2, iz);
+          if (s->gauge == 2) v += 0.5 * A2;
+          for (int o = 0; o < B; o++) {
+            cplx psi0 = fetch(s, in, k, o, ix, iy, iz);
+            cplx lap = 3.0 * c[0] * psi0;
+            cplx grad[3] = {0.0, 0.0, 0.0};
+            for (int m = 1; m <= M; m++) {
+              cplx xp = fetch(s, in, k, o, ix + m, iy, iz), xm = fetch(s, in, k, o, ix - m, iy, iz);
+              cplx yp = fetch(s, in, k, o, ix, iy + m, iz), ym = fetch(s, in, k, o, ix, iy - m, iz);
+              cplx zp = fetch(s, in, k, o, ix, iy, iz + m), zm = fetch(s, in, k, o, ix, iy, iz - m);
+              lap += c[m] * (xp + xm + yp + ym + zp + zm);
+              grad[0] += d[m] * (xp - xm);
+              grad[1] += d[m] * (yp - ym);
+              grad[2] += d[m] * (zp - zm);
+            }
+            cplx r = -0.5 * lap / h2 + v * psi0;
+            if (s->gauge == 2)
+              r += -I * (A[0] * grad[0] + A[1] * grad[1] + A[2] * grad[2]) / h;
+            out[((long)k * N + p) * B + o] = r;
+          }
+        }
+
+  /* non-local part: gather <beta_aj|psi>, then scatter beta_aj D_aj <beta_aj|psi> */
+  if (s->n_atoms <= 0 || s->D == NULL) return;
+  for (int a = 0; a < s->n_atoms; a++) {
+    sphere_pt *pts;
+    int np = sphere_points(s, a, &pts);
+    for (int k = 0; k < s->n_k; k++) {
+      const double *kk = s->kpts + 3 * k;
+      cplx *proj = (cplx *)calloc((size_t)4 * B, sizeof(cplx));
+      for (int q = 0; q < np; q++) {
+        double b[4];
+        beta_values(s, pts[q].d, b);
+        double ph = 0.0;
+        for (int ax = 0; ax < 3; ax++) ph += kk[ax] * pts[q].T[ax] + A[ax] * pts[q].d[ax];
+        cplx phase = (s->bc == 1 || s->gauge == 2) ? cexp(I * ph) : 1.0;
+        for (int j = 0; j < 4; j++)
+          for (int o = 0; o < B; o++)
+            proj[j * B + o] += h3 * b[j] * phase * in[((long)k * N + pts[q].cell) * B + o];
+      }
+      for (int q = 0; q < np; q++) {
+        double b[4];
+        beta_values(s, pts[q].d, b);
+        double ph = 0.0;
+        for (int ax = 0; ax < 3; ax++) ph += kk[ax] * pts[q].T[ax] + A[ax] * pts[q].d[ax];
+        cplx phase = (s->bc == 1 || s->gauge == 2) ? cexp(-I * ph) : 1.0;
+        for (int j = 0; j < 4; j++)
+          for (int o = 0; o < B; o++)
+            out[((long)k * N + pts[q].cell) * B + o] += b[j] * phase * s->D[4 * a + j] * proj[j * B + o];
+      }
+      free(proj);
+    }
+    free(pts);
+  }
+}
+
+/* --------------------------------------------------------------------------------
+ * One Taylor (sub-)step t -> t + dt with H frozen: density and v_x from psi(t), field at
+ * the midpoint t + dt/2;  t_0 = psi,  t_k = (-i dt / k) H t_(k-1),  psi <- sum_(k=0..4) t_k.
+ * ------------------------------------------------------------------------------ */
+void oracle_taylor_substep(const oracle_sys *s, double t, double dt, cplx *psi) {
+  long tot = (long)s->n_k * npts(s) * s->n_orb;
+  double *n = NULL, *vx = NULL;
+  if (s->xc == 1) {
+    n = (double *)malloc(sizeof(double) * (size_t)npts(s));
+    vx = (double *)malloc(sizeof(double) * (size_t)npts(s));
+    oracle_density(s, psi, n);
+    oracle_lda_x(s, n, vx);
+  }
+  cplx *term = (cplx *)malloc(sizeof(cplx) * (size_t)tot);
+  cplx *next = (cplx *)malloc(sizeof(cplx) * (size_t)tot);
+  cplx *acc = (cplx *)malloc(sizeof(cplx) * (size_t)tot);
+  memcpy(term, psi, sizeof(cplx) * (size_t)tot);
+  memcpy(acc, psi, sizeof(cplx) * (size_t)tot);
+  for (int k = 1; k <= 4; k++) {
+    oracle_apply_H(s, t + 0.5 * dt, vx, term, next);
+    cplx coef = -I * dt / (double)k;
+    for (long i = 0; i < tot; i++) {
+      term[i] = coef * next[i];
+      acc[i] += term[i];
+    }
+  }
+  memcpy(psi, acc, sizeof(cplx) * (size_t)tot);
+  free(term); free(next); free(acc); free(n); free(vx);
+}
+
+/* --------------------------------------------------------------------------------
+ * Observables of the state psi (recorded at state time t_state) with the field of the
+ * Hamiltonian taken at t_field.  obs = [t_state, norm, E, E_x, o_x, o_y, o_z, f] with
+ *   norm = sum_k w_k sum_i ||phi_ik||^2 h^3,
+ *   E    = sum_k w_k f_i <phi|H(t_field)|phi> - int n v_x + E_x,
+ *   o    = dipole int r n (finite systems) or the current
+ *          J = -(1/Omega) sum_k w_k f_i <phi|(-i grad_h + A)|phi> (periodic cells),
+ *   f    = field component along pol at t_field (E in length gauge, A in velocity gauge).
+ * ------------------------------------------------------------------------------ */
+void oracle_observables(const oracle_sys *s, double t_state, double t_field, const cplx *psi,
+                        double *obs) {
+  long N = npts(s), tot = (long)s->n_k * N * s->n_orb;
+  int B = s->n_orb, M = s->fd_order / 2;
+  double h = s->h, h3 = h * h * h;
+  double *n = (double *)malloc(sizeof(double) * (size_t)N);
+  double *vx = (double *)malloc(sizeof(double) * (size_t)N);
+  oracle_density(s, psi, n);
+  double ex = 0.0, nvx = 0.0;
+  if (s->xc == 1) {
+    ex = oracle_lda_x(s, n, vx);
+    for (long p = 0; p < N; p++) nvx += n[p] * vx[p] * h3;
+  }
+  cplx *hp = (cplx *)malloc(sizeof(cplx) * (size_t)tot);
+  oracle_apply_H(s, t_field, s->xc == 1 ? vx : NULL, psi, hp);
+  double norm = 0.0, eband = 0.0;
+  for (int k = 0; k < s->n_k; k++)
+    for (long p = 0; p < N; p++)
+      for (int o = 0; o < B; o++) {
+        long i = ((long)k * N + p) * B + o;
+        norm += s->kw[k] * creal(conj(psi[i]) * psi[i]) * h3;
+        eband += s->kw[k] * s->occ * creal(conj(psi[i]) * hp[i]) * h3;
+      }
+  double E[3], A[3];
+  oracle_field(s, t_field, E, A);
+  double o3[3] = {0.0, 0.0, 0.0};
+  if (s->bc == 0) {
+    for (int iz = 0; iz < s->nz; iz++)
+      for (int iy = 0; iy < s->ny; iy++)
+        for (int ix = 0; ix < s->nx; ix++) {
+          long p = ((long)iz * s->ny + iy) * s->nx + ix;
+          o3[0] += coord(s, 0, ix) * n[p] * h3;
+          o3[1] += coord(s, 1, iy) * n[p] * h3;
+          o3[2] += coord(s, 2, iz) * n[p] * h3;
+        }
+  } else {
+    double d[5];
+    oracle_fd_gradient_weights(M, d);
+    double omega_cell = (double)s->nx * s->ny * s->nz * h3;
+    double pexp[3] = {0.0, 0.0, 0.0}, nel = 0.0;
+    for (int k = 0; k < s->n_k; k++)
+      for (int iz = 0; iz < s->nz; iz++)
+        for (int iy = 0; iy < s->ny; iy++)
+          for (int ix = 0; ix < s->nx; ix++)
+            for (int o = 0; o < B; o++) {
+              long p = ((long)iz * s->ny + iy) * s->nx + ix;
+              cplx v = psi[((long)k * N + p) * B + o];
+              cplx g[3] = {0.0, 0.0, 0.0};
+              for (int m = 1; m <= M; m++) {
+                g[0] += d[m] * (fetch(s, psi, k, o, ix + m, iy, iz) - fetch(s, psi, k, o, ix - m, iy, iz));
+                g[1] += d[m] * (fetch(s, psi, k, o, ix, iy + m, iz) - fetch(s, psi, k, o, ix, iy - m, iz));
+                g[2] += d[m] * (fetch(s, psi, k, o, ix, iy, iz + m) - fetch(s, psi, k, o, ix, iy, iz - m));
+              }
+              for (int ax = 0; ax < 3; ax++)
+                pexp[ax] += s->kw[k] * s->occ * creal(conj(v) * (-I) * g[ax] / h) * h3;
+              nel += s->kw[k] * s->occ * creal(conj(v) * v) * h3;
+            }
+    for (int ax = 0; ax < 3; ax++) o3[ax] = -(pexp[ax] + A[ax] * nel) / omega_cell;
+  }
+  obs[0] = t_state;
+  obs[1] = norm;
+  obs[2] = eband - nvx + ex;
+  obs[3] = ex;
+  obs[4] = o3[0];
+  obs[5] = o3[1];
+  obs[6] = o3[2];
+  obs[7] = (s->gauge == 2 ? A[0] * s->pol[0] + A[1] * s->pol[1] + A[2] * s->pol[2]
+                          : E[0] * s->pol[0] + E[1] * s->pol[1] + E[2] * s->pol[2]);
+  free(n); free(vx); free(hp);
+}
+
+/* --------------------------------------------------------------------------------
+ * n_steps configured steps of length dt, each split into `substeps` equal Taylor
+ * sub-steps.  Record s holds the observables of psi(t0 + s dt), the state at the start
+ * of step s, with the field of the step's first sub-step (its midpoint).
+ * ------------------------------------------------------------------------------ */
+void oracle_propagate(const oracle_sys *s, double t0, double dt, int n_steps, int substeps,
+                      cplx *psi, double *obs) {
+  double dts = dt / (double)substeps;
+  for (int st = 0; st < n_steps; st++) {
+    double t = t0 + (double)st * dt;
+    if (obs) oracle_observables(s, t, t + 0.5 * dts, psi, obs + 8 * st);
+    for (int j = 0; j < substeps; j++) oracle_taylor_substep(s, t + (double)j * dts, dts, psi);
+  }
+}

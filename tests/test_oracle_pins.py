@@ -1,0 +1,532 @@
+"""Pins of the FP64 oracle against closed forms, invariants and brute force.
+
+Each test checks the oracle against something other than itself: exact rational FD
+weights, an independent weight recursion, the discrete plane-wave spectrum, polynomial
+exactness and the known truncation term, the exact norm and energy identities of the
+truncated Taylor series, free-Gaussian spreading, harmonic-oscillator (Ehrenfest)
+dynamics, a dense brute-force projector matrix, the Dirac exchange coefficient and the
+functional derivative of E_x.
+"""
+import dataclasses
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1912_07921_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _spec(**kw):
+    base = dict(nx=10, ny=12, nz=14, h=0.4, fd_order=4, bc=I.BC_ZERO, n_orb=2, n_atoms=0,
+                projectors=False, wells=False, xc=I.XC_NONE, gauge=I.GAUGE_NONE, amp=0.0)
+    base.update(kw)
+    return I.SystemSpec(**base)
+
+
+def _inputs(spec, vloc=None):
+    inp = I.make_inputs(spec, with_orbitals=False)
+    if vloc is not None:
+        inp.vloc = vloc
+    return inp
+
+
+def _axis(spec, n):
+    return I._axis(n, spec.h, spec.bc)
+
+
+def _grids(spec):
+    x, y, z = _axis(spec, spec.nx), _axis(spec, spec.ny), _axis(spec, spec.nz)
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    return X, Y, Z
+
+
+def _inner(a, b, h):
+    return np.vdot(a, b) * h ** 3
+
+
+# ---------------------------------------------------------------------------------
+# Finite-difference weights
+# ---------------------------------------------------------------------------------
+
+def _read_golden():
+    rows = {}
+    with open(os.path.join(GOLDEN, "fd_weights.txt")) as f:
+        for line in f:
+            if not line.strip() or line.startswith("#"):
+                continue
+            kind, order, *w = line.split()
+            rows[(kind, int(order))] = [Fraction(v) for v in w]
+    return rows
+
+
+def _fornberg(z, x, m):
+    """Weights c[j][k] of the k-th derivative at z from nodes x (Fornberg's recursion,
+    SIAM Review 40 (1998) 685), in exact rational arithmetic."""
+    n = len(x) - 1
+    c = [[Fraction(0)] * (m + 1) for _ in range(n + 1)]
+    c1, c4 = Fraction(1), x[0] - z
+    c[0][0] = Fraction(1)
+    for i in range(1, n + 1):
+        mn = min(i, m)
+        c2, c5, c4 = Fraction(1), c4, x[i] - z
+        for j in range(i):
+            c3 = x[i] - x[j]
+            c2 = c2 * c3
+            if j == i - 1:
+                for k in range(mn, 0, -1):
+                    c[i][k] = c1 * (k * c[i - 1][k - 1] - c5 * c[i - 1][k]) / c2
+                c[i][0] = -c1 * c5 * c[i - 1][0] / c2
+            for k in range(mn, 0, -1):
+                c[j][k] = (c4 * c[j][k] - k * c[j][k - 1]) / c3
+            c[j][0] = c4 * c[j][0] / c3
+        c1 = c2
+    return c
+
+
+@pytest.mark.parametrize("M", [1, 2, 3, 4])
+def test_fd_weights_match_golden_and_fornberg(M):
+    gold = _read_golden()
+    c, d = oracle.fd_weights(M)
+    lap, grad = gold[("lap", 2 * M)], gold[("grad", 2 * M)]
+    np.testing.assert_allclose(c, [float(v) for v in lap], rtol=1e-15, atol=1e-16)
+    np.testing.assert_allclose(d, [float(v) for v in grad], rtol=1e-15, atol=1e-16)
+    nodes = [Fraction(m) for m in range(-M, M + 1)]
+    w = _fornberg(Fraction(0), nodes, 2)
+    for m in range(0, M + 1):
+        assert w[M + m][2] == lap[m]
+        if m > 0:
+            assert w[M + m][1] == grad[m] and w[M - m][1] == -grad[m]
+
+
+# ---------------------------------------------------------------------------------
+# Kinetic operator: plane waves (Bloch), polynomials (finite box)
+# ---------------------------------------------------------------------------------
+
+def _plane_wave_case(fd_order, gauge, seed=5):
+    spec = _spec(bc=I.BC_BLOCH, fd_order=fd_order, n_orb=3, n_k=2, gauge=gauge, amp=0.3,
+                 omega=0.7, pol=(0.3, -0.5, 0.8), seed=seed)
+    inp = _inputs(spec)
+    L = np.array([spec.nx, spec.ny, spec.nz]) * spec.h
+    X, Y, Z = _grids(spec)
+    G = np.array([[0, 0, 0], [1, -2, 3], [-3, 4, 5]])
+    psi = np.empty((2, spec.nz, spec.ny, spec.nx, 3), dtype=np.complex128)
+    qs = np.empty((2, 3, 3))
+    for ik in range(2):
+        for o in range(3):
+            q = inp.kpts[ik] + 2 * np.pi * G[o] / L
+            qs[ik, o] = q
+            psi[ik, ..., o] = np.exp(1j * (q[0] * X + q[1] * Y + q[2] * Z))
+    return spec, inp, psi, qs
+
+
+def _pw_eigen(spec, q, A):
+    M = spec.fd_order // 2
+    c, d = oracle.fd_weights(M)
+    h = spec.h
+    kin = sum((-c[0] - 2 * sum(c[m] * math.cos(m * qa * h) for m in range(1, M + 1))) / (2 * h * h)
+              for qa in q)
+    grad = np.array([2.0 / h * sum(d[m] * math.sin(m * qa * h) for m in range(1, M + 1)) for qa in q])
+    return kin + float(np.dot(A, grad)) + 0.5 * float(np.dot(A, A)), grad
+
+
+@pytest.mark.parametrize("fd_order", [4, 8])
+@pytest.mark.parametrize("gauge", [I.GAUGE_NONE, I.GAUGE_VELOCITY])
+def test_plane_wave_spectrum(fd_order, gauge):
+    spec, inp, psi, qs = _plane_wave_case(fd_order, gauge)
+    o = oracle.System(spec, inp)
+    t = math.pi / (2 * spec.omega)  # sin(omega t) = 1 -> A = amp * pol
+    E, A = o.field(t)
+    if gauge == I.GAUGE_VELOCITY:
+        np.testing.assert_allclose(A, spec.amp * np.array(spec.pol), rtol=1e-14)
+    hpsi = o.apply_H(psi, t=t)
+    for ik in range(2):
+        for j in range(3):
+            lam, _ = _pw_eigen(spec, qs[ik, j], A)
+            np.testing.assert_allclose(hpsi[ik, ..., j], lam * psi[ik, ..., j], rtol=0, atol=1e-11 * max(1, abs(lam)))
+
+
+@pytest.mark.parametrize("fd_order", [4, 8])
+def test_polynomial_exactness_and_truncation_term(fd_order):
+    M = fd_order // 2
+    spec = _spec(nx=2 * M + 3, ny=2 * M + 5, nz=2 * M + 3, h=0.37, fd_order=fd_order, n_orb=1)
+    o = oracle.System(spec, _inputs(spec))
+    X, Y, Z = _grids(spec)
+    p = 2 * M + 1
+    # degree <= 2M+1: exact.  f = x^p + 0.3 x^2 y^(p-2) + y^3 z^2 - 1.7 z^p
+    f = X ** p + 0.3 * X ** 2 * Y ** (p - 2) + Y ** 3 * Z ** 2 - 1.7 * Z ** p
+    lap = (p * (p - 1) * X ** (p - 2) + 0.6 * Y ** (p - 2) + 0.3 * (p - 2) * (p - 3) * X ** 2 * Y ** (p - 4)
+           + 6 * Y * Z ** 2 + 2 * Y ** 3 - 1.7 * p * (p - 1) * Z ** (p - 2))
+    out = o.apply_H(f[None, ..., None])[0, ..., 0]
+    sl = (slice(M, spec.nz - M), slice(M, spec.ny - M), slice(M, spec.nx - M))
+    np.testing.assert_allclose(out[sl], -0.5 * lap[sl], rtol=1e-9, atol=1e-9 * np.abs(lap).max())
+    # degree 2M+2 at the box centre (x = 0): Lap_h x^(2M+2) = 2 h^(2M) sum_m c_m m^(2M+2) != 0
+    q = 2 * M + 2
+    g = X ** q
+    c, _ = oracle.fd_weights(M)
+    expect = 2 * spec.h ** (q - 2) * sum(c[m] * m ** q for m in range(1, M + 1))
+    cz, cy, cx = spec.nz // 2, spec.ny // 2, spec.nx // 2
+    assert abs(X[cz, cy, cx]) < 1e-15
+    got = o.apply_H(g[None, ..., None])[0, cz, cy, cx, 0]
+    assert abs(expect) > 1e-6
+    np.testing.assert_allclose(got.real, -0.5 * expect, rtol=1e-10)
+
+
+# ---------------------------------------------------------------------------------
+# Hermiticity of every term
+# ---------------------------------------------------------------------------------
+
+def _full_case(bc, seed=11):
+    if bc == I.BC_ZERO:
+        spec = _spec(nx=14, ny=13, nz=12, h=0.35, fd_order=8, n_orb=3, n_atoms=3, projectors=True,
+                     wells=True, xc=I.XC_LDA_X, gauge=I.GAUGE_LENGTH, amp=0.05, omega=0.3,
+                     envelope=I.ENV_SIN2, t_total=10.0, seed=seed)
+    else:
+        spec = _spec(nx=12, ny=12, nz=12, h=0.4, fd_order=4, bc=I.BC_BLOCH, n_orb=2, n_k=3,
+                     n_atoms=2, projectors=True, wells=True, xc=I.XC_LDA_X,
+                     gauge=I.GAUGE_VELOCITY, amp=0.2, omega=0.3, pol=(0.2, 0.3, 0.9),
+                     lattice="random", seed=seed)
+    inp = I.make_inputs(spec)
+    if bc == I.BC_BLOCH:
+        inp.pos = inp.pos + np.array([0.4, 2.3, 4.4])  # atoms near the cell faces: wrapped spheres
+    return spec, inp
+
+
+@pytest.mark.parametrize("bc", [I.BC_ZERO, I.BC_BLOCH])
+def test_hermiticity(bc):
+    spec, inp = _full_case(bc)
+    o = oracle.System(spec, inp)
+    phi = I.random_orbitals(spec, 1)
+    psi = I.random_orbitals(spec, 2)
+    vx = o.vx_of(inp.psi0)
+    t = 1.3
+    hphi = o.apply_H(phi, t, vx)
+    hpsi = o.apply_H(psi, t, vx)
+    for ik in range(phi.shape[0]):
+        for j in range(spec.n_orb):
+            a = _inner(phi[ik, ..., j], hpsi[ik, ..., j], spec.h)
+            b = np.conj(_inner(psi[ik, ..., j], hphi[ik, ..., j], spec.h))
+            assert abs(a - b) <= 1e-12 * abs(a)
+
+
+# ---------------------------------------------------------------------------------
+# Projectors: dense brute force and closed-form Gaussian integrals
+# ---------------------------------------------------------------------------------
+
+def _dense_vnl(spec, inp, k, A):
+    """Brute-force N x N matrix sum_aj |b_aj> D_aj <b_aj| h^3 built point by point over
+    every image of every atom in a 3x3x3 block of cells."""
+    N = spec.n_points
+    V = np.zeros((N, N), dtype=np.complex128)
+    L = np.array([spec.nx, spec.ny, spec.nz]) * spec.h
+    x, y, z = (_axis(spec, n) for n in (spec.nx, spec.ny, spec.nz))
+    shifts = [np.zeros(3)] if spec.bc == I.BC_ZERO else [
+        np.array([a, b, c]) * L for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1)]
+    for a in range(inp.pos.shape[0]):
+        # one Bloch projector per (a, j): the images of the sphere add into one vector
+        vec = [np.zeros(N, dtype=np.complex128) for _ in range(4)]
+        for T in shifts:
+            for iz in range(spec.nz):
+                for iy in range(spec.ny):
+                    for ix in range(spec.nx):
+                        u = np.array([x[ix], y[iy], z[iz]]) + T  # point image at r + T
+                        dvec = u - inp.pos[a]
+                        r2 = float(dvec @ dvec)
+                        if r2 > spec.r_cut ** 2:
+                            continue
+                        g = math.exp(-r2 / (2 * spec.r_c ** 2))
+                        # psi(u) = exp(i k.T) psi(r); gauge factor exp(i A.d)
+                        ph = np.exp(1j * (k @ T + A @ dvec))
+                        p = (iz * spec.ny + iy) * spec.nx + ix
+                        for j, b in enumerate((g, dvec[0] * g, dvec[1] * g, dvec[2] * g)):
+                            vec[j][p] += b * ph
+        for j in range(4):
+            V += inp.D[a, j] * spec.h ** 3 * np.outer(np.conj(vec[j]), vec[j])
+    return V
+
+
+@pytest.mark.parametrize("bc", [I.BC_ZERO, I.BC_BLOCH])
+def test_projectors_dense_bruteforce(bc):
+    if bc == I.BC_ZERO:
+        spec = _spec(nx=8, ny=8, nz=8, h=0.45, n_orb=2, n_atoms=2, projectors=True, seed=3)
+    else:
+        spec = _spec(nx=8, ny=8, nz=8, h=0.45, bc=I.BC_BLOCH, n_orb=2, n_k=2, n_atoms=2,
+                     projectors=True, gauge=I.GAUGE_VELOCITY, amp=0.4, omega=0.5,
+                     pol=(0.6, 0.0, 0.8), seed=3)
+    inp = I.make_inputs(spec)
+    if bc == I.BC_BLOCH:
+        inp.pos = np.array([[0.1, 0.2, 3.4], [3.3, 1.7, 0.05]])  # spheres cross cell faces
+    t = 0.9
+    o_with = oracle.System(spec, inp)
+    o_without = oracle.System(spec, inp, projectors=False)
+    _, A = o_with.field(t)
+    psi = I.random_orbitals(spec, 9)
+    vnl = o_with.apply_H(psi, t) - o_without.apply_H(psi, t)
+    for ik in range(psi.shape[0]):
+        V = _dense_vnl(spec, inp, inp.kpts[ik], A)
+        assert np.allclose(V, V.conj().T, atol=1e-14)
+        assert np.linalg.matrix_rank(V, tol=1e-10) <= 4 * inp.pos.shape[0]
+        for j in range(spec.n_orb):
+            ref = V @ psi[ik, ..., j].reshape(-1)
+            np.testing.assert_allclose(vnl[ik, ..., j].reshape(-1), ref, rtol=0,
+                                       atol=1e-12 * np.abs(ref).max())
+
+
+def test_projector_gaussian_integrals():
+    """<b_1|b_1> = int_(r<=R) g^2 and <b_2|b_2> = int_(r<=R) x^2 g^2, radial integrals
+    over the cut sphere (the full-space values are pi^(3/2) r_c^3 and pi^(3/2) r_c^5/2);
+    the grid sum at h = 0.1 matches them to better than 1e-4."""
+    from scipy.integrate import quad
+    spec = _spec(nx=41, ny=41, nz=41, h=0.1, n_orb=1, n_atoms=1, projectors=True)
+    inp = I.make_inputs(spec, with_orbitals=False)
+    inp.pos = np.zeros((1, 3))
+    X, Y, Z = _grids(spec)
+    g = np.exp(-(X ** 2 + Y ** 2 + Z ** 2) / (2 * spec.r_c ** 2))
+    g[(X ** 2 + Y ** 2 + Z ** 2) > spec.r_cut ** 2] = 0.0
+    a2, R = spec.r_c ** 2, spec.r_cut
+    i0 = quad(lambda r: 4 * math.pi * r * r * math.exp(-r * r / a2), 0, R, epsabs=0, epsrel=1e-13)[0]
+    i2 = quad(lambda r: 4 * math.pi / 3 * r ** 4 * math.exp(-r * r / a2), 0, R, epsabs=0, epsrel=1e-13)[0]
+    assert abs(i0 / (math.pi ** 1.5 * spec.r_c ** 3) - 1) < 1e-4
+    assert abs(i2 / (math.pi ** 1.5 * spec.r_c ** 5 / 2) - 1) < 1e-3
+    for j, (b, exact) in enumerate([(g, i0), (X * g, i2)]):
+        inp.D = np.zeros((1, 4))
+        inp.D[0, j] = 1.0
+        o1 = oracle.System(spec, inp)
+        o0 = oracle.System(spec, inp, projectors=False)
+        psi = b[None, ..., None].astype(np.complex128)
+        out = (o1.apply_H(psi) - o0.apply_H(psi))[0, ..., 0]
+        # V_NL b = b <b|b>
+        ratio = np.vdot(b, out).real / np.vdot(b, b).real
+        assert abs(ratio / exact - 1) < 1e-4, (ratio, exact)
+    assert o1.sphere_count(0) == int(((X ** 2 + Y ** 2 + Z ** 2) <= spec.r_cut ** 2).sum())
+
+
+# ---------------------------------------------------------------------------------
+# Taylor step: eigenvector, exact norm and energy identities
+# ---------------------------------------------------------------------------------
+
+def test_taylor_on_eigenvector():
+    spec, inp, psi, qs = _plane_wave_case(8, I.GAUGE_NONE)
+    o = oracle.System(spec, inp)
+    dt = 0.03
+    out = o.taylor_substep(psi, 0.0, dt)
+    for ik in range(2):
+        for j in range(3):
+            lam, _ = _pw_eigen(spec, qs[ik, j], np.zeros(3))
+            z = -1j * dt * lam
+            R = 1 + z + z ** 2 / 2 + z ** 3 / 6 + z ** 4 / 24
+            np.testing.assert_allclose(out[ik, ..., j], R * psi[ik, ..., j], rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("bc", [I.BC_ZERO, I.BC_BLOCH])
+def test_norm_and_energy_identities(bc):
+    """For Hermitian H frozen over the step, |R(-i tau x)|^2 = 1 - x^6/72 + x^8/576, so
+    ||psi'||^2 = ||psi||^2 - tau^6/72 ||H^3 psi||^2 + tau^8/576 ||H^4 psi||^2 and
+    <psi'|H|psi'> = <H> - tau^6/72 <H^3psi|H|H^3psi> + tau^8/576 <H^4psi|H|H^4psi>."""
+    spec, inp = _full_case(bc)
+    o = oracle.System(spec, inp)
+    psi = I.random_orbitals(spec, 4) * 0.05
+    t, tau = 0.7, 0.02
+    vx = o.vx_of(psi)
+    out = o.taylor_substep(psi, t, tau)
+    H = lambda v: o.apply_H(v, t + tau / 2, vx)
+    h1 = H(psi)
+    h2 = H(h1)
+    h3 = H(h2)
+    h4 = H(h3)
+    h3h, h4h = H(h3), H(h4)
+    hout = H(out)
+    for ik in range(psi.shape[0]):
+        for j in range(spec.n_orb):
+            s = (ik, Ellipsis, j)
+            n0 = _inner(psi[s], psi[s], spec.h).real
+            n1 = _inner(out[s], out[s], spec.h).real
+            c6 = _inner(h3[s], h3[s], spec.h).real
+            c8 = _inner(h4[s], h4[s], spec.h).real
+            pred = n0 - tau ** 6 / 72 * c6 + tau ** 8 / 576 * c8
+            assert abs(n1 - n0) > 1e-6 * n0  # the high-order terms are visible
+            assert abs(n1 - pred) <= 1e-12 * n0
+            e0 = _inner(psi[s], h1[s], spec.h).real
+            e1 = _inner(out[s], hout[s], spec.h).real
+            epred = (e0 - tau ** 6 / 72 * _inner(h3[s], h3h[s], spec.h).real
+                     + tau ** 8 / 576 * _inner(h4[s], h4h[s], spec.h).real)
+            assert abs(e1 - epred) <= 1e-11 * abs(e0)
+
+
+# ---------------------------------------------------------------------------------
+# Dynamics with closed forms: free Gaussian, harmonic oscillator (Ehrenfest)
+# ---------------------------------------------------------------------------------
+
+def test_free_gaussian_spreading():
+    a = 1.0
+    spec = _spec(nx=47, ny=47, nz=47, h=0.25, fd_order=8, n_orb=1)
+    o = oracle.System(spec, _inputs(spec))
+    X, Y, Z = _grids(spec)
+    psi = np.exp(-(X ** 2 + Y ** 2 + Z ** 2) / (2 * a * a)).astype(np.complex128)
+    psi /= math.sqrt(np.vdot(psi, psi).real * spec.h ** 3)
+    psi = psi[None, ..., None]
+    dt, nst = 0.01, 100
+    out, _ = o.propagate(psi, 0.0, dt, nst, 1, record=False)
+    n = o.density(out)
+    t = dt * nst
+    expect = a * a / 2 * (1 + t * t / a ** 4)
+    for C in (X, Y, Z):
+        got = (C ** 2 * n).sum() / n.sum()
+        assert abs(got / expect - 1) < 2e-6, (got, expect)
+
+
+def _ho_case(E0=0.0, omega=0.0):
+    w0, z0 = 1.0, 0.5
+    spec = _spec(nx=41, ny=41, nz=49, h=0.25, fd_order=8, n_orb=1,
+                 gauge=I.GAUGE_LENGTH if E0 else I.GAUGE_NONE, amp=E0, omega=omega)
+    X, Y, Z = _grids(spec)
+    v = 0.5 * w0 ** 2 * (X ** 2 + Y ** 2 + Z ** 2)
+    o = oracle.System(spec, _inputs(spec, vloc=v))
+    psi = np.exp(-w0 * (X ** 2 + Y ** 2 + (Z - z0) ** 2) / 2).astype(np.complex128)
+    psi /= math.sqrt(np.vdot(psi, psi).real * spec.h ** 3)
+    return spec, o, psi[None, ..., None], w0, z0
+
+
+def test_harmonic_oscillator_coherent_state():
+    spec, o, psi, w0, z0 = _ho_case()
+    dt, nst = 0.01, 150
+    _, obs = o.propagate(psi, 0.0, dt, nst, 1)
+    t = obs[:, 0]
+    zt = obs[:, 6] / (spec.occ * obs[:, 1])
+    np.testing.assert_allclose(zt, z0 * np.cos(w0 * t), atol=2e-6)
+    np.testing.assert_allclose(obs[:, 4:6], 0.0, atol=1e-12)
+    np.testing.assert_allclose(obs[:, 1], 1.0, atol=1e-9)
+
+
+def test_harmonic_oscillator_driven_ehrenfest():
+    """Quadratic V: <z> obeys z'' = -w0^2 z - E(t) exactly (charge -1, +E.r coupling)."""
+    E0, om = 0.05, 0.6
+    spec, o, psi, w0, z0 = _ho_case(E0, om)
+    dt, nst = 0.01, 150
+    _, obs = o.propagate(psi, 0.0, dt, nst, 1)
+    t = obs[:, 0]
+    zt = obs[:, 6] / (spec.occ * obs[:, 1])
+    exact = z0 * np.cos(w0 * t) + E0 / (w0 ** 2 - om ** 2) * (om / w0 * np.sin(w0 * t) - np.sin(om * t))
+    np.testing.assert_allclose(zt, exact, atol=3e-6)
+    # the field record is E_z at the first sub-step midpoint
+    np.testing.assert_allclose(obs[:, 7], E0 * np.sin(om * (t + dt / 2)), rtol=1e-13, atol=1e-16)
+    # two sub-steps of dt/2 per configured step: same trajectory, field at t + dt/4
+    _, obs2 = o.propagate(psi, 0.0, 2 * dt, nst // 2, 2)
+    t2 = obs2[:, 0]
+    np.testing.assert_allclose(t2, t[::2], rtol=1e-14)
+    z2 = obs2[:, 6] / (spec.occ * obs2[:, 1])
+    exact2 = z0 * np.cos(w0 * t2) + E0 / (w0 ** 2 - om ** 2) * (om / w0 * np.sin(w0 * t2) - np.sin(om * t2))
+    np.testing.assert_allclose(z2, exact2, atol=3e-6)
+    np.testing.assert_allclose(obs2[:, 7], E0 * np.sin(om * (t2 + dt / 2)), rtol=1e-13, atol=1e-16)
+
+
+def test_sin2_envelope_length_gauge():
+    T = 40.0
+    spec = _spec(gauge=I.GAUGE_LENGTH, amp=0.005, omega=0.057, envelope=I.ENV_SIN2, t_total=T)
+    o = oracle.System(spec, _inputs(spec))
+    for t, env in ((0.0, 0.0), (T / 2, 1.0), (T / 4, 0.5), (T, 0.0), (T + 1, 0.0)):
+        E, A = o.field(t)
+        np.testing.assert_allclose(E, [0, 0, spec.amp * env * math.sin(spec.omega * t)], atol=1e-18)
+        assert np.all(A == 0)
+
+
+# ---------------------------------------------------------------------------------
+# Field, LDA exchange, density, dipole, energy bookkeeping
+# ---------------------------------------------------------------------------------
+
+def test_velocity_gauge_field_is_minus_dA_dt():
+    spec = _spec(gauge=I.GAUGE_VELOCITY, amp=0.2, omega=0.03, envelope=I.ENV_SIN2, t_total=80.0,
+                 pol=(0.0, 0.6, 0.8))
+    o = oracle.System(spec, _inputs(spec))
+    for t in (3.0, 17.5, 41.0, 79.0):
+        eps = 1e-5
+        _, Ap = o.field(t + eps)
+        _, Am = o.field(t - eps)
+        E, _ = o.field(t)
+        np.testing.assert_allclose(E, -(Ap - Am) / (2 * eps), rtol=1e-8, atol=1e-13)
+    E, A = o.field(100.0)
+    assert np.all(A == 0) and np.all(E == 0)
+
+
+def test_lda_exchange_dirac_coefficient_and_derivative():
+    spec = _spec(nx=6, ny=5, nz=4, xc=I.XC_LDA_X)
+    o = oracle.System(spec, _inputs(spec))
+    n0 = 0.37
+    n = np.full(spec.n_points, n0)
+    ex, vx = o.lda_x(n)
+    C_x = 0.7385587663820224  # Dirac exchange constant (3/4)(3/pi)^(1/3)
+    vol = spec.n_points * spec.h ** 3
+    np.testing.assert_allclose(ex, -C_x * n0 ** (4 / 3) * vol, rtol=1e-14)
+    rng = np.random.default_rng(3)
+    n = rng.uniform(0.01, 1.0, spec.n_points)
+    _, vx = o.lda_x(n)
+    for p in (0, 7, 33, 100):
+        d = 1e-5
+        npl, nmi = n.copy(), n.copy()
+        npl[p] += d
+        nmi[p] -= d
+        der = (o.lda_x(npl)[0] - o.lda_x(nmi)[0]) / (2 * d * spec.h ** 3)
+        np.testing.assert_allclose(der, vx[p], rtol=1e-8)
+
+
+def test_density_and_dipole_of_shifted_gaussian():
+    spec = _spec(nx=41, ny=41, nz=41, h=0.3, n_orb=1, xc=I.XC_NONE)
+    o = oracle.System(spec, _inputs(spec))
+    X, Y, Z = _grids(spec)
+    c = np.array([0.7, -1.1, 0.4])
+    psi = np.exp(-((X - c[0]) ** 2 + (Y - c[1]) ** 2 + (Z - c[2]) ** 2) / 2).astype(np.complex128)
+    psi /= math.sqrt(np.vdot(psi, psi).real * spec.h ** 3)
+    obs = o.observables(psi[None, ..., None], 0.0, 0.0)
+    np.testing.assert_allclose(obs[1], 1.0, rtol=1e-13)
+    np.testing.assert_allclose(obs[4:7], spec.occ * c, rtol=1e-9)
+    n = o.density(psi[None, ..., None])
+    np.testing.assert_allclose(n.sum() * spec.h ** 3, spec.occ, rtol=1e-13)
+
+
+def test_energy_and_current_of_plane_waves_with_exchange():
+    """Plane waves have uniform density n0, so every term is closed form:
+    E = sum f (lam + v_x(n0)) - n0 v_x(n0) V + E_x,   J = -(1/V) sum f (g(q) + A)."""
+    spec, inp, psi, qs = _plane_wave_case(4, I.GAUGE_VELOCITY)
+    spec = dataclasses.replace(spec, xc=I.XC_LDA_X)
+    o = oracle.System(spec, inp)
+    vol = spec.n_points * spec.h ** 3
+    psi = psi / math.sqrt(vol)
+    t = 0.4
+    obs = o.observables(psi, 0.0, t)
+    _, A = o.field(t)
+    n0 = spec.occ * spec.n_orb * inp.kw.sum() / vol
+    vx0 = -(3 * n0 / math.pi) ** (1 / 3)
+    ex = -0.75 * (3 * n0 / math.pi) ** (1 / 3) * n0 * vol
+    eb, J = 0.0, np.zeros(3)
+    for ik in range(2):
+        for j in range(3):
+            lam, g = _pw_eigen(spec, qs[ik, j], A)
+            eb += inp.kw[ik] * spec.occ * (lam + vx0)
+            J += inp.kw[ik] * spec.occ * (g + A)
+    np.testing.assert_allclose(obs[3], ex, rtol=1e-13)
+    np.testing.assert_allclose(obs[2], eb - n0 * vx0 * vol + ex, rtol=1e-12)
+    np.testing.assert_allclose(obs[4:7], -J / vol, rtol=1e-12, atol=1e-15)
+
+
+def test_energy_conservation_at_zero_field():
+    """Zero field.  Without the exchange term H is fixed and the Taylor-4 energy error per
+    step is O(dt^6) (norm/energy identities), so over a fixed time the drift falls >= 16x
+    when dt halves.  With the exchange term frozen over each step the scheme is
+    first order in the density, so the drift falls ~2x when dt halves."""
+    spec = _spec(nx=16, ny=16, nz=16, h=0.35, fd_order=4, n_orb=2, n_atoms=2, wells=True,
+                 xc=I.XC_LDA_X, seed=6)
+    inp = I.make_inputs(spec)
+    for xc, factor in ((I.XC_NONE, 16.0), (I.XC_LDA_X, 1.8)):
+        o = oracle.System(spec, inp, xc=xc)
+        drifts = []
+        for dt, nst in ((0.02, 20), (0.01, 40)):
+            _, obs = o.propagate(inp.psi0, 0.0, dt, nst, 1)
+            psi_end, _ = o.propagate(inp.psi0, 0.0, dt, nst, 1, record=False)
+            e_end = o.observables(psi_end, dt * nst, dt * nst)[2]
+            drifts.append(abs(e_end - obs[0, 2]))
+        assert drifts[0] < 2e-3 * abs(obs[0, 2])
+        assert drifts[1] * factor < drifts[0], (xc, drifts)
