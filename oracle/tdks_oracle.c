@@ -59,6 +59,19 @@ typedef struct {
 
 static long npts(const oracle_sys *s) { return (long)s->nx * s->ny * s->nz; }
 
+/* Compensated (Kahan) running sum.  The grid integrals below add up to ~10^8 terms; a
+ * plain running sum of that many positive terms drifts by ~1e-11 relative, which would
+ * swamp the 1e-12 parity tolerance, while the compensated sum stays at rounding level.
+ * The paper defines these quantities as integrals; the order of summation is not part
+ * of the method. */
+typedef struct { double s, c; } ksum;
+static void kadd(ksum *k, double x) {
+  double y = x - k->c;
+  double t = k->s + y;
+  k->c = (t - k->s) - y;
+  k->s = t;
+}
+
 /* --------------------------------------------------------------------------------
  * Finite-difference weights.  Central differences of order 2M on a uniform grid; the
  * paper takes its weights from its Ref. (PRB 78, 075109) without printing them.  Closed
@@ -164,13 +177,14 @@ void oracle_density(const oracle_sys *s, const cplx *psi, double *n) {
  * ------------------------------------------------------------------------------ */
 double oracle_lda_x(const oracle_sys *s, const double *n, double *vx) {
   long N = npts(s);
-  double h3 = s->h * s->h * s->h, ex = 0.0;
+  double h3 = s->h * s->h * s->h;
+  ksum ex = {0.0, 0.0};
   for (long p = 0; p < N; p++) {
     double c = cbrt(3.0 * n[p] / M_PI);
     if (vx) vx[p] = -c;
-    ex += n[p] * (-0.75 * c) * h3;
+    kadd(&ex, n[p] * (-0.75 * c) * h3);
   }
-  return ex;
+  return ex.s;
 }
 
 /* --------------------------------------------------------------------------------
@@ -373,38 +387,41 @@ void oracle_observables(const oracle_sys *s, double t_state, double t_field, con
   double *n = (double *)malloc(sizeof(double) * (size_t)N);
   double *vx = (double *)malloc(sizeof(double) * (size_t)N);
   oracle_density(s, psi, n);
-  double ex = 0.0, nvx = 0.0;
+  double ex = 0.0;
+  ksum nvx = {0.0, 0.0};
   if (s->xc == 1) {
     ex = oracle_lda_x(s, n, vx);
-    for (long p = 0; p < N; p++) nvx += n[p] * vx[p] * h3;
+    for (long p = 0; p < N; p++) kadd(&nvx, n[p] * vx[p] * h3);
   }
   cplx *hp = (cplx *)malloc(sizeof(cplx) * (size_t)tot);
   oracle_apply_H(s, t_field, s->xc == 1 ? vx : NULL, psi, hp);
-  double norm = 0.0, eband = 0.0;
+  ksum norm = {0.0, 0.0}, eband = {0.0, 0.0};
   for (int k = 0; k < s->n_k; k++)
     for (long p = 0; p < N; p++)
       for (int o = 0; o < B; o++) {
         long i = ((long)k * N + p) * B + o;
-        norm += s->kw[k] * creal(conj(psi[i]) * psi[i]) * h3;
-        eband += s->kw[k] * s->occ * creal(conj(psi[i]) * hp[i]) * h3;
+        kadd(&norm, s->kw[k] * creal(conj(psi[i]) * psi[i]) * h3);
+        kadd(&eband, s->kw[k] * s->occ * creal(conj(psi[i]) * hp[i]) * h3);
       }
   double E[3], A[3];
   oracle_field(s, t_field, E, A);
   double o3[3] = {0.0, 0.0, 0.0};
   if (s->bc == 0) {
+    ksum dip[3] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
     for (int iz = 0; iz < s->nz; iz++)
       for (int iy = 0; iy < s->ny; iy++)
         for (int ix = 0; ix < s->nx; ix++) {
           long p = ((long)iz * s->ny + iy) * s->nx + ix;
-          o3[0] += coord(s, 0, ix) * n[p] * h3;
-          o3[1] += coord(s, 1, iy) * n[p] * h3;
-          o3[2] += coord(s, 2, iz) * n[p] * h3;
+          kadd(&dip[0], coord(s, 0, ix) * n[p] * h3);
+          kadd(&dip[1], coord(s, 1, iy) * n[p] * h3);
+          kadd(&dip[2], coord(s, 2, iz) * n[p] * h3);
         }
+    for (int ax = 0; ax < 3; ax++) o3[ax] = dip[ax].s;
   } else {
     double d[5];
     oracle_fd_gradient_weights(M, d);
     double omega_cell = (double)s->nx * s->ny * s->nz * h3;
-    double pexp[3] = {0.0, 0.0, 0.0}, nel = 0.0;
+    ksum pexp[3] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}}, nel = {0.0, 0.0};
     for (int k = 0; k < s->n_k; k++)
       for (int iz = 0; iz < s->nz; iz++)
         for (int iy = 0; iy < s->ny; iy++)
@@ -419,14 +436,14 @@ void oracle_observables(const oracle_sys *s, double t_state, double t_field, con
                 g[2] += d[m] * (fetch(s, psi, k, o, ix, iy, iz + m) - fetch(s, psi, k, o, ix, iy, iz - m));
               }
               for (int ax = 0; ax < 3; ax++)
-                pexp[ax] += s->kw[k] * s->occ * creal(conj(v) * (-I) * g[ax] / h) * h3;
-              nel += s->kw[k] * s->occ * creal(conj(v) * v) * h3;
+                kadd(&pexp[ax], s->kw[k] * s->occ * creal(conj(v) * (-I) * g[ax] / h) * h3);
+              kadd(&nel, s->kw[k] * s->occ * creal(conj(v) * v) * h3);
             }
-    for (int ax = 0; ax < 3; ax++) o3[ax] = -(pexp[ax] + A[ax] * nel) / omega_cell;
+    for (int ax = 0; ax < 3; ax++) o3[ax] = -(pexp[ax].s + A[ax] * nel.s) / omega_cell;
   }
   obs[0] = t_state;
-  obs[1] = norm;
-  obs[2] = eband - nvx + ex;
+  obs[1] = norm.s;
+  obs[2] = eband.s - nvx.s + ex;
   obs[3] = ex;
   obs[4] = o3[0];
   obs[5] = o3[1];
