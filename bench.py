@@ -1,0 +1,341 @@
+"""Benchmark: orbital-gridpoint updates per second of the real-time TDDFT step.
+
+Workload (one "step" = one configured time step of the whole hot path): the medium
+molecule, 96^3 grid, h = 0.25 bohr, 8th-order FD (25-point star), 64 orbitals, 16 atoms
+with Gaussian wells and 4 Kleinman-Bylander projectors each, sin^2 laser pulse, LDA
+exchange rebuilt from the density every sub-step, dt = 0.05 split into 4 Taylor-4
+sub-steps, FP64 density/norm/energy/dipole record every step.  Default precision is the
+mixed path (complex64 H psi and Taylor terms, complex128 state and FP64 reductions); the
+same step in complex128 is measured alongside.  An update is one orbital at one grid
+point advanced by one configured step.
+
+Timing: W warm-up steps, then K steps between CUDA events on the system's stream, with
+a device synchronise (and a barrier across ranks) on both sides; the working set
+(~2.3 GB) is far larger than L2, so no flush is needed.  Multi-GPU runs are independent
+replicas (weak scaling); the time is the maximum over ranks.
+
+``--impl reference`` times the FP64 CPU oracle on the host cores on a bounded sample of
+the same workload (a subset of the orbitals) and reports the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "H.psi orbital-gridpoint updates/s (medium molecule, Taylor-4 step)"
+UNIT = "updates/s"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            for k in ("hbm_gbs", "hbm_GBps", "hbm"):
+                if k in d:
+                    return float(d[k]), "measured"
+        except Exception:
+            pass
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(2)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _sweep_bytes(spec, sysm) -> float:
+    """Algorithmic HBM bytes of the 4 stencil sweeps of one Taylor sub-step.
+
+    Per (point, padded orbital): sweep 1 reads the complex128 state and writes t1;
+    sweeps 2-3 read t_(k-1) and write t_k; sweep 4 reads t3, the state, t1, t2 and
+    writes the state; plus per point V_eff (each sweep) and one density word per batch.
+    """
+    bs, nb, eb, _ = sysm.layout()
+    vals = spec.n_points * nb * bs * sysm.n_k
+    st = 16.0
+    per_val = (st + eb) + 2 * (eb + eb) + (eb + st + eb + eb + st)
+    veff = 4 * spec.n_points * (4 if eb == 8 else 8)
+    dens = spec.n_points * nb * sysm.n_k * 8
+    return vals * per_val + veff + dens
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1912_07921_gb300 import inputs as I
+    from paper_1912_07921_gb300.system import System
+    import __graft_entry__
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    prec = I.PREC_C64 if args.prec == "c64" else I.PREC_C128
+    spec = I.medium_molecule(prec=prec)
+    inp = I.make_inputs(spec)
+    stream = torch.cuda.Stream()
+    sysm = System(spec, inp, stream=stream.cuda_stream)
+    subs = spec.substeps
+    dt = spec.dt
+    upd_per_step = spec.n_points * spec.n_orb
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    t = 0.0
+    sysm.propagate(t, dt, args.warmup, subs)
+    t += args.warmup * dt
+    barrier()
+    sysm.set_profiling(True)
+    sysm.kernel_time(0), sysm.kernel_time(1), sysm.kernel_time(2)
+    l0 = sysm.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local_rank) as clk:
+        barrier()
+        ev0.record(stream)
+        sysm.propagate(t, dt, args.steps, subs)
+        ev1.record(stream)
+        barrier()
+    t += args.steps * dt
+    ms = ev0.elapsed_time(ev1)
+    launches = sysm.launch_count() - l0
+    sweep_ms, sweep_n = sysm.kernel_time(0)
+    gath_ms, gath_n = sysm.kernel_time(1)
+    aux_ms, aux_n = sysm.kernel_time(2)
+    sysm.set_profiling(False)
+    rec = sysm.reductions(sysm.step_count() - 1, 1)[0]
+    if dist is not None:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+
+    # end to end through the C interface with host buffers: upload the orbitals from
+    # pinned memory, one configured step, read the step's observable record back
+    psi_host = torch.from_numpy(inp.psi0.view(np.float64)).pin_memory()
+    h2d = psi_host.numel() * 8
+    e2e_steps = max(3, min(args.steps, 20))
+    barrier()
+    w0 = time.perf_counter()
+    for i in range(e2e_steps):
+        sysm.set_orbitals_ptr(psi_host.data_ptr())
+        sysm.propagate(t, dt, 1, subs)
+        r = sysm.reductions(sysm.step_count() - 1, 1)
+        t += dt
+    barrier()
+    e2e_s = time.perf_counter() - w0
+    if dist is not None:
+        tt = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+
+    out = None
+    if rank == 0:
+        peak, peak_kind = _peaks()
+        bytes_sub = _sweep_bytes(spec, sysm)
+        per_launch_bytes = bytes_sub / 4.0
+        avg_launch_s = (sweep_ms / 1e3) / max(sweep_n, 1)
+        achieved = per_launch_bytes / avg_launch_s / 1e9
+        value = upd_per_step * args.steps * world / (ms / 1e3)
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64 terms + f64 state/reductions" if prec == I.PREC_C64 else "c128 (f64)",
+            "data": "synthetic (seeded molecule: Gaussian orbitals, wells, KB projectors)",
+            "config": {"workload": "medium molecule 96^3 h=0.25 order-8 FD, 64 orbitals, 16 atoms x 4 KB "
+                                   "projectors, sin^2 pulse, LDA exchange, dt=0.05 as 4 Taylor-4 sub-steps",
+                       "grid": [spec.nx, spec.ny, spec.nz], "n_orb": spec.n_orb, "substeps": subs,
+                       "precision": args.prec, "l2": "working set > L2 (state 906 MB + terms), no flush",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "kernel": "taylor stencil sweep (4 per sub-step)",
+                         "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "bytes_per_launch": per_launch_bytes, "avg_launch_us": avg_launch_s * 1e6},
+            "kernel_ms": {"sweep": sweep_ms, "sweep_launches": sweep_n, "gather": gath_ms,
+                          "gather_launches": gath_n, "density_lda_finalize": aux_ms, "aux_launches": aux_n},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "e2e": {"value": upd_per_step * e2e_steps * world / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8 * 8},
+            "last_record": {"t": rec[0], "norm": rec[1], "energy": rec[2], "dipole": list(rec[4:7])},
+        }
+    sysm.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return out
+
+
+def run_c128_side(args):
+    """The same step fully in complex128 (the FP64 path), fewer steps."""
+    import torch
+    from paper_1912_07921_gb300 import inputs as I
+    from paper_1912_07921_gb300.system import System
+    spec = I.medium_molecule(prec=I.PREC_C128)
+    inp = I.make_inputs(spec)
+    stream = torch.cuda.Stream()
+    sysm = System(spec, inp, stream=stream.cuda_stream)
+    sysm.propagate(0.0, spec.dt, 2, spec.substeps)
+    torch.cuda.synchronize()
+    k = max(2, args.steps // 20)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sysm.propagate(0.1, spec.dt, k, spec.substeps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    sysm.close()
+    return {"value": spec.n_points * spec.n_orb * k / (ms / 1e3), "unit": UNIT, "steps": k,
+            "ms_per_step": ms / k}
+
+
+def cpu_baseline(n_orb_sample: int):
+    """The FP64 oracle as it stands, on the host cores, on a bounded sample: one
+    configured step (4 sub-steps plus the observable record) of the medium molecule with
+    n_orb_sample of its 64 orbitals."""
+    import oracle
+    from paper_1912_07921_gb300 import inputs as I
+    spec = I.medium_molecule(prec=I.PREC_C128)
+    inp = I.make_inputs(spec)
+    inp.psi0 = np.ascontiguousarray(inp.psi0[..., :n_orb_sample])
+    import dataclasses
+    sspec = dataclasses.replace(spec, n_orb=n_orb_sample)
+    o = oracle.System(sspec, inp)
+    cores = len(os.sched_getaffinity(0))
+    t0 = time.perf_counter()
+    o.propagate(inp.psi0, 0.0, spec.dt, 1, spec.substeps)
+    s = time.perf_counter() - t0
+    return {"value": spec.n_points * n_orb_sample / s, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"1 configured step (4 sub-steps + record) of the medium molecule with "
+                      f"{n_orb_sample} of 64 orbitals, {s:.1f} s"}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return None
+    import __graft_entry__
+    __graft_entry__.build()
+    import oracle
+    from paper_1912_07921_gb300 import inputs as I
+    import dataclasses
+    spec = I.medium_molecule(prec=I.PREC_C128)
+    inp = I.make_inputs(spec)
+    n_s = 2
+    sspec = dataclasses.replace(spec, n_orb=n_s)
+    psi = np.ascontiguousarray(inp.psi0[..., :n_s])
+    o = oracle.System(sspec, inp)
+    for _ in range(args.warmup):
+        psi, _ = o.propagate(psi, 0.0, spec.dt, 1, spec.substeps)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        psi, _ = o.propagate(psi, i * spec.dt, spec.dt, 1, spec.substeps)
+    s = time.perf_counter() - t0
+    v = spec.n_points * n_s * args.steps / s
+    cores = len(os.sched_getaffinity(0))
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": s / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded molecule)",
+            "config": {"workload": "medium molecule 96^3 h=0.25 order-8 FD, 16 atoms x 4 KB projectors, "
+                                   "dt=0.05 as 4 Taylor-4 sub-steps", "precision": "c128 oracle"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{n_s} of 64 orbitals per step, {args.steps} steps"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="c64", choices=["c64", "c128"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-c128", action="store_true", help="skip the complex128 side measurement")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank)
+        if out is not None:
+            print(json.dumps(out))
+        return
+    import __graft_entry__
+    __graft_entry__.build()
+    out = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        if not args.no_c128 and args.prec == "c64" and world == 1:
+            out["c128_path"] = run_c128_side(args)
+        if not args.no_cpu and world == 1:
+            out["cpu_baseline"] = cpu_baseline(8)
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

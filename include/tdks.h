@@ -1,0 +1,206 @@
+/*
+ * tdks.h — C interface of the GB300 real-time TDDFT propagation library.
+ *
+ * The library integrates the time-dependent Kohn-Sham equations in the form the paper
+ * states them (arXiv:1912.07921, Sec. "New propagators for real-time TDDFT", first three
+ * equations):  d phi_i / dt = -i H[n(t), t] phi_i,  phi(t0) = phi^0,  i = 1..N_orb,
+ * in the adiabatic approximation (the exchange potential depends on n(t) only).
+ *
+ * H = -1/2 Lap_h + V_loc(r) + v_x[n](r) + E(t).r  (length gauge, finite box), or
+ * H = 1/2 (-i grad_h + A(t))^2 + V_loc + v_x[n]    (velocity gauge, periodic cell,
+ *     E = -dA/dt, Sec. "Conductivities"),
+ * plus Kleinman-Bylander projectors V_NL = sum_aj |beta_aj> D_aj <beta_aj|.
+ * Lap_h and grad_h are central finite differences of order 4 or 8 on a uniform grid
+ * (Sec. "Maxwell ... coupling" and Sec. "Periodic systems"); v_x is LDA exchange
+ * (Sec. "Local domains", E_xc = int n e_xc(n)); orbitals are doubly occupied by default
+ * (closed shells, Sec. "t-SURFF").  The exponential exp(-i dt H) is a 4th-order Taylor
+ * series with H frozen over each sub-step: t_0 = psi, t_k = (-i dt/k) H t_(k-1),
+ * psi(t+dt) = t_0 + ... + t_4; the density is rebuilt and the field is taken at the
+ * sub-step midpoint.
+ *
+ * Conventions
+ *   - Every function returns a tdks_status and never aborts; tdks_last_error() returns a
+ *     thread-local message for the last failure on the calling thread.
+ *   - The system object owns all its device memory.  Host arrays passed in are copied;
+ *     host arrays passed out are filled before the call returns.
+ *   - Work is enqueued on the stream given to tdks_create_grid (a cudaStream_t, or NULL
+ *     for the legacy default stream) and may still run when a call returns, except for
+ *     calls documented as synchronising.
+ *   - Host orbital layout: complex128 as interleaved (re, im) doubles, index
+ *     [k][z][y][x][orb], the state index innermost (Sec. "Memory layout").
+ *   - Device (packed) layout used by tdks_apply_H: [k][batch][z][y][x][j], orbital
+ *     o = batch * BS + j, BS = 4 (complex128 systems) or 8 (complex64 systems),
+ *     zero-padded to a whole number of batches; elements are complex128 or complex64
+ *     as the system's precision.  tdks_layout() reports BS, the batch count and sizes.
+ *   - Grid coordinates: finite box x_i = (i - (nx-1)/2) h; periodic cell x_i = i h,
+ *     cell side L = nx h; the same for y and z.
+ *   - Errors: TDKS_EINVAL for bad arguments, TDKS_ENOMEM for failed device or host
+ *     allocation, TDKS_EUNSTABLE when a requested sub-step is beyond the stability
+ *     limit of the 4th-order Taylor series, TDKS_EDEVICE for a CUDA error (the message
+ *     names it), TDKS_ESTATE when a call needs data not set yet (e.g. orbitals).
+ */
+#ifndef TDKS_H
+#define TDKS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tdks_system *tdks_sys;
+
+typedef enum {
+  TDKS_OK = 0,
+  TDKS_EINVAL = 1,
+  TDKS_ENOMEM = 2,
+  TDKS_EUNSTABLE = 3,
+  TDKS_ETIMEOUT = 4,
+  TDKS_EDEVICE = 5,
+  TDKS_ESTATE = 6
+} tdks_status;
+
+enum { TDKS_BC_ZERO = 0, TDKS_BC_BLOCH = 1 };
+enum { TDKS_C128 = 0, TDKS_C64 = 1 };
+enum { TDKS_GAUGE_NONE = 0, TDKS_GAUGE_LENGTH = 1, TDKS_GAUGE_VELOCITY = 2 };
+enum { TDKS_ENV_NONE = 0, TDKS_ENV_SIN2 = 1 };
+enum { TDKS_XC_NONE = 0, TDKS_XC_LDA_X = 1 };
+
+/* Number of doubles in one observable record. */
+#define TDKS_RECORD 8
+
+/*
+ * Create a system on the current CUDA device.
+ *   nx, ny, nz  grid points per axis (each >= fd_order/2 + 1; for bc = TDKS_BC_BLOCH each >= fd_order/2)
+ *   h           grid spacing (bohr), > 0
+ *   fd_order    4 or 8 (13- or 25-point star Laplacian)
+ *   bc          TDKS_BC_ZERO: orbitals vanish outside the box (finite systems);
+ *               TDKS_BC_BLOCH: periodic cell whose orbitals obey the Bloch condition
+ *               psi(r + L e_a) = exp(i k_a L) psi(r) (Sec. "Periodic systems": Bloch theorem)
+ *   prec        TDKS_C128: all of H psi and the series in complex128;
+ *               TDKS_C64: H psi and the Taylor terms in complex64, the state (the sum of the
+ *               series), density, potentials and all reductions in FP64
+ *   n_orb       orbitals per k-point (>= 1)
+ *   n_k         k-points (1 for TDKS_BC_ZERO)
+ *   kpts        [n_k][3] k-vectors (bohr^-1), or NULL for k = 0
+ *   kweights    [n_k] weights, or NULL for 1/n_k each
+ *   stream      cudaStream_t on which all work of this system is enqueued (NULL: default)
+ *   out         receives the handle
+ * The local potential starts at zero, no projectors, no field, LDA exchange on with
+ * occupation 2.  Allocates all device buffers of the system.
+ */
+int tdks_create_grid(int nx, int ny, int nz, double h, int fd_order, int bc, int prec, int n_orb, int n_k,
+                     const double *kpts, const double *kweights, void *stream, tdks_sys *out);
+
+/* Free the system and its device memory (synchronises its stream first). */
+int tdks_destroy(tdks_sys sys);
+
+/* V_loc: host array [nz][ny][nx] of doubles (Ha), copied. */
+int tdks_set_local_potential(tdks_sys sys, const double *v);
+
+/* Orbitals: host array in the host layout (2 * n_k * N * n_orb doubles), copied and
+ * packed on the device; the density of the new state is rebuilt on first use. */
+int tdks_set_orbitals(tdks_sys sys, const double *psi);
+
+/* Copy the current orbitals out into the host layout.  Synchronises. */
+int tdks_get_orbitals(tdks_sys sys, double *psi_out);
+
+/*
+ * Kleinman-Bylander projectors (the paper's norm-conserving pseudopotentials carry
+ * non-local parts, Sec. "Magneto-optics"; their shape is not printed there, so the
+ * projectors are Gaussian-times-polynomial): for atom a at R_a and d = r - R_a,
+ *   beta_a1 = g, beta_a2..4 = (d_x, d_y, d_z) g,  g = exp(-|d|^2 / (2 r_c^2)),  |d| <= r_cut.
+ *   pos  [n_atoms][3] positions (bohr), D [n_atoms][4] strengths D_aj (Ha), both copied.
+ * In a periodic cell the sphere points are taken over the neighbouring images with the
+ * Bloch phase exp(i k.T); in the velocity gauge beta carries exp(-i A.d).
+ * n_atoms = 0 removes the projectors.
+ */
+int tdks_set_atoms_projectors(tdks_sys sys, int n_atoms, const double *pos, const double *D, double r_c,
+                              double r_cut);
+
+/*
+ * External field (forward coupling to a classical laser, Sec. "Maxwell ... coupling").
+ *   gauge     TDKS_GAUGE_NONE; TDKS_GAUGE_LENGTH (finite box only): +E(t).r with
+ *             E(t) = amp env(t) sin(omega t) pol; TDKS_GAUGE_VELOCITY (periodic cell only):
+ *             A(t) = amp env(t) sin(omega t) pol, E = -dA/dt.
+ *   envelope  TDKS_ENV_NONE (env = 1) or TDKS_ENV_SIN2: env = sin^2(pi t / t_total) on
+ *             [0, t_total], 0 outside.
+ */
+int tdks_set_field(tdks_sys sys, int gauge, const double pol[3], double amp, double omega, int envelope,
+                   double t_total);
+
+/* Exchange-correlation term: TDKS_XC_NONE or TDKS_XC_LDA_X (spin-unpolarised LDA
+ * exchange, v_x = -(3n/pi)^(1/3)); occupation f > 0 of every orbital (2 for closed shells). */
+int tdks_set_xc(tdks_sys sys, int xc, double occupation);
+
+/*
+ * Packed device layout: *bs = orbitals per batch, *n_batches per k-point,
+ * *elem_bytes = 16 (complex128) or 8 (complex64), *bytes = size of one packed array.
+ * Any output pointer may be NULL.
+ */
+int tdks_layout(tdks_sys sys, int *bs, int *n_batches, int *elem_bytes, long long *bytes);
+
+/*
+ * dev_out = H[n, t] dev_in for every orbital and k-point, where n is the density of the
+ * system's current orbitals and the field is taken at time t.  dev_in and dev_out are
+ * device arrays in the packed layout (see tdks_layout), distinct, owned by the caller.
+ * Asynchronous on the system's stream.
+ */
+int tdks_apply_H(tdks_sys sys, double t, const void *dev_in, void *dev_out);
+
+/*
+ * Advance the orbitals by n_steps steps of length dt from time t0.  Each step is split
+ * into `substeps` equal Taylor sub-steps (0: automatic, from a bound on |H|, so that
+ * dt_sub * |lambda_max| <= 2.5 < 2 sqrt 2, the stability limit of the 4th-order Taylor
+ * series).  A sub-step whose kinetic part alone exceeds the limit is refused with
+ * TDKS_EUNSTABLE.  One observable record is stored per step for the state at the start
+ * of that step (see tdks_reductions).  Asynchronous on the system's stream.
+ */
+int tdks_propagate_n(tdks_sys sys, double t0, double dt, int n_steps, int substeps);
+
+/* Sub-step count the automatic policy of tdks_propagate_n picks for step dt. */
+int tdks_auto_substeps(tdks_sys sys, double dt, int *substeps);
+
+/*
+ * Copy n observable records, starting at step index step_from (counted over the life of
+ * the system), into out[n][TDKS_RECORD]:
+ *   [0] t       state time t0 + s dt
+ *   [1] norm    sum_k w_k sum_i ||phi_ik||^2 h^3
+ *   [2] E       sum_k w_k f <phi|H|phi> - int n v_x + E_x  (field of the step's first
+ *               sub-step, i.e. at t + dt_sub/2)
+ *   [3] E_x     LDA exchange energy (0 when exchange is off)
+ *   [4..6]      finite box: dipole d = int r n(r) dr (Sec. "Local domains");
+ *               periodic cell: current J = -(1/Omega)(sum_k w_k f <phi|-i grad_h|phi> + A int n)
+ *               (eqn. current_density, local part)
+ *   [7]         field along pol at t + dt_sub/2 (E in length gauge, A in velocity gauge)
+ * Records are kept in a ring of 65536 steps.  Synchronises.
+ */
+int tdks_reductions(tdks_sys sys, long long step_from, int n, double *out);
+
+/* Number of steps recorded so far. */
+int tdks_step_count(tdks_sys sys, long long *count);
+
+/* Observable record of the current state at t_state with the field at t_field
+ * (layout as in tdks_reductions).  Synchronises. */
+int tdks_observe(tdks_sys sys, double t_state, double t_field, double *out);
+
+/*
+ * Kernel accounting.  tdks_set_profiling(sys, 1) brackets every stencil-sweep launch
+ * with CUDA events on the system's stream; tdks_kernel_time(sys, kind, &ms, &n) then
+ * returns the summed device time and launch count since the last call and resets them
+ * (kind 0: stencil sweeps, 1: projector gathers, 2: density/LDA/finalise).  Synchronises.
+ * tdks_launch_count returns the number of kernels this system has launched.
+ */
+int tdks_set_profiling(tdks_sys sys, int on);
+int tdks_kernel_time(tdks_sys sys, int kind, double *ms, long long *launches);
+int tdks_launch_count(tdks_sys sys, long long *count);
+
+/* Stencil tile shape (x, y points per CTA; one of 16x8, 32x4, 8x8) and z-chunk
+ * length (0: automatic).  Results do not depend on the choice except in the last bits of
+ * the energy and current sums. */
+int tdks_set_tile(tdks_sys sys, int tx, int ty, int zc);
+
+const char *tdks_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TDKS_H */

@@ -1,0 +1,286 @@
+// Auxiliary kernels of the TDKS library: Kleinman-Bylander gather-dot, density, LDA
+// exchange + effective potential, observable finalisation, layout packing.
+#include "tdks_internal.cuh"
+#include "tdks_vec.cuh"
+
+namespace tdks {
+
+// ---------------------------------------------------------------------------------
+// Projector gather-dot: q[kb][a][j][v] = D_aj h^3 sum_{u in S_a} beta_aj(u - R_a)
+//                                         exp(+i (k.T_u + A.d_u)) in(cell(u))[v]
+// (the <beta_aj|psi> of V_NL = sum |beta> D <beta|; the paper's norm-conserving
+// pseudopotentials, Sec. "Magneto-optics" and Sec. "Periodic systems", with synthetic
+// Gaussian-times-polynomial projectors).  One CTA per (atom, kb); 64 point lanes x OVC
+// vectors; lanes reduce with warp shuffles, warps through shared memory in a fixed
+// order, so the result does not depend on timing.
+// ---------------------------------------------------------------------------------
+constexpr int GATHER_THREADS = 256;
+
+template <int P, int BLOCH>
+__global__ void __launch_bounds__(GATHER_THREADS) gather_kernel(const GatherParams p) {
+  typedef VT<P> T;
+  typedef typename T::V V;
+  const int a = blockIdx.x, kb = blockIdx.y;
+  const int kidx = kb / p.n_batches;
+  const int tid = threadIdx.x, v = tid % OVC, lane = tid / OVC;
+  constexpr int LANES = GATHER_THREADS / OVC;
+  double2 acc[4][2];
+#pragma unroll
+  for (int j = 0; j < 4; j++) acc[j][0] = acc[j][1] = make_double2(0.0, 0.0);
+  const int e0 = p.atom_begin[a], e1 = p.atom_begin[a + 1];
+  const bool phase = BLOCH || (p.A[0] != 0.0 || p.A[1] != 0.0 || p.A[2] != 0.0);
+  for (int e = e0 + lane; e < e1; e += LANES) {
+    const ProjEntry &E = p.ent[e];
+    const long pt = (long)kb * p.N + E.cell;
+    V x;
+    if (p.from_psi) x = T::ld_state(reinterpret_cast<const double2 *>(p.in), pt, v);
+    else x = T::ld(reinterpret_cast<const V *>(p.in) + pt * OVC + v);
+    double2 xd[2];
+    T::to_d(x, xd);
+    double c = 1.0, s = 0.0;
+    if (phase) {
+      double ang = p.A[0] * E.d[0] + p.A[1] * E.d[1] + p.A[2] * E.d[2];
+      if (BLOCH) ang += p.kvec[3 * kidx] * E.T[0] + p.kvec[3 * kidx + 1] * E.T[1] + p.kvec[3 * kidx + 2] * E.T[2];
+      sincos(ang, &s, &c);
+    }
+#pragma unroll
+    for (int cc = 0; cc < T::CPV; cc++) {
+      const double xr = c * xd[cc].x - s * xd[cc].y, xi = c * xd[cc].y + s * xd[cc].x;
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        acc[j][cc].x += E.betad[j] * xr;
+        acc[j][cc].y += E.betad[j] * xi;
+      }
+    }
+  }
+  // reduce over lanes with equal v: lanes differ in bits 2..4 of the lane id, then warps
+  __shared__ double2 red[GATHER_THREADS / 32][4][OVC][2];
+#pragma unroll
+  for (int j = 0; j < 4; j++)
+#pragma unroll
+    for (int cc = 0; cc < 2; cc++) {
+      double2 x = acc[j][cc];
+      for (int o = 4; o < 32; o <<= 1) {
+        x.x += __shfl_xor_sync(0xffffffffu, x.x, o);
+        x.y += __shfl_xor_sync(0xffffffffu, x.y, o);
+      }
+      if ((tid & 31) < OVC) red[tid >> 5][j][v][cc] = x;
+    }
+  __syncthreads();
+  if (tid < 4 * OVC) {
+    const int j = tid / OVC, vv = tid % OVC;
+    double2 s0 = make_double2(0.0, 0.0), s1 = make_double2(0.0, 0.0);
+    for (int w = 0; w < GATHER_THREADS / 32; w++) {
+      s0.x += red[w][j][vv][0].x; s0.y += red[w][j][vv][0].y;
+      s1.x += red[w][j][vv][1].x; s1.y += red[w][j][vv][1].y;
+    }
+    const double f = p.D[4 * a + j] * p.h3;
+    V *q = reinterpret_cast<V *>(p.q) + ((long)(kb * p.n_atoms + a) * 4 + j) * OVC + vv;
+    if (P == P_C64) {
+      *reinterpret_cast<ulonglong2 *>(q) =
+          make_ulonglong2(pk2((float)(f * s0.x), (float)(f * s0.y)), pk2((float)(f * s1.x), (float)(f * s1.y)));
+    } else {
+      *reinterpret_cast<double2 *>(q) = make_double2(f * s0.x, f * s0.y);
+    }
+  }
+}
+
+cudaError_t launch_gather(int prec, int bloch, const GatherParams &p, cudaStream_t s) {
+  if (p.n_atoms <= 0) return cudaSuccess;
+  dim3 grid(p.n_atoms, p.n_kb);
+  if (prec == P_C64) {
+    if (bloch) gather_kernel<P_C64, 1><<<grid, GATHER_THREADS, 0, s>>>(p);
+    else gather_kernel<P_C64, 0><<<grid, GATHER_THREADS, 0, s>>>(p);
+  } else {
+    if (bloch) gather_kernel<P_C128, 1><<<grid, GATHER_THREADS, 0, s>>>(p);
+    else gather_kernel<P_C128, 0><<<grid, GATHER_THREADS, 0, s>>>(p);
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------
+// Density contribution of each (k, batch) block: dens_part[kb][r] = w_k f sum_j |psi|^2
+// (n(r) = sum_k w_k sum_i f_i |phi_ik(r)|^2, with closed-shell f_i = 2).
+// ---------------------------------------------------------------------------------
+template <int CPV>
+__global__ void density_kernel(long N, int n_kb, int n_batches, const double2 *psi,
+                               const double *wocc, double *dens_part) {
+  const long total = (long)n_kb * N;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+    const int kb = (int)(i / N);
+    const double2 *b = psi + i * (OVC * CPV);
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < OVC * CPV; j++) {
+      const double2 x = b[j];
+      s += x.x * x.x + x.y * x.y;
+    }
+    dens_part[i] = wocc[kb / n_batches] * s;
+  }
+}
+
+cudaError_t launch_density(int prec, long N, int n_kb, int n_batches, const void *psi,
+                           const double *wocc, double *dens_part, cudaStream_t s) {
+  const long total = (long)n_kb * N;
+  int grid = (int)((total + 255) / 256);
+  if (grid > 152 * 16) grid = 152 * 16;
+  if (prec == P_C64)
+    density_kernel<2><<<grid, 256, 0, s>>>(N, n_kb, n_batches, (const double2 *)psi, wocc, dens_part);
+  else
+    density_kernel<1><<<grid, 256, 0, s>>>(N, n_kb, n_batches, (const double2 *)psi, wocc, dens_part);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------
+// n(r) = sum_kb dens_part (fixed order); LDA exchange v_x = -(3n/pi)^(1/3),
+// e_x = 3/4 v_x (Sec. "Local domains": E_xc = int n e_xc(n)); adiabatic: from the
+// current density only (Sec. "New propagators").  V_eff = V_loc + v_x + E.r (length
+// gauge, finite box) + |A|^2/2 (velocity gauge).  Per-block partial sums for the
+// observables: [int n, int n e_x, int n v_x, int x n, int y n, int z n] (before h^3).
+// ---------------------------------------------------------------------------------
+constexpr int LDA_THREADS = 256;
+
+int lda_blocks(long N) {
+  long g = (N + LDA_THREADS - 1) / LDA_THREADS;
+  return (int)(g < 152 * 4 ? g : 152 * 4);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(LDA_THREADS)
+lda_kernel(long N, int nx, int ny, int nz, double h, int bloch, int n_kb, const double *dens_part,
+           const double *vloc, int xc, double Ex, double Ey, double Ez, double half_A2, R *veff,
+           double *lda_part) {
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  const double cx = bloch ? 0.0 : 0.5 * (nx - 1), cy = bloch ? 0.0 : 0.5 * (ny - 1),
+               cz = bloch ? 0.0 : 0.5 * (nz - 1);
+  for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < N; p += (long)gridDim.x * blockDim.x) {
+    double n = 0.0;
+    for (int kb = 0; kb < n_kb; kb++) n += dens_part[(long)kb * N + p];
+    const int ix = (int)(p % nx), iy = (int)((p / nx) % ny), iz = (int)(p / ((long)nx * ny));
+    const double x = (ix - cx) * h, y = (iy - cy) * h, z = (iz - cz) * h;
+    double vx = 0.0;
+    if (xc) vx = -cbrt(3.0 * n * 0.31830988618379067154);  // 1/pi
+    double v = vloc[p] + vx + half_A2;
+    if (!bloch) v += Ex * x + Ey * y + Ez * z;
+    veff[p] = (R)v;
+    acc[0] += n;
+    acc[1] += n * 0.75 * vx;
+    acc[2] += n * vx;
+    acc[3] += x * n;
+    acc[4] += y * n;
+    acc[5] += z * n;
+  }
+  __shared__ double red[LDA_THREADS / 32][6];
+  for (int i = 0; i < 6; i++) {
+    double x = acc[i];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][i] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    double x = 0.0;
+    for (int w = 0; w < LDA_THREADS / 32; w++) x += red[w][threadIdx.x];
+    lda_part[blockIdx.x * 6 + threadIdx.x] = x;
+  }
+}
+
+cudaError_t launch_lda(int prec, int bloch, long N, int nx, int ny, int nz, double h, int n_kb,
+                       const double *dens_part, const double *vloc, int xc, const double E[3],
+                       double half_A2, void *veff, double *lda_part, int n_blocks, cudaStream_t s) {
+  if (prec == P_C64)
+    lda_kernel<float><<<n_blocks, LDA_THREADS, 0, s>>>(N, nx, ny, nz, h, bloch, n_kb, dens_part, vloc, xc,
+                                                       E[0], E[1], E[2], half_A2, (float *)veff, lda_part);
+  else
+    lda_kernel<double><<<n_blocks, LDA_THREADS, 0, s>>>(N, nx, ny, nz, h, bloch, n_kb, dens_part, vloc, xc,
+                                                        E[0], E[1], E[2], half_A2, (double *)veff, lda_part);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------
+// Observable record [t, norm, E, E_x, o_x, o_y, o_z, field]:
+//   norm = int n / f;  E = sum_k w_k f <phi|H|phi> - int n v_x + E_x;
+//   o = dipole int r n (finite box, Sec. "Local domains") or the current
+//       J = -(1/Omega) (sum w f <phi|-i grad|phi> + A int n) (Sec. "Conductivities").
+// One CTA; partials are summed in index order.
+// ---------------------------------------------------------------------------------
+__global__ void finalize_kernel(const double *obs_part, long n_items, const double *lda_part, int n_lda,
+                                double *rec, double t_state, double h3, double occ, int bloch,
+                                double omega_cell, double Ax, double Ay, double Az, double field_val) {
+  __shared__ double s_obs[256][4];
+  __shared__ double s_lda[256][6];
+  const int t = threadIdx.x;
+  double o[4] = {0, 0, 0, 0}, l[6] = {0, 0, 0, 0, 0, 0};
+  for (long i = t; i < n_items; i += 256)
+    for (int c = 0; c < 4; c++) o[c] += obs_part[i * 4 + c];
+  for (int i = t; i < n_lda; i += 256)
+    for (int c = 0; c < 6; c++) l[c] += lda_part[i * 6 + c];
+  for (int c = 0; c < 4; c++) s_obs[t][c] = o[c];
+  for (int c = 0; c < 6; c++) s_lda[t][c] = l[c];
+  __syncthreads();
+  if (t == 0) {
+    double O[4] = {0, 0, 0, 0}, Lq[6] = {0, 0, 0, 0, 0, 0};
+    for (int i = 0; i < 256; i++) {
+      for (int c = 0; c < 4; c++) O[c] += s_obs[i][c];
+      for (int c = 0; c < 6; c++) Lq[c] += s_lda[i][c];
+    }
+    const double nint = Lq[0] * h3, ex = Lq[1] * h3, nvx = Lq[2] * h3;
+    rec[0] = t_state;
+    rec[1] = nint / occ;
+    rec[2] = O[0] * h3 - nvx + ex;
+    rec[3] = ex;
+    if (!bloch) {
+      rec[4] = Lq[3] * h3;
+      rec[5] = Lq[4] * h3;
+      rec[6] = Lq[5] * h3;
+    } else {
+      rec[4] = -(O[1] * h3 + Ax * nint) / omega_cell;
+      rec[5] = -(O[2] * h3 + Ay * nint) / omega_cell;
+      rec[6] = -(O[3] * h3 + Az * nint) / omega_cell;
+    }
+    rec[7] = field_val;
+  }
+}
+
+cudaError_t launch_finalize(const double *obs_part, long n_items, const double *lda_part, int n_lda,
+                            double *record, double t_state, double h3, double occ, int bloch,
+                            double omega_cell, const double A[3], double field_val, cudaStream_t s) {
+  finalize_kernel<<<1, 256, 0, s>>>(obs_part, n_items, lda_part, n_lda, record, t_state, h3, occ, bloch,
+                                    omega_cell, A[0], A[1], A[2], field_val);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------
+// Layout conversion between the host layout [k][r][n_orb] (complex128) and the packed
+// state [k][batch][r][BS] (complex128, zero-padded orbitals).
+// ---------------------------------------------------------------------------------
+__global__ void pack_kernel(int to_internal, long N, int n_k, int n_orb, int n_batches, int BS,
+                            double2 *internal, double2 *plain) {
+  const long total = (long)n_k * n_batches * N * BS;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+    const int j = (int)(i % BS);
+    long r = i / BS;
+    const long pt = r % N;
+    r /= N;
+    const int b = (int)(r % n_batches);
+    const int k = (int)(r / n_batches);
+    const int o = b * BS + j;
+    if (to_internal) {
+      internal[i] = o < n_orb ? plain[((long)k * N + pt) * n_orb + o] : make_double2(0.0, 0.0);
+    } else if (o < n_orb) {
+      plain[((long)k * N + pt) * n_orb + o] = internal[i];
+    }
+  }
+}
+
+cudaError_t launch_pack(int prec, int to_internal, long N, int n_k, int n_orb, int n_batches, void *internal,
+                        double *plain, cudaStream_t s) {
+  const int BS = prec == P_C64 ? 2 * OVC : OVC;
+  const long total = (long)n_k * n_batches * N * BS;
+  long g = (total + 255) / 256;
+  if (g > 152 * 32) g = 152 * 32;
+  pack_kernel<<<(int)g, 256, 0, s>>>(to_internal, N, n_k, n_orb, n_batches, BS, (double2 *)internal,
+                                     (double2 *)plain);
+  return cudaGetLastError();
+}
+
+}  // namespace tdks

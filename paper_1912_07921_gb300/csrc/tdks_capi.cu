@@ -1,0 +1,738 @@
+// C interface of the TDKS library: system objects, host-side set-up (finite-difference
+// weights, projector spheres, field, sub-step policy) and the propagation driver.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/tdks.h"
+#include "tdks_internal.cuh"
+
+using namespace tdks;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg) {
+  g_err = msg;
+  return code;
+}
+
+#define CU(call)                                                                             \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return fail(e_ == cudaErrorMemoryAllocation ? TDKS_ENOMEM : TDKS_EDEVICE,              \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                       \
+  } while (0)
+
+// Finite-difference weights by Fornberg's recursion (weights of derivatives 0..2 at
+// x = 0 from the nodes -M..M); central, order 2M.
+void fd_weights(int M, double *lap, double *grad) {
+  const int n = 2 * M;
+  std::vector<double> x(n + 1);
+  for (int i = 0; i <= n; i++) x[i] = (double)(i - M);
+  std::vector<std::vector<double>> c(n + 1, std::vector<double>(3, 0.0));
+  double c1 = 1.0, c4 = x[0];
+  c[0][0] = 1.0;
+  for (int i = 1; i <= n; i++) {
+    const int mn = std::min(i, 2);
+    double c2 = 1.0;
+    const double c5 = c4;
+    c4 = x[i];
+    for (int j = 0; j < i; j++) {
+      const double c3 = x[i] - x[j];
+      c2 *= c3;
+      if (j == i - 1) {
+        for (int k = mn; k > 0; k--) c[i][k] = c1 * (k * c[i - 1][k - 1] - c5 * c[i - 1][k]) / c2;
+        c[i][0] = -c1 * c5 * c[i - 1][0] / c2;
+      }
+      for (int k = mn; k > 0; k--) c[j][k] = (c4 * c[j][k] - k * c[j][k - 1]) / c3;
+      c[j][0] = c4 * c[j][0] / c3;
+    }
+    c1 = c2;
+  }
+  for (int m = 0; m <= M; m++) {
+    lap[m] = c[M + m][2];
+    grad[m] = m == 0 ? 0.0 : c[M + m][1];
+  }
+}
+
+}  // namespace
+
+struct tdks_system {
+  int nx, ny, nz, M, bc, prec, n_orb, n_k, BS, n_batches, n_kb;
+  long N;
+  double h;
+  std::vector<double> kpts, kw;
+  cudaStream_t stream;
+  int dev;
+  // physics parameters
+  int xc = TDKS_XC_LDA_X;
+  double occ = 2.0;
+  int gauge = TDKS_GAUGE_NONE, envelope = TDKS_ENV_NONE;
+  double pol[3] = {0, 0, 1}, amp = 0, omega = 0, t_total = 0;
+  int n_atoms = 0;
+  std::vector<double> pos, D;
+  double vloc_absmax = 0.0, vnl_bound = 0.0;
+  // device buffers
+  void *psi = nullptr;          // packed complex128 state
+  void *term[3] = {nullptr, nullptr, nullptr};
+  double *vloc = nullptr;
+  void *veff = nullptr;
+  double *dens_part = nullptr;
+  double *lda_part = nullptr;
+  double *obs_part = nullptr;
+  double *ring = nullptr;
+  double *obs_rec = nullptr;    // single record for tdks_observe
+  double *d_kvec = nullptr, *d_wocc = nullptr, *d_D = nullptr;
+  int *d_rowptr = nullptr, *d_rowent = nullptr, *d_atom_begin = nullptr;
+  ProjEntry *d_ent = nullptr;
+  void *d_q = nullptr;
+  double *staging = nullptr;
+  size_t state_bytes = 0, term_bytes = 0;
+  bool have_orbitals = false, dens_valid = false;
+  long long steps = 0;
+  static constexpr long long RING = 65536;
+  // stencil configuration
+  int tx = 16, ty = 8, zc = 0;
+  long long launches = 0;
+  // profiling
+  bool profile = false;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
+  std::vector<cudaEvent_t> ev_free;
+  double prof_ms[3] = {0, 0, 0};
+  long long prof_n[3] = {0, 0, 0};
+};
+
+namespace {
+
+double envelope_of(const tdks_system *s, double t, double *denv) {
+  if (s->envelope == TDKS_ENV_SIN2) {
+    if (t < 0.0 || t > s->t_total) { *denv = 0.0; return 0.0; }
+    const double a = M_PI * t / s->t_total;
+    *denv = 2.0 * std::sin(a) * std::cos(a) * M_PI / s->t_total;
+    return std::sin(a) * std::sin(a);
+  }
+  *denv = 0.0;
+  return 1.0;
+}
+
+// E(t), A(t) of the configured laser
+void field_at(const tdks_system *s, double t, double E[3], double A[3]) {
+  double denv;
+  const double env = envelope_of(s, t, &denv);
+  const double f = s->amp * env * std::sin(s->omega * t);
+  const double df = s->amp * (denv * std::sin(s->omega * t) + env * s->omega * std::cos(s->omega * t));
+  for (int a = 0; a < 3; a++) {
+    E[a] = A[a] = 0.0;
+    if (s->gauge == TDKS_GAUGE_LENGTH) E[a] = f * s->pol[a];
+    if (s->gauge == TDKS_GAUGE_VELOCITY) { A[a] = f * s->pol[a]; E[a] = -df * s->pol[a]; }
+  }
+}
+
+int ev_get(tdks_system *s, cudaEvent_t *e) {
+  if (!s->ev_free.empty()) { *e = s->ev_free.back(); s->ev_free.pop_back(); return 0; }
+  return cudaEventCreate(e) == cudaSuccess ? 0 : -1;
+}
+
+struct Timed {
+  tdks_system *s;
+  int kind;
+  cudaEvent_t a = nullptr, b = nullptr;
+  Timed(tdks_system *s_, int k) : s(s_), kind(k) {
+    if (s->profile && ev_get(s, &a) == 0 && ev_get(s, &b) == 0) cudaEventRecord(a, s->stream);
+    else a = b = nullptr;
+  }
+  ~Timed() {
+    if (a && b) {
+      cudaEventRecord(b, s->stream);
+      s->ev_used.push_back({kind, {a, b}});
+    }
+  }
+};
+
+void sweep_geometry(const tdks_system *s, SweepParams &p) {
+  p.nx = s->nx; p.ny = s->ny; p.nz = s->nz;
+  p.n_tx = (s->nx + s->tx - 1) / s->tx;
+  p.n_ty = (s->ny + s->ty - 1) / s->ty;
+  p.n_kb = s->n_kb;
+  p.n_batches = s->n_batches;
+  int zc = s->zc;
+  if (zc <= 0) {
+    // whole z columns unless that leaves fewer than ~4 CTAs per SM
+    const long per_plane = (long)p.n_tx * p.n_ty * p.n_kb;
+    zc = s->nz;
+    while (zc > 4 * s->M && per_plane * ((s->nz + zc - 1) / zc) < 152 * 4) zc = (zc + 1) / 2;
+  }
+  p.zc = zc;
+  p.n_zc = (s->nz + zc - 1) / zc;
+  p.n_items = (long)p.n_tx * p.n_ty * p.n_kb * p.n_zc;
+}
+
+long n_items_of(const tdks_system *s) {
+  SweepParams p{};
+  sweep_geometry(s, p);
+  return p.n_items;
+}
+
+void sweep_common(const tdks_system *s, SweepParams &p, const double A[3]) {
+  sweep_geometry(s, p);
+  double c[MAXM + 1], d[MAXM + 1];
+  fd_weights(s->M, c, d);
+  for (int m = 0; m <= MAXM; m++) { p.w[m] = 0.0; p.gw[m] = 0.0; }
+  p.w[0] = -1.5 * c[0] / (s->h * s->h);
+  for (int m = 1; m <= s->M; m++) {
+    p.w[m] = -0.5 * c[m] / (s->h * s->h);
+    p.gw[m] = d[m] / s->h;
+  }
+  p.veff = s->veff;
+  p.rowptr = s->n_atoms > 0 ? s->d_rowptr : nullptr;
+  p.rowent = s->d_rowent;
+  p.ent = s->d_ent;
+  p.q = s->d_q;
+  p.n_atoms = s->n_atoms;
+  p.kvec = s->d_kvec;
+  p.L[0] = s->nx * s->h; p.L[1] = s->ny * s->h; p.L[2] = s->nz * s->h;
+  for (int a = 0; a < 3; a++) p.A[a] = A[a];
+  p.grad_mask = 0;
+  if (s->bc == TDKS_BC_BLOCH)
+    for (int a = 0; a < 3; a++) if (A[a] != 0.0) p.grad_mask |= 1 << a;
+  p.wocc = s->d_wocc;
+  p.obs_part = s->obs_part;
+  p.dens_part = s->dens_part;
+  p.do_obs = 0;
+}
+
+int run_sweep(tdks_system *s, int mode, SweepParams &p) {
+  Timed tm(s, 0);
+  cudaError_t e = launch_sweep(s->M, s->prec, mode, s->bc == TDKS_BC_BLOCH, s->tx, s->ty, p, 0, s->stream);
+  s->launches++;
+  if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("stencil sweep: ") + cudaGetErrorString(e));
+  return TDKS_OK;
+}
+
+int run_gather(tdks_system *s, const void *in, int from_psi, const double A[3]) {
+  if (s->n_atoms <= 0) return TDKS_OK;
+  GatherParams g{};
+  g.n_kb = s->n_kb; g.n_batches = s->n_batches; g.n_atoms = s->n_atoms; g.N = s->N;
+  g.in = in; g.from_psi = from_psi;
+  g.atom_begin = s->d_atom_begin; g.ent = s->d_ent; g.D = s->d_D;
+  g.h3 = s->h * s->h * s->h;
+  g.kvec = s->d_kvec;
+  for (int a = 0; a < 3; a++) g.A[a] = s->gauge == TDKS_GAUGE_VELOCITY ? A[a] : 0.0;
+  g.q = s->d_q;
+  Timed tm(s, 1);
+  cudaError_t e = launch_gather(s->prec, s->bc == TDKS_BC_BLOCH, g, s->stream);
+  s->launches++;
+  if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("projector gather: ") + cudaGetErrorString(e));
+  return TDKS_OK;
+}
+
+int ensure_density(tdks_system *s) {
+  if (!s->have_orbitals) return fail(TDKS_ESTATE, "orbitals not set");
+  if (s->dens_valid) return TDKS_OK;
+  Timed tm(s, 2);
+  cudaError_t e = launch_density(s->prec, s->N, s->n_kb, s->n_batches, s->psi, s->d_wocc, s->dens_part, s->stream);
+  s->launches++;
+  if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("density: ") + cudaGetErrorString(e));
+  s->dens_valid = true;
+  return TDKS_OK;
+}
+
+int run_lda(tdks_system *s, const double E[3], const double A[3]) {
+  const double half_A2 = s->gauge == TDKS_GAUGE_VELOCITY ? 0.5 * (A[0] * A[0] + A[1] * A[1] + A[2] * A[2]) : 0.0;
+  const double El[3] = {s->gauge == TDKS_GAUGE_LENGTH ? E[0] : 0.0, s->gauge == TDKS_GAUGE_LENGTH ? E[1] : 0.0,
+                        s->gauge == TDKS_GAUGE_LENGTH ? E[2] : 0.0};
+  Timed tm(s, 2);
+  cudaError_t e = launch_lda(s->prec, s->bc == TDKS_BC_BLOCH, s->N, s->nx, s->ny, s->nz, s->h, s->n_kb,
+                             s->dens_part, s->vloc, s->xc, El, half_A2, s->veff, s->lda_part, lda_blocks(s->N),
+                             s->stream);
+  s->launches++;
+  if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("lda: ") + cudaGetErrorString(e));
+  return TDKS_OK;
+}
+
+int run_finalize(tdks_system *s, double *rec, double t_state, const double E[3], const double A[3]) {
+  const double h3 = s->h * s->h * s->h;
+  const double omega_cell = (double)s->N * h3;
+  double fv = 0.0;
+  for (int a = 0; a < 3; a++) fv += (s->gauge == TDKS_GAUGE_VELOCITY ? A[a] : E[a]) * s->pol[a];
+  const double Az[3] = {0, 0, 0};
+  Timed tm(s, 2);
+  cudaError_t e = launch_finalize(s->obs_part, n_items_of(s), s->lda_part, lda_blocks(s->N), rec, t_state, h3,
+                                  s->occ, s->bc == TDKS_BC_BLOCH, omega_cell,
+                                  s->gauge == TDKS_GAUGE_VELOCITY ? A : Az, fv, s->stream);
+  s->launches++;
+  if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("finalize: ") + cudaGetErrorString(e));
+  return TDKS_OK;
+}
+
+// Sweep 1 of a sub-step (or an observation): term[0] = coef * H psi, with the energy
+// and current partial sums when `obs` is set.
+int first_sweep(tdks_system *s, double cr, double ci, const double A[3], bool obs) {
+  int rc = run_gather(s, s->psi, 1, A);
+  if (rc) return rc;
+  SweepParams p{};
+  sweep_common(s, p, A);
+  p.cr = cr; p.ci = ci;
+  p.in = s->psi;
+  p.out = s->term[0];
+  p.do_obs = obs ? 1 : 0;
+  if (obs && s->bc == TDKS_BC_BLOCH) p.grad_mask |= 8;
+  return run_sweep(s, MODE_FIRST, p);
+}
+
+// Gershgorin-type bound on |lambda| of H: kinetic maximum (the +/- alternating mode of
+// the stencil), |V_loc|, exchange of a dense region, field terms, projector norms.
+double h_bound(const tdks_system *s, double dt_hint) {
+  double c[MAXM + 1], d[MAXM + 1];
+  fd_weights(s->M, c, d);
+  double smax = -c[0];
+  for (int m = 1; m <= s->M; m++) smax -= 2.0 * c[m] * ((m % 2) ? -1.0 : 1.0);
+  double dmax = 0.0;
+  for (int m = 1; m <= s->M; m++) dmax += std::fabs(d[m]);
+  dmax *= 2.0 / s->h;
+  double kin = 3.0 * smax / (2.0 * s->h * s->h);
+  double bound = kin + s->vloc_absmax + s->vnl_bound + 2.0;  // 2 Ha covers v_x at n <= 10
+  const double Lmax = 0.5 * std::max(s->nx, std::max(s->ny, s->nz)) * s->h * std::sqrt(3.0);
+  if (s->gauge == TDKS_GAUGE_LENGTH) bound += std::fabs(s->amp) * Lmax;
+  if (s->gauge == TDKS_GAUGE_VELOCITY) bound += std::fabs(s->amp) * dmax + 0.5 * s->amp * s->amp;
+  (void)dt_hint;
+  return bound;
+}
+
+double kinetic_max(const tdks_system *s) {
+  double c[MAXM + 1], d[MAXM + 1];
+  fd_weights(s->M, c, d);
+  double smax = -c[0];
+  for (int m = 1; m <= s->M; m++) smax -= 2.0 * c[m] * ((m % 2) ? -1.0 : 1.0);
+  return 3.0 * smax / (2.0 * s->h * s->h);
+}
+
+void free_proj(tdks_system *s) {
+  cudaFree(s->d_rowptr); cudaFree(s->d_rowent); cudaFree(s->d_atom_begin);
+  cudaFree(s->d_ent); cudaFree(s->d_q); cudaFree(s->d_D);
+  s->d_rowptr = s->d_rowent = s->d_atom_begin = nullptr;
+  s->d_ent = nullptr; s->d_q = nullptr; s->d_D = nullptr;
+  s->n_atoms = 0;
+  s->vnl_bound = 0.0;
+}
+
+double coord_of(const tdks_system *s, int axis, int i) {
+  const int n = axis == 0 ? s->nx : (axis == 1 ? s->ny : s->nz);
+  if (s->bc == TDKS_BC_ZERO) return ((double)i - 0.5 * (double)(n - 1)) * s->h;
+  return (double)i * s->h;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *tdks_last_error(void) { return g_err.c_str(); }
+
+int tdks_create_grid(int nx, int ny, int nz, double h, int fd_order, int bc, int prec, int n_orb, int n_k,
+                     const double *kpts, const double *kweights, void *stream, tdks_sys *out) {
+  if (!out) return fail(TDKS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (fd_order != 4 && fd_order != 8) return fail(TDKS_EINVAL, "fd_order must be 4 or 8");
+  const int M = fd_order / 2;
+  if (bc != TDKS_BC_ZERO && bc != TDKS_BC_BLOCH) return fail(TDKS_EINVAL, "bc must be TDKS_BC_ZERO or TDKS_BC_BLOCH");
+  if (prec != TDKS_C128 && prec != TDKS_C64) return fail(TDKS_EINVAL, "prec must be TDKS_C128 or TDKS_C64");
+  const int nmin = bc == TDKS_BC_BLOCH ? M : M + 1;
+  if (nx < nmin || ny < nmin || nz < nmin) return fail(TDKS_EINVAL, "grid too small for the stencil");
+  if (!(h > 0.0)) return fail(TDKS_EINVAL, "h must be > 0");
+  if (n_orb < 1 || n_k < 1) return fail(TDKS_EINVAL, "n_orb and n_k must be >= 1");
+  if (bc == TDKS_BC_ZERO && n_k != 1) return fail(TDKS_EINVAL, "a finite box takes exactly one k-point");
+  const long N = (long)nx * ny * nz;
+  if (N > (1L << 30)) return fail(TDKS_EINVAL, "grid larger than 2^30 points");
+  tdks_system *s = new (std::nothrow) tdks_system();
+  if (!s) return fail(TDKS_ENOMEM, "host allocation");
+  s->nx = nx; s->ny = ny; s->nz = nz; s->h = h; s->M = M; s->bc = bc; s->prec = prec;
+  s->n_orb = n_orb; s->n_k = n_k; s->N = N;
+  s->BS = prec == TDKS_C64 ? 2 * OVC : OVC;
+  s->n_batches = (n_orb + s->BS - 1) / s->BS;
+  s->n_kb = n_k * s->n_batches;
+  s->stream = (cudaStream_t)stream;
+  s->kpts.assign(3 * n_k, 0.0);
+  s->kw.assign(n_k, 1.0 / n_k);
+  if (kpts) for (int i = 0; i < 3 * n_k; i++) s->kpts[i] = kpts[i];
+  if (kweights) for (int i = 0; i < n_k; i++) s->kw[i] = kweights[i];
+  cudaGetDevice(&s->dev);
+  const size_t pts = (size_t)s->n_kb * N;
+  s->state_bytes = pts * OVC * 16 * (prec == TDKS_C64 ? 2 : 1);
+  s->term_bytes = pts * OVC * 16;
+  const int nlda = lda_blocks(N);
+  auto cleanup = [&](int code, const std::string &m) { tdks_destroy(s); return fail(code, m); };
+#define ALLOC(ptr, bytes)                                                                    \
+  do {                                                                                       \
+    cudaError_t e_ = cudaMalloc((void **)&(ptr), (bytes));                                   \
+    if (e_ != cudaSuccess) { cudaGetLastError(); return cleanup(TDKS_ENOMEM, std::string("cudaMalloc ") + #ptr); } \
+  } while (0)
+  ALLOC(s->psi, s->state_bytes);
+  for (int i = 0; i < 3; i++) ALLOC(s->term[i], s->term_bytes);
+  ALLOC(s->vloc, N * sizeof(double));
+  ALLOC(s->veff, N * (prec == TDKS_C64 ? sizeof(float) : sizeof(double)));
+  ALLOC(s->dens_part, pts * sizeof(double));
+  ALLOC(s->lda_part, (size_t)nlda * 6 * sizeof(double));
+  s->zc = 0;
+  // obs partials sized for the smallest tile (most items)
+  {
+    const long items = (long)((nx + 7) / 8) * ((ny + 3) / 4) * s->n_kb * nz;
+    ALLOC(s->obs_part, (size_t)items * 4 * sizeof(double));
+  }
+  ALLOC(s->ring, (size_t)tdks_system::RING * TDKS_RECORD * sizeof(double));
+  ALLOC(s->obs_rec, TDKS_RECORD * sizeof(double));
+  ALLOC(s->d_kvec, 3 * n_k * sizeof(double));
+  ALLOC(s->d_wocc, n_k * sizeof(double));
+#undef ALLOC
+  if (cudaMemcpy(s->d_kvec, s->kpts.data(), 3 * n_k * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemsetAsync(s->vloc, 0, N * sizeof(double), s->stream) != cudaSuccess ||
+      cudaMemsetAsync(s->psi, 0, s->state_bytes, s->stream) != cudaSuccess)
+    return cleanup(TDKS_EDEVICE, "initial copies");
+  std::vector<double> wocc(n_k);
+  for (int i = 0; i < n_k; i++) wocc[i] = s->kw[i] * s->occ;
+  if (cudaMemcpy(s->d_wocc, wocc.data(), n_k * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+    return cleanup(TDKS_EDEVICE, "initial copies");
+  *out = s;
+  return TDKS_OK;
+}
+
+int tdks_destroy(tdks_sys s) {
+  if (!s) return TDKS_OK;
+  cudaStreamSynchronize(s->stream);
+  free_proj(s);
+  cudaFree(s->psi);
+  for (int i = 0; i < 3; i++) cudaFree(s->term[i]);
+  cudaFree(s->vloc); cudaFree(s->veff); cudaFree(s->dens_part); cudaFree(s->lda_part);
+  cudaFree(s->obs_part); cudaFree(s->ring); cudaFree(s->obs_rec); cudaFree(s->d_kvec); cudaFree(s->d_wocc);
+  cudaFree(s->staging);
+  for (auto &u : s->ev_used) { cudaEventDestroy(u.second.first); cudaEventDestroy(u.second.second); }
+  for (auto e : s->ev_free) cudaEventDestroy(e);
+  delete s;
+  return TDKS_OK;
+}
+
+int tdks_set_local_potential(tdks_sys s, const double *v) {
+  if (!s || !v) return fail(TDKS_EINVAL, "NULL argument");
+  double mx = 0.0;
+  for (long i = 0; i < s->N; i++) mx = std::max(mx, std::fabs(v[i]));
+  s->vloc_absmax = mx;
+  CU(cudaMemcpyAsync(s->vloc, v, s->N * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+  CU(cudaStreamSynchronize(s->stream));
+  return TDKS_OK;
+}
+
+static int ensure_staging(tdks_system *s) {
+  if (s->staging) return TDKS_OK;
+  CU(cudaMalloc((void **)&s->staging, (size_t)s->n_k * s->N * s->n_orb * 16));
+  return TDKS_OK;
+}
+
+int tdks_set_orbitals(tdks_sys s, const double *psi) {
+  if (!s || !psi) return fail(TDKS_EINVAL, "NULL argument");
+  int rc = ensure_staging(s);
+  if (rc) return rc;
+  CU(cudaMemcpyAsync(s->staging, psi, (size_t)s->n_k * s->N * s->n_orb * 16, cudaMemcpyHostToDevice, s->stream));
+  CU(launch_pack(s->prec, 1, s->N, s->n_k, s->n_orb, s->n_batches, s->psi, s->staging, s->stream));
+  s->launches++;
+  s->have_orbitals = true;
+  s->dens_valid = false;
+  return TDKS_OK;
+}
+
+int tdks_get_orbitals(tdks_sys s, double *psi_out) {
+  if (!s || !psi_out) return fail(TDKS_EINVAL, "NULL argument");
+  int rc = ensure_staging(s);
+  if (rc) return rc;
+  CU(launch_pack(s->prec, 0, s->N, s->n_k, s->n_orb, s->n_batches, s->psi, s->staging, s->stream));
+  s->launches++;
+  CU(cudaMemcpyAsync(psi_out, s->staging, (size_t)s->n_k * s->N * s->n_orb * 16, cudaMemcpyDeviceToHost,
+                     s->stream));
+  CU(cudaStreamSynchronize(s->stream));
+  return TDKS_OK;
+}
+
+int tdks_set_atoms_projectors(tdks_sys s, int n_atoms, const double *pos, const double *D, double r_c,
+                              double r_cut) {
+  if (!s) return fail(TDKS_EINVAL, "NULL system");
+  if (n_atoms < 0) return fail(TDKS_EINVAL, "n_atoms < 0");
+  CU(cudaStreamSynchronize(s->stream));
+  free_proj(s);
+  if (n_atoms == 0) return TDKS_OK;
+  if (!pos || !D || !(r_c > 0.0) || !(r_cut > 0.0)) return fail(TDKS_EINVAL, "bad projector arguments");
+  const int n[3] = {s->nx, s->ny, s->nz};
+  std::vector<ProjEntry> ent;
+  std::vector<int> atom_begin(n_atoms + 1, 0);
+  double vnl = 0.0;
+  const double h3 = s->h * s->h * s->h;
+  for (int a = 0; a < n_atoms; a++) {
+    atom_begin[a] = (int)ent.size();
+    const double *R = pos + 3 * a;
+    int lo[3], hi[3];
+    for (int ax = 0; ax < 3; ax++) {
+      if (s->bc == TDKS_BC_ZERO) {
+        const double c0 = 0.5 * (n[ax] - 1);
+        lo[ax] = std::max(0, (int)std::floor((R[ax] - r_cut) / s->h + c0) - 1);
+        hi[ax] = std::min(n[ax] - 1, (int)std::ceil((R[ax] + r_cut) / s->h + c0) + 1);
+      } else {
+        lo[ax] = (int)std::floor((R[ax] - r_cut) / s->h) - 1;
+        hi[ax] = (int)std::ceil((R[ax] + r_cut) / s->h) + 1;
+      }
+    }
+    double nb[4] = {0, 0, 0, 0};
+    for (int iz = lo[2]; iz <= hi[2]; iz++)
+      for (int iy = lo[1]; iy <= hi[1]; iy++)
+        for (int ix = lo[0]; ix <= hi[0]; ix++) {
+          const int ii[3] = {ix, iy, iz};
+          double dd[3], r2 = 0.0;
+          for (int ax = 0; ax < 3; ax++) {
+            const double u = s->bc == TDKS_BC_ZERO ? coord_of(s, ax, ii[ax]) : (double)ii[ax] * s->h;
+            dd[ax] = u - R[ax];
+            r2 += dd[ax] * dd[ax];
+          }
+          if (r2 > r_cut * r_cut) continue;
+          ProjEntry e{};
+          int cc[3];
+          for (int ax = 0; ax < 3; ax++) {
+            int w = ii[ax] >= 0 ? ii[ax] / n[ax] : -((-ii[ax] - 1) / n[ax]) - 1;
+            cc[ax] = ii[ax] - w * n[ax];
+            e.T[ax] = (double)(w * n[ax]) * s->h;
+            e.d[ax] = dd[ax];
+          }
+          e.cell = (cc[2] * s->ny + cc[1]) * s->nx + cc[0];
+          e.atom = a;
+          const double g = std::exp(-r2 / (2.0 * r_c * r_c));
+          const double b[4] = {g, dd[0] * g, dd[1] * g, dd[2] * g};
+          for (int j = 0; j < 4; j++) {
+            e.betad[j] = b[j];
+            e.beta[j] = (float)b[j];
+            nb[j] += b[j] * b[j] * h3;
+          }
+          ent.push_back(e);
+        }
+    for (int j = 0; j < 4; j++) vnl += std::fabs(D[4 * a + j]) * nb[j];
+  }
+  atom_begin[n_atoms] = (int)ent.size();
+  if (ent.empty()) return TDKS_OK;
+  // point-major CSR for the scatter (entries in ascending entry order per point)
+  std::vector<int> rowptr(s->N + 1, 0), rowent(ent.size());
+  for (auto &e : ent) rowptr[e.cell + 1]++;
+  for (long i = 0; i < s->N; i++) rowptr[i + 1] += rowptr[i];
+  {
+    std::vector<int> fill(rowptr.begin(), rowptr.end() - 1);
+    for (size_t i = 0; i < ent.size(); i++) rowent[fill[ent[i].cell]++] = (int)i;
+  }
+  CU(cudaMalloc((void **)&s->d_rowptr, (s->N + 1) * sizeof(int)));
+  CU(cudaMalloc((void **)&s->d_rowent, ent.size() * sizeof(int)));
+  CU(cudaMalloc((void **)&s->d_atom_begin, (n_atoms + 1) * sizeof(int)));
+  CU(cudaMalloc((void **)&s->d_ent, ent.size() * sizeof(ProjEntry)));
+  CU(cudaMalloc((void **)&s->d_q, (size_t)s->n_kb * n_atoms * 4 * OVC * 16));
+  CU(cudaMalloc((void **)&s->d_D, (size_t)n_atoms * 4 * sizeof(double)));
+  CU(cudaMemcpy(s->d_rowptr, rowptr.data(), (s->N + 1) * sizeof(int), cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(s->d_rowent, rowent.data(), ent.size() * sizeof(int), cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(s->d_atom_begin, atom_begin.data(), (n_atoms + 1) * sizeof(int), cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(s->d_ent, ent.data(), ent.size() * sizeof(ProjEntry), cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(s->d_D, D, (size_t)n_atoms * 4 * sizeof(double), cudaMemcpyHostToDevice));
+  s->n_atoms = n_atoms;
+  s->pos.assign(pos, pos + 3 * n_atoms);
+  s->D.assign(D, D + 4 * n_atoms);
+  s->vnl_bound = vnl;
+  return TDKS_OK;
+}
+
+int tdks_set_field(tdks_sys s, int gauge, const double pol[3], double amp, double omega, int envelope,
+                   double t_total) {
+  if (!s) return fail(TDKS_EINVAL, "NULL system");
+  if (gauge < 0 || gauge > 2) return fail(TDKS_EINVAL, "bad gauge");
+  if (gauge == TDKS_GAUGE_LENGTH && s->bc != TDKS_BC_ZERO)
+    return fail(TDKS_EINVAL, "the length gauge needs a finite box (E.r is not periodic)");
+  if (gauge == TDKS_GAUGE_VELOCITY && s->bc != TDKS_BC_BLOCH)
+    return fail(TDKS_EINVAL, "the velocity gauge is implemented for periodic cells");
+  if (envelope != TDKS_ENV_NONE && envelope != TDKS_ENV_SIN2) return fail(TDKS_EINVAL, "bad envelope");
+  if (envelope == TDKS_ENV_SIN2 && !(t_total > 0.0)) return fail(TDKS_EINVAL, "t_total must be > 0");
+  s->gauge = gauge;
+  if (pol) for (int a = 0; a < 3; a++) s->pol[a] = pol[a];
+  s->amp = amp; s->omega = omega; s->envelope = envelope; s->t_total = t_total;
+  return TDKS_OK;
+}
+
+int tdks_set_xc(tdks_sys s, int xc, double occupation) {
+  if (!s) return fail(TDKS_EINVAL, "NULL system");
+  if (xc != TDKS_XC_NONE && xc != TDKS_XC_LDA_X) return fail(TDKS_EINVAL, "bad xc");
+  if (!(occupation > 0.0)) return fail(TDKS_EINVAL, "occupation must be > 0");
+  s->xc = xc;
+  s->occ = occupation;
+  std::vector<double> wocc(s->n_k);
+  for (int i = 0; i < s->n_k; i++) wocc[i] = s->kw[i] * s->occ;
+  CU(cudaMemcpyAsync(s->d_wocc, wocc.data(), s->n_k * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+  CU(cudaStreamSynchronize(s->stream));
+  s->dens_valid = false;
+  return TDKS_OK;
+}
+
+int tdks_layout(tdks_sys s, int *bs, int *n_batches, int *elem_bytes, long long *bytes) {
+  if (!s) return fail(TDKS_EINVAL, "NULL system");
+  if (bs) *bs = s->BS;
+  if (n_batches) *n_batches = s->n_batches;
+  if (elem_bytes) *elem_bytes = s->prec == TDKS_C64 ? 8 : 16;
+  if (bytes) *bytes = (long long)s->term_bytes;
+  return TDKS_OK;
+}
+
+int tdks_set_tile(tdks_sys s, int tx, int ty, int zc) {
+  if (!s) return fail(TDKS_EINVAL, "NULL system");
+  const bool ok = (tx == 16 && ty == 8) || (tx == 32 && ty == 4) || (tx == 8 && ty == 8);
+  if (!ok) return fail(TDKS_EINVAL, "tile must be one of 16x8, 32x4, 8x8");
+  if (zc < 0) return fail(TDKS_EINVAL, "zc < 0");
+  s->tx = tx; s->ty = ty; s->zc = zc;
+  return TDKS_OK;
+}
+
+int tdks_apply_H(tdks_sys s, double t, const void *dev_in, void *dev_out) {
+  if (!s || !dev_in || !dev_out) return fail(TDKS_EINVAL, "NULL argument");
+  if (dev_in == dev_out) return fail(TDKS_EINVAL, "dev_in and dev_out must differ");
+  double E[3], A[3];
+  field_at(s, t, E, A);
+  int rc = TDKS_OK;
+  if (s->have_orbitals) rc = ensure_density(s);
+  else if (s->xc == TDKS_XC_LDA_X) return fail(TDKS_ESTATE, "LDA exchange needs the density of set orbitals");
+  else CU(cudaMemsetAsync(s->dens_part, 0, (size_t)s->n_kb * s->N * sizeof(double), s->stream));
+  if (rc) return rc;
+  if ((rc = run_lda(s, E, A))) return rc;
+  if ((rc = run_gather(s, dev_in, 0, A))) return rc;
+  SweepParams p{};
+  sweep_common(s, p, A);
+  p.cr = 1.0; p.ci = 0.0;
+  p.in = dev_in;
+  p.out = dev_out;
+  return run_sweep(s, MODE_MID, p);
+}
+
+int tdks_auto_substeps(tdks_sys s, double dt, int *substeps) {
+  if (!s || !substeps) return fail(TDKS_EINVAL, "NULL argument");
+  const double b = h_bound(s, dt);
+  *substeps = std::max(1, (int)std::ceil(std::fabs(dt) * b / 2.5));
+  return TDKS_OK;
+}
+
+int tdks_propagate_n(tdks_sys s, double t0, double dt, int n_steps, int substeps) {
+  if (!s) return fail(TDKS_EINVAL, "NULL system");
+  if (n_steps < 0 || substeps < 0) return fail(TDKS_EINVAL, "negative count");
+  if (!s->have_orbitals) return fail(TDKS_ESTATE, "orbitals not set");
+  if (substeps == 0) tdks_auto_substeps(s, dt, &substeps);
+  const double dts = dt / substeps;
+  if (std::fabs(dts) * kinetic_max(s) > 2.0 * std::sqrt(2.0))
+    return fail(TDKS_EUNSTABLE, "sub-step beyond the Taylor-4 stability limit (dt_sub * K_max > 2 sqrt 2)");
+  int rc = ensure_density(s);
+  if (rc) return rc;
+  for (int st = 0; st < n_steps; st++) {
+    const double t = t0 + st * dt;
+    for (int j = 0; j < substeps; j++) {
+      const double tj = t + j * dts, tm = tj + 0.5 * dts;
+      double E[3], A[3];
+      field_at(s, tm, E, A);
+      const bool rec = (j == 0);
+      if ((rc = run_lda(s, E, A))) return rc;
+      if ((rc = first_sweep(s, 0.0, -dts, A, rec))) return rc;
+      if (rec) {
+        double *slot = s->ring + (s->steps % tdks_system::RING) * TDKS_RECORD;
+        if ((rc = run_finalize(s, slot, t, E, A))) return rc;
+      }
+      for (int k = 2; k <= 4; k++) {
+        const void *in = s->term[k - 2];
+        if ((rc = run_gather(s, in, 0, A))) return rc;
+        SweepParams p{};
+        sweep_common(s, p, A);
+        p.cr = 0.0; p.ci = -dts / k;
+        p.in = in;
+        if (k < 4) {
+          p.out = s->term[k - 1];
+          if ((rc = run_sweep(s, MODE_MID, p))) return rc;
+        } else {
+          p.psi = s->psi;
+          p.t1 = s->term[0];
+          p.t2 = s->term[1];
+          if ((rc = run_sweep(s, MODE_LAST, p))) return rc;
+        }
+      }
+      s->dens_valid = true;  // MODE_LAST wrote the density of the new state
+    }
+    s->steps++;
+  }
+  return TDKS_OK;
+}
+
+int tdks_reductions(tdks_sys s, long long step_from, int n, double *out) {
+  if (!s || (!out && n > 0)) return fail(TDKS_EINVAL, "NULL argument");
+  if (n < 0 || step_from < 0 || step_from + n > s->steps || step_from < s->steps - tdks_system::RING)
+    return fail(TDKS_EINVAL, "record range outside the stored ring");
+  CU(cudaStreamSynchronize(s->stream));
+  for (int i = 0; i < n;) {
+    const long long slot = (step_from + i) % tdks_system::RING;
+    const int cnt = (int)std::min<long long>(n - i, tdks_system::RING - slot);
+    CU(cudaMemcpy(out + (size_t)i * TDKS_RECORD, s->ring + slot * TDKS_RECORD, (size_t)cnt * TDKS_RECORD * sizeof(double),
+                  cudaMemcpyDeviceToHost));
+    i += cnt;
+  }
+  return TDKS_OK;
+}
+
+int tdks_step_count(tdks_sys s, long long *count) {
+  if (!s || !count) return fail(TDKS_EINVAL, "NULL argument");
+  *count = s->steps;
+  return TDKS_OK;
+}
+
+int tdks_observe(tdks_sys s, double t_state, double t_field, double *out) {
+  if (!s || !out) return fail(TDKS_EINVAL, "NULL argument");
+  int rc = ensure_density(s);
+  if (rc) return rc;
+  double E[3], A[3];
+  field_at(s, t_field, E, A);
+  if ((rc = run_lda(s, E, A))) return rc;
+  if ((rc = first_sweep(s, 1.0, 0.0, A, true))) return rc;
+  if ((rc = run_finalize(s, s->obs_rec, t_state, E, A))) return rc;
+  CU(cudaMemcpyAsync(out, s->obs_rec, TDKS_RECORD * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  CU(cudaStreamSynchronize(s->stream));
+  return TDKS_OK;
+}
+
+int tdks_set_profiling(tdks_sys s, int on) {
+  if (!s) return fail(TDKS_EINVAL, "NULL system");
+  s->profile = on != 0;
+  return TDKS_OK;
+}
+
+int tdks_kernel_time(tdks_sys s, int kind, double *ms, long long *launches) {
+  if (!s || kind < 0 || kind > 2) return fail(TDKS_EINVAL, "bad argument");
+  CU(cudaStreamSynchronize(s->stream));
+  for (auto &u : s->ev_used) {
+    float t = 0.0f;
+    if (cudaEventElapsedTime(&t, u.second.first, u.second.second) == cudaSuccess) {
+      s->prof_ms[u.first] += t;
+      s->prof_n[u.first]++;
+    }
+    s->ev_free.push_back(u.second.first);
+    s->ev_free.push_back(u.second.second);
+  }
+  s->ev_used.clear();
+  if (ms) *ms = s->prof_ms[kind];
+  if (launches) *launches = s->prof_n[kind];
+  s->prof_ms[kind] = 0.0;
+  s->prof_n[kind] = 0;
+  return TDKS_OK;
+}
+
+int tdks_launch_count(tdks_sys s, long long *count) {
+  if (!s || !count) return fail(TDKS_EINVAL, "NULL argument");
+  *count = s->launches;
+  return TDKS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,105 @@
+// Internal declarations of the GB300 TDKS library (not part of the C interface).
+//
+// Device layout of one system ("packed batches", the paper's Sec. "Memory layout": the
+// state index is innermost so every thread of a warp runs the same stencil on
+// neighbouring orbitals):
+//
+//   orbitals  [k][batch][z][y][x][j],  orbital o = batch * BS + j,  BS orbitals per batch
+//   vectors   one thread owns one 16-byte vector: complex128 -> 1 orbital,
+//             complex64 -> 2 orbitals; OVC = 4 vectors per (point, batch), i.e. 64 B.
+//
+// complex128 systems: BS = 4, the state and the Taylor terms are complex128.
+// complex64  systems: BS = 8, the Taylor terms are complex64 and the state (the running
+//                     sum of the series) stays complex128, so the state block of a
+//                     (point, batch) is 128 B and each thread owns two complex128.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tdks {
+
+constexpr int OVC = 4;        // 16-byte vectors per (point, batch)
+constexpr int MAXM = 4;       // largest FD half-width (8th order)
+
+enum Mode { MODE_FIRST = 0, MODE_MID = 1, MODE_LAST = 2 };
+enum Prec { P_C128 = 0, P_C64 = 1 };
+
+// Per-entry projector data (one grid point of one atom's sphere).
+struct ProjEntry {
+  int cell;        // flat grid index of the (wrapped) point
+  int atom;
+  float beta[4];   // beta_aj at the point (c64 path)
+  double betad[4]; // same, double (c128 path)
+  double T[3];     // lattice translation of the unwrapped point
+  double d[3];     // unwrapped point minus atom centre
+};
+
+struct SweepParams {
+  int nx, ny, nz;
+  int n_tx, n_ty, n_zc, zc;   // x/y tiles and z chunks
+  int n_kb, n_batches;        // kb = k * n_batches + batch
+  long n_items;
+  // stencil: H = w0 c + sum_m w[m] (sum of the 6 neighbours at distance m) + ...
+  double w[MAXM + 1];         // w[0] = -3 c_0 / (2 h^2), w[m] = -c_m / (2 h^2)
+  double gw[MAXM + 1];        // gradient weights d_m / h
+  double cr, ci;              // out = (cr + i ci) * (H in)
+  const void *in;             // stencil input (psi storage in MODE_FIRST, term storage else)
+  void *out;                  // term output (MODE_FIRST / MODE_MID)
+  void *psi;                  // MODE_LAST: state, read and written in place
+  const void *t1, *t2;        // MODE_LAST: earlier terms
+  const void *veff;           // [N] diagonal potential (float for c64, double for c128)
+  // projectors (scatter side)
+  const int *rowptr;          // [N+1] point -> entries (CSR), or null
+  const int *rowent;          // entry indices
+  const ProjEntry *ent;
+  const void *q;              // [kb][atom][4][OVC] vectors: D_aj h^3 <beta_aj|in>
+  int n_atoms;
+  // Bloch boundary
+  const double *kvec;         // [n_k][3]
+  double L[3];
+  double A[3];                // vector potential (velocity gauge)
+  int grad_mask;              // bit a: add -i A_a grad_a; bit 3: observables need all grads
+  // reductions
+  int do_obs;
+  double *obs_part;           // [n_items][4]: <psi|H psi> weighted, current x,y,z
+  const double *wocc;         // [n_k] k-weight times occupation
+  double *dens_part;          // [n_kb][N] (MODE_LAST)
+};
+
+struct GatherParams {
+  int n_kb, n_batches, n_atoms;
+  long N;
+  const void *in;             // psi storage (from_psi) or term storage
+  int from_psi;
+  const int *atom_begin;      // [n_atoms+1] entry ranges (atom-major)
+  const ProjEntry *ent;
+  const double *D;            // [n_atoms][4]
+  double h3;
+  const double *kvec;
+  double A[3];
+  void *q;                    // [kb][atom][4][OVC] vectors
+};
+
+// Launchers (tdks_sweep.cu)
+cudaError_t launch_sweep(int M, int prec, int mode, int bloch, int tx, int ty,
+                         const SweepParams &p, int grid, cudaStream_t s);
+int sweep_threads(int tx, int ty);
+size_t sweep_smem(int M, int tx, int ty);
+
+// Launchers (tdks_aux.cu)
+cudaError_t launch_gather(int prec, int bloch, const GatherParams &p, cudaStream_t s);
+cudaError_t launch_density(int prec, long N, int n_kb, int n_batches, const void *psi,
+                           const double *wocc, double *dens_part, cudaStream_t s);
+cudaError_t launch_lda(int prec, int bloch, long N, int nx, int ny, int nz, double h,
+                       int n_kb, const double *dens_part, const double *vloc, int xc,
+                       const double E[3], double half_A2, void *veff, double *lda_part,
+                       int n_blocks, cudaStream_t s);
+cudaError_t launch_finalize(const double *obs_part, long n_items, const double *lda_part,
+                            int n_lda_blocks, double *record, double t_state, double h3,
+                            double occ, int bloch, double omega_cell, const double A[3],
+                            double field_val, cudaStream_t s);
+cudaError_t launch_pack(int prec, int to_internal, long N, int n_k, int n_orb, int n_batches,
+                        void *internal, double *plain, cudaStream_t s);
+int lda_blocks(long N);
+
+}  // namespace tdks

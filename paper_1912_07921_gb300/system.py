@@ -1,0 +1,160 @@
+"""Python view of one propagation system of the C library (argument marshalling only).
+
+Device memory for ``apply_H`` operands and streams come from PyTorch; every step of the
+propagation runs in the library's kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional
+
+import numpy as np
+
+from . import _lib
+from .inputs import (BC_BLOCH, PREC_C64, GAUGE_NONE, SystemSpec, Inputs)
+
+RECORD = 8
+
+
+def _dp(a: np.ndarray) -> ctypes.c_void_p:
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+class System:
+    """One TDKS system resident on the current CUDA device."""
+
+    def __init__(self, spec: SystemSpec, inputs: Optional[Inputs] = None, stream: Optional[int] = None,
+                 orbitals: Optional[np.ndarray] = None, xc: Optional[int] = None,
+                 projectors: Optional[bool] = None, gauge: Optional[int] = None):
+        self.lib = _lib.load()
+        self.spec = spec
+        kpts = np.ascontiguousarray(inputs.kpts if inputs is not None else np.zeros((1, 3)), dtype=np.float64)
+        kw = np.ascontiguousarray(inputs.kw if inputs is not None else np.ones(1), dtype=np.float64)
+        self.n_k = kpts.shape[0]
+        h = ctypes.c_void_p()
+        _lib.check(self.lib.tdks_create_grid(spec.nx, spec.ny, spec.nz, spec.h, spec.fd_order, spec.bc,
+                                             spec.prec, spec.n_orb, self.n_k, _dp(kpts), _dp(kw),
+                                             ctypes.c_void_p(stream or 0), ctypes.byref(h)))
+        self.h = h
+        self.shape = (self.n_k, spec.nz, spec.ny, spec.nx, spec.n_orb)
+        if inputs is not None:
+            self.set_local_potential(inputs.vloc)
+            use_proj = spec.projectors if projectors is None else projectors
+            if use_proj and inputs.pos.shape[0] > 0:
+                self.set_projectors(inputs.pos, inputs.D, spec.r_c, spec.r_cut)
+        self.set_field(spec.gauge if gauge is None else gauge, spec.pol, spec.amp, spec.omega, spec.envelope,
+                       spec.t_total)
+        self.set_xc(spec.xc if xc is None else xc, spec.occ)
+        psi = orbitals if orbitals is not None else (inputs.psi0 if inputs is not None else None)
+        if psi is not None:
+            self.set_orbitals(psi)
+
+    # -- setters ---------------------------------------------------------------------
+    def set_local_potential(self, v):
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        _lib.check(self.lib.tdks_set_local_potential(self.h, _dp(v)))
+
+    def set_projectors(self, pos, D, r_c, r_cut):
+        pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+        D = np.ascontiguousarray(D, dtype=np.float64).reshape(-1, 4)
+        _lib.check(self.lib.tdks_set_atoms_projectors(self.h, pos.shape[0], _dp(pos), _dp(D), r_c, r_cut))
+
+    def set_field(self, gauge, pol, amp, omega, envelope, t_total):
+        pol = np.ascontiguousarray(pol, dtype=np.float64)
+        _lib.check(self.lib.tdks_set_field(self.h, gauge, _dp(pol), amp, omega, envelope, t_total))
+
+    def set_xc(self, xc, occ):
+        _lib.check(self.lib.tdks_set_xc(self.h, xc, occ))
+
+    def set_orbitals(self, psi):
+        psi = np.ascontiguousarray(psi, dtype=np.complex128)
+        assert psi.shape == self.shape, (psi.shape, self.shape)
+        _lib.check(self.lib.tdks_set_orbitals(self.h, _dp(psi)))
+
+    def set_orbitals_ptr(self, host_ptr: int):
+        """Orbitals from a host buffer (e.g. pinned memory) in the host layout."""
+        _lib.check(self.lib.tdks_set_orbitals(self.h, ctypes.c_void_p(host_ptr)))
+
+    def set_tile(self, tx, ty, zc=0):
+        _lib.check(self.lib.tdks_set_tile(self.h, tx, ty, zc))
+
+    # -- queries ---------------------------------------------------------------------
+    def get_orbitals(self) -> np.ndarray:
+        out = np.empty(self.shape, dtype=np.complex128)
+        _lib.check(self.lib.tdks_get_orbitals(self.h, _dp(out)))
+        return out
+
+    def layout(self):
+        bs, nb, eb, nbytes = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
+        _lib.check(self.lib.tdks_layout(self.h, ctypes.byref(bs), ctypes.byref(nb), ctypes.byref(eb),
+                                        ctypes.byref(nbytes)))
+        return bs.value, nb.value, eb.value, nbytes.value
+
+    def pack(self, psi: np.ndarray) -> np.ndarray:
+        """Host layout [k][z][y][x][orb] -> packed layout [k][b][z][y][x][BS] (zero-padded),
+        complex64 for complex64 systems."""
+        bs, nb, eb, _ = self.layout()
+        k, z, y, x, o = self.shape
+        pad = np.zeros((k, z, y, x, nb * bs), dtype=np.complex128)
+        pad[..., :o] = psi
+        out = pad.reshape(k, z, y, x, nb, bs).transpose(0, 4, 1, 2, 3, 5)
+        return np.ascontiguousarray(out, dtype=np.complex64 if eb == 8 else np.complex128)
+
+    def unpack(self, packed: np.ndarray) -> np.ndarray:
+        bs, nb, _, _ = self.layout()
+        k, z, y, x, o = self.shape
+        a = np.asarray(packed).reshape(k, nb, z, y, x, bs).transpose(0, 2, 3, 4, 1, 5)
+        return a.reshape(k, z, y, x, nb * bs)[..., :o].astype(np.complex128)
+
+    def apply_H(self, t: float, dev_in: int, dev_out: int):
+        """dev_in / dev_out: device pointers (e.g. torch tensor .data_ptr()) in the packed layout."""
+        _lib.check(self.lib.tdks_apply_H(self.h, t, ctypes.c_void_p(dev_in), ctypes.c_void_p(dev_out)))
+
+    def propagate(self, t0: float, dt: float, n_steps: int, substeps: int = 0):
+        _lib.check(self.lib.tdks_propagate_n(self.h, t0, dt, n_steps, substeps))
+
+    def auto_substeps(self, dt: float) -> int:
+        s = ctypes.c_int()
+        _lib.check(self.lib.tdks_auto_substeps(self.h, dt, ctypes.byref(s)))
+        return s.value
+
+    def step_count(self) -> int:
+        c = ctypes.c_longlong()
+        _lib.check(self.lib.tdks_step_count(self.h, ctypes.byref(c)))
+        return c.value
+
+    def reductions(self, step_from: int = 0, n: Optional[int] = None) -> np.ndarray:
+        if n is None:
+            n = self.step_count() - step_from
+        out = np.empty((n, RECORD))
+        _lib.check(self.lib.tdks_reductions(self.h, step_from, n, _dp(out)))
+        return out
+
+    def observe(self, t_state: float, t_field: float) -> np.ndarray:
+        out = np.empty(RECORD)
+        _lib.check(self.lib.tdks_observe(self.h, t_state, t_field, _dp(out)))
+        return out
+
+    def set_profiling(self, on: bool):
+        _lib.check(self.lib.tdks_set_profiling(self.h, int(on)))
+
+    def kernel_time(self, kind: int = 0):
+        ms, n = ctypes.c_double(), ctypes.c_longlong()
+        _lib.check(self.lib.tdks_kernel_time(self.h, kind, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
+    def launch_count(self) -> int:
+        c = ctypes.c_longlong()
+        _lib.check(self.lib.tdks_launch_count(self.h, ctypes.byref(c)))
+        return c.value
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.tdks_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,34 @@
+"""Shared helpers for the GPU parity tests (case construction, device round trips)."""
+import dataclasses
+
+import numpy as np
+
+from paper_1912_07921_gb300 import inputs as I
+
+
+def ragged_molecule(prec, fd_order=8, n_orb=5, **kw):
+    """Grid sizes that are not multiples of any tile, atoms whose spheres touch the faces."""
+    s = I.SystemSpec(nx=37, ny=21, nz=19, h=0.3, fd_order=fd_order, prec=prec, n_orb=n_orb, n_atoms=4,
+                     projectors=True, gauge=I.GAUGE_LENGTH, amp=0.02, omega=0.2, envelope=I.ENV_SIN2,
+                     t_total=3.0, dt=0.02, seed=21)
+    return dataclasses.replace(s, **kw)
+
+
+def bloch_cell(prec, fd_order=4, n_orb=3, n_k=3, **kw):
+    s = I.SystemSpec(nx=13, ny=12, nz=10, h=0.35, fd_order=fd_order, bc=I.BC_BLOCH, prec=prec,
+                     n_orb=n_orb, n_k=n_k, n_atoms=2, projectors=True, gauge=I.GAUGE_VELOCITY,
+                     amp=0.3, omega=0.4, pol=(0.2, 0.3, 0.9), dt=0.01, seed=31)
+    return dataclasses.replace(s, **kw)
+
+
+def bloch_inputs(spec):
+    inp = I.make_inputs(spec)
+    L = np.array([spec.nx, spec.ny, spec.nz]) * spec.h
+    # spheres crossing the cell faces (wrapped images, Bloch phases)
+    inp.pos = np.array([[0.2, 0.3, 0.5 * L[2]], [L[0] - 0.4, 0.6 * L[1], L[2] - 0.1]])[: spec.n_atoms]
+    return inp
+
+
+def rel_err(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))

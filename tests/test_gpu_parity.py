@@ -1,0 +1,193 @@
+"""CUDA path against the FP64 oracle, through the C interface, on the same seeded inputs.
+
+Tolerances: complex128 systems match the oracle to 1e-12 relative (max-norm over all
+values); complex64 systems run H psi in FP32, where a 25-point stencil sum of values of
+size |psi| carries a relative rounding error of ~1e-7 * (sum |c_m| / |c_0|) < 1e-6 of the
+largest value, so single H applications are checked to 5e-6 and the dipole over 1000
+steps to 1e-4 of its peak.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1912_07921_gb300 import inputs as I
+from tests._util import bloch_cell, bloch_inputs, ragged_molecule, rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+    assert torch.cuda.is_available()
+
+
+def _system(spec, inp, **kw):
+    from paper_1912_07921_gb300.system import System
+    return System(spec, inp, stream=torch.cuda.current_stream().cuda_stream, **kw)
+
+
+def _apply_gpu(sysm, psi, t):
+    packed = sysm.pack(psi)
+    din = torch.from_numpy(packed.view(np.float32 if packed.dtype == np.complex64 else np.float64)).cuda()
+    dout = torch.empty_like(din)
+    sysm.apply_H(t, din.data_ptr(), dout.data_ptr())
+    torch.cuda.synchronize()
+    out = dout.cpu().numpy().view(packed.dtype).reshape(packed.shape)
+    return sysm.unpack(out)
+
+
+APPLY_CASES = {
+    "tiny_c128": (lambda: I.tiny_molecule(), None),
+    "ragged_c128_order8": (lambda: ragged_molecule(I.PREC_C128), None),
+    "ragged_c128_order4": (lambda: ragged_molecule(I.PREC_C128, fd_order=4, n_orb=6), None),
+    "ragged_c64_order8": (lambda: ragged_molecule(I.PREC_C64, n_orb=11), None),
+    "bloch_c128_order4": (lambda: bloch_cell(I.PREC_C128), bloch_inputs),
+    "bloch_c128_order8": (lambda: bloch_cell(I.PREC_C128, fd_order=8, n_k=2), bloch_inputs),
+    "bloch_c64_order4": (lambda: bloch_cell(I.PREC_C64, n_orb=5), bloch_inputs),
+}
+
+
+@pytest.mark.parametrize("name", sorted(APPLY_CASES))
+def test_apply_H_matches_oracle(name):
+    make_spec, make_inp = APPLY_CASES[name]
+    spec = make_spec()
+    inp = (make_inp or I.make_inputs)(spec)
+    sysm = _system(spec, inp)
+    o = oracle.System(spec, inp)
+    psi = I.random_orbitals(spec, 77)
+    if spec.prec == I.PREC_C64:
+        psi = psi.astype(np.complex64).astype(np.complex128)
+    t = 0.37
+    got = _apply_gpu(sysm, psi, t)
+    ref = o.apply_H(psi, t, o.vx_of(inp.psi0))
+    tol = 1e-12 if spec.prec == I.PREC_C128 else 5e-6
+    assert rel_err(got, ref) < tol, rel_err(got, ref)
+    sysm.close()
+
+
+def test_apply_H_is_independent_of_the_tile_shape():
+    spec = ragged_molecule(I.PREC_C128)
+    inp = I.make_inputs(spec)
+    sysm = _system(spec, inp)
+    psi = I.random_orbitals(spec, 5)
+    outs = []
+    for tx, ty, zc in ((16, 8, 0), (32, 4, 0), (8, 8, 5), (16, 8, 7)):
+        sysm.set_tile(tx, ty, zc)
+        outs.append(_apply_gpu(sysm, psi, 0.2))
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+    sysm.close()
+
+
+def _propagate_both(spec, inp, n_steps, substeps, dt=None):
+    dt = spec.dt if dt is None else dt
+    sysm = _system(spec, inp)
+    sysm.propagate(0.0, dt, n_steps, substeps)
+    rec = sysm.reductions(0, n_steps)
+    psi = sysm.get_orbitals()
+    sysm.close()
+    o = oracle.System(spec, inp)
+    psi_o, rec_o = o.propagate(inp.psi0, 0.0, dt, n_steps, substeps)
+    return psi, rec, psi_o, rec_o
+
+
+def _rec_err(rec, rec_o):
+    """Per-column error relative to each column's scale (the dipole crosses zero)."""
+    return max(float(np.max(np.abs(rec[:, c] - rec_o[:, c])) / max(np.max(np.abs(rec_o[:, c])), 1e-300))
+               for c in range(rec.shape[1]) if np.max(np.abs(rec_o[:, c])) > 0)
+
+
+def test_tiny_molecule_full_run_c128():
+    """Tiny molecule: 24^3, order 4, 4 orbitals, 2 wells, LDA, E0=0.01, 100 steps dt=0.02."""
+    spec = I.tiny_molecule()
+    inp = I.make_inputs(spec)
+    psi, rec, psi_o, rec_o = _propagate_both(spec, inp, spec.n_steps, spec.substeps)
+    assert rel_err(psi, psi_o) < 1e-12
+    assert _rec_err(rec, rec_o) < 1e-12
+
+
+@pytest.mark.parametrize("case", ["ragged_c128", "bloch_c128"])
+def test_short_runs_with_substeps_c128(case):
+    if case == "ragged_c128":
+        spec = ragged_molecule(I.PREC_C128)
+        inp = I.make_inputs(spec)
+    else:
+        spec = bloch_cell(I.PREC_C128)
+        inp = bloch_inputs(spec)
+    psi, rec, psi_o, rec_o = _propagate_both(spec, inp, 4, 2, dt=0.03)
+    assert rel_err(psi, psi_o) < 1e-12
+    assert _rec_err(rec, rec_o) < 1e-12
+
+
+def test_tiny_molecule_c64_dipole_over_1000_steps():
+    """complex64 H psi with FP64 state and reductions: dipole within 1e-4 of its peak
+    after 1000 steps (norm and energy checked too)."""
+    spec = I.tiny_molecule(prec=I.PREC_C64, n_steps=1000)
+    inp = I.make_inputs(spec)
+    psi, rec, psi_o, rec_o = _propagate_both(spec, inp, spec.n_steps, spec.substeps)
+    d, d_o = rec[:, 4:7], rec_o[:, 4:7]
+    assert float(np.max(np.abs(d - d_o)) / np.max(np.abs(d_o))) < 1e-4
+    assert float(np.max(np.abs(rec[:, 1] - rec_o[:, 1]))) < 1e-5 * rec_o[0, 1]
+    assert float(np.max(np.abs(rec[:, 2] - rec_o[:, 2]))) < 1e-4 * np.max(np.abs(rec_o[:, 2]))
+
+
+def test_medium_molecule_full_size_one_step_c128():
+    """Medium molecule at full size (96^3, order 8, 64 orbitals, 16 atoms with projectors,
+    sin^2 pulse): one configured step of 4 Taylor sub-steps, every value compared."""
+    spec = I.medium_molecule(prec=I.PREC_C128)
+    inp = I.make_inputs(spec)
+    t0 = 20.0  # inside the pulse
+    sysm = _system(spec, inp)
+    sysm.propagate(t0, spec.dt, 1, spec.substeps)
+    rec = sysm.reductions(0, 1)
+    psi = sysm.get_orbitals()
+    sysm.close()
+    o = oracle.System(spec, inp)
+    psi_o, rec_o = o.propagate(inp.psi0, t0, spec.dt, 1, spec.substeps)
+    assert rel_err(psi, psi_o) < 1e-12
+    np.testing.assert_allclose(rec, rec_o, rtol=1e-12, atol=1e-12 * np.abs(rec_o).max())
+
+
+def test_medium_molecule_full_size_one_step_c64():
+    """Same step in the benchmark's precision (complex64 terms, FP64 state and sums)."""
+    spec = I.medium_molecule(prec=I.PREC_C64)
+    inp = I.make_inputs(spec)
+    t0 = 20.0
+    sysm = _system(spec, inp)
+    assert sysm.auto_substeps(spec.dt) == spec.substeps
+    sysm.propagate(t0, spec.dt, 1, spec.substeps)
+    rec = sysm.reductions(0, 1)
+    psi = sysm.get_orbitals()
+    sysm.close()
+    o = oracle.System(spec, inp)
+    psi_o, rec_o = o.propagate(inp.psi0, t0, spec.dt, 1, spec.substeps)
+    assert rel_err(psi, psi_o) < 1e-5
+    assert abs(rec[0, 1] - rec_o[0, 1]) < 1e-6 * rec_o[0, 1]
+    assert abs(rec[0, 2] - rec_o[0, 2]) < 1e-5 * abs(rec_o[0, 2])
+    assert np.max(np.abs(rec[0, 4:7] - rec_o[0, 4:7])) < 1e-5 * np.max(np.abs(rec_o[0, 4:7]))
+
+
+def test_observe_matches_oracle_observables():
+    spec = bloch_cell(I.PREC_C128)
+    inp = bloch_inputs(spec)
+    sysm = _system(spec, inp)
+    got = sysm.observe(1.0, 1.25)
+    sysm.close()
+    ref = oracle.System(spec, inp).observables(inp.psi0, 1.0, 1.25)
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-13 * np.abs(ref).max())
+
+
+def test_unstable_substep_is_refused():
+    from paper_1912_07921_gb300._lib import TdksError
+    spec = I.medium_molecule(prec=I.PREC_C64, nx=24, ny=24, nz=24, n_orb=8)
+    inp = I.make_inputs(spec)
+    sysm = _system(spec, inp)
+    with pytest.raises(TdksError) as e:
+        sysm.propagate(0.0, spec.dt, 1, 1)
+    assert e.value.code == 3
+    sysm.close()
