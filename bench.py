@@ -20,6 +20,7 @@ the same workload (a subset of the orbitals) and reports the same metric.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -135,6 +136,8 @@ def run_ours(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     prec = I.PREC_C64 if args.prec == "c64" else I.PREC_C128
     spec = I.medium_molecule(prec=prec)
+    if args.n_orb:
+        spec = dataclasses.replace(spec, n_orb=args.n_orb)
     inp = I.make_inputs(spec)
     stream = torch.cuda.Stream()
     sysm = System(spec, inp, stream=stream.cuda_stream)
@@ -316,6 +319,8 @@ def main():
     ap.add_argument("--prec", default="c64", choices=["c64", "c128"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-c128", action="store_true", help="skip the complex128 side measurement")
+    ap.add_argument("--n-orb", type=int, default=0,
+                    help="orbital count override (profiling on a smaller case); 0 = the workload's 64")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", "0"))
