@@ -110,14 +110,16 @@ class Clocks:
 def _sweep_bytes(spec, sysm) -> float:
     """Algorithmic HBM bytes of the 4 stencil sweeps of one Taylor sub-step.
 
-    Per (point, padded orbital): sweep 1 reads the complex128 state and writes t1;
-    sweeps 2-3 read t_(k-1) and write t_k; sweep 4 reads t3, the state, t1, t2 and
-    writes the state; plus per point V_eff (each sweep) and one density word per batch.
+    Per (point, padded orbital): sweep 1 reads the state and writes t1; sweeps 2-3 read
+    t_(k-1) and write t_k; sweep 4 reads t3, the state, t1, t2 and writes the state; plus
+    per point V_eff (each sweep) and one density word per batch.  complex128: every array
+    is 16 B per value.  complex64: terms 8 B; the state is hi + lo (8 B + 8 B), of which
+    sweep 1 reads only hi (the FP32 stencil input).
     """
     bs, nb, eb, _ = sysm.layout()
     vals = spec.n_points * nb * bs * sysm.n_k
-    st = 16.0
-    per_val = (st + eb) + 2 * (eb + eb) + (eb + st + eb + eb + st)
+    st_first, st = (8.0, 16.0) if eb == 8 else (16.0, 16.0)
+    per_val = (st_first + eb) + 2 * (eb + eb) + (eb + st + eb + eb + st)
     veff = 4 * spec.n_points * (4 if eb == 8 else 8)
     dens = spec.n_points * nb * sysm.n_k * 8
     return vals * per_val + veff + dens

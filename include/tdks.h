@@ -198,6 +198,12 @@ int tdks_launch_count(tdks_sys sys, long long *count);
  * the energy and current sums. */
 int tdks_set_tile(tdks_sys sys, int tx, int ty, int zc);
 
+/* Stencil sweep implementation: 0 (default) streams the input planes with TMA bulk
+ * tensor copies where that applies (finite boxes, 16x8 tiles), 1 always uses the general
+ * sweep (loads through L1/L2; the only one for periodic cells).  Both compute the same
+ * values (to the last bits of FP64 rounding). */
+int tdks_set_sweep_path(tdks_sys sys, int path);
+
 const char *tdks_last_error(void);
 
 #ifdef __cplusplus

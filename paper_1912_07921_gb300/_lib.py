@@ -35,6 +35,7 @@ SIGNATURES = {
     "tdks_kernel_time": ([P, I, PD, PLL], I),
     "tdks_launch_count": ([P, PLL], I),
     "tdks_set_tile": ([P, I, I, I], I),
+    "tdks_set_sweep_path": ([P, I], I),
     "tdks_last_error": ([], ctypes.c_char_p),
 }
 

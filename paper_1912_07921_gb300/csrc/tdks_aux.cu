@@ -24,32 +24,42 @@ __global__ void __launch_bounds__(GATHER_THREADS) gather_kernel(const GatherPara
   const int kidx = kb / p.n_batches;
   const int tid = threadIdx.x, v = tid % OVC, lane = tid / OVC;
   constexpr int LANES = GATHER_THREADS / OVC;
-  double2 acc[4][2];
-#pragma unroll
-  for (int j = 0; j < 4; j++) acc[j][0] = acc[j][1] = make_double2(0.0, 0.0);
+  // per-lane sums: FP64 for complex128 systems, FP32 for complex64 systems (about 33
+  // sphere points per lane); the cross-lane sums below are FP64 for both.
+  double2 accd[4] = {};
+  float2 accf[4][2] = {};
   const int e0 = p.atom_begin[a], e1 = p.atom_begin[a + 1];
   const bool phase = BLOCH || (p.A[0] != 0.0 || p.A[1] != 0.0 || p.A[2] != 0.0);
   for (int e = e0 + lane; e < e1; e += LANES) {
     const ProjEntry &E = p.ent[e];
     const long pt = (long)kb * p.N + E.cell;
-    V x;
-    if (p.from_psi) x = T::ld_state(reinterpret_cast<const double2 *>(p.in), pt, v);
-    else x = T::ld(reinterpret_cast<const V *>(p.in) + pt * OVC + v);
-    double2 xd[2];
-    T::to_d(x, xd);
-    double c = 1.0, s = 0.0;
+    const V x = T::ld(reinterpret_cast<const V *>(p.in) + pt * OVC + v);
+    double ang = 0.0;
     if (phase) {
-      double ang = p.A[0] * E.d[0] + p.A[1] * E.d[1] + p.A[2] * E.d[2];
+      ang = p.A[0] * E.d[0] + p.A[1] * E.d[1] + p.A[2] * E.d[2];
       if (BLOCH) ang += p.kvec[3 * kidx] * E.T[0] + p.kvec[3 * kidx + 1] * E.T[1] + p.kvec[3 * kidx + 2] * E.T[2];
-      sincos(ang, &s, &c);
     }
-#pragma unroll
-    for (int cc = 0; cc < T::CPV; cc++) {
-      const double xr = c * xd[cc].x - s * xd[cc].y, xi = c * xd[cc].y + s * xd[cc].x;
+    if constexpr (P == P_C64) {
+      float c = 1.f, s = 0.f;
+      if (phase) sincosf((float)ang, &s, &c);
+      const float2 x0 = up2(x.x), x1 = up2(x.y);
+      const float2 y0 = make_float2(c * x0.x - s * x0.y, c * x0.y + s * x0.x);
+      const float2 y1 = make_float2(c * x1.x - s * x1.y, c * x1.y + s * x1.x);
 #pragma unroll
       for (int j = 0; j < 4; j++) {
-        acc[j][cc].x += E.betad[j] * xr;
-        acc[j][cc].y += E.betad[j] * xi;
+        const float b = E.beta[j];
+        accf[j][0].x = fmaf(b, y0.x, accf[j][0].x); accf[j][0].y = fmaf(b, y0.y, accf[j][0].y);
+        accf[j][1].x = fmaf(b, y1.x, accf[j][1].x); accf[j][1].y = fmaf(b, y1.y, accf[j][1].y);
+      }
+    } else {
+      double c = 1.0, s = 0.0;
+      if (phase) sincos(ang, &s, &c);
+      const double2 xd = *reinterpret_cast<const double2 *>(&x);
+      const double xr = c * xd.x - s * xd.y, xi = c * xd.y + s * xd.x;
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        accd[j].x += E.betad[j] * xr;
+        accd[j].y += E.betad[j] * xi;
       }
     }
   }
@@ -59,7 +69,7 @@ __global__ void __launch_bounds__(GATHER_THREADS) gather_kernel(const GatherPara
   for (int j = 0; j < 4; j++)
 #pragma unroll
     for (int cc = 0; cc < 2; cc++) {
-      double2 x = acc[j][cc];
+      double2 x = P == P_C64 ? make_double2(accf[j][cc].x, accf[j][cc].y) : (cc == 0 ? accd[j] : make_double2(0, 0));
       for (int o = 4; o < 32; o <<= 1) {
         x.x += __shfl_xor_sync(0xffffffffu, x.x, o);
         x.y += __shfl_xor_sync(0xffffffffu, x.y, o);
@@ -76,11 +86,10 @@ __global__ void __launch_bounds__(GATHER_THREADS) gather_kernel(const GatherPara
     }
     const double f = p.D[4 * a + j] * p.h3;
     V *q = reinterpret_cast<V *>(p.q) + ((long)(kb * p.n_atoms + a) * 4 + j) * OVC + vv;
-    if (P == P_C64) {
-      *reinterpret_cast<ulonglong2 *>(q) =
-          make_ulonglong2(pk2((float)(f * s0.x), (float)(f * s0.y)), pk2((float)(f * s1.x), (float)(f * s1.y)));
+    if constexpr (P == P_C64) {
+      *q = make_ulonglong2(pk2((float)(f * s0.x), (float)(f * s0.y)), pk2((float)(f * s1.x), (float)(f * s1.y)));
     } else {
-      *reinterpret_cast<double2 *>(q) = make_double2(f * s0.x, f * s0.y);
+      *q = make_double2(f * s0.x, f * s0.y);
     }
   }
 }
@@ -100,34 +109,49 @@ cudaError_t launch_gather(int prec, int bloch, const GatherParams &p, cudaStream
 
 // ---------------------------------------------------------------------------------
 // Density contribution of each (k, batch) block: dens_part[kb][r] = w_k f sum_j |psi|^2
-// (n(r) = sum_k w_k sum_i f_i |phi_ik(r)|^2, with closed-shell f_i = 2).
+// (n(r) = sum_k w_k sum_i f_i |phi_ik(r)|^2, with closed-shell f_i = 2).  complex64
+// systems hold the state as hi + lo (two complex64 arrays).
 // ---------------------------------------------------------------------------------
-template <int CPV>
-__global__ void density_kernel(long N, int n_kb, int n_batches, const double2 *psi,
-                               const double *wocc, double *dens_part) {
+__global__ void density_c128_kernel(long N, int n_kb, int n_batches, const double2 *psi, const double *wocc,
+                                    double *dens_part) {
   const long total = (long)n_kb * N;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
-    const int kb = (int)(i / N);
-    const double2 *b = psi + i * (OVC * CPV);
+    const double2 *b = psi + i * OVC;
     double s = 0.0;
 #pragma unroll
-    for (int j = 0; j < OVC * CPV; j++) {
+    for (int j = 0; j < OVC; j++) {
       const double2 x = b[j];
       s += x.x * x.x + x.y * x.y;
     }
-    dens_part[i] = wocc[kb / n_batches] * s;
+    dens_part[i] = wocc[(int)(i / N) / n_batches] * s;
   }
 }
 
-cudaError_t launch_density(int prec, long N, int n_kb, int n_batches, const void *psi,
+__global__ void density_c64_kernel(long N, int n_kb, int n_batches, const float2 *hi, const float2 *lo,
+                                   const double *wocc, double *dens_part) {
+  const long total = (long)n_kb * N;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < 2 * OVC; j++) {
+      const float2 a = hi[i * 2 * OVC + j], b = lo[i * 2 * OVC + j];
+      const double re = (double)a.x + (double)b.x, im = (double)a.y + (double)b.y;
+      s += re * re + im * im;
+    }
+    dens_part[i] = wocc[(int)(i / N) / n_batches] * s;
+  }
+}
+
+cudaError_t launch_density(int prec, long N, int n_kb, int n_batches, const void *psi, const void *psi_lo,
                            const double *wocc, double *dens_part, cudaStream_t s) {
   const long total = (long)n_kb * N;
   int grid = (int)((total + 255) / 256);
   if (grid > 152 * 16) grid = 152 * 16;
   if (prec == P_C64)
-    density_kernel<2><<<grid, 256, 0, s>>>(N, n_kb, n_batches, (const double2 *)psi, wocc, dens_part);
+    density_c64_kernel<<<grid, 256, 0, s>>>(N, n_kb, n_batches, (const float2 *)psi, (const float2 *)psi_lo, wocc,
+                                            dens_part);
   else
-    density_kernel<1><<<grid, 256, 0, s>>>(N, n_kb, n_batches, (const double2 *)psi, wocc, dens_part);
+    density_c128_kernel<<<grid, 256, 0, s>>>(N, n_kb, n_batches, (const double2 *)psi, wocc, dens_part);
   return cudaGetLastError();
 }
 
@@ -251,10 +275,12 @@ cudaError_t launch_finalize(const double *obs_part, long n_items, const double *
 
 // ---------------------------------------------------------------------------------
 // Layout conversion between the host layout [k][r][n_orb] (complex128) and the packed
-// state [k][batch][r][BS] (complex128, zero-padded orbitals).
+// state [k][batch][r][BS] (zero-padded orbitals).  complex64 systems split each value
+// into hi = fl32(x) and lo = fl32(x - hi) (the double-float state); unpacking returns
+// hi + lo in FP64.
 // ---------------------------------------------------------------------------------
-__global__ void pack_kernel(int to_internal, long N, int n_k, int n_orb, int n_batches, int BS,
-                            double2 *internal, double2 *plain) {
+__global__ void pack_kernel(int to_internal, int c64, long N, int n_k, int n_orb, int n_batches, int BS,
+                            void *internal, void *internal_lo, double2 *plain) {
   const long total = (long)n_k * n_batches * N * BS;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
     const int j = (int)(i % BS);
@@ -264,22 +290,36 @@ __global__ void pack_kernel(int to_internal, long N, int n_k, int n_orb, int n_b
     const int b = (int)(r % n_batches);
     const int k = (int)(r / n_batches);
     const int o = b * BS + j;
+    const long pidx = ((long)k * N + pt) * n_orb + o;
     if (to_internal) {
-      internal[i] = o < n_orb ? plain[((long)k * N + pt) * n_orb + o] : make_double2(0.0, 0.0);
+      const double2 x = o < n_orb ? plain[pidx] : make_double2(0.0, 0.0);
+      if (c64) {
+        const float hx = (float)x.x, hy = (float)x.y;
+        reinterpret_cast<float2 *>(internal)[i] = make_float2(hx, hy);
+        reinterpret_cast<float2 *>(internal_lo)[i] = make_float2((float)(x.x - (double)hx), (float)(x.y - (double)hy));
+      } else {
+        reinterpret_cast<double2 *>(internal)[i] = x;
+      }
     } else if (o < n_orb) {
-      plain[((long)k * N + pt) * n_orb + o] = internal[i];
+      if (c64) {
+        const float2 h = reinterpret_cast<const float2 *>(internal)[i];
+        const float2 l = reinterpret_cast<const float2 *>(internal_lo)[i];
+        plain[pidx] = make_double2((double)h.x + (double)l.x, (double)h.y + (double)l.y);
+      } else {
+        plain[pidx] = reinterpret_cast<const double2 *>(internal)[i];
+      }
     }
   }
 }
 
 cudaError_t launch_pack(int prec, int to_internal, long N, int n_k, int n_orb, int n_batches, void *internal,
-                        double *plain, cudaStream_t s) {
+                        void *internal_lo, double *plain, cudaStream_t s) {
   const int BS = prec == P_C64 ? 2 * OVC : OVC;
   const long total = (long)n_k * n_batches * N * BS;
   long g = (total + 255) / 256;
   if (g > 152 * 32) g = 152 * 32;
-  pack_kernel<<<(int)g, 256, 0, s>>>(to_internal, N, n_k, n_orb, n_batches, BS, (double2 *)internal,
-                                     (double2 *)plain);
+  pack_kernel<<<(int)g, 256, 0, s>>>(to_internal, prec == P_C64, N, n_k, n_orb, n_batches, BS, internal,
+                                     internal_lo, (double2 *)plain);
   return cudaGetLastError();
 }
 

@@ -1,5 +1,6 @@
 // C interface of the TDKS library: system objects, host-side set-up (finite-difference
 // weights, projector spheres, field, sub-step policy) and the propagation driver.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -15,6 +16,24 @@
 using namespace tdks;
 
 namespace {
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(f);
+  }
+  return fn;
+}
 
 thread_local std::string g_err;
 
@@ -81,7 +100,9 @@ struct tdks_system {
   std::vector<double> pos, D;
   double vloc_absmax = 0.0, vnl_bound = 0.0;
   // device buffers
-  void *psi = nullptr;          // packed complex128 state
+  void *psi = nullptr;          // packed state: complex128, or the hi part (complex64) of a
+                                // complex64 system's double-float state
+  void *psi_lo = nullptr;       // lo part of a complex64 system's state
   void *term[3] = {nullptr, nullptr, nullptr};
   double *vloc = nullptr;
   void *veff = nullptr;
@@ -95,6 +116,11 @@ struct tdks_system {
   ProjEntry *d_ent = nullptr;
   void *d_q = nullptr;
   double *staging = nullptr;
+  int *d_err = nullptr;
+  // TMA tensor maps over the four sweep inputs (state, t1, t2, t3) for the current tile
+  alignas(64) CUtensorMap tmaps[4];
+  bool tmaps_ok = false;
+  int path = 0;                 // 0: TMA sweep where possible, 1: general sweep
   size_t state_bytes = 0, term_bytes = 0;
   bool have_orbitals = false, dens_valid = false;
   long long steps = 0;
@@ -165,10 +191,16 @@ void sweep_geometry(const tdks_system *s, SweepParams &p) {
   p.n_batches = s->n_batches;
   int zc = s->zc;
   if (zc <= 0) {
-    // whole z columns unless that leaves fewer than ~4 CTAs per SM
+    // z-chunk length minimising (waves of work items) x (planes per item, including the
+    // 2M planes that prime each item's z-queue); one resident CTA per SM.
     const long per_plane = (long)p.n_tx * p.n_ty * p.n_kb;
-    zc = s->nz;
-    while (zc > 4 * s->M && per_plane * ((s->nz + zc - 1) / zc) < 152 * 4) zc = (zc + 1) / 2;
+    const long slots = 152;
+    long best = -1;
+    for (int c = 1; c <= s->nz; c++) {
+      const long items = per_plane * ((s->nz + c - 1) / c);
+      const long cost = ((items + slots - 1) / slots) * (c + 2 * s->M);
+      if (best < 0 || cost < best) { best = cost; zc = c; }
+    }
   }
   p.zc = zc;
   p.n_zc = (s->nz + zc - 1) / zc;
@@ -209,19 +241,46 @@ void sweep_common(const tdks_system *s, SweepParams &p, const double A[3]) {
   p.do_obs = 0;
 }
 
-int run_sweep(tdks_system *s, int mode, SweepParams &p) {
-  Timed tm(s, 0);
-  cudaError_t e = launch_sweep(s->M, s->prec, mode, s->bc == TDKS_BC_BLOCH, s->tx, s->ty, p, 0, s->stream);
+bool encode_map(const tdks_system *s, const void *ptr, CUtensorMap *out) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn || (reinterpret_cast<uintptr_t>(ptr) & 15) != 0) return false;
+  const cuuint64_t dims[5] = {16, (cuuint64_t)s->nx, (cuuint64_t)s->ny, (cuuint64_t)s->nz, (cuuint64_t)s->n_kb};
+  const cuuint64_t strides[4] = {64, 64ull * s->nx, 64ull * s->nx * s->ny, 64ull * (cuuint64_t)s->N};
+  const cuuint32_t box[5] = {16, (cuuint32_t)(s->tx + 2 * s->M), (cuuint32_t)(s->ty + 2 * s->M), 1, 1};
+  const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  return fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<void *>(ptr), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+void build_tmaps(tdks_system *s) {
+  s->tmaps_ok = false;
+  if (s->bc != TDKS_BC_ZERO || !tma_supported(s->M, s->tx, s->ty)) return;
+  const void *ins[4] = {s->psi, s->term[0], s->term[1], s->term[2]};
+  for (int i = 0; i < 4; i++)
+    if (!encode_map(s, ins[i], &s->tmaps[i])) return;
+  s->tmaps_ok = true;
+}
+
+// tm: tensor map over p.in (or null): finite boxes with a 16x8 tile take the TMA sweep.
+int run_sweep(tdks_system *s, int mode, SweepParams &p, const CUtensorMap *tm) {
+  Timed tmr(s, 0);
+  p.err = s->d_err;
+  cudaError_t e;
+  if (tm && s->path == 0 && s->bc == TDKS_BC_ZERO && tma_supported(s->M, s->tx, s->ty))
+    e = launch_sweep_tma(s->M, s->prec, mode, s->tx, s->ty, tm, p, 0, s->stream);
+  else
+    e = launch_sweep(s->M, s->prec, mode, s->bc == TDKS_BC_BLOCH, s->tx, s->ty, p, 0, s->stream);
   s->launches++;
   if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("stencil sweep: ") + cudaGetErrorString(e));
   return TDKS_OK;
 }
 
-int run_gather(tdks_system *s, const void *in, int from_psi, const double A[3]) {
+int run_gather(tdks_system *s, const void *in, const double A[3]) {
   if (s->n_atoms <= 0) return TDKS_OK;
   GatherParams g{};
   g.n_kb = s->n_kb; g.n_batches = s->n_batches; g.n_atoms = s->n_atoms; g.N = s->N;
-  g.in = in; g.from_psi = from_psi;
+  g.in = in;
   g.atom_begin = s->d_atom_begin; g.ent = s->d_ent; g.D = s->d_D;
   g.h3 = s->h * s->h * s->h;
   g.kvec = s->d_kvec;
@@ -238,7 +297,8 @@ int ensure_density(tdks_system *s) {
   if (!s->have_orbitals) return fail(TDKS_ESTATE, "orbitals not set");
   if (s->dens_valid) return TDKS_OK;
   Timed tm(s, 2);
-  cudaError_t e = launch_density(s->prec, s->N, s->n_kb, s->n_batches, s->psi, s->d_wocc, s->dens_part, s->stream);
+  cudaError_t e = launch_density(s->prec, s->N, s->n_kb, s->n_batches, s->psi, s->psi_lo, s->d_wocc,
+                                 s->dens_part, s->stream);
   s->launches++;
   if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("density: ") + cudaGetErrorString(e));
   s->dens_valid = true;
@@ -276,7 +336,7 @@ int run_finalize(tdks_system *s, double *rec, double t_state, const double E[3],
 // Sweep 1 of a sub-step (or an observation): term[0] = coef * H psi, with the energy
 // and current partial sums when `obs` is set.
 int first_sweep(tdks_system *s, double cr, double ci, const double A[3], bool obs) {
-  int rc = run_gather(s, s->psi, 1, A);
+  int rc = run_gather(s, s->psi, A);
   if (rc) return rc;
   SweepParams p{};
   sweep_common(s, p, A);
@@ -285,7 +345,7 @@ int first_sweep(tdks_system *s, double cr, double ci, const double A[3], bool ob
   p.out = s->term[0];
   p.do_obs = obs ? 1 : 0;
   if (obs && s->bc == TDKS_BC_BLOCH) p.grad_mask |= 8;
-  return run_sweep(s, MODE_FIRST, p);
+  return run_sweep(s, MODE_FIRST, p, s->tmaps_ok ? &s->tmaps[0] : nullptr);
 }
 
 // Gershgorin-type bound on |lambda| of H: kinetic maximum (the +/- alternating mode of
@@ -322,6 +382,17 @@ void free_proj(tdks_system *s) {
   s->d_ent = nullptr; s->d_q = nullptr; s->d_D = nullptr;
   s->n_atoms = 0;
   s->vnl_bound = 0.0;
+}
+
+// After a stream synchronise: report a kernel that gave up a bounded wait.
+int check_err(tdks_system *s) {
+  int h = 0;
+  CU(cudaMemcpy(&h, s->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h) {
+    CU(cudaMemset(s->d_err, 0, sizeof(int)));
+    return fail(TDKS_ETIMEOUT, "a sweep kernel gave up waiting for its TMA copies");
+  }
+  return TDKS_OK;
 }
 
 double coord_of(const tdks_system *s, int axis, int i) {
@@ -365,8 +436,8 @@ int tdks_create_grid(int nx, int ny, int nz, double h, int fd_order, int bc, int
   if (kweights) for (int i = 0; i < n_k; i++) s->kw[i] = kweights[i];
   cudaGetDevice(&s->dev);
   const size_t pts = (size_t)s->n_kb * N;
-  s->state_bytes = pts * OVC * 16 * (prec == TDKS_C64 ? 2 : 1);
   s->term_bytes = pts * OVC * 16;
+  s->state_bytes = s->term_bytes;
   const int nlda = lda_blocks(N);
   auto cleanup = [&](int code, const std::string &m) { tdks_destroy(s); return fail(code, m); };
 #define ALLOC(ptr, bytes)                                                                    \
@@ -375,7 +446,9 @@ int tdks_create_grid(int nx, int ny, int nz, double h, int fd_order, int bc, int
     if (e_ != cudaSuccess) { cudaGetLastError(); return cleanup(TDKS_ENOMEM, std::string("cudaMalloc ") + #ptr); } \
   } while (0)
   ALLOC(s->psi, s->state_bytes);
+  if (prec == TDKS_C64) ALLOC(s->psi_lo, s->state_bytes);
   for (int i = 0; i < 3; i++) ALLOC(s->term[i], s->term_bytes);
+  ALLOC(s->d_err, sizeof(int));
   ALLOC(s->vloc, N * sizeof(double));
   ALLOC(s->veff, N * (prec == TDKS_C64 ? sizeof(float) : sizeof(double)));
   ALLOC(s->dens_part, pts * sizeof(double));
@@ -393,8 +466,11 @@ int tdks_create_grid(int nx, int ny, int nz, double h, int fd_order, int bc, int
 #undef ALLOC
   if (cudaMemcpy(s->d_kvec, s->kpts.data(), 3 * n_k * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemsetAsync(s->vloc, 0, N * sizeof(double), s->stream) != cudaSuccess ||
-      cudaMemsetAsync(s->psi, 0, s->state_bytes, s->stream) != cudaSuccess)
+      cudaMemsetAsync(s->psi, 0, s->state_bytes, s->stream) != cudaSuccess ||
+      (s->psi_lo && cudaMemsetAsync(s->psi_lo, 0, s->state_bytes, s->stream) != cudaSuccess) ||
+      cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream) != cudaSuccess)
     return cleanup(TDKS_EDEVICE, "initial copies");
+  build_tmaps(s);
   std::vector<double> wocc(n_k);
   for (int i = 0; i < n_k; i++) wocc[i] = s->kw[i] * s->occ;
   if (cudaMemcpy(s->d_wocc, wocc.data(), n_k * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
@@ -408,6 +484,8 @@ int tdks_destroy(tdks_sys s) {
   cudaStreamSynchronize(s->stream);
   free_proj(s);
   cudaFree(s->psi);
+  cudaFree(s->psi_lo);
+  cudaFree(s->d_err);
   for (int i = 0; i < 3; i++) cudaFree(s->term[i]);
   cudaFree(s->vloc); cudaFree(s->veff); cudaFree(s->dens_part); cudaFree(s->lda_part);
   cudaFree(s->obs_part); cudaFree(s->ring); cudaFree(s->obs_rec); cudaFree(s->d_kvec); cudaFree(s->d_wocc);
@@ -439,7 +517,7 @@ int tdks_set_orbitals(tdks_sys s, const double *psi) {
   int rc = ensure_staging(s);
   if (rc) return rc;
   CU(cudaMemcpyAsync(s->staging, psi, (size_t)s->n_k * s->N * s->n_orb * 16, cudaMemcpyHostToDevice, s->stream));
-  CU(launch_pack(s->prec, 1, s->N, s->n_k, s->n_orb, s->n_batches, s->psi, s->staging, s->stream));
+  CU(launch_pack(s->prec, 1, s->N, s->n_k, s->n_orb, s->n_batches, s->psi, s->psi_lo, s->staging, s->stream));
   s->launches++;
   s->have_orbitals = true;
   s->dens_valid = false;
@@ -450,12 +528,12 @@ int tdks_get_orbitals(tdks_sys s, double *psi_out) {
   if (!s || !psi_out) return fail(TDKS_EINVAL, "NULL argument");
   int rc = ensure_staging(s);
   if (rc) return rc;
-  CU(launch_pack(s->prec, 0, s->N, s->n_k, s->n_orb, s->n_batches, s->psi, s->staging, s->stream));
+  CU(launch_pack(s->prec, 0, s->N, s->n_k, s->n_orb, s->n_batches, s->psi, s->psi_lo, s->staging, s->stream));
   s->launches++;
   CU(cudaMemcpyAsync(psi_out, s->staging, (size_t)s->n_k * s->N * s->n_orb * 16, cudaMemcpyDeviceToHost,
                      s->stream));
   CU(cudaStreamSynchronize(s->stream));
-  return TDKS_OK;
+  return check_err(s);
 }
 
 int tdks_set_atoms_projectors(tdks_sys s, int n_atoms, const double *pos, const double *D, double r_c,
@@ -590,7 +668,16 @@ int tdks_set_tile(tdks_sys s, int tx, int ty, int zc) {
   const bool ok = (tx == 16 && ty == 8) || (tx == 32 && ty == 4) || (tx == 8 && ty == 8);
   if (!ok) return fail(TDKS_EINVAL, "tile must be one of 16x8, 32x4, 8x8");
   if (zc < 0) return fail(TDKS_EINVAL, "zc < 0");
+  CU(cudaStreamSynchronize(s->stream));
   s->tx = tx; s->ty = ty; s->zc = zc;
+  build_tmaps(s);
+  return TDKS_OK;
+}
+
+int tdks_set_sweep_path(tdks_sys s, int path) {
+  if (!s) return fail(TDKS_EINVAL, "NULL system");
+  if (path != 0 && path != 1) return fail(TDKS_EINVAL, "path must be 0 (TMA where possible) or 1 (general)");
+  s->path = path;
   return TDKS_OK;
 }
 
@@ -605,13 +692,15 @@ int tdks_apply_H(tdks_sys s, double t, const void *dev_in, void *dev_out) {
   else CU(cudaMemsetAsync(s->dens_part, 0, (size_t)s->n_kb * s->N * sizeof(double), s->stream));
   if (rc) return rc;
   if ((rc = run_lda(s, E, A))) return rc;
-  if ((rc = run_gather(s, dev_in, 0, A))) return rc;
+  if ((rc = run_gather(s, dev_in, A))) return rc;
   SweepParams p{};
   sweep_common(s, p, A);
   p.cr = 1.0; p.ci = 0.0;
   p.in = dev_in;
   p.out = dev_out;
-  return run_sweep(s, MODE_MID, p);
+  alignas(64) CUtensorMap tm;
+  const bool have_tm = s->bc == TDKS_BC_ZERO && tma_supported(s->M, s->tx, s->ty) && encode_map(s, dev_in, &tm);
+  return run_sweep(s, MODE_MID, p, have_tm ? &tm : nullptr);
 }
 
 int tdks_auto_substeps(tdks_sys s, double dt, int *substeps) {
@@ -646,19 +735,20 @@ int tdks_propagate_n(tdks_sys s, double t0, double dt, int n_steps, int substeps
       }
       for (int k = 2; k <= 4; k++) {
         const void *in = s->term[k - 2];
-        if ((rc = run_gather(s, in, 0, A))) return rc;
+        if ((rc = run_gather(s, in, A))) return rc;
         SweepParams p{};
         sweep_common(s, p, A);
         p.cr = 0.0; p.ci = -dts / k;
         p.in = in;
         if (k < 4) {
           p.out = s->term[k - 1];
-          if ((rc = run_sweep(s, MODE_MID, p))) return rc;
+          if ((rc = run_sweep(s, MODE_MID, p, s->tmaps_ok ? &s->tmaps[k - 1] : nullptr))) return rc;
         } else {
           p.psi = s->psi;
+          p.psi_lo = s->psi_lo;
           p.t1 = s->term[0];
           p.t2 = s->term[1];
-          if ((rc = run_sweep(s, MODE_LAST, p))) return rc;
+          if ((rc = run_sweep(s, MODE_LAST, p, s->tmaps_ok ? &s->tmaps[3] : nullptr))) return rc;
         }
       }
       s->dens_valid = true;  // MODE_LAST wrote the density of the new state
@@ -673,6 +763,7 @@ int tdks_reductions(tdks_sys s, long long step_from, int n, double *out) {
   if (n < 0 || step_from < 0 || step_from + n > s->steps || step_from < s->steps - tdks_system::RING)
     return fail(TDKS_EINVAL, "record range outside the stored ring");
   CU(cudaStreamSynchronize(s->stream));
+  if (int rc = check_err(s)) return rc;
   for (int i = 0; i < n;) {
     const long long slot = (step_from + i) % tdks_system::RING;
     const int cnt = (int)std::min<long long>(n - i, tdks_system::RING - slot);
@@ -700,7 +791,7 @@ int tdks_observe(tdks_sys s, double t_state, double t_field, double *out) {
   if ((rc = run_finalize(s, s->obs_rec, t_state, E, A))) return rc;
   CU(cudaMemcpyAsync(out, s->obs_rec, TDKS_RECORD * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
   CU(cudaStreamSynchronize(s->stream));
-  return TDKS_OK;
+  return check_err(s);
 }
 
 int tdks_set_profiling(tdks_sys s, int on) {

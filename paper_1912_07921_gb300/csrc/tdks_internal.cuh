@@ -9,9 +9,11 @@
 //             complex64 -> 2 orbitals; OVC = 4 vectors per (point, batch), i.e. 64 B.
 //
 // complex128 systems: BS = 4, the state and the Taylor terms are complex128.
-// complex64  systems: BS = 8, the Taylor terms are complex64 and the state (the running
-//                     sum of the series) stays complex128, so the state block of a
-//                     (point, batch) is 128 B and each thread owns two complex128.
+// complex64  systems: BS = 8, the Taylor terms are complex64; the state (the running sum
+//                     of the series) is a double-float pair hi + lo of two complex64
+//                     arrays (~48-bit significand), updated with error-free FP32
+//                     transformations, because GB300 runs FP64 at a small fraction of its
+//                     FP32 rate; density, potentials and reductions are FP64.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -45,7 +47,9 @@ struct SweepParams {
   double cr, ci;              // out = (cr + i ci) * (H in)
   const void *in;             // stencil input (psi storage in MODE_FIRST, term storage else)
   void *out;                  // term output (MODE_FIRST / MODE_MID)
-  void *psi;                  // MODE_LAST: state, read and written in place
+  void *psi;                  // MODE_LAST: state (complex128, or the hi part of a complex64
+                              // system's double-float state), read and written in place
+  void *psi_lo;               // MODE_LAST, complex64 systems: lo part of the state
   const void *t1, *t2;        // MODE_LAST: earlier terms
   const void *veff;           // [N] diagonal potential (float for c64, double for c128)
   // projectors (scatter side)
@@ -64,13 +68,13 @@ struct SweepParams {
   double *obs_part;           // [n_items][4]: <psi|H psi> weighted, current x,y,z
   const double *wocc;         // [n_k] k-weight times occupation
   double *dens_part;          // [n_kb][N] (MODE_LAST)
+  int *err;                   // device error word (bounded waits that ran out set it)
 };
 
 struct GatherParams {
   int n_kb, n_batches, n_atoms;
   long N;
-  const void *in;             // psi storage (from_psi) or term storage
-  int from_psi;
+  const void *in;             // stencil input (state or hi part of the state, or a term)
   const int *atom_begin;      // [n_atoms+1] entry ranges (atom-major)
   const ProjEntry *ent;
   const double *D;            // [n_atoms][4]
@@ -88,7 +92,7 @@ size_t sweep_smem(int M, int tx, int ty);
 
 // Launchers (tdks_aux.cu)
 cudaError_t launch_gather(int prec, int bloch, const GatherParams &p, cudaStream_t s);
-cudaError_t launch_density(int prec, long N, int n_kb, int n_batches, const void *psi,
+cudaError_t launch_density(int prec, long N, int n_kb, int n_batches, const void *psi, const void *psi_lo,
                            const double *wocc, double *dens_part, cudaStream_t s);
 cudaError_t launch_lda(int prec, int bloch, long N, int nx, int ny, int nz, double h,
                        int n_kb, const double *dens_part, const double *vloc, int xc,
@@ -99,7 +103,13 @@ cudaError_t launch_finalize(const double *obs_part, long n_items, const double *
                             double occ, int bloch, double omega_cell, const double A[3],
                             double field_val, cudaStream_t s);
 cudaError_t launch_pack(int prec, int to_internal, long N, int n_k, int n_orb, int n_batches,
-                        void *internal, double *plain, cudaStream_t s);
+                        void *internal, void *internal_lo, double *plain, cudaStream_t s);
+
+// TMA sweep for finite boxes (tdks_sweep_tma.cu).  tmap: CUtensorMap (64-byte aligned
+// blob) over the stencil input, dims {16 floats, nx, ny, nz, n_kb}, box {16, TX+2M, TY+2M, 1, 1}.
+cudaError_t launch_sweep_tma(int M, int prec, int mode, int tx, int ty, const void *tmap,
+                             const SweepParams &p, int grid, cudaStream_t s);
+bool tma_supported(int M, int tx, int ty);
 int lda_blocks(long N);
 
 }  // namespace tdks

@@ -19,22 +19,16 @@
 //     (mostly L2 hits: concurrently running CTAs march the same z range);
 //   * next-plane loads are issued before the barrier of the current plane, so their
 //     latency overlaps the current plane's arithmetic; one __syncthreads per plane;
-//   * MODE_FIRST reads the complex128 state and (optionally) accumulates the energy and
-//     current partial sums; MODE_LAST adds psi + t1 + t2 + t3 + t4 in FP64 in place and
+//   * MODE_FIRST reads the state (the hi part of a complex64 system's double-float state)
+//     and optionally accumulates the energy and current partial sums; MODE_LAST adds
+//     psi + t1 + t2 + t3 + t4 in place (FP64, or double-float for complex64 systems) and
 //     writes each point's density contribution for the next sub-step.
+// This is the general path (any boundary, loads through L1/L2); finite boxes use the
+// TMA-fed sweep of tdks_sweep_tma.cu.
 #include "tdks_internal.cuh"
-#include "tdks_vec.cuh"
+#include "tdks_sweep_common.cuh"
 
 namespace tdks {
-
-template <int P, int MODE>
-struct InLoad {
-  typedef typename VT<P>::V V;
-  static __device__ __forceinline__ V ld(const void *base, long pt, int v) {
-    if (MODE == MODE_FIRST) return VT<P>::ld_state(reinterpret_cast<const double2 *>(base), pt, v);
-    return VT<P>::ld(reinterpret_cast<const V *>(base) + pt * OVC + v);
-  }
-};
 
 // floor(i / n) for possibly negative i
 __device__ __forceinline__ int floordiv(int i, int n) { return i >= 0 ? i / n : -((-i - 1) / n) - 1; }
@@ -67,8 +61,9 @@ sweep_kernel(const SweepParams p) {
   S W[M + 1];
 #pragma unroll
   for (int m = 0; m <= M; m++) W[m] = T::bc(p.w[m]);
-  const S CR = T::bc(p.cr), CI = T::bc(p.ci);
+  const typename W0T<P>::type w0 = (typename W0T<P>::type)p.w[0];
   const bool need_grad = BLOCH && (p.grad_mask != 0);
+  const bool grads = BLOCH && MODE == MODE_FIRST && (p.grad_mask & 8);
 
   for (long item = blockIdx.x; item < p.n_items; item += gridDim.x) {
     long it = item;
@@ -86,18 +81,26 @@ sweep_kernel(const SweepParams p) {
       kL[1] = p.kvec[3 * kidx + 1] * p.L[1];
       kL[2] = p.kvec[3 * kidx + 2] * p.L[2];
     }
+    const V *in = reinterpret_cast<const V *>(p.in);
 
     // boundary-extended load of the stencil input at grid position (x, y, z)
     auto load = [&](int x, int y, int z) -> V {
       if ((unsigned)x < (unsigned)nx && (unsigned)y < (unsigned)ny && (unsigned)z < (unsigned)nz)
-        return InLoad<P, MODE>::ld(p.in, kbN + ((long)z * ny + y) * nx + x, v);
+        return T::ld(in + (kbN + ((long)z * ny + y) * nx + x) * OVC + v);
       if (!BLOCH) return T::zero();
       const int wx = floordiv(x, nx), wy = floordiv(y, ny), wz = floordiv(z, nz);
       x -= wx * nx; y -= wy * ny; z -= wz * nz;
-      V a = InLoad<P, MODE>::ld(p.in, kbN + ((long)z * ny + y) * nx + x, v);
-      double s, c;
-      sincos(kL[0] * wx + kL[1] * wy + kL[2] * wz, &s, &c);
-      return T::cmul(T::bc(c), T::bc(s), a);
+      const V a = T::ld(in + (kbN + ((long)z * ny + y) * nx + x) * OVC + v);
+      const double ang = kL[0] * wx + kL[1] * wy + kL[2] * wz;
+      if constexpr (P == P_C64) {
+        float s, c;
+        sincosf((float)ang, &s, &c);
+        return T::cmul(pk2(c, c), pk2(s, s), a);
+      } else {
+        double s, c;
+        sincos(ang, &s, &c);
+        return T::cmul(T::bc(c), T::bc(s), a);
+      }
     };
 
     const int gx = tx * TX + lx, gy = ty * TY + ly;
@@ -128,7 +131,7 @@ sweep_kernel(const SweepParams p) {
     }
     const int csl = ((ly + M) * SX + (lx + M)) * OVC + v;
 
-    V Q[2 * M];
+    V Q[2 * M + 1];
 #pragma unroll
     for (int j = 0; j < 2 * M; j++) Q[j] = load(gx, gy, z0 - M + j);
     V H[HPT];
@@ -140,155 +143,47 @@ sweep_kernel(const SweepParams p) {
     for (int j = 0; j < HPT; j++)
       if (hsl[j] >= 0) sm[hsl[j]] = H[j];
 
-    double acc_e = 0.0, acc_j[3] = {0.0, 0.0, 0.0};
+    ObsAcc<P> oa;
 
     for (int z = z0; z < z1; z++) {
       const int buf = (z - z0) & 1;
-      const V Qn = load(gx, gy, z + M);
+      Q[2 * M] = load(gx, gy, z + M);
 #pragma unroll
       for (int j = 0; j < HPT; j++)
         if (hsl[j] >= 0) H[j] = load(hgx[j], hgy[j], z + 1);
       const long pt = ((long)z * ny + gy) * nx + gx;
+      const long idx = (kbN + pt) * OVC + v;
       R ve = R(0);
       int r0 = 0, r1 = 0;
-      V T1 = T::zero(), T2 = T::zero();
-      double2 PS[2] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+      LastOperands<P> lop;
+      lop.hi = lop.lo = lop.t1 = lop.t2 = T::zero();
       if (own) {
         ve = reinterpret_cast<const R *>(p.veff)[pt];
         if (p.rowptr) { r0 = __ldg(p.rowptr + pt); r1 = __ldg(p.rowptr + pt + 1); }
-        if (MODE == MODE_LAST) {
-          T1 = T::ld(reinterpret_cast<const V *>(p.t1) + (kbN + pt) * OVC + v);
-          T2 = T::ld(reinterpret_cast<const V *>(p.t2) + (kbN + pt) * OVC + v);
-          const double2 *ps = reinterpret_cast<const double2 *>(p.psi) + (kbN + pt) * (OVC * T::CPV) + T::CPV * v;
-#pragma unroll
-          for (int c = 0; c < T::CPV; c++) PS[c] = ps[c];
-        }
+        if (MODE == MODE_LAST) load_last<P>(p, idx, lop);
       }
       __syncthreads();
-      const V *Sp = sm + buf * PLANE;
-      const V c0 = Q[M];
-      V acc = T::mul(T::bc((double)ve + p.w[0]), c0);
-      V gsum = T::zero();
       V gax[3] = {T::zero(), T::zero(), T::zero()};
-#pragma unroll
-      for (int m = 1; m <= M; m++) {
-        const V zm = Q[M - m];
-        const V zp = (M + m < 2 * M) ? Q[M + m] : Qn;
-        const V xm = Sp[csl - m * OVC], xp = Sp[csl + m * OVC];
-        const V ym = Sp[csl - m * SX * OVC], yp = Sp[csl + m * SX * OVC];
-        const V s6 = T::add(T::add(T::add(zm, zp), T::add(xm, xp)), T::add(ym, yp));
-        acc = T::fma(W[m], s6, acc);
-        if (need_grad) {
-          const V dx = T::sub(xp, xm), dy = T::sub(yp, ym), dz = T::sub(zp, zm);
-          gsum = T::fma(T::bc(p.A[0] * p.gw[m]), dx,
-                        T::fma(T::bc(p.A[1] * p.gw[m]), dy, T::fma(T::bc(p.A[2] * p.gw[m]), dz, gsum)));
-          if (MODE == MODE_FIRST && (p.grad_mask & 8)) {
-            const S gm = T::bc(p.gw[m]);
-            gax[0] = T::fma(gm, dx, gax[0]);
-            gax[1] = T::fma(gm, dy, gax[1]);
-            gax[2] = T::fma(gm, dz, gax[2]);
-          }
-        }
-      }
-      if (need_grad) acc = T::add(acc, T::negi(gsum));
-      // Kleinman-Bylander scatter: sum_aj beta_aj(r) phase* q_aj
-      if (own && r1 > r0) {
-        for (int e = r0; e < r1; e++) {
-          const ProjEntry &E = p.ent[__ldg(p.rowent + e)];
-          const V *qa = reinterpret_cast<const V *>(p.q) + ((long)(kb * p.n_atoms + E.atom) * 4) * OVC + v;
-          V nl;
-          if (P == P_C64) {
-            nl = T::mul(T::bc(E.beta[0]), T::ld(qa));
-#pragma unroll
-            for (int j = 1; j < 4; j++) nl = T::fma(T::bc(E.beta[j]), T::ld(qa + j * OVC), nl);
-          } else {
-            nl = T::mul(T::bc(E.betad[0]), T::ld(qa));
-#pragma unroll
-            for (int j = 1; j < 4; j++) nl = T::fma(T::bc(E.betad[j]), T::ld(qa + j * OVC), nl);
-          }
-          if (BLOCH || p.grad_mask) {
-            double ang = 0.0;
-            if (BLOCH)
-              ang += p.kvec[3 * kidx] * E.T[0] + p.kvec[3 * kidx + 1] * E.T[1] + p.kvec[3 * kidx + 2] * E.T[2];
-            ang += p.A[0] * E.d[0] + p.A[1] * E.d[1] + p.A[2] * E.d[2];
-            double s, c;
-            sincos(ang, &s, &c);
-            nl = T::cmul(T::bc(c), T::bc(-s), nl);
-          }
-          acc = T::add(acc, nl);
-        }
-      }
+      V acc = stencil_point<M, P, BLOCH>(p, W, w0, Q, sm + buf * PLANE, csl, SX * OVC, ve, need_grad, grads, gax);
+      if (own && r1 > r0) acc = kb_scatter<P, BLOCH>(p, kb, kidx, v, r0, r1, acc);
       if (MODE == MODE_FIRST && p.do_obs && own) {
-        double2 cd[2], hd[2];
-        T::to_d(c0, cd);
-        T::to_d(acc, hd);
+        oa.add_e(Q[M], acc);
+        if (grads) {
 #pragma unroll
-        for (int c = 0; c < T::CPV; c++) acc_e += cd[c].x * hd[c].x + cd[c].y * hd[c].y;
-        if (BLOCH && (p.grad_mask & 8)) {
-#pragma unroll
-          for (int a = 0; a < 3; a++) {
-            double2 gd[2];
-            T::to_d(gax[a], gd);
-#pragma unroll
-            for (int c = 0; c < T::CPV; c++) acc_j[a] += cd[c].x * gd[c].y - cd[c].y * gd[c].x;
-          }
+          for (int a = 0; a < 3; a++) oa.add_j(a, Q[M], gax[a]);
         }
       }
-      const V outv = T::cmul(CR, CI, acc);
-      if (MODE != MODE_LAST) {
-        if (own) reinterpret_cast<V *>(p.out)[(kbN + pt) * OVC + v] = outv;
-      } else {
-        double2 a1[2], a2[2], a3[2], a4[2];
-        T::to_d(T1, a1);
-        T::to_d(T2, a2);
-        T::to_d(c0, a3);
-        T::to_d(outv, a4);
-        double dsum = 0.0;
-#pragma unroll
-        for (int c = 0; c < T::CPV; c++) {
-          double re = PS[c].x + a1[c].x;
-          double im = PS[c].y + a1[c].y;
-          re += a2[c].x; im += a2[c].y;
-          re += a3[c].x; im += a3[c].y;
-          re += a4[c].x; im += a4[c].y;
-          PS[c] = make_double2(re, im);
-          dsum += re * re + im * im;
-        }
-        if (own) {
-          double2 *ps = reinterpret_cast<double2 *>(p.psi) + (kbN + pt) * (OVC * T::CPV) + T::CPV * v;
-#pragma unroll
-          for (int c = 0; c < T::CPV; c++) ps[c] = PS[c];
-        }
-        // lanes 4j..4j+3 hold the OVC vectors of one point
-        dsum += __shfl_xor_sync(0xffffffffu, dsum, 1);
-        dsum += __shfl_xor_sync(0xffffffffu, dsum, 2);
-        if (own && v == 0) p.dens_part[kbN + pt] = p.wocc[kidx] * dsum;
-      }
+      finish_point<P, MODE>(p, own, idx, v, kidx, Q[M], acc, lop);
       // plane z+1 into the other buffer
       V *Sn = sm + (buf ^ 1) * PLANE;
-      Sn[csl] = (M + 1 < 2 * M) ? Q[M + 1] : Qn;
+      Sn[csl] = Q[M + 1];
 #pragma unroll
       for (int j = 0; j < HPT; j++)
         if (hsl[j] >= 0) Sn[hsl[j]] = H[j];
 #pragma unroll
-      for (int j = 0; j < 2 * M - 1; j++) Q[j] = Q[j + 1];
-      Q[2 * M - 1] = Qn;
+      for (int j = 0; j < 2 * M; j++) Q[j] = Q[j + 1];
     }
-    if (MODE == MODE_FIRST && p.do_obs) {
-      double vals[4] = {acc_e, acc_j[0], acc_j[1], acc_j[2]};
-#pragma unroll
-      for (int i = 0; i < 4; i++) {
-        double x = vals[i];
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        if ((tid & 31) == 0) red[tid >> 5][i] = x;
-      }
-      __syncthreads();
-      if (tid < 4) {
-        double x = 0.0;
-        for (int w = 0; w < NT / 32; w++) x += red[w][tid];
-        p.obs_part[item * 4 + tid] = p.wocc[kidx] * x;
-      }
-    }
+    if (MODE == MODE_FIRST && p.do_obs) reduce_obs<P, NT>(p, oa, item, kidx, red);
     __syncthreads();
   }
 }

@@ -48,6 +48,35 @@ __device__ __forceinline__ u64 ipos2(u64 a) {
   float2 f = up2(a);
   return pk2(-f.y, f.x);
 }
+constexpr u64 SIGN2 = 0x8000000080000000ull;
+
+// Double-float arithmetic (a value is the unevaluated sum hi + lo of two FP32 numbers,
+// |lo| <= ulp(hi)/2, ~48-bit significand), from the error-free transformations of
+// Knuth (TwoSum) and Dekker (FastTwoSum); lane-wise on packed pairs.
+// (hi, lo) + d  ->  (ho, lout)
+__device__ __forceinline__ void df_add2(u64 hi, u64 lo, u64 d, u64 &ho, u64 &lout) {
+  const u64 s = add2(hi, d);
+  const u64 bb = sub2(s, hi);
+  u64 e = add2(sub2(hi, sub2(s, bb)), sub2(d, bb));
+  e = add2(e, lo);
+  ho = add2(s, e);
+  lout = sub2(e, sub2(ho, s));
+}
+// scalar TwoSum: s + e = a + b exactly
+__device__ __forceinline__ float two_sum(float a, float b, float &e) {
+  const float s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+  return s;
+}
+// accumulate x into the double-float (h, l)
+__device__ __forceinline__ void df_acc(float &h, float &l, float x) {
+  float e;
+  const float s = two_sum(h, x, e);
+  l += e;
+  h = s + l;
+  l = l - (h - s);
+}
 
 template <int P> struct VT;
 
@@ -57,6 +86,8 @@ template <> struct VT<P_C128> {
   typedef double R;   // scalar type of the potential arrays
   static __device__ __forceinline__ V zero() { return make_double2(0.0, 0.0); }
   static __device__ __forceinline__ S bc(double s) { return s; }
+  // diagonal (V_eff(r) + w0) broadcast, in the compute precision
+  static __device__ __forceinline__ S diag(R ve, double w0) { return ve + w0; }
   static __device__ __forceinline__ V add(V a, V b) { return make_double2(a.x + b.x, a.y + b.y); }
   static __device__ __forceinline__ V sub(V a, V b) { return make_double2(a.x - b.x, a.y - b.y); }
   static __device__ __forceinline__ V mul(S s, V a) { return make_double2(s * a.x, s * a.y); }
@@ -70,11 +101,6 @@ template <> struct VT<P_C128> {
   // -i a
   static __device__ __forceinline__ V negi(V a) { return make_double2(a.y, -a.x); }
   static __device__ __forceinline__ V ld(const V *p) { return __ldg(p); }
-  // state storage (complex128) -> compute vector
-  static __device__ __forceinline__ V ld_state(const double2 *psi, long pt, int v) {
-    return __ldg(psi + pt * OVC + v);
-  }
-  // sum over the vector's complex entries of w * |a|^2, and the vector as doubles
   static __device__ __forceinline__ void to_d(V a, double2 *o) { o[0] = a; }
   static constexpr int CPV = 1;  // complex values per vector
 };
@@ -85,6 +111,7 @@ template <> struct VT<P_C64> {
   typedef float R;
   static __device__ __forceinline__ V zero() { return make_ulonglong2(0ull, 0ull); }
   static __device__ __forceinline__ S bc(double s) { float f = (float)s; return pk2(f, f); }
+  static __device__ __forceinline__ S diag(R ve, float w0) { const float d = ve + w0; return pk2(d, d); }
   static __device__ __forceinline__ V add(V a, V b) { return make_ulonglong2(add2(a.x, b.x), add2(a.y, b.y)); }
   static __device__ __forceinline__ V sub(V a, V b) { return make_ulonglong2(sub2(a.x, b.x), sub2(a.y, b.y)); }
   static __device__ __forceinline__ V mul(S s, V a) { return make_ulonglong2(mul2(s, a.x), mul2(s, a.y)); }
@@ -97,17 +124,85 @@ template <> struct VT<P_C64> {
     return make_ulonglong2(pk2(p.y, -p.x), pk2(q.y, -q.x));
   }
   static __device__ __forceinline__ V ld(const V *p) { return __ldg(p); }
-  static __device__ __forceinline__ V ld_state(const double2 *psi, long pt, int v) {
-    const double2 *b = psi + pt * (2 * OVC) + 2 * v;
-    double2 a = __ldg(b), c = __ldg(b + 1);
-    return make_ulonglong2(pk2((float)a.x, (float)a.y), pk2((float)c.x, (float)c.y));
-  }
   static __device__ __forceinline__ void to_d(V a, double2 *o) {
     float2 p = up2(a.x), q = up2(a.y);
     o[0] = make_double2(p.x, p.y);
     o[1] = make_double2(q.x, q.y);
   }
   static constexpr int CPV = 2;
+};
+
+// ---------------------------------------------------------------------------------
+// Taylor combine of the last sweep and the point's density contribution.
+//   complex128: psi' = (((psi + t1) + t2) + t3) + t4 in FP64;
+//   complex64 : the state is the double-float pair (hi, lo); delta = t1+t2+t3+t4 in FP32,
+//               psi' = (hi, lo) + delta by TwoSum/FastTwoSum; |psi'|^2 as a double-float
+//               partial (hi^2 exactly by FMA, + 2 hi lo), no FP64 instruction per value.
+// dens_hi + dens_lo receives sum over the thread's complex entries of |psi'|^2.
+// ---------------------------------------------------------------------------------
+template <int P> struct Combine;
+
+template <> struct Combine<P_C128> {
+  typedef double2 V;
+  typedef double A;
+  static __device__ __forceinline__ void run(V &psi, V lo_unused, V t1, V t2, V t3, V t4, V &lo_out,
+                                             A &dh, A &dl) {
+    (void)lo_unused;
+    double re = psi.x + t1.x, im = psi.y + t1.y;
+    re += t2.x; im += t2.y;
+    re += t3.x; im += t3.y;
+    re += t4.x; im += t4.y;
+    psi = make_double2(re, im);
+    lo_out = make_double2(0.0, 0.0);
+    dh = re * re + im * im;
+    dl = 0.0;
+  }
+  // sum over the 4 consecutive lanes that hold one (point, batch)
+  static __device__ __forceinline__ void reduce4(A &h, A &l) {
+    h += __shfl_xor_sync(0xffffffffu, h, 1);
+    h += __shfl_xor_sync(0xffffffffu, h, 2);
+    (void)l;
+  }
+  static __device__ __forceinline__ double value(A h, A l) { (void)l; return h; }
+};
+
+template <> struct Combine<P_C64> {
+  typedef ulonglong2 V;
+  typedef float A;
+  static __device__ __forceinline__ float sq_parts(u64 h, u64 l, float &err) {
+    // sum of the two lanes' |x|^2 = (h + l)^2 ~ h^2 + 2 h l, returned as s + err
+    const u64 p = mul2(h, h);
+    const u64 e = fma2(add2(h, h), l, fma2(h, h, p ^ SIGN2));
+    const float2 pp = up2(p), ee = up2(e);
+    float e2;
+    const float s = two_sum(pp.x, pp.y, e2);
+    err = e2 + ee.x + ee.y;
+    return s;
+  }
+  static __device__ __forceinline__ void run(V &hi, V lo, V t1, V t2, V t3, V t4, V &lo_out,
+                                             A &dh, A &dl) {
+    const u64 dx = add2(add2(add2(t1.x, t2.x), t3.x), t4.x);
+    const u64 dy = add2(add2(add2(t1.y, t2.y), t3.y), t4.y);
+    u64 hx, lx, hy, ly;
+    df_add2(hi.x, lo.x, dx, hx, lx);
+    df_add2(hi.y, lo.y, dy, hy, ly);
+    hi = make_ulonglong2(hx, hy);
+    lo_out = make_ulonglong2(lx, ly);
+    float ea, eb, ec;
+    const float sa = sq_parts(hx, lx, ea), sb = sq_parts(hy, ly, eb);
+    dh = two_sum(sa, sb, ec);
+    dl = ea + eb + ec;
+  }
+  static __device__ __forceinline__ void reduce4(A &h, A &l) {
+#pragma unroll
+    for (int o = 1; o <= 2; o <<= 1) {
+      const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
+      float e;
+      h = two_sum(h, oh, e);
+      l = l + ol + e;
+    }
+  }
+  static __device__ __forceinline__ double value(A h, A l) { return (double)h + (double)l; }
 };
 
 }  // namespace tdks

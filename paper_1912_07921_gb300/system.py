@@ -78,6 +78,10 @@ class System:
     def set_tile(self, tx, ty, zc=0):
         _lib.check(self.lib.tdks_set_tile(self.h, tx, ty, zc))
 
+    def set_sweep_path(self, path: int):
+        """0: TMA-fed sweep where it applies (finite boxes, 16x8 tiles); 1: general sweep."""
+        _lib.check(self.lib.tdks_set_sweep_path(self.h, path))
+
     # -- queries ---------------------------------------------------------------------
     def get_orbitals(self) -> np.ndarray:
         out = np.empty(self.shape, dtype=np.complex128)
