@@ -38,6 +38,34 @@ METRIC = "H.psi orbital-gridpoint updates/s (medium molecule, Taylor-4 step)"
 UNIT = "updates/s"
 
 
+SWEEP_SOURCES = ["tdks_sweep_tma.cu", "tdks_sweep_common.cuh", "tdks_vec.cuh", "tdks_internal.cuh"]
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "tma_sweep_medium_molecule.md")
+
+
+def sweep_source_hash() -> str:
+    """Hash of the stencil-sweep sources: a DRAM traffic figure taken with ncu is used only
+    while the kernel it was measured on is unchanged."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in SWEEP_SOURCES:
+        with open(os.path.join(ROOT, "paper_1912_07921_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_per_launch():
+    """DRAM bytes (read + write) per sweep launch at 64 orbitals from the committed ncu
+    summary, or None when the summary is absent or was taken on other kernel sources."""
+    import re
+    if not os.path.exists(TRAFFIC_PROFILE):
+        return None
+    m = re.search(r"traffic_bytes_per_launch_64_orbitals:\s*([0-9.eE+]+)\s*\(sweep source hash ([0-9a-f]+)\)",
+                  open(TRAFFIC_PROFILE).read())
+    if not m or m.group(2) != sweep_source_hash():
+        return None
+    return float(m.group(1))
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -219,7 +247,9 @@ def run_ours(args, rank, world, local_rank):
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "kernel": "taylor stencil sweep (4 per sub-step)",
                          "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": _traffic_per_launch() if spec.n_orb == 64 and prec == I.PREC_C64 else None,
+                         "sweep_source_hash": sweep_source_hash(),
                          "bytes_per_launch": per_launch_bytes, "avg_launch_us": avg_launch_s * 1e6},
             "kernel_ms": {"sweep": sweep_ms, "sweep_launches": sweep_n, "gather": gath_ms,
                           "gather_launches": gath_n, "density_lda_finalize": aux_ms, "aux_launches": aux_n},
@@ -256,6 +286,58 @@ def run_c128_side(args):
     sysm.close()
     return {"value": spec.n_points * spec.n_orb * k / (ms / 1e3), "unit": UNIT, "steps": k,
             "ms_per_step": ms / k}
+
+
+def run_batched(args):
+    """The batched workload: n independent molecules (edges U[32,80], 4..32 orbitals,
+    0..12 atoms with projectors, complex64, 4th-order FD, h = 0.25, dt = 0.015), advanced
+    by one persistent sweep launch per Taylor term over all of them, replayed as a CUDA
+    graph."""
+    import torch
+    from paper_1912_07921_gb300 import inputs as I
+    from paper_1912_07921_gb300.system import Batch, System
+    specs = I.batched_systems(args.batched)
+    stream = torch.cuda.Stream()
+    systems = []
+    for sp in specs:
+        s = System(sp, I.make_inputs(sp), stream=stream.cuda_stream)
+        s.set_clock(0.0, sp.dt, sp.substeps)
+        systems.append(s)
+    b = Batch(systems, stream=stream.cuda_stream)
+    b.propagate(2)
+    torch.cuda.synchronize()
+    k = max(2, args.steps // 10)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = b.launch_count()
+    e0.record(stream)
+    b.propagate(k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    upd = sum(sp.n_points * sp.n_orb for sp in specs)
+    out = {"systems": len(specs), "value": upd * k / (ms / 1e3), "unit": UNIT, "steps": k,
+           "ms_per_step": ms / k, "values_per_step": upd, "launches": b.launch_count() - l0,
+           "graph": True}
+    b.close()
+    for s in systems:
+        s.close()
+    return out
+
+
+def run_serving(args):
+    """A scaled serving trace (Poisson arrivals) through the continuous-batching server."""
+    import torch
+    from paper_1912_07921_gb300 import serving
+    jobs = serving.serving_trace(args.serving, rate=20.0, seed=5, edge=(32, 64), orbitals=(4, 32),
+                                 steps=(50, 400), atoms=(0, 16))
+    stream = torch.cuda.Stream()
+    srv = serving.Server(hbm_budget=150 * 10 ** 9, max_slots=64, quantum=50, stream=stream.cuda_stream,
+                         sync=torch.cuda.synchronize)
+    srv.run(jobs)
+    r = srv.report()
+    r["trace"] = (f"{args.serving} jobs, Poisson 20/s, edges U[32,64], orbitals U[4,32], steps U[50,400], "
+                  f"atoms U[0,16], half complex64 / half complex128, 150 GB budget, 64 slots, quantum 50")
+    return r
 
 
 def cpu_baseline(n_orb_sample: int):
@@ -321,6 +403,10 @@ def main():
     ap.add_argument("--prec", default="c64", choices=["c64", "c128"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-c128", action="store_true", help="skip the complex128 side measurement")
+    ap.add_argument("--batched", type=int, default=0,
+                    help="also measure the batched workload with this many systems (e.g. 256)")
+    ap.add_argument("--serving", type=int, default=0,
+                    help="also run a serving trace with this many jobs")
     ap.add_argument("--n-orb", type=int, default=0,
                     help="orbital count override (profiling on a smaller case); 0 = the workload's 64")
     args = ap.parse_args()
@@ -339,6 +425,10 @@ def main():
     if rank == 0:
         if not args.no_c128 and args.prec == "c64" and world == 1:
             out["c128_path"] = run_c128_side(args)
+        if args.batched and world == 1:
+            out["batched"] = run_batched(args)
+        if args.serving and world == 1:
+            out["serving"] = run_serving(args)
         if not args.no_cpu and world == 1:
             out["cpu_baseline"] = cpu_baseline(8)
         print(json.dumps(out))

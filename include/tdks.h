@@ -204,6 +204,35 @@ int tdks_set_tile(tdks_sys sys, int tx, int ty, int zc);
  * values (to the last bits of FP64 rounding). */
 int tdks_set_sweep_path(tdks_sys sys, int path);
 
+/*
+ * Batched propagation of many independent finite-box systems (uneven grids, orbital and
+ * atom counts), the many-systems workload: per Taylor term one persistent sweep launch
+ * walks the work items of every system, with one batched projector gather, one batched
+ * LDA/V_eff launch and the record/clock kernels; a sub-step is captured once as a CUDA
+ * graph and replayed.  Each system advances from its own clock.  Results equal those of
+ * tdks_propagate_n on each system alone (the same per-point arithmetic and reduction
+ * order).
+ */
+typedef struct tdks_batch *tdks_batch_t;
+
+/* Clock of a system for batched propagation: state time t, step length dt, sub-steps
+ * per step (checked against the stability limit like tdks_propagate_n).
+ * tdks_propagate_n also leaves the clock at t0 + n_steps dt. */
+int tdks_set_clock(tdks_sys sys, double t, double dt, int substeps);
+int tdks_get_clock(tdks_sys sys, double *t, long long *steps);
+
+/* systems[n]: finite boxes sharing fd_order, precision and sub-step count, with orbitals
+ * set; they must outlive the batch and use the batch's stream (their work is enqueued
+ * there).  Device parameter tables are built here; the systems' potentials, projectors
+ * and fields must not change while the batch exists. */
+int tdks_batch_create(const tdks_sys *systems, int n, void *stream, tdks_batch_t *out);
+/* Advance every system of the batch by n_steps steps of its own dt (one observable record
+ * per step, as tdks_propagate_n).  use_graph = 1 replays a captured CUDA graph per
+ * sub-step.  Asynchronous on the batch's stream. */
+int tdks_batch_propagate(tdks_batch_t batch, int n_steps, int use_graph);
+int tdks_batch_launch_count(tdks_batch_t batch, long long *count);
+int tdks_batch_destroy(tdks_batch_t batch);
+
 const char *tdks_last_error(void);
 
 #ifdef __cplusplus

@@ -36,6 +36,12 @@ SIGNATURES = {
     "tdks_launch_count": ([P, PLL], I),
     "tdks_set_tile": ([P, I, I, I], I),
     "tdks_set_sweep_path": ([P, I], I),
+    "tdks_set_clock": ([P, D, D, I], I),
+    "tdks_get_clock": ([P, PD, PLL], I),
+    "tdks_batch_create": ([P, I, P, ctypes.POINTER(P)], I),
+    "tdks_batch_propagate": ([P, I, I], I),
+    "tdks_batch_launch_count": ([P, PLL], I),
+    "tdks_batch_destroy": ([P], I),
     "tdks_last_error": ([], ctypes.c_char_p),
 }
 

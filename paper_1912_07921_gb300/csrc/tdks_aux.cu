@@ -17,10 +17,9 @@ namespace tdks {
 constexpr int GATHER_THREADS = 256;
 
 template <int P, int BLOCH>
-__global__ void __launch_bounds__(GATHER_THREADS) gather_kernel(const GatherParams p) {
+__device__ __forceinline__ void gather_body(const GatherParams &p, int a, int kb) {
   typedef VT<P> T;
   typedef typename T::V V;
-  const int a = blockIdx.x, kb = blockIdx.y;
   const int kidx = kb / p.n_batches;
   const int tid = threadIdx.x, v = tid % OVC, lane = tid / OVC;
   constexpr int LANES = GATHER_THREADS / OVC;
@@ -92,6 +91,39 @@ __global__ void __launch_bounds__(GATHER_THREADS) gather_kernel(const GatherPara
       *q = make_double2(f * s0.x, f * s0.y);
     }
   }
+}
+
+template <int P, int BLOCH>
+__global__ void __launch_bounds__(GATHER_THREADS) gather_kernel(const GatherParams p) {
+  gather_body<P, BLOCH>(p, blockIdx.x, blockIdx.y);
+}
+
+// index of the system that owns unit u: begin[s] <= u < begin[s+1]
+__device__ __forceinline__ int find_sys(const long *begin, int n, long u) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (begin[mid] <= u) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Batched gather: one CTA per (system, atom, k-batch) over every system of a batch.
+template <int P>
+__global__ void __launch_bounds__(GATHER_THREADS)
+gather_batch_kernel(const GatherParams *gp, const long *begin, int n_sys) {
+  const int s = find_sys(begin, n_sys, blockIdx.x);
+  const GatherParams &p = gp[s];
+  const long u = blockIdx.x - begin[s];
+  gather_body<P, 0>(p, (int)(u % p.n_atoms), (int)(u / p.n_atoms));
+}
+
+cudaError_t launch_gather_batch(int prec, const GatherParams *gp, const long *begin, int n_sys, long total,
+                                cudaStream_t s) {
+  if (total <= 0) return cudaSuccess;
+  if (prec == P_C64) gather_batch_kernel<P_C64><<<(unsigned)total, GATHER_THREADS, 0, s>>>(gp, begin, n_sys);
+  else gather_batch_kernel<P_C128><<<(unsigned)total, GATHER_THREADS, 0, s>>>(gp, begin, n_sys);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_gather(int prec, int bloch, const GatherParams &p, cudaStream_t s) {
@@ -170,14 +202,13 @@ int lda_blocks(long N) {
 }
 
 template <typename R>
-__global__ void __launch_bounds__(LDA_THREADS)
-lda_kernel(long N, int nx, int ny, int nz, double h, int bloch, int n_kb, const double *dens_part,
-           const double *vloc, int xc, double Ex, double Ey, double Ez, double half_A2, R *veff,
-           double *lda_part) {
+__device__ __forceinline__ void lda_body(long N, int nx, int ny, int nz, double h, int bloch, int n_kb,
+                                         const double *dens_part, const double *vloc, int xc, double Ex, double Ey,
+                                         double Ez, double half_A2, R *veff, double *lda_part, int blk, int nblk) {
   double acc[6] = {0, 0, 0, 0, 0, 0};
   const double cx = bloch ? 0.0 : 0.5 * (nx - 1), cy = bloch ? 0.0 : 0.5 * (ny - 1),
                cz = bloch ? 0.0 : 0.5 * (nz - 1);
-  for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < N; p += (long)gridDim.x * blockDim.x) {
+  for (long p = blk * (long)blockDim.x + threadIdx.x; p < N; p += (long)nblk * blockDim.x) {
     double n = 0.0;
     for (int kb = 0; kb < n_kb; kb++) n += dens_part[(long)kb * N + p];
     const int ix = (int)(p % nx), iy = (int)((p / nx) % ny), iz = (int)(p / ((long)nx * ny));
@@ -204,8 +235,55 @@ lda_kernel(long N, int nx, int ny, int nz, double h, int bloch, int n_kb, const 
   if (threadIdx.x < 6) {
     double x = 0.0;
     for (int w = 0; w < LDA_THREADS / 32; w++) x += red[w][threadIdx.x];
-    lda_part[blockIdx.x * 6 + threadIdx.x] = x;
+    lda_part[blk * 6 + threadIdx.x] = x;
   }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(LDA_THREADS)
+lda_kernel(long N, int nx, int ny, int nz, double h, int bloch, int n_kb, const double *dens_part,
+           const double *vloc, int xc, double Ex, double Ey, double Ez, double half_A2, R *veff,
+           double *lda_part) {
+  lda_body<R>(N, nx, ny, nz, h, bloch, n_kb, dens_part, vloc, xc, Ex, Ey, Ez, half_A2, veff, lda_part, blockIdx.x,
+              gridDim.x);
+}
+
+// Laser field of a batched system at time t (finite boxes: length gauge or none).
+__device__ __forceinline__ double batch_field(const BatchAux &a, double t) {
+  if (a.gauge != 1) return 0.0;
+  double env = 1.0;
+  if (a.envelope == 1) {
+    if (t < 0.0 || t > a.t_total) return 0.0;
+    const double x = sin(3.14159265358979323846 * t / a.t_total);
+    env = x * x;
+  }
+  return a.amp * env * sin(a.omega * t);
+}
+
+// Batched LDA: the systems' CTA ranges are concatenated; the field is evaluated at each
+// system's current sub-step midpoint from its device clock.
+template <typename R>
+__global__ void __launch_bounds__(LDA_THREADS)
+lda_batch_kernel(const BatchAux *aux, const BatchClock *clk, const long *begin, int n_sys) {
+  __shared__ double f;
+  const int s = find_sys(begin, n_sys, blockIdx.x);
+  const BatchAux &a = aux[s];
+  if (threadIdx.x == 0) {
+    const BatchClock c = clk[s];
+    f = batch_field(a, c.t + (c.j + 0.5) * c.dt / c.substeps);
+  }
+  __syncthreads();
+  const double E = f;
+  lda_body<R>(a.N, a.nx, a.ny, a.nz, a.h, 0, a.n_kb, a.dens_part, a.vloc, a.xc, E * a.pol[0], E * a.pol[1],
+              E * a.pol[2], 0.0, reinterpret_cast<R *>(a.veff), a.lda_part, (int)(blockIdx.x - begin[s]),
+              a.n_lda);
+}
+
+cudaError_t launch_lda_batch(int prec, const BatchAux *aux, const BatchClock *clk, const long *begin, int n_sys,
+                             long total, cudaStream_t s) {
+  if (prec == P_C64) lda_batch_kernel<float><<<(unsigned)total, LDA_THREADS, 0, s>>>(aux, clk, begin, n_sys);
+  else lda_batch_kernel<double><<<(unsigned)total, LDA_THREADS, 0, s>>>(aux, clk, begin, n_sys);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_lda(int prec, int bloch, long N, int nx, int ny, int nz, double h, int n_kb,
@@ -227,9 +305,10 @@ cudaError_t launch_lda(int prec, int bloch, long N, int nx, int ny, int nz, doub
 //       J = -(1/Omega) (sum w f <phi|-i grad|phi> + A int n) (Sec. "Conductivities").
 // One CTA; partials are summed in index order.
 // ---------------------------------------------------------------------------------
-__global__ void finalize_kernel(const double *obs_part, long n_items, const double *lda_part, int n_lda,
-                                double *rec, double t_state, double h3, double occ, int bloch,
-                                double omega_cell, double Ax, double Ay, double Az, double field_val) {
+__device__ __forceinline__ void finalize_body(const double *obs_part, long n_items, const double *lda_part,
+                                              int n_lda, double *rec, double t_state, double h3, double occ,
+                                              int bloch, double omega_cell, double Ax, double Ay, double Az,
+                                              double field_val) {
   __shared__ double s_obs[256][4];
   __shared__ double s_lda[256][6];
   const int t = threadIdx.x;
@@ -263,6 +342,45 @@ __global__ void finalize_kernel(const double *obs_part, long n_items, const doub
     }
     rec[7] = field_val;
   }
+}
+
+__global__ void finalize_kernel(const double *obs_part, long n_items, const double *lda_part, int n_lda,
+                                double *rec, double t_state, double h3, double occ, int bloch,
+                                double omega_cell, double Ax, double Ay, double Az, double field_val) {
+  finalize_body(obs_part, n_items, lda_part, n_lda, rec, t_state, h3, occ, bloch, omega_cell, Ax, Ay, Az,
+                field_val);
+}
+
+// Batched observable records: one CTA per system, at the first sub-step of each step.
+__global__ void finalize_batch_kernel(const BatchAux *aux, const BatchClock *clk, int n_sys) {
+  const int s = blockIdx.x;
+  const BatchClock c = clk[s];
+  if (c.j != 0) return;
+  const BatchAux &a = aux[s];
+  const double h3 = a.h * a.h * a.h;
+  const double fv = batch_field(a, c.t + 0.5 * c.dt / c.substeps);
+  const double fpol = fv * (a.pol[0] * a.pol[0] + a.pol[1] * a.pol[1] + a.pol[2] * a.pol[2]);
+  finalize_body(a.obs_part, a.n_items, a.lda_part, a.n_lda, a.ring + (c.step % a.ring_len) * 8, c.t, h3, a.occ, 0,
+                (double)a.N * h3, 0.0, 0.0, 0.0, fpol);
+}
+
+// Advance every batched system's clock by one sub-step.
+__global__ void clock_batch_kernel(BatchClock *clk, int n_sys) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n_sys) return;
+  BatchClock c = clk[s];
+  if (++c.j == c.substeps) {
+    c.j = 0;
+    c.step++;
+    c.t += c.dt;
+  }
+  clk[s] = c;
+}
+
+cudaError_t launch_batch_tail(const BatchAux *aux, BatchClock *clk, int n_sys, int which, cudaStream_t s) {
+  if (which == 0) finalize_batch_kernel<<<n_sys, 256, 0, s>>>(aux, clk, n_sys);
+  else clock_batch_kernel<<<(n_sys + 127) / 128, 128, 0, s>>>(clk, n_sys);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_finalize(const double *obs_part, long n_items, const double *lda_part, int n_lda,

@@ -1,0 +1,261 @@
+// Batched propagation: many independent finite-box systems advanced together with one
+// persistent TMA sweep launch per Taylor term (plus one batched projector gather, one
+// batched LDA/V_eff and the record/clock kernels), the whole sub-step captured once as a
+// CUDA graph and replayed.  Every system keeps its own device clock (time, step length,
+// sub-step counter), so the graph needs no host-side parameter change between replays.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "tdks_system.h"
+
+using namespace tdks;
+using namespace tdks_host;
+
+struct tdks_batch {
+  std::vector<tdks_system *> sys;
+  cudaStream_t stream = nullptr;   // the caller's stream
+  cudaStream_t work = nullptr;     // private stream the batch captures and runs on
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  int M = 0, prec = 0, substeps = 0;
+  // device arrays
+  SweepParams *d_sweep[4] = {nullptr, nullptr, nullptr, nullptr};   // per Taylor term
+  GatherParams *d_gather[4] = {nullptr, nullptr, nullptr, nullptr};
+  CUtensorMap *d_maps = nullptr;                                    // 4 per system
+  long *d_item_begin = nullptr, *d_gather_begin = nullptr, *d_lda_begin = nullptr;
+  BatchAux *d_aux = nullptr;
+  BatchClock *d_clock = nullptr;
+  long total_items = 0, total_gather = 0, total_lda = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  long long launches = 0;
+};
+
+namespace {
+
+void batch_free(tdks_batch *b) {
+  for (int k = 0; k < 4; k++) { cudaFree(b->d_sweep[k]); cudaFree(b->d_gather[k]); }
+  cudaFree(b->d_maps); cudaFree(b->d_item_begin); cudaFree(b->d_gather_begin); cudaFree(b->d_lda_begin);
+  cudaFree(b->d_aux); cudaFree(b->d_clock);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->ev_in) cudaEventDestroy(b->ev_in);
+  if (b->ev_out) cudaEventDestroy(b->ev_out);
+  if (b->work) cudaStreamDestroy(b->work);
+}
+
+// Enqueue one sub-step of every system of the batch (11 launches).
+int enqueue_substep(tdks_batch *b) {
+  const int n = (int)b->sys.size();
+  cudaError_t e = launch_lda_batch(b->prec, b->d_aux, b->d_clock, b->d_lda_begin, n, b->total_lda, b->work);
+  if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("batched lda: ") + cudaGetErrorString(e));
+  for (int k = 0; k < 4; k++) {
+    e = launch_gather_batch(b->prec, b->d_gather[k], b->d_gather_begin, n, b->total_gather, b->work);
+    if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("batched gather: ") + cudaGetErrorString(e));
+    BatchSweepArgs a{b->d_sweep[k], b->d_maps, k, b->d_item_begin, n, b->total_items};
+    const int mode = k == 0 ? MODE_FIRST : (k == 3 ? MODE_LAST : MODE_MID);
+    e = launch_sweep_tma_batch(b->M, b->prec, mode, a, b->work);
+    if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("batched sweep: ") + cudaGetErrorString(e));
+    if (k == 0) {
+      e = launch_batch_tail(b->d_aux, b->d_clock, n, 0, b->work);
+      if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("batched records: ") + cudaGetErrorString(e));
+    }
+  }
+  e = launch_batch_tail(b->d_aux, b->d_clock, n, 1, b->work);
+  if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("batched clocks: ") + cudaGetErrorString(e));
+  b->launches += 11;
+  return TDKS_OK;
+}
+
+template <class T>
+int upload(T **dst, const std::vector<T> &v) {
+  CU(cudaMalloc((void **)dst, std::max<size_t>(1, v.size()) * sizeof(T)));
+  if (!v.empty()) CU(cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return TDKS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tdks_set_clock(tdks_sys s, double t, double dt, int substeps) {
+  if (!s) return fail(TDKS_EINVAL, "NULL system");
+  if (substeps < 1) return fail(TDKS_EINVAL, "substeps must be >= 1");
+  if (std::fabs(dt / substeps) * kinetic_max(s) > 2.0 * std::sqrt(2.0))
+    return fail(TDKS_EUNSTABLE, "sub-step beyond the Taylor-4 stability limit (dt_sub * K_max > 2 sqrt 2)");
+  s->clock_t = t;
+  s->clock_dt = dt;
+  s->clock_substeps = substeps;
+  return TDKS_OK;
+}
+
+int tdks_get_clock(tdks_sys s, double *t, long long *steps) {
+  if (!s) return fail(TDKS_EINVAL, "NULL system");
+  if (t) *t = s->clock_t;
+  if (steps) *steps = s->steps;
+  return TDKS_OK;
+}
+
+int tdks_batch_create(const tdks_sys *systems, int n, void *stream, tdks_batch_t *out) {
+  if (!systems || n < 1 || !out) return fail(TDKS_EINVAL, "bad arguments");
+  *out = nullptr;
+  tdks_batch *b = new (std::nothrow) tdks_batch();
+  if (!b) return fail(TDKS_ENOMEM, "host allocation");
+  b->stream = (cudaStream_t)stream;
+  b->sys.assign(systems, systems + n);
+  tdks_system *s0 = b->sys[0];
+  b->M = s0->M;
+  b->prec = s0->prec;
+  b->substeps = s0->clock_substeps;
+  auto bad = [&](const char *m) { delete b; return fail(TDKS_EINVAL, m); };
+  for (tdks_system *s : b->sys) {
+    if (!s) return bad("NULL system in batch");
+    if (s->bc != TDKS_BC_ZERO) return bad("batched propagation takes finite boxes only");
+    if (s->M != b->M || s->prec != b->prec) return bad("a batch shares the FD order and the precision");
+    if (s->clock_substeps != b->substeps) return bad("a batch shares the sub-step count (tdks_set_clock)");
+    if (s->gauge == TDKS_GAUGE_VELOCITY) return bad("velocity gauge is not batched");
+    if (!s->have_orbitals) return bad("orbitals not set");
+    if (!tma_supported(s->M, 16, 8)) return bad("no TMA sweep for this FD order");
+  }
+  std::vector<SweepParams> sp[4];
+  std::vector<GatherParams> gp[4];
+  std::vector<CUtensorMap> maps(4 * n);
+  std::vector<long> item_begin(n + 1, 0), gather_begin(n + 1, 0), lda_begin(n + 1, 0);
+  std::vector<BatchAux> aux(n);
+  std::vector<BatchClock> clk(n);
+  for (int i = 0; i < n; i++) {
+    tdks_system *s = b->sys[i];
+    const int save_tx = s->tx, save_ty = s->ty, save_zc = s->zc;
+    s->tx = 16; s->ty = 8; s->zc = s->nz;  // whole columns: many systems already balance the grid
+    const void *ins[4] = {s->psi, s->term[0], s->term[1], s->term[2]};
+    const int modes[4] = {MODE_FIRST, MODE_MID, MODE_MID, MODE_LAST};
+    const double A0[3] = {0.0, 0.0, 0.0};
+    const double dts = s->clock_dt / s->clock_substeps;
+    for (int k = 0; k < 4; k++) {
+      if (!encode_map(s, ins[k], modes[k], &maps[4 * i + k])) {
+        s->tx = save_tx; s->ty = save_ty; s->zc = save_zc;
+        return bad("tensor map encoding failed");
+      }
+      SweepParams p{};
+      sweep_common(s, p, A0);
+      p.cr = 0.0;
+      p.ci = -dts / (k + 1);
+      p.in = ins[k];
+      p.do_obs = k == 0;
+      p.err = s->d_err;
+      if (k < 3) p.out = s->term[k];
+      else { p.psi = s->psi; p.psi_lo = s->psi_lo; p.t1 = s->term[0]; p.t2 = s->term[1]; }
+      sp[k].push_back(p);
+      GatherParams g{};
+      g.n_kb = s->n_kb; g.n_batches = s->n_batches; g.n_atoms = s->n_atoms; g.N = s->N;
+      g.in = ins[k]; g.atom_begin = s->d_atom_begin; g.ent = s->d_ent; g.D = s->d_D;
+      g.h3 = s->h * s->h * s->h; g.kvec = s->d_kvec; g.q = s->d_q;
+      gp[k].push_back(g);
+    }
+    item_begin[i + 1] = item_begin[i] + sp[0].back().n_items;
+    gather_begin[i + 1] = gather_begin[i] + (long)s->n_atoms * s->n_kb;
+    const int nl = lda_blocks(s->N);
+    lda_begin[i + 1] = lda_begin[i] + nl;
+    BatchAux &a = aux[i];
+    a.N = s->N; a.nx = s->nx; a.ny = s->ny; a.nz = s->nz; a.n_kb = s->n_kb; a.xc = s->xc;
+    a.h = s->h; a.occ = s->occ; a.gauge = s->gauge; a.envelope = s->envelope;
+    for (int d = 0; d < 3; d++) a.pol[d] = s->pol[d];
+    a.amp = s->amp; a.omega = s->omega; a.t_total = s->t_total;
+    a.dens_part = s->dens_part; a.vloc = s->vloc; a.veff = s->veff; a.lda_part = s->lda_part; a.n_lda = nl;
+    a.obs_part = s->obs_part; a.n_items = sp[0].back().n_items; a.ring = s->ring;
+    a.ring_len = tdks_system::RING;
+    s->tx = save_tx; s->ty = save_ty; s->zc = save_zc;
+  }
+  b->total_items = item_begin[n];
+  b->total_gather = gather_begin[n];
+  b->total_lda = lda_begin[n];
+  int rc = TDKS_OK;
+  for (int k = 0; k < 4 && !rc; k++) {
+    if (!rc) rc = upload(&b->d_sweep[k], sp[k]);
+    if (!rc) rc = upload(&b->d_gather[k], gp[k]);
+  }
+  if (!rc) rc = upload(&b->d_maps, maps);
+  if (!rc) rc = upload(&b->d_item_begin, item_begin);
+  if (!rc) rc = upload(&b->d_gather_begin, gather_begin);
+  if (!rc) rc = upload(&b->d_lda_begin, lda_begin);
+  if (!rc) rc = upload(&b->d_aux, aux);
+  if (!rc) rc = upload(&b->d_clock, clk);
+  if (!rc && (cudaStreamCreateWithFlags(&b->work, cudaStreamNonBlocking) != cudaSuccess ||
+              cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+              cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess))
+    rc = fail(TDKS_EDEVICE, "batch stream/event creation");
+  if (rc) {
+    batch_free(b);
+    delete b;
+    return rc;
+  }
+  *out = b;
+  return TDKS_OK;
+}
+
+int tdks_batch_destroy(tdks_batch_t b) {
+  if (!b) return TDKS_OK;
+  cudaStreamSynchronize(b->stream);
+  if (b->work) cudaStreamSynchronize(b->work);
+  batch_free(b);
+  delete b;
+  return TDKS_OK;
+}
+
+int tdks_batch_propagate(tdks_batch_t b, int n_steps, int use_graph) {
+  if (!b || n_steps < 0) return fail(TDKS_EINVAL, "bad arguments");
+  const int n = (int)b->sys.size();
+  // densities of the current states, and the device clocks from each system's clock
+  std::vector<BatchClock> clk(n);
+  for (int i = 0; i < n; i++) {
+    tdks_system *s = b->sys[i];
+    if (s->stream != b->stream) CU(cudaStreamSynchronize(s->stream));
+    if (int rc = ensure_density(s)) return rc;
+    if (s->stream != b->stream) CU(cudaStreamSynchronize(s->stream));
+    clk[i] = BatchClock{s->clock_t, s->clock_dt, s->steps, s->clock_substeps, 0};
+  }
+  // the batch's work follows everything enqueued on the caller's stream
+  CU(cudaEventRecord(b->ev_in, b->stream));
+  CU(cudaStreamWaitEvent(b->work, b->ev_in, 0));
+  CU(cudaMemcpyAsync(b->d_clock, clk.data(), n * sizeof(BatchClock), cudaMemcpyHostToDevice, b->work));
+  if (use_graph && !b->exec) {
+    CU(cudaStreamBeginCapture(b->work, cudaStreamCaptureModeThreadLocal));
+    const int rc = enqueue_substep(b);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(b->work, &g);
+    if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+    if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("graph capture: ") + cudaGetErrorString(e));
+    b->graph = g;
+    CU(cudaGraphInstantiate(&b->exec, b->graph, 0));
+    b->launches -= 11;
+  }
+  const long long subs = (long long)n_steps * b->substeps;
+  for (long long i = 0; i < subs; i++) {
+    if (use_graph) {
+      CU(cudaGraphLaunch(b->exec, b->work));
+      b->launches += 11;
+    } else if (int rc = enqueue_substep(b)) {
+      return rc;
+    }
+  }
+  // and everything enqueued on the caller's stream afterwards follows the batch
+  CU(cudaEventRecord(b->ev_out, b->work));
+  CU(cudaStreamWaitEvent(b->stream, b->ev_out, 0));
+  for (tdks_system *s : b->sys) {
+    s->steps += n_steps;
+    s->clock_t += n_steps * s->clock_dt;
+    s->dens_valid = true;
+  }
+  return TDKS_OK;
+}
+
+int tdks_batch_launch_count(tdks_batch_t b, long long *count) {
+  if (!b || !count) return fail(TDKS_EINVAL, "NULL argument");
+  *count = b->launches;
+  return TDKS_OK;
+}
+
+}  // extern "C"

@@ -10,12 +10,12 @@
 #include <string>
 #include <vector>
 
-#include "../../include/tdks.h"
-#include "tdks_internal.cuh"
+#include "tdks_system.h"
 
 using namespace tdks;
+using namespace tdks_host;
 
-namespace {
+namespace tdks_host {
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -42,13 +42,7 @@ int fail(int code, const std::string &msg) {
   return code;
 }
 
-#define CU(call)                                                                             \
-  do {                                                                                       \
-    cudaError_t e_ = (call);                                                                 \
-    if (e_ != cudaSuccess)                                                                   \
-      return fail(e_ == cudaErrorMemoryAllocation ? TDKS_ENOMEM : TDKS_EDEVICE,              \
-                  std::string(#call) + ": " + cudaGetErrorString(e_));                       \
-  } while (0)
+
 
 // Finite-difference weights by Fornberg's recursion (weights of derivatives 0..2 at
 // x = 0 from the nodes -M..M); central, order 2M.
@@ -84,59 +78,7 @@ void fd_weights(int M, double *lap, double *grad) {
 
 }  // namespace
 
-struct tdks_system {
-  int nx, ny, nz, M, bc, prec, n_orb, n_k, BS, n_batches, n_kb;
-  long N;
-  double h;
-  std::vector<double> kpts, kw;
-  cudaStream_t stream;
-  int dev;
-  // physics parameters
-  int xc = TDKS_XC_LDA_X;
-  double occ = 2.0;
-  int gauge = TDKS_GAUGE_NONE, envelope = TDKS_ENV_NONE;
-  double pol[3] = {0, 0, 1}, amp = 0, omega = 0, t_total = 0;
-  int n_atoms = 0;
-  std::vector<double> pos, D;
-  double vloc_absmax = 0.0, vnl_bound = 0.0;
-  // device buffers
-  void *psi = nullptr;          // packed state: complex128, or the hi part (complex64) of a
-                                // complex64 system's double-float state
-  void *psi_lo = nullptr;       // lo part of a complex64 system's state
-  void *term[3] = {nullptr, nullptr, nullptr};
-  double *vloc = nullptr;
-  void *veff = nullptr;
-  double *dens_part = nullptr;
-  double *lda_part = nullptr;
-  double *obs_part = nullptr;
-  double *ring = nullptr;
-  double *obs_rec = nullptr;    // single record for tdks_observe
-  double *d_kvec = nullptr, *d_wocc = nullptr, *d_D = nullptr;
-  int *d_rowptr = nullptr, *d_rowent = nullptr, *d_atom_begin = nullptr;
-  ProjEntry *d_ent = nullptr;
-  void *d_q = nullptr;
-  double *staging = nullptr;
-  int *d_err = nullptr;
-  // TMA tensor maps over the four sweep inputs (state, t1, t2, t3) for the current tile
-  alignas(64) CUtensorMap tmaps[4];
-  bool tmaps_ok = false;
-  int path = 0;                 // 0: TMA sweep where possible, 1: general sweep
-  size_t state_bytes = 0, term_bytes = 0;
-  bool have_orbitals = false, dens_valid = false;
-  long long steps = 0;
-  static constexpr long long RING = 65536;
-  // stencil configuration
-  int tx = 16, ty = 8, zc = 0;
-  long long launches = 0;
-  // profiling
-  bool profile = false;
-  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
-  std::vector<cudaEvent_t> ev_free;
-  double prof_ms[3] = {0, 0, 0};
-  long long prof_n[3] = {0, 0, 0};
-};
-
-namespace {
+namespace tdks_host {
 
 double envelope_of(const tdks_system *s, double t, double *denv) {
   if (s->envelope == TDKS_ENV_SIN2) {
@@ -241,12 +183,14 @@ void sweep_common(const tdks_system *s, SweepParams &p, const double A[3]) {
   p.do_obs = 0;
 }
 
-bool encode_map(const tdks_system *s, const void *ptr, CUtensorMap *out) {
+// Tensor map over a packed array for the TMA sweep of `mode` (box depth = planes per copy).
+bool encode_map(const tdks_system *s, const void *ptr, int mode, CUtensorMap *out) {
   EncodeTiledFn fn = encode_fn();
   if (!fn || (reinterpret_cast<uintptr_t>(ptr) & 15) != 0) return false;
   const cuuint64_t dims[5] = {16, (cuuint64_t)s->nx, (cuuint64_t)s->ny, (cuuint64_t)s->nz, (cuuint64_t)s->n_kb};
   const cuuint64_t strides[4] = {64, 64ull * s->nx, 64ull * s->nx * s->ny, 64ull * (cuuint64_t)s->N};
-  const cuuint32_t box[5] = {16, (cuuint32_t)(s->tx + 2 * s->M), (cuuint32_t)(s->ty + 2 * s->M), 1, 1};
+  const cuuint32_t box[5] = {16, (cuuint32_t)(s->tx + 2 * s->M), (cuuint32_t)(s->ty + 2 * s->M),
+                             (cuuint32_t)tma_planes(s->prec, mode), 1};
   const cuuint32_t es[5] = {1, 1, 1, 1, 1};
   return fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<void *>(ptr), dims, strides, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -257,8 +201,9 @@ void build_tmaps(tdks_system *s) {
   s->tmaps_ok = false;
   if (s->bc != TDKS_BC_ZERO || !tma_supported(s->M, s->tx, s->ty)) return;
   const void *ins[4] = {s->psi, s->term[0], s->term[1], s->term[2]};
+  const int modes[4] = {MODE_FIRST, MODE_MID, MODE_MID, MODE_LAST};
   for (int i = 0; i < 4; i++)
-    if (!encode_map(s, ins[i], &s->tmaps[i])) return;
+    if (!encode_map(s, ins[i], modes[i], &s->tmaps[i])) return;
   s->tmaps_ok = true;
 }
 
@@ -698,8 +643,9 @@ int tdks_apply_H(tdks_sys s, double t, const void *dev_in, void *dev_out) {
   p.cr = 1.0; p.ci = 0.0;
   p.in = dev_in;
   p.out = dev_out;
-  alignas(64) CUtensorMap tm;
-  const bool have_tm = s->bc == TDKS_BC_ZERO && tma_supported(s->M, s->tx, s->ty) && encode_map(s, dev_in, &tm);
+  CUtensorMap tm;
+  const bool have_tm =
+      s->bc == TDKS_BC_ZERO && tma_supported(s->M, s->tx, s->ty) && encode_map(s, dev_in, MODE_MID, &tm);
   return run_sweep(s, MODE_MID, p, have_tm ? &tm : nullptr);
 }
 
@@ -755,6 +701,9 @@ int tdks_propagate_n(tdks_sys s, double t0, double dt, int n_steps, int substeps
     }
     s->steps++;
   }
+  s->clock_t = t0 + n_steps * dt;
+  s->clock_dt = dt;
+  s->clock_substeps = substeps;
   return TDKS_OK;
 }
 

@@ -84,6 +84,43 @@ struct GatherParams {
   void *q;                    // [kb][atom][4][OVC] vectors
 };
 
+// Per-system data of a batch (device copies), for the batched LDA and finalise kernels.
+struct BatchAux {
+  long N;
+  int nx, ny, nz, n_kb, xc;
+  double h, occ;
+  int gauge, envelope;
+  double pol[3], amp, omega, t_total;
+  const double *dens_part;
+  const double *vloc;
+  void *veff;
+  double *lda_part;
+  int n_lda;
+  double *obs_part;
+  long n_items;
+  double *ring;
+  long long ring_len;
+};
+
+// Device clock of a batched system: state time t of the current step, step length dt,
+// sub-steps per step, current sub-step j, steps completed.
+struct BatchClock {
+  double t, dt;
+  long long step;
+  int substeps, j;
+};
+
+// Batched stencil sweep over many systems (tdks_sweep_tma.cu): params[s] and
+// tmaps[4*s + which] of system s; item_begin[s] = first work item of system s.
+struct BatchSweepArgs {
+  const SweepParams *params;
+  const void *tmaps;  // CUtensorMap array, 4 per system
+  int which;
+  const long *item_begin;
+  int n_sys;
+  long total_items;
+};
+
 // Launchers (tdks_sweep.cu)
 cudaError_t launch_sweep(int M, int prec, int mode, int bloch, int tx, int ty,
                          const SweepParams &p, int grid, cudaStream_t s);
@@ -106,10 +143,19 @@ cudaError_t launch_pack(int prec, int to_internal, long N, int n_k, int n_orb, i
                         void *internal, void *internal_lo, double *plain, cudaStream_t s);
 
 // TMA sweep for finite boxes (tdks_sweep_tma.cu).  tmap: CUtensorMap (64-byte aligned
-// blob) over the stencil input, dims {16 floats, nx, ny, nz, n_kb}, box {16, TX+2M, TY+2M, 1, 1}.
+// blob) over the stencil input, dims {16 floats, nx, ny, nz, n_kb},
+// box {16, TX+2M, TY+2M, tma_planes(prec, mode), 1}.
 cudaError_t launch_sweep_tma(int M, int prec, int mode, int tx, int ty, const void *tmap,
                              const SweepParams &p, int grid, cudaStream_t s);
 bool tma_supported(int M, int tx, int ty);
+int tma_planes(int prec, int mode);
 int lda_blocks(long N);
+cudaError_t launch_sweep_tma_batch(int M, int prec, int mode, const BatchSweepArgs &a, cudaStream_t s);
+cudaError_t launch_gather_batch(int prec, const GatherParams *gp, const long *begin, int n_sys, long total,
+                                cudaStream_t s);
+cudaError_t launch_lda_batch(int prec, const BatchAux *aux, const BatchClock *clk, const long *begin, int n_sys,
+                             long total, cudaStream_t s);
+// which = 0: observable records (first sub-step of a step); 1: advance the clocks
+cudaError_t launch_batch_tail(const BatchAux *aux, BatchClock *clk, int n_sys, int which, cudaStream_t s);
 
 }  // namespace tdks

@@ -62,6 +62,7 @@ sweep_kernel(const SweepParams p) {
 #pragma unroll
   for (int m = 0; m <= M; m++) W[m] = T::bc(p.w[m]);
   const typename W0T<P>::type w0 = (typename W0T<P>::type)p.w[0];
+  const S CR = T::bc(p.cr), CI = T::bc(p.ci);
   const bool need_grad = BLOCH && (p.grad_mask != 0);
   const bool grads = BLOCH && MODE == MODE_FIRST && (p.grad_mask & 8);
 
@@ -173,7 +174,7 @@ sweep_kernel(const SweepParams p) {
           for (int a = 0; a < 3; a++) oa.add_j(a, Q[M], gax[a]);
         }
       }
-      finish_point<P, MODE>(p, own, idx, v, kidx, Q[M], acc, lop);
+      finish_point<P, MODE>(p, CR, CI, own, idx, v, kidx, Q[M], acc, lop);
       // plane z+1 into the other buffer
       V *Sn = sm + (buf ^ 1) * PLANE;
       Sn[csl] = Q[M + 1];

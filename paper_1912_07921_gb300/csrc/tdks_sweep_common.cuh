@@ -41,19 +41,18 @@ template <> struct ObsAcc<P_C64> {
 template <int P> struct W0T { typedef double type; };
 template <> struct W0T<P_C64> { typedef float type; };
 
-// H applied at one point.  The z-column queue is the circular register array Q of 2M+1
-// entries; plane z+j (j = -M..M) sits in Q[(QB + M + j) % (2M+1)] (QB: compile-time
+// H applied at one point.  The z-column queue is the circular register array Q of QN
+// (>= 2M+1) entries; plane z+j (j = -M..M) sits in Q[(QB + M + j) % QN] (QB: compile-time
 // rotation, so no register moves per plane).  Sp = shared plane z (vectors, row stride SXO
 // vectors), csl = own slot.  Returns H t; gax receives the three FD gradients when `grads`
 // is set (observables of periodic cells).
-template <int M, int P, int BLOCH, int QB = 0>
+template <int M, int P, int BLOCH, int QB = 0, int QN = 2 * M + 1>
 __device__ __forceinline__ typename VT<P>::V
 stencil_point(const SweepParams &p, const typename VT<P>::S *W, typename W0T<P>::type w0,
               const typename VT<P>::V *Q, const typename VT<P>::V *Sp, int csl, int SXO,
               typename VT<P>::R ve, bool need_grad, bool grads, typename VT<P>::V *gax) {
   typedef VT<P> T;
   typedef typename T::V V;
-  constexpr int QN = 2 * M + 1;
   const V c0 = Q[(QB + M) % QN];
   V acc = T::mul(T::diag(ve, w0), c0);
   V gsum = T::zero();
@@ -133,14 +132,15 @@ __device__ __forceinline__ void load_last(const SweepParams &p, long idx, LastOp
   o.t2 = VT<P>::ld(reinterpret_cast<const V *>(p.t2) + idx);
 }
 
-// Epilogue of one output vector.  idx = vector index ((kb*N + pt)*OVC + v).
+// Epilogue of one output vector.  idx = vector index ((kb*N + pt)*OVC + v); (CR, CI) = the
+// Taylor coefficient, converted to the compute precision once per work item.
 template <int P, int MODE>
-__device__ __forceinline__ void finish_point(const SweepParams &p, bool own, long idx, int v, int kidx,
-                                             typename VT<P>::V c0, typename VT<P>::V acc,
-                                             const LastOperands<P> &lo_ops) {
+__device__ __forceinline__ void finish_point(const SweepParams &p, typename VT<P>::S CR, typename VT<P>::S CI,
+                                             bool own, long idx, int v, int kidx, typename VT<P>::V c0,
+                                             typename VT<P>::V acc, const LastOperands<P> &lo_ops) {
   typedef VT<P> T;
   typedef typename T::V V;
-  const V outv = T::cmul(T::bc(p.cr), T::bc(p.ci), acc);
+  const V outv = T::cmul(CR, CI, acc);
   if (MODE != MODE_LAST) {
     if (own) reinterpret_cast<V *>(p.out)[idx] = outv;
   } else {

@@ -1,0 +1,96 @@
+// Host-side system object and helpers shared by the C interface translation units
+// (not part of the public interface).
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/tdks.h"
+#include "tdks_internal.cuh"
+
+namespace tdks_host {
+
+int fail(int code, const std::string &msg);
+
+#define CU(call)                                                                             \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return tdks_host::fail(e_ == cudaErrorMemoryAllocation ? TDKS_ENOMEM : TDKS_EDEVICE,   \
+                             std::string(#call) + ": " + cudaGetErrorString(e_));            \
+  } while (0)
+
+}  // namespace tdks_host
+
+struct tdks_system {
+  int nx, ny, nz, M, bc, prec, n_orb, n_k, BS, n_batches, n_kb;
+  long N;
+  double h;
+  std::vector<double> kpts, kw;
+  cudaStream_t stream;
+  int dev;
+  // physics parameters
+  int xc = TDKS_XC_LDA_X;
+  double occ = 2.0;
+  int gauge = TDKS_GAUGE_NONE, envelope = TDKS_ENV_NONE;
+  double pol[3] = {0, 0, 1}, amp = 0, omega = 0, t_total = 0;
+  int n_atoms = 0;
+  std::vector<double> pos, D;
+  double vloc_absmax = 0.0, vnl_bound = 0.0;
+  // device buffers
+  void *psi = nullptr;          // packed state: complex128, or the hi part (complex64) of a
+                                // complex64 system's double-float state
+  void *psi_lo = nullptr;       // lo part of a complex64 system's state
+  void *term[3] = {nullptr, nullptr, nullptr};
+  double *vloc = nullptr;
+  void *veff = nullptr;
+  double *dens_part = nullptr;
+  double *lda_part = nullptr;
+  double *obs_part = nullptr;
+  double *ring = nullptr;
+  double *obs_rec = nullptr;    // single record for tdks_observe
+  double *d_kvec = nullptr, *d_wocc = nullptr, *d_D = nullptr;
+  int *d_rowptr = nullptr, *d_rowent = nullptr, *d_atom_begin = nullptr;
+  tdks::ProjEntry *d_ent = nullptr;
+  void *d_q = nullptr;
+  double *staging = nullptr;
+  int *d_err = nullptr;
+  // TMA tensor maps over the four sweep inputs (state, t1, t2, t3) for the current tile
+  CUtensorMap tmaps[4];
+  bool tmaps_ok = false;
+  int path = 0;                 // 0: TMA sweep where possible, 1: general sweep
+  size_t state_bytes = 0, term_bytes = 0;
+  bool have_orbitals = false, dens_valid = false;
+  long long steps = 0;
+  // clock used by batched propagation: state time, step length, sub-steps per step
+  double clock_t = 0.0, clock_dt = 0.0;
+  int clock_substeps = 1;
+  static constexpr long long RING = 65536;
+  // stencil configuration
+  int tx = 16, ty = 8, zc = 0;
+  long long launches = 0;
+  // profiling
+  bool profile = false;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
+  std::vector<cudaEvent_t> ev_free;
+  double prof_ms[3] = {0, 0, 0};
+  long long prof_n[3] = {0, 0, 0};
+};
+
+namespace tdks_host {
+
+void fd_weights(int M, double *lap, double *grad);
+void field_at(const tdks_system *s, double t, double E[3], double A[3]);
+double envelope_of(const tdks_system *s, double t, double *denv);
+void sweep_geometry(const tdks_system *s, tdks::SweepParams &p);
+void sweep_common(const tdks_system *s, tdks::SweepParams &p, const double A[3]);
+long n_items_of(const tdks_system *s);
+bool encode_map(const tdks_system *s, const void *ptr, int mode, CUtensorMap *out);
+int ensure_density(tdks_system *s);
+int check_err(tdks_system *s);
+double kinetic_max(const tdks_system *s);
+
+}  // namespace tdks_host

@@ -1,0 +1,189 @@
+"""Continuous-batching server for propagation jobs (host-side scheduling only).
+
+Jobs (a seeded system, a number of steps, an arrival time) are admitted while device
+slots and an HBM budget allow; each admitted job's orbitals, potentials and projector
+tables stay resident on the device until it finishes.  Every scheduler tick advances all
+active jobs together: jobs sharing precision, FD order and sub-step count form one batch,
+advanced with one persistent sweep launch per Taylor term (``Batch``, replayed as a CUDA
+graph), and the batch is rebuilt whenever a job joins or leaves.  A job that arrives
+while others are on the GPU joins at the next tick; a finished job releases its memory
+and slot at once.  Latency is measured from arrival to the moment the job's results
+(its observable records and final orbitals' norm) are on the host.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+import time
+from typing import Callable, Dict, List, Optional, Tuple
+
+import numpy as np
+
+from . import inputs as I
+from .system import Batch, System
+
+
+@dataclasses.dataclass
+class Job:
+    jid: int
+    spec: I.SystemSpec
+    n_steps: int
+    arrival: float
+    # filled by the server
+    admitted: float = math.nan
+    finished: float = math.nan
+    steps_done: int = 0
+    records: Optional[np.ndarray] = None
+    orbitals: Optional[np.ndarray] = None
+    system: Optional[System] = None
+    nbytes: int = 0
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.arrival
+
+    @property
+    def updates(self) -> int:
+        return self.spec.n_points * self.spec.n_orb * self.n_steps
+
+
+def job_bytes(spec: I.SystemSpec) -> int:
+    """Device memory a job holds while resident (the library's allocation for it)."""
+    bs = 8 if spec.prec == I.PREC_C64 else 4
+    nb = -(-spec.n_orb // bs)
+    vals = spec.n_points * nb * bs * spec.n_k
+    term = 8 if spec.prec == I.PREC_C64 else 16
+    state = 16
+    per_point = 8 + (4 if spec.prec == I.PREC_C64 else 8) + 8 * nb * spec.n_k + 4
+    staging = spec.n_points * spec.n_orb * spec.n_k * 16
+    ring = 65536 * 8 * 8
+    return vals * (state + 3 * term) + spec.n_points * per_point + staging + ring + (1 << 20)
+
+
+def serving_trace(n_jobs: int, rate: float, seed: int, edge=(32, 128), orbitals=(4, 128),
+                  steps=(200, 5000), atoms=(0, 32)) -> List[Job]:
+    """Poisson arrivals of propagation requests (grid edge, orbitals, steps, atoms drawn
+    uniformly; half complex64, half complex128; h = 0.25, 4th-order FD, dt = 0.015)."""
+    rng = I.SplitMix64(seed)
+    t = 0.0
+    jobs = []
+    for j in range(n_jobs):
+        t += rng.exponential(rate)
+        e = rng.randint(*edge)
+        n_orb = rng.randint(*orbitals)
+        n_steps = rng.randint(*steps)
+        n_atoms = rng.randint(*atoms)
+        prec = I.PREC_C64 if rng.uniform() < 0.5 else I.PREC_C128
+        spec = I.SystemSpec(nx=e, ny=e, nz=e, h=0.25, fd_order=4, prec=prec, n_orb=n_orb, n_atoms=n_atoms,
+                            projectors=n_atoms > 0, gauge=I.GAUGE_LENGTH, amp=0.005, omega=0.057, dt=0.015,
+                            n_steps=n_steps, substeps=1, seed=(seed << 24) + j)
+        jobs.append(Job(jid=j, spec=spec, n_steps=n_steps, arrival=t))
+    return jobs
+
+
+class Server:
+    """Admission by HBM budget and slot count; continuous batching of the active jobs."""
+
+    def __init__(self, hbm_budget: int, max_slots: int = 64, quantum: int = 50, stream: Optional[int] = None,
+                 use_graph: bool = True, sync: Optional[Callable[[], None]] = None,
+                 make_inputs: Callable[[I.SystemSpec], I.Inputs] = I.make_inputs):
+        self.budget = hbm_budget
+        self.max_slots = max_slots
+        self.quantum = quantum
+        self.stream = stream
+        self.use_graph = use_graph
+        self.sync = sync or (lambda: None)
+        self.make_inputs = make_inputs
+        self.used = 0
+        self.peak_used = 0
+        self.active: List[Job] = []
+        self.done: List[Job] = []
+        self.batches: Dict[Tuple, Tuple[Tuple[int, ...], Batch]] = {}
+        self.ticks = 0
+        self.max_concurrent = 0
+
+    # -- admission / eviction -----------------------------------------------------------
+    def _admit(self, job: Job, now: float):
+        job.nbytes = job_bytes(job.spec)
+        inp = self.make_inputs(job.spec)
+        job.system = System(job.spec, inp, stream=self.stream)
+        job.system.set_clock(0.0, job.spec.dt, job.spec.substeps)
+        job.admitted = now
+        self.used += job.nbytes
+        self.peak_used = max(self.peak_used, self.used)
+        self.active.append(job)
+        self.max_concurrent = max(self.max_concurrent, len(self.active))
+
+    def _finish(self, job: Job, now_fn):
+        job.records = job.system.reductions(0, job.n_steps)
+        job.orbitals = job.system.get_orbitals() if self.keep_orbitals else None
+        job.finished = now_fn()
+        job.system.close()
+        job.system = None
+        self.used -= job.nbytes
+        self.active.remove(job)
+        self.done.append(job)
+
+    # -- one tick: every active job advances ---------------------------------------------
+    def _tick(self):
+        groups: Dict[Tuple, List[Job]] = {}
+        for j in self.active:
+            key = (j.spec.prec, j.spec.fd_order, j.spec.substeps)
+            groups.setdefault(key, []).append(j)
+        for key in list(self.batches):
+            if key not in groups:
+                self.batches.pop(key)[1].close()
+        advanced = []
+        for key, jobs in groups.items():
+            ids = tuple(j.jid for j in jobs)
+            if key not in self.batches or self.batches[key][0] != ids:
+                if key in self.batches:
+                    self.batches[key][1].close()
+                self.batches[key] = (ids, Batch([j.system for j in jobs], stream=self.stream))
+            q = min(self.quantum, min(j.n_steps - j.steps_done for j in jobs))
+            self.batches[key][1].propagate(q, use_graph=self.use_graph)
+            advanced.append((jobs, q))
+        self.sync()
+        for jobs, q in advanced:
+            for j in jobs:
+                j.steps_done += q
+        self.ticks += 1
+
+    def run(self, jobs: List[Job], keep_orbitals: bool = False, time_scale: float = 1.0) -> List[Job]:
+        """Serve the trace in real time (arrival times scaled by time_scale)."""
+        self.keep_orbitals = keep_orbitals
+        pending = sorted(jobs, key=lambda j: j.arrival)
+        queue: List[Job] = []
+        t0 = time.perf_counter()
+        now = lambda: (time.perf_counter() - t0) / time_scale
+        while pending or queue or self.active:
+            t = now()
+            while pending and pending[0].arrival <= t:
+                queue.append(pending.pop(0))
+            while queue and len(self.active) < self.max_slots:
+                nb = job_bytes(queue[0].spec)
+                if nb > self.budget:
+                    raise ValueError(f"job {queue[0].jid} needs {nb} bytes, more than the whole budget")
+                if self.used + nb > self.budget:
+                    break
+                self._admit(queue.pop(0), t)
+            if not self.active:
+                if pending:
+                    time.sleep(max(0.0, (pending[0].arrival - now()) * time_scale))
+                continue
+            self._tick()
+            for j in [j for j in self.active if j.steps_done >= j.n_steps]:
+                self._finish(j, now)
+        for _, b in self.batches.values():
+            b.close()
+        self.batches.clear()
+        self.wall = now()
+        return self.done
+
+    def report(self) -> dict:
+        lat = np.array([j.latency for j in self.done])
+        upd = sum(j.updates for j in self.done)
+        return {"jobs": len(self.done), "wall_s": self.wall, "updates": upd,
+                "throughput": upd / self.wall if self.wall > 0 else math.nan,
+                "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                "ticks": self.ticks, "peak_hbm_bytes": self.peak_used, "max_concurrent": self.max_concurrent}

@@ -152,9 +152,51 @@ class System:
         _lib.check(self.lib.tdks_launch_count(self.h, ctypes.byref(c)))
         return c.value
 
+    def set_clock(self, t: float, dt: float, substeps: int):
+        _lib.check(self.lib.tdks_set_clock(self.h, t, dt, substeps))
+
+    def clock(self):
+        t, n = ctypes.c_double(), ctypes.c_longlong()
+        _lib.check(self.lib.tdks_get_clock(self.h, ctypes.byref(t), ctypes.byref(n)))
+        return t.value, n.value
+
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:
             self.lib.tdks_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many finite-box systems advanced together (one persistent sweep launch per Taylor
+    term over all of them, replayed as a CUDA graph).  The systems must use the batch's
+    stream and share FD order, precision and sub-step count."""
+
+    def __init__(self, systems, stream: Optional[int] = None):
+        self.lib = _lib.load()
+        self.systems = list(systems)
+        arr = (ctypes.c_void_p * len(self.systems))(*[s.h.value for s in self.systems])
+        h = ctypes.c_void_p()
+        _lib.check(self.lib.tdks_batch_create(arr, len(self.systems), ctypes.c_void_p(stream or 0),
+                                              ctypes.byref(h)))
+        self.h = h
+
+    def propagate(self, n_steps: int, use_graph: bool = True):
+        _lib.check(self.lib.tdks_batch_propagate(self.h, n_steps, int(use_graph)))
+
+    def launch_count(self) -> int:
+        c = ctypes.c_longlong()
+        _lib.check(self.lib.tdks_batch_launch_count(self.h, ctypes.byref(c)))
+        return c.value
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.tdks_batch_destroy(self.h)
             self.h = ctypes.c_void_p()
 
     def __del__(self):

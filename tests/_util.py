@@ -32,3 +32,19 @@ def bloch_inputs(spec):
 def rel_err(a, b):
     a, b = np.asarray(a), np.asarray(b)
     return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def small_uneven_batch(prec, n=5, seed=7):
+    """Uneven finite boxes (edges 17..33, 3..11 orbitals, 0..3 atoms with projectors) that
+    share FD order 4, h = 0.25, dt = 0.015 and one sub-step, as the batched workload does."""
+    rng = I.SplitMix64(seed)
+    out = []
+    for i in range(n):
+        nx, ny, nz = (rng.randint(17, 33) for _ in range(3))
+        n_orb = rng.randint(3, 11)
+        n_atoms = rng.randint(0, 3)
+        out.append(I.SystemSpec(nx=nx, ny=ny, nz=nz, h=0.25, fd_order=4, prec=prec, n_orb=n_orb,
+                                n_atoms=n_atoms, projectors=n_atoms > 0, gauge=I.GAUGE_LENGTH,
+                                amp=0.01 * (i + 1), omega=0.2, envelope=I.ENV_SIN2 if i % 2 else I.ENV_NONE,
+                                t_total=0.5, dt=0.015, substeps=1, seed=(seed << 8) + i))
+    return out

@@ -212,3 +212,29 @@ def test_unstable_substep_is_refused():
         sysm.propagate(0.0, spec.dt, 1, 1)
     assert e.value.code == 3
     sysm.close()
+
+
+@pytest.mark.parametrize("prec", [I.PREC_C128, I.PREC_C64])
+def test_periodic_cell_full_grid_one_step(prec):
+    """Periodic cell at full size (64^3, side 10.2, 8 diamond atoms with projectors,
+    velocity gauge A0 = 0.2, 6 sub-steps of the configured dt = 0.04) with 2 of its 32
+    k-points x 16 bands; every value compared, current and energy records too."""
+    spec = I.periodic_cell(n_k=2, prec=prec)
+    inp = I.make_inputs(spec)
+    t0 = 30.0
+    sysm = _system(spec, inp)
+    sysm.propagate(t0, spec.dt, 1, spec.substeps)
+    rec = sysm.reductions(0, 1)
+    psi = sysm.get_orbitals()
+    sysm.close()
+    o = oracle.System(spec, inp)
+    psi_o, rec_o = o.propagate(inp.psi0, t0, spec.dt, 1, spec.substeps)
+    if prec == I.PREC_C128:
+        assert rel_err(psi, psi_o) < 1e-12
+        np.testing.assert_allclose(rec, rec_o, rtol=1e-12, atol=1e-12 * np.abs(rec_o).max())
+    else:
+        assert rel_err(psi, psi_o) < 1e-5
+        # <phi|H|phi> from an FP32 H phi: the kinetic terms (up to K_max ~ 315 Ha here) cancel
+        # down to ~0.45 Ha per orbital, so the relative error is ~eps32 * K_max / e ~ 4e-5
+        assert abs(rec[0, 2] - rec_o[0, 2]) < 2e-4 * abs(rec_o[0, 2])
+        assert np.max(np.abs(rec[0, 4:7] - rec_o[0, 4:7])) < 1e-4 * np.max(np.abs(rec_o[0, 4:7]))
