@@ -233,6 +233,30 @@ int tdks_batch_propagate(tdks_batch_t batch, int n_steps, int use_graph);
 int tdks_batch_launch_count(tdks_batch_t batch, long long *count);
 int tdks_batch_destroy(tdks_batch_t batch);
 
+/*
+ * H applied without allocating device memory.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc, such as code running inside a
+ * host framework that owns all device memory through its own pool, or a real-time loop
+ * that cannot afford the device-wide synchronisation an allocation or free may cause.
+ *
+ * dev_out = (-1/2 Lap_h + V_loc) dev_in on a finite box (zero boundary), for one k-point:
+ * no exchange term, no projectors, no field.  nx, ny, nz, h, fd_order, prec and n_orb as in
+ * tdks_create_grid; dev_vloc: device array [nz][ny][nx] of doubles; dev_in / dev_out:
+ * distinct device arrays in the packed layout of such a system (BS = 4 for TDKS_C128,
+ * 8 for TDKS_C64, zero-padded batches); stream: cudaStream_t or NULL.  The caller owns all
+ * three buffers.  The call synchronises the stream before it returns.
+ *
+ * Scratch (the potential in the compute precision and an error word) lives in a fixed
+ * file-scope device array of 8 MiB + 256 B that every GPU loading the library holds until
+ * the process exits; grids above 2^20 = 1,048,576 points are rejected with TDKS_EINVAL.
+ * All calls on a device share that array and each call overwrites it, so calls whose work
+ * overlaps on the GPU (several streams or host threads) race: serialise them.  The first
+ * call on a device looks up the array's device address on that device (make it before
+ * any stream capture).  Returns TDKS_ETIMEOUT if a sweep gave up waiting for its copies.
+ */
+int tdks_apply_H_noalloc(int nx, int ny, int nz, double h, int fd_order, int prec, int n_orb,
+                         const double *dev_vloc, const void *dev_in, void *dev_out, void *stream);
+
 const char *tdks_last_error(void);
 
 #ifdef __cplusplus
