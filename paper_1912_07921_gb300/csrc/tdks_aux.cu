@@ -10,24 +10,32 @@ namespace tdks {
 //                                         exp(+i (k.T_u + A.d_u)) in(cell(u))[v]
 // (the <beta_aj|psi> of V_NL = sum |beta> D <beta|; the paper's norm-conserving
 // pseudopotentials, Sec. "Magneto-optics" and Sec. "Periodic systems", with synthetic
-// Gaussian-times-polynomial projectors).  One CTA per (atom, kb); 64 point lanes x OVC
-// vectors; lanes reduce with warp shuffles, warps through shared memory in a fixed
-// order, so the result does not depend on timing.
+// Gaussian-times-polynomial projectors).  Stage 1: n_chunks CTAs per (atom, kb), each
+// summing a contiguous share of the sphere with 64 point lanes x OVC vectors (warp
+// shuffles, then warps through shared memory in a fixed order); stage 2 adds the chunks in
+// order and applies D_aj h^3.  No atomics: the result does not depend on timing.
 // ---------------------------------------------------------------------------------
 constexpr int GATHER_THREADS = 256;
 
+int gather_chunks(long units) {
+  const long want = (152L * 4 + units - 1) / units;
+  return (int)(want < 1 ? 1 : (want > 16 ? 16 : want));
+}
+
 template <int P, int BLOCH>
-__device__ __forceinline__ void gather_body(const GatherParams &p, int a, int kb) {
+__device__ __forceinline__ void gather_body(const GatherParams &p, int a, int kb, int chunk) {
   typedef VT<P> T;
   typedef typename T::V V;
   const int kidx = kb / p.n_batches;
   const int tid = threadIdx.x, v = tid % OVC, lane = tid / OVC;
   constexpr int LANES = GATHER_THREADS / OVC;
-  // per-lane sums: FP64 for complex128 systems, FP32 for complex64 systems (about 33
-  // sphere points per lane); the cross-lane sums below are FP64 for both.
+  // per-lane sums: FP64 for complex128 systems, FP32 for complex64 systems; the cross-lane
+  // sums below are FP64 for both.
   double2 accd[4] = {};
   float2 accf[4][2] = {};
-  const int e0 = p.atom_begin[a], e1 = p.atom_begin[a + 1];
+  const int a0 = p.atom_begin[a], a1 = p.atom_begin[a + 1];
+  const int len = (a1 - a0 + p.n_chunks - 1) / p.n_chunks;
+  const int e0 = a0 + chunk * len, e1 = min(a1, e0 + len);
   const bool phase = BLOCH || (p.A[0] != 0.0 || p.A[1] != 0.0 || p.A[2] != 0.0);
   for (int e = e0 + lane; e < e1; e += LANES) {
     const ProjEntry &E = p.ent[e];
@@ -83,19 +91,43 @@ __device__ __forceinline__ void gather_body(const GatherParams &p, int a, int kb
       s0.x += red[w][j][vv][0].x; s0.y += red[w][j][vv][0].y;
       s1.x += red[w][j][vv][1].x; s1.y += red[w][j][vv][1].y;
     }
-    const double f = p.D[4 * a + j] * p.h3;
-    V *q = reinterpret_cast<V *>(p.q) + ((long)(kb * p.n_atoms + a) * 4 + j) * OVC + vv;
-    if constexpr (P == P_C64) {
-      *q = make_ulonglong2(pk2((float)(f * s0.x), (float)(f * s0.y)), pk2((float)(f * s1.x), (float)(f * s1.y)));
-    } else {
-      *q = make_double2(f * s0.x, f * s0.y);
-    }
+    double2 *qp = p.qpart + ((((long)(kb * p.n_atoms + a) * p.n_chunks + chunk) * 4 + j) * OVC + vv) * 2;
+    qp[0] = s0;
+    qp[1] = s1;
+  }
+}
+
+// Stage 2 for one (atom, kb): thread (j, v) adds the chunk partials in order, times D h^3.
+template <int P>
+__device__ __forceinline__ void gather_finish(const GatherParams &p, int a, int kb, int t) {
+  typedef typename VT<P>::V V;
+  const int j = t / OVC, vv = t % OVC;
+  double2 s0 = make_double2(0.0, 0.0), s1 = make_double2(0.0, 0.0);
+  for (int c = 0; c < p.n_chunks; c++) {
+    const double2 *qp = p.qpart + ((((long)(kb * p.n_atoms + a) * p.n_chunks + c) * 4 + j) * OVC + vv) * 2;
+    s0.x += qp[0].x; s0.y += qp[0].y;
+    s1.x += qp[1].x; s1.y += qp[1].y;
+  }
+  const double f = p.D[4 * a + j] * p.h3;
+  V *q = reinterpret_cast<V *>(p.q) + ((long)(kb * p.n_atoms + a) * 4 + j) * OVC + vv;
+  if constexpr (P == P_C64) {
+    *q = make_ulonglong2(pk2((float)(f * s0.x), (float)(f * s0.y)), pk2((float)(f * s1.x), (float)(f * s1.y)));
+  } else {
+    *q = make_double2(f * s0.x, f * s0.y);
   }
 }
 
 template <int P, int BLOCH>
 __global__ void __launch_bounds__(GATHER_THREADS) gather_kernel(const GatherParams p) {
-  gather_body<P, BLOCH>(p, blockIdx.x, blockIdx.y);
+  gather_body<P, BLOCH>(p, blockIdx.x / p.n_chunks, blockIdx.y, blockIdx.x % p.n_chunks);
+}
+
+// 16 threads per (atom, kb) unit, 8 units per CTA
+template <int P>
+__global__ void __launch_bounds__(128) gather_finish_kernel(const GatherParams p) {
+  const long u = blockIdx.x * 8L + threadIdx.x / 16;
+  if (u >= (long)p.n_atoms * p.n_kb) return;
+  gather_finish<P>(p, (int)(u % p.n_atoms), (int)(u / p.n_atoms), threadIdx.x % 16);
 }
 
 // index of the system that owns unit u: begin[s] <= u < begin[s+1]
@@ -108,33 +140,55 @@ __device__ __forceinline__ int find_sys(const long *begin, int n, long u) {
   return lo;
 }
 
-// Batched gather: one CTA per (system, atom, k-batch) over every system of a batch.
+// Batched gather: stage 1 over every system's (atom, kb, chunk) CTAs, stage 2 over every
+// system's (atom, kb) units.
 template <int P>
 __global__ void __launch_bounds__(GATHER_THREADS)
 gather_batch_kernel(const GatherParams *gp, const long *begin, int n_sys) {
   const int s = find_sys(begin, n_sys, blockIdx.x);
   const GatherParams &p = gp[s];
   const long u = blockIdx.x - begin[s];
-  gather_body<P, 0>(p, (int)(u % p.n_atoms), (int)(u / p.n_atoms));
+  const long unit = u / p.n_chunks;
+  gather_body<P, 0>(p, (int)(unit % p.n_atoms), (int)(unit / p.n_atoms), (int)(u % p.n_chunks));
 }
 
-cudaError_t launch_gather_batch(int prec, const GatherParams *gp, const long *begin, int n_sys, long total,
-                                cudaStream_t s) {
+template <int P>
+__global__ void __launch_bounds__(128)
+gather_finish_batch_kernel(const GatherParams *gp, const long *ubegin, int n_sys, long total_units) {
+  const long u = blockIdx.x * 8L + threadIdx.x / 16;
+  if (u >= total_units) return;
+  const int s = find_sys(ubegin, n_sys, u);
+  const GatherParams &p = gp[s];
+  const long local = u - ubegin[s];
+  gather_finish<P>(p, (int)(local % p.n_atoms), (int)(local / p.n_atoms), threadIdx.x % 16);
+}
+
+cudaError_t launch_gather_batch(int prec, const GatherParams *gp, const long *begin, const long *ubegin, int n_sys,
+                                long total, long total_units, cudaStream_t s) {
   if (total <= 0) return cudaSuccess;
-  if (prec == P_C64) gather_batch_kernel<P_C64><<<(unsigned)total, GATHER_THREADS, 0, s>>>(gp, begin, n_sys);
-  else gather_batch_kernel<P_C128><<<(unsigned)total, GATHER_THREADS, 0, s>>>(gp, begin, n_sys);
+  const unsigned fgrid = (unsigned)((total_units + 7) / 8);
+  if (prec == P_C64) {
+    gather_batch_kernel<P_C64><<<(unsigned)total, GATHER_THREADS, 0, s>>>(gp, begin, n_sys);
+    gather_finish_batch_kernel<P_C64><<<fgrid, 128, 0, s>>>(gp, ubegin, n_sys, total_units);
+  } else {
+    gather_batch_kernel<P_C128><<<(unsigned)total, GATHER_THREADS, 0, s>>>(gp, begin, n_sys);
+    gather_finish_batch_kernel<P_C128><<<fgrid, 128, 0, s>>>(gp, ubegin, n_sys, total_units);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_gather(int prec, int bloch, const GatherParams &p, cudaStream_t s) {
   if (p.n_atoms <= 0) return cudaSuccess;
-  dim3 grid(p.n_atoms, p.n_kb);
+  dim3 grid(p.n_atoms * p.n_chunks, p.n_kb);
+  const unsigned fgrid = (unsigned)(((long)p.n_atoms * p.n_kb + 7) / 8);
   if (prec == P_C64) {
     if (bloch) gather_kernel<P_C64, 1><<<grid, GATHER_THREADS, 0, s>>>(p);
     else gather_kernel<P_C64, 0><<<grid, GATHER_THREADS, 0, s>>>(p);
+    gather_finish_kernel<P_C64><<<fgrid, 128, 0, s>>>(p);
   } else {
     if (bloch) gather_kernel<P_C128, 1><<<grid, GATHER_THREADS, 0, s>>>(p);
     else gather_kernel<P_C128, 0><<<grid, GATHER_THREADS, 0, s>>>(p);
+    gather_finish_kernel<P_C128><<<fgrid, 128, 0, s>>>(p);
   }
   return cudaGetLastError();
 }
@@ -201,29 +255,55 @@ int lda_blocks(long N) {
   return (int)(g < 152 * 4 ? g : 152 * 4);
 }
 
+// complex128 systems: everything in FP64.
+// complex64 systems (V_eff is FP32 there): v_x and V_eff in FP32, the per-point terms of the
+// observables in FP32 accumulated as double-float per thread, the sums over k-point
+// batches and across threads in FP64; this keeps GB300's slow FP64 pipe out of the loop.
 template <typename R>
 __device__ __forceinline__ void lda_body(long N, int nx, int ny, int nz, double h, int bloch, int n_kb,
                                          const double *dens_part, const double *vloc, int xc, double Ex, double Ey,
-                                         double Ez, double half_A2, R *veff, double *lda_part, int blk, int nblk) {
+                                         double Ez, double half_A2, PointAux *aux, double *lda_part, int blk,
+                                         int nblk) {
+  constexpr bool F32 = sizeof(R) == 4;
   double acc[6] = {0, 0, 0, 0, 0, 0};
+  float fh[6] = {0, 0, 0, 0, 0, 0}, fl[6] = {0, 0, 0, 0, 0, 0};
   const double cx = bloch ? 0.0 : 0.5 * (nx - 1), cy = bloch ? 0.0 : 0.5 * (ny - 1),
                cz = bloch ? 0.0 : 0.5 * (nz - 1);
+  const float hf = (float)h, cxf = (float)cx, cyf = (float)cy, czf = (float)cz;
+  const float Exf = (float)Ex, Eyf = (float)Ey, Ezf = (float)Ez, hA2f = (float)half_A2;
   for (long p = blk * (long)blockDim.x + threadIdx.x; p < N; p += (long)nblk * blockDim.x) {
     double n = 0.0;
     for (int kb = 0; kb < n_kb; kb++) n += dens_part[(long)kb * N + p];
     const int ix = (int)(p % nx), iy = (int)((p / nx) % ny), iz = (int)(p / ((long)nx * ny));
-    const double x = (ix - cx) * h, y = (iy - cy) * h, z = (iz - cz) * h;
-    double vx = 0.0;
-    if (xc) vx = -cbrt(3.0 * n * 0.31830988618379067154);  // 1/pi
-    double v = vloc[p] + vx + half_A2;
-    if (!bloch) v += Ex * x + Ey * y + Ez * z;
-    veff[p] = (R)v;
-    acc[0] += n;
-    acc[1] += n * 0.75 * vx;
-    acc[2] += n * vx;
-    acc[3] += x * n;
-    acc[4] += y * n;
-    acc[5] += z * n;
+    if constexpr (F32) {
+      const float nf = (float)n;
+      const float x = (ix - cxf) * hf, y = (iy - cyf) * hf, z = (iz - czf) * hf;
+      const float vx = xc ? -cbrtf(3.0f * nf * 0.318309886f) : 0.0f;
+      float v = (float)vloc[p] + vx + hA2f;
+      if (!bloch) v += Exf * x + Eyf * y + Ezf * z;
+      *reinterpret_cast<float *>(&aux[p].veff) = v;
+      const float t[6] = {nf, nf * 0.75f * vx, nf * vx, x * nf, y * nf, z * nf};
+#pragma unroll
+      for (int c = 0; c < 6; c++) df_acc(fh[c], fl[c], t[c]);
+      fl[0] += (float)(n - (double)nf);  // the electron count keeps the FP64 density in full
+    } else {
+      const double x = (ix - cx) * h, y = (iy - cy) * h, z = (iz - cz) * h;
+      double vx = 0.0;
+      if (xc) vx = -cbrt(3.0 * n * 0.31830988618379067154);  // 1/pi
+      double v = vloc[p] + vx + half_A2;
+      if (!bloch) v += Ex * x + Ey * y + Ez * z;
+      *reinterpret_cast<double *>(&aux[p].veff) = v;
+      acc[0] += n;
+      acc[1] += n * 0.75 * vx;
+      acc[2] += n * vx;
+      acc[3] += x * n;
+      acc[4] += y * n;
+      acc[5] += z * n;
+    }
+  }
+  if constexpr (F32) {
+#pragma unroll
+    for (int c = 0; c < 6; c++) acc[c] = (double)fh[c] + (double)fl[c];
   }
   __shared__ double red[LDA_THREADS / 32][6];
   for (int i = 0; i < 6; i++) {
@@ -242,9 +322,9 @@ __device__ __forceinline__ void lda_body(long N, int nx, int ny, int nz, double 
 template <typename R>
 __global__ void __launch_bounds__(LDA_THREADS)
 lda_kernel(long N, int nx, int ny, int nz, double h, int bloch, int n_kb, const double *dens_part,
-           const double *vloc, int xc, double Ex, double Ey, double Ez, double half_A2, R *veff,
+           const double *vloc, int xc, double Ex, double Ey, double Ez, double half_A2, PointAux *aux,
            double *lda_part) {
-  lda_body<R>(N, nx, ny, nz, h, bloch, n_kb, dens_part, vloc, xc, Ex, Ey, Ez, half_A2, veff, lda_part, blockIdx.x,
+  lda_body<R>(N, nx, ny, nz, h, bloch, n_kb, dens_part, vloc, xc, Ex, Ey, Ez, half_A2, aux, lda_part, blockIdx.x,
               gridDim.x);
 }
 
@@ -275,7 +355,7 @@ lda_batch_kernel(const BatchAux *aux, const BatchClock *clk, const long *begin, 
   __syncthreads();
   const double E = f;
   lda_body<R>(a.N, a.nx, a.ny, a.nz, a.h, 0, a.n_kb, a.dens_part, a.vloc, a.xc, E * a.pol[0], E * a.pol[1],
-              E * a.pol[2], 0.0, reinterpret_cast<R *>(a.veff), a.lda_part, (int)(blockIdx.x - begin[s]),
+              E * a.pol[2], 0.0, a.aux, a.lda_part, (int)(blockIdx.x - begin[s]),
               a.n_lda);
 }
 
@@ -288,13 +368,13 @@ cudaError_t launch_lda_batch(int prec, const BatchAux *aux, const BatchClock *cl
 
 cudaError_t launch_lda(int prec, int bloch, long N, int nx, int ny, int nz, double h, int n_kb,
                        const double *dens_part, const double *vloc, int xc, const double E[3],
-                       double half_A2, void *veff, double *lda_part, int n_blocks, cudaStream_t s) {
+                       double half_A2, PointAux *aux, double *lda_part, int n_blocks, cudaStream_t s) {
   if (prec == P_C64)
     lda_kernel<float><<<n_blocks, LDA_THREADS, 0, s>>>(N, nx, ny, nz, h, bloch, n_kb, dens_part, vloc, xc,
-                                                       E[0], E[1], E[2], half_A2, (float *)veff, lda_part);
+                                                       E[0], E[1], E[2], half_A2, aux, lda_part);
   else
     lda_kernel<double><<<n_blocks, LDA_THREADS, 0, s>>>(N, nx, ny, nz, h, bloch, n_kb, dens_part, vloc, xc,
-                                                        E[0], E[1], E[2], half_A2, (double *)veff, lda_part);
+                                                        E[0], E[1], E[2], half_A2, aux, lda_part);
   return cudaGetLastError();
 }
 

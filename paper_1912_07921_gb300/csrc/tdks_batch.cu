@@ -24,11 +24,11 @@ struct tdks_batch {
   // device arrays
   SweepParams *d_sweep[4] = {nullptr, nullptr, nullptr, nullptr};   // per Taylor term
   GatherParams *d_gather[4] = {nullptr, nullptr, nullptr, nullptr};
-  CUtensorMap *d_maps = nullptr;                                    // 4 per system
-  long *d_item_begin = nullptr, *d_gather_begin = nullptr, *d_lda_begin = nullptr;
+  SweepMaps *d_maps = nullptr;                                      // 4 per system
+  long *d_item_begin = nullptr, *d_gather_begin = nullptr, *d_unit_begin = nullptr, *d_lda_begin = nullptr;
   BatchAux *d_aux = nullptr;
   BatchClock *d_clock = nullptr;
-  long total_items = 0, total_gather = 0, total_lda = 0;
+  long total_items = 0, total_gather = 0, total_units = 0, total_lda = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   long long launches = 0;
@@ -39,6 +39,7 @@ namespace {
 void batch_free(tdks_batch *b) {
   for (int k = 0; k < 4; k++) { cudaFree(b->d_sweep[k]); cudaFree(b->d_gather[k]); }
   cudaFree(b->d_maps); cudaFree(b->d_item_begin); cudaFree(b->d_gather_begin); cudaFree(b->d_lda_begin);
+  cudaFree(b->d_unit_begin);
   cudaFree(b->d_aux); cudaFree(b->d_clock);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
@@ -53,7 +54,8 @@ int enqueue_substep(tdks_batch *b) {
   cudaError_t e = launch_lda_batch(b->prec, b->d_aux, b->d_clock, b->d_lda_begin, n, b->total_lda, b->work);
   if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("batched lda: ") + cudaGetErrorString(e));
   for (int k = 0; k < 4; k++) {
-    e = launch_gather_batch(b->prec, b->d_gather[k], b->d_gather_begin, n, b->total_gather, b->work);
+    e = launch_gather_batch(b->prec, b->d_gather[k], b->d_gather_begin, b->d_unit_begin, n, b->total_gather,
+                            b->total_units, b->work);
     if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("batched gather: ") + cudaGetErrorString(e));
     BatchSweepArgs a{b->d_sweep[k], b->d_maps, k, b->d_item_begin, n, b->total_items};
     const int mode = k == 0 ? MODE_FIRST : (k == 3 ? MODE_LAST : MODE_MID);
@@ -122,8 +124,8 @@ int tdks_batch_create(const tdks_sys *systems, int n, void *stream, tdks_batch_t
   }
   std::vector<SweepParams> sp[4];
   std::vector<GatherParams> gp[4];
-  std::vector<CUtensorMap> maps(4 * n);
-  std::vector<long> item_begin(n + 1, 0), gather_begin(n + 1, 0), lda_begin(n + 1, 0);
+  std::vector<SweepMaps> maps(4 * n);
+  std::vector<long> item_begin(n + 1, 0), gather_begin(n + 1, 0), unit_begin(n + 1, 0), lda_begin(n + 1, 0);
   std::vector<BatchAux> aux(n);
   std::vector<BatchClock> clk(n);
   for (int i = 0; i < n; i++) {
@@ -135,7 +137,7 @@ int tdks_batch_create(const tdks_sys *systems, int n, void *stream, tdks_batch_t
     const double A0[3] = {0.0, 0.0, 0.0};
     const double dts = s->clock_dt / s->clock_substeps;
     for (int k = 0; k < 4; k++) {
-      if (!encode_map(s, ins[k], modes[k], &maps[4 * i + k])) {
+      if (!encode_sweep_maps(s, ins[k], modes[k], &maps[4 * i + k])) {
         s->tx = save_tx; s->ty = save_ty; s->zc = save_zc;
         return bad("tensor map encoding failed");
       }
@@ -153,10 +155,12 @@ int tdks_batch_create(const tdks_sys *systems, int n, void *stream, tdks_batch_t
       g.n_kb = s->n_kb; g.n_batches = s->n_batches; g.n_atoms = s->n_atoms; g.N = s->N;
       g.in = ins[k]; g.atom_begin = s->d_atom_begin; g.ent = s->d_ent; g.D = s->d_D;
       g.h3 = s->h * s->h * s->h; g.kvec = s->d_kvec; g.q = s->d_q;
+      g.n_chunks = s->gchunks; g.qpart = s->d_qpart;
       gp[k].push_back(g);
     }
     item_begin[i + 1] = item_begin[i] + sp[0].back().n_items;
-    gather_begin[i + 1] = gather_begin[i] + (long)s->n_atoms * s->n_kb;
+    gather_begin[i + 1] = gather_begin[i] + (long)s->n_atoms * s->n_kb * (s->n_atoms > 0 ? s->gchunks : 0);
+    unit_begin[i + 1] = unit_begin[i] + (long)s->n_atoms * s->n_kb;
     const int nl = lda_blocks(s->N);
     lda_begin[i + 1] = lda_begin[i] + nl;
     BatchAux &a = aux[i];
@@ -164,13 +168,14 @@ int tdks_batch_create(const tdks_sys *systems, int n, void *stream, tdks_batch_t
     a.h = s->h; a.occ = s->occ; a.gauge = s->gauge; a.envelope = s->envelope;
     for (int d = 0; d < 3; d++) a.pol[d] = s->pol[d];
     a.amp = s->amp; a.omega = s->omega; a.t_total = s->t_total;
-    a.dens_part = s->dens_part; a.vloc = s->vloc; a.veff = s->veff; a.lda_part = s->lda_part; a.n_lda = nl;
+    a.dens_part = s->dens_part; a.vloc = s->vloc; a.aux = s->aux; a.lda_part = s->lda_part; a.n_lda = nl;
     a.obs_part = s->obs_part; a.n_items = sp[0].back().n_items; a.ring = s->ring;
     a.ring_len = tdks_system::RING;
     s->tx = save_tx; s->ty = save_ty; s->zc = save_zc;
   }
   b->total_items = item_begin[n];
   b->total_gather = gather_begin[n];
+  b->total_units = unit_begin[n];
   b->total_lda = lda_begin[n];
   int rc = TDKS_OK;
   for (int k = 0; k < 4 && !rc; k++) {
@@ -180,6 +185,7 @@ int tdks_batch_create(const tdks_sys *systems, int n, void *stream, tdks_batch_t
   if (!rc) rc = upload(&b->d_maps, maps);
   if (!rc) rc = upload(&b->d_item_begin, item_begin);
   if (!rc) rc = upload(&b->d_gather_begin, gather_begin);
+  if (!rc) rc = upload(&b->d_unit_begin, unit_begin);
   if (!rc) rc = upload(&b->d_lda_begin, lda_begin);
   if (!rc) rc = upload(&b->d_aux, aux);
   if (!rc) rc = upload(&b->d_clock, clk);

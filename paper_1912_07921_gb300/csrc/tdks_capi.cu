@@ -165,8 +165,8 @@ void sweep_common(const tdks_system *s, SweepParams &p, const double A[3]) {
     p.w[m] = -0.5 * c[m] / (s->h * s->h);
     p.gw[m] = d[m] / s->h;
   }
-  p.veff = s->veff;
-  p.rowptr = s->n_atoms > 0 ? s->d_rowptr : nullptr;
+  p.aux = s->aux;
+  p.has_proj = s->n_atoms > 0;
   p.rowent = s->d_rowent;
   p.ent = s->d_ent;
   p.q = s->d_q;
@@ -197,23 +197,63 @@ bool encode_map(const tdks_system *s, const void *ptr, int mode, CUtensorMap *ou
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Map over the per-point records, tile box of the mode's depth.
+bool encode_aux_map(const tdks_system *s, int mode, CUtensorMap *out) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn || (reinterpret_cast<uintptr_t>(s->aux) & 15) != 0) return false;
+  const cuuint64_t dims[4] = {4, (cuuint64_t)s->nx, (cuuint64_t)s->ny, (cuuint64_t)s->nz};
+  const cuuint64_t strides[3] = {16, 16ull * s->nx, 16ull * s->nx * s->ny};
+  const cuuint32_t box[4] = {4, (cuuint32_t)s->tx, (cuuint32_t)s->ty, (cuuint32_t)tma_planes(s->prec, mode)};
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  return fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, s->aux, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Map over a packed array with the tile box (no halo) of z depth `depth`.
+bool encode_op_map(const tdks_system *s, const void *ptr, CUtensorMap *out, int depth = 1) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn || (reinterpret_cast<uintptr_t>(ptr) & 15) != 0) return false;
+  const cuuint64_t dims[5] = {16, (cuuint64_t)s->nx, (cuuint64_t)s->ny, (cuuint64_t)s->nz, (cuuint64_t)s->n_kb};
+  const cuuint64_t strides[4] = {64, 64ull * s->nx, 64ull * s->nx * s->ny, 64ull * (cuuint64_t)s->N};
+  const cuuint32_t box[5] = {16, (cuuint32_t)s->tx, (cuuint32_t)s->ty, (cuuint32_t)depth, 1};
+  const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  return fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<void *>(ptr), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool encode_sweep_maps(const tdks_system *s, const void *in, int mode, SweepMaps *out) {
+  if (!encode_map(s, in, mode, &out->in) || !encode_aux_map(s, mode, &out->aux) ||
+      !encode_op_map(s, in, &out->ctr, tma_planes(s->prec, mode)))
+    return false;
+  if (mode == MODE_LAST) {
+    const void *ops[4] = {s->psi, s->psi_lo ? s->psi_lo : s->psi, s->term[0], s->term[1]};
+    for (int j = 0; j < 4; j++)
+      if (!encode_op_map(s, ops[j], &out->op[j])) return false;
+  } else {
+    for (int j = 0; j < 4; j++) out->op[j] = out->in;  // unused
+  }
+  return true;
+}
+
 void build_tmaps(tdks_system *s) {
   s->tmaps_ok = false;
   if (s->bc != TDKS_BC_ZERO || !tma_supported(s->M, s->tx, s->ty)) return;
   const void *ins[4] = {s->psi, s->term[0], s->term[1], s->term[2]};
   const int modes[4] = {MODE_FIRST, MODE_MID, MODE_MID, MODE_LAST};
   for (int i = 0; i < 4; i++)
-    if (!encode_map(s, ins[i], modes[i], &s->tmaps[i])) return;
+    if (!encode_sweep_maps(s, ins[i], modes[i], &s->smaps[i])) return;
   s->tmaps_ok = true;
 }
 
-// tm: tensor map over p.in (or null): finite boxes with a 16x8 tile take the TMA sweep.
-int run_sweep(tdks_system *s, int mode, SweepParams &p, const CUtensorMap *tm) {
+// tm: tensor maps of the sweep (or null): finite boxes with a 16x8 tile take the TMA sweep.
+int run_sweep(tdks_system *s, int mode, SweepParams &p, const SweepMaps *tm) {
   Timed tmr(s, 0);
   p.err = s->d_err;
   cudaError_t e;
   if (tm && s->path == 0 && s->bc == TDKS_BC_ZERO && tma_supported(s->M, s->tx, s->ty))
-    e = launch_sweep_tma(s->M, s->prec, mode, s->tx, s->ty, tm, p, 0, s->stream);
+    e = launch_sweep_tma(s->M, s->prec, mode, s->tx, s->ty, *tm, p, 0, s->stream);
   else
     e = launch_sweep(s->M, s->prec, mode, s->bc == TDKS_BC_BLOCH, s->tx, s->ty, p, 0, s->stream);
   s->launches++;
@@ -231,6 +271,8 @@ int run_gather(tdks_system *s, const void *in, const double A[3]) {
   g.kvec = s->d_kvec;
   for (int a = 0; a < 3; a++) g.A[a] = s->gauge == TDKS_GAUGE_VELOCITY ? A[a] : 0.0;
   g.q = s->d_q;
+  g.n_chunks = s->gchunks;
+  g.qpart = s->d_qpart;
   Timed tm(s, 1);
   cudaError_t e = launch_gather(s->prec, s->bc == TDKS_BC_BLOCH, g, s->stream);
   s->launches++;
@@ -256,7 +298,7 @@ int run_lda(tdks_system *s, const double E[3], const double A[3]) {
                         s->gauge == TDKS_GAUGE_LENGTH ? E[2] : 0.0};
   Timed tm(s, 2);
   cudaError_t e = launch_lda(s->prec, s->bc == TDKS_BC_BLOCH, s->N, s->nx, s->ny, s->nz, s->h, s->n_kb,
-                             s->dens_part, s->vloc, s->xc, El, half_A2, s->veff, s->lda_part, lda_blocks(s->N),
+                             s->dens_part, s->vloc, s->xc, El, half_A2, s->aux, s->lda_part, lda_blocks(s->N),
                              s->stream);
   s->launches++;
   if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("lda: ") + cudaGetErrorString(e));
@@ -290,7 +332,7 @@ int first_sweep(tdks_system *s, double cr, double ci, const double A[3], bool ob
   p.out = s->term[0];
   p.do_obs = obs ? 1 : 0;
   if (obs && s->bc == TDKS_BC_BLOCH) p.grad_mask |= 8;
-  return run_sweep(s, MODE_FIRST, p, s->tmaps_ok ? &s->tmaps[0] : nullptr);
+  return run_sweep(s, MODE_FIRST, p, s->tmaps_ok ? &s->smaps[0] : nullptr);
 }
 
 // Gershgorin-type bound on |lambda| of H: kinetic maximum (the +/- alternating mode of
@@ -321,10 +363,11 @@ double kinetic_max(const tdks_system *s) {
 }
 
 void free_proj(tdks_system *s) {
-  cudaFree(s->d_rowptr); cudaFree(s->d_rowent); cudaFree(s->d_atom_begin);
-  cudaFree(s->d_ent); cudaFree(s->d_q); cudaFree(s->d_D);
-  s->d_rowptr = s->d_rowent = s->d_atom_begin = nullptr;
-  s->d_ent = nullptr; s->d_q = nullptr; s->d_D = nullptr;
+  cudaFree(s->d_rowent); cudaFree(s->d_atom_begin);
+  cudaFree(s->d_ent); cudaFree(s->d_q); cudaFree(s->d_D); cudaFree(s->d_qpart);
+  s->d_rowent = s->d_atom_begin = nullptr;
+  if (s->aux) cudaMemsetAsync(s->aux, 0, s->N * sizeof(PointAux), s->stream);  // no entries anywhere
+  s->d_ent = nullptr; s->d_q = nullptr; s->d_D = nullptr; s->d_qpart = nullptr;
   s->n_atoms = 0;
   s->vnl_bound = 0.0;
 }
@@ -395,7 +438,7 @@ int tdks_create_grid(int nx, int ny, int nz, double h, int fd_order, int bc, int
   for (int i = 0; i < 3; i++) ALLOC(s->term[i], s->term_bytes);
   ALLOC(s->d_err, sizeof(int));
   ALLOC(s->vloc, N * sizeof(double));
-  ALLOC(s->veff, N * (prec == TDKS_C64 ? sizeof(float) : sizeof(double)));
+  ALLOC(s->aux, N * sizeof(PointAux));
   ALLOC(s->dens_part, pts * sizeof(double));
   ALLOC(s->lda_part, (size_t)nlda * 6 * sizeof(double));
   s->zc = 0;
@@ -411,6 +454,7 @@ int tdks_create_grid(int nx, int ny, int nz, double h, int fd_order, int bc, int
 #undef ALLOC
   if (cudaMemcpy(s->d_kvec, s->kpts.data(), 3 * n_k * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemsetAsync(s->vloc, 0, N * sizeof(double), s->stream) != cudaSuccess ||
+      cudaMemsetAsync(s->aux, 0, N * sizeof(PointAux), s->stream) != cudaSuccess ||
       cudaMemsetAsync(s->psi, 0, s->state_bytes, s->stream) != cudaSuccess ||
       (s->psi_lo && cudaMemsetAsync(s->psi_lo, 0, s->state_bytes, s->stream) != cudaSuccess) ||
       cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream) != cudaSuccess)
@@ -432,7 +476,7 @@ int tdks_destroy(tdks_sys s) {
   cudaFree(s->psi_lo);
   cudaFree(s->d_err);
   for (int i = 0; i < 3; i++) cudaFree(s->term[i]);
-  cudaFree(s->vloc); cudaFree(s->veff); cudaFree(s->dens_part); cudaFree(s->lda_part);
+  cudaFree(s->vloc); cudaFree(s->aux); cudaFree(s->dens_part); cudaFree(s->lda_part);
   cudaFree(s->obs_part); cudaFree(s->ring); cudaFree(s->obs_rec); cudaFree(s->d_kvec); cudaFree(s->d_wocc);
   cudaFree(s->staging);
   for (auto &u : s->ev_used) { cudaEventDestroy(u.second.first); cudaEventDestroy(u.second.second); }
@@ -551,13 +595,19 @@ int tdks_set_atoms_projectors(tdks_sys s, int n_atoms, const double *pos, const 
     std::vector<int> fill(rowptr.begin(), rowptr.end() - 1);
     for (size_t i = 0; i < ent.size(); i++) rowent[fill[ent[i].cell]++] = (int)i;
   }
-  CU(cudaMalloc((void **)&s->d_rowptr, (s->N + 1) * sizeof(int)));
   CU(cudaMalloc((void **)&s->d_rowent, ent.size() * sizeof(int)));
   CU(cudaMalloc((void **)&s->d_atom_begin, (n_atoms + 1) * sizeof(int)));
   CU(cudaMalloc((void **)&s->d_ent, ent.size() * sizeof(ProjEntry)));
   CU(cudaMalloc((void **)&s->d_q, (size_t)s->n_kb * n_atoms * 4 * OVC * 16));
+  s->gchunks = gather_chunks((long)n_atoms * s->n_kb);
+  CU(cudaMalloc((void **)&s->d_qpart, (size_t)s->n_kb * n_atoms * s->gchunks * 4 * OVC * 2 * sizeof(double2)));
   CU(cudaMalloc((void **)&s->d_D, (size_t)n_atoms * 4 * sizeof(double)));
-  CU(cudaMemcpy(s->d_rowptr, rowptr.data(), (s->N + 1) * sizeof(int), cudaMemcpyHostToDevice));
+  {
+    // per-point entry ranges (V_eff is rewritten by the LDA kernel before every sweep)
+    std::vector<PointAux> aux(s->N);
+    for (long i = 0; i < s->N; i++) aux[i] = PointAux{0.0, rowptr[i], rowptr[i + 1]};
+    CU(cudaMemcpy(s->aux, aux.data(), s->N * sizeof(PointAux), cudaMemcpyHostToDevice));
+  }
   CU(cudaMemcpy(s->d_rowent, rowent.data(), ent.size() * sizeof(int), cudaMemcpyHostToDevice));
   CU(cudaMemcpy(s->d_atom_begin, atom_begin.data(), (n_atoms + 1) * sizeof(int), cudaMemcpyHostToDevice));
   CU(cudaMemcpy(s->d_ent, ent.data(), ent.size() * sizeof(ProjEntry), cudaMemcpyHostToDevice));
@@ -643,9 +693,9 @@ int tdks_apply_H(tdks_sys s, double t, const void *dev_in, void *dev_out) {
   p.cr = 1.0; p.ci = 0.0;
   p.in = dev_in;
   p.out = dev_out;
-  CUtensorMap tm;
-  const bool have_tm =
-      s->bc == TDKS_BC_ZERO && tma_supported(s->M, s->tx, s->ty) && encode_map(s, dev_in, MODE_MID, &tm);
+  SweepMaps tm;
+  const bool have_tm = s->bc == TDKS_BC_ZERO && tma_supported(s->M, s->tx, s->ty) &&
+                       encode_sweep_maps(s, dev_in, MODE_MID, &tm);
   return run_sweep(s, MODE_MID, p, have_tm ? &tm : nullptr);
 }
 
@@ -688,13 +738,13 @@ int tdks_propagate_n(tdks_sys s, double t0, double dt, int n_steps, int substeps
         p.in = in;
         if (k < 4) {
           p.out = s->term[k - 1];
-          if ((rc = run_sweep(s, MODE_MID, p, s->tmaps_ok ? &s->tmaps[k - 1] : nullptr))) return rc;
+          if ((rc = run_sweep(s, MODE_MID, p, s->tmaps_ok ? &s->smaps[k - 1] : nullptr))) return rc;
         } else {
           p.psi = s->psi;
           p.psi_lo = s->psi_lo;
           p.t1 = s->term[0];
           p.t2 = s->term[1];
-          if ((rc = run_sweep(s, MODE_LAST, p, s->tmaps_ok ? &s->tmaps[3] : nullptr))) return rc;
+          if ((rc = run_sweep(s, MODE_LAST, p, s->tmaps_ok ? &s->smaps[3] : nullptr))) return rc;
         }
       }
       s->dens_valid = true;  // MODE_LAST wrote the density of the new state

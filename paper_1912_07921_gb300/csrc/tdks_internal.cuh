@@ -15,6 +15,7 @@
 //                     transformations, because GB300 runs FP64 at a small fraction of its
 //                     FP32 rate; density, potentials and reductions are FP64.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -36,6 +37,14 @@ struct ProjEntry {
   double d[3];     // unwrapped point minus atom centre
 };
 
+// Per-point record read by the sweeps (16 bytes): the diagonal potential V_eff (double
+// for complex128 systems; float in the first 4 bytes for complex64 systems) and the point's
+// range [r0, r1) in the point-major projector entry list.
+struct __align__(16) PointAux {
+  double veff;
+  int r0, r1;
+};
+
 struct SweepParams {
   int nx, ny, nz;
   int n_tx, n_ty, n_zc, zc;   // x/y tiles and z chunks
@@ -51,10 +60,10 @@ struct SweepParams {
                               // system's double-float state), read and written in place
   void *psi_lo;               // MODE_LAST, complex64 systems: lo part of the state
   const void *t1, *t2;        // MODE_LAST: earlier terms
-  const void *veff;           // [N] diagonal potential (float for c64, double for c128)
+  const PointAux *aux;        // [N] V_eff and projector entry ranges
   // projectors (scatter side)
-  const int *rowptr;          // [N+1] point -> entries (CSR), or null
-  const int *rowent;          // entry indices
+  int has_proj;               // the system has projector entries
+  const int *rowent;          // entry indices (point-major)
   const ProjEntry *ent;
   const void *q;              // [kb][atom][4][OVC] vectors: D_aj h^3 <beta_aj|in>
   int n_atoms;
@@ -82,6 +91,8 @@ struct GatherParams {
   const double *kvec;
   double A[3];
   void *q;                    // [kb][atom][4][OVC] vectors
+  int n_chunks;               // CTAs per (atom, kb): each sums a contiguous share of the sphere
+  double2 *qpart;             // [kb][atom][chunk][4][OVC][2] partial sums (FP64)
 };
 
 // Per-system data of a batch (device copies), for the batched LDA and finalise kernels.
@@ -93,7 +104,7 @@ struct BatchAux {
   double pol[3], amp, omega, t_total;
   const double *dens_part;
   const double *vloc;
-  void *veff;
+  PointAux *aux;
   double *lda_part;
   int n_lda;
   double *obs_part;
@@ -110,11 +121,19 @@ struct BatchClock {
   int substeps, j;
 };
 
+// Tensor maps of one TMA sweep launch: the stencil input with halo (z depth = planes per
+// copy), the stencil input as tiles without halo (same depth), the per-point records (tile
+// box, same depth) and, for the last Taylor term, the four own-point operands state hi,
+// state lo, t1, t2 (tile boxes, depth 1).
+struct SweepMaps {
+  CUtensorMap in, ctr, aux, op[4];
+};
+
 // Batched stencil sweep over many systems (tdks_sweep_tma.cu): params[s] and
-// tmaps[4*s + which] of system s; item_begin[s] = first work item of system s.
+// maps[4*s + which] of system s; item_begin[s] = first work item of system s.
 struct BatchSweepArgs {
   const SweepParams *params;
-  const void *tmaps;  // CUtensorMap array, 4 per system
+  const SweepMaps *maps;  // 4 per system (one per Taylor term)
   int which;
   const long *item_begin;
   int n_sys;
@@ -129,11 +148,13 @@ size_t sweep_smem(int M, int tx, int ty);
 
 // Launchers (tdks_aux.cu)
 cudaError_t launch_gather(int prec, int bloch, const GatherParams &p, cudaStream_t s);
+// chunks per (atom, k-batch) that fill the GPU for n_atoms * n_kb units
+int gather_chunks(long units);
 cudaError_t launch_density(int prec, long N, int n_kb, int n_batches, const void *psi, const void *psi_lo,
                            const double *wocc, double *dens_part, cudaStream_t s);
 cudaError_t launch_lda(int prec, int bloch, long N, int nx, int ny, int nz, double h,
                        int n_kb, const double *dens_part, const double *vloc, int xc,
-                       const double E[3], double half_A2, void *veff, double *lda_part,
+                       const double E[3], double half_A2, PointAux *aux, double *lda_part,
                        int n_blocks, cudaStream_t s);
 cudaError_t launch_finalize(const double *obs_part, long n_items, const double *lda_part,
                             int n_lda_blocks, double *record, double t_state, double h3,
@@ -142,17 +163,19 @@ cudaError_t launch_finalize(const double *obs_part, long n_items, const double *
 cudaError_t launch_pack(int prec, int to_internal, long N, int n_k, int n_orb, int n_batches,
                         void *internal, void *internal_lo, double *plain, cudaStream_t s);
 
-// TMA sweep for finite boxes (tdks_sweep_tma.cu).  tmap: CUtensorMap (64-byte aligned
-// blob) over the stencil input, dims {16 floats, nx, ny, nz, n_kb},
-// box {16, TX+2M, TY+2M, tma_planes(prec, mode), 1}.
-cudaError_t launch_sweep_tma(int M, int prec, int mode, int tx, int ty, const void *tmap,
+// TMA sweep for finite boxes (tdks_sweep_tma.cu).  maps.in: dims {16 floats, nx, ny, nz,
+// n_kb}, box {16, TX+2M, TY+2M, tma_planes(prec, mode), 1}; maps.aux: dims {4, nx, ny, nz}
+// (4-byte words), box {4, TX, TY, tma_planes}; maps.op[i]: dims as maps.in, box
+// {16, TX, TY, 1, 1}.
+cudaError_t launch_sweep_tma(int M, int prec, int mode, int tx, int ty, const SweepMaps &maps,
                              const SweepParams &p, int grid, cudaStream_t s);
 bool tma_supported(int M, int tx, int ty);
 int tma_planes(int prec, int mode);
 int lda_blocks(long N);
 cudaError_t launch_sweep_tma_batch(int M, int prec, int mode, const BatchSweepArgs &a, cudaStream_t s);
-cudaError_t launch_gather_batch(int prec, const GatherParams *gp, const long *begin, int n_sys, long total,
-                                cudaStream_t s);
+// begin: prefix sums of n_atoms * n_kb * n_chunks (stage 1 CTAs); ubegin: of n_atoms * n_kb
+cudaError_t launch_gather_batch(int prec, const GatherParams *gp, const long *begin, const long *ubegin, int n_sys,
+                                long total, long total_units, cudaStream_t s);
 cudaError_t launch_lda_batch(int prec, const BatchAux *aux, const BatchClock *clk, const long *begin, int n_sys,
                              long total, cudaStream_t s);
 // which = 0: observable records (first sub-step of a step); 1: advance the clocks

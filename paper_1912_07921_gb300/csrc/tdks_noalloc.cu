@@ -30,8 +30,9 @@ namespace {
 constexpr long NOALLOC_MAX_POINTS = 1L << 20;
 constexpr int NOALLOC_MAX_DEVICES = 64;
 
-// [0, 8 * NOALLOC_MAX_POINTS): potential (float or double per point); then the error word.
-static __device__ __align__(256) unsigned char g_noalloc_scratch[8 * NOALLOC_MAX_POINTS + 256];
+// [0, 16 * NOALLOC_MAX_POINTS): one 16-byte record per point (the potential in the compute
+// precision, an empty projector range); then the error word.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[16 * NOALLOC_MAX_POINTS + 256];
 
 std::mutex g_addr_mutex;
 void *g_addr[NOALLOC_MAX_DEVICES] = {};
@@ -53,10 +54,14 @@ int scratch_address(void **out) {
 }
 
 template <typename R>
-__global__ void noalloc_prepare(long N, const double *vloc, R *veff, int *err) {
+__global__ void noalloc_prepare(long N, const double *vloc, PointAux *aux, int *err) {
   const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (i == 0) *err = 0;  // the error word must start at zero on every call
-  if (i < N) veff[i] = (R)vloc[i];
+  if (i < N) {
+    PointAux a{0.0, 0, 0};
+    *reinterpret_cast<R *>(&a.veff) = (R)vloc[i];
+    aux[i] = a;
+  }
 }
 
 }  // namespace
@@ -76,7 +81,8 @@ extern "C" int tdks_apply_H_noalloc(int nx, int ny, int nz, double h, int fd_ord
   void *scratch = nullptr;
   if (int rc = scratch_address(&scratch)) return rc;
   unsigned char *base = static_cast<unsigned char *>(scratch);
-  int *err = reinterpret_cast<int *>(base + 8 * NOALLOC_MAX_POINTS);
+  int *err = reinterpret_cast<int *>(base + 16 * NOALLOC_MAX_POINTS);
+  PointAux *aux = reinterpret_cast<PointAux *>(base);
   cudaStream_t st = (cudaStream_t)stream;
 
   // a host-side description of the grid (no device memory behind it)
@@ -86,12 +92,12 @@ extern "C" int tdks_apply_H_noalloc(int nx, int ny, int nz, double h, int fd_ord
   s.BS = prec == TDKS_C64 ? 2 * OVC : OVC;
   s.n_batches = (n_orb + s.BS - 1) / s.BS;
   s.n_kb = s.n_batches;
-  s.veff = base;
+  s.aux = aux;
   s.stream = st;
 
   const int blocks = (int)((N + 255) / 256);
-  if (prec == TDKS_C64) noalloc_prepare<float><<<blocks, 256, 0, st>>>(N, dev_vloc, (float *)base, err);
-  else noalloc_prepare<double><<<blocks, 256, 0, st>>>(N, dev_vloc, (double *)base, err);
+  if (prec == TDKS_C64) noalloc_prepare<float><<<blocks, 256, 0, st>>>(N, dev_vloc, aux, err);
+  else noalloc_prepare<double><<<blocks, 256, 0, st>>>(N, dev_vloc, aux, err);
   CU(cudaGetLastError());
 
   const double A0[3] = {0.0, 0.0, 0.0};
@@ -101,10 +107,10 @@ extern "C" int tdks_apply_H_noalloc(int nx, int ny, int nz, double h, int fd_ord
   p.in = dev_in;
   p.out = dev_out;
   p.err = err;
-  CUtensorMap tm;
+  SweepMaps tm;
   cudaError_t e;
-  if (tma_supported(M, s.tx, s.ty) && encode_map(&s, dev_in, MODE_MID, &tm))
-    e = launch_sweep_tma(M, prec, MODE_MID, s.tx, s.ty, &tm, p, 0, st);
+  if (tma_supported(M, s.tx, s.ty) && encode_sweep_maps(&s, dev_in, MODE_MID, &tm))
+    e = launch_sweep_tma(M, prec, MODE_MID, s.tx, s.ty, tm, p, 0, st);
   else
     e = launch_sweep(M, prec, MODE_MID, 0, s.tx, s.ty, p, 0, st);
   if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("stencil sweep: ") + cudaGetErrorString(e));

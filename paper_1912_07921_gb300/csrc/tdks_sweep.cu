@@ -159,8 +159,9 @@ sweep_kernel(const SweepParams p) {
       LastOperands<P> lop;
       lop.hi = lop.lo = lop.t1 = lop.t2 = T::zero();
       if (own) {
-        ve = reinterpret_cast<const R *>(p.veff)[pt];
-        if (p.rowptr) { r0 = __ldg(p.rowptr + pt); r1 = __ldg(p.rowptr + pt + 1); }
+        const PointAux a = p.aux[pt];
+        ve = *reinterpret_cast<const R *>(&a.veff);
+        if (p.has_proj) { r0 = a.r0; r1 = a.r1; }
         if (MODE == MODE_LAST) load_last<P>(p, idx, lop);
       }
       __syncthreads();

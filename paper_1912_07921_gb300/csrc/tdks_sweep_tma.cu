@@ -27,6 +27,7 @@ namespace tdks {
 namespace {
 
 constexpr long long WAIT_LIMIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
+constexpr long long DRAIN_LIMIT_CYCLES = 200000000LL;  // ~0.1 s per copy on the error path
 
 __device__ __forceinline__ uint32_t smem_u32(const void *ptr) {
   return (uint32_t)__cvta_generic_to_shared(ptr);
@@ -49,11 +50,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  long long limit = WAIT_LIMIT_CYCLES) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity))
-    if (clock64() - t0 > WAIT_LIMIT_CYCLES) return false;
+    if (clock64() - t0 > limit) return false;
   return true;
 }
 __device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *tmap, uint64_t *bar, int c0, int c1,
@@ -62,6 +64,15 @@ __device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *tmap, 
       "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
       "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *tmap, uint64_t *bar, int c0, int c1,
+                                            int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
       : "memory");
 }
 
@@ -76,32 +87,50 @@ __device__ __forceinline__ void static_for(F &&f) {
   }
 }
 
-// U planes per copy (box depth U in z) and per loop iteration; each thread computes U
-// independent outputs per iteration, which halves the per-output cost of the barrier,
-// the waits and the address arithmetic and doubles the independent work in flight.
-// The ring holds 8 planes.
-template <int M, int TX, int TY, int U>
+// Shared-memory plan: three TMA-fed rings, each slot completed by one mbarrier.
+//   centre ring (SC slots): U planes of the input tile (no halo), which feed the per-thread
+//     register z-queue; a slot is free again as soon as its planes are in registers;
+//   halo ring (SH slots): U output planes of the input with their x/y halo, followed by the
+//     U planes' per-point records; read when those planes are computed;
+//   operand ring (SO slots, last Taylor term only): the four own-point operand tiles of one
+//     output plane (state hi, state lo, t1, t2).
+// Keeping the z history in registers (not in the ring) lets every ring run several slots
+// ahead of the plane being computed.
+template <int M, int TX, int TY, int U, bool OPS>
 struct TmaGeom {
   static constexpr int SX = TX + 2 * M, SY = TY + 2 * M;
-  static constexpr int PLANE = SX * SY * OVC;  // 16-byte vectors per plane
-  static constexpr int SLOT = PLANE * U;       // vectors per ring slot
-  static constexpr uint32_t SLOT_BYTES = SLOT * 16;
-  static constexpr int S = 8 / U;              // ring depth (slots)
-  static constexpr size_t SMEM = (size_t)S * SLOT_BYTES + 128;
+  static constexpr int PLANE = SX * SY * OVC;                        // vectors per halo plane
+  static constexpr int CPLANE = TX * TY * OVC;                       // vectors per centre plane
+  static constexpr uint32_t CSLOT_BYTES = (uint32_t)CPLANE * 16 * U;
+  static constexpr uint32_t IN_BYTES = (uint32_t)PLANE * 16 * U;
+  static constexpr uint32_t AUX_BYTES = (uint32_t)TX * TY * 16 * U;
+  static constexpr uint32_t HSLOT_BYTES = IN_BYTES + AUX_BYTES;
+  static constexpr uint32_t OPT_BYTES = (uint32_t)CPLANE * 16;       // one operand tile
+  static constexpr uint32_t OP_BYTES = 4 * OPT_BYTES;
+  static constexpr int SO = OPS ? 2 : 0;
+  static constexpr int SC = U == 1 ? (OPS ? 4 : 6) : 4;
+  static constexpr size_t BUDGET = 227 * 1024 - 2048;                // dynamic smem available
+  static constexpr int SH_FIT =
+      (int)((BUDGET - 128 - (size_t)SO * OP_BYTES - (size_t)SC * CSLOT_BYTES) / HSLOT_BYTES);
+  static constexpr int SH = SH_FIT < 8 ? SH_FIT : 8;
+  static constexpr size_t SMEM = (size_t)SC * CSLOT_BYTES + (size_t)SH * HSLOT_BYTES + (size_t)SO * OP_BYTES + 128;
+  static_assert(SH >= 2, "halo ring too small");
 };
 
-// Work sources: a single system (parameters and tensor map are kernel parameters), or a
+// Work sources: a single system (parameters and tensor maps are kernel parameters), or a
 // batch of systems (per-system parameters and tensor maps in device arrays; a CTA stages
 // the parameters of its current item in shared memory).
 struct SingleSrc {
   const SweepParams *p;
-  const CUtensorMap *tmap;
+  const SweepMaps *maps;
   __device__ __forceinline__ long n_items() const { return p->n_items; }
-  __device__ __forceinline__ void item(long it, const SweepParams *&pp, const CUtensorMap *&tm, long &local) const {
+  __device__ __forceinline__ void item(long it, const SweepParams *&pp, const SweepMaps *&mp, long &local) const {
     pp = p;
-    tm = tmap;
+    mp = maps;
     local = it;
   }
+  __device__ __forceinline__ int sys_of(long) const { return 0; }
+  __device__ __forceinline__ const SweepMaps *maps_of(int) const { return maps; }
 };
 
 __device__ __forceinline__ int find_item_sys(const long *begin, int n, long u) {
@@ -116,11 +145,103 @@ __device__ __forceinline__ int find_item_sys(const long *begin, int n, long u) {
 struct BatchSrc {
   const BatchSweepArgs *a;
   __device__ __forceinline__ long n_items() const { return a->total_items; }
-  __device__ __forceinline__ void item(long it, const SweepParams *&pp, const CUtensorMap *&tm, long &local) const {
+  __device__ __forceinline__ void item(long it, const SweepParams *&pp, const SweepMaps *&mp, long &local) const {
     const int s = find_item_sys(a->item_begin, a->n_sys, it);
     pp = a->params + s;
-    tm = reinterpret_cast<const CUtensorMap *>(a->tmaps) + 4 * s + a->which;
+    mp = a->maps + 4 * s + a->which;
     local = it - a->item_begin[s];
+  }
+  __device__ __forceinline__ int sys_of(long it) const { return find_item_sys(a->item_begin, a->n_sys, it); }
+  __device__ __forceinline__ const SweepMaps *maps_of(int s) const { return a->maps + 4 * s + a->which; }
+};
+
+// Sequential cursor over one kind of load of the CTA's items (thread 0 only).  The item's
+// geometry is decoded once, when the cursor enters the item, so issuing a load costs a few
+// instructions: the other threads wait for thread 0 at the next barrier.
+struct LoadCursor {
+  long ii;     // item index among the CTA's items (-1: not entered yet)
+  int l;       // load index within the item
+  int n;       // loads of this kind in the item
+  int tx, ty, kb, z0;
+  int sys;     // system of the item (batch)
+  long issued; // loads issued so far
+};
+
+// Work item -> tile (tx, ty), orbital block kb and z chunk [z0, z1).
+__device__ __forceinline__ void item_geom(const SweepParams &q, long it, int &tx, int &ty, int &kb, int &z0,
+                                          int &z1) {
+  tx = (int)(it % q.n_tx);
+  it /= q.n_tx;
+  ty = (int)(it % q.n_ty);
+  it /= q.n_ty;
+  kb = (int)(it % q.n_kb);
+  it /= q.n_kb;
+  z0 = (int)it * q.zc;
+  z1 = min(z0 + q.zc, q.nz);
+}
+
+// Loads per item: 0 = centre (queue planes z0-M .. z1+M-1, U per load), 1 = halo (output
+// planes, U per load), 2 = operands (one per output plane).
+template <int M, int U>
+__device__ __forceinline__ int loads_of(int kind, int z0, int z1) {
+  if (kind == 0) return (z1 - z0 + 2 * M + U - 1) / U;
+  if (kind == 1) return (z1 - z0 + U - 1) / U;
+  return z1 - z0;
+}
+
+// The producer side of the rings (thread 0 only).
+template <int M, int TX, int TY, int U, class G, int SC, int SH, int SO, class Src>
+struct Loader {
+  Src src;
+  long n_my;
+  unsigned char *cbase, *hbase, *obase;
+  uint64_t *cfull, *hfull, *ofull;
+
+  // move the cursor onto its next load (decoding the geometry of an item it enters)
+  __device__ __forceinline__ void advance(LoadCursor &c, int kind) const {
+    while (c.ii < n_my && (c.ii < 0 || c.l >= c.n)) {
+      c.ii += 1;
+      c.l = 0;
+      c.n = 0;
+      if (c.ii < n_my) {
+        const SweepParams *qp = nullptr;
+        const SweepMaps *mq = nullptr;
+        long local = 0;
+        src.item(blockIdx.x + c.ii * gridDim.x, qp, mq, local);
+        int z1 = 0;
+        item_geom(*qp, local, c.tx, c.ty, c.kb, c.z0, z1);
+        c.sys = src.sys_of(blockIdx.x + c.ii * gridDim.x);
+        c.n = loads_of<M, U>(kind, c.z0, z1);
+      }
+    }
+  }
+
+  // issue the next load of `kind`; nothing past the CTA's last item
+  __device__ __forceinline__ void issue(LoadCursor &c, int kind) const {
+    advance(c, kind);
+    if (c.ii >= n_my) return;
+    const SweepMaps *mp = src.maps_of(c.sys);
+    if (kind == 0) {
+      const int slot = (int)(c.issued % SC);
+      mbar_expect_tx(&cfull[slot], G::CSLOT_BYTES);
+      tma_load_5d(cbase + (size_t)slot * G::CSLOT_BYTES, &mp->ctr, &cfull[slot], 0, c.tx * TX, c.ty * TY,
+                  c.z0 - M + U * c.l, c.kb);
+    } else if (kind == 1) {
+      const int slot = (int)(c.issued % SH);
+      unsigned char *dst = hbase + (size_t)slot * G::HSLOT_BYTES;
+      const int zp = c.z0 + U * c.l;
+      mbar_expect_tx(&hfull[slot], G::HSLOT_BYTES);
+      tma_load_5d(dst, &mp->in, &hfull[slot], 0, c.tx * TX - M, c.ty * TY - M, zp, c.kb);
+      tma_load_4d(dst + G::IN_BYTES, &mp->aux, &hfull[slot], 0, c.tx * TX, c.ty * TY, zp);
+    } else {
+      const int slot = (int)(c.issued % SO);
+      unsigned char *dst = obase + (size_t)slot * G::OP_BYTES;
+      mbar_expect_tx(&ofull[slot], G::OP_BYTES);
+      for (int j = 0; j < 4; j++)
+        tma_load_5d(dst + j * G::OPT_BYTES, &mp->op[j], &ofull[slot], 0, c.tx * TX, c.ty * TY, c.z0 + c.l, c.kb);
+    }
+    c.issued++;
+    c.l++;
   }
 };
 
@@ -130,16 +251,22 @@ __device__ __forceinline__ void tma_sweep_body(const Src &src) {
   typedef typename T::V V;
   typedef typename T::S S_;
   typedef typename T::R R;
-  typedef TmaGeom<M, TX, TY, U> G;
+  constexpr bool OPS = MODE == MODE_LAST;
+  typedef TmaGeom<M, TX, TY, U, OPS> G;
   static_assert(M % U == 0, "M must be a multiple of U");
+  static_assert(!OPS || U == 1, "the last Taylor term takes one plane per iteration");
   constexpr int NT = OVC * TX * TY;
-  constexpr int S = G::S;
+  constexpr int SC = G::SC, SH = G::SH;
+  constexpr int SO = G::SO > 0 ? G::SO : 1;
   constexpr int QN = 2 * M + U;   // z-queue entries
-  constexpr int LP = 2 * M / U;   // priming loads per item
-  constexpr int MU = M / U;       // loads between a plane's arrival and its output
+  constexpr int LP = 2 * M / U;   // priming centre loads per item
   extern __shared__ unsigned char smem_raw[];
-  V *ring = reinterpret_cast<V *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
-  __shared__ __align__(8) uint64_t full[S];
+  unsigned char *cbase = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
+  unsigned char *hbase = cbase + (size_t)SC * G::CSLOT_BYTES;
+  unsigned char *obase = hbase + (size_t)SH * G::HSLOT_BYTES;
+  __shared__ __align__(8) uint64_t cfull[SC];
+  __shared__ __align__(8) uint64_t hfull[SH];
+  __shared__ __align__(8) uint64_t ofull[SO];
   __shared__ double red[NT / 32][4];
   __shared__ int s_abort;
   __shared__ SweepParams s_params;  // batch: parameters of the current item's system
@@ -148,55 +275,41 @@ __device__ __forceinline__ void tma_sweep_body(const Src &src) {
   const int v = tid % OVC;
   const int lx = (tid / OVC) % TX;
   const int ly = tid / (OVC * TX);
-  const int csl = ((ly + M) * G::SX + (lx + M)) * OVC + v;
+  const int hsl = ((ly + M) * G::SX + (lx + M)) * OVC + v;  // own vector in a halo plane
+  const int tsl = ly * TX + lx;                              // own point in a tile
+  const int csl = tsl * OVC + v;                             // own vector in a centre plane
   const long n_items_all = src.n_items();
   const long n_my = (long)blockIdx.x < n_items_all ? (n_items_all - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   if (n_my == 0) return;
 
   if (tid == 0) {
-    for (int s = 0; s < S; s++) mbar_init(&full[s], 1);
+    for (int s = 0; s < SC; s++) mbar_init(&cfull[s], 1);
+    for (int s = 0; s < SH; s++) mbar_init(&hfull[s], 1);
+    for (int s = 0; s < SO; s++) mbar_init(&ofull[s], 1);
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
 
-  auto geom = [&](const SweepParams &q, long it, int &tx, int &ty, int &kb, int &z0, int &z1) {
-    tx = (int)(it % q.n_tx); it /= q.n_tx;
-    ty = (int)(it % q.n_ty); it /= q.n_ty;
-    kb = (int)(it % q.n_kb); it /= q.n_kb;
-    z0 = (int)it * q.zc;
-    z1 = min(z0 + q.zc, q.nz);
-  };
-  auto loads_of = [&](int z0, int z1) { return (z1 - z0 + 2 * M + U - 1) / U; };
+  const Loader<M, TX, TY, U, G, SC, SH, SO, Src> ld{src, n_my, cbase, hbase, obase, cfull, hfull, ofull};
+  // the cursors live in shared memory: only thread 0 uses them, and registers are scarce
+  __shared__ LoadCursor cur[3];
+  LoadCursor &cc = cur[0], &hc = cur[1], &oc = cur[2];
+  if (tid == 0) {
+    for (int k = 0; k < 3; k++) cur[k] = LoadCursor{-1, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int s = 0; s < SC; s++) ld.issue(cc, 0);
+    for (int s = 0; s < SH; s++) ld.issue(hc, 1);
+    if (OPS)
+      for (int s = 0; s < SO; s++) ld.issue(oc, 2);
+  }
 
-  // producer cursor (thread 0 only): the slot loads of all this CTA's items, in order
-  long pi = 0, issued = 0;
-  int pl = 0;
-  auto issue_next = [&]() {
-    if (pi >= n_my) return;
-    const SweepParams *qp;
-    const CUtensorMap *tm;
-    long local;
-    src.item(blockIdx.x + pi * gridDim.x, qp, tm, local);
-    int tx, ty, kb, z0, z1;
-    geom(*qp, local, tx, ty, kb, z0, z1);
-    const int slot = (int)(issued % S);
-    mbar_expect_tx(&full[slot], G::SLOT_BYTES);
-    tma_load_5d(ring + (size_t)slot * G::SLOT, tm, &full[slot], 0, tx * TX - M, ty * TY - M,
-                z0 - M + U * pl, kb);
-    issued++;
-    if (++pl >= loads_of(z0, z1)) { pl = 0; pi++; }
-  };
-  if (tid == 0)
-    for (int s = 0; s < S; s++) issue_next();
-
-  long g = 0;  // slot loads consumed
+  long gc = 0, gh = 0;  // centre / halo (and operand) loads consumed
   for (long ii = 0; ii < n_my; ii++) {
     const long item = blockIdx.x + ii * gridDim.x;
     const SweepParams *pp;
-    const CUtensorMap *tm_unused;
+    const SweepMaps *mp_unused;
     long local;
-    src.item(item, pp, tm_unused, local);
+    src.item(item, pp, mp_unused, local);
     if constexpr (BATCH) {
       __syncthreads();  // everyone is done with the previous item's parameters
       if (tid == 0) s_params = *pp;
@@ -213,83 +326,79 @@ __device__ __forceinline__ void tma_sweep_body(const Src &src) {
     const typename W0T<P>::type w0 = (typename W0T<P>::type)p.w[0];
     const S_ CR = T::bc(p.cr), CI = T::bc(p.ci);
     int tx, ty, kb, z0, z1;
-    geom(p, local, tx, ty, kb, z0, z1);
+    item_geom(p, local, tx, ty, kb, z0, z1);
     const int kidx = kb / p.n_batches;
     const int gx = tx * TX + lx, gy = ty * TY + ly;
     const bool own = gx < nx && gy < ny;
-    const int nl = loads_of(z0, z1);
-    // own point of the next output plane: grid index and vector index
-    long pt = ((long)z0 * ny + gy) * nx + gx;
-    long idx = ((long)kb * N + pt) * OVC + v;
+    const int nl = loads_of<M, U>(0, z0, z1);
+    // vector index of the own point in the first output plane (advances one plane per output)
+    long idx = ((long)kb * N + ((long)z0 * ny + gy) * nx + gx) * OVC + v;
     V Q[QN];
 #pragma unroll
     for (int j = 0; j < QN; j++) Q[j] = T::zero();
     ObsAcc<P> oa;
-    // own-point operands of the next U output planes (prefetched one iteration ahead)
-    R ve[U];
-    int r0[U], r1[U];
-    LastOperands<P> lop[U];
-    auto prefetch = [&](int zfirst) {
-#pragma unroll
-      for (int u = 0; u < U; u++) {
-        ve[u] = R(0);
-        r0[u] = r1[u] = 0;
-        lop[u].hi = lop[u].lo = lop[u].t1 = lop[u].t2 = T::zero();
-        if (own && zfirst + u < z1) {
-          const long q = pt + u * plane_pts;
-          ve[u] = reinterpret_cast<const R *>(p.veff)[q];
-          if (p.rowptr) { r0[u] = __ldg(p.rowptr + q); r1[u] = __ldg(p.rowptr + q + 1); }
-          if (MODE == MODE_LAST) load_last<P>(p, idx + u * plane_pts * OVC, lop[u]);
-        }
-      }
-    };
-    prefetch(z0);
 
     int l = 0;
     bool aborted = false;
-    // one slot load; RQ = compile-time queue position of its first plane
+    // one centre load (and, past the priming loads, one halo load); RQ = compile-time
+    // queue position of its first plane
     auto iteration = [&](auto rq) {
       constexpr int RQ = decltype(rq)::value;
-      const int slot = (int)(g & (S - 1));
-      if (!mbar_wait_bounded(&full[slot], (uint32_t)((g / S) & 1))) s_abort = 1;
-      const V *in_slot = ring + (size_t)slot * G::SLOT;
+      const int cs = (int)(gc % SC);
+      if (!mbar_wait_bounded(&cfull[cs], (uint32_t)((gc / SC) & 1))) s_abort = 1;
+      const V *cslot = reinterpret_cast<const V *>(cbase + (size_t)cs * G::CSLOT_BYTES);
 #pragma unroll
-      for (int u = 0; u < U; u++) Q[(RQ + u) % QN] = in_slot[u * G::PLANE + csl];
-      if (l >= LP) {
+      for (int u = 0; u < U; u++) Q[(RQ + u) % QN] = cslot[u * G::CPLANE + csl];
+      const bool out = l >= LP;
+      if (out) {
         const int zf = z0 + U * (l - LP);
-        const V *xs = ring + (size_t)((g - MU) & (S - 1)) * G::SLOT;
-        R ve_c[U];
-        int r0_c[U], r1_c[U];
-        LastOperands<P> cur[U];
-#pragma unroll
-        for (int u = 0; u < U; u++) { ve_c[u] = ve[u]; r0_c[u] = r0[u]; r1_c[u] = r1[u]; cur[u] = lop[u]; }
-        const long cidx = idx;
-        pt += U * plane_pts;
-        idx += U * plane_pts * OVC;
-        prefetch(zf + U);
+        const int hs = (int)(gh % SH);
+        if (!mbar_wait_bounded(&hfull[hs], (uint32_t)((gh / SH) & 1))) s_abort = 1;
+        const unsigned char *hslot = hbase + (size_t)hs * G::HSLOT_BYTES;
+        const V *xs = reinterpret_cast<const V *>(hslot);
+        const PointAux *ax = reinterpret_cast<const PointAux *>(hslot + G::IN_BYTES);
+        LastOperands<P> lop;
+        lop.hi = lop.lo = lop.t1 = lop.t2 = T::zero();
+        if constexpr (OPS) {
+          const int os = (int)(gh % SO);
+          if (!mbar_wait_bounded(&ofull[os], (uint32_t)((gh / SO) & 1))) s_abort = 1;
+          const V *ob = reinterpret_cast<const V *>(obase + (size_t)os * G::OP_BYTES);
+          lop.hi = ob[csl];
+          lop.lo = ob[G::CPLANE + csl];
+          lop.t1 = ob[2 * G::CPLANE + csl];
+          lop.t2 = ob[3 * G::CPLANE + csl];
+        }
         static_for<0, U>([&](auto uc) {
           constexpr int u = decltype(uc)::value;
           constexpr int QB = (RQ + U + u) % QN;  // queue position of plane (zf + u) - M
+          const PointAux a = ax[u * TX * TY + tsl];
+          const R ve = *reinterpret_cast<const R *>(&a.veff);
           V gax[3];
-          V acc = stencil_point<M, P, 0, QB, QN>(p, W, w0, Q, xs + u * G::PLANE, csl, G::SX * OVC, ve_c[u], false,
+          V acc = stencil_point<M, P, 0, QB, QN>(p, W, w0, Q, xs + u * G::PLANE, hsl, G::SX * OVC, ve, false,
                                                  false, gax);
           const bool live = own && (zf + u < z1);
-          if (live && r1_c[u] > r0_c[u]) acc = kb_scatter<P, 0>(p, kb, kidx, v, r0_c[u], r1_c[u], acc);
+          if (live && p.has_proj && a.r1 > a.r0) acc = kb_scatter<P, 0>(p, kb, kidx, v, a.r0, a.r1, acc);
           const V c0 = Q[(QB + M) % QN];
           if (MODE == MODE_FIRST && p.do_obs && live) oa.add_e(c0, acc);
-          finish_point<P, MODE>(p, CR, CI, live, cidx + (long)u * plane_pts * OVC, v, kidx, c0, acc, cur[u]);
+          finish_point<P, MODE>(p, CR, CI, live, idx + (long)u * plane_pts * OVC, v, kidx, c0, acc, lop);
         });
+        idx += U * plane_pts * OVC;
       }
       __syncthreads();
       if (s_abort) {
         aborted = true;
         return;
       }
-      if (tid == 0 && g >= MU) {
+      if (tid == 0) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        issue_next();
+        ld.issue(cc, 0);
+        if (out) {
+          ld.issue(hc, 1);
+          if (OPS) ld.issue(oc, 2);
+        }
       }
-      g++;
+      gc++;
+      if (out) gh++;
       l++;
     };
     int rq = 0;
@@ -306,9 +415,14 @@ __device__ __forceinline__ void tma_sweep_body(const Src &src) {
       rq = rq + U >= QN ? rq + U - QN : rq + U;
     }
     if (aborted) {
-      if (tid == 0) {
+      if (tid == 0) {  // (the cursors are thread 0's; nobody else reads them)
         if (p.err) atomicExch(p.err, 1);
-        for (long j = g; j < issued; j++) mbar_wait_bounded(&full[j & (S - 1)], (uint32_t)((j / S) & 1));
+        for (long j = gc; j < cc.issued; j++)
+          mbar_wait_bounded(&cfull[j % SC], (uint32_t)((j / SC) & 1), DRAIN_LIMIT_CYCLES);
+        for (long j = gh; j < hc.issued; j++)
+          mbar_wait_bounded(&hfull[j % SH], (uint32_t)((j / SH) & 1), DRAIN_LIMIT_CYCLES);
+        for (long j = gh; j < oc.issued; j++)
+          mbar_wait_bounded(&ofull[j % SO], (uint32_t)((j / SO) & 1), DRAIN_LIMIT_CYCLES);
       }
       return;
     }
@@ -318,8 +432,8 @@ __device__ __forceinline__ void tma_sweep_body(const Src &src) {
 
 template <int M, int P, int MODE, int TX, int TY, int U>
 __global__ void __launch_bounds__(OVC * TX * TY, 1)
-tma_sweep_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ SweepParams p) {
-  const SingleSrc src{&p, &tmap};
+tma_sweep_kernel(const __grid_constant__ SweepMaps maps, const __grid_constant__ SweepParams p) {
+  const SingleSrc src{&p, &maps};
   tma_sweep_body<M, P, MODE, TX, TY, U, false>(src);
 }
 
@@ -330,16 +444,16 @@ tma_sweep_batch_kernel(const __grid_constant__ BatchSweepArgs a) {
   tma_sweep_body<M, P, MODE, TX, TY, U, true>(src);
 }
 
-// Planes per TMA copy of a sweep mode (the z depth of its tensor-map box): complex64 term
-// sweeps take two planes per iteration, everything else one.
+// Planes per TMA copy of a sweep mode (the z depth of its tensor-map boxes): complex64
+// term sweeps take two planes per iteration, everything else one.
 int tma_planes(int prec, int mode) { return (prec == P_C64 && mode != MODE_LAST) ? 2 : 1; }
 
 bool tma_supported(int M, int tx, int ty) { return (M == 2 || M == 4) && tx == 16 && ty == 8; }
 
-template <int M, int P, int MODE, int TX, int TY, int U>
-static cudaError_t launch_tma_t(const void *tmap, const SweepParams &p, int grid, cudaStream_t s) {
-  typedef TmaGeom<M, TX, TY, U> G;
-  auto k = tma_sweep_kernel<M, P, MODE, TX, TY, U>;
+template <int M, int P, int MODE, int U>
+static cudaError_t launch_tma_t(const SweepMaps &maps, const SweepParams &p, int grid, cudaStream_t s) {
+  typedef TmaGeom<M, 16, 8, U, MODE == MODE_LAST> G;
+  auto k = tma_sweep_kernel<M, P, MODE, 16, 8, U>;
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
@@ -352,14 +466,14 @@ static cudaError_t launch_tma_t(const void *tmap, const SweepParams &p, int grid
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     grid = (int)(p.n_items < sms ? p.n_items : sms);
   }
-  k<<<grid, OVC * TX * TY, G::SMEM, s>>>(*reinterpret_cast<const CUtensorMap *>(tmap), p);
+  k<<<grid, OVC * 16 * 8, G::SMEM, s>>>(maps, p);
   return cudaGetLastError();
 }
 
-template <int M, int P, int MODE, int TX, int TY, int U>
+template <int M, int P, int MODE, int U>
 static cudaError_t launch_tma_batch_t(const BatchSweepArgs &a, cudaStream_t s) {
-  typedef TmaGeom<M, TX, TY, U> G;
-  auto k = tma_sweep_batch_kernel<M, P, MODE, TX, TY, U>;
+  typedef TmaGeom<M, 16, 8, U, MODE == MODE_LAST> G;
+  auto k = tma_sweep_batch_kernel<M, P, MODE, 16, 8, U>;
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
@@ -371,16 +485,18 @@ static cudaError_t launch_tma_batch_t(const BatchSweepArgs &a, cudaStream_t s) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = (int)(a.total_items < sms ? a.total_items : sms);
   if (grid <= 0) return cudaSuccess;
-  k<<<grid, OVC * TX * TY, G::SMEM, s>>>(a);
+  k<<<grid, OVC * 16 * 8, G::SMEM, s>>>(a);
   return cudaGetLastError();
 }
 
+// complex64: two planes per iteration in the term sweeps (= tma_planes); complex128
+// (FP64-bound, twice the registers per value) one plane; the last term one plane.
 template <int M, int P>
 static cudaError_t tma_batch_by_mode(int mode, const BatchSweepArgs &a, cudaStream_t s) {
   switch (mode) {
-    case MODE_FIRST: return launch_tma_batch_t<M, P, MODE_FIRST, 16, 8, P == P_C64 ? 2 : 1>(a, s);
-    case MODE_MID: return launch_tma_batch_t<M, P, MODE_MID, 16, 8, P == P_C64 ? 2 : 1>(a, s);
-    case MODE_LAST: return launch_tma_batch_t<M, P, MODE_LAST, 16, 8, 1>(a, s);
+    case MODE_FIRST: return launch_tma_batch_t<M, P, MODE_FIRST, P == P_C64 ? 2 : 1>(a, s);
+    case MODE_MID: return launch_tma_batch_t<M, P, MODE_MID, P == P_C64 ? 2 : 1>(a, s);
+    case MODE_LAST: return launch_tma_batch_t<M, P, MODE_LAST, 1>(a, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -392,24 +508,22 @@ cudaError_t launch_sweep_tma_batch(int M, int prec, int mode, const BatchSweepAr
 }
 
 template <int M, int P>
-static cudaError_t tma_by_mode(int mode, const void *tmap, const SweepParams &p, int grid, cudaStream_t s) {
+static cudaError_t tma_by_mode(int mode, const SweepMaps &maps, const SweepParams &p, int grid, cudaStream_t s) {
   switch (mode) {
-    // complex64: two planes per iteration in the term sweeps; complex128 (FP64-bound, and
-    // twice the registers per value) one plane
-    case MODE_FIRST: return launch_tma_t<M, P, MODE_FIRST, 16, 8, P == P_C64 ? 2 : 1>(tmap, p, grid, s);
-    case MODE_MID: return launch_tma_t<M, P, MODE_MID, 16, 8, P == P_C64 ? 2 : 1>(tmap, p, grid, s);  // = tma_planes
-    case MODE_LAST: return launch_tma_t<M, P, MODE_LAST, 16, 8, 1>(tmap, p, grid, s);
+    case MODE_FIRST: return launch_tma_t<M, P, MODE_FIRST, P == P_C64 ? 2 : 1>(maps, p, grid, s);
+    case MODE_MID: return launch_tma_t<M, P, MODE_MID, P == P_C64 ? 2 : 1>(maps, p, grid, s);
+    case MODE_LAST: return launch_tma_t<M, P, MODE_LAST, 1>(maps, p, grid, s);
   }
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_sweep_tma(int M, int prec, int mode, int tx, int ty, const void *tmap, const SweepParams &p,
+cudaError_t launch_sweep_tma(int M, int prec, int mode, int tx, int ty, const SweepMaps &maps, const SweepParams &p,
                              int grid, cudaStream_t s) {
   if (!tma_supported(M, tx, ty)) return cudaErrorInvalidValue;
-  if (M == 2) return prec == P_C64 ? tma_by_mode<2, P_C64>(mode, tmap, p, grid, s)
-                                   : tma_by_mode<2, P_C128>(mode, tmap, p, grid, s);
-  return prec == P_C64 ? tma_by_mode<4, P_C64>(mode, tmap, p, grid, s)
-                       : tma_by_mode<4, P_C128>(mode, tmap, p, grid, s);
+  if (M == 2) return prec == P_C64 ? tma_by_mode<2, P_C64>(mode, maps, p, grid, s)
+                                   : tma_by_mode<2, P_C128>(mode, maps, p, grid, s);
+  return prec == P_C64 ? tma_by_mode<4, P_C64>(mode, maps, p, grid, s)
+                       : tma_by_mode<4, P_C128>(mode, maps, p, grid, s);
 }
 
 }  // namespace tdks

@@ -46,20 +46,22 @@ struct tdks_system {
   void *psi_lo = nullptr;       // lo part of a complex64 system's state
   void *term[3] = {nullptr, nullptr, nullptr};
   double *vloc = nullptr;
-  void *veff = nullptr;
+  tdks::PointAux *aux = nullptr;   // V_eff and projector entry range per point
   double *dens_part = nullptr;
   double *lda_part = nullptr;
   double *obs_part = nullptr;
   double *ring = nullptr;
   double *obs_rec = nullptr;    // single record for tdks_observe
   double *d_kvec = nullptr, *d_wocc = nullptr, *d_D = nullptr;
-  int *d_rowptr = nullptr, *d_rowent = nullptr, *d_atom_begin = nullptr;
+  int *d_rowent = nullptr, *d_atom_begin = nullptr;
   tdks::ProjEntry *d_ent = nullptr;
   void *d_q = nullptr;
+  double2 *d_qpart = nullptr;   // gather partial sums, gchunks per (atom, k-batch)
+  int gchunks = 1;
   double *staging = nullptr;
   int *d_err = nullptr;
   // TMA tensor maps over the four sweep inputs (state, t1, t2, t3) for the current tile
-  CUtensorMap tmaps[4];
+  tdks::SweepMaps smaps[4];   // TMA maps of the four Taylor-term sweeps
   bool tmaps_ok = false;
   int path = 0;                 // 0: TMA sweep where possible, 1: general sweep
   size_t state_bytes = 0, term_bytes = 0;
@@ -89,6 +91,8 @@ void sweep_geometry(const tdks_system *s, tdks::SweepParams &p);
 void sweep_common(const tdks_system *s, tdks::SweepParams &p, const double A[3]);
 long n_items_of(const tdks_system *s);
 bool encode_map(const tdks_system *s, const void *ptr, int mode, CUtensorMap *out);
+// all maps of a TMA sweep of `mode` over input `in` (the operand maps only for the last term)
+bool encode_sweep_maps(const tdks_system *s, const void *in, int mode, tdks::SweepMaps *out);
 int ensure_density(tdks_system *s);
 int check_err(tdks_system *s);
 double kinetic_max(const tdks_system *s);
