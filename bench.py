@@ -171,6 +171,8 @@ def run_ours(args, rank, world, local_rank):
     inp = I.make_inputs(spec)
     stream = torch.cuda.Stream()
     sysm = System(spec, inp, stream=stream.cuda_stream)
+    if args.sweep_path:
+        sysm.set_sweep_path(args.sweep_path)
     subs = spec.substeps
     dt = spec.dt
     upd_per_step = spec.n_points * spec.n_orb
@@ -251,8 +253,8 @@ def run_ours(args, rank, world, local_rank):
                          "traffic": _traffic_per_launch() if spec.n_orb == 64 and prec == I.PREC_C64 else None,
                          "sweep_source_hash": sweep_source_hash(),
                          "bytes_per_launch": per_launch_bytes, "avg_launch_us": avg_launch_s * 1e6},
-            "kernel_ms": {"sweep": sweep_ms, "sweep_launches": sweep_n, "gather": gath_ms,
-                          "gather_launches": gath_n, "density_lda_finalize": aux_ms, "aux_launches": aux_n},
+            "kernel_ms": {"sweep": sweep_ms, "sweep_launches": sweep_n, "projector": gath_ms,
+                          "projector_steps": gath_n, "density_lda_finalize": aux_ms, "aux_launches": aux_n},
             "gpu_launches": launches,
             "clocks": clk.summary(),
             "e2e": {"value": upd_per_step * e2e_steps * world / e2e_s, "unit": UNIT,
@@ -409,6 +411,8 @@ def main():
                     help="also run a serving trace with this many jobs")
     ap.add_argument("--n-orb", type=int, default=0,
                     help="orbital count override (profiling on a smaller case); 0 = the workload's 64")
+    ap.add_argument("--sweep-path", type=int, default=0,
+                    help="stencil sweep variant: 0 warp-specialised TMA (default), 1 general, 2 lockstep TMA")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", "0"))

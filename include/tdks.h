@@ -199,9 +199,11 @@ int tdks_launch_count(tdks_sys sys, long long *count);
 int tdks_set_tile(tdks_sys sys, int tx, int ty, int zc);
 
 /* Stencil sweep implementation: 0 (default) streams the input planes with TMA bulk
- * tensor copies where that applies (finite boxes, 16x8 tiles), 1 always uses the general
- * sweep (loads through L1/L2; the only one for periodic cells).  Both compute the same
- * values (to the last bits of FP64 rounding). */
+ * tensor copies where that applies (finite boxes, 16x8 tiles) into a warp-specialised
+ * kernel (one producer warp, eight consumer warps); 1 always uses the general sweep (loads
+ * through L1/L2; the only one for periodic cells); 2 is the TMA sweep in which all warps of
+ * a CTA advance plane by plane together.  All compute the same values (to the last bits of
+ * FP64 rounding in the energy and current sums). */
 int tdks_set_sweep_path(tdks_sys sys, int path);
 
 /*

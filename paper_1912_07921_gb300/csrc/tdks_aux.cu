@@ -130,6 +130,58 @@ __global__ void __launch_bounds__(128) gather_finish_kernel(const GatherParams p
   gather_finish<P>(p, (int)(u % p.n_atoms), (int)(u / p.n_atoms), threadIdx.x % 16);
 }
 
+// Non-local term at every point inside a sphere (the scatter half of V_nl):
+//   nl(r) = sum over the point's entries (a, j) of beta_aj(r) e^{-i phi} q_aj,
+//   phi = k . T + A . d (Bloch cells / velocity gauge), q_aj = D_aj h^3 <beta_aj|in>,
+// summed in entry order from zero and stored at row r0 (the point's first entry) of
+// nl[kb]; the sweeps add it to H in at the point.  Thread = (sphere point, v).
+template <int P, int BLOCH>
+__device__ __forceinline__ void nl_body(const GatherParams &p, long t, int kb) {
+  typedef VT<P> T;
+  typedef typename T::V V;
+  const long sidx = t / OVC;
+  const int v = (int)(t % OVC);
+  if (sidx >= p.n_sp) return;
+  const int2 r = p.sp[sidx];
+  const int kidx = kb / p.n_batches;
+  const bool phase = BLOCH || (p.A[0] != 0.0 || p.A[1] != 0.0 || p.A[2] != 0.0);
+  V acc = T::zero();
+  for (int e = r.x; e < r.y; e++) {
+    const ProjEntry &E = p.ent[p.rowent[e]];
+    const V *qa = reinterpret_cast<const V *>(p.q) + ((long)(kb * p.n_atoms + E.atom) * 4) * OVC + v;
+    V x;
+    if constexpr (P == P_C64) {
+      x = T::mul(T::coef(0.0, E.beta[0]), T::ld(qa));
+#pragma unroll
+      for (int j = 1; j < 4; j++) x = T::fma(T::coef(0.0, E.beta[j]), T::ld(qa + j * OVC), x);
+    } else {
+      x = T::mul(E.betad[0], T::ld(qa));
+#pragma unroll
+      for (int j = 1; j < 4; j++) x = T::fma(E.betad[j], T::ld(qa + j * OVC), x);
+    }
+    if (phase) {
+      double ang = p.A[0] * E.d[0] + p.A[1] * E.d[1] + p.A[2] * E.d[2];
+      if (BLOCH) ang += p.kvec[3 * kidx] * E.T[0] + p.kvec[3 * kidx + 1] * E.T[1] + p.kvec[3 * kidx + 2] * E.T[2];
+      if constexpr (P == P_C64) {
+        float sn, cs;
+        sincosf((float)ang, &sn, &cs);
+        x = T::cmul(pk2(cs, cs), pk2(-sn, -sn), x);
+      } else {
+        double sn, cs;
+        sincos(ang, &sn, &cs);
+        x = T::cmul(cs, -sn, x);
+      }
+    }
+    acc = T::add(acc, x);
+  }
+  reinterpret_cast<V *>(p.nl)[((long)kb * (p.n_ent + 1) + r.x) * OVC + v] = acc;
+}
+
+template <int P, int BLOCH>
+__global__ void __launch_bounds__(NL_THREADS) nl_kernel(const GatherParams p) {
+  nl_body<P, BLOCH>(p, (long)blockIdx.x * NL_THREADS + threadIdx.x, blockIdx.y);
+}
+
 // index of the system that owns unit u: begin[s] <= u < begin[s+1]
 __device__ __forceinline__ int find_sys(const long *begin, int n, long u) {
   int lo = 0, hi = n - 1;
@@ -163,16 +215,31 @@ gather_finish_batch_kernel(const GatherParams *gp, const long *ubegin, int n_sys
   gather_finish<P>(p, (int)(local % p.n_atoms), (int)(local / p.n_atoms), threadIdx.x % 16);
 }
 
-cudaError_t launch_gather_batch(int prec, const GatherParams *gp, const long *begin, const long *ubegin, int n_sys,
-                                long total, long total_units, cudaStream_t s) {
+// CTA c of the batched non-local kernel: system s with nbegin[s] <= c < nbegin[s+1]; within
+// it, kb = local / chunks, chunk = local % chunks.
+template <int P>
+__global__ void __launch_bounds__(NL_THREADS)
+nl_batch_kernel(const GatherParams *gp, const long *nbegin, int n_sys) {
+  const int s = find_sys(nbegin, n_sys, blockIdx.x);
+  const GatherParams &p = gp[s];
+  const long local = blockIdx.x - nbegin[s];
+  const long chunks = ((long)p.n_sp * OVC + NL_THREADS - 1) / NL_THREADS;
+  nl_body<P, 0>(p, (local % chunks) * NL_THREADS + threadIdx.x, (int)(local / chunks));
+}
+
+cudaError_t launch_gather_batch(int prec, const GatherParams *gp, const long *begin, const long *ubegin,
+                                const long *nbegin, int n_sys, long total, long total_units, long total_nl,
+                                cudaStream_t s) {
   if (total <= 0) return cudaSuccess;
   const unsigned fgrid = (unsigned)((total_units + 7) / 8);
   if (prec == P_C64) {
     gather_batch_kernel<P_C64><<<(unsigned)total, GATHER_THREADS, 0, s>>>(gp, begin, n_sys);
     gather_finish_batch_kernel<P_C64><<<fgrid, 128, 0, s>>>(gp, ubegin, n_sys, total_units);
+    if (total_nl > 0) nl_batch_kernel<P_C64><<<(unsigned)total_nl, NL_THREADS, 0, s>>>(gp, nbegin, n_sys);
   } else {
     gather_batch_kernel<P_C128><<<(unsigned)total, GATHER_THREADS, 0, s>>>(gp, begin, n_sys);
     gather_finish_batch_kernel<P_C128><<<fgrid, 128, 0, s>>>(gp, ubegin, n_sys, total_units);
+    if (total_nl > 0) nl_batch_kernel<P_C128><<<(unsigned)total_nl, NL_THREADS, 0, s>>>(gp, nbegin, n_sys);
   }
   return cudaGetLastError();
 }
@@ -181,14 +248,19 @@ cudaError_t launch_gather(int prec, int bloch, const GatherParams &p, cudaStream
   if (p.n_atoms <= 0) return cudaSuccess;
   dim3 grid(p.n_atoms * p.n_chunks, p.n_kb);
   const unsigned fgrid = (unsigned)(((long)p.n_atoms * p.n_kb + 7) / 8);
+  const dim3 ngrid((unsigned)(((long)p.n_sp * OVC + NL_THREADS - 1) / NL_THREADS), (unsigned)p.n_kb);
   if (prec == P_C64) {
     if (bloch) gather_kernel<P_C64, 1><<<grid, GATHER_THREADS, 0, s>>>(p);
     else gather_kernel<P_C64, 0><<<grid, GATHER_THREADS, 0, s>>>(p);
     gather_finish_kernel<P_C64><<<fgrid, 128, 0, s>>>(p);
+    if (p.n_sp > 0 && bloch) nl_kernel<P_C64, 1><<<ngrid, NL_THREADS, 0, s>>>(p);
+    else if (p.n_sp > 0) nl_kernel<P_C64, 0><<<ngrid, NL_THREADS, 0, s>>>(p);
   } else {
     if (bloch) gather_kernel<P_C128, 1><<<grid, GATHER_THREADS, 0, s>>>(p);
     else gather_kernel<P_C128, 0><<<grid, GATHER_THREADS, 0, s>>>(p);
     gather_finish_kernel<P_C128><<<fgrid, 128, 0, s>>>(p);
+    if (p.n_sp > 0 && bloch) nl_kernel<P_C128, 1><<<ngrid, NL_THREADS, 0, s>>>(p);
+    else if (p.n_sp > 0) nl_kernel<P_C128, 0><<<ngrid, NL_THREADS, 0, s>>>(p);
   }
   return cudaGetLastError();
 }

@@ -26,9 +26,10 @@ struct tdks_batch {
   GatherParams *d_gather[4] = {nullptr, nullptr, nullptr, nullptr};
   SweepMaps *d_maps = nullptr;                                      // 4 per system
   long *d_item_begin = nullptr, *d_gather_begin = nullptr, *d_unit_begin = nullptr, *d_lda_begin = nullptr;
+  long *d_nl_begin = nullptr;
   BatchAux *d_aux = nullptr;
   BatchClock *d_clock = nullptr;
-  long total_items = 0, total_gather = 0, total_units = 0, total_lda = 0;
+  long total_items = 0, total_gather = 0, total_units = 0, total_lda = 0, total_nl = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   long long launches = 0;
@@ -39,6 +40,7 @@ namespace {
 void batch_free(tdks_batch *b) {
   for (int k = 0; k < 4; k++) { cudaFree(b->d_sweep[k]); cudaFree(b->d_gather[k]); }
   cudaFree(b->d_maps); cudaFree(b->d_item_begin); cudaFree(b->d_gather_begin); cudaFree(b->d_lda_begin);
+  cudaFree(b->d_nl_begin);
   cudaFree(b->d_unit_begin);
   cudaFree(b->d_aux); cudaFree(b->d_clock);
   if (b->exec) cudaGraphExecDestroy(b->exec);
@@ -48,14 +50,22 @@ void batch_free(tdks_batch *b) {
   if (b->work) cudaStreamDestroy(b->work);
 }
 
-// Enqueue one sub-step of every system of the batch (11 launches).
+// Kernels one sub-step launches: the LDA/V_eff kernel, per Taylor term the projector step
+// (gather stages 1 and 2 and the non-local term, where any system has atoms) and the sweep,
+// and the record and clock kernels.
+long long substep_launches(const tdks_batch *b) {
+  const int proj = b->total_gather > 0 ? 2 + (b->total_nl > 0 ? 1 : 0) : 0;
+  return 1 + 4 * (proj + 1) + 2;
+}
+
+// Enqueue one sub-step of every system of the batch.
 int enqueue_substep(tdks_batch *b) {
   const int n = (int)b->sys.size();
   cudaError_t e = launch_lda_batch(b->prec, b->d_aux, b->d_clock, b->d_lda_begin, n, b->total_lda, b->work);
   if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("batched lda: ") + cudaGetErrorString(e));
   for (int k = 0; k < 4; k++) {
-    e = launch_gather_batch(b->prec, b->d_gather[k], b->d_gather_begin, b->d_unit_begin, n, b->total_gather,
-                            b->total_units, b->work);
+    e = launch_gather_batch(b->prec, b->d_gather[k], b->d_gather_begin, b->d_unit_begin, b->d_nl_begin, n,
+                            b->total_gather, b->total_units, b->total_nl, b->work);
     if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("batched gather: ") + cudaGetErrorString(e));
     BatchSweepArgs a{b->d_sweep[k], b->d_maps, k, b->d_item_begin, n, b->total_items};
     const int mode = k == 0 ? MODE_FIRST : (k == 3 ? MODE_LAST : MODE_MID);
@@ -68,7 +78,7 @@ int enqueue_substep(tdks_batch *b) {
   }
   e = launch_batch_tail(b->d_aux, b->d_clock, n, 1, b->work);
   if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("batched clocks: ") + cudaGetErrorString(e));
-  b->launches += 11;
+  b->launches += substep_launches(b);
   return TDKS_OK;
 }
 
@@ -126,6 +136,7 @@ int tdks_batch_create(const tdks_sys *systems, int n, void *stream, tdks_batch_t
   std::vector<GatherParams> gp[4];
   std::vector<SweepMaps> maps(4 * n);
   std::vector<long> item_begin(n + 1, 0), gather_begin(n + 1, 0), unit_begin(n + 1, 0), lda_begin(n + 1, 0);
+  std::vector<long> nl_begin(n + 1, 0);
   std::vector<BatchAux> aux(n);
   std::vector<BatchClock> clk(n);
   for (int i = 0; i < n; i++) {
@@ -137,14 +148,13 @@ int tdks_batch_create(const tdks_sys *systems, int n, void *stream, tdks_batch_t
     const double A0[3] = {0.0, 0.0, 0.0};
     const double dts = s->clock_dt / s->clock_substeps;
     for (int k = 0; k < 4; k++) {
-      if (!encode_sweep_maps(s, ins[k], modes[k], &maps[4 * i + k])) {
+      if (!encode_sweep_maps(s, ins[k], modes[k], &maps[4 * i + k], false)) {
         s->tx = save_tx; s->ty = save_ty; s->zc = save_zc;
         return bad("tensor map encoding failed");
       }
       SweepParams p{};
       sweep_common(s, p, A0);
-      p.cr = 0.0;
-      p.ci = -dts / (k + 1);
+      set_coef(p, 0.0, -dts / (k + 1));
       p.in = ins[k];
       p.do_obs = k == 0;
       p.err = s->d_err;
@@ -156,11 +166,13 @@ int tdks_batch_create(const tdks_sys *systems, int n, void *stream, tdks_batch_t
       g.in = ins[k]; g.atom_begin = s->d_atom_begin; g.ent = s->d_ent; g.D = s->d_D;
       g.h3 = s->h * s->h * s->h; g.kvec = s->d_kvec; g.q = s->d_q;
       g.n_chunks = s->gchunks; g.qpart = s->d_qpart;
+      g.sp = s->d_sp; g.n_sp = s->n_sp; g.rowent = s->d_rowent; g.n_ent = s->n_ent; g.nl = s->d_nl;
       gp[k].push_back(g);
     }
     item_begin[i + 1] = item_begin[i] + sp[0].back().n_items;
     gather_begin[i + 1] = gather_begin[i] + (long)s->n_atoms * s->n_kb * (s->n_atoms > 0 ? s->gchunks : 0);
     unit_begin[i + 1] = unit_begin[i] + (long)s->n_atoms * s->n_kb;
+    nl_begin[i + 1] = nl_begin[i] + (s->n_atoms > 0 ? nl_blocks(s->n_sp, s->n_kb) : 0);
     const int nl = lda_blocks(s->N);
     lda_begin[i + 1] = lda_begin[i] + nl;
     BatchAux &a = aux[i];
@@ -177,6 +189,7 @@ int tdks_batch_create(const tdks_sys *systems, int n, void *stream, tdks_batch_t
   b->total_gather = gather_begin[n];
   b->total_units = unit_begin[n];
   b->total_lda = lda_begin[n];
+  b->total_nl = nl_begin[n];
   int rc = TDKS_OK;
   for (int k = 0; k < 4 && !rc; k++) {
     if (!rc) rc = upload(&b->d_sweep[k], sp[k]);
@@ -187,6 +200,7 @@ int tdks_batch_create(const tdks_sys *systems, int n, void *stream, tdks_batch_t
   if (!rc) rc = upload(&b->d_gather_begin, gather_begin);
   if (!rc) rc = upload(&b->d_unit_begin, unit_begin);
   if (!rc) rc = upload(&b->d_lda_begin, lda_begin);
+  if (!rc) rc = upload(&b->d_nl_begin, nl_begin);
   if (!rc) rc = upload(&b->d_aux, aux);
   if (!rc) rc = upload(&b->d_clock, clk);
   if (!rc && (cudaStreamCreateWithFlags(&b->work, cudaStreamNonBlocking) != cudaSuccess ||
@@ -236,13 +250,13 @@ int tdks_batch_propagate(tdks_batch_t b, int n_steps, int use_graph) {
     if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("graph capture: ") + cudaGetErrorString(e));
     b->graph = g;
     CU(cudaGraphInstantiate(&b->exec, b->graph, 0));
-    b->launches -= 11;
+    b->launches -= substep_launches(b);
   }
   const long long subs = (long long)n_steps * b->substeps;
   for (long long i = 0; i < subs; i++) {
     if (use_graph) {
       CU(cudaGraphLaunch(b->exec, b->work));
-      b->launches += 11;
+      b->launches += substep_launches(b);
     } else if (int rc = enqueue_substep(b)) {
       return rc;
     }

@@ -165,12 +165,12 @@ void sweep_common(const tdks_system *s, SweepParams &p, const double A[3]) {
     p.w[m] = -0.5 * c[m] / (s->h * s->h);
     p.gw[m] = d[m] / s->h;
   }
+  for (int m = 0; m <= MAXM; m++) p.wf[m] = (float)p.w[m];
+  set_coef(p, 1.0, 0.0);
   p.aux = s->aux;
   p.has_proj = s->n_atoms > 0;
-  p.rowent = s->d_rowent;
-  p.ent = s->d_ent;
-  p.q = s->d_q;
-  p.n_atoms = s->n_atoms;
+  p.nl = s->d_nl;
+  p.n_ent = s->n_ent;
   p.kvec = s->d_kvec;
   p.L[0] = s->nx * s->h; p.L[1] = s->ny * s->h; p.L[2] = s->nz * s->h;
   for (int a = 0; a < 3; a++) p.A[a] = A[a];
@@ -184,13 +184,13 @@ void sweep_common(const tdks_system *s, SweepParams &p, const double A[3]) {
 }
 
 // Tensor map over a packed array for the TMA sweep of `mode` (box depth = planes per copy).
-bool encode_map(const tdks_system *s, const void *ptr, int mode, CUtensorMap *out) {
+bool encode_map(const tdks_system *s, const void *ptr, int mode, CUtensorMap *out, bool lockstep) {
   EncodeTiledFn fn = encode_fn();
   if (!fn || (reinterpret_cast<uintptr_t>(ptr) & 15) != 0) return false;
   const cuuint64_t dims[5] = {16, (cuuint64_t)s->nx, (cuuint64_t)s->ny, (cuuint64_t)s->nz, (cuuint64_t)s->n_kb};
   const cuuint64_t strides[4] = {64, 64ull * s->nx, 64ull * s->nx * s->ny, 64ull * (cuuint64_t)s->N};
   const cuuint32_t box[5] = {16, (cuuint32_t)(s->tx + 2 * s->M), (cuuint32_t)(s->ty + 2 * s->M),
-                             (cuuint32_t)tma_planes(s->prec, mode), 1};
+                             (cuuint32_t)tma_planes(s->prec, mode, lockstep), 1};
   const cuuint32_t es[5] = {1, 1, 1, 1, 1};
   return fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<void *>(ptr), dims, strides, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -198,12 +198,12 @@ bool encode_map(const tdks_system *s, const void *ptr, int mode, CUtensorMap *ou
 }
 
 // Map over the per-point records, tile box of the mode's depth.
-bool encode_aux_map(const tdks_system *s, int mode, CUtensorMap *out) {
+bool encode_aux_map(const tdks_system *s, int mode, CUtensorMap *out, bool lockstep) {
   EncodeTiledFn fn = encode_fn();
   if (!fn || (reinterpret_cast<uintptr_t>(s->aux) & 15) != 0) return false;
   const cuuint64_t dims[4] = {4, (cuuint64_t)s->nx, (cuuint64_t)s->ny, (cuuint64_t)s->nz};
   const cuuint64_t strides[3] = {16, 16ull * s->nx, 16ull * s->nx * s->ny};
-  const cuuint32_t box[4] = {4, (cuuint32_t)s->tx, (cuuint32_t)s->ty, (cuuint32_t)tma_planes(s->prec, mode)};
+  const cuuint32_t box[4] = {4, (cuuint32_t)s->tx, (cuuint32_t)s->ty, (cuuint32_t)tma_planes(s->prec, mode, lockstep)};
   const cuuint32_t es[4] = {1, 1, 1, 1};
   return fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, s->aux, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -223,9 +223,9 @@ bool encode_op_map(const tdks_system *s, const void *ptr, CUtensorMap *out, int 
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-bool encode_sweep_maps(const tdks_system *s, const void *in, int mode, SweepMaps *out) {
-  if (!encode_map(s, in, mode, &out->in) || !encode_aux_map(s, mode, &out->aux) ||
-      !encode_op_map(s, in, &out->ctr, tma_planes(s->prec, mode)))
+bool encode_sweep_maps(const tdks_system *s, const void *in, int mode, SweepMaps *out, bool lockstep) {
+  if (!encode_map(s, in, mode, &out->in, lockstep) || !encode_aux_map(s, mode, &out->aux, lockstep) ||
+      !encode_op_map(s, in, &out->ctr, tma_planes(s->prec, mode, lockstep)))
     return false;
   if (mode == MODE_LAST) {
     const void *ops[4] = {s->psi, s->psi_lo ? s->psi_lo : s->psi, s->term[0], s->term[1]};
@@ -243,7 +243,7 @@ void build_tmaps(tdks_system *s) {
   const void *ins[4] = {s->psi, s->term[0], s->term[1], s->term[2]};
   const int modes[4] = {MODE_FIRST, MODE_MID, MODE_MID, MODE_LAST};
   for (int i = 0; i < 4; i++)
-    if (!encode_sweep_maps(s, ins[i], modes[i], &s->smaps[i])) return;
+    if (!encode_sweep_maps(s, ins[i], modes[i], &s->smaps[i], s->path == 2)) return;
   s->tmaps_ok = true;
 }
 
@@ -252,8 +252,8 @@ int run_sweep(tdks_system *s, int mode, SweepParams &p, const SweepMaps *tm) {
   Timed tmr(s, 0);
   p.err = s->d_err;
   cudaError_t e;
-  if (tm && s->path == 0 && s->bc == TDKS_BC_ZERO && tma_supported(s->M, s->tx, s->ty))
-    e = launch_sweep_tma(s->M, s->prec, mode, s->tx, s->ty, *tm, p, 0, s->stream);
+  if (tm && s->path != 1 && s->bc == TDKS_BC_ZERO && tma_supported(s->M, s->tx, s->ty))
+    e = launch_sweep_tma(s->M, s->prec, mode, s->tx, s->ty, *tm, p, 0, s->stream, s->path == 2);
   else
     e = launch_sweep(s->M, s->prec, mode, s->bc == TDKS_BC_BLOCH, s->tx, s->ty, p, 0, s->stream);
   s->launches++;
@@ -273,9 +273,12 @@ int run_gather(tdks_system *s, const void *in, const double A[3]) {
   g.q = s->d_q;
   g.n_chunks = s->gchunks;
   g.qpart = s->d_qpart;
+  g.sp = s->d_sp; g.n_sp = s->n_sp;
+  g.rowent = s->d_rowent; g.n_ent = s->n_ent;
+  g.nl = s->d_nl;
   Timed tm(s, 1);
   cudaError_t e = launch_gather(s->prec, s->bc == TDKS_BC_BLOCH, g, s->stream);
-  s->launches++;
+  s->launches += s->n_sp > 0 ? 3 : 2;  // gather stages 1 and 2, the non-local term
   if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("projector gather: ") + cudaGetErrorString(e));
   return TDKS_OK;
 }
@@ -327,7 +330,7 @@ int first_sweep(tdks_system *s, double cr, double ci, const double A[3], bool ob
   if (rc) return rc;
   SweepParams p{};
   sweep_common(s, p, A);
-  p.cr = cr; p.ci = ci;
+  set_coef(p, cr, ci);
   p.in = s->psi;
   p.out = s->term[0];
   p.do_obs = obs ? 1 : 0;
@@ -365,7 +368,10 @@ double kinetic_max(const tdks_system *s) {
 void free_proj(tdks_system *s) {
   cudaFree(s->d_rowent); cudaFree(s->d_atom_begin);
   cudaFree(s->d_ent); cudaFree(s->d_q); cudaFree(s->d_D); cudaFree(s->d_qpart);
+  cudaFree(s->d_sp); cudaFree(s->d_nl);
   s->d_rowent = s->d_atom_begin = nullptr;
+  s->d_sp = nullptr; s->d_nl = nullptr;
+  s->n_sp = s->n_ent = 0;
   if (s->aux) cudaMemsetAsync(s->aux, 0, s->N * sizeof(PointAux), s->stream);  // no entries anywhere
   s->d_ent = nullptr; s->d_q = nullptr; s->d_D = nullptr; s->d_qpart = nullptr;
   s->n_atoms = 0;
@@ -605,8 +611,20 @@ int tdks_set_atoms_projectors(tdks_sys s, int n_atoms, const double *pos, const 
   {
     // per-point entry ranges (V_eff is rewritten by the LDA kernel before every sweep)
     std::vector<PointAux> aux(s->N);
-    for (long i = 0; i < s->N; i++) aux[i] = PointAux{0.0, rowptr[i], rowptr[i + 1]};
+    std::vector<int2> sp;
+    for (long i = 0; i < s->N; i++) {
+      aux[i] = PointAux{0.0, rowptr[i], rowptr[i + 1]};
+      if (rowptr[i + 1] > rowptr[i]) sp.push_back(make_int2(rowptr[i], rowptr[i + 1]));
+    }
     CU(cudaMemcpy(s->aux, aux.data(), s->N * sizeof(PointAux), cudaMemcpyHostToDevice));
+    s->n_sp = (int)sp.size();
+    s->n_ent = (int)ent.size();
+    CU(cudaMalloc((void **)&s->d_sp, sp.size() * sizeof(int2)));
+    CU(cudaMemcpy(s->d_sp, sp.data(), sp.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    // one 16-byte vector per (kb, entry row, v) plus a zero row per kb
+    const size_t nl_bytes = (size_t)s->n_kb * (s->n_ent + 1) * OVC * 16;
+    CU(cudaMalloc(&s->d_nl, nl_bytes));
+    CU(cudaMemset(s->d_nl, 0, nl_bytes));
   }
   CU(cudaMemcpy(s->d_rowent, rowent.data(), ent.size() * sizeof(int), cudaMemcpyHostToDevice));
   CU(cudaMemcpy(s->d_atom_begin, atom_begin.data(), (n_atoms + 1) * sizeof(int), cudaMemcpyHostToDevice));
@@ -671,8 +689,10 @@ int tdks_set_tile(tdks_sys s, int tx, int ty, int zc) {
 
 int tdks_set_sweep_path(tdks_sys s, int path) {
   if (!s) return fail(TDKS_EINVAL, "NULL system");
-  if (path != 0 && path != 1) return fail(TDKS_EINVAL, "path must be 0 (TMA where possible) or 1 (general)");
+  if (path < 0 || path > 2)
+    return fail(TDKS_EINVAL, "path must be 0 (TMA where possible), 1 (general) or 2 (TMA, lockstep warps)");
   s->path = path;
+  build_tmaps(s);  // the box depth of the maps depends on the kernel variant
   return TDKS_OK;
 }
 
@@ -690,12 +710,12 @@ int tdks_apply_H(tdks_sys s, double t, const void *dev_in, void *dev_out) {
   if ((rc = run_gather(s, dev_in, A))) return rc;
   SweepParams p{};
   sweep_common(s, p, A);
-  p.cr = 1.0; p.ci = 0.0;
+  set_coef(p, 1.0, 0.0);
   p.in = dev_in;
   p.out = dev_out;
   SweepMaps tm;
   const bool have_tm = s->bc == TDKS_BC_ZERO && tma_supported(s->M, s->tx, s->ty) &&
-                       encode_sweep_maps(s, dev_in, MODE_MID, &tm);
+                       encode_sweep_maps(s, dev_in, MODE_MID, &tm, s->path == 2);
   return run_sweep(s, MODE_MID, p, have_tm ? &tm : nullptr);
 }
 
@@ -734,7 +754,7 @@ int tdks_propagate_n(tdks_sys s, double t0, double dt, int n_steps, int substeps
         if ((rc = run_gather(s, in, A))) return rc;
         SweepParams p{};
         sweep_common(s, p, A);
-        p.cr = 0.0; p.ci = -dts / k;
+        set_coef(p, 0.0, -dts / k);
         p.in = in;
         if (k < 4) {
           p.out = s->term[k - 1];

@@ -54,6 +54,8 @@ struct SweepParams {
   double w[MAXM + 1];         // w[0] = -3 c_0 / (2 h^2), w[m] = -c_m / (2 h^2)
   double gw[MAXM + 1];        // gradient weights d_m / h
   double cr, ci;              // out = (cr + i ci) * (H in)
+  float wf[MAXM + 1];         // w rounded to FP32 (complex64 sweeps)
+  float crf, cif;             // cr, ci rounded to FP32
   const void *in;             // stencil input (psi storage in MODE_FIRST, term storage else)
   void *out;                  // term output (MODE_FIRST / MODE_MID)
   void *psi;                  // MODE_LAST: state (complex128, or the hi part of a complex64
@@ -61,12 +63,11 @@ struct SweepParams {
   void *psi_lo;               // MODE_LAST, complex64 systems: lo part of the state
   const void *t1, *t2;        // MODE_LAST: earlier terms
   const PointAux *aux;        // [N] V_eff and projector entry ranges
-  // projectors (scatter side)
+  // projectors
   int has_proj;               // the system has projector entries
-  const int *rowent;          // entry indices (point-major)
-  const ProjEntry *ent;
-  const void *q;              // [kb][atom][4][OVC] vectors: D_aj h^3 <beta_aj|in>
-  int n_atoms;
+  const void *nl;             // [kb][n_ent + 1][OVC] vectors: sum_aj beta_aj(r) phase q_aj at the
+                              // sphere point whose entries start at r0; row n_ent is zero
+  int n_ent;                  // projector entries
   // Bloch boundary
   const double *kvec;         // [n_k][3]
   double L[3];
@@ -79,6 +80,14 @@ struct SweepParams {
   double *dens_part;          // [n_kb][N] (MODE_LAST)
   int *err;                   // device error word (bounded waits that ran out set it)
 };
+
+// Sets the Taylor coefficient (cr + i ci) with its FP32 copies.
+inline void set_coef(SweepParams &p, double cr, double ci) {
+  p.cr = cr;
+  p.ci = ci;
+  p.crf = (float)cr;
+  p.cif = (float)ci;
+}
 
 struct GatherParams {
   int n_kb, n_batches, n_atoms;
@@ -93,6 +102,12 @@ struct GatherParams {
   void *q;                    // [kb][atom][4][OVC] vectors
   int n_chunks;               // CTAs per (atom, kb): each sums a contiguous share of the sphere
   double2 *qpart;             // [kb][atom][chunk][4][OVC][2] partial sums (FP64)
+  // scatter side: the non-local term at every sphere point
+  const int2 *sp;             // [n_sp] entry range [r0, r1) of each point inside a sphere
+  int n_sp;
+  const int *rowent;          // entry indices, point-major
+  int n_ent;
+  void *nl;                   // [kb][n_ent + 1][OVC] vectors, row r0 of each sphere point
 };
 
 // Per-system data of a batch (device copies), for the batched LDA and finalise kernels.
@@ -146,7 +161,9 @@ cudaError_t launch_sweep(int M, int prec, int mode, int bloch, int tx, int ty,
 int sweep_threads(int tx, int ty);
 size_t sweep_smem(int M, int tx, int ty);
 
-// Launchers (tdks_aux.cu)
+// Launchers (tdks_aux.cu).  The projector step is three kernels: the gather-dot (stages 1
+// and 2) and the non-local term at every sphere point (skipped when no point is in a sphere).
+constexpr int NL_THREADS = 256;
 cudaError_t launch_gather(int prec, int bloch, const GatherParams &p, cudaStream_t s);
 // chunks per (atom, k-batch) that fill the GPU for n_atoms * n_kb units
 int gather_chunks(long units);
@@ -166,16 +183,22 @@ cudaError_t launch_pack(int prec, int to_internal, long N, int n_k, int n_orb, i
 // TMA sweep for finite boxes (tdks_sweep_tma.cu).  maps.in: dims {16 floats, nx, ny, nz,
 // n_kb}, box {16, TX+2M, TY+2M, tma_planes(prec, mode), 1}; maps.aux: dims {4, nx, ny, nz}
 // (4-byte words), box {4, TX, TY, tma_planes}; maps.op[i]: dims as maps.in, box
-// {16, TX, TY, 1, 1}.
+// {16, TX, TY, 1, 1}; maps.ctr: as maps.op with tma_planes planes.  Default: the
+// warp-specialised kernel (a producer warp and eight consumer warps); lockstep: the variant
+// in which all warps of a CTA advance plane by plane together.
 cudaError_t launch_sweep_tma(int M, int prec, int mode, int tx, int ty, const SweepMaps &maps,
-                             const SweepParams &p, int grid, cudaStream_t s);
+                             const SweepParams &p, int grid, cudaStream_t s, bool lockstep = false);
 bool tma_supported(int M, int tx, int ty);
-int tma_planes(int prec, int mode);
+int tma_planes(int prec, int mode, bool lockstep = false);
 int lda_blocks(long N);
 cudaError_t launch_sweep_tma_batch(int M, int prec, int mode, const BatchSweepArgs &a, cudaStream_t s);
-// begin: prefix sums of n_atoms * n_kb * n_chunks (stage 1 CTAs); ubegin: of n_atoms * n_kb
-cudaError_t launch_gather_batch(int prec, const GatherParams *gp, const long *begin, const long *ubegin, int n_sys,
-                                long total, long total_units, cudaStream_t s);
+// begin: prefix sums of n_atoms * n_kb * n_chunks (stage 1 CTAs); ubegin: of n_atoms * n_kb;
+// nbegin: of the non-local kernel's CTAs, n_kb * ceil(n_sp * OVC / NL_THREADS)
+cudaError_t launch_gather_batch(int prec, const GatherParams *gp, const long *begin, const long *ubegin,
+                                const long *nbegin, int n_sys, long total, long total_units, long total_nl,
+                                cudaStream_t s);
+// CTAs of the non-local kernel of one system
+inline long nl_blocks(int n_sp, int n_kb) { return (long)n_kb * (((long)n_sp * OVC + NL_THREADS - 1) / NL_THREADS); }
 cudaError_t launch_lda_batch(int prec, const BatchAux *aux, const BatchClock *clk, const long *begin, int n_sys,
                              long total, cudaStream_t s);
 // which = 0: observable records (first sub-step of a step); 1: advance the clocks

@@ -103,13 +103,13 @@ extern "C" int tdks_apply_H_noalloc(int nx, int ny, int nz, double h, int fd_ord
   const double A0[3] = {0.0, 0.0, 0.0};
   SweepParams p{};
   sweep_common(&s, p, A0);
-  p.cr = 1.0; p.ci = 0.0;
+  set_coef(p, 1.0, 0.0);
   p.in = dev_in;
   p.out = dev_out;
   p.err = err;
   SweepMaps tm;
   cudaError_t e;
-  if (tma_supported(M, s.tx, s.ty) && encode_sweep_maps(&s, dev_in, MODE_MID, &tm))
+  if (tma_supported(M, s.tx, s.ty) && encode_sweep_maps(&s, dev_in, MODE_MID, &tm, false))
     e = launch_sweep_tma(M, prec, MODE_MID, s.tx, s.ty, tm, p, 0, st);
   else
     e = launch_sweep(M, prec, MODE_MID, 0, s.tx, s.ty, p, 0, st);

@@ -60,9 +60,9 @@ sweep_kernel(const SweepParams p) {
 
   S W[M + 1];
 #pragma unroll
-  for (int m = 0; m <= M; m++) W[m] = T::bc(p.w[m]);
-  const typename W0T<P>::type w0 = (typename W0T<P>::type)p.w[0];
-  const S CR = T::bc(p.cr), CI = T::bc(p.ci);
+  for (int m = 0; m <= M; m++) W[m] = T::coef(p.w[m], p.wf[m]);
+  const typename W0T<P>::type w0 = P == P_C64 ? (typename W0T<P>::type)p.wf[0] : (typename W0T<P>::type)p.w[0];
+  const S CR = T::coef(p.cr, p.crf), CI = T::coef(p.ci, p.cif);
   const bool need_grad = BLOCH && (p.grad_mask != 0);
   const bool grads = BLOCH && MODE == MODE_FIRST && (p.grad_mask & 8);
 
@@ -73,6 +73,7 @@ sweep_kernel(const SweepParams p) {
     const int kb = (int)(it % p.n_kb); it /= p.n_kb;
     const int zc = (int)it;
     const int kidx = kb / p.n_batches;
+    const V *nlk = nl_column<P>(p, kb, v);
     const int z0 = zc * p.zc;
     const int z1 = min(z0 + p.zc, nz);
     const long kbN = (long)kb * N;
@@ -167,7 +168,7 @@ sweep_kernel(const SweepParams p) {
       __syncthreads();
       V gax[3] = {T::zero(), T::zero(), T::zero()};
       V acc = stencil_point<M, P, BLOCH>(p, W, w0, Q, sm + buf * PLANE, csl, SX * OVC, ve, need_grad, grads, gax);
-      if (own && r1 > r0) acc = kb_scatter<P, BLOCH>(p, kb, kidx, v, r0, r1, acc);
+      if (own && r1 > r0) acc = T::add(acc, T::ld(nlk + (long)r0 * OVC));
       if (MODE == MODE_FIRST && p.do_obs && own) {
         oa.add_e(Q[M], acc);
         if (grads) {

@@ -5,7 +5,8 @@
 //
 // H t(r) = (w0 + V_eff(r)) t(r) + sum_m w_m [sum of the 6 neighbours at distance m]
 //          [- i A . grad_h t(r)]  (velocity gauge, periodic cells)
-//          + sum_(a,j) beta_aj(r) phase* q_aj    (Kleinman-Bylander scatter)
+//          + sum_(a,j) beta_aj(r) phase* q_aj    (Kleinman-Bylander term, precomputed per
+//                                                 sphere point by the projector step)
 // with w0 = -3 c_0 / (2 h^2), w_m = -c_m / (2 h^2) (central FD weights c_m of order 2M).
 #pragma once
 #include "tdks_internal.cuh"
@@ -79,43 +80,16 @@ stencil_point(const SweepParams &p, const typename VT<P>::S *W, typename W0T<P>:
   return acc;
 }
 
-// Kleinman-Bylander scatter at one point: sum over the point's sphere entries.
-template <int P, int BLOCH>
-__device__ __forceinline__ typename VT<P>::V
-kb_scatter(const SweepParams &p, int kb, int kidx, int v, int r0, int r1, typename VT<P>::V acc) {
-  typedef VT<P> T;
-  typedef typename T::V V;
-  for (int e = r0; e < r1; e++) {
-    const ProjEntry &E = p.ent[__ldg(p.rowent + e)];
-    const V *qa = reinterpret_cast<const V *>(p.q) + ((long)(kb * p.n_atoms + E.atom) * 4) * OVC + v;
-    V nl;
-    if (P == P_C64) {
-      nl = T::mul(T::bc(E.beta[0]), T::ld(qa));
-#pragma unroll
-      for (int j = 1; j < 4; j++) nl = T::fma(T::bc(E.beta[j]), T::ld(qa + j * OVC), nl);
-    } else {
-      nl = T::mul(T::bc(E.betad[0]), T::ld(qa));
-#pragma unroll
-      for (int j = 1; j < 4; j++) nl = T::fma(T::bc(E.betad[j]), T::ld(qa + j * OVC), nl);
-    }
-    if (BLOCH || p.grad_mask) {
-      double ang = 0.0;
-      if (BLOCH)
-        ang += p.kvec[3 * kidx] * E.T[0] + p.kvec[3 * kidx + 1] * E.T[1] + p.kvec[3 * kidx + 2] * E.T[2];
-      ang += p.A[0] * E.d[0] + p.A[1] * E.d[1] + p.A[2] * E.d[2];
-      if constexpr (P == P_C64) {
-        float s, c;
-        sincosf((float)ang, &s, &c);
-        nl = T::cmul(pk2(c, c), pk2(-s, -s), nl);
-      } else {
-        double s, c;
-        sincos(ang, &s, &c);
-        nl = T::cmul(T::bc(c), T::bc(-s), nl);
-      }
-    }
-    acc = T::add(acc, nl);
-  }
-  return acc;
+// Non-local (Kleinman-Bylander) term of a point, precomputed per sphere point by the
+// projector step: nlk = the item's (kb, v) column of nl; row r0 for points with entries,
+// the zero row n_ent for the others (a branch-free load that can be issued early).
+template <int P>
+__device__ __forceinline__ typename VT<P>::V nl_term(const typename VT<P>::V *nlk, int n_ent, int r0, int r1) {
+  return VT<P>::ld(nlk + (long)(r1 > r0 ? r0 : n_ent) * OVC);
+}
+template <int P>
+__device__ __forceinline__ const typename VT<P>::V *nl_column(const SweepParams &p, int kb, int v) {
+  return reinterpret_cast<const typename VT<P>::V *>(p.nl) + (long)kb * (p.n_ent + 1) * OVC + v;
 }
 
 // Own-point operands of the last sweep (state parts and earlier terms).
@@ -132,28 +106,46 @@ __device__ __forceinline__ void load_last(const SweepParams &p, long idx, LastOp
   o.t2 = VT<P>::ld(reinterpret_cast<const V *>(p.t2) + idx);
 }
 
+// Per-item epilogue operands, read from the parameters once per work item (inside the
+// plane loop every asm memory clobber would make the compiler load them again).
+struct Epi {
+  void *out, *psi, *psi_lo;
+  double *dens_part;
+  double wocc;  // k-weight times occupation of the item's k-point
+};
+__device__ __forceinline__ Epi make_epi(const SweepParams &p, int kidx) {
+  return Epi{p.out, p.psi, p.psi_lo, p.dens_part, p.wocc[kidx]};
+}
+
 // Epilogue of one output vector.  idx = vector index ((kb*N + pt)*OVC + v); (CR, CI) = the
 // Taylor coefficient, converted to the compute precision once per work item.
 template <int P, int MODE>
-__device__ __forceinline__ void finish_point(const SweepParams &p, typename VT<P>::S CR, typename VT<P>::S CI,
-                                             bool own, long idx, int v, int kidx, typename VT<P>::V c0,
-                                             typename VT<P>::V acc, const LastOperands<P> &lo_ops) {
+__device__ __forceinline__ void finish_point(const Epi &ep, typename VT<P>::S CR, typename VT<P>::S CI, bool own,
+                                             long idx, int v, typename VT<P>::V c0, typename VT<P>::V acc,
+                                             const LastOperands<P> &lo_ops) {
   typedef VT<P> T;
   typedef typename T::V V;
   const V outv = T::cmul(CR, CI, acc);
   if (MODE != MODE_LAST) {
-    if (own) reinterpret_cast<V *>(p.out)[idx] = outv;
+    if (own) reinterpret_cast<V *>(ep.out)[idx] = outv;
   } else {
     V hi = lo_ops.hi, lo_out;
     typename Combine<P>::A dh, dl;
     Combine<P>::run(hi, lo_ops.lo, lo_ops.t1, lo_ops.t2, c0, outv, lo_out, dh, dl);
     if (own) {
-      reinterpret_cast<V *>(p.psi)[idx] = hi;
-      if (P == P_C64) reinterpret_cast<V *>(p.psi_lo)[idx] = lo_out;
+      reinterpret_cast<V *>(ep.psi)[idx] = hi;
+      if (P == P_C64) reinterpret_cast<V *>(ep.psi_lo)[idx] = lo_out;
     }
     Combine<P>::reduce4(dh, dl);
-    if (own && v == 0) p.dens_part[idx / OVC] = p.wocc[kidx] * Combine<P>::value(dh, dl);
+    if (own && v == 0) ep.dens_part[idx / OVC] = ep.wocc * Combine<P>::value(dh, dl);
   }
+}
+
+template <int P, int MODE>
+__device__ __forceinline__ void finish_point(const SweepParams &p, typename VT<P>::S CR, typename VT<P>::S CI,
+                                             bool own, long idx, int v, int kidx, typename VT<P>::V c0,
+                                             typename VT<P>::V acc, const LastOperands<P> &lo_ops) {
+  finish_point<P, MODE>(make_epi(p, kidx), CR, CI, own, idx, v, c0, acc, lo_ops);
 }
 
 // Block reduction of the observable partials of one work item into obs_part[item].

@@ -58,6 +58,30 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     if (clock64() - t0 > limit) return false;
   return true;
 }
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// Consumer wait: bounded, and gives up at once when another warp has given up.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *bar, uint32_t parity, const volatile int *abort) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort) return false;
+    if (clock64() - t0 > WAIT_LIMIT_CYCLES) return false;
+  }
+  return true;
+}
 __device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *tmap, uint64_t *bar, int c0, int c1,
                                             int c2, int c3, int c4) {
   asm volatile(
@@ -86,6 +110,19 @@ __device__ __forceinline__ void static_for(F &&f) {
     static_for<I + 1, N>(f);
   }
 }
+
+// Position in a ring of S slots: slot index and the parity of the slot's current use.
+struct RingPos {
+  int slot = 0;
+  uint32_t phase = 0;
+  template <int S>
+  __device__ __forceinline__ void next() {
+    if (++slot == S) {
+      slot = 0;
+      phase ^= 1u;
+    }
+  }
+};
 
 // Shared-memory plan: three TMA-fed rings, each slot completed by one mbarrier.
 //   centre ring (SC slots): U planes of the input tile (no halo), which feed the per-thread
@@ -304,6 +341,7 @@ __device__ __forceinline__ void tma_sweep_body(const Src &src) {
   }
 
   long gc = 0, gh = 0;  // centre / halo (and operand) loads consumed
+  RingPos rc, rh, ro;   // their ring positions
   for (long ii = 0; ii < n_my; ii++) {
     const long item = blockIdx.x + ii * gridDim.x;
     const SweepParams *pp;
@@ -322,12 +360,16 @@ __device__ __forceinline__ void tma_sweep_body(const Src &src) {
     const long plane_pts = (long)nx * ny;
     S_ W[M + 1];
 #pragma unroll
-    for (int m = 0; m <= M; m++) W[m] = T::bc(p.w[m]);
-    const typename W0T<P>::type w0 = (typename W0T<P>::type)p.w[0];
-    const S_ CR = T::bc(p.cr), CI = T::bc(p.ci);
+    for (int m = 0; m <= M; m++) W[m] = T::coef(p.w[m], p.wf[m]);
+    const typename W0T<P>::type w0 = P == P_C64 ? (typename W0T<P>::type)p.wf[0] : (typename W0T<P>::type)p.w[0];
+    const S_ CR = T::coef(p.cr, p.crf), CI = T::coef(p.ci, p.cif);
     int tx, ty, kb, z0, z1;
     item_geom(p, local, tx, ty, kb, z0, z1);
     const int kidx = kb / p.n_batches;
+    const Epi epi = make_epi(p, kidx);
+    const bool has_proj = p.has_proj != 0, do_obs = p.do_obs != 0;
+    const V *nlk = nl_column<P>(p, kb, v);
+    const int n_ent = p.n_ent;
     const int gx = tx * TX + lx, gy = ty * TY + ly;
     const bool own = gx < nx && gy < ny;
     const int nl = loads_of<M, U>(0, z0, z1);
@@ -344,24 +386,24 @@ __device__ __forceinline__ void tma_sweep_body(const Src &src) {
     // queue position of its first plane
     auto iteration = [&](auto rq) {
       constexpr int RQ = decltype(rq)::value;
-      const int cs = (int)(gc % SC);
-      if (!mbar_wait_bounded(&cfull[cs], (uint32_t)((gc / SC) & 1))) s_abort = 1;
+      const int cs = rc.slot;
+      if (!mbar_wait_bounded(&cfull[cs], rc.phase)) s_abort = 1;
       const V *cslot = reinterpret_cast<const V *>(cbase + (size_t)cs * G::CSLOT_BYTES);
 #pragma unroll
       for (int u = 0; u < U; u++) Q[(RQ + u) % QN] = cslot[u * G::CPLANE + csl];
       const bool out = l >= LP;
       if (out) {
         const int zf = z0 + U * (l - LP);
-        const int hs = (int)(gh % SH);
-        if (!mbar_wait_bounded(&hfull[hs], (uint32_t)((gh / SH) & 1))) s_abort = 1;
+        const int hs = rh.slot;
+        if (!mbar_wait_bounded(&hfull[hs], rh.phase)) s_abort = 1;
         const unsigned char *hslot = hbase + (size_t)hs * G::HSLOT_BYTES;
         const V *xs = reinterpret_cast<const V *>(hslot);
         const PointAux *ax = reinterpret_cast<const PointAux *>(hslot + G::IN_BYTES);
         LastOperands<P> lop;
         lop.hi = lop.lo = lop.t1 = lop.t2 = T::zero();
         if constexpr (OPS) {
-          const int os = (int)(gh % SO);
-          if (!mbar_wait_bounded(&ofull[os], (uint32_t)((gh / SO) & 1))) s_abort = 1;
+          const int os = ro.slot;
+          if (!mbar_wait_bounded(&ofull[os], ro.phase)) s_abort = 1;
           const V *ob = reinterpret_cast<const V *>(obase + (size_t)os * G::OP_BYTES);
           lop.hi = ob[csl];
           lop.lo = ob[G::CPLANE + csl];
@@ -373,14 +415,15 @@ __device__ __forceinline__ void tma_sweep_body(const Src &src) {
           constexpr int QB = (RQ + U + u) % QN;  // queue position of plane (zf + u) - M
           const PointAux a = ax[u * TX * TY + tsl];
           const R ve = *reinterpret_cast<const R *>(&a.veff);
+          const V nlv = has_proj ? nl_term<P>(nlk, n_ent, a.r0, a.r1) : T::zero();
           V gax[3];
           V acc = stencil_point<M, P, 0, QB, QN>(p, W, w0, Q, xs + u * G::PLANE, hsl, G::SX * OVC, ve, false,
                                                  false, gax);
           const bool live = own && (zf + u < z1);
-          if (live && p.has_proj && a.r1 > a.r0) acc = kb_scatter<P, 0>(p, kb, kidx, v, a.r0, a.r1, acc);
+          if (has_proj) acc = T::add(acc, nlv);
           const V c0 = Q[(QB + M) % QN];
-          if (MODE == MODE_FIRST && p.do_obs && live) oa.add_e(c0, acc);
-          finish_point<P, MODE>(p, CR, CI, live, idx + (long)u * plane_pts * OVC, v, kidx, c0, acc, lop);
+          if (MODE == MODE_FIRST && do_obs && live) oa.add_e(c0, acc);
+          finish_point<P, MODE>(epi, CR, CI, live, idx + (long)u * plane_pts * OVC, v, c0, acc, lop);
         });
         idx += U * plane_pts * OVC;
       }
@@ -398,7 +441,12 @@ __device__ __forceinline__ void tma_sweep_body(const Src &src) {
         }
       }
       gc++;
-      if (out) gh++;
+      rc.next<SC>();
+      if (out) {
+        gh++;
+        rh.next<SH>();
+        if (OPS) ro.next<SO>();
+      }
       l++;
     };
     int rq = 0;
@@ -444,16 +492,344 @@ tma_sweep_batch_kernel(const __grid_constant__ BatchSweepArgs a) {
   tma_sweep_body<M, P, MODE, TX, TY, U, true>(src);
 }
 
-// Planes per TMA copy of a sweep mode (the z depth of its tensor-map boxes): complex64
-// term sweeps take two planes per iteration, everything else one.
-int tma_planes(int prec, int mode) { return (prec == P_C64 && mode != MODE_LAST) ? 2 : 1; }
+// ---------------------------------------------------------------------------------------
+// Warp-specialised variant: one producer warp keeps the three rings full, eight consumer
+// warps compute.  A ring slot is handed back by an "empty" mbarrier that each consumer
+// warp arrives on once it has read the slot, so the consumer warps never wait for one
+// another inside a work item: while some warps read their shared-memory neighbours,
+// others do arithmetic or store.  Each consumer thread computes one 16-byte vector of two
+// y-adjacent points, which share the ten y-column values they read (the two points need
+// 2M+2 column loads instead of 4M).
+constexpr int WS_CWARPS = 8;                   // consumer warps
+constexpr int WS_CTHREADS = WS_CWARPS * 32;    // = OVC * TX * TY / 2 for a 16x8 tile
+constexpr int WS_THREADS = WS_CTHREADS + 32;   // + the producer warp
+
+__device__ __forceinline__ void consumer_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(WS_CTHREADS) : "memory");
+}
+
+// H at two y-adjacent points (rows 0 and 1) of one plane, from their z queues Q0/Q1 and
+// the halo plane Sp (row 0's own vector at hs0, row stride SXO vectors).  Same terms and
+// summation order as stencil_point.
+template <int M, int P, int QB, int QN>
+__device__ __forceinline__ void stencil_rows2(const typename VT<P>::S *W, typename W0T<P>::type w0,
+                                              const typename VT<P>::V *Q0, const typename VT<P>::V *Q1,
+                                              const typename VT<P>::V *Sp, int hs0, int SXO,
+                                              typename VT<P>::R ve0, typename VT<P>::R ve1,
+                                              typename VT<P>::V &acc0, typename VT<P>::V &acc1) {
+  typedef VT<P> T;
+  typedef typename T::V V;
+  V col[2 * M + 2];  // Sp[hs0 + k SXO], k = -M .. M+1
+#pragma unroll
+  for (int k = 0; k < 2 * M + 2; k++) col[k] = Sp[hs0 + (k - M) * SXO];
+  const int hs1 = hs0 + SXO;
+  acc0 = T::mul(T::diag(ve0, w0), Q0[(QB + M) % QN]);
+  acc1 = T::mul(T::diag(ve1, w0), Q1[(QB + M) % QN]);
+#pragma unroll
+  for (int m = 1; m <= M; m++) {
+    const V s0 = T::add(T::add(T::add(Q0[(QB + M - m) % QN], Q0[(QB + M + m) % QN]),
+                               T::add(Sp[hs0 - m * OVC], Sp[hs0 + m * OVC])),
+                        T::add(col[M - m], col[M + m]));
+    const V s1 = T::add(T::add(T::add(Q1[(QB + M - m) % QN], Q1[(QB + M + m) % QN]),
+                               T::add(Sp[hs1 - m * OVC], Sp[hs1 + m * OVC])),
+                        T::add(col[M + 1 - m], col[M + 1 + m]));
+    acc0 = T::fma(W[m], s0, acc0);
+    acc1 = T::fma(W[m], s1, acc1);
+  }
+}
+
+template <int M, int P, int MODE, int TX, int TY, int U, bool BATCH, class Src>
+__device__ __forceinline__ void ws_sweep_body(const Src &src) {
+  typedef VT<P> T;
+  typedef typename T::V V;
+  typedef typename T::S S_;
+  typedef typename T::R R;
+  constexpr bool OPS = MODE == MODE_LAST;
+  typedef TmaGeom<M, TX, TY, U, OPS> G;
+  static_assert(M % U == 0, "M must be a multiple of U");
+  static_assert(!OPS || U == 1, "the last Taylor term takes one plane per iteration");
+  static_assert(OVC * TX * TY == 2 * WS_CTHREADS, "two points per consumer thread");
+  constexpr int SC = G::SC, SH = G::SH;
+  constexpr int SO = G::SO > 0 ? G::SO : 1;
+  constexpr int QN = 2 * M + U;   // z-queue entries
+  constexpr int LP = 2 * M / U;   // priming centre loads per item
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *cbase = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
+  unsigned char *hbase = cbase + (size_t)SC * G::CSLOT_BYTES;
+  unsigned char *obase = hbase + (size_t)SH * G::HSLOT_BYTES;
+  __shared__ __align__(8) uint64_t cfull[SC], cempty[SC];
+  __shared__ __align__(8) uint64_t hfull[SH], hempty[SH];
+  __shared__ __align__(8) uint64_t ofull[SO], oempty[SO];
+  __shared__ double red[WS_CWARPS][4];
+  __shared__ int s_abort;
+  __shared__ SweepParams s_params;  // batch: parameters of the current item's system
+  volatile int *abort_flag = &s_abort;
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const long n_items_all = src.n_items();
+  const long n_my = (long)blockIdx.x < n_items_all ? (n_items_all - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  if (n_my == 0) return;
+
+  if (tid == 0) {
+    for (int s = 0; s < SC; s++) { mbar_init(&cfull[s], 1); mbar_init(&cempty[s], WS_CWARPS); }
+    for (int s = 0; s < SH; s++) { mbar_init(&hfull[s], 1); mbar_init(&hempty[s], WS_CWARPS); }
+    for (int s = 0; s < SO; s++) { mbar_init(&ofull[s], 1); mbar_init(&oempty[s], WS_CWARPS); }
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();  // the last CTA-wide barrier: from here on the warps run decoupled
+
+  const Loader<M, TX, TY, U, G, SC, SH, SO, Src> ld{src, n_my, cbase, hbase, obase, cfull, hfull, ofull};
+
+  if (warp == WS_CWARPS) {
+    // ---- producer: issue every ring's loads as soon as a slot is free -----------------
+    if (lane == 0) {
+      LoadCursor c[3];
+      for (int k = 0; k < 3; k++) c[k] = LoadCursor{-1, 0, 0, 0, 0, 0, 0, 0, 0};
+      long long idle_since = clock64();
+      for (;;) {
+        bool left = false, progressed = false;
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+          if (k == 2 && !OPS) continue;
+          ld.advance(c[k], k);
+          if (c[k].ii >= n_my) continue;
+          left = true;
+          const int S = k == 0 ? SC : (k == 1 ? SH : SO);
+          uint64_t *empty = k == 0 ? cempty : (k == 1 ? hempty : oempty);
+          const long n = c[k].issued;
+          // slot n % S is free once the consumers have released its previous use
+          if (n >= S && !mbar_test(&empty[n % S], (uint32_t)(((n / S) - 1) & 1))) continue;
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          ld.issue(c[k], k);
+          progressed = true;
+        }
+        if (!left) break;
+        if (progressed) {
+          idle_since = clock64();
+        } else {
+          if (*abort_flag || clock64() - idle_since > WAIT_LIMIT_CYCLES) {
+            *abort_flag = 1;
+            break;
+          }
+          __nanosleep(32);
+        }
+      }
+      // copies still in flight must land before the CTA's shared memory goes away
+      for (int k = 0; k < 3; k++) {
+        if (k == 2 && !OPS) continue;
+        const int S = k == 0 ? SC : (k == 1 ? SH : SO);
+        uint64_t *full = k == 0 ? cfull : (k == 1 ? hfull : ofull);
+        const long n = c[k].issued;
+        for (long j = n > S ? n - S : 0; j < n; j++)
+          mbar_wait_bounded(&full[j % S], (uint32_t)((j / S) & 1), DRAIN_LIMIT_CYCLES);
+      }
+    }
+    return;
+  }
+
+  // ---- consumers ------------------------------------------------------------------------
+  const int v = tid % OVC;
+  const int lx = (tid / OVC) % TX;
+  const int ly0 = 2 * (tid / (OVC * TX));
+  const int hs0 = ((ly0 + M) * G::SX + (lx + M)) * OVC + v;  // row 0's vector in a halo plane
+  const int tsl0 = ly0 * TX + lx;                             // row 0's point in a tile
+  const int csl0 = tsl0 * OVC + v;                            // row 0's vector in a centre plane
+  constexpr int SXO = G::SX * OVC;
+
+  RingPos rc, rh, ro;  // ring positions of the next centre / halo / operand load
+  bool aborted = false;
+  for (long ii = 0; ii < n_my; ii++) {
+    const long item = blockIdx.x + ii * gridDim.x;
+    const SweepParams *pp;
+    const SweepMaps *mp_unused;
+    long local;
+    src.item(item, pp, mp_unused, local);
+    if constexpr (BATCH) {
+      consumer_sync();  // every consumer is done with the previous item's parameters
+      if (tid == 0) s_params = *pp;
+      consumer_sync();
+      pp = &s_params;
+    }
+    const SweepParams &p = *pp;
+    const int nx = p.nx, ny = p.ny;
+    const long N = (long)nx * ny * p.nz;
+    const long plane_pts = (long)nx * ny;
+    S_ W[M + 1];
+#pragma unroll
+    for (int m = 0; m <= M; m++) W[m] = T::coef(p.w[m], p.wf[m]);
+    const typename W0T<P>::type w0 = P == P_C64 ? (typename W0T<P>::type)p.wf[0] : (typename W0T<P>::type)p.w[0];
+    const S_ CR = T::coef(p.cr, p.crf), CI = T::coef(p.ci, p.cif);
+    int tx, ty, kb, z0, z1;
+    item_geom(p, local, tx, ty, kb, z0, z1);
+    const int kidx = kb / p.n_batches;
+    const Epi epi = make_epi(p, kidx);
+    const bool has_proj = p.has_proj != 0, do_obs = p.do_obs != 0;
+    const V *nlk = nl_column<P>(p, kb, v);
+    const int n_ent = p.n_ent;
+    const int gx = tx * TX + lx, gy0 = ty * TY + ly0;
+    const bool own0 = gx < nx && gy0 < ny, own1 = gx < nx && gy0 + 1 < ny;
+    const int nl = loads_of<M, U>(0, z0, z1);
+    // vector index of row 0's point in the first output plane (advances one plane per output)
+    long idx = ((long)kb * N + ((long)z0 * ny + gy0) * nx + gx) * OVC + v;
+    const long row = (long)nx * OVC;
+    V Q0[QN], Q1[QN];
+#pragma unroll
+    for (int j = 0; j < QN; j++) Q0[j] = Q1[j] = T::zero();
+    ObsAcc<P> oa;
+
+    int l = 0;
+    // one centre load (and, past the priming loads, one halo load); RQ = compile-time
+    // queue position of its first plane
+    auto iteration = [&](auto rq) {
+      constexpr int RQ = decltype(rq)::value;
+      const int cs = rc.slot;
+      if (!mbar_wait_or_abort(&cfull[cs], rc.phase, abort_flag)) {
+        aborted = true;
+        return;
+      }
+      const V *cslot = reinterpret_cast<const V *>(cbase + (size_t)cs * G::CSLOT_BYTES);
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        Q0[(RQ + u) % QN] = cslot[u * G::CPLANE + csl0];
+        Q1[(RQ + u) % QN] = cslot[u * G::CPLANE + csl0 + TX * OVC];
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&cempty[cs]);
+      rc.next<SC>();
+      if (l >= LP) {
+        const int zf = z0 + U * (l - LP);
+        const int hs = rh.slot;
+        if (!mbar_wait_or_abort(&hfull[hs], rh.phase, abort_flag)) {
+          aborted = true;
+          return;
+        }
+        const unsigned char *hslot = hbase + (size_t)hs * G::HSLOT_BYTES;
+        const V *xs = reinterpret_cast<const V *>(hslot);
+        const PointAux *ax = reinterpret_cast<const PointAux *>(hslot + G::IN_BYTES);
+        const V *ob = nullptr;  // last term: the operand slot, read row by row at the epilogue
+        int os = 0;
+        if constexpr (OPS) {
+          os = ro.slot;
+          if (!mbar_wait_or_abort(&ofull[os], ro.phase, abort_flag)) {
+            aborted = true;
+            return;
+          }
+          ob = reinterpret_cast<const V *>(obase + (size_t)os * G::OP_BYTES);
+        }
+        auto operands = [&](int c) {
+          LastOperands<P> o;
+          if constexpr (OPS) {
+            o.hi = ob[c];
+            o.lo = ob[G::CPLANE + c];
+            o.t1 = ob[2 * G::CPLANE + c];
+            o.t2 = ob[3 * G::CPLANE + c];
+          } else {
+            o.hi = o.lo = o.t1 = o.t2 = T::zero();
+          }
+          return o;
+        };
+        static_for<0, U>([&](auto uc) {
+          constexpr int u = decltype(uc)::value;
+          constexpr int QB = (RQ + U + u) % QN;  // queue position of plane (zf + u) - M
+          const PointAux a0 = ax[u * TX * TY + tsl0];
+          const PointAux a1 = ax[u * TX * TY + tsl0 + TX];
+          const V nl0 = has_proj ? nl_term<P>(nlk, n_ent, a0.r0, a0.r1) : T::zero();
+          const V nl1 = has_proj ? nl_term<P>(nlk, n_ent, a1.r0, a1.r1) : T::zero();
+          V acc0, acc1;
+          stencil_rows2<M, P, QB, QN>(W, w0, Q0, Q1, xs + u * G::PLANE, hs0, SXO,
+                                      *reinterpret_cast<const R *>(&a0.veff), *reinterpret_cast<const R *>(&a1.veff),
+                                      acc0, acc1);
+          const bool live0 = own0 && (zf + u < z1), live1 = own1 && (zf + u < z1);
+          if (has_proj) {
+            acc0 = T::add(acc0, nl0);
+            acc1 = T::add(acc1, nl1);
+          }
+          const V c00 = Q0[(QB + M) % QN], c01 = Q1[(QB + M) % QN];
+          if (MODE == MODE_FIRST && do_obs) {
+            if (live0) oa.add_e(c00, acc0);
+            if (live1) oa.add_e(c01, acc1);
+          }
+          const long iu = idx + (long)u * plane_pts * OVC;
+          finish_point<P, MODE>(epi, CR, CI, live0, iu, v, c00, acc0, operands(csl0));
+          finish_point<P, MODE>(epi, CR, CI, live1, iu + row, v, c01, acc1, operands(csl0 + TX * OVC));
+        });
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(&hempty[hs]);
+          if constexpr (OPS) mbar_arrive(&oempty[os]);
+        }
+        idx += U * plane_pts * OVC;
+        rh.next<SH>();
+        if (OPS) ro.next<SO>();
+      }
+      l++;
+    };
+    int rq = 0;
+    while (l < nl && !aborted) {
+      switch (rq) {
+#define TDKS_CASE(k)                                                  \
+  case k:                                                             \
+    if constexpr (k % U == 0 && k < QN) iteration(std::integral_constant<int, k>{}); \
+    break;
+        TDKS_CASE(0) TDKS_CASE(1) TDKS_CASE(2) TDKS_CASE(3) TDKS_CASE(4)
+        TDKS_CASE(5) TDKS_CASE(6) TDKS_CASE(7) TDKS_CASE(8) TDKS_CASE(9)
+#undef TDKS_CASE
+      }
+      rq = rq + U >= QN ? rq + U - QN : rq + U;
+    }
+    if (aborted) {
+      // keep walking the items (no waits, no stores) so that every consumer warp reaches
+      // the same consumer barriers
+      *abort_flag = 1;
+      if (lane == 0 && p.err) atomicExch(p.err, 1);
+    }
+    if (MODE == MODE_FIRST && p.do_obs) {
+      double vals[4] = {oa.get_e(), oa.get_j(0), oa.get_j(1), oa.get_j(2)};
+#pragma unroll
+      for (int i = 0; i < 4; i++) {
+        double x = vals[i];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) red[warp][i] = x;
+      }
+      consumer_sync();
+      if (tid < 4) {
+        double x = 0.0;
+        for (int w = 0; w < WS_CWARPS; w++) x += red[w][tid];
+        p.obs_part[local * 4 + tid] = p.wocc[kidx] * x;
+      }
+      consumer_sync();
+    }
+  }
+}
+
+template <int M, int P, int MODE, int TX, int TY, int U>
+__global__ void __launch_bounds__(WS_THREADS, 1)
+ws_sweep_kernel(const __grid_constant__ SweepMaps maps, const __grid_constant__ SweepParams p) {
+  const SingleSrc src{&p, &maps};
+  ws_sweep_body<M, P, MODE, TX, TY, U, false>(src);
+}
+
+template <int M, int P, int MODE, int TX, int TY, int U>
+__global__ void __launch_bounds__(WS_THREADS, 1)
+ws_sweep_batch_kernel(const __grid_constant__ BatchSweepArgs a) {
+  const BatchSrc src{&a};
+  ws_sweep_body<M, P, MODE, TX, TY, U, true>(src);
+}
+
+// Planes per TMA copy of a sweep mode (the z depth of its tensor-map boxes): the lockstep
+// kernel takes two planes per iteration in the complex64 term sweeps, everything else one.
+int tma_planes(int prec, int mode, bool lockstep) { return (lockstep && prec == P_C64 && mode != MODE_LAST) ? 2 : 1; }
 
 bool tma_supported(int M, int tx, int ty) { return (M == 2 || M == 4) && tx == 16 && ty == 8; }
 
-template <int M, int P, int MODE, int U>
+template <int M, int P, int MODE, int U, bool WS>
 static cudaError_t launch_tma_t(const SweepMaps &maps, const SweepParams &p, int grid, cudaStream_t s) {
   typedef TmaGeom<M, 16, 8, U, MODE == MODE_LAST> G;
-  auto k = tma_sweep_kernel<M, P, MODE, 16, 8, U>;
+  void (*k)(const SweepMaps, const SweepParams);
+  if constexpr (WS) k = ws_sweep_kernel<M, P, MODE, 16, 8, U>;
+  else k = tma_sweep_kernel<M, P, MODE, 16, 8, U>;
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
@@ -466,14 +842,14 @@ static cudaError_t launch_tma_t(const SweepMaps &maps, const SweepParams &p, int
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     grid = (int)(p.n_items < sms ? p.n_items : sms);
   }
-  k<<<grid, OVC * 16 * 8, G::SMEM, s>>>(maps, p);
+  k<<<grid, WS ? WS_THREADS : OVC * 16 * 8, G::SMEM, s>>>(maps, p);
   return cudaGetLastError();
 }
 
 template <int M, int P, int MODE, int U>
 static cudaError_t launch_tma_batch_t(const BatchSweepArgs &a, cudaStream_t s) {
   typedef TmaGeom<M, 16, 8, U, MODE == MODE_LAST> G;
-  auto k = tma_sweep_batch_kernel<M, P, MODE, 16, 8, U>;
+  auto k = ws_sweep_batch_kernel<M, P, MODE, 16, 8, U>;
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
@@ -485,17 +861,16 @@ static cudaError_t launch_tma_batch_t(const BatchSweepArgs &a, cudaStream_t s) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = (int)(a.total_items < sms ? a.total_items : sms);
   if (grid <= 0) return cudaSuccess;
-  k<<<grid, OVC * 16 * 8, G::SMEM, s>>>(a);
+  k<<<grid, WS_THREADS, G::SMEM, s>>>(a);
   return cudaGetLastError();
 }
 
-// complex64: two planes per iteration in the term sweeps (= tma_planes); complex128
-// (FP64-bound, twice the registers per value) one plane; the last term one plane.
+// One plane per iteration (= tma_planes for the warp-specialised kernel).
 template <int M, int P>
 static cudaError_t tma_batch_by_mode(int mode, const BatchSweepArgs &a, cudaStream_t s) {
   switch (mode) {
-    case MODE_FIRST: return launch_tma_batch_t<M, P, MODE_FIRST, P == P_C64 ? 2 : 1>(a, s);
-    case MODE_MID: return launch_tma_batch_t<M, P, MODE_MID, P == P_C64 ? 2 : 1>(a, s);
+    case MODE_FIRST: return launch_tma_batch_t<M, P, MODE_FIRST, 1>(a, s);
+    case MODE_MID: return launch_tma_batch_t<M, P, MODE_MID, 1>(a, s);
     case MODE_LAST: return launch_tma_batch_t<M, P, MODE_LAST, 1>(a, s);
   }
   return cudaErrorInvalidValue;
@@ -507,23 +882,31 @@ cudaError_t launch_sweep_tma_batch(int M, int prec, int mode, const BatchSweepAr
   return cudaErrorInvalidValue;
 }
 
-template <int M, int P>
+// Planes per iteration = tma_planes(prec, mode, !WS).
+template <int M, int P, bool WS>
 static cudaError_t tma_by_mode(int mode, const SweepMaps &maps, const SweepParams &p, int grid, cudaStream_t s) {
   switch (mode) {
-    case MODE_FIRST: return launch_tma_t<M, P, MODE_FIRST, P == P_C64 ? 2 : 1>(maps, p, grid, s);
-    case MODE_MID: return launch_tma_t<M, P, MODE_MID, P == P_C64 ? 2 : 1>(maps, p, grid, s);
-    case MODE_LAST: return launch_tma_t<M, P, MODE_LAST, 1>(maps, p, grid, s);
+    case MODE_FIRST: return launch_tma_t<M, P, MODE_FIRST, (P == P_C64 && !WS) ? 2 : 1, WS>(maps, p, grid, s);
+    case MODE_MID: return launch_tma_t<M, P, MODE_MID, (P == P_C64 && !WS) ? 2 : 1, WS>(maps, p, grid, s);
+    case MODE_LAST: return launch_tma_t<M, P, MODE_LAST, 1, WS>(maps, p, grid, s);
   }
   return cudaErrorInvalidValue;
 }
 
+template <bool WS>
+static cudaError_t tma_dispatch(int M, int prec, int mode, const SweepMaps &maps, const SweepParams &p, int grid,
+                                cudaStream_t s) {
+  if (M == 2) return prec == P_C64 ? tma_by_mode<2, P_C64, WS>(mode, maps, p, grid, s)
+                                   : tma_by_mode<2, P_C128, WS>(mode, maps, p, grid, s);
+  return prec == P_C64 ? tma_by_mode<4, P_C64, WS>(mode, maps, p, grid, s)
+                       : tma_by_mode<4, P_C128, WS>(mode, maps, p, grid, s);
+}
+
 cudaError_t launch_sweep_tma(int M, int prec, int mode, int tx, int ty, const SweepMaps &maps, const SweepParams &p,
-                             int grid, cudaStream_t s) {
+                             int grid, cudaStream_t s, bool lockstep) {
   if (!tma_supported(M, tx, ty)) return cudaErrorInvalidValue;
-  if (M == 2) return prec == P_C64 ? tma_by_mode<2, P_C64>(mode, maps, p, grid, s)
-                                   : tma_by_mode<2, P_C128>(mode, maps, p, grid, s);
-  return prec == P_C64 ? tma_by_mode<4, P_C64>(mode, maps, p, grid, s)
-                       : tma_by_mode<4, P_C128>(mode, maps, p, grid, s);
+  return lockstep ? tma_dispatch<false>(M, prec, mode, maps, p, grid, s)
+                  : tma_dispatch<true>(M, prec, mode, maps, p, grid, s);
 }
 
 }  // namespace tdks

@@ -54,6 +54,9 @@ struct tdks_system {
   double *obs_rec = nullptr;    // single record for tdks_observe
   double *d_kvec = nullptr, *d_wocc = nullptr, *d_D = nullptr;
   int *d_rowent = nullptr, *d_atom_begin = nullptr;
+  int2 *d_sp = nullptr;       // entry ranges of the points inside a sphere
+  void *d_nl = nullptr;       // non-local term per sphere point, [n_kb][n_ent + 1][OVC]
+  int n_sp = 0, n_ent = 0;
   tdks::ProjEntry *d_ent = nullptr;
   void *d_q = nullptr;
   double2 *d_qpart = nullptr;   // gather partial sums, gchunks per (atom, k-batch)
@@ -90,9 +93,11 @@ double envelope_of(const tdks_system *s, double t, double *denv);
 void sweep_geometry(const tdks_system *s, tdks::SweepParams &p);
 void sweep_common(const tdks_system *s, tdks::SweepParams &p, const double A[3]);
 long n_items_of(const tdks_system *s);
-bool encode_map(const tdks_system *s, const void *ptr, int mode, CUtensorMap *out);
+bool encode_map(const tdks_system *s, const void *ptr, int mode, CUtensorMap *out, bool lockstep);
 // all maps of a TMA sweep of `mode` over input `in` (the operand maps only for the last term)
-bool encode_sweep_maps(const tdks_system *s, const void *in, int mode, tdks::SweepMaps *out);
+// lockstep: box depths for the lockstep TMA kernel (tdks_set_sweep_path 2), else for the
+// warp-specialised one
+bool encode_sweep_maps(const tdks_system *s, const void *in, int mode, tdks::SweepMaps *out, bool lockstep);
 int ensure_density(tdks_system *s);
 int check_err(tdks_system *s);
 double kinetic_max(const tdks_system *s);

@@ -86,6 +86,8 @@ template <> struct VT<P_C128> {
   typedef double R;   // scalar type of the potential arrays
   static __device__ __forceinline__ V zero() { return make_double2(0.0, 0.0); }
   static __device__ __forceinline__ S bc(double s) { return s; }
+  // a coefficient from its FP64 value (the FP32 copy is for complex64)
+  static __device__ __forceinline__ S coef(double d, float) { return d; }
   // diagonal (V_eff(r) + w0) broadcast, in the compute precision
   static __device__ __forceinline__ S diag(R ve, double w0) { return ve + w0; }
   static __device__ __forceinline__ V add(V a, V b) { return make_double2(a.x + b.x, a.y + b.y); }
@@ -111,6 +113,8 @@ template <> struct VT<P_C64> {
   typedef float R;
   static __device__ __forceinline__ V zero() { return make_ulonglong2(0ull, 0ull); }
   static __device__ __forceinline__ S bc(double s) { float f = (float)s; return pk2(f, f); }
+  // a coefficient from its FP32 copy (no FP64 conversion in the kernel)
+  static __device__ __forceinline__ S coef(double, float f) { return pk2(f, f); }
   static __device__ __forceinline__ S diag(R ve, float w0) { const float d = ve + w0; return pk2(d, d); }
   static __device__ __forceinline__ V add(V a, V b) { return make_ulonglong2(add2(a.x, b.x), add2(a.y, b.y)); }
   static __device__ __forceinline__ V sub(V a, V b) { return make_ulonglong2(sub2(a.x, b.x), sub2(a.y, b.y)); }

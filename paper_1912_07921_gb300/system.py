@@ -79,7 +79,8 @@ class System:
         _lib.check(self.lib.tdks_set_tile(self.h, tx, ty, zc))
 
     def set_sweep_path(self, path: int):
-        """0: TMA-fed sweep where it applies (finite boxes, 16x8 tiles); 1: general sweep."""
+        """0: TMA-fed warp-specialised sweep where it applies (finite boxes, 16x8 tiles);
+        1: general sweep; 2: TMA-fed sweep with all warps of a CTA in lockstep."""
         _lib.check(self.lib.tdks_set_sweep_path(self.h, path))
 
     # -- queries ---------------------------------------------------------------------

@@ -72,14 +72,16 @@ def test_apply_H_matches_oracle(name):
 
 @pytest.mark.parametrize("prec", [I.PREC_C128, I.PREC_C64])
 def test_apply_H_is_independent_of_tile_and_sweep_path(prec):
-    """TMA sweep (16x8 tiles) and general sweep (any tile, any z-chunk) agree to the last
-    bits of rounding (the same per-point arithmetic; only FMA contraction may differ)."""
+    """TMA sweeps (warp-specialised and lockstep, 16x8 tiles) and the general sweep (any
+    tile, any z-chunk) agree to the last bits of rounding (the same per-point arithmetic;
+    only FMA contraction may differ)."""
     spec = ragged_molecule(prec)
     inp = I.make_inputs(spec)
     sysm = _system(spec, inp)
     psi = I.random_orbitals(spec, 5)
     outs = []
-    for tx, ty, zc, path in ((16, 8, 0, 0), (16, 8, 0, 1), (32, 4, 0, 1), (8, 8, 5, 1), (16, 8, 7, 0)):
+    for tx, ty, zc, path in ((16, 8, 0, 0), (16, 8, 0, 1), (32, 4, 0, 1), (8, 8, 5, 1), (16, 8, 7, 0), (16, 8, 7, 2),
+                             (16, 8, 0, 2)):
         sysm.set_tile(tx, ty, zc)
         sysm.set_sweep_path(path)
         outs.append(_apply_gpu(sysm, psi, 0.2))
@@ -94,15 +96,16 @@ def test_propagation_tma_and_general_paths_agree(prec):
     spec = ragged_molecule(prec)
     inp = I.make_inputs(spec)
     res = []
-    for path in (0, 1):
+    for path in (0, 1, 2):
         sysm = _system(spec, inp)
         sysm.set_sweep_path(path)
         sysm.propagate(0.0, 0.02, 3, 1)
         res.append((sysm.get_orbitals(), sysm.reductions(0, 3)))
         sysm.close()
     tol = 1e-13 if prec == I.PREC_C128 else 1e-6
-    assert rel_err(res[1][0], res[0][0]) < tol
-    assert rel_err(res[1][1], res[0][1]) < tol
+    for r in res[1:]:
+        assert rel_err(r[0], res[0][0]) < tol
+        assert rel_err(r[1], res[0][1]) < tol
 
 
 def _propagate_both(spec, inp, n_steps, substeps, dt=None):
