@@ -248,8 +248,8 @@ int tdks_batch_destroy(tdks_batch_t batch);
  * 8 for TDKS_C64, zero-padded batches); stream: cudaStream_t or NULL.  The caller owns all
  * three buffers.  The call synchronises the stream before it returns.
  *
- * Scratch (one 16-byte record per point with the potential, and an error word) lives in a fixed
- * file-scope device array of 16 MiB + 256 B that every GPU loading the library holds until
+ * Scratch (one 16-byte record per point with the potential, an error word and a work-item
+ * counter) lives in a fixed file-scope device array of 16 MiB + 256 B that every GPU loading the library holds until
  * the process exits; grids above 2^20 = 1,048,576 points are rejected with TDKS_EINVAL.
  * All calls on a device share that array and each call overwrites it, so calls whose work
  * overlaps on the GPU (several streams or host threads) race: serialise them.  The first

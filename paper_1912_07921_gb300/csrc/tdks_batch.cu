@@ -27,6 +27,7 @@ struct tdks_batch {
   SweepMaps *d_maps = nullptr;                                      // 4 per system
   long *d_item_begin = nullptr, *d_gather_begin = nullptr, *d_unit_begin = nullptr, *d_lda_begin = nullptr;
   long *d_nl_begin = nullptr;
+  unsigned int *d_work = nullptr;  // work-item counter of the batched sweep (zero between launches)
   BatchAux *d_aux = nullptr;
   BatchClock *d_clock = nullptr;
   long total_items = 0, total_gather = 0, total_units = 0, total_lda = 0, total_nl = 0;
@@ -40,7 +41,7 @@ namespace {
 void batch_free(tdks_batch *b) {
   for (int k = 0; k < 4; k++) { cudaFree(b->d_sweep[k]); cudaFree(b->d_gather[k]); }
   cudaFree(b->d_maps); cudaFree(b->d_item_begin); cudaFree(b->d_gather_begin); cudaFree(b->d_lda_begin);
-  cudaFree(b->d_nl_begin);
+  cudaFree(b->d_nl_begin); cudaFree(b->d_work);
   cudaFree(b->d_unit_begin);
   cudaFree(b->d_aux); cudaFree(b->d_clock);
   if (b->exec) cudaGraphExecDestroy(b->exec);
@@ -67,7 +68,7 @@ int enqueue_substep(tdks_batch *b) {
     e = launch_gather_batch(b->prec, b->d_gather[k], b->d_gather_begin, b->d_unit_begin, b->d_nl_begin, n,
                             b->total_gather, b->total_units, b->total_nl, b->work);
     if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("batched gather: ") + cudaGetErrorString(e));
-    BatchSweepArgs a{b->d_sweep[k], b->d_maps, k, b->d_item_begin, n, b->total_items};
+    BatchSweepArgs a{b->d_sweep[k], b->d_maps, k, b->d_item_begin, n, b->total_items, b->d_work};
     const int mode = k == 0 ? MODE_FIRST : (k == 3 ? MODE_LAST : MODE_MID);
     e = launch_sweep_tma_batch(b->M, b->prec, mode, a, b->work);
     if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("batched sweep: ") + cudaGetErrorString(e));
@@ -181,7 +182,8 @@ int tdks_batch_create(const tdks_sys *systems, int n, void *stream, tdks_batch_t
     for (int d = 0; d < 3; d++) a.pol[d] = s->pol[d];
     a.amp = s->amp; a.omega = s->omega; a.t_total = s->t_total;
     a.dens_part = s->dens_part; a.vloc = s->vloc; a.aux = s->aux; a.lda_part = s->lda_part; a.n_lda = nl;
-    a.obs_part = s->obs_part; a.n_items = sp[0].back().n_items; a.ring = s->ring;
+    // the warp-specialised sweep writes one partial record per consumer warp and item
+    a.obs_part = s->obs_part; a.n_items = sp[0].back().n_items * WS_CONSUMER_WARPS; a.ring = s->ring;
     a.ring_len = tdks_system::RING;
     s->tx = save_tx; s->ty = save_ty; s->zc = save_zc;
   }
@@ -201,6 +203,7 @@ int tdks_batch_create(const tdks_sys *systems, int n, void *stream, tdks_batch_t
   if (!rc) rc = upload(&b->d_unit_begin, unit_begin);
   if (!rc) rc = upload(&b->d_lda_begin, lda_begin);
   if (!rc) rc = upload(&b->d_nl_begin, nl_begin);
+  if (!rc) rc = upload(&b->d_work, std::vector<unsigned int>(1, 0u));
   if (!rc) rc = upload(&b->d_aux, aux);
   if (!rc) rc = upload(&b->d_clock, clk);
   if (!rc && (cudaStreamCreateWithFlags(&b->work, cudaStreamNonBlocking) != cudaSuccess ||

@@ -132,7 +132,20 @@ void sweep_geometry(const tdks_system *s, SweepParams &p) {
   p.n_kb = s->n_kb;
   p.n_batches = s->n_batches;
   int zc = s->zc;
-  if (zc <= 0) {
+  const bool dynamic = s->path == 0 && s->bc == TDKS_BC_ZERO && tma_supported(s->M, s->tx, s->ty);
+  if (zc <= 0 && dynamic) {
+    // warp-specialised TMA sweep: CTAs claim items from a counter, so the cost is the total
+    // work spread over the SMs (the 2M priming planes of an item only load a centre tile,
+    // about a quarter of an output plane each) plus half an item of tail; the items of
+    // one column's z chunks are claimed one after another and share their halo planes in L2.
+    const long per_plane = (long)p.n_tx * p.n_ty * p.n_kb;
+    double best = -1.0;
+    for (int c = 1; c <= s->nz; c++) {
+      const long items = per_plane * ((s->nz + c - 1) / c);
+      const double cost = (double)items * (c + 0.25 * 2 * s->M) / 152.0 + 0.5 * c;
+      if (best < 0.0 || cost < best) { best = cost; zc = c; }
+    }
+  } else if (zc <= 0) {
     // z-chunk length minimising (waves of work items) x (planes per item, including the
     // 2M planes that prime each item's z-queue); one resident CTA per SM.
     const long per_plane = (long)p.n_tx * p.n_ty * p.n_kb;
@@ -179,6 +192,7 @@ void sweep_common(const tdks_system *s, SweepParams &p, const double A[3]) {
     for (int a = 0; a < 3; a++) if (A[a] != 0.0) p.grad_mask |= 1 << a;
   p.wocc = s->d_wocc;
   p.obs_part = s->obs_part;
+  p.work = s->d_err ? reinterpret_cast<unsigned int *>(s->d_err + 1) : nullptr;
   p.dens_part = s->dens_part;
   p.do_obs = 0;
 }
@@ -252,10 +266,13 @@ int run_sweep(tdks_system *s, int mode, SweepParams &p, const SweepMaps *tm) {
   Timed tmr(s, 0);
   p.err = s->d_err;
   cudaError_t e;
-  if (tm && s->path != 1 && s->bc == TDKS_BC_ZERO && tma_supported(s->M, s->tx, s->ty))
-    e = launch_sweep_tma(s->M, s->prec, mode, s->tx, s->ty, *tm, p, 0, s->stream, s->path == 2);
+  const bool tma = tm && s->path != 1 && s->bc == TDKS_BC_ZERO && tma_supported(s->M, s->tx, s->ty);
+  const bool ws = tma && s->path == 0;
+  if (tma)
+    e = launch_sweep_tma(s->M, s->prec, mode, s->tx, s->ty, *tm, p, 0, s->stream, !ws);
   else
     e = launch_sweep(s->M, s->prec, mode, s->bc == TDKS_BC_BLOCH, s->tx, s->ty, p, 0, s->stream);
+  if (mode == MODE_FIRST && p.do_obs) s->obs_count = p.n_items * (ws ? WS_CONSUMER_WARPS : 1);
   s->launches++;
   if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("stencil sweep: ") + cudaGetErrorString(e));
   return TDKS_OK;
@@ -315,7 +332,7 @@ int run_finalize(tdks_system *s, double *rec, double t_state, const double E[3],
   for (int a = 0; a < 3; a++) fv += (s->gauge == TDKS_GAUGE_VELOCITY ? A[a] : E[a]) * s->pol[a];
   const double Az[3] = {0, 0, 0};
   Timed tm(s, 2);
-  cudaError_t e = launch_finalize(s->obs_part, n_items_of(s), s->lda_part, lda_blocks(s->N), rec, t_state, h3,
+  cudaError_t e = launch_finalize(s->obs_part, s->obs_count, s->lda_part, lda_blocks(s->N), rec, t_state, h3,
                                   s->occ, s->bc == TDKS_BC_BLOCH, omega_cell,
                                   s->gauge == TDKS_GAUGE_VELOCITY ? A : Az, fv, s->stream);
   s->launches++;
@@ -383,7 +400,7 @@ int check_err(tdks_system *s) {
   int h = 0;
   CU(cudaMemcpy(&h, s->d_err, sizeof(int), cudaMemcpyDeviceToHost));
   if (h) {
-    CU(cudaMemset(s->d_err, 0, sizeof(int)));
+    CU(cudaMemset(s->d_err, 0, 2 * sizeof(int)));  // and the work counter an aborted sweep left
     return fail(TDKS_ETIMEOUT, "a sweep kernel gave up waiting for its TMA copies");
   }
   return TDKS_OK;
@@ -442,16 +459,18 @@ int tdks_create_grid(int nx, int ny, int nz, double h, int fd_order, int bc, int
   ALLOC(s->psi, s->state_bytes);
   if (prec == TDKS_C64) ALLOC(s->psi_lo, s->state_bytes);
   for (int i = 0; i < 3; i++) ALLOC(s->term[i], s->term_bytes);
-  ALLOC(s->d_err, sizeof(int));
+  ALLOC(s->d_err, 2 * sizeof(int));
   ALLOC(s->vloc, N * sizeof(double));
   ALLOC(s->aux, N * sizeof(PointAux));
   ALLOC(s->dens_part, pts * sizeof(double));
   ALLOC(s->lda_part, (size_t)nlda * 6 * sizeof(double));
   s->zc = 0;
-  // obs partials sized for the smallest tile (most items)
+  // obs partials sized for the most records a first sweep can write: the smallest tile of
+  // the general sweep, or the warp-specialised sweep's per-warp records (z chunks of 1 plane)
   {
-    const long items = (long)((nx + 7) / 8) * ((ny + 3) / 4) * s->n_kb * nz;
-    ALLOC(s->obs_part, (size_t)items * 4 * sizeof(double));
+    const long items_gen = (long)((nx + 7) / 8) * ((ny + 3) / 4) * s->n_kb * nz;
+    const long items_ws = (long)((nx + 15) / 16) * ((ny + 7) / 8) * s->n_kb * nz * WS_CONSUMER_WARPS;
+    ALLOC(s->obs_part, (size_t)std::max(items_gen, items_ws) * 4 * sizeof(double));
   }
   ALLOC(s->ring, (size_t)tdks_system::RING * TDKS_RECORD * sizeof(double));
   ALLOC(s->obs_rec, TDKS_RECORD * sizeof(double));
@@ -463,7 +482,7 @@ int tdks_create_grid(int nx, int ny, int nz, double h, int fd_order, int bc, int
       cudaMemsetAsync(s->aux, 0, N * sizeof(PointAux), s->stream) != cudaSuccess ||
       cudaMemsetAsync(s->psi, 0, s->state_bytes, s->stream) != cudaSuccess ||
       (s->psi_lo && cudaMemsetAsync(s->psi_lo, 0, s->state_bytes, s->stream) != cudaSuccess) ||
-      cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream) != cudaSuccess)
+      cudaMemsetAsync(s->d_err, 0, 2 * sizeof(int), s->stream) != cudaSuccess)
     return cleanup(TDKS_EDEVICE, "initial copies");
   build_tmaps(s);
   std::vector<double> wocc(n_k);

@@ -79,6 +79,8 @@ struct SweepParams {
   const double *wocc;         // [n_k] k-weight times occupation
   double *dens_part;          // [n_kb][N] (MODE_LAST)
   int *err;                   // device error word (bounded waits that ran out set it)
+  unsigned int *work;         // work-item counter of the warp-specialised TMA sweep (zero
+                              // between launches: the launch's last claim resets it)
 };
 
 // Sets the Taylor coefficient (cr + i ci) with its FP32 copies.
@@ -153,7 +155,12 @@ struct BatchSweepArgs {
   const long *item_begin;
   int n_sys;
   long total_items;
+  unsigned int *work;     // work-item counter (zero between launches)
 };
+
+// Consumer warps of the warp-specialised TMA sweep; each writes its own energy/current
+// partials, so an item of that kernel has WS_CONSUMER_WARPS partial records.
+constexpr int WS_CONSUMER_WARPS = 8;
 
 // Launchers (tdks_sweep.cu)
 cudaError_t launch_sweep(int M, int prec, int mode, int bloch, int tx, int ty,

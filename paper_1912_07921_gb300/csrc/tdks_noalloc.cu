@@ -5,7 +5,8 @@
 // loop in which a cudaMalloc/cudaFree (which can synchronise the device and stall other
 // streams) is not acceptable.  tdks_apply_H_noalloc serves them.  The caller passes the
 // potential, the input orbitals and the output buffer; the only scratch this path needs
-// (the potential in the compute precision and an error word) lives in a file-scope
+// (a per-point record with the potential in the compute precision, an error word and the
+// sweep's work counter) lives in a file-scope
 // __device__ array of fixed size, which every GPU that loads the library holds until the
 // process exits.
 //
@@ -31,7 +32,7 @@ constexpr long NOALLOC_MAX_POINTS = 1L << 20;
 constexpr int NOALLOC_MAX_DEVICES = 64;
 
 // [0, 16 * NOALLOC_MAX_POINTS): one 16-byte record per point (the potential in the compute
-// precision, an empty projector range); then the error word.
+// precision, an empty projector range); then the error word and the sweep's work counter.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[16 * NOALLOC_MAX_POINTS + 256];
 
 std::mutex g_addr_mutex;
@@ -56,7 +57,10 @@ int scratch_address(void **out) {
 template <typename R>
 __global__ void noalloc_prepare(long N, const double *vloc, PointAux *aux, int *err) {
   const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  if (i == 0) *err = 0;  // the error word must start at zero on every call
+  if (i == 0) {  // the error word and the sweep's work counter must start at zero on every call
+    err[0] = 0;
+    err[1] = 0;
+  }
   if (i < N) {
     PointAux a{0.0, 0, 0};
     *reinterpret_cast<R *>(&a.veff) = (R)vloc[i];
@@ -107,6 +111,7 @@ extern "C" int tdks_apply_H_noalloc(int nx, int ny, int nz, double h, int fd_ord
   p.in = dev_in;
   p.out = dev_out;
   p.err = err;
+  p.work = reinterpret_cast<unsigned int *>(err + 1);
   SweepMaps tm;
   cudaError_t e;
   if (tma_supported(M, s.tx, s.ty) && encode_sweep_maps(&s, dev_in, MODE_MID, &tm, false))

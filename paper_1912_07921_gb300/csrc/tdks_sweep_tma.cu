@@ -168,6 +168,7 @@ struct SingleSrc {
   }
   __device__ __forceinline__ int sys_of(long) const { return 0; }
   __device__ __forceinline__ const SweepMaps *maps_of(int) const { return maps; }
+  __device__ __forceinline__ int *err0() const { return p->err; }
 };
 
 __device__ __forceinline__ int find_item_sys(const long *begin, int n, long u) {
@@ -190,6 +191,7 @@ struct BatchSrc {
   }
   __device__ __forceinline__ int sys_of(long it) const { return find_item_sys(a->item_begin, a->n_sys, it); }
   __device__ __forceinline__ const SweepMaps *maps_of(int s) const { return a->maps + 4 * s + a->which; }
+  __device__ __forceinline__ int *err0() const { return a->params[0].err; }
 };
 
 // Sequential cursor over one kind of load of the CTA's items (thread 0 only).  The item's
@@ -207,13 +209,15 @@ struct LoadCursor {
 // Work item -> tile (tx, ty), orbital block kb and z chunk [z0, z1).
 __device__ __forceinline__ void item_geom(const SweepParams &q, long it, int &tx, int &ty, int &kb, int &z0,
                                           int &z1) {
+  // z chunks fastest: consecutive items are the chunks of one column, which run at about the
+  // same time on different SMs and share the planes at their boundaries through L2
+  z0 = (int)(it % q.n_zc) * q.zc;
+  it /= q.n_zc;
   tx = (int)(it % q.n_tx);
   it /= q.n_tx;
   ty = (int)(it % q.n_ty);
   it /= q.n_ty;
-  kb = (int)(it % q.n_kb);
-  it /= q.n_kb;
-  z0 = (int)it * q.zc;
+  kb = (int)it;
   z1 = min(z0 + q.zc, q.nz);
 }
 
@@ -257,6 +261,11 @@ struct Loader {
   __device__ __forceinline__ void issue(LoadCursor &c, int kind) const {
     advance(c, kind);
     if (c.ii >= n_my) return;
+    emit(c, kind);
+  }
+
+  // issue the load the cursor is positioned on
+  __device__ __forceinline__ void emit(LoadCursor &c, int kind) const {
     const SweepMaps *mp = src.maps_of(c.sys);
     if (kind == 0) {
       const int slot = (int)(c.issued % SC);
@@ -504,10 +513,6 @@ constexpr int WS_CWARPS = 8;                   // consumer warps
 constexpr int WS_CTHREADS = WS_CWARPS * 32;    // = OVC * TX * TY / 2 for a 16x8 tile
 constexpr int WS_THREADS = WS_CTHREADS + 32;   // + the producer warp
 
-__device__ __forceinline__ void consumer_sync() {
-  asm volatile("bar.sync 1, %0;" ::"n"(WS_CTHREADS) : "memory");
-}
-
 // H at two y-adjacent points (rows 0 and 1) of one plane, from their z queues Q0/Q1 and
 // the halo plane Sp (row 0's own vector at hs0, row stride SXO vectors).  Same terms and
 // summation order as stencil_point.
@@ -539,7 +544,7 @@ __device__ __forceinline__ void stencil_rows2(const typename VT<P>::S *W, typena
 }
 
 template <int M, int P, int MODE, int TX, int TY, int U, bool BATCH, class Src>
-__device__ __forceinline__ void ws_sweep_body(const Src &src) {
+__device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work) {
   typedef VT<P> T;
   typedef typename T::V V;
   typedef typename T::S S_;
@@ -549,10 +554,12 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src) {
   static_assert(M % U == 0, "M must be a multiple of U");
   static_assert(!OPS || U == 1, "the last Taylor term takes one plane per iteration");
   static_assert(OVC * TX * TY == 2 * WS_CTHREADS, "two points per consumer thread");
+  static_assert(WS_CWARPS == WS_CONSUMER_WARPS, "per-warp partial records");
   constexpr int SC = G::SC, SH = G::SH;
   constexpr int SO = G::SO > 0 ? G::SO : 1;
   constexpr int QN = 2 * M + U;   // z-queue entries
   constexpr int LP = 2 * M / U;   // priming centre loads per item
+  constexpr int IR = 16;          // claimed-item ring (the producer runs at most a few items ahead)
   extern __shared__ unsigned char smem_raw[];
   unsigned char *cbase = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
   unsigned char *hbase = cbase + (size_t)SC * G::CSLOT_BYTES;
@@ -560,49 +567,81 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src) {
   __shared__ __align__(8) uint64_t cfull[SC], cempty[SC];
   __shared__ __align__(8) uint64_t hfull[SH], hempty[SH];
   __shared__ __align__(8) uint64_t ofull[SO], oempty[SO];
-  __shared__ double red[WS_CWARPS][4];
+  __shared__ __align__(8) uint64_t ibar[IR];  // completes when s_item[seq % IR] is written
+  __shared__ long s_item[IR];                 // item of the CTA's seq-th claim (-1: no more)
   __shared__ int s_abort;
-  __shared__ SweepParams s_params;  // batch: parameters of the current item's system
   volatile int *abort_flag = &s_abort;
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   const long n_items_all = src.n_items();
-  const long n_my = (long)blockIdx.x < n_items_all ? (n_items_all - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  if (n_my == 0) return;
 
   if (tid == 0) {
     for (int s = 0; s < SC; s++) { mbar_init(&cfull[s], 1); mbar_init(&cempty[s], WS_CWARPS); }
     for (int s = 0; s < SH; s++) { mbar_init(&hfull[s], 1); mbar_init(&hempty[s], WS_CWARPS); }
     for (int s = 0; s < SO; s++) { mbar_init(&ofull[s], 1); mbar_init(&oempty[s], WS_CWARPS); }
+    for (int s = 0; s < IR; s++) mbar_init(&ibar[s], 1);
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  __syncthreads();  // the last CTA-wide barrier: from here on the warps run decoupled
-
-  const Loader<M, TX, TY, U, G, SC, SH, SO, Src> ld{src, n_my, cbase, hbase, obase, cfull, hfull, ofull};
+  __syncthreads();  // the only CTA-wide barrier: from here on the warps run decoupled
 
   if (warp == WS_CWARPS) {
-    // ---- producer: issue every ring's loads as soon as a slot is free -----------------
+    // ---- producer: claim items, and issue every ring's loads as soon as a slot is free ----
     if (lane == 0) {
+      const Loader<M, TX, TY, U, G, SC, SH, SO, Src> ld{src, 0, cbase, hbase, obase, cfull, hfull, ofull};
       LoadCursor c[3];
+      bool done[3] = {false, false, !OPS};
       for (int k = 0; k < 3; k++) c[k] = LoadCursor{-1, 0, 0, 0, 0, 0, 0, 0, 0};
+      long claimed = 0;  // claims made (their items are in s_item)
+      // position cursor k on its next load; false if it has none yet (or none at all)
+      auto position = [&](int k) -> bool {
+        LoadCursor &cu = c[k];
+        while (!done[k] && cu.l >= cu.n) {
+          const long ns = cu.ii + 1;
+          if (ns >= claimed) {
+            if (k != 0) return false;  // the centre cursor, always ahead, makes the claims
+            const unsigned int t = atomicAdd(work, 1u);
+            // every CTA ends with one claim past the last item: the launch's last claim
+            // returns the counter to zero for the next launch
+            if ((long)t == n_items_all + (long)gridDim.x - 1) atomicExch(work, 0u);
+            s_item[claimed % IR] = (long)t < n_items_all ? (long)t : -1;
+            mbar_arrive(&ibar[claimed % IR]);
+            claimed++;
+          }
+          const long it = s_item[ns % IR];
+          if (it < 0) {
+            done[k] = true;
+            break;
+          }
+          const SweepParams *qp = nullptr;
+          const SweepMaps *mq = nullptr;
+          long local = 0;
+          src.item(it, qp, mq, local);
+          int z1 = 0;
+          item_geom(*qp, local, cu.tx, cu.ty, cu.kb, cu.z0, z1);
+          cu.sys = src.sys_of(it);
+          cu.ii = ns;
+          cu.l = 0;
+          cu.n = loads_of<M, U>(k, cu.z0, z1);
+        }
+        return !done[k];
+      };
       long long idle_since = clock64();
       for (;;) {
         bool left = false, progressed = false;
 #pragma unroll
         for (int k = 0; k < 3; k++) {
-          if (k == 2 && !OPS) continue;
-          ld.advance(c[k], k);
-          if (c[k].ii >= n_my) continue;
+          if (done[k]) continue;
           left = true;
+          if (!position(k)) continue;
           const int S = k == 0 ? SC : (k == 1 ? SH : SO);
           uint64_t *empty = k == 0 ? cempty : (k == 1 ? hempty : oempty);
           const long n = c[k].issued;
           // slot n % S is free once the consumers have released its previous use
           if (n >= S && !mbar_test(&empty[n % S], (uint32_t)(((n / S) - 1) & 1))) continue;
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          ld.issue(c[k], k);
+          ld.emit(c[k], k);
           progressed = true;
         }
         if (!left) break;
@@ -629,7 +668,8 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src) {
     return;
   }
 
-  // ---- consumers ------------------------------------------------------------------------
+  // ---- consumers: no barrier between warps; a warp that gives up stops, and the others
+  // give up at their next wait ----------------------------------------------------------------
   const int v = tid % OVC;
   const int lx = (tid / OVC) % TX;
   const int ly0 = 2 * (tid / (OVC * TX));
@@ -640,19 +680,20 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src) {
 
   RingPos rc, rh, ro;  // ring positions of the next centre / halo / operand load
   bool aborted = false;
-  for (long ii = 0; ii < n_my; ii++) {
-    const long item = blockIdx.x + ii * gridDim.x;
+  int *errp = src.err0();  // then the current item's system's
+  for (long seq = 0;; seq++) {
+    if (!mbar_wait_or_abort(&ibar[seq % IR], (uint32_t)((seq / IR) & 1), abort_flag)) {
+      aborted = true;
+      break;
+    }
+    const long item = s_item[seq % IR];
+    if (item < 0) break;
     const SweepParams *pp;
     const SweepMaps *mp_unused;
     long local;
     src.item(item, pp, mp_unused, local);
-    if constexpr (BATCH) {
-      consumer_sync();  // every consumer is done with the previous item's parameters
-      if (tid == 0) s_params = *pp;
-      consumer_sync();
-      pp = &s_params;
-    }
-    const SweepParams &p = *pp;
+    const SweepParams &p = *pp;  // (batch: read from the parameter array, once per item)
+    errp = p.err;
     const int nx = p.nx, ny = p.ny;
     const long N = (long)nx * ny * p.nz;
     const long plane_pts = (long)nx * ny;
@@ -779,28 +820,21 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src) {
       }
       rq = rq + U >= QN ? rq + U - QN : rq + U;
     }
-    if (aborted) {
-      // keep walking the items (no waits, no stores) so that every consumer warp reaches
-      // the same consumer barriers
-      *abort_flag = 1;
-      if (lane == 0 && p.err) atomicExch(p.err, 1);
-    }
-    if (MODE == MODE_FIRST && p.do_obs) {
+    if (aborted) break;
+    if (MODE == MODE_FIRST && do_obs) {
+      // this warp's partials of the item: record local * WS_CWARPS + warp
       double vals[4] = {oa.get_e(), oa.get_j(0), oa.get_j(1), oa.get_j(2)};
 #pragma unroll
       for (int i = 0; i < 4; i++) {
         double x = vals[i];
         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        if (lane == 0) red[warp][i] = x;
+        if (lane == 0) p.obs_part[(local * WS_CWARPS + warp) * 4 + i] = epi.wocc * x;
       }
-      consumer_sync();
-      if (tid < 4) {
-        double x = 0.0;
-        for (int w = 0; w < WS_CWARPS; w++) x += red[w][tid];
-        p.obs_part[local * 4 + tid] = p.wocc[kidx] * x;
-      }
-      consumer_sync();
     }
+  }
+  if (aborted) {
+    *abort_flag = 1;
+    if (lane == 0 && errp) atomicExch(errp, 1);
   }
 }
 
@@ -808,14 +842,14 @@ template <int M, int P, int MODE, int TX, int TY, int U>
 __global__ void __launch_bounds__(WS_THREADS, 1)
 ws_sweep_kernel(const __grid_constant__ SweepMaps maps, const __grid_constant__ SweepParams p) {
   const SingleSrc src{&p, &maps};
-  ws_sweep_body<M, P, MODE, TX, TY, U, false>(src);
+  ws_sweep_body<M, P, MODE, TX, TY, U, false>(src, p.work);
 }
 
 template <int M, int P, int MODE, int TX, int TY, int U>
 __global__ void __launch_bounds__(WS_THREADS, 1)
 ws_sweep_batch_kernel(const __grid_constant__ BatchSweepArgs a) {
   const BatchSrc src{&a};
-  ws_sweep_body<M, P, MODE, TX, TY, U, true>(src);
+  ws_sweep_body<M, P, MODE, TX, TY, U, true>(src, a.work);
 }
 
 // Planes per TMA copy of a sweep mode (the z depth of its tensor-map boxes): the lockstep

@@ -62,7 +62,8 @@ struct tdks_system {
   double2 *d_qpart = nullptr;   // gather partial sums, gchunks per (atom, k-batch)
   int gchunks = 1;
   double *staging = nullptr;
-  int *d_err = nullptr;
+  int *d_err = nullptr;       // [0]: error word of the bounded waits; [1]: sweep work counter
+  long obs_count = 0;         // energy/current partial records written by the last first sweep
   // TMA tensor maps over the four sweep inputs (state, t1, t2, t3) for the current tile
   tdks::SweepMaps smaps[4];   // TMA maps of the four Taylor-term sweeps
   bool tmaps_ok = false;
