@@ -807,18 +807,12 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
       }
       l++;
     };
-    int rq = 0;
+    // every item starts at queue rotation 0, so the plane loop runs in unrolled blocks of
+    // QN / U iterations (one full turn of the queue), each with its compile-time rotation
     while (l < nl && !aborted) {
-      switch (rq) {
-#define TDKS_CASE(k)                                                  \
-  case k:                                                             \
-    if constexpr (k % U == 0 && k < QN) iteration(std::integral_constant<int, k>{}); \
-    break;
-        TDKS_CASE(0) TDKS_CASE(1) TDKS_CASE(2) TDKS_CASE(3) TDKS_CASE(4)
-        TDKS_CASE(5) TDKS_CASE(6) TDKS_CASE(7) TDKS_CASE(8) TDKS_CASE(9)
-#undef TDKS_CASE
-      }
-      rq = rq + U >= QN ? rq + U - QN : rq + U;
+      static_for<0, QN / U>([&](auto j) {
+        if (l < nl && !aborted) iteration(std::integral_constant<int, decltype(j)::value * U>{});
+      });
     }
     if (aborted) break;
     if (MODE == MODE_FIRST && do_obs) {
