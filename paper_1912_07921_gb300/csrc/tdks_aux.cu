@@ -266,9 +266,12 @@ cudaError_t launch_gather(int prec, int bloch, const GatherParams &p, cudaStream
 }
 
 // ---------------------------------------------------------------------------------
-// Density contribution of each (k, batch) block: dens_part[kb][r] = w_k f sum_j |psi|^2
-// (n(r) = sum_k w_k sum_i f_i |phi_ik(r)|^2, with closed-shell f_i = 2).  complex64
-// systems hold the state as hi + lo (two complex64 arrays).
+// Density contribution of each (k, batch) block (n(r) = sum_k w_k sum_i f_i |phi_ik(r)|^2,
+// with closed-shell f_i = 2):
+//   complex128 systems: dens_part[kb][r] = w_k f sum_j |psi|^2 (double);
+//   complex64 systems (state hi + lo): the 8-byte slot holds sum_j |psi|^2 unweighted, as a
+//   double-float pair (float hi, float lo); the LDA kernel weights and adds the blocks in
+//   FP64, so the sweeps that produce it run no FP64 instruction.
 // ---------------------------------------------------------------------------------
 __global__ void density_c128_kernel(long N, int n_kb, int n_batches, const double2 *psi, const double *wocc,
                                     double *dens_part) {
@@ -288,6 +291,8 @@ __global__ void density_c128_kernel(long N, int n_kb, int n_batches, const doubl
 __global__ void density_c64_kernel(long N, int n_kb, int n_batches, const float2 *hi, const float2 *lo,
                                    const double *wocc, double *dens_part) {
   const long total = (long)n_kb * N;
+  (void)wocc;
+  (void)n_batches;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
     double s = 0.0;
 #pragma unroll
@@ -296,7 +301,8 @@ __global__ void density_c64_kernel(long N, int n_kb, int n_batches, const float2
       const double re = (double)a.x + (double)b.x, im = (double)a.y + (double)b.y;
       s += re * re + im * im;
     }
-    dens_part[i] = wocc[(int)(i / N) / n_batches] * s;
+    const float sh = (float)s;
+    reinterpret_cast<float2 *>(dens_part)[i] = make_float2(sh, (float)(s - (double)sh));
   }
 }
 
@@ -333,9 +339,9 @@ int lda_blocks(long N) {
 // batches and across threads in FP64; this keeps GB300's slow FP64 pipe out of the loop.
 template <typename R>
 __device__ __forceinline__ void lda_body(long N, int nx, int ny, int nz, double h, int bloch, int n_kb,
-                                         const double *dens_part, const double *vloc, int xc, double Ex, double Ey,
-                                         double Ez, double half_A2, PointAux *aux, double *lda_part, int blk,
-                                         int nblk) {
+                                         int n_batches, const double *wocc, const double *dens_part,
+                                         const double *vloc, int xc, double Ex, double Ey, double Ez,
+                                         double half_A2, PointAux *aux, double *lda_part, int blk, int nblk) {
   constexpr bool F32 = sizeof(R) == 4;
   double acc[6] = {0, 0, 0, 0, 0, 0};
   float fh[6] = {0, 0, 0, 0, 0, 0}, fl[6] = {0, 0, 0, 0, 0, 0};
@@ -345,7 +351,15 @@ __device__ __forceinline__ void lda_body(long N, int nx, int ny, int nz, double 
   const float Exf = (float)Ex, Eyf = (float)Ey, Ezf = (float)Ez, hA2f = (float)half_A2;
   for (long p = blk * (long)blockDim.x + threadIdx.x; p < N; p += (long)nblk * blockDim.x) {
     double n = 0.0;
-    for (int kb = 0; kb < n_kb; kb++) n += dens_part[(long)kb * N + p];
+    if constexpr (F32) {
+      const float2 *d2 = reinterpret_cast<const float2 *>(dens_part);
+      for (int kb = 0; kb < n_kb; kb++) {
+        const float2 d = d2[(long)kb * N + p];
+        n += wocc[kb / n_batches] * ((double)d.x + (double)d.y);
+      }
+    } else {
+      for (int kb = 0; kb < n_kb; kb++) n += dens_part[(long)kb * N + p];
+    }
     const int ix = (int)(p % nx), iy = (int)((p / nx) % ny), iz = (int)(p / ((long)nx * ny));
     if constexpr (F32) {
       const float nf = (float)n;
@@ -393,11 +407,11 @@ __device__ __forceinline__ void lda_body(long N, int nx, int ny, int nz, double 
 
 template <typename R>
 __global__ void __launch_bounds__(LDA_THREADS)
-lda_kernel(long N, int nx, int ny, int nz, double h, int bloch, int n_kb, const double *dens_part,
-           const double *vloc, int xc, double Ex, double Ey, double Ez, double half_A2, PointAux *aux,
-           double *lda_part) {
-  lda_body<R>(N, nx, ny, nz, h, bloch, n_kb, dens_part, vloc, xc, Ex, Ey, Ez, half_A2, aux, lda_part, blockIdx.x,
-              gridDim.x);
+lda_kernel(long N, int nx, int ny, int nz, double h, int bloch, int n_kb, int n_batches, const double *wocc,
+           const double *dens_part, const double *vloc, int xc, double Ex, double Ey, double Ez, double half_A2,
+           PointAux *aux, double *lda_part) {
+  lda_body<R>(N, nx, ny, nz, h, bloch, n_kb, n_batches, wocc, dens_part, vloc, xc, Ex, Ey, Ez, half_A2, aux,
+              lda_part, blockIdx.x, gridDim.x);
 }
 
 // Laser field of a batched system at time t (finite boxes: length gauge or none).
@@ -426,8 +440,8 @@ lda_batch_kernel(const BatchAux *aux, const BatchClock *clk, const long *begin, 
   }
   __syncthreads();
   const double E = f;
-  lda_body<R>(a.N, a.nx, a.ny, a.nz, a.h, 0, a.n_kb, a.dens_part, a.vloc, a.xc, E * a.pol[0], E * a.pol[1],
-              E * a.pol[2], 0.0, a.aux, a.lda_part, (int)(blockIdx.x - begin[s]),
+  lda_body<R>(a.N, a.nx, a.ny, a.nz, a.h, 0, a.n_kb, a.n_batches, a.wocc, a.dens_part, a.vloc, a.xc,
+              E * a.pol[0], E * a.pol[1], E * a.pol[2], 0.0, a.aux, a.lda_part, (int)(blockIdx.x - begin[s]),
               a.n_lda);
 }
 
@@ -438,15 +452,15 @@ cudaError_t launch_lda_batch(int prec, const BatchAux *aux, const BatchClock *cl
   return cudaGetLastError();
 }
 
-cudaError_t launch_lda(int prec, int bloch, long N, int nx, int ny, int nz, double h, int n_kb,
-                       const double *dens_part, const double *vloc, int xc, const double E[3],
+cudaError_t launch_lda(int prec, int bloch, long N, int nx, int ny, int nz, double h, int n_kb, int n_batches,
+                       const double *wocc, const double *dens_part, const double *vloc, int xc, const double E[3],
                        double half_A2, PointAux *aux, double *lda_part, int n_blocks, cudaStream_t s) {
   if (prec == P_C64)
-    lda_kernel<float><<<n_blocks, LDA_THREADS, 0, s>>>(N, nx, ny, nz, h, bloch, n_kb, dens_part, vloc, xc,
-                                                       E[0], E[1], E[2], half_A2, aux, lda_part);
+    lda_kernel<float><<<n_blocks, LDA_THREADS, 0, s>>>(N, nx, ny, nz, h, bloch, n_kb, n_batches, wocc, dens_part,
+                                                       vloc, xc, E[0], E[1], E[2], half_A2, aux, lda_part);
   else
-    lda_kernel<double><<<n_blocks, LDA_THREADS, 0, s>>>(N, nx, ny, nz, h, bloch, n_kb, dens_part, vloc, xc,
-                                                        E[0], E[1], E[2], half_A2, aux, lda_part);
+    lda_kernel<double><<<n_blocks, LDA_THREADS, 0, s>>>(N, nx, ny, nz, h, bloch, n_kb, n_batches, wocc, dens_part,
+                                                        vloc, xc, E[0], E[1], E[2], half_A2, aux, lda_part);
   return cudaGetLastError();
 }
 

@@ -178,6 +178,7 @@ int tdks_batch_create(const tdks_sys *systems, int n, void *stream, tdks_batch_t
     lda_begin[i + 1] = lda_begin[i] + nl;
     BatchAux &a = aux[i];
     a.N = s->N; a.nx = s->nx; a.ny = s->ny; a.nz = s->nz; a.n_kb = s->n_kb; a.xc = s->xc;
+    a.n_batches = s->n_batches; a.wocc = s->d_wocc;
     a.h = s->h; a.occ = s->occ; a.gauge = s->gauge; a.envelope = s->envelope;
     for (int d = 0; d < 3; d++) a.pol[d] = s->pol[d];
     a.amp = s->amp; a.omega = s->omega; a.t_total = s->t_total;

@@ -318,8 +318,8 @@ int run_lda(tdks_system *s, const double E[3], const double A[3]) {
                         s->gauge == TDKS_GAUGE_LENGTH ? E[2] : 0.0};
   Timed tm(s, 2);
   cudaError_t e = launch_lda(s->prec, s->bc == TDKS_BC_BLOCH, s->N, s->nx, s->ny, s->nz, s->h, s->n_kb,
-                             s->dens_part, s->vloc, s->xc, El, half_A2, s->aux, s->lda_part, lda_blocks(s->N),
-                             s->stream);
+                             s->n_batches, s->d_wocc, s->dens_part, s->vloc, s->xc, El, half_A2, s->aux,
+                             s->lda_part, lda_blocks(s->N), s->stream);
   s->launches++;
   if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("lda: ") + cudaGetErrorString(e));
   return TDKS_OK;

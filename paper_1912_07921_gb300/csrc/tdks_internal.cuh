@@ -77,7 +77,8 @@ struct SweepParams {
   int do_obs;
   double *obs_part;           // [n_items][4]: <psi|H psi> weighted, current x,y,z
   const double *wocc;         // [n_k] k-weight times occupation
-  double *dens_part;          // [n_kb][N] (MODE_LAST)
+  double *dens_part;          // [n_kb][N] (MODE_LAST): w_k f sum |psi|^2 (complex128); for
+                              // complex64, the unweighted sum as a (float hi, float lo) pair
   int *err;                   // device error word (bounded waits that ran out set it)
   unsigned int *work;         // work-item counter of the warp-specialised TMA sweep (zero
                               // between launches: the launch's last claim resets it)
@@ -115,8 +116,9 @@ struct GatherParams {
 // Per-system data of a batch (device copies), for the batched LDA and finalise kernels.
 struct BatchAux {
   long N;
-  int nx, ny, nz, n_kb, xc;
+  int nx, ny, nz, n_kb, n_batches, xc;
   double h, occ;
+  const double *wocc;       // [n_k] k-weight times occupation
   int gauge, envelope;
   double pol[3], amp, omega, t_total;
   const double *dens_part;
@@ -177,7 +179,8 @@ int gather_chunks(long units);
 cudaError_t launch_density(int prec, long N, int n_kb, int n_batches, const void *psi, const void *psi_lo,
                            const double *wocc, double *dens_part, cudaStream_t s);
 cudaError_t launch_lda(int prec, int bloch, long N, int nx, int ny, int nz, double h,
-                       int n_kb, const double *dens_part, const double *vloc, int xc,
+                       int n_kb, int n_batches, const double *wocc, const double *dens_part,
+                       const double *vloc, int xc,
                        const double E[3], double half_A2, PointAux *aux, double *lda_part,
                        int n_blocks, cudaStream_t s);
 cudaError_t launch_finalize(const double *obs_part, long n_items, const double *lda_part,

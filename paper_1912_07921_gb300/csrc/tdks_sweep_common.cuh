@@ -137,7 +137,7 @@ __device__ __forceinline__ void finish_point(const Epi &ep, typename VT<P>::S CR
       if (P == P_C64) reinterpret_cast<V *>(ep.psi_lo)[idx] = lo_out;
     }
     Combine<P>::reduce4(dh, dl);
-    if (own && v == 0) ep.dens_part[idx / OVC] = ep.wocc * Combine<P>::value(dh, dl);
+    if (own && v == 0) Combine<P>::store_density(ep.dens_part + idx / OVC, ep.wocc, dh, dl);
   }
 }
 

@@ -168,6 +168,11 @@ template <> struct Combine<P_C128> {
     (void)l;
   }
   static __device__ __forceinline__ double value(A h, A l) { (void)l; return h; }
+  // the point's density partial: w_k f sum |psi|^2 in FP64
+  static __device__ __forceinline__ void store_density(double *slot, double wocc, A h, A l) {
+    (void)l;
+    *slot = wocc * h;
+  }
 };
 
 template <> struct Combine<P_C64> {
@@ -207,6 +212,12 @@ template <> struct Combine<P_C64> {
     }
   }
   static __device__ __forceinline__ double value(A h, A l) { return (double)h + (double)l; }
+  // the point's density partial: sum |psi|^2 unweighted, as the pair (h, l) in the 8-byte
+  // slot (the LDA kernel forms w_k f ((double)h + (double)l)); no FP64 instruction here
+  static __device__ __forceinline__ void store_density(double *slot, double wocc, A h, A l) {
+    (void)wocc;
+    *reinterpret_cast<float2 *>(slot) = make_float2(h, l);
+  }
 };
 
 }  // namespace tdks
