@@ -96,8 +96,10 @@ int tdks_destroy(tdks_sys sys);
 /* V_loc: host array [nz][ny][nx] of doubles (Ha), copied. */
 int tdks_set_local_potential(tdks_sys sys, const double *v);
 
-/* Orbitals: host array in the host layout (2 * n_k * N * n_orb doubles), copied and
- * packed on the device; the density of the new state is rebuilt on first use. */
+/* Orbitals: host array in the host layout (2 * n_k * N * n_orb doubles), copied (the call
+ * returns once the buffer has been read; pinned memory gives the fastest upload) and packed
+ * on the device in chunks that overlap the copy, together with the density of the new
+ * state.  The packing is asynchronous on the system's stream. */
 int tdks_set_orbitals(tdks_sys sys, const double *psi);
 
 /* Copy the current orbitals out into the host layout.  Synchronises. */

@@ -596,6 +596,68 @@ __global__ void pack_kernel(int to_internal, int c64, long N, int n_k, int n_orb
   }
 }
 
+// Host layout -> internal layout for the points [pt0, pt0 + npts) of k-point k, with the
+// density partials of those points (the values launch_density would write), so a state
+// set from the host needs no separate density pass.  Thread = one orbital value of one
+// (batch, point): the BS threads of a point are adjacent lanes, so reads and writes are
+// contiguous, and they add their |psi|^2 with shuffles in the density kernel's order.
+__global__ void pack_in_kernel(int c64, long N, int k, long pt0, long npts, int n_orb, int n_batches, int BS,
+                               const double2 *plain, void *internal, void *internal_lo, const double *wocc,
+                               double *dens_part) {
+  const long total = (long)n_batches * npts * BS;
+  const long stride = (long)gridDim.x * blockDim.x;  // a multiple of 32, so lanes keep their j
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i - threadIdx.x % 32 < total; i += stride) {
+    const bool live = i < total;
+    const int j = (int)(i % BS);
+    const long q = i / BS;
+    const long pt = pt0 + q % npts;
+    const int b = (int)(q / npts);
+    const long kb = (long)k * n_batches + b;
+    const int o = b * BS + j;
+    const double2 x = live && o < n_orb ? plain[((long)k * N + pt) * n_orb + o] : make_double2(0.0, 0.0);
+    const long dst = (kb * N + pt) * BS + j;
+    double s;
+    if (c64) {
+      const float hx = (float)x.x, hy = (float)x.y;
+      const float lx = (float)(x.x - (double)hx), ly = (float)(x.y - (double)hy);
+      if (live) {
+        reinterpret_cast<float2 *>(internal)[dst] = make_float2(hx, hy);
+        reinterpret_cast<float2 *>(internal_lo)[dst] = make_float2(lx, ly);
+      }
+      const double re = (double)hx + (double)lx, im = (double)hy + (double)ly;
+      s = re * re + im * im;
+    } else {
+      if (live) reinterpret_cast<double2 *>(internal)[dst] = x;
+      s = x.x * x.x + x.y * x.y;
+    }
+    // lane j of the point gathers the sum over the point's values in index order
+    double acc = 0.0;
+    for (int t = 0; t < BS; t++) acc += __shfl_sync(0xffffffffu, s, (threadIdx.x & 31 & ~(BS - 1)) + t);
+    if (live && j == 0) {
+      if (c64) {
+        const float sh = (float)acc;
+        reinterpret_cast<float2 *>(dens_part)[kb * N + pt] = make_float2(sh, (float)(acc - (double)sh));
+      } else {
+        dens_part[kb * N + pt] = wocc[k] * acc;
+      }
+    }
+  }
+}
+
+cudaError_t launch_pack_in(int prec, long N, int k, long pt0, long npts, int n_orb, int n_batches,
+                           const double *plain, void *internal, void *internal_lo, const double *wocc,
+                           double *dens_part, cudaStream_t s) {
+  const int BS = prec == P_C64 ? 2 * OVC : OVC;
+  const long total = (long)n_batches * npts * BS;
+  long g = (total + 255) / 256;
+  if (g > 152 * 32) g = 152 * 32;
+  if (g <= 0) return cudaSuccess;
+  pack_in_kernel<<<(int)g, 256, 0, s>>>(prec == P_C64, N, k, pt0, npts, n_orb, n_batches, BS,
+                                        reinterpret_cast<const double2 *>(plain), internal, internal_lo, wocc,
+                                        dens_part);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pack(int prec, int to_internal, long N, int n_k, int n_orb, int n_batches, void *internal,
                         void *internal_lo, double *plain, cudaStream_t s) {
   const int BS = prec == P_C64 ? 2 * OVC : OVC;

@@ -504,6 +504,9 @@ int tdks_destroy(tdks_sys s) {
   cudaFree(s->vloc); cudaFree(s->aux); cudaFree(s->dens_part); cudaFree(s->lda_part);
   cudaFree(s->obs_part); cudaFree(s->ring); cudaFree(s->obs_rec); cudaFree(s->d_kvec); cudaFree(s->d_wocc);
   cudaFree(s->staging);
+  if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
+  if (s->ev_upload_ready) cudaEventDestroy(s->ev_upload_ready);
+  for (auto e : s->ev_chunk) cudaEventDestroy(e);
   for (auto &u : s->ev_used) { cudaEventDestroy(u.second.first); cudaEventDestroy(u.second.second); }
   for (auto e : s->ev_free) cudaEventDestroy(e);
   delete s;
@@ -526,15 +529,47 @@ static int ensure_staging(tdks_system *s) {
   return TDKS_OK;
 }
 
+// The upload runs in chunks (point ranges of each k-point) on a copy stream; each chunk is
+// packed into the internal layout, with its density partials, on the system stream as soon
+// as it has landed, so packing overlaps the remaining copies.
+constexpr int UPLOAD_CHUNKS = 8;
+
 int tdks_set_orbitals(tdks_sys s, const double *psi) {
   if (!s || !psi) return fail(TDKS_EINVAL, "NULL argument");
   int rc = ensure_staging(s);
   if (rc) return rc;
-  CU(cudaMemcpyAsync(s->staging, psi, (size_t)s->n_k * s->N * s->n_orb * 16, cudaMemcpyHostToDevice, s->stream));
-  CU(launch_pack(s->prec, 1, s->N, s->n_k, s->n_orb, s->n_batches, s->psi, s->psi_lo, s->staging, s->stream));
-  s->launches++;
+  const int per_k = std::max(1, (UPLOAD_CHUNKS + s->n_k - 1) / s->n_k);
+  const int n_chunks = per_k * s->n_k;
+  if (!s->copy_stream) {
+    CU(cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking));
+    CU(cudaEventCreateWithFlags(&s->ev_upload_ready, cudaEventDisableTiming));
+  }
+  while ((int)s->ev_chunk.size() < n_chunks) {
+    cudaEvent_t e;
+    CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    s->ev_chunk.push_back(e);
+  }
+  // the copies overwrite the staging buffer only after earlier work of the system reading it
+  CU(cudaEventRecord(s->ev_upload_ready, s->stream));
+  CU(cudaStreamWaitEvent(s->copy_stream, s->ev_upload_ready, 0));
+  const long len = (s->N + per_k - 1) / per_k;
+  int c = 0;
+  for (int k = 0; k < s->n_k; k++)
+    for (long pt0 = 0; pt0 < s->N; pt0 += len, c++) {
+      const long npts = std::min(len, s->N - pt0);
+      const size_t off = ((size_t)k * s->N + pt0) * s->n_orb * 2;  // doubles
+      CU(cudaMemcpyAsync(s->staging + off, psi + off, (size_t)npts * s->n_orb * 16, cudaMemcpyHostToDevice,
+                         s->copy_stream));
+      CU(cudaEventRecord(s->ev_chunk[c], s->copy_stream));
+      CU(cudaStreamWaitEvent(s->stream, s->ev_chunk[c], 0));
+      CU(launch_pack_in(s->prec, s->N, k, pt0, npts, s->n_orb, s->n_batches, s->staging, s->psi, s->psi_lo,
+                        s->d_wocc, s->dens_part, s->stream));
+      s->launches++;
+    }
+  // the host buffer has been read once the copies are done ("copied")
+  CU(cudaStreamSynchronize(s->copy_stream));
   s->have_orbitals = true;
-  s->dens_valid = false;
+  s->dens_valid = true;
   return TDKS_OK;
 }
 

@@ -187,6 +187,10 @@ cudaError_t launch_finalize(const double *obs_part, long n_items, const double *
                             int n_lda_blocks, double *record, double t_state, double h3,
                             double occ, int bloch, double omega_cell, const double A[3],
                             double field_val, cudaStream_t s);
+// host layout -> internal layout and density partials, points [pt0, pt0 + npts) of k-point k
+cudaError_t launch_pack_in(int prec, long N, int k, long pt0, long npts, int n_orb, int n_batches,
+                           const double *plain, void *internal, void *internal_lo, const double *wocc,
+                           double *dens_part, cudaStream_t s);
 cudaError_t launch_pack(int prec, int to_internal, long N, int n_k, int n_orb, int n_batches,
                         void *internal, void *internal_lo, double *plain, cudaStream_t s);
 

@@ -62,6 +62,9 @@ struct tdks_system {
   double2 *d_qpart = nullptr;   // gather partial sums, gchunks per (atom, k-batch)
   int gchunks = 1;
   double *staging = nullptr;
+  cudaStream_t copy_stream = nullptr;  // host uploads, chunked so that packing overlaps them
+  cudaEvent_t ev_upload_ready = nullptr;
+  std::vector<cudaEvent_t> ev_chunk;
   int *d_err = nullptr;       // [0]: error word of the bounded waits; [1]: sweep work counter
   long obs_count = 0;         // energy/current partial records written by the last first sweep
   // TMA tensor maps over the four sweep inputs (state, t1, t2, t3) for the current tile
