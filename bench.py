@@ -38,7 +38,8 @@ METRIC = "H.psi orbital-gridpoint updates/s (medium molecule, Taylor-4 step)"
 UNIT = "updates/s"
 
 
-SWEEP_SOURCES = ["tdks_sweep_tma.cu", "tdks_sweep_common.cuh", "tdks_vec.cuh", "tdks_internal.cuh"]
+SWEEP_SOURCES = ["tdks_sweep_tma.cu", "tdks_tma.cuh", "tdks_sweep_ws1.cu", "tdks_sweep_ws2.cu", "tdks_sweep_ws3.cu",
+                 "tdks_sweep_ws4.cu", "tdks_sweep_common.cuh", "tdks_vec.cuh", "tdks_internal.cuh"]
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "tma_sweep_medium_molecule.md")
 
 
@@ -172,7 +173,7 @@ def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_1912_07921_gb300 import inputs as I
-    from paper_1912_07921_gb300.system import System
+    from paper_1912_07921_gb300.system import System, shape_count, shape_info
     import __graft_entry__
 
     torch.cuda.set_device(local_rank)
@@ -189,6 +190,13 @@ def run_ours(args, rank, world, local_rank):
     sysm = System(spec, inp, stream=stream.cuda_stream)
     if args.sweep_path:
         sysm.set_sweep_path(args.sweep_path)
+    tune = None
+    if args.shape >= 0:
+        sysm.set_sweep_shape(-1, args.shape)
+    elif not args.no_tune:
+        # the autotuner times every tile shape on each Taylor-term sweep of this system
+        # (outside the timed region) and keeps the fastest per sweep
+        tune = sysm.autotune(reps=5)
     subs = spec.substeps
     dt = spec.dt
     upd_per_step = spec.n_points * spec.n_orb
@@ -265,6 +273,12 @@ def run_ours(args, rank, world, local_rank):
                          "bytes_per_launch": per_launch_bytes, "avg_launch_us": avg_launch_s * 1e6},
             "kernel_ms": {"sweep": sweep_ms, "sweep_launches": sweep_n, "projector": gath_ms,
                           "projector_steps": gath_n, "density_lda_finalize": aux_ms, "aux_launches": aux_n},
+            "sweep_shapes": {"chosen": sysm.sweep_shapes(),
+                             "autotune_ms_per_launch": None if tune is None else
+                             [[round(float(x), 4) for x in r] for r in tune],
+                             "shapes": [list(shape_info(i)) for i in range(shape_count())],
+                             "legend": "shape = (tile tx, ty, points per thread, consumer warps); "
+                                       "ms[shape][sweep], sweeps t1..t4"},
             "gpu_launches": launches,
             "clocks": clk.summary(),
             "e2e": {"value": whole_job_rate(upd_per_step * e2e_steps, world, e2e_s), "unit": UNIT,
@@ -456,6 +470,8 @@ def main():
                     help="also run a serving trace with this many jobs")
     ap.add_argument("--n-orb", type=int, default=0,
                     help="orbital count override (profiling on a smaller case); 0 = the workload's 64")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default sweep tile shape (no autotuner)")
+    ap.add_argument("--shape", type=int, default=-1, help="force one sweep tile shape for all Taylor terms")
     ap.add_argument("--sweep-path", type=int, default=0,
                     help="stencil sweep variant: 0 warp-specialised TMA (default), 1 general, 2 lockstep TMA")
     args = ap.parse_args()

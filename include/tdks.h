@@ -209,6 +209,34 @@ int tdks_set_tile(tdks_sys sys, int tx, int ty, int zc);
 int tdks_set_sweep_path(tdks_sys sys, int path);
 
 /*
+ * Tile shapes of the warp-specialised TMA sweep (path 0, finite boxes, 16x8 system tile)
+ * and the autotuner that picks one per Taylor-term sweep.  No passage of the paper
+ * defines these: they choose how the stencil (Sec. "Maxwell ... coupling", finite
+ * differences on a uniform grid) is tiled on the GPU and do not change its values (each
+ * point's arithmetic and order of terms is the same in every shape; energy and current
+ * partial sums are grouped per consumer warp, so those change in the last bits).
+ *
+ * tdks_sweep_shape_info: shape s (0 .. count-1) covers tx x ty points of one orbital batch
+ * per work item with `warps` consumer warps, each thread computing `rows` y-adjacent
+ * points.  *count (if not NULL) receives the number of shapes; tx/ty/rows/warps may be
+ * NULL.  TDKS_EINVAL for a shape out of range.
+ */
+int tdks_sweep_shape_info(int shape, int *count, int *tx, int *ty, int *rows, int *warps);
+/* Shape of Taylor-term sweep `sweep` (0 = t1 from psi, 1 = t2, 2 = t3, 3 = t4 and the
+ * combine), or of all four when sweep = -1.  Synchronises the system's stream. */
+int tdks_set_sweep_shape(tdks_sys sys, int sweep, int shape);
+int tdks_get_sweep_shape(tdks_sys sys, int sweep, int *shape);
+/* Autotuner: times every shape on each of the four Taylor-term sweeps of this system, on
+ * its own grid, orbitals and projectors (reps launches each after one warm-up launch, CUDA
+ * events on the system's stream), and keeps the fastest shape per sweep.  The state psi is
+ * not changed; the Taylor-term buffers and the density partials are overwritten (the next
+ * propagation or H application rebuilds them).  ms (if not NULL) receives the mean
+ * milliseconds per launch as ms[shape * 4 + sweep] (count * 4 values).  Systems that do not
+ * take the warp-specialised sweep keep their settings and ms is filled with -1.
+ * Synchronises; TDKS_ETIMEOUT if a sweep gave up waiting for its copies. */
+int tdks_autotune(tdks_sys sys, int reps, double *ms);
+
+/*
  * Batched propagation of many independent finite-box systems (uneven grids, orbital and
  * atom counts), the many-systems workload: per Taylor term one persistent sweep launch
  * walks the work items of every system, with one batched projector gather, one batched

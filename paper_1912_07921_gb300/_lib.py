@@ -36,6 +36,10 @@ SIGNATURES = {
     "tdks_launch_count": ([P, PLL], I),
     "tdks_set_tile": ([P, I, I, I], I),
     "tdks_set_sweep_path": ([P, I], I),
+    "tdks_sweep_shape_info": ([I, PI, PI, PI, PI, PI], I),
+    "tdks_set_sweep_shape": ([P, I, I], I),
+    "tdks_get_sweep_shape": ([P, I, PI], I),
+    "tdks_autotune": ([P, I, PD], I),
     "tdks_set_clock": ([P, D, D, I], I),
     "tdks_get_clock": ([P, PD, PLL], I),
     "tdks_batch_create": ([P, I, P, ctypes.POINTER(P)], I),

@@ -38,29 +38,37 @@ __device__ __forceinline__ void gather_body(const GatherParams &p, int a, int kb
   const int e0 = a0 + chunk * len, e1 = min(a1, e0 + len);
   const bool phase = BLOCH || (p.A[0] != 0.0 || p.A[1] != 0.0 || p.A[2] != 0.0);
   for (int e = e0 + lane; e < e1; e += LANES) {
-    const ProjEntry &E = p.ent[e];
-    const long pt = (long)kb * p.N + E.cell;
-    const V x = T::ld(reinterpret_cast<const V *>(p.in) + pt * OVC + v);
-    double ang = 0.0;
-    if (phase) {
-      ang = p.A[0] * E.d[0] + p.A[1] * E.d[1] + p.A[2] * E.d[2];
-      if (BLOCH) ang += p.kvec[3 * kidx] * E.T[0] + p.kvec[3 * kidx + 1] * E.T[1] + p.kvec[3 * kidx + 2] * E.T[2];
-    }
     if constexpr (P == P_C64) {
+      // compact entry arrays: 8 + 16 bytes per entry instead of the full record
+      const int2 ca = p.ent_ca[e];
+      const float4 b4 = p.ent_beta[e];
+      const V x = T::ld(reinterpret_cast<const V *>(p.in) + ((long)kb * p.N + ca.x) * OVC + v);
       float c = 1.f, s = 0.f;
-      if (phase) sincosf((float)ang, &s, &c);
+      if (phase) {
+        const ProjEntry &E = p.ent[e];
+        double ang = p.A[0] * E.d[0] + p.A[1] * E.d[1] + p.A[2] * E.d[2];
+        if (BLOCH) ang += p.kvec[3 * kidx] * E.T[0] + p.kvec[3 * kidx + 1] * E.T[1] + p.kvec[3 * kidx + 2] * E.T[2];
+        sincosf((float)ang, &s, &c);
+      }
       const float2 x0 = up2(x.x), x1 = up2(x.y);
       const float2 y0 = make_float2(c * x0.x - s * x0.y, c * x0.y + s * x0.x);
       const float2 y1 = make_float2(c * x1.x - s * x1.y, c * x1.y + s * x1.x);
+      const float b[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
       for (int j = 0; j < 4; j++) {
-        const float b = E.beta[j];
-        accf[j][0].x = fmaf(b, y0.x, accf[j][0].x); accf[j][0].y = fmaf(b, y0.y, accf[j][0].y);
-        accf[j][1].x = fmaf(b, y1.x, accf[j][1].x); accf[j][1].y = fmaf(b, y1.y, accf[j][1].y);
+        accf[j][0].x = fmaf(b[j], y0.x, accf[j][0].x); accf[j][0].y = fmaf(b[j], y0.y, accf[j][0].y);
+        accf[j][1].x = fmaf(b[j], y1.x, accf[j][1].x); accf[j][1].y = fmaf(b[j], y1.y, accf[j][1].y);
       }
     } else {
+      const ProjEntry &E = p.ent[e];
+      const long pt = (long)kb * p.N + E.cell;
+      const V x = T::ld(reinterpret_cast<const V *>(p.in) + pt * OVC + v);
       double c = 1.0, s = 0.0;
-      if (phase) sincos(ang, &s, &c);
+      if (phase) {
+        double ang = p.A[0] * E.d[0] + p.A[1] * E.d[1] + p.A[2] * E.d[2];
+        if (BLOCH) ang += p.kvec[3 * kidx] * E.T[0] + p.kvec[3 * kidx + 1] * E.T[1] + p.kvec[3 * kidx + 2] * E.T[2];
+        sincos(ang, &s, &c);
+      }
       const double2 xd = *reinterpret_cast<const double2 *>(&x);
       const double xr = c * xd.x - s * xd.y, xi = c * xd.y + s * xd.x;
 #pragma unroll
@@ -70,18 +78,32 @@ __device__ __forceinline__ void gather_body(const GatherParams &p, int a, int kb
       }
     }
   }
-  // reduce over lanes with equal v: lanes differ in bits 2..4 of the lane id, then warps
+  // reduce over lanes with equal v (they differ in bits 2..4 of the lane id), then over the
+  // warps in a fixed order.  complex64: the lane sums are FP32 (as the per-lane sums), so
+  // the shuffles stay off GB300's slow FP64 pipe; the warp partials are FP64.
   __shared__ double2 red[GATHER_THREADS / 32][4][OVC][2];
 #pragma unroll
   for (int j = 0; j < 4; j++)
 #pragma unroll
     for (int cc = 0; cc < 2; cc++) {
-      double2 x = P == P_C64 ? make_double2(accf[j][cc].x, accf[j][cc].y) : (cc == 0 ? accd[j] : make_double2(0, 0));
-      for (int o = 4; o < 32; o <<= 1) {
-        x.x += __shfl_xor_sync(0xffffffffu, x.x, o);
-        x.y += __shfl_xor_sync(0xffffffffu, x.y, o);
+      if constexpr (P == P_C64) {
+        float2 x = accf[j][cc];
+        for (int o = 4; o < 32; o <<= 1) {
+          x.x += __shfl_xor_sync(0xffffffffu, x.x, o);
+          x.y += __shfl_xor_sync(0xffffffffu, x.y, o);
+        }
+        if ((tid & 31) < OVC) red[tid >> 5][j][v][cc] = make_double2(x.x, x.y);
+      } else if (cc == 0) {
+        double2 x = accd[j];
+        for (int o = 4; o < 32; o <<= 1) {
+          x.x += __shfl_xor_sync(0xffffffffu, x.x, o);
+          x.y += __shfl_xor_sync(0xffffffffu, x.y, o);
+        }
+        if ((tid & 31) < OVC) {
+          red[tid >> 5][j][v][0] = x;
+          red[tid >> 5][j][v][1] = make_double2(0.0, 0.0);
+        }
       }
-      if ((tid & 31) < OVC) red[tid >> 5][j][v][cc] = x;
     }
   __syncthreads();
   if (tid < 4 * OVC) {
@@ -147,26 +169,33 @@ __device__ __forceinline__ void nl_body(const GatherParams &p, long t, int kb) {
   const bool phase = BLOCH || (p.A[0] != 0.0 || p.A[1] != 0.0 || p.A[2] != 0.0);
   V acc = T::zero();
   for (int e = r.x; e < r.y; e++) {
-    const ProjEntry &E = p.ent[p.rowent[e]];
-    const V *qa = reinterpret_cast<const V *>(p.q) + ((long)(kb * p.n_atoms + E.atom) * 4) * OVC + v;
+    const int ei = p.rowent[e];
     V x;
     if constexpr (P == P_C64) {
-      x = T::mul(T::coef(0.0, E.beta[0]), T::ld(qa));
-#pragma unroll
-      for (int j = 1; j < 4; j++) x = T::fma(T::coef(0.0, E.beta[j]), T::ld(qa + j * OVC), x);
-    } else {
-      x = T::mul(E.betad[0], T::ld(qa));
-#pragma unroll
-      for (int j = 1; j < 4; j++) x = T::fma(E.betad[j], T::ld(qa + j * OVC), x);
-    }
-    if (phase) {
-      double ang = p.A[0] * E.d[0] + p.A[1] * E.d[1] + p.A[2] * E.d[2];
-      if (BLOCH) ang += p.kvec[3 * kidx] * E.T[0] + p.kvec[3 * kidx + 1] * E.T[1] + p.kvec[3 * kidx + 2] * E.T[2];
-      if constexpr (P == P_C64) {
+      const int2 ca = p.ent_ca[ei];
+      const float4 b4 = p.ent_beta[ei];
+      const V *qa = reinterpret_cast<const V *>(p.q) + ((long)(kb * p.n_atoms + ca.y) * 4) * OVC + v;
+      x = T::mul(T::coef(0.0, b4.x), T::ld(qa));
+      x = T::fma(T::coef(0.0, b4.y), T::ld(qa + OVC), x);
+      x = T::fma(T::coef(0.0, b4.z), T::ld(qa + 2 * OVC), x);
+      x = T::fma(T::coef(0.0, b4.w), T::ld(qa + 3 * OVC), x);
+      if (phase) {
+        const ProjEntry &E = p.ent[ei];
+        double ang = p.A[0] * E.d[0] + p.A[1] * E.d[1] + p.A[2] * E.d[2];
+        if (BLOCH) ang += p.kvec[3 * kidx] * E.T[0] + p.kvec[3 * kidx + 1] * E.T[1] + p.kvec[3 * kidx + 2] * E.T[2];
         float sn, cs;
         sincosf((float)ang, &sn, &cs);
         x = T::cmul(pk2(cs, cs), pk2(-sn, -sn), x);
-      } else {
+      }
+    } else {
+      const ProjEntry &E = p.ent[ei];
+      const V *qa = reinterpret_cast<const V *>(p.q) + ((long)(kb * p.n_atoms + E.atom) * 4) * OVC + v;
+      x = T::mul(E.betad[0], T::ld(qa));
+#pragma unroll
+      for (int j = 1; j < 4; j++) x = T::fma(E.betad[j], T::ld(qa + j * OVC), x);
+      if (phase) {
+        double ang = p.A[0] * E.d[0] + p.A[1] * E.d[1] + p.A[2] * E.d[2];
+        if (BLOCH) ang += p.kvec[3 * kidx] * E.T[0] + p.kvec[3 * kidx + 1] * E.T[1] + p.kvec[3 * kidx + 2] * E.T[2];
         double sn, cs;
         sincos(ang, &sn, &cs);
         x = T::cmul(cs, -sn, x);
@@ -334,15 +363,28 @@ int lda_blocks(long N) {
 }
 
 // complex128 systems: everything in FP64.
-// complex64 systems (V_eff is FP32 there): v_x and V_eff in FP32, the per-point terms of the
-// observables in FP32 accumulated as double-float per thread, the sums over k-point
-// batches and across threads in FP64; this keeps GB300's slow FP64 pipe out of the loop.
+// complex64 systems (V_eff is FP32 there): the density is summed over the k-point batches
+// as double-float (two FP32 numbers, ~44-bit significand) and weighted by w_k f split into
+// two floats; v_x and V_eff in FP32; the per-point terms of the observables in FP32
+// accumulated as double-float per thread; the sums across threads in FP64.  This keeps
+// GB300's slow FP64 pipe out of the per-point loop.
+constexpr int LDA_MAXK = 256;  // k-points whose split weights are staged in shared memory
+
 template <typename R>
 __device__ __forceinline__ void lda_body(long N, int nx, int ny, int nz, double h, int bloch, int n_kb,
                                          int n_batches, const double *wocc, const double *dens_part,
                                          const double *vloc, int xc, double Ex, double Ey, double Ez,
                                          double half_A2, PointAux *aux, double *lda_part, int blk, int nblk) {
   constexpr bool F32 = sizeof(R) == 4;
+  const int n_k = n_kb / n_batches;
+  __shared__ float2 s_w[LDA_MAXK];  // complex64: w_k f = hi + lo
+  if constexpr (F32) {
+    for (int k = threadIdx.x; k < n_k && k < LDA_MAXK; k += blockDim.x) {
+      const float hi = (float)wocc[k];
+      s_w[k] = make_float2(hi, (float)(wocc[k] - (double)hi));
+    }
+    __syncthreads();
+  }
   double acc[6] = {0, 0, 0, 0, 0, 0};
   float fh[6] = {0, 0, 0, 0, 0, 0}, fl[6] = {0, 0, 0, 0, 0, 0};
   const double cx = bloch ? 0.0 : 0.5 * (nx - 1), cy = bloch ? 0.0 : 0.5 * (ny - 1),
@@ -351,18 +393,33 @@ __device__ __forceinline__ void lda_body(long N, int nx, int ny, int nz, double 
   const float Exf = (float)Ex, Eyf = (float)Ey, Ezf = (float)Ez, hA2f = (float)half_A2;
   for (long p = blk * (long)blockDim.x + threadIdx.x; p < N; p += (long)nblk * blockDim.x) {
     double n = 0.0;
+    float nh = 0.f, nl = 0.f;  // complex64: n = nh + nl
     if constexpr (F32) {
       const float2 *d2 = reinterpret_cast<const float2 *>(dens_part);
-      for (int kb = 0; kb < n_kb; kb++) {
-        const float2 d = d2[(long)kb * N + p];
-        n += wocc[kb / n_batches] * ((double)d.x + (double)d.y);
+      for (int k = 0; k < n_k; k++) {
+        float sh = 0.f, sl = 0.f;  // sum over the k-point's batches of sum |psi|^2
+        for (int b = 0; b < n_batches; b++) {
+          const float2 d = d2[(long)(k * n_batches + b) * N + p];
+          df_add_df(sh, sl, d.x, d.y);
+        }
+        float2 w;
+        if (k < LDA_MAXK) {
+          w = s_w[k];
+        } else {
+          const float hi = (float)wocc[k];
+          w = make_float2(hi, (float)(wocc[k] - (double)hi));
+        }
+        // (sh + sl)(w.x + w.y): the leading product exactly (FMA residual), the cross terms rounded
+        const float ph = sh * w.x;
+        const float pl = fmaf(sh, w.x, -ph) + (sh * w.y + sl * w.x);
+        df_add_df(nh, nl, ph, pl);
       }
     } else {
       for (int kb = 0; kb < n_kb; kb++) n += dens_part[(long)kb * N + p];
     }
     const int ix = (int)(p % nx), iy = (int)((p / nx) % ny), iz = (int)(p / ((long)nx * ny));
     if constexpr (F32) {
-      const float nf = (float)n;
+      const float nf = nh;
       const float x = (ix - cxf) * hf, y = (iy - cyf) * hf, z = (iz - czf) * hf;
       const float vx = xc ? -cbrtf(3.0f * nf * 0.318309886f) : 0.0f;
       float v = (float)vloc[p] + vx + hA2f;
@@ -371,7 +428,7 @@ __device__ __forceinline__ void lda_body(long N, int nx, int ny, int nz, double 
       const float t[6] = {nf, nf * 0.75f * vx, nf * vx, x * nf, y * nf, z * nf};
 #pragma unroll
       for (int c = 0; c < 6; c++) df_acc(fh[c], fl[c], t[c]);
-      fl[0] += (float)(n - (double)nf);  // the electron count keeps the FP64 density in full
+      fl[0] += nl;  // the electron count keeps the double-float density in full
     } else {
       const double x = (ix - cx) * h, y = (iy - cy) * h, z = (iz - cz) * h;
       double vx = 0.0;
@@ -471,50 +528,92 @@ cudaError_t launch_lda(int prec, int bloch, long N, int nx, int ny, int nz, doub
 //       J = -(1/Omega) (sum w f <phi|-i grad|phi> + A int n) (Sec. "Conductivities").
 // One CTA; partials are summed in index order.
 // ---------------------------------------------------------------------------------
+// The record from the summed partials O (energy, current x, y, z) and Lq (LDA sums).
+__device__ __forceinline__ void write_record(const double O[4], const double Lq[6], double *rec, double t_state,
+                                             double h3, double occ, int bloch, double omega_cell, double Ax,
+                                             double Ay, double Az, double field_val) {
+  const double nint = Lq[0] * h3, ex = Lq[1] * h3, nvx = Lq[2] * h3;
+  rec[0] = t_state;
+  rec[1] = nint / occ;
+  rec[2] = O[0] * h3 - nvx + ex;
+  rec[3] = ex;
+  if (!bloch) {
+    rec[4] = Lq[3] * h3;
+    rec[5] = Lq[4] * h3;
+    rec[6] = Lq[5] * h3;
+  } else {
+    rec[4] = -(O[1] * h3 + Ax * nint) / omega_cell;
+    rec[5] = -(O[2] * h3 + Ay * nint) / omega_cell;
+    rec[6] = -(O[3] * h3 + Az * nint) / omega_cell;
+  }
+  rec[7] = field_val;
+}
+
+// Sum of the 10 per-thread values v over the CTA (FIN_THREADS threads): a fixed xor tree
+// within each warp, then the warps in order; thread c < 10 returns component c.
+constexpr int FIN_THREADS = 128;
+__device__ __forceinline__ double block_sum10(double v[10], int t) {
+  __shared__ double red[FIN_THREADS / 32][10];
+#pragma unroll
+  for (int c = 0; c < 10; c++) {
+    double x = v[c];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if ((t & 31) == 0) red[t >> 5][c] = x;
+  }
+  __syncthreads();
+  double x = 0.0;
+  if (t < 10)
+    for (int w = 0; w < FIN_THREADS / 32; w++) x += red[w][t];
+  return x;
+}
+
+// Partials of records [i0, i1) and LDA blocks [l0, l1), summed by one CTA.
+__device__ __forceinline__ double partial_sums(const double *obs_part, long i0, long i1, const double *lda_part,
+                                               long l0, long l1, int t) {
+  double v[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (long i = i0 + t; i < i1; i += FIN_THREADS)
+    for (int c = 0; c < 4; c++) v[c] += obs_part[i * 4 + c];
+  for (long i = l0 + t; i < l1; i += FIN_THREADS)
+    for (int c = 0; c < 6; c++) v[4 + c] += lda_part[i * 6 + c];
+  return block_sum10(v, t);
+}
+
+// One CTA of FIN_THREADS threads (batched systems: one CTA per system).
 __device__ __forceinline__ void finalize_body(const double *obs_part, long n_items, const double *lda_part,
                                               int n_lda, double *rec, double t_state, double h3, double occ,
                                               int bloch, double omega_cell, double Ax, double Ay, double Az,
                                               double field_val) {
-  __shared__ double s_obs[256][4];
-  __shared__ double s_lda[256][6];
+  __shared__ double tot[10];
   const int t = threadIdx.x;
-  double o[4] = {0, 0, 0, 0}, l[6] = {0, 0, 0, 0, 0, 0};
-  for (long i = t; i < n_items; i += 256)
-    for (int c = 0; c < 4; c++) o[c] += obs_part[i * 4 + c];
-  for (int i = t; i < n_lda; i += 256)
-    for (int c = 0; c < 6; c++) l[c] += lda_part[i * 6 + c];
-  for (int c = 0; c < 4; c++) s_obs[t][c] = o[c];
-  for (int c = 0; c < 6; c++) s_lda[t][c] = l[c];
+  const double x = partial_sums(obs_part, 0, n_items, lda_part, 0, n_lda, t);
+  if (t < 10) tot[t] = x;
   __syncthreads();
-  if (t == 0) {
-    double O[4] = {0, 0, 0, 0}, Lq[6] = {0, 0, 0, 0, 0, 0};
-    for (int i = 0; i < 256; i++) {
-      for (int c = 0; c < 4; c++) O[c] += s_obs[i][c];
-      for (int c = 0; c < 6; c++) Lq[c] += s_lda[i][c];
-    }
-    const double nint = Lq[0] * h3, ex = Lq[1] * h3, nvx = Lq[2] * h3;
-    rec[0] = t_state;
-    rec[1] = nint / occ;
-    rec[2] = O[0] * h3 - nvx + ex;
-    rec[3] = ex;
-    if (!bloch) {
-      rec[4] = Lq[3] * h3;
-      rec[5] = Lq[4] * h3;
-      rec[6] = Lq[5] * h3;
-    } else {
-      rec[4] = -(O[1] * h3 + Ax * nint) / omega_cell;
-      rec[5] = -(O[2] * h3 + Ay * nint) / omega_cell;
-      rec[6] = -(O[3] * h3 + Az * nint) / omega_cell;
-    }
-    rec[7] = field_val;
-  }
+  if (t == 0) write_record(tot, tot + 4, rec, t_state, h3, occ, bloch, omega_cell, Ax, Ay, Az, field_val);
 }
 
-__global__ void finalize_kernel(const double *obs_part, long n_items, const double *lda_part, int n_lda,
-                                double *rec, double t_state, double h3, double occ, int bloch,
-                                double omega_cell, double Ax, double Ay, double Az, double field_val) {
-  finalize_body(obs_part, n_items, lda_part, n_lda, rec, t_state, h3, occ, bloch, omega_cell, Ax, Ay, Az,
-                field_val);
+// Two stages for one system: CTA b of stage 1 sums the b-th contiguous share of the
+// partials; stage 2 adds the CTAs' sums in order.  The shares depend only on the counts,
+// so the record is the same on every run.
+__global__ void __launch_bounds__(FIN_THREADS)
+finalize_stage1_kernel(const double *obs_part, long n_items, const double *lda_part, int n_lda, double *fin_part) {
+  const long b = blockIdx.x, nb = gridDim.x;
+  const double x = partial_sums(obs_part, n_items * b / nb, n_items * (b + 1) / nb, lda_part, n_lda * b / nb,
+                                n_lda * (b + 1) / nb, threadIdx.x);
+  if (threadIdx.x < 10) fin_part[b * 10 + threadIdx.x] = x;
+}
+
+__global__ void __launch_bounds__(32)
+finalize_stage2_kernel(const double *fin_part, int nb, double *rec, double t_state, double h3, double occ,
+                       int bloch, double omega_cell, double Ax, double Ay, double Az, double field_val) {
+  __shared__ double tot[10];
+  const int t = threadIdx.x;
+  if (t < 10) {
+    double x = 0.0;
+    for (int b = 0; b < nb; b++) x += fin_part[b * 10 + t];
+    tot[t] = x;
+  }
+  __syncwarp();
+  if (t == 0) write_record(tot, tot + 4, rec, t_state, h3, occ, bloch, omega_cell, Ax, Ay, Az, field_val);
 }
 
 // Batched observable records: one CTA per system, at the first sub-step of each step.
@@ -544,16 +643,20 @@ __global__ void clock_batch_kernel(BatchClock *clk, int n_sys) {
 }
 
 cudaError_t launch_batch_tail(const BatchAux *aux, BatchClock *clk, int n_sys, int which, cudaStream_t s) {
-  if (which == 0) finalize_batch_kernel<<<n_sys, 256, 0, s>>>(aux, clk, n_sys);
+  if (which == 0) finalize_batch_kernel<<<n_sys, FIN_THREADS, 0, s>>>(aux, clk, n_sys);
   else clock_batch_kernel<<<(n_sys + 127) / 128, 128, 0, s>>>(clk, n_sys);
   return cudaGetLastError();
 }
 
 cudaError_t launch_finalize(const double *obs_part, long n_items, const double *lda_part, int n_lda,
                             double *record, double t_state, double h3, double occ, int bloch,
-                            double omega_cell, const double A[3], double field_val, cudaStream_t s) {
-  finalize_kernel<<<1, 256, 0, s>>>(obs_part, n_items, lda_part, n_lda, record, t_state, h3, occ, bloch,
-                                    omega_cell, A[0], A[1], A[2], field_val);
+                            double omega_cell, const double A[3], double field_val, double *fin_part,
+                            cudaStream_t s) {
+  const long want = (n_items + n_lda + 4L * FIN_THREADS - 1) / (4L * FIN_THREADS);
+  const int nb = (int)(want < 1 ? 1 : (want > FIN_BLOCKS ? FIN_BLOCKS : want));
+  finalize_stage1_kernel<<<nb, FIN_THREADS, 0, s>>>(obs_part, n_items, lda_part, n_lda, fin_part);
+  finalize_stage2_kernel<<<1, 32, 0, s>>>(fin_part, nb, record, t_state, h3, occ, bloch, omega_cell, A[0], A[1],
+                                          A[2], field_val);
   return cudaGetLastError();
 }
 

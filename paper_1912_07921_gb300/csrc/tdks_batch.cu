@@ -165,6 +165,7 @@ int tdks_batch_create(const tdks_sys *systems, int n, void *stream, tdks_batch_t
       GatherParams g{};
       g.n_kb = s->n_kb; g.n_batches = s->n_batches; g.n_atoms = s->n_atoms; g.N = s->N;
       g.in = ins[k]; g.atom_begin = s->d_atom_begin; g.ent = s->d_ent; g.D = s->d_D;
+      g.ent_beta = s->d_ent_beta; g.ent_ca = s->d_ent_ca;
       g.h3 = s->h * s->h * s->h; g.kvec = s->d_kvec; g.q = s->d_q;
       g.n_chunks = s->gchunks; g.qpart = s->d_qpart;
       g.sp = s->d_sp; g.n_sp = s->n_sp; g.rowent = s->d_rowent; g.n_ent = s->n_ent; g.nl = s->d_nl;

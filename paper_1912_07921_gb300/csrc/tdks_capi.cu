@@ -125,10 +125,23 @@ struct Timed {
   }
 };
 
-void sweep_geometry(const tdks_system *s, SweepParams &p) {
+bool ws_path(const tdks_system *s) {
+  return s->path == 0 && s->bc == TDKS_BC_ZERO && tma_supported(s->M, s->tx, s->ty);
+}
+
+// Tile of a sweep: the warp-specialised TMA sweep's shape, else the system's tile.
+static void sweep_tile(const tdks_system *s, int sweep, int &tx, int &ty) {
+  tx = s->tx;
+  ty = s->ty;
+  if (sweep >= 0 && ws_path(s)) ws_shape_info(s->wshape[sweep], &tx, &ty, nullptr, nullptr);
+}
+
+void sweep_geometry(const tdks_system *s, SweepParams &p, int sweep) {
+  int tx, ty;
+  sweep_tile(s, sweep, tx, ty);
   p.nx = s->nx; p.ny = s->ny; p.nz = s->nz;
-  p.n_tx = (s->nx + s->tx - 1) / s->tx;
-  p.n_ty = (s->ny + s->ty - 1) / s->ty;
+  p.n_tx = (s->nx + tx - 1) / tx;
+  p.n_ty = (s->ny + ty - 1) / ty;
   p.n_kb = s->n_kb;
   p.n_batches = s->n_batches;
   int zc = s->zc;
@@ -168,8 +181,8 @@ long n_items_of(const tdks_system *s) {
   return p.n_items;
 }
 
-void sweep_common(const tdks_system *s, SweepParams &p, const double A[3]) {
-  sweep_geometry(s, p);
+void sweep_common(const tdks_system *s, SweepParams &p, const double A[3], int sweep) {
+  sweep_geometry(s, p, sweep);
   double c[MAXM + 1], d[MAXM + 1];
   fd_weights(s->M, c, d);
   for (int m = 0; m <= MAXM; m++) { p.w[m] = 0.0; p.gw[m] = 0.0; }
@@ -198,12 +211,12 @@ void sweep_common(const tdks_system *s, SweepParams &p, const double A[3]) {
 }
 
 // Tensor map over a packed array for the TMA sweep of `mode` (box depth = planes per copy).
-bool encode_map(const tdks_system *s, const void *ptr, int mode, CUtensorMap *out, bool lockstep) {
+bool encode_map(const tdks_system *s, const void *ptr, int mode, CUtensorMap *out, bool lockstep, int tx, int ty) {
   EncodeTiledFn fn = encode_fn();
   if (!fn || (reinterpret_cast<uintptr_t>(ptr) & 15) != 0) return false;
   const cuuint64_t dims[5] = {16, (cuuint64_t)s->nx, (cuuint64_t)s->ny, (cuuint64_t)s->nz, (cuuint64_t)s->n_kb};
   const cuuint64_t strides[4] = {64, 64ull * s->nx, 64ull * s->nx * s->ny, 64ull * (cuuint64_t)s->N};
-  const cuuint32_t box[5] = {16, (cuuint32_t)(s->tx + 2 * s->M), (cuuint32_t)(s->ty + 2 * s->M),
+  const cuuint32_t box[5] = {16, (cuuint32_t)(tx + 2 * s->M), (cuuint32_t)(ty + 2 * s->M),
                              (cuuint32_t)tma_planes(s->prec, mode, lockstep), 1};
   const cuuint32_t es[5] = {1, 1, 1, 1, 1};
   return fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<void *>(ptr), dims, strides, box, es,
@@ -212,12 +225,12 @@ bool encode_map(const tdks_system *s, const void *ptr, int mode, CUtensorMap *ou
 }
 
 // Map over the per-point records, tile box of the mode's depth.
-bool encode_aux_map(const tdks_system *s, int mode, CUtensorMap *out, bool lockstep) {
+bool encode_aux_map(const tdks_system *s, int mode, CUtensorMap *out, bool lockstep, int tx, int ty) {
   EncodeTiledFn fn = encode_fn();
   if (!fn || (reinterpret_cast<uintptr_t>(s->aux) & 15) != 0) return false;
   const cuuint64_t dims[4] = {4, (cuuint64_t)s->nx, (cuuint64_t)s->ny, (cuuint64_t)s->nz};
   const cuuint64_t strides[3] = {16, 16ull * s->nx, 16ull * s->nx * s->ny};
-  const cuuint32_t box[4] = {4, (cuuint32_t)s->tx, (cuuint32_t)s->ty, (cuuint32_t)tma_planes(s->prec, mode, lockstep)};
+  const cuuint32_t box[4] = {4, (cuuint32_t)tx, (cuuint32_t)ty, (cuuint32_t)tma_planes(s->prec, mode, lockstep)};
   const cuuint32_t es[4] = {1, 1, 1, 1};
   return fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, s->aux, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -225,26 +238,28 @@ bool encode_aux_map(const tdks_system *s, int mode, CUtensorMap *out, bool locks
 }
 
 // Map over a packed array with the tile box (no halo) of z depth `depth`.
-bool encode_op_map(const tdks_system *s, const void *ptr, CUtensorMap *out, int depth = 1) {
+bool encode_op_map(const tdks_system *s, const void *ptr, CUtensorMap *out, int tx, int ty, int depth = 1) {
   EncodeTiledFn fn = encode_fn();
   if (!fn || (reinterpret_cast<uintptr_t>(ptr) & 15) != 0) return false;
   const cuuint64_t dims[5] = {16, (cuuint64_t)s->nx, (cuuint64_t)s->ny, (cuuint64_t)s->nz, (cuuint64_t)s->n_kb};
   const cuuint64_t strides[4] = {64, 64ull * s->nx, 64ull * s->nx * s->ny, 64ull * (cuuint64_t)s->N};
-  const cuuint32_t box[5] = {16, (cuuint32_t)s->tx, (cuuint32_t)s->ty, (cuuint32_t)depth, 1};
+  const cuuint32_t box[5] = {16, (cuuint32_t)tx, (cuuint32_t)ty, (cuuint32_t)depth, 1};
   const cuuint32_t es[5] = {1, 1, 1, 1, 1};
   return fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<void *>(ptr), dims, strides, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-bool encode_sweep_maps(const tdks_system *s, const void *in, int mode, SweepMaps *out, bool lockstep) {
-  if (!encode_map(s, in, mode, &out->in, lockstep) || !encode_aux_map(s, mode, &out->aux, lockstep) ||
-      !encode_op_map(s, in, &out->ctr, tma_planes(s->prec, mode, lockstep)))
+bool encode_sweep_maps(const tdks_system *s, const void *in, int mode, SweepMaps *out, bool lockstep, int sweep) {
+  int tx = s->tx, ty = s->ty;
+  if (!lockstep) sweep_tile(s, sweep, tx, ty);
+  if (!encode_map(s, in, mode, &out->in, lockstep, tx, ty) || !encode_aux_map(s, mode, &out->aux, lockstep, tx, ty) ||
+      !encode_op_map(s, in, &out->ctr, tx, ty, tma_planes(s->prec, mode, lockstep)))
     return false;
   if (mode == MODE_LAST) {
     const void *ops[4] = {s->psi, s->psi_lo ? s->psi_lo : s->psi, s->term[0], s->term[1]};
     for (int j = 0; j < 4; j++)
-      if (!encode_op_map(s, ops[j], &out->op[j])) return false;
+      if (!encode_op_map(s, ops[j], &out->op[j], tx, ty)) return false;
   } else {
     for (int j = 0; j < 4; j++) out->op[j] = out->in;  // unused
   }
@@ -257,22 +272,29 @@ void build_tmaps(tdks_system *s) {
   const void *ins[4] = {s->psi, s->term[0], s->term[1], s->term[2]};
   const int modes[4] = {MODE_FIRST, MODE_MID, MODE_MID, MODE_LAST};
   for (int i = 0; i < 4; i++)
-    if (!encode_sweep_maps(s, ins[i], modes[i], &s->smaps[i], s->path == 2)) return;
+    if (!encode_sweep_maps(s, ins[i], modes[i], &s->smaps[i], s->path == 2, i)) return;
   s->tmaps_ok = true;
 }
 
 // tm: tensor maps of the sweep (or null): finite boxes with a 16x8 tile take the TMA sweep.
-int run_sweep(tdks_system *s, int mode, SweepParams &p, const SweepMaps *tm) {
+// sweep: which Taylor-term sweep (0..3; its tile shape on the warp-specialised TMA path), or
+// -1 for the default shape
+int run_sweep(tdks_system *s, int mode, SweepParams &p, const SweepMaps *tm, int sweep = -1) {
   Timed tmr(s, 0);
   p.err = s->d_err;
   cudaError_t e;
   const bool tma = tm && s->path != 1 && s->bc == TDKS_BC_ZERO && tma_supported(s->M, s->tx, s->ty);
   const bool ws = tma && s->path == 0;
+  const int shape = (ws && sweep >= 0) ? s->wshape[sweep] : 0;
   if (tma)
-    e = launch_sweep_tma(s->M, s->prec, mode, s->tx, s->ty, *tm, p, 0, s->stream, !ws);
+    e = launch_sweep_tma(s->M, s->prec, mode, s->tx, s->ty, *tm, p, 0, s->stream, !ws, shape);
   else
     e = launch_sweep(s->M, s->prec, mode, s->bc == TDKS_BC_BLOCH, s->tx, s->ty, p, 0, s->stream);
-  if (mode == MODE_FIRST && p.do_obs) s->obs_count = p.n_items * (ws ? WS_CONSUMER_WARPS : 1);
+  if (mode == MODE_FIRST && p.do_obs) {
+    int warps = 1;
+    if (ws) ws_shape_info(shape, nullptr, nullptr, nullptr, &warps);
+    s->obs_count = p.n_items * warps;
+  }
   s->launches++;
   if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("stencil sweep: ") + cudaGetErrorString(e));
   return TDKS_OK;
@@ -284,6 +306,7 @@ int run_gather(tdks_system *s, const void *in, const double A[3]) {
   g.n_kb = s->n_kb; g.n_batches = s->n_batches; g.n_atoms = s->n_atoms; g.N = s->N;
   g.in = in;
   g.atom_begin = s->d_atom_begin; g.ent = s->d_ent; g.D = s->d_D;
+  g.ent_beta = s->d_ent_beta; g.ent_ca = s->d_ent_ca;
   g.h3 = s->h * s->h * s->h;
   g.kvec = s->d_kvec;
   for (int a = 0; a < 3; a++) g.A[a] = s->gauge == TDKS_GAUGE_VELOCITY ? A[a] : 0.0;
@@ -334,8 +357,8 @@ int run_finalize(tdks_system *s, double *rec, double t_state, const double E[3],
   Timed tm(s, 2);
   cudaError_t e = launch_finalize(s->obs_part, s->obs_count, s->lda_part, lda_blocks(s->N), rec, t_state, h3,
                                   s->occ, s->bc == TDKS_BC_BLOCH, omega_cell,
-                                  s->gauge == TDKS_GAUGE_VELOCITY ? A : Az, fv, s->stream);
-  s->launches++;
+                                  s->gauge == TDKS_GAUGE_VELOCITY ? A : Az, fv, s->fin_part, s->stream);
+  s->launches += 2;
   if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("finalize: ") + cudaGetErrorString(e));
   return TDKS_OK;
 }
@@ -346,13 +369,13 @@ int first_sweep(tdks_system *s, double cr, double ci, const double A[3], bool ob
   int rc = run_gather(s, s->psi, A);
   if (rc) return rc;
   SweepParams p{};
-  sweep_common(s, p, A);
+  sweep_common(s, p, A, 0);
   set_coef(p, cr, ci);
   p.in = s->psi;
   p.out = s->term[0];
   p.do_obs = obs ? 1 : 0;
   if (obs && s->bc == TDKS_BC_BLOCH) p.grad_mask |= 8;
-  return run_sweep(s, MODE_FIRST, p, s->tmaps_ok ? &s->smaps[0] : nullptr);
+  return run_sweep(s, MODE_FIRST, p, s->tmaps_ok ? &s->smaps[0] : nullptr, 0);
 }
 
 // Gershgorin-type bound on |lambda| of H: kinetic maximum (the +/- alternating mode of
@@ -385,6 +408,8 @@ double kinetic_max(const tdks_system *s) {
 void free_proj(tdks_system *s) {
   cudaFree(s->d_rowent); cudaFree(s->d_atom_begin);
   cudaFree(s->d_ent); cudaFree(s->d_q); cudaFree(s->d_D); cudaFree(s->d_qpart);
+  cudaFree(s->d_ent_beta); cudaFree(s->d_ent_ca);
+  s->d_ent_beta = nullptr; s->d_ent_ca = nullptr;
   cudaFree(s->d_sp); cudaFree(s->d_nl);
   s->d_rowent = s->d_atom_begin = nullptr;
   s->d_sp = nullptr; s->d_nl = nullptr;
@@ -469,10 +494,16 @@ int tdks_create_grid(int nx, int ny, int nz, double h, int fd_order, int bc, int
   // the general sweep, or the warp-specialised sweep's per-warp records (z chunks of 1 plane)
   {
     const long items_gen = (long)((nx + 7) / 8) * ((ny + 3) / 4) * s->n_kb * nz;
-    const long items_ws = (long)((nx + 15) / 16) * ((ny + 7) / 8) * s->n_kb * nz * WS_CONSUMER_WARPS;
+    long items_ws = 0;
+    for (int sh = 0; sh < WS_SHAPES; sh++) {
+      int tx = 16, ty = 8, warps = 8;
+      ws_shape_info(sh, &tx, &ty, nullptr, &warps);
+      items_ws = std::max(items_ws, (long)((nx + tx - 1) / tx) * ((ny + ty - 1) / ty) * s->n_kb * nz * warps);
+    }
     ALLOC(s->obs_part, (size_t)std::max(items_gen, items_ws) * 4 * sizeof(double));
   }
   ALLOC(s->ring, (size_t)tdks_system::RING * TDKS_RECORD * sizeof(double));
+  ALLOC(s->fin_part, (size_t)FIN_BLOCKS * 10 * sizeof(double));
   ALLOC(s->obs_rec, TDKS_RECORD * sizeof(double));
   ALLOC(s->d_kvec, 3 * n_k * sizeof(double));
   ALLOC(s->d_wocc, n_k * sizeof(double));
@@ -502,7 +533,7 @@ int tdks_destroy(tdks_sys s) {
   cudaFree(s->d_err);
   for (int i = 0; i < 3; i++) cudaFree(s->term[i]);
   cudaFree(s->vloc); cudaFree(s->aux); cudaFree(s->dens_part); cudaFree(s->lda_part);
-  cudaFree(s->obs_part); cudaFree(s->ring); cudaFree(s->obs_rec); cudaFree(s->d_kvec); cudaFree(s->d_wocc);
+  cudaFree(s->obs_part); cudaFree(s->ring); cudaFree(s->fin_part); cudaFree(s->obs_rec); cudaFree(s->d_kvec); cudaFree(s->d_wocc);
   cudaFree(s->staging);
   if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
   if (s->ev_upload_ready) cudaEventDestroy(s->ev_upload_ready);
@@ -683,6 +714,18 @@ int tdks_set_atoms_projectors(tdks_sys s, int n_atoms, const double *pos, const 
   CU(cudaMemcpy(s->d_rowent, rowent.data(), ent.size() * sizeof(int), cudaMemcpyHostToDevice));
   CU(cudaMemcpy(s->d_atom_begin, atom_begin.data(), (n_atoms + 1) * sizeof(int), cudaMemcpyHostToDevice));
   CU(cudaMemcpy(s->d_ent, ent.data(), ent.size() * sizeof(ProjEntry), cudaMemcpyHostToDevice));
+  {
+    std::vector<float4> eb(ent.size());
+    std::vector<int2> eca(ent.size());
+    for (size_t i = 0; i < ent.size(); i++) {
+      eb[i] = make_float4(ent[i].beta[0], ent[i].beta[1], ent[i].beta[2], ent[i].beta[3]);
+      eca[i] = make_int2(ent[i].cell, ent[i].atom);
+    }
+    CU(cudaMalloc((void **)&s->d_ent_beta, ent.size() * sizeof(float4)));
+    CU(cudaMalloc((void **)&s->d_ent_ca, ent.size() * sizeof(int2)));
+    CU(cudaMemcpy(s->d_ent_beta, eb.data(), ent.size() * sizeof(float4), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(s->d_ent_ca, eca.data(), ent.size() * sizeof(int2), cudaMemcpyHostToDevice));
+  }
   CU(cudaMemcpy(s->d_D, D, (size_t)n_atoms * 4 * sizeof(double), cudaMemcpyHostToDevice));
   s->n_atoms = n_atoms;
   s->pos.assign(pos, pos + 3 * n_atoms);
@@ -750,6 +793,101 @@ int tdks_set_sweep_path(tdks_sys s, int path) {
   return TDKS_OK;
 }
 
+int tdks_sweep_shape_info(int shape, int *count, int *tx, int *ty, int *rows, int *warps) {
+  if (count) *count = WS_SHAPES;
+  if (!ws_shape_info(shape, tx, ty, rows, warps)) return fail(TDKS_EINVAL, "no such sweep shape");
+  return TDKS_OK;
+}
+
+int tdks_set_sweep_shape(tdks_sys s, int sweep, int shape) {
+  if (!s) return fail(TDKS_EINVAL, "NULL system");
+  if (sweep < -1 || sweep > 3) return fail(TDKS_EINVAL, "sweep must be 0..3 or -1");
+  if (!ws_shape_info(shape, nullptr, nullptr, nullptr, nullptr)) return fail(TDKS_EINVAL, "no such sweep shape");
+  CU(cudaStreamSynchronize(s->stream));
+  for (int i = 0; i < 4; i++)
+    if (sweep < 0 || sweep == i) s->wshape[i] = shape;
+  build_tmaps(s);
+  return TDKS_OK;
+}
+
+int tdks_get_sweep_shape(tdks_sys s, int sweep, int *shape) {
+  if (!s || !shape) return fail(TDKS_EINVAL, "NULL argument");
+  if (sweep < 0 || sweep > 3) return fail(TDKS_EINVAL, "sweep must be 0..3");
+  *shape = s->wshape[sweep];
+  return TDKS_OK;
+}
+
+// One timed Taylor-term sweep of the autotuner: sweep 0 reads the state and writes t1,
+// sweeps 1 and 2 read t(k-1) and write t(k); sweep 3 reads t3 and combines into t1/t2 in
+// place of the state (state hi <- t1, state lo <- t2), so the state itself is untouched.
+static int tune_launch(tdks_system *s, int sweep) {
+  const double A0[3] = {0.0, 0.0, 0.0};
+  const int modes[4] = {MODE_FIRST, MODE_MID, MODE_MID, MODE_LAST};
+  const int mode = modes[sweep];
+  SweepParams p{};
+  sweep_common(s, p, A0, sweep);
+  set_coef(p, 0.0, -0.01 / (sweep + 1));
+  p.in = sweep == 0 ? s->psi : s->term[sweep - 1];
+  SweepMaps tm;
+  if (!encode_sweep_maps(s, p.in, mode, &tm, false, sweep)) return fail(TDKS_EDEVICE, "tensor map encoding failed");
+  if (mode == MODE_LAST) {
+    int tx = 16, ty = 8;
+    ws_shape_info(s->wshape[sweep], &tx, &ty, nullptr, nullptr);
+    const void *ops[4] = {s->term[0], s->term[1], s->term[0], s->term[1]};
+    for (int j = 0; j < 4; j++)
+      if (!encode_op_map(s, ops[j], &tm.op[j], tx, ty)) return fail(TDKS_EDEVICE, "tensor map encoding failed");
+    p.psi = s->term[0];
+    p.psi_lo = s->term[1];
+    p.t1 = s->term[0];
+    p.t2 = s->term[1];
+  } else {
+    p.out = s->term[sweep];
+  }
+  return run_sweep(s, mode, p, &tm, sweep);
+}
+
+int tdks_autotune(tdks_sys s, int reps, double *ms) {
+  if (!s) return fail(TDKS_EINVAL, "NULL system");
+  if (reps < 1) return fail(TDKS_EINVAL, "reps < 1");
+  if (ms)
+    for (int i = 0; i < WS_SHAPES * 4; i++) ms[i] = -1.0;
+  if (!ws_path(s)) return TDKS_OK;
+  CU(cudaStreamSynchronize(s->stream));
+  const int saved[4] = {s->wshape[0], s->wshape[1], s->wshape[2], s->wshape[3]};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CU(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(TDKS_EDEVICE, "cudaEventCreate");
+  }
+  double best[4] = {-1.0, -1.0, -1.0, -1.0};
+  int pick[4] = {saved[0], saved[1], saved[2], saved[3]};
+  int rc = TDKS_OK;
+  for (int sh = 0; sh < WS_SHAPES && rc == TDKS_OK; sh++) {
+    for (int i = 0; i < 4; i++) s->wshape[i] = sh;
+    for (int sw = 0; sw < 4 && rc == TDKS_OK; sw++) {
+      if ((rc = tune_launch(s, sw))) break;  // warm-up (and fills this sweep's output)
+      cudaEventRecord(e0, s->stream);
+      for (int r = 0; r < reps && rc == TDKS_OK; r++) rc = tune_launch(s, sw);
+      cudaEventRecord(e1, s->stream);
+      if (rc) break;
+      if (cudaEventSynchronize(e1) != cudaSuccess) { rc = fail(TDKS_EDEVICE, "autotune timing"); break; }
+      if ((rc = check_err(s))) break;
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      const double per = (double)t / reps;
+      if (ms) ms[sh * 4 + sw] = per;
+      if (best[sw] < 0.0 || per < best[sw]) { best[sw] = per; pick[sw] = sh; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (int i = 0; i < 4; i++) s->wshape[i] = rc == TDKS_OK ? pick[i] : saved[i];
+  build_tmaps(s);
+  s->dens_valid = false;  // the last sweeps overwrote the density partials
+  return rc;
+}
+
 int tdks_apply_H(tdks_sys s, double t, const void *dev_in, void *dev_out) {
   if (!s || !dev_in || !dev_out) return fail(TDKS_EINVAL, "NULL argument");
   if (dev_in == dev_out) return fail(TDKS_EINVAL, "dev_in and dev_out must differ");
@@ -763,14 +901,14 @@ int tdks_apply_H(tdks_sys s, double t, const void *dev_in, void *dev_out) {
   if ((rc = run_lda(s, E, A))) return rc;
   if ((rc = run_gather(s, dev_in, A))) return rc;
   SweepParams p{};
-  sweep_common(s, p, A);
+  sweep_common(s, p, A, 1);
   set_coef(p, 1.0, 0.0);
   p.in = dev_in;
   p.out = dev_out;
   SweepMaps tm;
   const bool have_tm = s->bc == TDKS_BC_ZERO && tma_supported(s->M, s->tx, s->ty) &&
-                       encode_sweep_maps(s, dev_in, MODE_MID, &tm, s->path == 2);
-  return run_sweep(s, MODE_MID, p, have_tm ? &tm : nullptr);
+                       encode_sweep_maps(s, dev_in, MODE_MID, &tm, s->path == 2, 1);
+  return run_sweep(s, MODE_MID, p, have_tm ? &tm : nullptr, 1);
 }
 
 int tdks_auto_substeps(tdks_sys s, double dt, int *substeps) {
@@ -807,18 +945,18 @@ int tdks_propagate_n(tdks_sys s, double t0, double dt, int n_steps, int substeps
         const void *in = s->term[k - 2];
         if ((rc = run_gather(s, in, A))) return rc;
         SweepParams p{};
-        sweep_common(s, p, A);
+        sweep_common(s, p, A, k - 1);
         set_coef(p, 0.0, -dts / k);
         p.in = in;
         if (k < 4) {
           p.out = s->term[k - 1];
-          if ((rc = run_sweep(s, MODE_MID, p, s->tmaps_ok ? &s->smaps[k - 1] : nullptr))) return rc;
+          if ((rc = run_sweep(s, MODE_MID, p, s->tmaps_ok ? &s->smaps[k - 1] : nullptr, k - 1))) return rc;
         } else {
           p.psi = s->psi;
           p.psi_lo = s->psi_lo;
           p.t1 = s->term[0];
           p.t2 = s->term[1];
-          if ((rc = run_sweep(s, MODE_LAST, p, s->tmaps_ok ? &s->smaps[3] : nullptr))) return rc;
+          if ((rc = run_sweep(s, MODE_LAST, p, s->tmaps_ok ? &s->smaps[3] : nullptr, 3))) return rc;
         }
       }
       s->dens_valid = true;  // MODE_LAST wrote the density of the new state

@@ -98,6 +98,8 @@ struct GatherParams {
   const void *in;             // stencil input (state or hi part of the state, or a term)
   const int *atom_begin;      // [n_atoms+1] entry ranges (atom-major)
   const ProjEntry *ent;
+  const float4 *ent_beta;     // [n_ent] beta_aj of each entry in FP32 (complex64 kernels)
+  const int2 *ent_ca;         // [n_ent] (cell, atom) of each entry
   const double *D;            // [n_atoms][4]
   double h3;
   const double *kvec;
@@ -183,10 +185,12 @@ cudaError_t launch_lda(int prec, int bloch, long N, int nx, int ny, int nz, doub
                        const double *vloc, int xc,
                        const double E[3], double half_A2, PointAux *aux, double *lda_part,
                        int n_blocks, cudaStream_t s);
+// fin_part: device scratch of FIN_BLOCKS * 10 doubles for the first of the two stages
+constexpr int FIN_BLOCKS = 64;
 cudaError_t launch_finalize(const double *obs_part, long n_items, const double *lda_part,
                             int n_lda_blocks, double *record, double t_state, double h3,
                             double occ, int bloch, double omega_cell, const double A[3],
-                            double field_val, cudaStream_t s);
+                            double field_val, double *fin_part, cudaStream_t s);
 // host layout -> internal layout and density partials, points [pt0, pt0 + npts) of k-point k
 cudaError_t launch_pack_in(int prec, long N, int k, long pt0, long npts, int n_orb, int n_batches,
                            const double *plain, void *internal, void *internal_lo, const double *wocc,
@@ -195,13 +199,20 @@ cudaError_t launch_pack(int prec, int to_internal, long N, int n_k, int n_orb, i
                         void *internal, void *internal_lo, double *plain, cudaStream_t s);
 
 // TMA sweep for finite boxes (tdks_sweep_tma.cu).  maps.in: dims {16 floats, nx, ny, nz,
-// n_kb}, box {16, TX+2M, TY+2M, tma_planes(prec, mode), 1}; maps.aux: dims {4, nx, ny, nz}
+// n_kb}, box {16, TX+2M, TY+2M, tma_planes(prec, mode), 1} (TY: the shape's tile height); maps.aux: dims {4, nx, ny, nz}
 // (4-byte words), box {4, TX, TY, tma_planes}; maps.op[i]: dims as maps.in, box
 // {16, TX, TY, 1, 1}; maps.ctr: as maps.op with tma_planes planes.  Default: the
 // warp-specialised kernel (a producer warp and eight consumer warps); lockstep: the variant
 // in which all warps of a CTA advance plane by plane together.
 cudaError_t launch_sweep_tma(int M, int prec, int mode, int tx, int ty, const SweepMaps &maps,
-                             const SweepParams &p, int grid, cudaStream_t s, bool lockstep = false);
+                             const SweepParams &p, int grid, cudaStream_t s, bool lockstep = false,
+                             int shape = 0);
+// Tile shapes of the warp-specialised sweep: shape s covers tx x ty points of one orbital
+// block with `warps` consumer warps, each thread computing `rows` y-adjacent points.
+// Shape 0 (16 x 8, two points per thread, eight consumer warps) is the default and the one
+// the batched sweep uses.  Null outputs are skipped; false for a shape out of range.
+constexpr int WS_SHAPES = 5;
+bool ws_shape_info(int shape, int *tx, int *ty, int *rows, int *warps);
 bool tma_supported(int M, int tx, int ty);
 int tma_planes(int prec, int mode, bool lockstep = false);
 int lda_blocks(long N);

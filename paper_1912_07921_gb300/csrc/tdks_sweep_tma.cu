@@ -15,281 +15,9 @@
 //     from the ring buffer of the output plane.
 // Every wait is bounded: a wait that runs out sets the error word, waits (bounded) for
 // the copies still in flight, and the CTA returns.
-#include <cuda.h>
-
-#include <type_traits>
-
-#include "tdks_internal.cuh"
-#include "tdks_sweep_common.cuh"
+#include "tdks_tma.cuh"
 
 namespace tdks {
-
-namespace {
-
-constexpr long long WAIT_LIMIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
-constexpr long long DRAIN_LIMIT_CYCLES = 200000000LL;  // ~0.1 s per copy on the error path
-
-__device__ __forceinline__ uint32_t smem_u32(const void *ptr) {
-  return (uint32_t)__cvta_generic_to_shared(ptr);
-}
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
-                                                  long long limit = WAIT_LIMIT_CYCLES) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity))
-    if (clock64() - t0 > limit) return false;
-  return true;
-}
-__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-// Consumer wait: bounded, and gives up at once when another warp has given up.
-__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *bar, uint32_t parity, const volatile int *abort) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
-    if (*abort) return false;
-    if (clock64() - t0 > WAIT_LIMIT_CYCLES) return false;
-  }
-  return true;
-}
-__device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *tmap, uint64_t *bar, int c0, int c1,
-                                            int c2, int c3, int c4) {
-  asm volatile(
-      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-      "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *tmap, uint64_t *bar, int c0, int c1,
-                                            int c2, int c3) {
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-      "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
-      : "memory");
-}
-
-}  // namespace
-
-// Compile-time loop: f(integral_constant<int, 0>) ... f(integral_constant<int, N-1>).
-template <int I, int N, class F>
-__device__ __forceinline__ void static_for(F &&f) {
-  if constexpr (I < N) {
-    f(std::integral_constant<int, I>{});
-    static_for<I + 1, N>(f);
-  }
-}
-
-// Position in a ring of S slots: slot index and the parity of the slot's current use.
-struct RingPos {
-  int slot = 0;
-  uint32_t phase = 0;
-  template <int S>
-  __device__ __forceinline__ void next() {
-    if (++slot == S) {
-      slot = 0;
-      phase ^= 1u;
-    }
-  }
-};
-
-// Shared-memory plan: three TMA-fed rings, each slot completed by one mbarrier.
-//   centre ring (SC slots): U planes of the input tile (no halo), which feed the per-thread
-//     register z-queue; a slot is free again as soon as its planes are in registers;
-//   halo ring (SH slots): U output planes of the input with their x/y halo, followed by the
-//     U planes' per-point records; read when those planes are computed;
-//   operand ring (SO slots, last Taylor term only): the four own-point operand tiles of one
-//     output plane (state hi, state lo, t1, t2).
-// Keeping the z history in registers (not in the ring) lets every ring run several slots
-// ahead of the plane being computed.
-template <int M, int TX, int TY, int U, bool OPS>
-struct TmaGeom {
-  static constexpr int SX = TX + 2 * M, SY = TY + 2 * M;
-  static constexpr int PLANE = SX * SY * OVC;                        // vectors per halo plane
-  static constexpr int CPLANE = TX * TY * OVC;                       // vectors per centre plane
-  static constexpr uint32_t CSLOT_BYTES = (uint32_t)CPLANE * 16 * U;
-  static constexpr uint32_t IN_BYTES = (uint32_t)PLANE * 16 * U;
-  static constexpr uint32_t AUX_BYTES = (uint32_t)TX * TY * 16 * U;
-  static constexpr uint32_t HSLOT_BYTES = IN_BYTES + AUX_BYTES;
-  static constexpr uint32_t OPT_BYTES = (uint32_t)CPLANE * 16;       // one operand tile
-  static constexpr uint32_t OP_BYTES = 4 * OPT_BYTES;
-  static constexpr int SO = OPS ? 2 : 0;
-  static constexpr int SC = U == 1 ? (OPS ? 4 : 6) : 4;
-  static constexpr size_t BUDGET = 227 * 1024 - 2048;                // dynamic smem available
-  static constexpr int SH_FIT =
-      (int)((BUDGET - 128 - (size_t)SO * OP_BYTES - (size_t)SC * CSLOT_BYTES) / HSLOT_BYTES);
-  static constexpr int SH = SH_FIT < 8 ? SH_FIT : 8;
-  static constexpr size_t SMEM = (size_t)SC * CSLOT_BYTES + (size_t)SH * HSLOT_BYTES + (size_t)SO * OP_BYTES + 128;
-  static_assert(SH >= 2, "halo ring too small");
-};
-
-// Work sources: a single system (parameters and tensor maps are kernel parameters), or a
-// batch of systems (per-system parameters and tensor maps in device arrays; a CTA stages
-// the parameters of its current item in shared memory).
-struct SingleSrc {
-  const SweepParams *p;
-  const SweepMaps *maps;
-  __device__ __forceinline__ long n_items() const { return p->n_items; }
-  __device__ __forceinline__ void item(long it, const SweepParams *&pp, const SweepMaps *&mp, long &local) const {
-    pp = p;
-    mp = maps;
-    local = it;
-  }
-  __device__ __forceinline__ int sys_of(long) const { return 0; }
-  __device__ __forceinline__ const SweepMaps *maps_of(int) const { return maps; }
-  __device__ __forceinline__ int *err0() const { return p->err; }
-};
-
-__device__ __forceinline__ int find_item_sys(const long *begin, int n, long u) {
-  int lo = 0, hi = n - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (begin[mid] <= u) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
-struct BatchSrc {
-  const BatchSweepArgs *a;
-  __device__ __forceinline__ long n_items() const { return a->total_items; }
-  __device__ __forceinline__ void item(long it, const SweepParams *&pp, const SweepMaps *&mp, long &local) const {
-    const int s = find_item_sys(a->item_begin, a->n_sys, it);
-    pp = a->params + s;
-    mp = a->maps + 4 * s + a->which;
-    local = it - a->item_begin[s];
-  }
-  __device__ __forceinline__ int sys_of(long it) const { return find_item_sys(a->item_begin, a->n_sys, it); }
-  __device__ __forceinline__ const SweepMaps *maps_of(int s) const { return a->maps + 4 * s + a->which; }
-  __device__ __forceinline__ int *err0() const { return a->params[0].err; }
-};
-
-// Sequential cursor over one kind of load of the CTA's items (thread 0 only).  The item's
-// geometry is decoded once, when the cursor enters the item, so issuing a load costs a few
-// instructions: the other threads wait for thread 0 at the next barrier.
-struct LoadCursor {
-  long ii;     // item index among the CTA's items (-1: not entered yet)
-  int l;       // load index within the item
-  int n;       // loads of this kind in the item
-  int tx, ty, kb, z0;
-  int sys;     // system of the item (batch)
-  long issued; // loads issued so far
-};
-
-// Work item -> tile (tx, ty), orbital block kb and z chunk [z0, z1).
-__device__ __forceinline__ void item_geom(const SweepParams &q, long it, int &tx, int &ty, int &kb, int &z0,
-                                          int &z1) {
-  // z chunks fastest: consecutive items are the chunks of one column, which run at about the
-  // same time on different SMs and share the planes at their boundaries through L2
-  z0 = (int)(it % q.n_zc) * q.zc;
-  it /= q.n_zc;
-  tx = (int)(it % q.n_tx);
-  it /= q.n_tx;
-  ty = (int)(it % q.n_ty);
-  it /= q.n_ty;
-  kb = (int)it;
-  z1 = min(z0 + q.zc, q.nz);
-}
-
-// Loads per item: 0 = centre (queue planes z0-M .. z1+M-1, U per load), 1 = halo (output
-// planes, U per load), 2 = operands (one per output plane).
-template <int M, int U>
-__device__ __forceinline__ int loads_of(int kind, int z0, int z1) {
-  if (kind == 0) return (z1 - z0 + 2 * M + U - 1) / U;
-  if (kind == 1) return (z1 - z0 + U - 1) / U;
-  return z1 - z0;
-}
-
-// The producer side of the rings (thread 0 only).
-template <int M, int TX, int TY, int U, class G, int SC, int SH, int SO, class Src>
-struct Loader {
-  Src src;
-  long n_my;
-  unsigned char *cbase, *hbase, *obase;
-  uint64_t *cfull, *hfull, *ofull;
-
-  // move the cursor onto its next load (decoding the geometry of an item it enters)
-  __device__ __forceinline__ void advance(LoadCursor &c, int kind) const {
-    while (c.ii < n_my && (c.ii < 0 || c.l >= c.n)) {
-      c.ii += 1;
-      c.l = 0;
-      c.n = 0;
-      if (c.ii < n_my) {
-        const SweepParams *qp = nullptr;
-        const SweepMaps *mq = nullptr;
-        long local = 0;
-        src.item(blockIdx.x + c.ii * gridDim.x, qp, mq, local);
-        int z1 = 0;
-        item_geom(*qp, local, c.tx, c.ty, c.kb, c.z0, z1);
-        c.sys = src.sys_of(blockIdx.x + c.ii * gridDim.x);
-        c.n = loads_of<M, U>(kind, c.z0, z1);
-      }
-    }
-  }
-
-  // issue the next load of `kind`; nothing past the CTA's last item
-  __device__ __forceinline__ void issue(LoadCursor &c, int kind) const {
-    advance(c, kind);
-    if (c.ii >= n_my) return;
-    emit(c, kind);
-  }
-
-  // issue the load the cursor is positioned on
-  __device__ __forceinline__ void emit(LoadCursor &c, int kind) const {
-    const SweepMaps *mp = src.maps_of(c.sys);
-    if (kind == 0) {
-      const int slot = (int)(c.issued % SC);
-      mbar_expect_tx(&cfull[slot], G::CSLOT_BYTES);
-      tma_load_5d(cbase + (size_t)slot * G::CSLOT_BYTES, &mp->ctr, &cfull[slot], 0, c.tx * TX, c.ty * TY,
-                  c.z0 - M + U * c.l, c.kb);
-    } else if (kind == 1) {
-      const int slot = (int)(c.issued % SH);
-      unsigned char *dst = hbase + (size_t)slot * G::HSLOT_BYTES;
-      const int zp = c.z0 + U * c.l;
-      mbar_expect_tx(&hfull[slot], G::HSLOT_BYTES);
-      tma_load_5d(dst, &mp->in, &hfull[slot], 0, c.tx * TX - M, c.ty * TY - M, zp, c.kb);
-      tma_load_4d(dst + G::IN_BYTES, &mp->aux, &hfull[slot], 0, c.tx * TX, c.ty * TY, zp);
-    } else {
-      const int slot = (int)(c.issued % SO);
-      unsigned char *dst = obase + (size_t)slot * G::OP_BYTES;
-      mbar_expect_tx(&ofull[slot], G::OP_BYTES);
-      for (int j = 0; j < 4; j++)
-        tma_load_5d(dst + j * G::OPT_BYTES, &mp->op[j], &ofull[slot], 0, c.tx * TX, c.ty * TY, c.z0 + c.l, c.kb);
-    }
-    c.issued++;
-    c.l++;
-  }
-};
 
 template <int M, int P, int MODE, int TX, int TY, int U, bool BATCH, class Src>
 __device__ __forceinline__ void tma_sweep_body(const Src &src) {
@@ -501,363 +229,17 @@ tma_sweep_batch_kernel(const __grid_constant__ BatchSweepArgs a) {
   tma_sweep_body<M, P, MODE, TX, TY, U, true>(src);
 }
 
-// ---------------------------------------------------------------------------------------
-// Warp-specialised variant: one producer warp keeps the three rings full, eight consumer
-// warps compute.  A ring slot is handed back by an "empty" mbarrier that each consumer
-// warp arrives on once it has read the slot, so the consumer warps never wait for one
-// another inside a work item: while some warps read their shared-memory neighbours,
-// others do arithmetic or store.  Each consumer thread computes one 16-byte vector of two
-// y-adjacent points, which share the ten y-column values they read (the two points need
-// 2M+2 column loads instead of 4M).
-constexpr int WS_CWARPS = 8;                   // consumer warps
-constexpr int WS_CTHREADS = WS_CWARPS * 32;    // = OVC * TX * TY / 2 for a 16x8 tile
-constexpr int WS_THREADS = WS_CTHREADS + 32;   // + the producer warp
-
-// H at two y-adjacent points (rows 0 and 1) of one plane, from their z queues Q0/Q1 and
-// the halo plane Sp (row 0's own vector at hs0, row stride SXO vectors).  Same terms and
-// summation order as stencil_point.
-template <int M, int P, int QB, int QN>
-__device__ __forceinline__ void stencil_rows2(const typename VT<P>::S *W, typename W0T<P>::type w0,
-                                              const typename VT<P>::V *Q0, const typename VT<P>::V *Q1,
-                                              const typename VT<P>::V *Sp, int hs0, int SXO,
-                                              typename VT<P>::R ve0, typename VT<P>::R ve1,
-                                              typename VT<P>::V &acc0, typename VT<P>::V &acc1) {
-  typedef VT<P> T;
-  typedef typename T::V V;
-  V col[2 * M + 2];  // Sp[hs0 + k SXO], k = -M .. M+1
-#pragma unroll
-  for (int k = 0; k < 2 * M + 2; k++) col[k] = Sp[hs0 + (k - M) * SXO];
-  const int hs1 = hs0 + SXO;
-  acc0 = T::mul(T::diag(ve0, w0), Q0[(QB + M) % QN]);
-  acc1 = T::mul(T::diag(ve1, w0), Q1[(QB + M) % QN]);
-#pragma unroll
-  for (int m = 1; m <= M; m++) {
-    const V s0 = T::add(T::add(T::add(Q0[(QB + M - m) % QN], Q0[(QB + M + m) % QN]),
-                               T::add(Sp[hs0 - m * OVC], Sp[hs0 + m * OVC])),
-                        T::add(col[M - m], col[M + m]));
-    const V s1 = T::add(T::add(T::add(Q1[(QB + M - m) % QN], Q1[(QB + M + m) % QN]),
-                               T::add(Sp[hs1 - m * OVC], Sp[hs1 + m * OVC])),
-                        T::add(col[M + 1 - m], col[M + 1 + m]));
-    acc0 = T::fma(W[m], s0, acc0);
-    acc1 = T::fma(W[m], s1, acc1);
-  }
-}
-
-template <int M, int P, int MODE, int TX, int TY, int U, bool BATCH, class Src>
-__device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work) {
-  typedef VT<P> T;
-  typedef typename T::V V;
-  typedef typename T::S S_;
-  typedef typename T::R R;
-  constexpr bool OPS = MODE == MODE_LAST;
-  typedef TmaGeom<M, TX, TY, U, OPS> G;
-  static_assert(M % U == 0, "M must be a multiple of U");
-  static_assert(!OPS || U == 1, "the last Taylor term takes one plane per iteration");
-  static_assert(OVC * TX * TY == 2 * WS_CTHREADS, "two points per consumer thread");
-  static_assert(WS_CWARPS == WS_CONSUMER_WARPS, "per-warp partial records");
-  constexpr int SC = G::SC, SH = G::SH;
-  constexpr int SO = G::SO > 0 ? G::SO : 1;
-  constexpr int QN = 2 * M + U;   // z-queue entries
-  constexpr int LP = 2 * M / U;   // priming centre loads per item
-  constexpr int IR = 16;          // claimed-item ring (the producer runs at most a few items ahead)
-  extern __shared__ unsigned char smem_raw[];
-  unsigned char *cbase = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
-  unsigned char *hbase = cbase + (size_t)SC * G::CSLOT_BYTES;
-  unsigned char *obase = hbase + (size_t)SH * G::HSLOT_BYTES;
-  __shared__ __align__(8) uint64_t cfull[SC], cempty[SC];
-  __shared__ __align__(8) uint64_t hfull[SH], hempty[SH];
-  __shared__ __align__(8) uint64_t ofull[SO], oempty[SO];
-  __shared__ __align__(8) uint64_t ibar[IR];  // completes when s_item[seq % IR] is written
-  __shared__ long s_item[IR];                 // item of the CTA's seq-th claim (-1: no more)
-  __shared__ int s_abort;
-  volatile int *abort_flag = &s_abort;
-
-  const int tid = threadIdx.x;
-  const int warp = tid >> 5, lane = tid & 31;
-  const long n_items_all = src.n_items();
-
-  if (tid == 0) {
-    for (int s = 0; s < SC; s++) { mbar_init(&cfull[s], 1); mbar_init(&cempty[s], WS_CWARPS); }
-    for (int s = 0; s < SH; s++) { mbar_init(&hfull[s], 1); mbar_init(&hempty[s], WS_CWARPS); }
-    for (int s = 0; s < SO; s++) { mbar_init(&ofull[s], 1); mbar_init(&oempty[s], WS_CWARPS); }
-    for (int s = 0; s < IR; s++) mbar_init(&ibar[s], 1);
-    s_abort = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();  // the only CTA-wide barrier: from here on the warps run decoupled
-
-  if (warp == WS_CWARPS) {
-    // ---- producer: claim items, and issue every ring's loads as soon as a slot is free ----
-    if (lane == 0) {
-      const Loader<M, TX, TY, U, G, SC, SH, SO, Src> ld{src, 0, cbase, hbase, obase, cfull, hfull, ofull};
-      LoadCursor c[3];
-      bool done[3] = {false, false, !OPS};
-      for (int k = 0; k < 3; k++) c[k] = LoadCursor{-1, 0, 0, 0, 0, 0, 0, 0, 0};
-      long claimed = 0;  // claims made (their items are in s_item)
-      // position cursor k on its next load; false if it has none yet (or none at all)
-      auto position = [&](int k) -> bool {
-        LoadCursor &cu = c[k];
-        while (!done[k] && cu.l >= cu.n) {
-          const long ns = cu.ii + 1;
-          if (ns >= claimed) {
-            if (k != 0) return false;  // the centre cursor, always ahead, makes the claims
-            const unsigned int t = atomicAdd(work, 1u);
-            // every CTA ends with one claim past the last item: the launch's last claim
-            // returns the counter to zero for the next launch
-            if ((long)t == n_items_all + (long)gridDim.x - 1) atomicExch(work, 0u);
-            s_item[claimed % IR] = (long)t < n_items_all ? (long)t : -1;
-            mbar_arrive(&ibar[claimed % IR]);
-            claimed++;
-          }
-          const long it = s_item[ns % IR];
-          if (it < 0) {
-            done[k] = true;
-            break;
-          }
-          const SweepParams *qp = nullptr;
-          const SweepMaps *mq = nullptr;
-          long local = 0;
-          src.item(it, qp, mq, local);
-          int z1 = 0;
-          item_geom(*qp, local, cu.tx, cu.ty, cu.kb, cu.z0, z1);
-          cu.sys = src.sys_of(it);
-          cu.ii = ns;
-          cu.l = 0;
-          cu.n = loads_of<M, U>(k, cu.z0, z1);
-        }
-        return !done[k];
-      };
-      long long idle_since = clock64();
-      for (;;) {
-        bool left = false, progressed = false;
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-          if (done[k]) continue;
-          left = true;
-          if (!position(k)) continue;
-          const int S = k == 0 ? SC : (k == 1 ? SH : SO);
-          uint64_t *empty = k == 0 ? cempty : (k == 1 ? hempty : oempty);
-          const long n = c[k].issued;
-          // slot n % S is free once the consumers have released its previous use
-          if (n >= S && !mbar_test(&empty[n % S], (uint32_t)(((n / S) - 1) & 1))) continue;
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          ld.emit(c[k], k);
-          progressed = true;
-        }
-        if (!left) break;
-        if (progressed) {
-          idle_since = clock64();
-        } else {
-          if (*abort_flag || clock64() - idle_since > WAIT_LIMIT_CYCLES) {
-            *abort_flag = 1;
-            break;
-          }
-          __nanosleep(32);
-        }
-      }
-      // copies still in flight must land before the CTA's shared memory goes away
-      for (int k = 0; k < 3; k++) {
-        if (k == 2 && !OPS) continue;
-        const int S = k == 0 ? SC : (k == 1 ? SH : SO);
-        uint64_t *full = k == 0 ? cfull : (k == 1 ? hfull : ofull);
-        const long n = c[k].issued;
-        for (long j = n > S ? n - S : 0; j < n; j++)
-          mbar_wait_bounded(&full[j % S], (uint32_t)((j / S) & 1), DRAIN_LIMIT_CYCLES);
-      }
-    }
-    return;
-  }
-
-  // ---- consumers: no barrier between warps; a warp that gives up stops, and the others
-  // give up at their next wait ----------------------------------------------------------------
-  const int v = tid % OVC;
-  const int lx = (tid / OVC) % TX;
-  const int ly0 = 2 * (tid / (OVC * TX));
-  const int hs0 = ((ly0 + M) * G::SX + (lx + M)) * OVC + v;  // row 0's vector in a halo plane
-  const int tsl0 = ly0 * TX + lx;                             // row 0's point in a tile
-  const int csl0 = tsl0 * OVC + v;                            // row 0's vector in a centre plane
-  constexpr int SXO = G::SX * OVC;
-
-  RingPos rc, rh, ro;  // ring positions of the next centre / halo / operand load
-  bool aborted = false;
-  int *errp = src.err0();  // then the current item's system's
-  for (long seq = 0;; seq++) {
-    if (!mbar_wait_or_abort(&ibar[seq % IR], (uint32_t)((seq / IR) & 1), abort_flag)) {
-      aborted = true;
-      break;
-    }
-    const long item = s_item[seq % IR];
-    if (item < 0) break;
-    const SweepParams *pp;
-    const SweepMaps *mp_unused;
-    long local;
-    src.item(item, pp, mp_unused, local);
-    const SweepParams &p = *pp;  // (batch: read from the parameter array, once per item)
-    errp = p.err;
-    const int nx = p.nx, ny = p.ny;
-    const long N = (long)nx * ny * p.nz;
-    const long plane_pts = (long)nx * ny;
-    S_ W[M + 1];
-#pragma unroll
-    for (int m = 0; m <= M; m++) W[m] = T::coef(p.w[m], p.wf[m]);
-    const typename W0T<P>::type w0 = P == P_C64 ? (typename W0T<P>::type)p.wf[0] : (typename W0T<P>::type)p.w[0];
-    const S_ CR = T::coef(p.cr, p.crf), CI = T::coef(p.ci, p.cif);
-    int tx, ty, kb, z0, z1;
-    item_geom(p, local, tx, ty, kb, z0, z1);
-    const int kidx = kb / p.n_batches;
-    const Epi epi = make_epi(p, kidx);
-    const bool has_proj = p.has_proj != 0, do_obs = p.do_obs != 0;
-    const V *nlk = nl_column<P>(p, kb, v);
-    const int n_ent = p.n_ent;
-    const int gx = tx * TX + lx, gy0 = ty * TY + ly0;
-    const bool own0 = gx < nx && gy0 < ny, own1 = gx < nx && gy0 + 1 < ny;
-    const int nl = loads_of<M, U>(0, z0, z1);
-    // vector index of row 0's point in the first output plane (advances one plane per output)
-    long idx = ((long)kb * N + ((long)z0 * ny + gy0) * nx + gx) * OVC + v;
-    const long row = (long)nx * OVC;
-    V Q0[QN], Q1[QN];
-#pragma unroll
-    for (int j = 0; j < QN; j++) Q0[j] = Q1[j] = T::zero();
-    ObsAcc<P> oa;
-
-    int l = 0;
-    // one centre load (and, past the priming loads, one halo load); RQ = compile-time
-    // queue position of its first plane
-    auto iteration = [&](auto rq) {
-      constexpr int RQ = decltype(rq)::value;
-      const int cs = rc.slot;
-      if (!mbar_wait_or_abort(&cfull[cs], rc.phase, abort_flag)) {
-        aborted = true;
-        return;
-      }
-      const V *cslot = reinterpret_cast<const V *>(cbase + (size_t)cs * G::CSLOT_BYTES);
-#pragma unroll
-      for (int u = 0; u < U; u++) {
-        Q0[(RQ + u) % QN] = cslot[u * G::CPLANE + csl0];
-        Q1[(RQ + u) % QN] = cslot[u * G::CPLANE + csl0 + TX * OVC];
-      }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&cempty[cs]);
-      rc.next<SC>();
-      if (l >= LP) {
-        const int zf = z0 + U * (l - LP);
-        const int hs = rh.slot;
-        if (!mbar_wait_or_abort(&hfull[hs], rh.phase, abort_flag)) {
-          aborted = true;
-          return;
-        }
-        const unsigned char *hslot = hbase + (size_t)hs * G::HSLOT_BYTES;
-        const V *xs = reinterpret_cast<const V *>(hslot);
-        const PointAux *ax = reinterpret_cast<const PointAux *>(hslot + G::IN_BYTES);
-        const V *ob = nullptr;  // last term: the operand slot, read row by row at the epilogue
-        int os = 0;
-        if constexpr (OPS) {
-          os = ro.slot;
-          if (!mbar_wait_or_abort(&ofull[os], ro.phase, abort_flag)) {
-            aborted = true;
-            return;
-          }
-          ob = reinterpret_cast<const V *>(obase + (size_t)os * G::OP_BYTES);
-        }
-        auto operands = [&](int c) {
-          LastOperands<P> o;
-          if constexpr (OPS) {
-            o.hi = ob[c];
-            o.lo = ob[G::CPLANE + c];
-            o.t1 = ob[2 * G::CPLANE + c];
-            o.t2 = ob[3 * G::CPLANE + c];
-          } else {
-            o.hi = o.lo = o.t1 = o.t2 = T::zero();
-          }
-          return o;
-        };
-        static_for<0, U>([&](auto uc) {
-          constexpr int u = decltype(uc)::value;
-          constexpr int QB = (RQ + U + u) % QN;  // queue position of plane (zf + u) - M
-          const PointAux a0 = ax[u * TX * TY + tsl0];
-          const PointAux a1 = ax[u * TX * TY + tsl0 + TX];
-          const V nl0 = has_proj ? nl_term<P>(nlk, n_ent, a0.r0, a0.r1) : T::zero();
-          const V nl1 = has_proj ? nl_term<P>(nlk, n_ent, a1.r0, a1.r1) : T::zero();
-          V acc0, acc1;
-          stencil_rows2<M, P, QB, QN>(W, w0, Q0, Q1, xs + u * G::PLANE, hs0, SXO,
-                                      *reinterpret_cast<const R *>(&a0.veff), *reinterpret_cast<const R *>(&a1.veff),
-                                      acc0, acc1);
-          const bool live0 = own0 && (zf + u < z1), live1 = own1 && (zf + u < z1);
-          if (has_proj) {
-            acc0 = T::add(acc0, nl0);
-            acc1 = T::add(acc1, nl1);
-          }
-          const V c00 = Q0[(QB + M) % QN], c01 = Q1[(QB + M) % QN];
-          if (MODE == MODE_FIRST && do_obs) {
-            if (live0) oa.add_e(c00, acc0);
-            if (live1) oa.add_e(c01, acc1);
-          }
-          const long iu = idx + (long)u * plane_pts * OVC;
-          finish_point<P, MODE>(epi, CR, CI, live0, iu, v, c00, acc0, operands(csl0));
-          finish_point<P, MODE>(epi, CR, CI, live1, iu + row, v, c01, acc1, operands(csl0 + TX * OVC));
-        });
-        __syncwarp();
-        if (lane == 0) {
-          mbar_arrive(&hempty[hs]);
-          if constexpr (OPS) mbar_arrive(&oempty[os]);
-        }
-        idx += U * plane_pts * OVC;
-        rh.next<SH>();
-        if (OPS) ro.next<SO>();
-      }
-      l++;
-    };
-    // every item starts at queue rotation 0, so the plane loop runs in unrolled blocks of
-    // QN / U iterations (one full turn of the queue), each with its compile-time rotation
-    while (l < nl && !aborted) {
-      static_for<0, QN / U>([&](auto j) {
-        if (l < nl && !aborted) iteration(std::integral_constant<int, decltype(j)::value * U>{});
-      });
-    }
-    if (aborted) break;
-    if (MODE == MODE_FIRST && do_obs) {
-      // this warp's partials of the item: record local * WS_CWARPS + warp
-      double vals[4] = {oa.get_e(), oa.get_j(0), oa.get_j(1), oa.get_j(2)};
-#pragma unroll
-      for (int i = 0; i < 4; i++) {
-        double x = vals[i];
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        if (lane == 0) p.obs_part[(local * WS_CWARPS + warp) * 4 + i] = epi.wocc * x;
-      }
-    }
-  }
-  if (aborted) {
-    *abort_flag = 1;
-    if (lane == 0 && errp) atomicExch(errp, 1);
-  }
-}
-
-template <int M, int P, int MODE, int TX, int TY, int U>
-__global__ void __launch_bounds__(WS_THREADS, 1)
-ws_sweep_kernel(const __grid_constant__ SweepMaps maps, const __grid_constant__ SweepParams p) {
-  const SingleSrc src{&p, &maps};
-  ws_sweep_body<M, P, MODE, TX, TY, U, false>(src, p.work);
-}
-
-template <int M, int P, int MODE, int TX, int TY, int U>
-__global__ void __launch_bounds__(WS_THREADS, 1)
-ws_sweep_batch_kernel(const __grid_constant__ BatchSweepArgs a) {
-  const BatchSrc src{&a};
-  ws_sweep_body<M, P, MODE, TX, TY, U, true>(src, a.work);
-}
-
 // Planes per TMA copy of a sweep mode (the z depth of its tensor-map boxes): the lockstep
 // kernel takes two planes per iteration in the complex64 term sweeps, everything else one.
 int tma_planes(int prec, int mode, bool lockstep) { return (lockstep && prec == P_C64 && mode != MODE_LAST) ? 2 : 1; }
 
 bool tma_supported(int M, int tx, int ty) { return (M == 2 || M == 4) && tx == 16 && ty == 8; }
 
-template <int M, int P, int MODE, int U, bool WS>
-static cudaError_t launch_tma_t(const SweepMaps &maps, const SweepParams &p, int grid, cudaStream_t s) {
+// Lockstep kernel (16x8 tiles; complex64 term sweeps take two planes per iteration).
+template <int M, int P, int MODE, int U>
+static cudaError_t launch_lockstep_t(const SweepMaps &maps, const SweepParams &p, int grid, cudaStream_t s) {
   typedef TmaGeom<M, 16, 8, U, MODE == MODE_LAST> G;
-  void (*k)(const SweepMaps, const SweepParams);
-  if constexpr (WS) k = ws_sweep_kernel<M, P, MODE, 16, 8, U>;
-  else k = tma_sweep_kernel<M, P, MODE, 16, 8, U>;
+  auto k = tma_sweep_kernel<M, P, MODE, 16, 8, U>;
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
@@ -870,14 +252,17 @@ static cudaError_t launch_tma_t(const SweepMaps &maps, const SweepParams &p, int
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     grid = (int)(p.n_items < sms ? p.n_items : sms);
   }
-  k<<<grid, WS ? WS_THREADS : OVC * 16 * 8, G::SMEM, s>>>(maps, p);
+  k<<<grid, OVC * 16 * 8, G::SMEM, s>>>(maps, p);
   return cudaGetLastError();
 }
 
 template <int M, int P, int MODE, int U>
 static cudaError_t launch_tma_batch_t(const BatchSweepArgs &a, cudaStream_t s) {
-  typedef TmaGeom<M, 16, 8, U, MODE == MODE_LAST> G;
-  auto k = ws_sweep_batch_kernel<M, P, MODE, 16, 8, U>;
+  constexpr int TX = WsShape<0>::TX, TY = WsShape<0>::TY, R = WsShape<0>::R;
+  typedef TmaGeom<M, TX, TY, U, MODE == MODE_LAST> G;
+  auto k = ws_sweep_batch_kernel<M, P, MODE, TX, TY, R, U>;
+  static_assert(WsWarps<TX, TY, R>::CW == WS_CONSUMER_WARPS, "batched sweeps write one partial record per consumer warp");
+  static_assert(TX == 16 && TY == 8, "batched tensor maps use 16x8 tiles");
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
@@ -889,7 +274,7 @@ static cudaError_t launch_tma_batch_t(const BatchSweepArgs &a, cudaStream_t s) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = (int)(a.total_items < sms ? a.total_items : sms);
   if (grid <= 0) return cudaSuccess;
-  k<<<grid, WS_THREADS, G::SMEM, s>>>(a);
+  k<<<grid, WsWarps<TX, TY, R>::THREADS, G::SMEM, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -910,31 +295,61 @@ cudaError_t launch_sweep_tma_batch(int M, int prec, int mode, const BatchSweepAr
   return cudaErrorInvalidValue;
 }
 
-// Planes per iteration = tma_planes(prec, mode, !WS).
-template <int M, int P, bool WS>
-static cudaError_t tma_by_mode(int mode, const SweepMaps &maps, const SweepParams &p, int grid, cudaStream_t s) {
+template <int M, int P>
+static cudaError_t lockstep_by_mode(int mode, const SweepMaps &maps, const SweepParams &p, int grid, cudaStream_t s) {
   switch (mode) {
-    case MODE_FIRST: return launch_tma_t<M, P, MODE_FIRST, (P == P_C64 && !WS) ? 2 : 1, WS>(maps, p, grid, s);
-    case MODE_MID: return launch_tma_t<M, P, MODE_MID, (P == P_C64 && !WS) ? 2 : 1, WS>(maps, p, grid, s);
-    case MODE_LAST: return launch_tma_t<M, P, MODE_LAST, 1, WS>(maps, p, grid, s);
+    case MODE_FIRST: return launch_lockstep_t<M, P, MODE_FIRST, P == P_C64 ? 2 : 1>(maps, p, grid, s);
+    case MODE_MID: return launch_lockstep_t<M, P, MODE_MID, P == P_C64 ? 2 : 1>(maps, p, grid, s);
+    case MODE_LAST: return launch_lockstep_t<M, P, MODE_LAST, 1>(maps, p, grid, s);
   }
   return cudaErrorInvalidValue;
 }
 
-template <bool WS>
-static cudaError_t tma_dispatch(int M, int prec, int mode, const SweepMaps &maps, const SweepParams &p, int grid,
-                                cudaStream_t s) {
-  if (M == 2) return prec == P_C64 ? tma_by_mode<2, P_C64, WS>(mode, maps, p, grid, s)
-                                   : tma_by_mode<2, P_C128, WS>(mode, maps, p, grid, s);
-  return prec == P_C64 ? tma_by_mode<4, P_C64, WS>(mode, maps, p, grid, s)
-                       : tma_by_mode<4, P_C128, WS>(mode, maps, p, grid, s);
+// Shapes 1..4 are compiled in translation units of their own (tdks_sweep_ws*.cu).
+extern template cudaError_t launch_ws_shape<1>(int, int, int, const SweepMaps &, const SweepParams &, int, cudaStream_t);
+extern template cudaError_t launch_ws_shape<2>(int, int, int, const SweepMaps &, const SweepParams &, int, cudaStream_t);
+extern template cudaError_t launch_ws_shape<3>(int, int, int, const SweepMaps &, const SweepParams &, int, cudaStream_t);
+extern template cudaError_t launch_ws_shape<4>(int, int, int, const SweepMaps &, const SweepParams &, int, cudaStream_t);
+template cudaError_t launch_ws_shape<0>(int, int, int, const SweepMaps &, const SweepParams &, int, cudaStream_t);
+
+template <int SHAPE>
+static void shape_of(int *tx, int *ty, int *rows, int *warps) {
+  typedef WsShape<SHAPE> S;
+  if (tx) *tx = S::TX;
+  if (ty) *ty = S::TY;
+  if (rows) *rows = S::R;
+  if (warps) *warps = WsWarps<S::TX, S::TY, S::R>::CW;
+}
+
+bool ws_shape_info(int shape, int *tx, int *ty, int *rows, int *warps) {
+  switch (shape) {
+    case 0: shape_of<0>(tx, ty, rows, warps); return true;
+    case 1: shape_of<1>(tx, ty, rows, warps); return true;
+    case 2: shape_of<2>(tx, ty, rows, warps); return true;
+    case 3: shape_of<3>(tx, ty, rows, warps); return true;
+    case 4: shape_of<4>(tx, ty, rows, warps); return true;
+  }
+  return false;
 }
 
 cudaError_t launch_sweep_tma(int M, int prec, int mode, int tx, int ty, const SweepMaps &maps, const SweepParams &p,
-                             int grid, cudaStream_t s, bool lockstep) {
+                             int grid, cudaStream_t s, bool lockstep, int shape) {
   if (!tma_supported(M, tx, ty)) return cudaErrorInvalidValue;
-  return lockstep ? tma_dispatch<false>(M, prec, mode, maps, p, grid, s)
-                  : tma_dispatch<true>(M, prec, mode, maps, p, grid, s);
+  if (lockstep) {
+    if (M == 2) return prec == P_C64 ? lockstep_by_mode<2, P_C64>(mode, maps, p, grid, s)
+                                     : lockstep_by_mode<2, P_C128>(mode, maps, p, grid, s);
+    return prec == P_C64 ? lockstep_by_mode<4, P_C64>(mode, maps, p, grid, s)
+                         : lockstep_by_mode<4, P_C128>(mode, maps, p, grid, s);
+  }
+  switch (shape) {
+    case 0: return launch_ws_shape<0>(M, prec, mode, maps, p, grid, s);
+    case 1: return launch_ws_shape<1>(M, prec, mode, maps, p, grid, s);
+    case 2: return launch_ws_shape<2>(M, prec, mode, maps, p, grid, s);
+    case 3: return launch_ws_shape<3>(M, prec, mode, maps, p, grid, s);
+    case 4: return launch_ws_shape<4>(M, prec, mode, maps, p, grid, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace tdks
+

@@ -1,0 +1,7 @@
+// Warp-specialised TMA sweep, tile shape 4 (see WsShape in tdks_tma.cuh), compiled on its
+// own so that the shapes build in parallel.
+#include "tdks_tma.cuh"
+
+namespace tdks {
+template cudaError_t launch_ws_shape<4>(int, int, int, const SweepMaps &, const SweepParams &, int, cudaStream_t);
+}  // namespace tdks

@@ -58,6 +58,9 @@ struct tdks_system {
   void *d_nl = nullptr;       // non-local term per sphere point, [n_kb][n_ent + 1][OVC]
   int n_sp = 0, n_ent = 0;
   tdks::ProjEntry *d_ent = nullptr;
+  float4 *d_ent_beta = nullptr;  // compact copies of the entries' FP32 beta and (cell, atom)
+  int2 *d_ent_ca = nullptr;
+  double *fin_part = nullptr;    // first-stage partials of the observable record
   void *d_q = nullptr;
   double2 *d_qpart = nullptr;   // gather partial sums, gchunks per (atom, k-batch)
   int gchunks = 1;
@@ -80,6 +83,7 @@ struct tdks_system {
   static constexpr long long RING = 65536;
   // stencil configuration
   int tx = 16, ty = 8, zc = 0;
+  int wshape[4] = {0, 0, 0, 0};  // warp-specialised TMA sweep: tile shape of each Taylor term
   long long launches = 0;
   // profiling
   bool profile = false;
@@ -94,14 +98,19 @@ namespace tdks_host {
 void fd_weights(int M, double *lap, double *grad);
 void field_at(const tdks_system *s, double t, double E[3], double A[3]);
 double envelope_of(const tdks_system *s, double t, double *denv);
-void sweep_geometry(const tdks_system *s, tdks::SweepParams &p);
-void sweep_common(const tdks_system *s, tdks::SweepParams &p, const double A[3]);
+// sweep: which of the four Taylor-term sweeps (0..3) the parameters are for, so that the
+// warp-specialised TMA sweep takes that sweep's tile shape; -1: the system's tile (16x8 on
+// the TMA path)
+bool ws_path(const tdks_system *s);
+void sweep_geometry(const tdks_system *s, tdks::SweepParams &p, int sweep = -1);
+void sweep_common(const tdks_system *s, tdks::SweepParams &p, const double A[3], int sweep = -1);
 long n_items_of(const tdks_system *s);
-bool encode_map(const tdks_system *s, const void *ptr, int mode, CUtensorMap *out, bool lockstep);
+bool encode_map(const tdks_system *s, const void *ptr, int mode, CUtensorMap *out, bool lockstep, int tx, int ty);
 // all maps of a TMA sweep of `mode` over input `in` (the operand maps only for the last term)
 // lockstep: box depths for the lockstep TMA kernel (tdks_set_sweep_path 2), else for the
 // warp-specialised one
-bool encode_sweep_maps(const tdks_system *s, const void *in, int mode, tdks::SweepMaps *out, bool lockstep);
+bool encode_sweep_maps(const tdks_system *s, const void *in, int mode, tdks::SweepMaps *out, bool lockstep,
+                       int sweep = -1);
 int ensure_density(tdks_system *s);
 int check_err(tdks_system *s);
 double kinetic_max(const tdks_system *s);

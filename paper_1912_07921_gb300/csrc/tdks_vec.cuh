@@ -69,6 +69,14 @@ __device__ __forceinline__ float two_sum(float a, float b, float &e) {
   e = (a - (s - bb)) + (b - bb);
   return s;
 }
+// (h, l) += (bh, bl), both double-float
+__device__ __forceinline__ void df_add_df(float &h, float &l, float bh, float bl) {
+  float e;
+  const float s = two_sum(h, bh, e);
+  e += l + bl;
+  h = s + e;
+  l = e - (h - s);
+}
 // accumulate x into the double-float (h, l)
 __device__ __forceinline__ void df_acc(float &h, float &l, float x) {
   float e;

@@ -20,6 +20,21 @@ def _dp(a: np.ndarray) -> ctypes.c_void_p:
     return ctypes.c_void_p(a.ctypes.data)
 
 
+def shape_count() -> int:
+    n = ctypes.c_int()
+    _lib.check(_lib.load().tdks_sweep_shape_info(0, ctypes.byref(n), None, None, None, None))
+    return n.value
+
+
+def shape_info(shape: int):
+    """(tx, ty, rows, warps) of a TMA sweep tile shape: tx x ty points per work item, rows
+    y-adjacent points per consumer thread, `warps` consumer warps."""
+    tx, ty, rows, warps = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _lib.check(_lib.load().tdks_sweep_shape_info(shape, None, ctypes.byref(tx), ctypes.byref(ty),
+                                                  ctypes.byref(rows), ctypes.byref(warps)))
+    return tx.value, ty.value, rows.value, warps.value
+
+
 class System:
     """One TDKS system resident on the current CUDA device."""
 
@@ -82,6 +97,28 @@ class System:
         """0: TMA-fed warp-specialised sweep where it applies (finite boxes, 16x8 tiles);
         1: general sweep; 2: TMA-fed sweep with all warps of a CTA in lockstep."""
         _lib.check(self.lib.tdks_set_sweep_path(self.h, path))
+
+    def set_sweep_shape(self, sweep: int, shape: int):
+        """Tile shape of one Taylor-term sweep (0..3; -1: all) of the TMA sweep."""
+        _lib.check(self.lib.tdks_set_sweep_shape(self.h, sweep, shape))
+
+    def sweep_shapes(self):
+        """The tile shape of each of the four Taylor-term sweeps."""
+        out = []
+        for i in range(4):
+            v = ctypes.c_int()
+            _lib.check(self.lib.tdks_get_sweep_shape(self.h, i, ctypes.byref(v)))
+            out.append(v.value)
+        return out
+
+    def autotune(self, reps: int = 5) -> np.ndarray:
+        """Time every tile shape on each Taylor-term sweep of this system and keep the
+        fastest per sweep; returns the mean ms per launch as [shape][sweep] (-1 where the
+        system does not take the TMA sweep)."""
+        n = shape_count()
+        ms = np.zeros(n * 4, dtype=np.float64)
+        _lib.check(self.lib.tdks_autotune(self.h, reps, ms.ctypes.data_as(_lib.PD)))
+        return ms.reshape(n, 4)
 
     # -- queries ---------------------------------------------------------------------
     def get_orbitals(self) -> np.ndarray:

@@ -108,6 +108,85 @@ def test_propagation_tma_and_general_paths_agree(prec):
         assert rel_err(r[1], res[0][1]) < tol
 
 
+@pytest.mark.parametrize("prec", [I.PREC_C128, I.PREC_C64])
+def test_apply_H_is_independent_of_sweep_shape(prec):
+    """Every tile shape of the warp-specialised TMA sweep (16x8, 16x12 and 14x8 tiles; 1 to
+    4 points per thread; 6 to 16 consumer warps) applies the same per-point arithmetic in
+    the same order, on a 37 x 21 x 19 grid that is ragged for all of them."""
+    from paper_1912_07921_gb300.system import shape_count, shape_info
+    spec = ragged_molecule(prec, n_orb=11 if prec == I.PREC_C64 else 5)
+    inp = I.make_inputs(spec)
+    sysm = _system(spec, inp)
+    psi = I.random_orbitals(spec, 9)
+    outs = []
+    n = shape_count()
+    assert n >= 2
+    for sh in range(n):
+        tx, ty, rows, warps = shape_info(sh)
+        assert 4 * tx * ty == 32 * warps * rows and ty % rows == 0
+        sysm.set_sweep_shape(-1, sh)
+        assert sysm.sweep_shapes() == [sh] * 4
+        outs.append(_apply_gpu(sysm, psi, 0.3))
+    tol = 1e-14 if prec == I.PREC_C128 else 1e-6
+    for o in outs[1:]:
+        assert rel_err(o, outs[0]) < tol
+    sysm.close()
+
+
+def test_mixed_sweep_shapes_match_oracle_c128():
+    """A different tile shape for each of the four Taylor-term sweeps: the propagation
+    (2 sub-steps per step, projectors, laser, LDA) still matches the FP64 oracle."""
+    from paper_1912_07921_gb300.system import shape_count
+    spec = ragged_molecule(I.PREC_C128)
+    inp = I.make_inputs(spec)
+    n = shape_count()
+    sysm = _system(spec, inp)
+    for sweep in range(4):
+        sysm.set_sweep_shape(sweep, (sweep + 1) % n)
+    sysm.propagate(0.0, 0.03, 3, 2)
+    rec = sysm.reductions(0, 3)
+    psi = sysm.get_orbitals()
+    sysm.close()
+    o = oracle.System(spec, inp)
+    psi_o, rec_o = o.propagate(inp.psi0, 0.0, 0.03, 3, 2)
+    assert rel_err(psi, psi_o) < 1e-12
+    assert _rec_err(rec, rec_o) < 1e-12
+
+
+@pytest.mark.parametrize("prec", [I.PREC_C128, I.PREC_C64])
+def test_autotune_keeps_state_and_results(prec):
+    """The autotuner times every shape on every sweep, keeps the fastest, leaves the state
+    untouched, and the propagation that follows equals one with the default shapes."""
+    from paper_1912_07921_gb300.system import shape_count
+    spec = ragged_molecule(prec, n_orb=11 if prec == I.PREC_C64 else 5)
+    inp = I.make_inputs(spec)
+    a = _system(spec, inp)
+    before = a.get_orbitals()
+    ms = a.autotune(reps=2)
+    assert ms.shape == (shape_count(), 4)
+    assert np.all(ms > 0)
+    assert a.sweep_shapes() == [int(i) for i in np.argmin(ms, axis=0)]
+    assert np.array_equal(a.get_orbitals(), before)
+    a.propagate(0.0, 0.03, 2, 2)
+    b = _system(spec, inp)
+    b.propagate(0.0, 0.03, 2, 2)
+    tol = 1e-13 if prec == I.PREC_C128 else 1e-6
+    assert rel_err(a.get_orbitals(), b.get_orbitals()) < tol
+    assert rel_err(a.reductions(0, 2), b.reductions(0, 2)) < tol
+    a.close()
+    b.close()
+
+
+def test_autotune_leaves_periodic_cells_alone():
+    """Periodic cells take the general sweep: nothing to tune, -1 everywhere."""
+    spec = bloch_cell(I.PREC_C64)
+    sysm = _system(spec, bloch_inputs(spec))
+    ms = sysm.autotune(reps=1)
+    assert np.all(ms == -1.0)
+    assert sysm.sweep_shapes() == [0, 0, 0, 0]
+    sysm.close()
+
+
 def _propagate_both(spec, inp, n_steps, substeps, dt=None):
     dt = spec.dt if dt is None else dt
     sysm = _system(spec, inp)
