@@ -314,11 +314,11 @@ def run_c128_side(args):
             "ms_per_step": ms / k}
 
 
-def run_batched(args):
+def run_batched(args, n_sample=16):
     """The batched workload: n independent molecules (edges U[32,80], 4..32 orbitals,
     0..12 atoms with projectors, complex64, 4th-order FD, h = 0.25, dt = 0.015), advanced
     by one persistent sweep launch per Taylor term over all of them, replayed as a CUDA
-    graph."""
+    graph.  Also returns the first n_sample systems' records (for the precision check)."""
     import torch
     from paper_1912_07921_gb300 import inputs as I
     from paper_1912_07921_gb300.system import Batch, System
@@ -330,6 +330,9 @@ def run_batched(args):
         s.set_clock(0.0, sp.dt, sp.substeps)
         systems.append(s)
     b = Batch(systems, stream=stream.cuda_stream)
+    # the autotuner times every tile shape on each Taylor term's batched sweep (outside the
+    # timed region) and keeps the fastest per term
+    tune = None if args.no_tune else b.autotune(reps=2)
     b.propagate(2)
     torch.cuda.synchronize()
     k = max(2, args.steps // 10)
@@ -343,11 +346,67 @@ def run_batched(args):
     upd = sum(sp.n_points * sp.n_orb for sp in specs)
     out = {"systems": len(specs), "value": upd * k / (ms / 1e3), "unit": UNIT, "steps": k,
            "ms_per_step": ms / k, "values_per_step": upd, "launches": b.launch_count() - l0,
-           "graph": True}
+           "graph": True, "sweep_shapes": b.shapes(),
+           "autotune_ms_per_launch": None if tune is None else [[round(float(x), 4) for x in r] for r in tune]}
+    records = [systems[i].reductions(0, 2 + k) for i in range(min(n_sample, len(systems)))]
     b.close()
     for s in systems:
         s.close()
-    return out
+    return out, specs[:len(records)], records
+
+
+def run_fp64_reference_path(specs, records32):
+    """The plain FP64 single-system path on a sample of the batched systems: each system
+    alone in complex128 (FP64 H psi, FP64 state), propagated over the same steps as the
+    batched complex64 run.  Returns its throughput and the complex64 batch's dipole error
+    against it: max over systems of max_t |d32(t) - d64(t)| / max_t |d64(t)|, and the same
+    for the induced dipole d(t) - d(0)."""
+    import dataclasses as dc
+    import torch
+    from paper_1912_07921_gb300 import inputs as I
+    from paper_1912_07921_gb300.system import System
+    stream = torch.cuda.Stream()
+    tot_ms, tot_upd, err, err_ind = 0.0, 0, 0.0, 0.0
+    for sp, r32 in zip(specs, records32):
+        n = r32.shape[0]
+        sp64 = dc.replace(sp, prec=I.PREC_C128)
+        s = System(sp64, I.make_inputs(sp64), stream=stream.cuda_stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.propagate(0.0, sp.dt, n, sp.substeps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tot_ms += e0.elapsed_time(e1)
+        tot_upd += sp.n_points * sp.n_orb * n
+        r64 = s.reductions(0, n)
+        s.close()
+        d32, d64 = r32[:, 4:7], r64[:, 4:7]
+        err = max(err, float(np.max(np.abs(d32 - d64)) / np.max(np.abs(d64))))
+        i32, i64 = d32 - d32[0], d64 - d64[0]
+        if np.max(np.abs(i64)) > 0:
+            err_ind = max(err_ind, float(np.max(np.abs(i32 - i64)) / np.max(np.abs(i64))))
+    return {"value": tot_upd / (tot_ms / 1e3), "unit": UNIT, "systems": len(specs),
+            "steps": int(records32[0].shape[0]), "dipole_err": err, "induced_dipole_err": err_ind}
+
+
+def run_tiny_dipole_check():
+    """Dipole of the tiny molecule over 1000 steps: complex64 H psi (double-float state,
+    FP64 reductions) against complex128, both on the GPU."""
+    import dataclasses as dc
+    import torch
+    from paper_1912_07921_gb300 import inputs as I
+    from paper_1912_07921_gb300.system import System
+    stream = torch.cuda.Stream()
+    recs = []
+    for prec in (I.PREC_C64, I.PREC_C128):
+        spec = I.tiny_molecule(prec=prec, n_steps=1000)
+        s = System(spec, I.make_inputs(spec), stream=stream.cuda_stream)
+        s.propagate(0.0, spec.dt, spec.n_steps, spec.substeps)
+        torch.cuda.synchronize()
+        recs.append(s.reductions(0, spec.n_steps))
+        s.close()
+    d32, d64 = recs[0][:, 4:7], recs[1][:, 4:7]
+    return float(np.max(np.abs(d32 - d64)) / np.max(np.abs(d64)))
 
 
 def run_periodic_side(args):
@@ -385,11 +444,15 @@ def run_periodic_side(args):
 
 
 def run_serving(args):
-    """A scaled serving trace (Poisson arrivals) through the continuous-batching server."""
+    """A scaled serving trace (Poisson arrivals) through the continuous-batching server.
+    Each request carries its inputs (built before the server starts, as a client would
+    send them); latency runs from arrival to results on the host."""
     import torch
-    from paper_1912_07921_gb300 import serving
+    from paper_1912_07921_gb300 import inputs as I, serving
     jobs = serving.serving_trace(args.serving, rate=20.0, seed=5, edge=(32, 64), orbitals=(4, 32),
                                  steps=(50, 400), atoms=(0, 16))
+    for j in jobs:
+        j.inputs = I.make_inputs(j.spec)
     stream = torch.cuda.Stream()
     srv = serving.Server(hbm_budget=150 * 10 ** 9, max_slots=64, quantum=50, stream=stream.cuda_stream,
                          sync=torch.cuda.synchronize)
@@ -466,7 +529,7 @@ def main():
     ap.add_argument("--batched", type=int, default=256,
                     help="also measure the batched workload with this many systems (0: skip)")
     ap.add_argument("--no-periodic", action="store_true", help="skip the periodic-cell side measurement")
-    ap.add_argument("--serving", type=int, default=0,
+    ap.add_argument("--serving", type=int, default=48,
                     help="also run a serving trace with this many jobs")
     ap.add_argument("--n-orb", type=int, default=0,
                     help="orbital count override (profiling on a smaller case); 0 = the workload's 64")
@@ -491,7 +554,17 @@ def main():
         if not args.no_c128 and args.prec == "c64" and world == 1:
             out["c128_path"] = run_c128_side(args)
         if args.batched and world == 1:
-            out["batched"] = run_batched(args)
+            out["batched"], sample, rec32 = run_batched(args)
+            ref = run_fp64_reference_path(sample, rec32)
+            out["fp32_vs_fp64"] = {
+                "factor": out["batched"]["value"] / ref["value"],
+                "fp32": "batched complex64 H psi (double-float state, FP64 reductions), all systems, graph",
+                "fp64": f"each of the first {ref['systems']} batched systems alone in complex128",
+                "fp64_value": ref["value"], "unit": UNIT,
+                "dipole_err": ref["dipole_err"], "induced_dipole_err": ref["induced_dipole_err"],
+                "dipole_err_over": f"{ref['steps']} steps of those systems",
+                "tiny_molecule_dipole_err_1000_steps": run_tiny_dipole_check(),
+                "err_definition": "max_t |d32 - d64| / max_t |d64| (induced: d(t) - d(0))"}
         if not args.no_periodic and world == 1:
             out["periodic"] = run_periodic_side(args)
         if args.serving and world == 1:

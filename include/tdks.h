@@ -263,6 +263,18 @@ int tdks_batch_create(const tdks_sys *systems, int n, void *stream, tdks_batch_t
  * sub-step.  Asynchronous on the batch's stream. */
 int tdks_batch_propagate(tdks_batch_t batch, int n_steps, int use_graph);
 int tdks_batch_launch_count(tdks_batch_t batch, long long *count);
+/* Sweep tile shape of Taylor term `term` (0..3, or -1 for all) of the batched sweep (see
+ * tdks_sweep_shape_info); synchronises the batch's streams.  No passage of the paper
+ * defines tiles; results do not depend on the choice except in the last bits of the
+ * energy sums. */
+int tdks_batch_set_shape(tdks_batch_t batch, int term, int shape);
+int tdks_batch_get_shape(tdks_batch_t batch, int term, int *shape);
+/* Autotuner of the batched sweep: times every shape on each Taylor term's batched sweep
+ * over all the batch's systems (reps launches after one warm-up, CUDA events) and keeps
+ * the fastest per term.  No system's state changes; the Taylor-term buffers and density
+ * partials are overwritten and rebuilt by the next tdks_batch_propagate.  ms (if not NULL):
+ * mean milliseconds per launch as ms[shape * 4 + term].  Synchronises. */
+int tdks_batch_autotune(tdks_batch_t batch, int reps, double *ms);
 int tdks_batch_destroy(tdks_batch_t batch);
 
 /*

@@ -46,6 +46,9 @@ SIGNATURES = {
     "tdks_batch_propagate": ([P, I, I], I),
     "tdks_batch_launch_count": ([P, PLL], I),
     "tdks_batch_destroy": ([P], I),
+    "tdks_batch_set_shape": ([P, I, I], I),
+    "tdks_batch_get_shape": ([P, I, PI], I),
+    "tdks_batch_autotune": ([P, I, PD], I),
     "tdks_apply_H_noalloc": ([I, I, I, D, I, I, I, P, P, P, P], I),
     "tdks_last_error": ([], ctypes.c_char_p),
 }

@@ -21,16 +21,20 @@ struct tdks_batch {
   cudaStream_t work = nullptr;     // private stream the batch captures and runs on
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   int M = 0, prec = 0, substeps = 0;
+  int shape[4] = {0, 0, 0, 0};     // sweep tile shape of each Taylor term (tdks_batch_autotune)
   // device arrays
   SweepParams *d_sweep[4] = {nullptr, nullptr, nullptr, nullptr};   // per Taylor term
   GatherParams *d_gather[4] = {nullptr, nullptr, nullptr, nullptr};
   SweepMaps *d_maps = nullptr;                                      // 4 per system
-  long *d_item_begin = nullptr, *d_gather_begin = nullptr, *d_unit_begin = nullptr, *d_lda_begin = nullptr;
+  long *d_item_begin[4] = {nullptr, nullptr, nullptr, nullptr};     // per Taylor term
+  long *d_gather_begin = nullptr, *d_unit_begin = nullptr, *d_lda_begin = nullptr;
   long *d_nl_begin = nullptr;
   unsigned int *d_work = nullptr;  // work-item counter of the batched sweep (zero between launches)
   BatchAux *d_aux = nullptr;
+  std::vector<BatchAux> aux_h;     // host copy (the record count follows the first term's shape)
   BatchClock *d_clock = nullptr;
-  long total_items = 0, total_gather = 0, total_units = 0, total_lda = 0, total_nl = 0;
+  long total_items[4] = {0, 0, 0, 0};
+  long total_gather = 0, total_units = 0, total_lda = 0, total_nl = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   long long launches = 0;
@@ -39,8 +43,8 @@ struct tdks_batch {
 namespace {
 
 void batch_free(tdks_batch *b) {
-  for (int k = 0; k < 4; k++) { cudaFree(b->d_sweep[k]); cudaFree(b->d_gather[k]); }
-  cudaFree(b->d_maps); cudaFree(b->d_item_begin); cudaFree(b->d_gather_begin); cudaFree(b->d_lda_begin);
+  for (int k = 0; k < 4; k++) { cudaFree(b->d_sweep[k]); cudaFree(b->d_gather[k]); cudaFree(b->d_item_begin[k]); }
+  cudaFree(b->d_maps); cudaFree(b->d_gather_begin); cudaFree(b->d_lda_begin);
   cudaFree(b->d_nl_begin); cudaFree(b->d_work);
   cudaFree(b->d_unit_begin);
   cudaFree(b->d_aux); cudaFree(b->d_clock);
@@ -68,9 +72,9 @@ int enqueue_substep(tdks_batch *b) {
     e = launch_gather_batch(b->prec, b->d_gather[k], b->d_gather_begin, b->d_unit_begin, b->d_nl_begin, n,
                             b->total_gather, b->total_units, b->total_nl, b->work);
     if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("batched gather: ") + cudaGetErrorString(e));
-    BatchSweepArgs a{b->d_sweep[k], b->d_maps, k, b->d_item_begin, n, b->total_items, b->d_work};
+    BatchSweepArgs a{b->d_sweep[k], b->d_maps, k, b->d_item_begin[k], n, b->total_items[k], b->d_work};
     const int mode = k == 0 ? MODE_FIRST : (k == 3 ? MODE_LAST : MODE_MID);
-    e = launch_sweep_tma_batch(b->M, b->prec, mode, a, b->work);
+    e = launch_sweep_tma_batch(b->M, b->prec, mode, a, b->work, b->shape[k]);
     if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("batched sweep: ") + cudaGetErrorString(e));
     if (k == 0) {
       e = launch_batch_tail(b->d_aux, b->d_clock, n, 0, b->work);
@@ -88,6 +92,74 @@ int upload(T **dst, const std::vector<T> &v) {
   CU(cudaMalloc((void **)dst, std::max<size_t>(1, v.size()) * sizeof(T)));
   if (!v.empty()) CU(cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
   return TDKS_OK;
+}
+
+// Sweep tables of the batch for its current shapes: per Taylor term the systems' sweep
+// parameters, tensor maps (one per system and term) and work-item prefix sums; whole z
+// columns per item (many systems already balance the grid).  tune: the last term's
+// tables point the state operands at the Taylor-term buffers (state hi <- t1, lo <- t2), so
+// the autotuner can time it without touching any state.  The captured graph, which holds
+// the old tables, is dropped.
+int build_sweep_tables(tdks_batch *b, bool tune) {
+  const int n = (int)b->sys.size();
+  std::vector<SweepParams> sp[4];
+  std::vector<SweepMaps> maps(4 * (size_t)n);
+  std::vector<long> ib[4];
+  for (int k = 0; k < 4; k++) ib[k].assign(n + 1, 0);
+  const int modes[4] = {MODE_FIRST, MODE_MID, MODE_MID, MODE_LAST};
+  const double A0[3] = {0.0, 0.0, 0.0};
+  for (int i = 0; i < n; i++) {
+    tdks_system *s = b->sys[i];
+    const int save_tx = s->tx, save_ty = s->ty, save_zc = s->zc;
+    const void *ins[4] = {s->psi, s->term[0], s->term[1], s->term[2]};
+    const double dts = s->clock_dt / s->clock_substeps;
+    bool ok = true;
+    for (int k = 0; k < 4 && ok; k++) {
+      int tx = 16, ty = 8;
+      ws_shape_info(b->shape[k], &tx, &ty, nullptr, nullptr);
+      s->tx = tx; s->ty = ty; s->zc = s->nz;
+      ok = encode_sweep_maps(s, ins[k], modes[k], &maps[4 * i + k], false);
+      SweepParams p{};
+      sweep_common(s, p, A0);
+      set_coef(p, 0.0, -dts / (k + 1));
+      p.in = ins[k];
+      p.do_obs = k == 0;
+      p.err = s->d_err;
+      if (k < 3) {
+        p.out = s->term[k];
+      } else if (!tune) {
+        p.psi = s->psi; p.psi_lo = s->psi_lo; p.t1 = s->term[0]; p.t2 = s->term[1];
+      } else {
+        p.psi = s->term[0]; p.psi_lo = s->term[1]; p.t1 = s->term[0]; p.t2 = s->term[1];
+        const void *ops[4] = {s->term[0], s->term[1], s->term[0], s->term[1]};
+        for (int j = 0; j < 4 && ok; j++) ok = encode_op_map(s, ops[j], &maps[4 * i + k].op[j], tx, ty);
+      }
+      sp[k].push_back(p);
+      ib[k][i + 1] = ib[k][i] + p.n_items;
+    }
+    s->tx = save_tx; s->ty = save_ty; s->zc = save_zc;
+    if (!ok) return fail(TDKS_EDEVICE, "tensor map encoding failed");
+    // the warp-specialised sweep writes one partial record per consumer warp and item
+    int warps = 8;
+    ws_shape_info(b->shape[0], nullptr, nullptr, nullptr, &warps);
+    b->aux_h[i].n_items = sp[0].back().n_items * warps;
+  }
+  for (int k = 0; k < 4; k++) {
+    cudaFree(b->d_sweep[k]); b->d_sweep[k] = nullptr;
+    cudaFree(b->d_item_begin[k]); b->d_item_begin[k] = nullptr;
+  }
+  cudaFree(b->d_maps); b->d_maps = nullptr;
+  int rc = TDKS_OK;
+  for (int k = 0; k < 4 && !rc; k++) {
+    rc = upload(&b->d_sweep[k], sp[k]);
+    if (!rc) rc = upload(&b->d_item_begin[k], ib[k]);
+    b->total_items[k] = ib[k][n];
+  }
+  if (!rc) rc = upload(&b->d_maps, maps);
+  if (!rc && b->d_aux) CU(cudaMemcpy(b->d_aux, b->aux_h.data(), n * sizeof(BatchAux), cudaMemcpyHostToDevice));
+  if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+  if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+  return rc;
 }
 
 }  // namespace
@@ -133,35 +205,16 @@ int tdks_batch_create(const tdks_sys *systems, int n, void *stream, tdks_batch_t
     if (!s->have_orbitals) return bad("orbitals not set");
     if (!tma_supported(s->M, 16, 8)) return bad("no TMA sweep for this FD order");
   }
-  std::vector<SweepParams> sp[4];
   std::vector<GatherParams> gp[4];
-  std::vector<SweepMaps> maps(4 * n);
-  std::vector<long> item_begin(n + 1, 0), gather_begin(n + 1, 0), unit_begin(n + 1, 0), lda_begin(n + 1, 0);
+  std::vector<long> gather_begin(n + 1, 0), unit_begin(n + 1, 0), lda_begin(n + 1, 0);
   std::vector<long> nl_begin(n + 1, 0);
-  std::vector<BatchAux> aux(n);
+  std::vector<BatchAux> &aux = b->aux_h;
+  aux.assign(n, BatchAux{});
   std::vector<BatchClock> clk(n);
   for (int i = 0; i < n; i++) {
     tdks_system *s = b->sys[i];
-    const int save_tx = s->tx, save_ty = s->ty, save_zc = s->zc;
-    s->tx = 16; s->ty = 8; s->zc = s->nz;  // whole columns: many systems already balance the grid
     const void *ins[4] = {s->psi, s->term[0], s->term[1], s->term[2]};
-    const int modes[4] = {MODE_FIRST, MODE_MID, MODE_MID, MODE_LAST};
-    const double A0[3] = {0.0, 0.0, 0.0};
-    const double dts = s->clock_dt / s->clock_substeps;
     for (int k = 0; k < 4; k++) {
-      if (!encode_sweep_maps(s, ins[k], modes[k], &maps[4 * i + k], false)) {
-        s->tx = save_tx; s->ty = save_ty; s->zc = save_zc;
-        return bad("tensor map encoding failed");
-      }
-      SweepParams p{};
-      sweep_common(s, p, A0);
-      set_coef(p, 0.0, -dts / (k + 1));
-      p.in = ins[k];
-      p.do_obs = k == 0;
-      p.err = s->d_err;
-      if (k < 3) p.out = s->term[k];
-      else { p.psi = s->psi; p.psi_lo = s->psi_lo; p.t1 = s->term[0]; p.t2 = s->term[1]; }
-      sp[k].push_back(p);
       GatherParams g{};
       g.n_kb = s->n_kb; g.n_batches = s->n_batches; g.n_atoms = s->n_atoms; g.N = s->N;
       g.in = ins[k]; g.atom_begin = s->d_atom_begin; g.ent = s->d_ent; g.D = s->d_D;
@@ -171,7 +224,6 @@ int tdks_batch_create(const tdks_sys *systems, int n, void *stream, tdks_batch_t
       g.sp = s->d_sp; g.n_sp = s->n_sp; g.rowent = s->d_rowent; g.n_ent = s->n_ent; g.nl = s->d_nl;
       gp[k].push_back(g);
     }
-    item_begin[i + 1] = item_begin[i] + sp[0].back().n_items;
     gather_begin[i + 1] = gather_begin[i] + (long)s->n_atoms * s->n_kb * (s->n_atoms > 0 ? s->gchunks : 0);
     unit_begin[i + 1] = unit_begin[i] + (long)s->n_atoms * s->n_kb;
     nl_begin[i + 1] = nl_begin[i] + (s->n_atoms > 0 ? nl_blocks(s->n_sp, s->n_kb) : 0);
@@ -184,23 +236,15 @@ int tdks_batch_create(const tdks_sys *systems, int n, void *stream, tdks_batch_t
     for (int d = 0; d < 3; d++) a.pol[d] = s->pol[d];
     a.amp = s->amp; a.omega = s->omega; a.t_total = s->t_total;
     a.dens_part = s->dens_part; a.vloc = s->vloc; a.aux = s->aux; a.lda_part = s->lda_part; a.n_lda = nl;
-    // the warp-specialised sweep writes one partial record per consumer warp and item
-    a.obs_part = s->obs_part; a.n_items = sp[0].back().n_items * WS_CONSUMER_WARPS; a.ring = s->ring;
+    a.obs_part = s->obs_part; a.ring = s->ring;  // a.n_items: set with the sweep tables
     a.ring_len = tdks_system::RING;
-    s->tx = save_tx; s->ty = save_ty; s->zc = save_zc;
   }
-  b->total_items = item_begin[n];
+  int rc = build_sweep_tables(b, false);
   b->total_gather = gather_begin[n];
   b->total_units = unit_begin[n];
   b->total_lda = lda_begin[n];
   b->total_nl = nl_begin[n];
-  int rc = TDKS_OK;
-  for (int k = 0; k < 4 && !rc; k++) {
-    if (!rc) rc = upload(&b->d_sweep[k], sp[k]);
-    if (!rc) rc = upload(&b->d_gather[k], gp[k]);
-  }
-  if (!rc) rc = upload(&b->d_maps, maps);
-  if (!rc) rc = upload(&b->d_item_begin, item_begin);
+  for (int k = 0; k < 4 && !rc; k++) rc = upload(&b->d_gather[k], gp[k]);
   if (!rc) rc = upload(&b->d_gather_begin, gather_begin);
   if (!rc) rc = upload(&b->d_unit_begin, unit_begin);
   if (!rc) rc = upload(&b->d_lda_begin, lda_begin);
@@ -275,6 +319,73 @@ int tdks_batch_propagate(tdks_batch_t b, int n_steps, int use_graph) {
     s->dens_valid = true;
   }
   return TDKS_OK;
+}
+
+int tdks_batch_set_shape(tdks_batch_t b, int term, int shape) {
+  if (!b) return fail(TDKS_EINVAL, "NULL batch");
+  if (term < -1 || term > 3) return fail(TDKS_EINVAL, "term must be 0..3 or -1");
+  if (!ws_shape_info(shape, nullptr, nullptr, nullptr, nullptr)) return fail(TDKS_EINVAL, "no such sweep shape");
+  CU(cudaStreamSynchronize(b->stream));
+  CU(cudaStreamSynchronize(b->work));
+  for (int k = 0; k < 4; k++)
+    if (term < 0 || term == k) b->shape[k] = shape;
+  return build_sweep_tables(b, false);
+}
+
+int tdks_batch_get_shape(tdks_batch_t b, int term, int *shape) {
+  if (!b || !shape) return fail(TDKS_EINVAL, "NULL argument");
+  if (term < 0 || term > 3) return fail(TDKS_EINVAL, "term must be 0..3");
+  *shape = b->shape[term];
+  return TDKS_OK;
+}
+
+int tdks_batch_autotune(tdks_batch_t b, int reps, double *ms) {
+  if (!b) return fail(TDKS_EINVAL, "NULL batch");
+  if (reps < 1) return fail(TDKS_EINVAL, "reps < 1");
+  if (ms)
+    for (int i = 0; i < WS_SHAPES * 4; i++) ms[i] = -1.0;
+  CU(cudaStreamSynchronize(b->stream));
+  CU(cudaStreamSynchronize(b->work));
+  const int n = (int)b->sys.size();
+  const int saved[4] = {b->shape[0], b->shape[1], b->shape[2], b->shape[3]};
+  int pick[4] = {saved[0], saved[1], saved[2], saved[3]};
+  double best[4] = {-1.0, -1.0, -1.0, -1.0};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CU(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(TDKS_EDEVICE, "cudaEventCreate");
+  }
+  int rc = TDKS_OK;
+  const int modes[4] = {MODE_FIRST, MODE_MID, MODE_MID, MODE_LAST};
+  for (int sh = 0; sh < WS_SHAPES && !rc; sh++) {
+    for (int k = 0; k < 4; k++) b->shape[k] = sh;
+    if ((rc = build_sweep_tables(b, true))) break;
+    for (int k = 0; k < 4 && !rc; k++) {
+      BatchSweepArgs a{b->d_sweep[k], b->d_maps, k, b->d_item_begin[k], n, b->total_items[k], b->d_work};
+      cudaError_t e = launch_sweep_tma_batch(b->M, b->prec, modes[k], a, b->work, sh);  // warm-up
+      cudaEventRecord(e0, b->work);
+      for (int r = 0; r < reps && e == cudaSuccess; r++)
+        e = launch_sweep_tma_batch(b->M, b->prec, modes[k], a, b->work, sh);
+      cudaEventRecord(e1, b->work);
+      if (e != cudaSuccess) { rc = fail(TDKS_EDEVICE, std::string("batched sweep: ") + cudaGetErrorString(e)); break; }
+      if (cudaEventSynchronize(e1) != cudaSuccess) { rc = fail(TDKS_EDEVICE, "batch autotune timing"); break; }
+      for (tdks_system *s : b->sys)
+        if ((rc = check_err(s))) break;
+      if (rc) break;
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      const double per = (double)t / reps;
+      if (ms) ms[sh * 4 + k] = per;
+      if (best[k] < 0.0 || per < best[k]) { best[k] = per; pick[k] = sh; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (int k = 0; k < 4; k++) b->shape[k] = rc ? saved[k] : pick[k];
+  const int rc2 = build_sweep_tables(b, false);
+  for (tdks_system *s : b->sys) s->dens_valid = false;  // the timed last terms wrote density partials
+  return rc ? rc : rc2;
 }
 
 int tdks_batch_launch_count(tdks_batch_t b, long long *count) {

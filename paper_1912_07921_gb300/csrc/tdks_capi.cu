@@ -238,7 +238,7 @@ bool encode_aux_map(const tdks_system *s, int mode, CUtensorMap *out, bool locks
 }
 
 // Map over a packed array with the tile box (no halo) of z depth `depth`.
-bool encode_op_map(const tdks_system *s, const void *ptr, CUtensorMap *out, int tx, int ty, int depth = 1) {
+bool encode_op_map(const tdks_system *s, const void *ptr, CUtensorMap *out, int tx, int ty, int depth) {
   EncodeTiledFn fn = encode_fn();
   if (!fn || (reinterpret_cast<uintptr_t>(ptr) & 15) != 0) return false;
   const cuuint64_t dims[5] = {16, (cuuint64_t)s->nx, (cuuint64_t)s->ny, (cuuint64_t)s->nz, (cuuint64_t)s->n_kb};

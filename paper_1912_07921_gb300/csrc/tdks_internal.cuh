@@ -162,9 +162,6 @@ struct BatchSweepArgs {
   unsigned int *work;     // work-item counter (zero between launches)
 };
 
-// Consumer warps of the warp-specialised TMA sweep; each writes its own energy/current
-// partials, so an item of that kernel has WS_CONSUMER_WARPS partial records.
-constexpr int WS_CONSUMER_WARPS = 8;
 
 // Launchers (tdks_sweep.cu)
 cudaError_t launch_sweep(int M, int prec, int mode, int bloch, int tx, int ty,
@@ -216,7 +213,8 @@ bool ws_shape_info(int shape, int *tx, int *ty, int *rows, int *warps);
 bool tma_supported(int M, int tx, int ty);
 int tma_planes(int prec, int mode, bool lockstep = false);
 int lda_blocks(long N);
-cudaError_t launch_sweep_tma_batch(int M, int prec, int mode, const BatchSweepArgs &a, cudaStream_t s);
+cudaError_t launch_sweep_tma_batch(int M, int prec, int mode, const BatchSweepArgs &a, cudaStream_t s,
+                                   int shape = 0);
 // begin: prefix sums of n_atoms * n_kb * n_chunks (stage 1 CTAs); ubegin: of n_atoms * n_kb;
 // nbegin: of the non-local kernel's CTAs, n_kb * ceil(n_sp * OVC / NL_THREADS)
 cudaError_t launch_gather_batch(int prec, const GatherParams *gp, const long *begin, const long *ubegin,

@@ -256,42 +256,21 @@ static cudaError_t launch_lockstep_t(const SweepMaps &maps, const SweepParams &p
   return cudaGetLastError();
 }
 
-template <int M, int P, int MODE, int U>
-static cudaError_t launch_tma_batch_t(const BatchSweepArgs &a, cudaStream_t s) {
-  constexpr int TX = WsShape<0>::TX, TY = WsShape<0>::TY, R = WsShape<0>::R;
-  typedef TmaGeom<M, TX, TY, U, MODE == MODE_LAST> G;
-  auto k = ws_sweep_batch_kernel<M, P, MODE, TX, TY, R, U>;
-  static_assert(WsWarps<TX, TY, R>::CW == WS_CONSUMER_WARPS, "batched sweeps write one partial record per consumer warp");
-  static_assert(TX == 16 && TY == 8, "batched tensor maps use 16x8 tiles");
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = (int)(a.total_items < sms ? a.total_items : sms);
-  if (grid <= 0) return cudaSuccess;
-  k<<<grid, WsWarps<TX, TY, R>::THREADS, G::SMEM, s>>>(a);
-  return cudaGetLastError();
-}
+extern template cudaError_t launch_ws_batch_shape<1>(int, int, int, const BatchSweepArgs &, cudaStream_t);
+extern template cudaError_t launch_ws_batch_shape<2>(int, int, int, const BatchSweepArgs &, cudaStream_t);
+extern template cudaError_t launch_ws_batch_shape<3>(int, int, int, const BatchSweepArgs &, cudaStream_t);
+extern template cudaError_t launch_ws_batch_shape<4>(int, int, int, const BatchSweepArgs &, cudaStream_t);
+template cudaError_t launch_ws_batch_shape<0>(int, int, int, const BatchSweepArgs &, cudaStream_t);
 
-// One plane per iteration (= tma_planes for the warp-specialised kernel).
-template <int M, int P>
-static cudaError_t tma_batch_by_mode(int mode, const BatchSweepArgs &a, cudaStream_t s) {
-  switch (mode) {
-    case MODE_FIRST: return launch_tma_batch_t<M, P, MODE_FIRST, 1>(a, s);
-    case MODE_MID: return launch_tma_batch_t<M, P, MODE_MID, 1>(a, s);
-    case MODE_LAST: return launch_tma_batch_t<M, P, MODE_LAST, 1>(a, s);
+cudaError_t launch_sweep_tma_batch(int M, int prec, int mode, const BatchSweepArgs &a, cudaStream_t s, int shape) {
+  if (M != 2 && M != 4) return cudaErrorInvalidValue;
+  switch (shape) {
+    case 0: return launch_ws_batch_shape<0>(M, prec, mode, a, s);
+    case 1: return launch_ws_batch_shape<1>(M, prec, mode, a, s);
+    case 2: return launch_ws_batch_shape<2>(M, prec, mode, a, s);
+    case 3: return launch_ws_batch_shape<3>(M, prec, mode, a, s);
+    case 4: return launch_ws_batch_shape<4>(M, prec, mode, a, s);
   }
-  return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_sweep_tma_batch(int M, int prec, int mode, const BatchSweepArgs &a, cudaStream_t s) {
-  if (M == 2) return prec == P_C64 ? tma_batch_by_mode<2, P_C64>(mode, a, s) : tma_batch_by_mode<2, P_C128>(mode, a, s);
-  if (M == 4) return prec == P_C64 ? tma_batch_by_mode<4, P_C64>(mode, a, s) : tma_batch_by_mode<4, P_C128>(mode, a, s);
   return cudaErrorInvalidValue;
 }
 

@@ -106,6 +106,8 @@ void sweep_geometry(const tdks_system *s, tdks::SweepParams &p, int sweep = -1);
 void sweep_common(const tdks_system *s, tdks::SweepParams &p, const double A[3], int sweep = -1);
 long n_items_of(const tdks_system *s);
 bool encode_map(const tdks_system *s, const void *ptr, int mode, CUtensorMap *out, bool lockstep, int tx, int ty);
+// tile box (no halo) of z depth `depth` over a packed array
+bool encode_op_map(const tdks_system *s, const void *ptr, CUtensorMap *out, int tx, int ty, int depth = 1);
 // all maps of a TMA sweep of `mode` over input `in` (the operand maps only for the last term)
 // lockstep: box depths for the lockstep TMA kernel (tdks_set_sweep_path 2), else for the
 // warp-specialised one

@@ -666,6 +666,47 @@ static cudaError_t launch_ws_t(const SweepMaps &maps, const SweepParams &p, int 
   return cudaGetLastError();
 }
 
+// Launch of the batched warp-specialised sweep of shape SHAPE: 152 persistent CTAs (one per
+// SM, at most one per work item) walk the items of every system of the batch.
+template <int SHAPE, int M, int P, int MODE>
+static cudaError_t launch_ws_batch_t(const BatchSweepArgs &a, cudaStream_t s) {
+  constexpr int TX = WsShape<SHAPE>::TX, TY = WsShape<SHAPE>::TY, R = WsShape<SHAPE>::R;
+  typedef TmaGeom<M, TX, TY, 1, MODE == MODE_LAST> G;
+  auto k = ws_sweep_batch_kernel<M, P, MODE, TX, TY, R, 1>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = (int)(a.total_items < sms ? a.total_items : sms);
+  if (grid <= 0) return cudaSuccess;
+  k<<<grid, WsWarps<TX, TY, R>::THREADS, G::SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int SHAPE>
+cudaError_t launch_ws_batch_shape(int M, int prec, int mode, const BatchSweepArgs &a, cudaStream_t s) {
+#define TDKS_WSB_MODES(MM, PP)                                                    \
+  switch (mode) {                                                                 \
+    case MODE_FIRST: return launch_ws_batch_t<SHAPE, MM, PP, MODE_FIRST>(a, s);   \
+    case MODE_MID: return launch_ws_batch_t<SHAPE, MM, PP, MODE_MID>(a, s);       \
+    case MODE_LAST: return launch_ws_batch_t<SHAPE, MM, PP, MODE_LAST>(a, s);     \
+  }                                                                               \
+  return cudaErrorInvalidValue;
+  if (M == 2) {
+    if (prec == P_C64) { TDKS_WSB_MODES(2, P_C64) } else { TDKS_WSB_MODES(2, P_C128) }
+  }
+  if (M == 4) {
+    if (prec == P_C64) { TDKS_WSB_MODES(4, P_C64) } else { TDKS_WSB_MODES(4, P_C128) }
+  }
+#undef TDKS_WSB_MODES
+  return cudaErrorInvalidValue;
+}
+
 // Every mode, FD order and precision of one shape (instantiated once per shape, in a
 // translation unit of its own).
 template <int SHAPE>

@@ -35,6 +35,7 @@ class Job:
     steps_done: int = 0
     records: Optional[np.ndarray] = None
     orbitals: Optional[np.ndarray] = None
+    inputs: Optional[I.Inputs] = None  # the request's payload (built at admission when absent)
     system: Optional[System] = None
     nbytes: int = 0
 
@@ -105,7 +106,7 @@ class Server:
     # -- admission / eviction -----------------------------------------------------------
     def _admit(self, job: Job, now: float):
         job.nbytes = job_bytes(job.spec)
-        inp = self.make_inputs(job.spec)
+        inp = job.inputs if job.inputs is not None else self.make_inputs(job.spec)
         job.system = System(job.spec, inp, stream=self.stream)
         job.system.set_clock(0.0, job.spec.dt, job.spec.substeps)
         job.admitted = now
@@ -120,6 +121,7 @@ class Server:
         job.finished = now_fn()
         job.system.close()
         job.system = None
+        job.inputs = None
         self.used -= job.nbytes
         self.active.remove(job)
         self.done.append(job)

@@ -232,6 +232,26 @@ class Batch:
         _lib.check(self.lib.tdks_batch_launch_count(self.h, ctypes.byref(c)))
         return c.value
 
+    def set_shape(self, term: int, shape: int):
+        """Sweep tile shape of one Taylor term (0..3; -1: all) of the batched sweep."""
+        _lib.check(self.lib.tdks_batch_set_shape(self.h, term, shape))
+
+    def shapes(self):
+        out = []
+        for k in range(4):
+            v = ctypes.c_int()
+            _lib.check(self.lib.tdks_batch_get_shape(self.h, k, ctypes.byref(v)))
+            out.append(v.value)
+        return out
+
+    def autotune(self, reps: int = 3) -> np.ndarray:
+        """Time every tile shape on each Taylor term's batched sweep and keep the fastest;
+        returns the mean ms per launch as [shape][term]."""
+        n = shape_count()
+        ms = np.zeros(n * 4, dtype=np.float64)
+        _lib.check(self.lib.tdks_batch_autotune(self.h, reps, ms.ctypes.data_as(_lib.PD)))
+        return ms.reshape(n, 4)
+
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:
             self.lib.tdks_batch_destroy(self.h)

@@ -72,3 +72,38 @@ def test_batch_matches_oracle_c128():
         psi_o, rec_o = oracle.System(spec, inp).propagate(inp.psi0, 0.0, spec.dt, 3, 1)
         assert rel_err(psi, psi_o) < 1e-12
         np.testing.assert_allclose(rec, rec_o, rtol=1e-12, atol=1e-12 * np.abs(rec_o).max())
+
+
+@pytest.mark.parametrize("prec", [I.PREC_C128, I.PREC_C64])
+def test_batch_autotune_and_shapes_keep_results(prec):
+    """The batched autotuner times every tile shape on each Taylor term without touching
+    any state; a batch with tuned (or mixed) shapes gives each system its alone result."""
+    from paper_1912_07921_gb300.system import Batch, System, shape_count
+    specs = small_uneven_batch(prec, n=4, seed=13)
+    inps = [I.make_inputs(s) for s in specs]
+    alone, _ = _run(specs, inps, 2, batched=False)
+    stream = torch.cuda.current_stream().cuda_stream
+    for mode in ("tuned", "mixed"):
+        systems = [System(s, i, stream=stream) for s, i in zip(specs, inps)]
+        for s in systems:
+            s.set_clock(0.0, s.spec.dt, s.spec.substeps)
+        b = Batch(systems, stream=stream)
+        before = [s.get_orbitals() for s in systems]
+        if mode == "tuned":
+            ms = b.autotune(reps=2)
+            assert ms.shape == (shape_count(), 4) and np.all(ms > 0)
+            assert b.shapes() == [int(i) for i in np.argmin(ms, axis=0)]
+            for s, p0 in zip(systems, before):
+                assert np.array_equal(s.get_orbitals(), p0)
+        else:
+            for k in range(4):
+                b.set_shape(k, (k + 2) % shape_count())
+        b.propagate(2)
+        torch.cuda.synchronize()
+        tol = 1e-13 if prec == I.PREC_C128 else 1e-6
+        for s, (pa, ra) in zip(systems, alone):
+            assert rel_err(s.get_orbitals(), pa) < tol
+            assert rel_err(s.reductions(0, 2), ra) < tol
+        b.close()
+        for s in systems:
+            s.close()
