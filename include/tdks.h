@@ -99,7 +99,9 @@ int tdks_set_local_potential(tdks_sys sys, const double *v);
 /* Orbitals: host array in the host layout (2 * n_k * N * n_orb doubles), copied (the call
  * returns once the buffer has been read; pinned memory gives the fastest upload) and packed
  * on the device in chunks that overlap the copy, together with the density of the new
- * state.  The packing is asynchronous on the system's stream. */
+ * state.  The packing is asynchronous on the system's stream and replaces the state after
+ * all work enqueued there before the call; the copy itself waits only for the previous
+ * upload's packing, so an upload issued while a propagation runs overlaps it. */
 int tdks_set_orbitals(tdks_sys sys, const double *psi);
 
 /* Copy the current orbitals out into the host layout.  Synchronises. */

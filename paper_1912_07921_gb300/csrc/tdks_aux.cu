@@ -299,8 +299,8 @@ cudaError_t launch_gather(int prec, int bloch, const GatherParams &p, cudaStream
 // with closed-shell f_i = 2):
 //   complex128 systems: dens_part[kb][r] = w_k f sum_j |psi|^2 (double);
 //   complex64 systems (state hi + lo): the 8-byte slot holds sum_j |psi|^2 unweighted, as a
-//   double-float pair (float hi, float lo); the LDA kernel weights and adds the blocks in
-//   FP64, so the sweeps that produce it run no FP64 instruction.
+//   double-float pair (float hi, float lo); the LDA kernel weights and adds the blocks as
+//   double-float, so neither the kernels that produce it nor the LDA run FP64 per point.
 // ---------------------------------------------------------------------------------
 __global__ void density_c128_kernel(long N, int n_kb, int n_batches, const double2 *psi, const double *wocc,
                                     double *dens_part) {
@@ -317,27 +317,43 @@ __global__ void density_c128_kernel(long N, int n_kb, int n_batches, const doubl
   }
 }
 
+// |psi|^2 of one complex64 value held as the double-float pair (h, l), as s + e with FP32
+// operations only (h^2 exactly by FMA, + 2 h l), then summed over the 2 * OVC lanes of a
+// (point, batch) block with an xor tree (1, 2, 4) of double-float additions.  Lane 0 of the
+// block returns the block's sum.  pack_in_kernel and density_c64_kernel both use it, so a
+// state's density partials do not depend on which of them wrote them.
+__device__ __forceinline__ void block_sq_c64(float hx, float hy, float lx, float ly, float &sh, float &sl) {
+  float e;
+  sh = Combine<P_C64>::sq_parts(pk2(hx, hy), pk2(lx, ly), e);
+  sl = e;
+#pragma unroll
+  for (int o = 1; o < 2 * OVC; o <<= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, sh, o), ol = __shfl_xor_sync(0xffffffffu, sl, o);
+    float t;
+    sh = two_sum(sh, oh, t);
+    sl = sl + ol + t;
+  }
+}
+
+// Thread = one complex value of one (k-batch, point): 8 adjacent lanes per block.
 __global__ void density_c64_kernel(long N, int n_kb, int n_batches, const float2 *hi, const float2 *lo,
                                    const double *wocc, double *dens_part) {
-  const long total = (long)n_kb * N;
+  const long total = (long)n_kb * N * 2 * OVC;
   (void)wocc;
   (void)n_batches;
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
-    double s = 0.0;
-#pragma unroll
-    for (int j = 0; j < 2 * OVC; j++) {
-      const float2 a = hi[i * 2 * OVC + j], b = lo[i * 2 * OVC + j];
-      const double re = (double)a.x + (double)b.x, im = (double)a.y + (double)b.y;
-      s += re * re + im * im;
-    }
-    const float sh = (float)s;
-    reinterpret_cast<float2 *>(dens_part)[i] = make_float2(sh, (float)(s - (double)sh));
+  const long stride = (long)gridDim.x * blockDim.x;  // a multiple of 32, so lanes keep their value index
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i - threadIdx.x % 32 < total; i += stride) {
+    const bool live = i < total;
+    const float2 a = live ? hi[i] : make_float2(0.f, 0.f), b = live ? lo[i] : make_float2(0.f, 0.f);
+    float sh, sl;
+    block_sq_c64(a.x, a.y, b.x, b.y, sh, sl);
+    if (live && i % (2 * OVC) == 0) reinterpret_cast<float2 *>(dens_part)[i / (2 * OVC)] = make_float2(sh, sl);
   }
 }
 
 cudaError_t launch_density(int prec, long N, int n_kb, int n_batches, const void *psi, const void *psi_lo,
                            const double *wocc, double *dens_part, cudaStream_t s) {
-  const long total = (long)n_kb * N;
+  const long total = (long)n_kb * N * (prec == P_C64 ? 2 * OVC : 1);
   int grid = (int)((total + 255) / 256);
   if (grid > 152 * 16) grid = 152 * 16;
   if (prec == P_C64)
@@ -719,30 +735,25 @@ __global__ void pack_in_kernel(int c64, long N, int k, long pt0, long npts, int 
     const int o = b * BS + j;
     const double2 x = live && o < n_orb ? plain[((long)k * N + pt) * n_orb + o] : make_double2(0.0, 0.0);
     const long dst = (kb * N + pt) * BS + j;
-    double s;
     if (c64) {
+      // the value as a double-float pair, and the block's density partial with FP32
+      // operations only (GB300's FP64 pipe would otherwise bound this kernel)
       const float hx = (float)x.x, hy = (float)x.y;
       const float lx = (float)(x.x - (double)hx), ly = (float)(x.y - (double)hy);
       if (live) {
         reinterpret_cast<float2 *>(internal)[dst] = make_float2(hx, hy);
         reinterpret_cast<float2 *>(internal_lo)[dst] = make_float2(lx, ly);
       }
-      const double re = (double)hx + (double)lx, im = (double)hy + (double)ly;
-      s = re * re + im * im;
+      float sh, sl;
+      block_sq_c64(hx, hy, lx, ly, sh, sl);
+      if (live && j == 0) reinterpret_cast<float2 *>(dens_part)[kb * N + pt] = make_float2(sh, sl);
     } else {
       if (live) reinterpret_cast<double2 *>(internal)[dst] = x;
-      s = x.x * x.x + x.y * x.y;
-    }
-    // lane j of the point gathers the sum over the point's values in index order
-    double acc = 0.0;
-    for (int t = 0; t < BS; t++) acc += __shfl_sync(0xffffffffu, s, (threadIdx.x & 31 & ~(BS - 1)) + t);
-    if (live && j == 0) {
-      if (c64) {
-        const float sh = (float)acc;
-        reinterpret_cast<float2 *>(dens_part)[kb * N + pt] = make_float2(sh, (float)(acc - (double)sh));
-      } else {
-        dens_part[kb * N + pt] = wocc[k] * acc;
-      }
+      const double s = x.x * x.x + x.y * x.y;
+      // lane j of the point gathers the sum over the point's values in index order
+      double acc = 0.0;
+      for (int t = 0; t < BS; t++) acc += __shfl_sync(0xffffffffu, s, (threadIdx.x & 31 & ~(BS - 1)) + t);
+      if (live && j == 0) dens_part[kb * N + pt] = wocc[k] * acc;
     }
   }
 }

@@ -66,7 +66,8 @@ struct tdks_system {
   int gchunks = 1;
   double *staging = nullptr;
   cudaStream_t copy_stream = nullptr;  // host uploads, chunked so that packing overlaps them
-  cudaEvent_t ev_upload_ready = nullptr;
+  cudaEvent_t ev_staging_free = nullptr;  // recorded after the last kernel that reads the staging buffer
+  bool staging_pending = false;            // ev_staging_free has been recorded
   std::vector<cudaEvent_t> ev_chunk;
   int *d_err = nullptr;       // [0]: error word of the bounded waits; [1]: sweep work counter
   long obs_count = 0;         // energy/current partial records written by the last first sweep

@@ -187,6 +187,28 @@ def test_autotune_leaves_periodic_cells_alone():
     sysm.close()
 
 
+@pytest.mark.parametrize("prec", [I.PREC_C128, I.PREC_C64])
+def test_upload_issued_during_a_propagation_is_ordered(prec):
+    """tdks_set_orbitals issued right after an asynchronous tdks_propagate_n (its copy
+    overlaps the propagation) replaces the state only after the propagation: the records
+    equal those of an undisturbed run, and the new state is the uploaded one."""
+    spec = I.tiny_molecule(prec=prec)
+    inp = I.make_inputs(spec)
+    a = _system(spec, inp)
+    a.propagate(0.0, spec.dt, 40, 1)          # ~40 steps of GPU work still queued
+    psi1 = I.random_orbitals(spec, 3)
+    a.set_orbitals(psi1)                       # copied while the steps run
+    rec = a.reductions(0, 40)
+    got = a.get_orbitals()
+    b = _system(spec, inp)
+    b.propagate(0.0, spec.dt, 40, 1)
+    rec_b = b.reductions(0, 40)
+    assert np.array_equal(rec, rec_b)
+    assert rel_err(got, psi1) < 1e-13
+    a.close()
+    b.close()
+
+
 def _propagate_both(spec, inp, n_steps, substeps, dt=None):
     dt = spec.dt if dt is None else dt
     sysm = _system(spec, inp)
