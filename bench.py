@@ -425,7 +425,8 @@ def run_tiny_dipole_check():
 
 def run_periodic_side(args):
     """The periodic cell (64^3 Bloch cell, 32 k-points x 16 bands in complex64, velocity
-    gauge, 6 sub-steps per step) through the general sweep, a few steps."""
+    gauge, 6 sub-steps per step) through the TMA sweep with autotuned tile shapes, a few
+    steps."""
     import torch
     from paper_1912_07921_gb300 import inputs as I
     from paper_1912_07921_gb300.system import System
@@ -433,6 +434,7 @@ def run_periodic_side(args):
     inp = I.make_inputs(spec)
     stream = torch.cuda.Stream()
     sysm = System(spec, inp, stream=stream.cuda_stream)
+    tune = None if args.no_tune else sysm.autotune(reps=3)
     sysm.propagate(0.0, spec.dt, 2, spec.substeps)
     torch.cuda.synchronize()
     k = max(2, args.steps // 20)
@@ -446,15 +448,17 @@ def run_periodic_side(args):
     ms = e0.elapsed_time(e1)
     sweep_ms, sweep_n = sysm.kernel_time(0)
     sysm.set_profiling(False)
+    shapes = sysm.sweep_shapes()
     sysm.close()
     states = spec.n_orb * spec.n_k
     # algorithmic bytes per sweep launch: 104 B per value per sub-step (as the medium molecule's
     # complex64 path) over four sweeps, plus the 16-byte point records per orbital block
     per_launch = (spec.n_points * states * 104 + spec.n_points * 16 * 4 * (states // 8)) / 4
     return {"workload": "periodic cell 64^3 L=10.2 order-4 FD, 32 k x 16 bands c64, 8 atoms x 4 KB, "
-                        "velocity gauge A0=0.2, dt=0.04 as 6 Taylor-4 sub-steps (general sweep)",
+                        "velocity gauge A0=0.2, dt=0.04 as 6 Taylor-4 sub-steps",
             "value": spec.n_points * states * k / (ms / 1e3), "unit": UNIT, "steps": k, "ms_per_step": ms / k,
-            "sweep_gbs": per_launch / ((sweep_ms / 1e3) / max(sweep_n, 1)) / 1e9}
+            "sweep_gbs": per_launch / ((sweep_ms / 1e3) / max(sweep_n, 1)) / 1e9, "sweep_shapes": shapes,
+            "autotune_ms_per_launch": None if tune is None else [[round(float(x), 4) for x in r] for r in tune]}
 
 
 def run_serving(args):

@@ -125,8 +125,12 @@ struct Timed {
   }
 };
 
-bool ws_path(const tdks_system *s) {
-  return s->path == 0 && s->bc == TDKS_BC_ZERO && tma_supported(s->M, s->tx, s->ty);
+// The warp-specialised TMA sweep serves finite boxes and periodic cells (path 0, 16x8 system
+// tile); the lockstep TMA sweep (path 2) serves finite boxes only.
+bool ws_path(const tdks_system *s) { return s->path == 0 && tma_supported(s->M, s->tx, s->ty); }
+
+static bool tma_path(const tdks_system *s) {
+  return ws_path(s) || (s->path == 2 && s->bc == TDKS_BC_ZERO && tma_supported(s->M, s->tx, s->ty));
 }
 
 // Tile of a sweep: the warp-specialised TMA sweep's shape, else the system's tile.
@@ -145,7 +149,7 @@ void sweep_geometry(const tdks_system *s, SweepParams &p, int sweep) {
   p.n_kb = s->n_kb;
   p.n_batches = s->n_batches;
   int zc = s->zc;
-  const bool dynamic = s->path == 0 && s->bc == TDKS_BC_ZERO && tma_supported(s->M, s->tx, s->ty);
+  const bool dynamic = ws_path(s);
   if (zc <= 0 && dynamic) {
     // warp-specialised TMA sweep: CTAs claim items from a counter, so the cost is the total
     // work spread over the SMs (the 2M priming planes of an item only load a centre tile,
@@ -198,6 +202,7 @@ void sweep_common(const tdks_system *s, SweepParams &p, const double A[3], int s
   p.nl = s->d_nl;
   p.n_ent = s->n_ent;
   p.kvec = s->d_kvec;
+  p.bloch = s->bc == TDKS_BC_BLOCH;
   p.L[0] = s->nx * s->h; p.L[1] = s->ny * s->h; p.L[2] = s->nz * s->h;
   for (int a = 0; a < 3; a++) p.A[a] = A[a];
   p.grad_mask = 0;
@@ -256,6 +261,14 @@ bool encode_sweep_maps(const tdks_system *s, const void *in, int mode, SweepMaps
   if (!encode_map(s, in, mode, &out->in, lockstep, tx, ty) || !encode_aux_map(s, mode, &out->aux, lockstep, tx, ty) ||
       !encode_op_map(s, in, &out->ctr, tx, ty, tma_planes(s->prec, mode, lockstep)))
     return false;
+  if (s->bc == TDKS_BC_BLOCH) {
+    // periodic-image strips of boundary tiles: M columns over the slot's rows, M rows over
+    // the tile's columns
+    if (!encode_op_map(s, in, &out->sx, s->M, ty + 2 * s->M) || !encode_op_map(s, in, &out->sy, tx, s->M))
+      return false;
+  } else {
+    out->sx = out->sy = out->in;  // unused
+  }
   if (mode == MODE_LAST) {
     const void *ops[4] = {s->psi, s->psi_lo ? s->psi_lo : s->psi, s->term[0], s->term[1]};
     for (int j = 0; j < 4; j++)
@@ -268,7 +281,7 @@ bool encode_sweep_maps(const tdks_system *s, const void *in, int mode, SweepMaps
 
 void build_tmaps(tdks_system *s) {
   s->tmaps_ok = false;
-  if (s->bc != TDKS_BC_ZERO || !tma_supported(s->M, s->tx, s->ty)) return;
+  if (!tma_path(s)) return;
   const void *ins[4] = {s->psi, s->term[0], s->term[1], s->term[2]};
   const int modes[4] = {MODE_FIRST, MODE_MID, MODE_MID, MODE_LAST};
   for (int i = 0; i < 4; i++)
@@ -283,7 +296,7 @@ int run_sweep(tdks_system *s, int mode, SweepParams &p, const SweepMaps *tm, int
   Timed tmr(s, 0);
   p.err = s->d_err;
   cudaError_t e;
-  const bool tma = tm && s->path != 1 && s->bc == TDKS_BC_ZERO && tma_supported(s->M, s->tx, s->ty);
+  const bool tma = tm && tma_path(s);
   const bool ws = tma && s->path == 0;
   const int shape = (ws && sweep >= 0) ? s->wshape[sweep] : 0;
   if (tma)
@@ -912,8 +925,7 @@ int tdks_apply_H(tdks_sys s, double t, const void *dev_in, void *dev_out) {
   p.in = dev_in;
   p.out = dev_out;
   SweepMaps tm;
-  const bool have_tm = s->bc == TDKS_BC_ZERO && tma_supported(s->M, s->tx, s->ty) &&
-                       encode_sweep_maps(s, dev_in, MODE_MID, &tm, s->path == 2, 1);
+  const bool have_tm = tma_path(s) && encode_sweep_maps(s, dev_in, MODE_MID, &tm, s->path == 2, 1);
   return run_sweep(s, MODE_MID, p, have_tm ? &tm : nullptr, 1);
 }
 

@@ -69,6 +69,7 @@ struct SweepParams {
                               // sphere point whose entries start at r0; row n_ent is zero
   int n_ent;                  // projector entries
   // Bloch boundary
+  int bloch;                  // periodic cell: values across a face carry exp(i k.L) per wrap
   const double *kvec;         // [n_k][3]
   double L[3];
   double A[3];                // vector potential (velocity gauge)
@@ -148,6 +149,7 @@ struct BatchClock {
 // state lo, t1, t2 (tile boxes, depth 1).
 struct SweepMaps {
   CUtensorMap in, ctr, aux, op[4];
+  CUtensorMap sx, sy;  // periodic cells: the input as M x (TY + 2M) and TX x M strip boxes
 };
 
 // Batched stencil sweep over many systems (tdks_sweep_tma.cu): params[s] and

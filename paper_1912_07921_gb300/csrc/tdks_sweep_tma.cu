@@ -70,7 +70,7 @@ __device__ __forceinline__ void tma_sweep_body(const Src &src) {
   __shared__ LoadCursor cur[3];
   LoadCursor &cc = cur[0], &hc = cur[1], &oc = cur[2];
   if (tid == 0) {
-    for (int k = 0; k < 3; k++) cur[k] = LoadCursor{-1, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int k = 0; k < 3; k++) cur[k] = LoadCursor{-1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (int s = 0; s < SC; s++) ld.issue(cc, 0);
     for (int s = 0; s < SH; s++) ld.issue(hc, 1);
     if (OPS)
@@ -285,11 +285,15 @@ static cudaError_t lockstep_by_mode(int mode, const SweepMaps &maps, const Sweep
 }
 
 // Shapes 1..4 are compiled in translation units of their own (tdks_sweep_ws*.cu).
-extern template cudaError_t launch_ws_shape<1>(int, int, int, const SweepMaps &, const SweepParams &, int, cudaStream_t);
-extern template cudaError_t launch_ws_shape<2>(int, int, int, const SweepMaps &, const SweepParams &, int, cudaStream_t);
-extern template cudaError_t launch_ws_shape<3>(int, int, int, const SweepMaps &, const SweepParams &, int, cudaStream_t);
-extern template cudaError_t launch_ws_shape<4>(int, int, int, const SweepMaps &, const SweepParams &, int, cudaStream_t);
-template cudaError_t launch_ws_shape<0>(int, int, int, const SweepMaps &, const SweepParams &, int, cudaStream_t);
+extern template cudaError_t launch_ws_shape<1>(int, int, int, int, const SweepMaps &, const SweepParams &, int,
+                                                 cudaStream_t);
+extern template cudaError_t launch_ws_shape<2>(int, int, int, int, const SweepMaps &, const SweepParams &, int,
+                                                 cudaStream_t);
+extern template cudaError_t launch_ws_shape<3>(int, int, int, int, const SweepMaps &, const SweepParams &, int,
+                                                 cudaStream_t);
+extern template cudaError_t launch_ws_shape<4>(int, int, int, int, const SweepMaps &, const SweepParams &, int,
+                                                 cudaStream_t);
+template cudaError_t launch_ws_shape<0>(int, int, int, int, const SweepMaps &, const SweepParams &, int, cudaStream_t);
 
 template <int SHAPE>
 static void shape_of(int *tx, int *ty, int *rows, int *warps) {
@@ -314,6 +318,8 @@ bool ws_shape_info(int shape, int *tx, int *ty, int *rows, int *warps) {
 cudaError_t launch_sweep_tma(int M, int prec, int mode, int tx, int ty, const SweepMaps &maps, const SweepParams &p,
                              int grid, cudaStream_t s, bool lockstep, int shape) {
   if (!tma_supported(M, tx, ty)) return cudaErrorInvalidValue;
+  if (lockstep && p.bloch) return cudaErrorInvalidValue;  // periodic cells: warp-specialised sweep only
+  const int b = p.bloch;
   if (lockstep) {
     if (M == 2) return prec == P_C64 ? lockstep_by_mode<2, P_C64>(mode, maps, p, grid, s)
                                      : lockstep_by_mode<2, P_C128>(mode, maps, p, grid, s);
@@ -321,11 +327,11 @@ cudaError_t launch_sweep_tma(int M, int prec, int mode, int tx, int ty, const Sw
                          : lockstep_by_mode<4, P_C128>(mode, maps, p, grid, s);
   }
   switch (shape) {
-    case 0: return launch_ws_shape<0>(M, prec, mode, maps, p, grid, s);
-    case 1: return launch_ws_shape<1>(M, prec, mode, maps, p, grid, s);
-    case 2: return launch_ws_shape<2>(M, prec, mode, maps, p, grid, s);
-    case 3: return launch_ws_shape<3>(M, prec, mode, maps, p, grid, s);
-    case 4: return launch_ws_shape<4>(M, prec, mode, maps, p, grid, s);
+    case 0: return launch_ws_shape<0>(M, prec, mode, b, maps, p, grid, s);
+    case 1: return launch_ws_shape<1>(M, prec, mode, b, maps, p, grid, s);
+    case 2: return launch_ws_shape<2>(M, prec, mode, b, maps, p, grid, s);
+    case 3: return launch_ws_shape<3>(M, prec, mode, b, maps, p, grid, s);
+    case 4: return launch_ws_shape<4>(M, prec, mode, b, maps, p, grid, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -122,7 +122,10 @@ struct RingPos {
 //     output plane (state hi, state lo, t1, t2).
 // Keeping the z history in registers (not in the ring) lets every ring run several slots
 // ahead of the plane being computed.
-template <int M, int TX, int TY, int U, bool OPS>
+//   periodic cells (BL): each halo slot also holds the four periodic-image strips a boundary
+//     tile needs (the M columns beyond each x face over the slot's SY rows, the M rows beyond
+//     each y face over the tile's TX columns), loaded by TMA from the opposite faces.
+template <int M, int TX, int TY, int U, bool OPS, bool BL = false>
 struct TmaGeom {
   static constexpr int SX = TX + 2 * M, SY = TY + 2 * M;
   static constexpr int PLANE = SX * SY * OVC;                        // vectors per halo plane
@@ -130,7 +133,11 @@ struct TmaGeom {
   static constexpr uint32_t CSLOT_BYTES = (uint32_t)CPLANE * 16 * U;
   static constexpr uint32_t IN_BYTES = (uint32_t)PLANE * 16 * U;
   static constexpr uint32_t AUX_BYTES = (uint32_t)TX * TY * 16 * U;
-  static constexpr uint32_t HSLOT_BYTES = IN_BYTES + AUX_BYTES;
+  static constexpr uint32_t STRIPX_BYTES = (uint32_t)M * SY * OVC * 16;   // beyond x = 0 or x = nx - 1
+  static constexpr uint32_t STRIPY_BYTES = (uint32_t)TX * M * OVC * 16;   // beyond y = 0 or y = ny - 1
+  static constexpr uint32_t STRIP_BYTES = BL ? 2 * (STRIPX_BYTES + STRIPY_BYTES) : 0;
+  static constexpr uint32_t HSLOT_BYTES = IN_BYTES + AUX_BYTES + STRIP_BYTES;
+  static_assert(!BL || U == 1, "periodic cells take one plane per iteration");
   static constexpr uint32_t OPT_BYTES = (uint32_t)CPLANE * 16;       // one operand tile
   static constexpr uint32_t OP_BYTES = 4 * OPT_BYTES;
   static constexpr int SO = OPS ? 2 : 0;
@@ -194,7 +201,12 @@ struct LoadCursor {
   int tx, ty, kb, z0;
   int sys;     // system of the item (batch)
   long issued; // loads issued so far
+  int nx, ny, nz, wrap;  // periodic cell: centre planes outside [0, nz) are loaded wrapped, and
+                         // the halo slots of boundary tiles get their periodic-image strips
 };
+
+// floor(i / n) for possibly negative i
+__device__ __forceinline__ int floordiv_i(int i, int n) { return i >= 0 ? i / n : -((-i - 1) / n) - 1; }
 
 // Work item -> tile (tx, ty), orbital block kb and z chunk [z0, z1).
 __device__ __forceinline__ void item_geom(const SweepParams &q, long it, int &tx, int &ty, int &kb, int &z0,
@@ -243,6 +255,10 @@ struct Loader {
         item_geom(*qp, local, c.tx, c.ty, c.kb, c.z0, z1);
         c.sys = src.sys_of(blockIdx.x + c.ii * gridDim.x);
         c.n = loads_of<M, U>(kind, c.z0, z1);
+        c.nx = qp->nx;
+        c.ny = qp->ny;
+        c.nz = qp->nz;
+        c.wrap = qp->bloch;
       }
     }
   }
@@ -260,15 +276,30 @@ struct Loader {
     if (kind == 0) {
       const int slot = (int)(c.issued % SC);
       mbar_expect_tx(&cfull[slot], G::CSLOT_BYTES);
-      tma_load_5d(cbase + (size_t)slot * G::CSLOT_BYTES, &mp->ctr, &cfull[slot], 0, c.tx * TX, c.ty * TY,
-                  c.z0 - M + U * c.l, c.kb);
+      int zc = c.z0 - M + U * c.l;
+      if (c.wrap) zc -= floordiv_i(zc, c.nz) * c.nz;  // (U = 1 for periodic cells)
+      tma_load_5d(cbase + (size_t)slot * G::CSLOT_BYTES, &mp->ctr, &cfull[slot], 0, c.tx * TX, c.ty * TY, zc,
+                  c.kb);
     } else if (kind == 1) {
       const int slot = (int)(c.issued % SH);
       unsigned char *dst = hbase + (size_t)slot * G::HSLOT_BYTES;
       const int zp = c.z0 + U * c.l;
-      mbar_expect_tx(&hfull[slot], G::HSLOT_BYTES);
-      tma_load_5d(dst, &mp->in, &hfull[slot], 0, c.tx * TX - M, c.ty * TY - M, zp, c.kb);
-      tma_load_4d(dst + G::IN_BYTES, &mp->aux, &hfull[slot], 0, c.tx * TX, c.ty * TY, zp);
+      const int x0 = c.tx * TX, y0 = c.ty * TY;
+      // periodic cell: the strips this tile's halo crosses (the slot holds zeros there)
+      const bool sl = G::STRIP_BYTES && c.wrap && x0 - M < 0, sr = G::STRIP_BYTES && c.wrap && x0 + TX + M > c.nx;
+      const bool st = G::STRIP_BYTES && c.wrap && y0 - M < 0, sb = G::STRIP_BYTES && c.wrap && y0 + TY + M > c.ny;
+      const uint32_t bytes = G::IN_BYTES + G::AUX_BYTES + (uint32_t)(sl + sr) * G::STRIPX_BYTES +
+                             (uint32_t)(st + sb) * G::STRIPY_BYTES;
+      mbar_expect_tx(&hfull[slot], bytes);
+      tma_load_5d(dst, &mp->in, &hfull[slot], 0, x0 - M, y0 - M, zp, c.kb);
+      tma_load_4d(dst + G::IN_BYTES, &mp->aux, &hfull[slot], 0, x0, y0, zp);
+      if constexpr (G::STRIP_BYTES > 0) {
+        unsigned char *sd = dst + G::IN_BYTES + G::AUX_BYTES;
+        if (sl) tma_load_5d(sd, &mp->sx, &hfull[slot], 0, c.nx - M, y0 - M, zp, c.kb);
+        if (sr) tma_load_5d(sd + G::STRIPX_BYTES, &mp->sx, &hfull[slot], 0, 0, y0 - M, zp, c.kb);
+        if (st) tma_load_5d(sd + 2 * G::STRIPX_BYTES, &mp->sy, &hfull[slot], 0, x0, c.ny - M, zp, c.kb);
+        if (sb) tma_load_5d(sd + 2 * G::STRIPX_BYTES + G::STRIPY_BYTES, &mp->sy, &hfull[slot], 0, x0, 0, zp, c.kb);
+      }
     } else {
       const int slot = (int)(c.issued % SO);
       unsigned char *dst = obase + (size_t)slot * G::OP_BYTES;
@@ -338,14 +369,97 @@ __device__ __forceinline__ void stencil_rows(const typename VT<P>::S *W, typenam
   }
 }
 
-template <int M, int P, int MODE, int TX, int TY, int R, int U, bool BATCH, class Src>
+// Bloch phase of one wrap, e^{i ang} = c + i s, in the compute precision.
+template <int P>
+__device__ __forceinline__ void bloch_phase(double ang, typename VT<P>::S &c, typename VT<P>::S &s) {
+  if constexpr (P == P_C64) {
+    float sn, cs;
+    sincosf((float)ang, &sn, &cs);
+    c = pk2(cs, cs);
+    s = pk2(sn, sn);
+  } else {
+    double sn, cs;
+    sincos(ang, &sn, &cs);
+    c = cs;
+    s = sn;
+  }
+}
+// a times the phase of w wraps, (c + i s)^w (w = +-1 except in grids smaller than the stencil)
+template <int P>
+__device__ __forceinline__ typename VT<P>::V apply_phase(typename VT<P>::S c, typename VT<P>::S s, int w,
+                                                         typename VT<P>::V a) {
+  typedef VT<P> T;
+  if (w < 0) {
+    if constexpr (P == P_C64) s ^= SIGN2; else s = -s;
+  }
+  for (int i = w < 0 ? -w : w; i > 0; i--) a = T::cmul(c, s, a);
+  return a;
+}
+
+// Periodic (Bloch) cell: as stencil_rows, with the velocity-gauge gradient term -i A.grad_h
+// (and, for the current, the three gradients gax) in the order of stencil_point.  The halo
+// slot S already holds the phased periodic images beyond the faces (the patcher warp wrote
+// them), so the neighbours are read as in a finite box.
+template <int M, int P, int QB, int QN, int R>
+__device__ __forceinline__ void stencil_rows_bloch(const SweepParams &p, const typename VT<P>::S *W,
+                                                   typename W0T<P>::type w0, const typename VT<P>::V (*Q)[QN],
+                                                   const typename VT<P>::V *S, int hs0, int SXO,
+                                                   const typename VT<P>::R *ve, typename VT<P>::V *acc,
+                                                   typename VT<P>::V (*gax)[3], bool need_grad, bool grads) {
+  typedef VT<P> T;
+  typedef typename T::V V;
+  V col[2 * M + R];  // y = gy0 - M + k
+#pragma unroll
+  for (int k = 0; k < 2 * M + R; k++) col[k] = S[hs0 + (k - M) * SXO];
+  // gradient term as sum_m gw_m (A . d_m): 3 + M coefficients live instead of 3 M
+  typename T::S A3[3] = {};
+  if (need_grad) {
+#pragma unroll
+    for (int a = 0; a < 3; a++) A3[a] = T::bc(p.A[a]);
+  }
+  V gsum[R];
+#pragma unroll
+  for (int r = 0; r < R; r++) {
+    acc[r] = T::mul(T::diag(ve[r], w0), Q[r][(QB + M) % QN]);
+    gsum[r] = T::zero();
+    gax[r][0] = gax[r][1] = gax[r][2] = T::zero();
+  }
+#pragma unroll
+  for (int m = 1; m <= M; m++) {
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      const V xm = S[hs0 + r * SXO - m * OVC], xp = S[hs0 + r * SXO + m * OVC];
+      const V zm = Q[r][(QB + M - m) % QN], zp = Q[r][(QB + M + m) % QN];
+      const V ym = col[M + r - m], yp = col[M + r + m];
+      const V s6 = T::add(T::add(T::add(zm, zp), T::add(xm, xp)), T::add(ym, yp));
+      acc[r] = T::fma(W[m], s6, acc[r]);
+      if (need_grad) {
+        const V dx = T::sub(xp, xm), dy = T::sub(yp, ym), dz = T::sub(zp, zm);
+        const typename T::S gm = T::bc(p.gw[m]);
+        const V dA = T::fma(A3[0], dx, T::fma(A3[1], dy, T::mul(A3[2], dz)));
+        gsum[r] = T::fma(gm, dA, gsum[r]);
+        if (grads) {
+          gax[r][0] = T::fma(gm, dx, gax[r][0]);
+          gax[r][1] = T::fma(gm, dy, gax[r][1]);
+          gax[r][2] = T::fma(gm, dz, gax[r][2]);
+        }
+      }
+    }
+  }
+  if (need_grad) {
+#pragma unroll
+    for (int r = 0; r < R; r++) acc[r] = T::add(acc[r], T::negi(gsum[r]));
+  }
+}
+
+template <int M, int P, int MODE, int TX, int TY, int R, int U, bool BATCH, int BLOCH, class Src>
 __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work) {
   typedef VT<P> T;
   typedef typename T::V V;
   typedef typename T::S S_;
   typedef typename T::R Rv;
   constexpr bool OPS = MODE == MODE_LAST;
-  typedef TmaGeom<M, TX, TY, U, OPS> G;
+  typedef TmaGeom<M, TX, TY, U, OPS, BLOCH != 0> G;
   static_assert(M % U == 0, "M must be a multiple of U");
   static_assert(!OPS || U == 1, "the last Taylor term takes one plane per iteration");
   constexpr int CW = WsWarps<TX, TY, R>::CW;
@@ -360,6 +474,7 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
   unsigned char *obase = hbase + (size_t)SH * G::HSLOT_BYTES;
   __shared__ __align__(8) uint64_t cfull[SC], cempty[SC];
   __shared__ __align__(8) uint64_t hfull[SH], hempty[SH];
+  __shared__ __align__(8) uint64_t hready[BLOCH ? SH : 1];  // periodic cells: face images written
   __shared__ __align__(8) uint64_t ofull[SO], oempty[SO];
   __shared__ __align__(8) uint64_t ibar[IR];  // completes when s_item[seq % IR] is written
   __shared__ long s_item[IR];                 // item of the CTA's seq-th claim (-1: no more)
@@ -373,6 +488,8 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
   if (tid == 0) {
     for (int s = 0; s < SC; s++) { mbar_init(&cfull[s], 1); mbar_init(&cempty[s], CW); }
     for (int s = 0; s < SH; s++) { mbar_init(&hfull[s], 1); mbar_init(&hempty[s], CW); }
+    if (BLOCH)
+      for (int s = 0; s < SH; s++) mbar_init(&hready[s], 1);
     for (int s = 0; s < SO; s++) { mbar_init(&ofull[s], 1); mbar_init(&oempty[s], CW); }
     for (int s = 0; s < IR; s++) mbar_init(&ibar[s], 1);
     s_abort = 0;
@@ -386,7 +503,7 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
       const Loader<M, TX, TY, U, G, SC, SH, SO, Src> ld{src, 0, cbase, hbase, obase, cfull, hfull, ofull};
       LoadCursor c[3];
       bool done[3] = {false, false, !OPS};
-      for (int k = 0; k < 3; k++) c[k] = LoadCursor{-1, 0, 0, 0, 0, 0, 0, 0, 0};
+      for (int k = 0; k < 3; k++) c[k] = LoadCursor{-1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
       long claimed = 0;  // claims made (their items are in s_item)
       // position cursor k on its next load; false if it has none yet (or none at all)
       auto position = [&](int k) -> bool {
@@ -418,6 +535,10 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
           cu.ii = ns;
           cu.l = 0;
           cu.n = loads_of<M, U>(k, cu.z0, z1);
+          cu.nx = qp->nx;
+          cu.ny = qp->ny;
+          cu.nz = qp->nz;
+          cu.wrap = qp->bloch;
         }
         return !done[k];
       };
@@ -457,6 +578,81 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
         const long n = c[k].issued;
         for (long j = n > S ? n - S : 0; j < n; j++)
           mbar_wait_bounded(&full[j % S], (uint32_t)((j / S) & 1), DRAIN_LIMIT_CYCLES);
+      }
+    }
+    return;
+  }
+
+  if (BLOCH && warp == CW + 1) {
+    // ---- patcher (periodic cells): for each output plane of each item, once the halo slot
+    // has landed, write the Bloch-phased periodic images of the strips beyond the cell's
+    // x and y faces into the halo box (where the TMA box holds zeros), then release the
+    // slot to the consumers -----------------------------------------------------------------
+    RingPos rp;
+    for (long seq = 0;; seq++) {
+      if (!mbar_wait_or_abort(&ibar[seq % IR], (uint32_t)((seq / IR) & 1), abort_flag)) {
+        *abort_flag = 1;
+        break;
+      }
+      const long item = s_item[seq % IR];
+      if (item < 0) break;
+      const SweepParams *pp;
+      const SweepMaps *mp_unused;
+      long local;
+      src.item(item, pp, mp_unused, local);
+      const SweepParams &p = *pp;
+      int tx, ty, kb, z0, z1;
+      item_geom(p, local, tx, ty, kb, z0, z1);
+      const int nx = p.nx, ny = p.ny, x0 = tx * TX, y0 = ty * TY;
+      const bool sl = x0 - M < 0, sr = x0 + TX + M > nx, st = y0 - M < 0, sb = y0 + TY + M > ny;
+      const int kidx = kb / p.n_batches;
+      S_ cx, sx, cy, sy;
+      bloch_phase<P>(p.kvec[3 * kidx] * p.L[0], cx, sx);
+      bloch_phase<P>(p.kvec[3 * kidx + 1] * p.L[1], cy, sy);
+      constexpr int SLB = (int)((G::IN_BYTES + G::AUX_BYTES) / 16);
+      constexpr int SRB = SLB + (int)(G::STRIPX_BYTES / 16);
+      constexpr int STB = SRB + (int)(G::STRIPX_BYTES / 16);
+      constexpr int SBB = STB + (int)(G::STRIPY_BYTES / 16);
+      bool gave_up = false;
+      for (int z = z0; z < z1; z++) {
+        const int hs = rp.slot;
+        if (!mbar_wait_or_abort(&hfull[hs], rp.phase, abort_flag)) {
+          gave_up = true;
+          break;
+        }
+        V *box = reinterpret_cast<V *>(hbase + (size_t)hs * G::HSLOT_BYTES);
+        if (sl || sr) {
+          // box columns c with grid x = x0 - M + c beyond x = 0 (c < M) or beyond x = nx - 1
+          const int cr0 = nx - x0 + M;  // first box column past the last grid column
+          for (int i = lane; i < 2 * G::SY * M * OVC; i += 32) {
+            const int v = i % OVC, j = (i / OVC) % M, row = (i / (OVC * M)) % G::SY, side = i / (OVC * M * G::SY);
+            if (side == 0 ? !sl : !sr) continue;
+            const int c = side == 0 ? j : cr0 + j;
+            if (c >= G::SX) continue;
+            const V a = box[(side == 0 ? SLB : SRB) + (row * M + j) * OVC + v];
+            box[(row * G::SX + c) * OVC + v] = apply_phase<P>(cx, sx, side == 0 ? -1 : 1, a);
+          }
+        }
+        if (st || sb) {
+          // box rows rr with grid y = y0 - M + rr beyond y = 0 (rr < M) or beyond y = ny - 1,
+          // over the tile's columns (the star stencil never reads the corners)
+          const int rb0 = ny - y0 + M;
+          for (int i = lane; i < 2 * M * TX * OVC; i += 32) {
+            const int v = i % OVC, c = (i / OVC) % TX, j = (i / (OVC * TX)) % M, side = i / (OVC * TX * M);
+            if (side == 0 ? !st : !sb) continue;
+            const int rr = side == 0 ? j : rb0 + j;
+            if (rr >= G::SY) continue;
+            const V a = box[(side == 0 ? STB : SBB) + (j * TX + c) * OVC + v];
+            box[(rr * G::SX + c + M) * OVC + v] = apply_phase<P>(cy, sy, side == 0 ? -1 : 1, a);
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&hready[hs]);
+        rp.next<SH>();
+      }
+      if (gave_up) {
+        *abort_flag = 1;
+        break;
       }
     }
     return;
@@ -504,6 +700,12 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
     const V *nlk = nl_column<P>(p, kb, v);
     const int n_ent = p.n_ent;
     const int gx = tx * TX + lx, gy0 = ty * TY + ly0;
+    // periodic cell: the Bloch phase of one wrap along z, e^{i k_z L_z} = cz + i sz, applied to
+    // the queue planes loaded from beyond a z face (the patcher warp handles x and y)
+    S_ cz{}, sz{};
+    if constexpr (BLOCH) bloch_phase<P>(p.kvec[3 * kidx + 2] * p.L[2], cz, sz);
+    const bool need_grad = BLOCH && p.grad_mask != 0;
+    const bool grads = BLOCH && MODE == MODE_FIRST && (p.grad_mask & 8);
     bool own[R];
 #pragma unroll
     for (int r = 0; r < R; r++) own[r] = gx < nx && gy0 + r < ny;
@@ -530,16 +732,27 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
       }
       const V *cslot = reinterpret_cast<const V *>(cbase + (size_t)cs * G::CSLOT_BYTES);
 #pragma unroll
-      for (int u = 0; u < U; u++)
+      for (int u = 0; u < U; u++) {
 #pragma unroll
         for (int r = 0; r < R; r++) Q[r][(RQ + u) % QN] = cslot[u * G::CPLANE + csl0 + r * TX * OVC];
+        if constexpr (BLOCH) {
+          // a plane beyond a z face was loaded from its periodic image: apply the Bloch phase
+          const int zq = z0 - M + U * l + u;
+          if ((unsigned)zq >= (unsigned)p.nz) {
+            const int wz = floordiv_i(zq, p.nz);
+#pragma unroll
+            for (int r = 0; r < R; r++) Q[r][(RQ + u) % QN] = apply_phase<P>(cz, sz, wz, Q[r][(RQ + u) % QN]);
+          }
+        }
+      }
       __syncwarp();
       if (lane == 0) mbar_arrive(&cempty[cs]);
       rc.next<SC>();
       if (l >= LP) {
         const int zf = z0 + U * (l - LP);
         const int hs = rh.slot;
-        if (!mbar_wait_or_abort(&hfull[hs], rh.phase, abort_flag)) {
+        // periodic cells: the slot is ready once the patcher warp has written the face images
+        if (!mbar_wait_or_abort(BLOCH ? &hready[hs] : &hfull[hs], rh.phase, abort_flag)) {
           aborted = true;
           return;
         }
@@ -582,14 +795,27 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
             ve[r] = *reinterpret_cast<const Rv *>(&a.veff);
             nlv[r] = has_proj ? nl_term<P>(nlk, n_ent, a.r0, a.r1) : T::zero();
           }
-          stencil_rows<M, P, QB, QN, R>(W, w0, Q, xs + u * G::PLANE, hs0, SXO, ve, acc);
+          V gax[BLOCH ? R : 1][3];
+          if constexpr (BLOCH) {
+            stencil_rows_bloch<M, P, QB, QN, R>(p, W, w0, Q, xs, hs0, SXO, ve, acc, gax, need_grad, grads);
+          } else {
+            stencil_rows<M, P, QB, QN, R>(W, w0, Q, xs + u * G::PLANE, hs0, SXO, ve, acc);
+          }
           const long iu = idx + (long)u * plane_pts * OVC;
 #pragma unroll
           for (int r = 0; r < R; r++) {
             const bool live = own[r] && (zf + u < z1);
             if (has_proj) acc[r] = T::add(acc[r], nlv[r]);
             const V c0 = Q[r][(QB + M) % QN];
-            if (MODE == MODE_FIRST && do_obs && live) oa.add_e(c0, acc[r]);
+            if (MODE == MODE_FIRST && do_obs && live) {
+              oa.add_e(c0, acc[r]);
+              if constexpr (BLOCH) {
+                if (grads) {
+#pragma unroll
+                  for (int a = 0; a < 3; a++) oa.add_j(a, c0, gax[r][a]);
+                }
+              }
+            }
             finish_point<P, MODE>(epi, CR, CI, live, iu + r * row, v, c0, acc[r], operands(csl0 + r * TX * OVC));
           }
         });
@@ -629,27 +855,27 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
   }
 }
 
-template <int M, int P, int MODE, int TX, int TY, int R, int U>
-__global__ void __launch_bounds__(WsWarps<TX, TY, R>::THREADS, 1)
+template <int M, int P, int MODE, int TX, int TY, int R, int U, int BLOCH>
+__global__ void __launch_bounds__(WsWarps<TX, TY, R>::THREADS + 32 * BLOCH, 1)
 ws_sweep_kernel(const __grid_constant__ SweepMaps maps, const __grid_constant__ SweepParams p) {
   const SingleSrc src{&p, &maps};
-  ws_sweep_body<M, P, MODE, TX, TY, R, U, false>(src, p.work);
+  ws_sweep_body<M, P, MODE, TX, TY, R, U, false, BLOCH>(src, p.work);
 }
 
 template <int M, int P, int MODE, int TX, int TY, int R, int U>
 __global__ void __launch_bounds__(WsWarps<TX, TY, R>::THREADS, 1)
 ws_sweep_batch_kernel(const __grid_constant__ BatchSweepArgs a) {
   const BatchSrc src{&a};
-  ws_sweep_body<M, P, MODE, TX, TY, R, U, true>(src, a.work);
+  ws_sweep_body<M, P, MODE, TX, TY, R, U, true, 0>(src, a.work);
 }
 
 // Launch of the warp-specialised sweep of shape SHAPE for one system (one plane per
 // iteration; grid <= 0: one CTA per SM, at most one per work item).
-template <int SHAPE, int M, int P, int MODE>
+template <int SHAPE, int M, int P, int MODE, int BLOCH>
 static cudaError_t launch_ws_t(const SweepMaps &maps, const SweepParams &p, int grid, cudaStream_t s) {
   constexpr int TX = WsShape<SHAPE>::TX, TY = WsShape<SHAPE>::TY, R = WsShape<SHAPE>::R;
-  typedef TmaGeom<M, TX, TY, 1, MODE == MODE_LAST> G;
-  auto k = ws_sweep_kernel<M, P, MODE, TX, TY, R, 1>;
+  typedef TmaGeom<M, TX, TY, 1, MODE == MODE_LAST, BLOCH != 0> G;
+  auto k = ws_sweep_kernel<M, P, MODE, TX, TY, R, 1, BLOCH>;
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
@@ -662,7 +888,7 @@ static cudaError_t launch_ws_t(const SweepMaps &maps, const SweepParams &p, int 
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     grid = (int)(p.n_items < sms ? p.n_items : sms);
   }
-  k<<<grid, WsWarps<TX, TY, R>::THREADS, G::SMEM, s>>>(maps, p);
+  k<<<grid, WsWarps<TX, TY, R>::THREADS + 32 * BLOCH, G::SMEM, s>>>(maps, p);  // (+ the patcher warp)
   return cudaGetLastError();
 }
 
@@ -707,17 +933,16 @@ cudaError_t launch_ws_batch_shape(int M, int prec, int mode, const BatchSweepArg
   return cudaErrorInvalidValue;
 }
 
-// Every mode, FD order and precision of one shape (instantiated once per shape, in a
-// translation unit of its own).
-template <int SHAPE>
-cudaError_t launch_ws_shape(int M, int prec, int mode, const SweepMaps &maps, const SweepParams &p, int grid,
-                            cudaStream_t s) {
-#define TDKS_WS_MODES(MM, PP)                                                         \
-  switch (mode) {                                                                     \
-    case MODE_FIRST: return launch_ws_t<SHAPE, MM, PP, MODE_FIRST>(maps, p, grid, s); \
-    case MODE_MID: return launch_ws_t<SHAPE, MM, PP, MODE_MID>(maps, p, grid, s);     \
-    case MODE_LAST: return launch_ws_t<SHAPE, MM, PP, MODE_LAST>(maps, p, grid, s);   \
-  }                                                                                   \
+// One boundary kind of one shape: every mode, FD order and precision.
+template <int SHAPE, int BLOCH>
+static cudaError_t launch_ws_bc(int M, int prec, int mode, const SweepMaps &maps, const SweepParams &p, int grid,
+                                cudaStream_t s) {
+#define TDKS_WS_MODES(MM, PP)                                                                \
+  switch (mode) {                                                                            \
+    case MODE_FIRST: return launch_ws_t<SHAPE, MM, PP, MODE_FIRST, BLOCH>(maps, p, grid, s); \
+    case MODE_MID: return launch_ws_t<SHAPE, MM, PP, MODE_MID, BLOCH>(maps, p, grid, s);     \
+    case MODE_LAST: return launch_ws_t<SHAPE, MM, PP, MODE_LAST, BLOCH>(maps, p, grid, s);   \
+  }                                                                                          \
   return cudaErrorInvalidValue;
   if (M == 2) {
     if (prec == P_C64) { TDKS_WS_MODES(2, P_C64) } else { TDKS_WS_MODES(2, P_C128) }
@@ -727,6 +952,15 @@ cudaError_t launch_ws_shape(int M, int prec, int mode, const SweepMaps &maps, co
   }
 #undef TDKS_WS_MODES
   return cudaErrorInvalidValue;
+}
+
+// Every mode, FD order, precision and boundary (finite box or periodic cell) of one shape
+// (instantiated once per shape, in a translation unit of its own).
+template <int SHAPE>
+cudaError_t launch_ws_shape(int M, int prec, int mode, int bloch, const SweepMaps &maps, const SweepParams &p,
+                            int grid, cudaStream_t s) {
+  return bloch ? launch_ws_bc<SHAPE, 1>(M, prec, mode, maps, p, grid, s)
+               : launch_ws_bc<SHAPE, 0>(M, prec, mode, maps, p, grid, s);
 }
 
 }  // namespace tdks

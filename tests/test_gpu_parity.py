@@ -177,14 +177,50 @@ def test_autotune_keeps_state_and_results(prec):
     b.close()
 
 
-def test_autotune_leaves_periodic_cells_alone():
-    """Periodic cells take the general sweep: nothing to tune, -1 everywhere."""
-    spec = bloch_cell(I.PREC_C64)
-    sysm = _system(spec, bloch_inputs(spec))
+@pytest.mark.parametrize("prec", [I.PREC_C128, I.PREC_C64])
+def test_periodic_cell_tma_sweep_matches_general_sweep(prec):
+    """Bloch cells on the TMA sweep (wrapped z planes with their phase in the register
+    queue, x/y neighbours across a face read with the phase, velocity-gauge gradient and
+    current) agree with the general sweep, in every tile shape: H applications, and a short
+    propagation with its energy and current records."""
+    from paper_1912_07921_gb300.system import shape_count
+    spec = bloch_cell(prec, n_orb=11 if prec == I.PREC_C64 else 5, n_k=2)
+    inp = bloch_inputs(spec)
+    psi = I.random_orbitals(spec, 4)
+    tol = 1e-13 if prec == I.PREC_C128 else 1e-6
+    ref_sys = _system(spec, inp)
+    ref_sys.set_sweep_path(1)
+    ref = _apply_gpu(ref_sys, psi, 0.3)
+    ref_sys.propagate(0.0, 0.01, 3, 2)
+    ref_psi, ref_rec = ref_sys.get_orbitals(), ref_sys.reductions(0, 3)
+    ref_sys.close()
+    for sh in range(shape_count()):
+        sysm = _system(spec, inp)
+        sysm.set_sweep_shape(-1, sh)
+        assert rel_err(_apply_gpu(sysm, psi, 0.3), ref) < tol
+        sysm.propagate(0.0, 0.01, 3, 2)
+        assert rel_err(sysm.get_orbitals(), ref_psi) < tol
+        assert rel_err(sysm.reductions(0, 3), ref_rec) < tol
+        sysm.close()
+
+
+def test_autotune_periodic_cell_keeps_state_and_results():
+    """Periodic cells take the TMA sweep too: the autotuner times every shape, leaves the
+    state untouched, and the propagation that follows matches the oracle."""
+    from paper_1912_07921_gb300.system import shape_count
+    spec = bloch_cell(I.PREC_C128)
+    inp = bloch_inputs(spec)
+    sysm = _system(spec, inp)
+    before = sysm.get_orbitals()
     ms = sysm.autotune(reps=1)
-    assert np.all(ms == -1.0)
-    assert sysm.sweep_shapes() == [0, 0, 0, 0]
+    assert ms.shape == (shape_count(), 4) and np.all(ms > 0)
+    assert np.array_equal(sysm.get_orbitals(), before)
+    sysm.propagate(0.0, 0.03, 2, 2)
+    psi, rec = sysm.get_orbitals(), sysm.reductions(0, 2)
     sysm.close()
+    psi_o, rec_o = oracle.System(spec, inp).propagate(inp.psi0, 0.0, 0.03, 2, 2)
+    assert rel_err(psi, psi_o) < 1e-12
+    assert _rec_err(rec, rec_o) < 1e-12
 
 
 @pytest.mark.parametrize("prec", [I.PREC_C128, I.PREC_C64])
