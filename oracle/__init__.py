@@ -63,6 +63,9 @@ def _load():
         _lib.oracle_propagate.argtypes = [S, D, D, I, I, P, P]
         _lib.oracle_sphere_count.argtypes = [S, I]
         _lib.oracle_sphere_count.restype = I
+        _lib.oracle_propagate_cfm4.argtypes = [S, D, D, I, I, P, P]
+        _lib.oracle_cfm4_weights.argtypes = [I, P, P]
+        _lib.oracle_cfm4_constants.argtypes = [P, P]
     return _lib
 
 
@@ -161,6 +164,15 @@ class System:
                                   _ptr(obs) if record else None)
         return psi, obs
 
+    def propagate_cfm4(self, psi, t0, dt, n_steps, substeps, record=True):
+        """CFM4 (two exponentials per sub-step, v_x extrapolated from the last four
+        sub-steps); length gauge or no field."""
+        psi = self._psi(psi).copy()
+        obs = np.empty((n_steps, 8)) if record else None
+        self.lib.oracle_propagate_cfm4(self.ref, t0, dt, n_steps, substeps, _ptr(psi),
+                                       _ptr(obs) if record else None)
+        return psi, obs
+
     def sphere_count(self, a: int) -> int:
         return self.lib.oracle_sphere_count(self.ref, a)
 
@@ -171,3 +183,20 @@ def fd_weights(M: int):
     lib.oracle_fd_laplacian_weights(M, _ptr(c))
     lib.oracle_fd_gradient_weights(M, _ptr(d))
     return c, d
+
+
+def cfm4_weights(nh: int):
+    """Weights of the newest nh v_x (newest first) in the effective potentials of the
+    first and second CFM4 exponentials."""
+    lib = _load()
+    wf, ws = np.zeros(4), np.zeros(4)
+    lib.oracle_cfm4_weights(nh, _ptr(wf), _ptr(ws))
+    return wf[:nh], ws[:nh]
+
+
+def cfm4_constants():
+    """(a1, a2), (theta1, theta2) of CFM4."""
+    lib = _load()
+    a, th = np.zeros(2), np.zeros(2)
+    lib.oracle_cfm4_constants(_ptr(a), _ptr(th))
+    return a, th

@@ -263,13 +263,22 @@ int oracle_sphere_count(const oracle_sys *s, int a) {
  * (length gauge) or H = 1/2 (-i grad_h + A(t))^2 + V_loc + v_x (velocity gauge),
  * plus V_NL.  vx may be NULL (no exchange term).  The field is taken at time t.
  * ------------------------------------------------------------------------------ */
+static void apply_H_field(const oracle_sys *s, const double *E, const double *A, const double *vx, const cplx *in,
+                          cplx *out);
+
 void oracle_apply_H(const oracle_sys *s, double t, const double *vx, const cplx *in, cplx *out) {
+  double E[3], A[3];
+  oracle_field(s, t, E, A);
+  apply_H_field(s, E, A, vx, in, out);
+}
+
+/* H psi with the field given explicitly (E in the length gauge, A in the velocity gauge). */
+static void apply_H_field(const oracle_sys *s, const double *E, const double *A, const double *vx, const cplx *in,
+                          cplx *out) {
   int M = s->fd_order / 2;
   double c[5], d[5];
   oracle_fd_laplacian_weights(M, c);
   oracle_fd_gradient_weights(M, d);
-  double E[3], A[3];
-  oracle_field(s, t, E, A);
   double h = s->h, h2 = h * h, h3 = h * h * h;
   long N = npts(s);
   int B = s->n_orb;
@@ -466,4 +475,131 @@ void oracle_propagate(const oracle_sys *s, double t0, double dt, int n_steps, in
     if (obs) oracle_observables(s, t, t + 0.5 * dts, psi, obs + 8 * st);
     for (int j = 0; j < substeps; j++) oracle_taylor_substep(s, t + (double)j * dts, dts, psi);
   }
+}
+
+/* --------------------------------------------------------------------------------
+ * CFM4 (Sec. "New propagators for real-time TDDFT": the order-four commutator-free Magnus
+ * expansion with two exponentials),
+ *   phi(t + ds) = exp(-i ds (a1 H[t1] + a2 H[t2])) exp(-i ds (a2 H[t1] + a1 H[t2])) phi(t),
+ *   a1 = (3 - 2 sqrt3)/12, a2 = (3 + 2 sqrt3)/12, t1,2 = t + (1/2 -+ sqrt3/6) ds.
+ * In the length gauge H[t] = H0 + v_x(t) + E(t).r, and a1 + a2 = 1/2, so each exponential is
+ * exp(-i (ds/2) H_eff) with H_eff = H0 + v_eff + E_eff.r:
+ *   first  (applied first):  E_eff = 2 (a2 E(t1) + a1 E(t2)),  v_eff = 2 (a2 v_x(t1) + a1 v_x(t2)),
+ *   second:                  E_eff = 2 (a1 E(t1) + a2 E(t2)),  v_eff = 2 (a1 v_x(t1) + a2 v_x(t2)).
+ * v_x at t1, t2 is not known (it depends on the states); as the paper does for the
+ * exchange-correlation part, it is extrapolated from earlier sub-steps: the Lagrange
+ * polynomial through v_x at the starts of the last nh <= 4 sub-steps (offsets 0, -1, -2, -3
+ * in units of ds; order four with four points).  Each exponential is applied with the
+ * Taylor-4 series of this file.
+ * ------------------------------------------------------------------------------ */
+/* Lagrange weights of the nh history points at offsets 0, -1, .., -(nh-1), evaluated at x. */
+static void lagrange_weights(int nh, double x, double *L) {
+  for (int j = 0; j < nh; j++) {
+    double w = 1.0;
+    for (int i = 0; i < nh; i++)
+      if (i != j) w *= (x - (double)(-i)) / ((double)(-j) - (double)(-i));
+    L[j] = w;
+  }
+}
+
+/* CFM4 constants: a[0] = a1, a[1] = a2, theta[0,1] = offsets of t1, t2 in units of ds. */
+void oracle_cfm4_constants(double *a, double *theta) {
+  const double r3 = sqrt(3.0);
+  a[0] = (3.0 - 2.0 * r3) / 12.0;
+  a[1] = (3.0 + 2.0 * r3) / 12.0;
+  theta[0] = 0.5 - r3 / 6.0;
+  theta[1] = 0.5 + r3 / 6.0;
+}
+
+/* Weights of the history v_x[j] (j = 0 the newest) in the effective potentials of the first
+ * (wf) and second (ws) exponential. */
+void oracle_cfm4_weights(int nh, double *wf, double *ws) {
+  double a[2], th[2], L1[4], L2[4];
+  oracle_cfm4_constants(a, th);
+  lagrange_weights(nh, th[0], L1);
+  lagrange_weights(nh, th[1], L2);
+  for (int j = 0; j < nh; j++) {
+    wf[j] = 2.0 * (a[1] * L1[j] + a[0] * L2[j]);
+    ws[j] = 2.0 * (a[0] * L1[j] + a[1] * L2[j]);
+  }
+}
+
+/* psi <- sum_(k=0..4) (-i tau H)^k / k! psi with H = H0 + v + E.r (v may be NULL). */
+static void taylor_exp_field(const oracle_sys *s, const double *E, const double *v, double tau, cplx *psi) {
+  long tot = (long)s->n_k * npts(s) * s->n_orb;
+  const double A0[3] = {0.0, 0.0, 0.0};
+  cplx *term = (cplx *)malloc(sizeof(cplx) * (size_t)tot);
+  cplx *next = (cplx *)malloc(sizeof(cplx) * (size_t)tot);
+  cplx *acc = (cplx *)malloc(sizeof(cplx) * (size_t)tot);
+  memcpy(term, psi, sizeof(cplx) * (size_t)tot);
+  memcpy(acc, psi, sizeof(cplx) * (size_t)tot);
+  for (int k = 1; k <= 4; k++) {
+    apply_H_field(s, E, A0, v, term, next);
+    cplx coef = -I * tau / (double)k;
+    for (long i = 0; i < tot; i++) {
+      term[i] = coef * next[i];
+      acc[i] += term[i];
+    }
+  }
+  memcpy(psi, acc, sizeof(cplx) * (size_t)tot);
+  free(term); free(next); free(acc);
+}
+
+/* n_steps configured steps of CFM4, each split into `substeps` equal CFM4 sub-steps ds; the
+ * v_x history starts empty at t0.  Records as oracle_propagate (state at the start of each
+ * step, Hamiltonian of t + ds/2 with v_x of that state).  Length gauge or no field only. */
+void oracle_propagate_cfm4(const oracle_sys *s, double t0, double dt, int n_steps, int substeps, cplx *psi,
+                           double *obs) {
+  if (s->gauge == 2) return;  /* the effective-Hamiltonian form needs a field linear in H */
+  const long N = npts(s);
+  const double ds = dt / (double)substeps;
+  double a[2], th[2];
+  oracle_cfm4_constants(a, th);
+  double *hist[4] = {NULL, NULL, NULL, NULL};
+  int nh = 0;
+  double *n = (double *)malloc(sizeof(double) * (size_t)N);
+  double *vf = (double *)malloc(sizeof(double) * (size_t)N);
+  double *vs = (double *)malloc(sizeof(double) * (size_t)N);
+  for (int j = 0; j < 4; j++) hist[j] = (double *)malloc(sizeof(double) * (size_t)N);
+  for (int st = 0; st < n_steps; st++) {
+    double t = t0 + (double)st * dt;
+    if (obs) oracle_observables(s, t, t + 0.5 * ds, psi, obs + 8 * st);
+    for (int j = 0; j < substeps; j++) {
+      const double tj = t + (double)j * ds;
+      const double *pf = NULL, *ps = NULL;
+      if (s->xc == 1) {
+        /* push v_x of the current state as the newest history entry */
+        double *oldest = hist[3];
+        for (int q = 3; q > 0; q--) hist[q] = hist[q - 1];
+        hist[0] = oldest;
+        oracle_density(s, psi, n);
+        oracle_lda_x(s, n, hist[0]);
+        if (nh < 4) nh++;
+        double wf[4], wsw[4];
+        oracle_cfm4_weights(nh, wf, wsw);
+        for (long p = 0; p < N; p++) {
+          double x = 0.0, y = 0.0;
+          for (int q = 0; q < nh; q++) {
+            x += wf[q] * hist[q][p];
+            y += wsw[q] * hist[q][p];
+          }
+          vf[p] = x;
+          vs[p] = y;
+        }
+        pf = vf;
+        ps = vs;
+      }
+      double E1[3], E2[3], A[3], Ef[3], Es[3];
+      oracle_field(s, tj + th[0] * ds, E1, A);
+      oracle_field(s, tj + th[1] * ds, E2, A);
+      for (int ax = 0; ax < 3; ax++) {
+        Ef[ax] = 2.0 * (a[1] * E1[ax] + a[0] * E2[ax]);
+        Es[ax] = 2.0 * (a[0] * E1[ax] + a[1] * E2[ax]);
+      }
+      taylor_exp_field(s, Ef, pf, 0.5 * ds, psi);
+      taylor_exp_field(s, Es, ps, 0.5 * ds, psi);
+    }
+  }
+  for (int j = 0; j < 4; j++) free(hist[j]);
+  free(n); free(vf); free(vs);
 }

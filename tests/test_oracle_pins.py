@@ -530,3 +530,74 @@ def test_energy_conservation_at_zero_field():
             drifts.append(abs(e_end - obs[0, 2]))
         assert drifts[0] < 2e-3 * abs(obs[0, 2])
         assert drifts[1] * factor < drifts[0], (xc, drifts)
+
+
+# ---------------------------------------------------------------------------------------
+# CFM4 (Sec. "New propagators for real-time TDDFT": two exponentials with the Hamiltonian
+# at the Gauss points t1,2 = t + (1/2 -+ sqrt3/6) dt, weights a1,2 = (3 -+ 2 sqrt3)/12)
+# ---------------------------------------------------------------------------------------
+def test_cfm4_constants_and_exchange_extrapolation():
+    """The constants are the printed ones; the history weights are Lagrange extrapolation
+    (exact on polynomials of degree nh - 1, summing to one), combined with the a's."""
+    (a1, a2), (th1, th2) = oracle.cfm4_constants()
+    r3 = math.sqrt(3.0)
+    assert a1 == pytest.approx((3 - 2 * r3) / 12, abs=1e-16) and a2 == pytest.approx((3 + 2 * r3) / 12, abs=1e-16)
+    assert th1 == pytest.approx(0.5 - r3 / 6, abs=1e-16) and th2 == pytest.approx(0.5 + r3 / 6, abs=1e-16)
+    assert a1 + a2 == pytest.approx(0.5, abs=1e-15)
+    rng = np.random.default_rng(3)
+    for nh in range(1, 5):
+        wf, ws = oracle.cfm4_weights(nh)
+        assert wf.sum() == pytest.approx(1.0, abs=1e-13) and ws.sum() == pytest.approx(1.0, abs=1e-13)
+        xs = -np.arange(nh, dtype=float)       # history offsets, newest first
+        coef = rng.standard_normal(nh)         # a random polynomial of degree nh - 1
+        p = np.polynomial.polynomial.Polynomial(coef)
+        assert wf @ p(xs) == pytest.approx(2 * (a2 * p(th1) + a1 * p(th2)), abs=1e-12)
+        assert ws @ p(xs) == pytest.approx(2 * (a1 * p(th1) + a2 * p(th2)), abs=1e-12)
+
+
+def _cfm_case(xc):
+    spec = I.SystemSpec(nx=12, ny=12, nz=12, h=0.5, fd_order=4, prec=I.PREC_C128, n_orb=2, n_atoms=2,
+                        projectors=False, gauge=I.GAUGE_LENGTH, amp=0.3, omega=3.0, dt=0.02, seed=9)
+    inp = I.make_inputs(spec)
+    return spec, inp, oracle.System(spec, inp, xc=xc)
+
+
+def test_cfm4_without_field_is_two_taylor_half_steps():
+    """With H time-independent (no field, no exchange) both exponentials are exp(-i dt/2 H):
+    a CFM4 step is two Taylor-4 steps of dt/2."""
+    spec, inp, o = _cfm_case(0)
+    o0 = oracle.System(spec, inp, xc=0, gauge=I.GAUGE_NONE)
+    c, obs_c = o0.propagate_cfm4(inp.psi0, 0.0, 0.04, 5, 1)
+    t, obs_t = o0.propagate(inp.psi0, 0.0, 0.04, 5, 2)
+    assert np.max(np.abs(c - t)) < 1e-14
+    np.testing.assert_allclose(obs_c, obs_t, rtol=1e-13, atol=1e-14)
+
+
+def test_cfm4_is_fourth_order_for_a_driven_linear_problem():
+    """Fast laser (omega = 3 Ha), no exchange: halving dt divides the CFM4 error by 16
+    (Taylor-4 with the field at the step midpoint: by 4); reference: CFM4 at dt/32."""
+    spec, inp, o = _cfm_case(0)
+    T = 0.64
+    ref, _ = o.propagate_cfm4(inp.psi0, 0.0, T / 256, 256, 1, record=False)
+    e = [np.linalg.norm(o.propagate_cfm4(inp.psi0, 0.0, T / n, n, 1, record=False)[0] - ref) for n in (8, 16, 32)]
+    et = [np.linalg.norm(o.propagate(inp.psi0, 0.0, T / n, n, 1, record=False)[0] - ref) for n in (8, 16, 32)]
+    for a, b in zip(e, e[1:]):
+        assert 14.0 < a / b < 18.0
+    for a, b in zip(et, et[1:]):
+        assert 3.5 < a / b < 5.0
+    assert e[-1] < 0.02 * et[-1]
+
+
+def test_cfm4_with_exchange_converges_faster_than_taylor():
+    """With LDA exchange v_x at the Gauss points comes from the extrapolated history; the
+    first three sub-steps have fewer than four points, which lowers the observed order (~3:
+    error ratio > 6 per halving) but keeps it above Taylor-4 with a frozen density (~1)."""
+    spec, inp, o = _cfm_case(1)
+    T = 0.64
+    ref, _ = o.propagate_cfm4(inp.psi0, 0.0, T / 256, 256, 1, record=False)
+    e = [np.linalg.norm(o.propagate_cfm4(inp.psi0, 0.0, T / n, n, 1, record=False)[0] - ref) for n in (16, 32, 64)]
+    et = [np.linalg.norm(o.propagate(inp.psi0, 0.0, T / n, n, 1, record=False)[0] - ref) for n in (16, 32, 64)]
+    for a, b in zip(e, e[1:]):
+        assert a / b > 6.0
+    for a, b in zip(et, et[1:]):
+        assert 1.7 < a / b < 2.3
