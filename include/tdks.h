@@ -160,6 +160,25 @@ int tdks_apply_H(tdks_sys sys, double t, const void *dev_in, void *dev_out);
  */
 int tdks_propagate_n(tdks_sys sys, double t0, double dt, int n_steps, int substeps);
 
+/*
+ * Propagator of tdks_propagate_n.  TDKS_PROP_TAYLOR4 (default): the 4th-order Taylor series
+ * above.  TDKS_PROP_CFM4: the order-four commutator-free Magnus expansion of Sec. "New
+ * propagators for real-time TDDFT",
+ *   phi(t + ds) = exp(-i ds (a1 H[t1] + a2 H[t2])) exp(-i ds (a2 H[t1] + a1 H[t2])) phi(t),
+ *   a1,2 = (3 -+ 2 sqrt3)/12,  t1,2 = t + (1/2 -+ sqrt3/6) ds,
+ * per sub-step ds = dt / substeps.  As a1 + a2 = 1/2, each factor is a Taylor-4
+ * exponential of ds/2 of H with the field 2 (a2 E(t1) + a1 E(t2)) (first factor; a1 and
+ * a2 swapped in the second) and the exchange potential extrapolated the same way to t1 and
+ * t2 from its values at the starts of the last four sub-steps (Lagrange, order four; fewer
+ * points while the history fills).  The history is cleared by tdks_set_orbitals and by
+ * this call.  Length gauge or no field (TDKS_EINVAL with the velocity gauge at
+ * propagation); the stability limit applies to ds/2.  Records as for Taylor-4.  Batches
+ * propagate with Taylor-4.
+ */
+#define TDKS_PROP_TAYLOR4 0
+#define TDKS_PROP_CFM4 1
+int tdks_set_propagator(tdks_sys sys, int propagator);
+
 /* Sub-step count the automatic policy of tdks_propagate_n picks for step dt. */
 int tdks_auto_substeps(tdks_sys sys, double dt, int *substeps);
 

@@ -27,6 +27,7 @@ SIGNATURES = {
     "tdks_layout": ([P, PI, PI, PI, PLL], I),
     "tdks_apply_H": ([P, D, P, P], I),
     "tdks_propagate_n": ([P, D, D, I, I], I),
+    "tdks_set_propagator": ([P, I], I),
     "tdks_auto_substeps": ([P, D, PI], I),
     "tdks_reductions": ([P, LL, I, P], I),
     "tdks_step_count": ([P, PLL], I),

@@ -487,6 +487,83 @@ lda_kernel(long N, int nx, int ny, int nz, double h, int bloch, int n_kb, int n_
               lda_part, blockIdx.x, gridDim.x);
 }
 
+// ---------------------------------------------------------------------------------
+// CFM4 (Sec. "New propagators for real-time TDDFT"): the effective potential of one of the
+// two exponentials, V_eff = V_loc + sum_j w_j v_x,j + E.r, where v_x,j is the exchange
+// potential at the start of the j-th latest sub-step (the history) and the w_j extrapolate
+// it to the Gauss points (the host forms them).  push: first store v_x of the current
+// density (dens_part, summed as the LDA kernel does) into hist.v[0], the slot the host has
+// rotated to the front.  The history is FP64; complex64 systems compute v_x in FP32 as their
+// LDA kernel does and round V_eff to FP32.
+// ---------------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(LDA_THREADS)
+cfm_veff_kernel(long N, int nx, int ny, int nz, double h, int bloch, int n_kb, int n_batches, const double *wocc,
+                const double *dens_part, const double *vloc, int xc, int push, CfmHist hist, double Ex, double Ey,
+                double Ez, PointAux *aux) {
+  constexpr bool F32 = sizeof(R) == 4;
+  const int n_k = n_kb / n_batches;
+  __shared__ float2 s_w[LDA_MAXK];
+  if constexpr (F32) {
+    for (int k = threadIdx.x; k < n_k && k < LDA_MAXK; k += blockDim.x) {
+      const float hi = (float)wocc[k];
+      s_w[k] = make_float2(hi, (float)(wocc[k] - (double)hi));
+    }
+    __syncthreads();
+  }
+  const double cx = bloch ? 0.0 : 0.5 * (nx - 1), cy = bloch ? 0.0 : 0.5 * (ny - 1), cz = bloch ? 0.0 : 0.5 * (nz - 1);
+  for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < N; p += (long)gridDim.x * blockDim.x) {
+    if (push && xc) {
+      double vx;
+      if constexpr (F32) {
+        const float2 *d2 = reinterpret_cast<const float2 *>(dens_part);
+        float nh = 0.f, nl = 0.f;
+        for (int k = 0; k < n_k; k++) {
+          float sh = 0.f, sl = 0.f;
+          for (int b = 0; b < n_batches; b++) {
+            const float2 d = d2[(long)(k * n_batches + b) * N + p];
+            df_add_df(sh, sl, d.x, d.y);
+          }
+          float2 w;
+          if (k < LDA_MAXK) {
+            w = s_w[k];
+          } else {
+            const float hi = (float)wocc[k];
+            w = make_float2(hi, (float)(wocc[k] - (double)hi));
+          }
+          const float ph = sh * w.x;
+          const float pl = fmaf(sh, w.x, -ph) + (sh * w.y + sl * w.x);
+          df_add_df(nh, nl, ph, pl);
+        }
+        vx = (double)(-cbrtf(3.0f * nh * 0.318309886f));
+      } else {
+        double n = 0.0;
+        for (int kb = 0; kb < n_kb; kb++) n += dens_part[(long)kb * N + p];
+        vx = -cbrt(3.0 * n * 0.31830988618379067154);
+      }
+      hist.v[0][p] = vx;
+    }
+    const int ix = (int)(p % nx), iy = (int)((p / nx) % ny), iz = (int)(p / ((long)nx * ny));
+    double v = vloc[p];
+    for (int j = 0; j < hist.nh; j++) v += hist.w[j] * hist.v[j][p];
+    v += Ex * ((ix - cx) * h) + Ey * ((iy - cy) * h) + Ez * ((iz - cz) * h);
+    *reinterpret_cast<R *>(&aux[p].veff) = (R)v;
+  }
+}
+
+cudaError_t launch_cfm_veff(int prec, int bloch, long N, int nx, int ny, int nz, double h, int n_kb, int n_batches,
+                            const double *wocc, const double *dens_part, const double *vloc, int xc, int push,
+                            const CfmHist &hist, const double E[3], PointAux *aux, cudaStream_t s) {
+  const int blocks = lda_blocks(N);
+  if (prec == P_C64)
+    cfm_veff_kernel<float><<<blocks, LDA_THREADS, 0, s>>>(N, nx, ny, nz, h, bloch, n_kb, n_batches, wocc, dens_part,
+                                                          vloc, xc, push, hist, E[0], E[1], E[2], aux);
+  else
+    cfm_veff_kernel<double><<<blocks, LDA_THREADS, 0, s>>>(N, nx, ny, nz, h, bloch, n_kb, n_batches, wocc, dens_part,
+                                                           vloc, xc, push, hist, E[0], E[1], E[2], aux);
+  return cudaGetLastError();
+}
+
 // Laser field of a batched system at time t (finite boxes: length gauge or none).
 __device__ __forceinline__ double batch_field(const BatchAux &a, double t) {
   if (a.gauge != 1) return 0.0;

@@ -548,7 +548,8 @@ int tdks_destroy(tdks_sys s) {
   cudaFree(s->d_err);
   for (int i = 0; i < 3; i++) cudaFree(s->term[i]);
   cudaFree(s->vloc); cudaFree(s->aux); cudaFree(s->dens_part); cudaFree(s->lda_part);
-  cudaFree(s->obs_part); cudaFree(s->ring); cudaFree(s->fin_part); cudaFree(s->obs_rec); cudaFree(s->d_kvec); cudaFree(s->d_wocc);
+  cudaFree(s->obs_part); cudaFree(s->ring); cudaFree(s->fin_part);
+  for (int j = 0; j < 4; j++) cudaFree(s->vx_hist[j]); cudaFree(s->obs_rec); cudaFree(s->d_kvec); cudaFree(s->d_wocc);
   cudaFree(s->staging);
   if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
   if (s->ev_staging_free) cudaEventDestroy(s->ev_staging_free);
@@ -620,6 +621,7 @@ int tdks_set_orbitals(tdks_sys s, const double *psi) {
   CU(cudaStreamSynchronize(s->copy_stream));
   s->have_orbitals = true;
   s->dens_valid = true;
+  s->n_hist = 0;  // a new state starts a new CFM4 exchange history
   return TDKS_OK;
 }
 
@@ -936,11 +938,152 @@ int tdks_auto_substeps(tdks_sys s, double dt, int *substeps) {
   return TDKS_OK;
 }
 
+// CFM4 constants (Sec. "New propagators for real-time TDDFT"): weights a1, a2 and the Gauss
+// points t + theta_i ds of the two Hamiltonians.
+static void cfm4_constants(double a[2], double theta[2]) {
+  const double r3 = std::sqrt(3.0);
+  a[0] = (3.0 - 2.0 * r3) / 12.0;
+  a[1] = (3.0 + 2.0 * r3) / 12.0;
+  theta[0] = 0.5 - r3 / 6.0;
+  theta[1] = 0.5 + r3 / 6.0;
+}
+
+// Extrapolation of the exchange history (values at offsets 0, -1, .., -(nh-1) sub-steps)
+// to the Gauss points, folded with the a's: weights of the first (wf) and second (ws)
+// exponential's effective potential.
+static void cfm4_history_weights(int nh, double wf[4], double ws[4]) {
+  double a[2], th[2];
+  cfm4_constants(a, th);
+  for (int j = 0; j < nh; j++) {
+    double l1 = 1.0, l2 = 1.0;  // Lagrange basis polynomial j at theta_1, theta_2
+    for (int i = 0; i < nh; i++) {
+      if (i == j) continue;
+      l1 *= (th[0] + i) / (double)(i - j);
+      l2 *= (th[1] + i) / (double)(i - j);
+    }
+    wf[j] = 2.0 * (a[1] * l1 + a[0] * l2);
+    ws[j] = 2.0 * (a[0] * l1 + a[1] * l2);
+  }
+}
+
+// Taylor terms 2..4 of a sub-step of length dts (term 1 is already in term[0]); the last
+// sweep adds the series into the state and writes its density.
+static int taylor_tail(tdks_system *s, double dts, const double A[3]) {
+  int rc = TDKS_OK;
+  for (int k = 2; k <= 4; k++) {
+    const void *in = s->term[k - 2];
+    if ((rc = run_gather(s, in, A))) return rc;
+    SweepParams p{};
+    sweep_common(s, p, A, k - 1);
+    set_coef(p, 0.0, -dts / k);
+    p.in = in;
+    if (k < 4) {
+      p.out = s->term[k - 1];
+      if ((rc = run_sweep(s, MODE_MID, p, s->tmaps_ok ? &s->smaps[k - 1] : nullptr, k - 1))) return rc;
+    } else {
+      p.psi = s->psi;
+      p.psi_lo = s->psi_lo;
+      p.t1 = s->term[0];
+      p.t2 = s->term[1];
+      if ((rc = run_sweep(s, MODE_LAST, p, s->tmaps_ok ? &s->smaps[3] : nullptr, 3))) return rc;
+    }
+  }
+  return rc;
+}
+
+// V_eff of one CFM4 exponential (push: first store v_x of the current density as the newest
+// history entry).
+static int run_cfm_veff(tdks_system *s, bool push, const double w[4], const double E[3]) {
+  CfmHist h{};
+  for (int j = 0; j < 4; j++) h.v[j] = s->vx_hist[j];
+  h.nh = s->xc == TDKS_XC_LDA_X ? s->n_hist : 0;
+  for (int j = 0; j < 4; j++) h.w[j] = j < h.nh ? w[j] : 0.0;
+  const double El[3] = {s->gauge == TDKS_GAUGE_LENGTH ? E[0] : 0.0, s->gauge == TDKS_GAUGE_LENGTH ? E[1] : 0.0,
+                        s->gauge == TDKS_GAUGE_LENGTH ? E[2] : 0.0};
+  Timed tm(s, 2);
+  cudaError_t e = launch_cfm_veff(s->prec, s->bc == TDKS_BC_BLOCH, s->N, s->nx, s->ny, s->nz, s->h, s->n_kb,
+                                  s->n_batches, s->d_wocc, s->dens_part, s->vloc, s->xc == TDKS_XC_LDA_X,
+                                  push ? 1 : 0, h, El, s->aux, s->stream);
+  s->launches++;
+  if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("cfm4 potential: ") + cudaGetErrorString(e));
+  return TDKS_OK;
+}
+
+// CFM4 steps (see tdks_set_propagator).
+static int propagate_cfm4(tdks_system *s, double t0, double dt, int n_steps, int substeps) {
+  if (s->gauge == TDKS_GAUGE_VELOCITY)
+    return fail(TDKS_EINVAL, "CFM4 needs a field that enters H linearly (length gauge or no field)");
+  const double ds = dt / substeps;
+  if (std::fabs(0.5 * ds) * kinetic_max(s) > 2.0 * std::sqrt(2.0))
+    return fail(TDKS_EUNSTABLE, "CFM4 half sub-step beyond the Taylor-4 stability limit (dt_sub/2 * K_max > 2 sqrt 2)");
+  int rc = ensure_density(s);
+  if (rc) return rc;
+  double a[2], th[2];
+  cfm4_constants(a, th);
+  const double A0[3] = {0.0, 0.0, 0.0};
+  for (int st = 0; st < n_steps; st++) {
+    const double t = t0 + st * dt;
+    for (int j = 0; j < substeps; j++) {
+      const double tj = t + j * ds;
+      if (j == 0) {
+        // record of the state at t: the Hamiltonian of t + ds/2 with v_x of this state
+        double E[3], A[3];
+        field_at(s, tj + 0.5 * ds, E, A);
+        if ((rc = run_lda(s, E, A))) return rc;
+        if ((rc = first_sweep(s, 1.0, 0.0, A, true))) return rc;
+        double *slot = s->ring + (s->steps % tdks_system::RING) * TDKS_RECORD;
+        if ((rc = run_finalize(s, slot, t, E, A))) return rc;
+      }
+      double E1[3], E2[3], Af[3], Ef[3], Es[3];
+      field_at(s, tj + th[0] * ds, E1, Af);
+      field_at(s, tj + th[1] * ds, E2, Af);
+      for (int ax = 0; ax < 3; ax++) {
+        Ef[ax] = 2.0 * (a[1] * E1[ax] + a[0] * E2[ax]);
+        Es[ax] = 2.0 * (a[0] * E1[ax] + a[1] * E2[ax]);
+      }
+      const bool xc = s->xc == TDKS_XC_LDA_X;
+      if (xc) {  // the oldest history slot becomes the newest
+        double *oldest = s->vx_hist[3];
+        for (int q = 3; q > 0; q--) s->vx_hist[q] = s->vx_hist[q - 1];
+        s->vx_hist[0] = oldest;
+        s->n_hist = std::min(s->n_hist + 1, 4);
+      }
+      double wf[4] = {0, 0, 0, 0}, ws[4] = {0, 0, 0, 0};
+      if (xc) cfm4_history_weights(s->n_hist, wf, ws);
+      if ((rc = run_cfm_veff(s, xc, wf, Ef))) return rc;
+      if ((rc = first_sweep(s, 0.0, -0.5 * ds, A0, false))) return rc;
+      if ((rc = taylor_tail(s, 0.5 * ds, A0))) return rc;
+      if ((rc = run_cfm_veff(s, false, ws, Es))) return rc;
+      if ((rc = first_sweep(s, 0.0, -0.5 * ds, A0, false))) return rc;
+      if ((rc = taylor_tail(s, 0.5 * ds, A0))) return rc;
+      s->dens_valid = true;  // the last sweep wrote the density of the new state
+    }
+    s->steps++;
+  }
+  s->clock_t = t0 + n_steps * dt;
+  s->clock_dt = dt;
+  s->clock_substeps = substeps;
+  return TDKS_OK;
+}
+
+int tdks_set_propagator(tdks_sys s, int propagator) {
+  if (!s) return fail(TDKS_EINVAL, "NULL system");
+  if (propagator != TDKS_PROP_TAYLOR4 && propagator != TDKS_PROP_CFM4)
+    return fail(TDKS_EINVAL, "propagator must be TDKS_PROP_TAYLOR4 or TDKS_PROP_CFM4");
+  CU(cudaStreamSynchronize(s->stream));
+  if (propagator == TDKS_PROP_CFM4 && !s->vx_hist[0])
+    for (int j = 0; j < 4; j++) CU(cudaMalloc((void **)&s->vx_hist[j], (size_t)s->N * sizeof(double)));
+  s->prop = propagator;
+  s->n_hist = 0;
+  return TDKS_OK;
+}
+
 int tdks_propagate_n(tdks_sys s, double t0, double dt, int n_steps, int substeps) {
   if (!s) return fail(TDKS_EINVAL, "NULL system");
   if (n_steps < 0 || substeps < 0) return fail(TDKS_EINVAL, "negative count");
   if (!s->have_orbitals) return fail(TDKS_ESTATE, "orbitals not set");
   if (substeps == 0) tdks_auto_substeps(s, dt, &substeps);
+  if (s->prop == TDKS_PROP_CFM4) return propagate_cfm4(s, t0, dt, n_steps, substeps);
   const double dts = dt / substeps;
   if (std::fabs(dts) * kinetic_max(s) > 2.0 * std::sqrt(2.0))
     return fail(TDKS_EUNSTABLE, "sub-step beyond the Taylor-4 stability limit (dt_sub * K_max > 2 sqrt 2)");
@@ -959,24 +1102,7 @@ int tdks_propagate_n(tdks_sys s, double t0, double dt, int n_steps, int substeps
         double *slot = s->ring + (s->steps % tdks_system::RING) * TDKS_RECORD;
         if ((rc = run_finalize(s, slot, t, E, A))) return rc;
       }
-      for (int k = 2; k <= 4; k++) {
-        const void *in = s->term[k - 2];
-        if ((rc = run_gather(s, in, A))) return rc;
-        SweepParams p{};
-        sweep_common(s, p, A, k - 1);
-        set_coef(p, 0.0, -dts / k);
-        p.in = in;
-        if (k < 4) {
-          p.out = s->term[k - 1];
-          if ((rc = run_sweep(s, MODE_MID, p, s->tmaps_ok ? &s->smaps[k - 1] : nullptr, k - 1))) return rc;
-        } else {
-          p.psi = s->psi;
-          p.psi_lo = s->psi_lo;
-          p.t1 = s->term[0];
-          p.t2 = s->term[1];
-          if ((rc = run_sweep(s, MODE_LAST, p, s->tmaps_ok ? &s->smaps[3] : nullptr, 3))) return rc;
-        }
-      }
+      if ((rc = taylor_tail(s, dts, A))) return rc;
       s->dens_valid = true;  // MODE_LAST wrote the density of the new state
     }
     s->steps++;

@@ -186,6 +186,16 @@ cudaError_t launch_lda(int prec, int bloch, long N, int nx, int ny, int nz, doub
                        int n_blocks, cudaStream_t s);
 // fin_part: device scratch of FIN_BLOCKS * 10 doubles for the first of the two stages
 constexpr int FIN_BLOCKS = 64;
+// CFM4 exchange history: v[j] is v_x at the start of the j-th latest sub-step (v[0] the
+// newest), w[j] its weight in an exponential's effective potential, nh the points in use.
+struct CfmHist {
+  double *v[4];
+  double w[4];
+  int nh;
+};
+cudaError_t launch_cfm_veff(int prec, int bloch, long N, int nx, int ny, int nz, double h, int n_kb, int n_batches,
+                            const double *wocc, const double *dens_part, const double *vloc, int xc, int push,
+                            const CfmHist &hist, const double E[3], PointAux *aux, cudaStream_t s);
 cudaError_t launch_finalize(const double *obs_part, long n_items, const double *lda_part,
                             int n_lda_blocks, double *record, double t_state, double h3,
                             double occ, int bloch, double omega_cell, const double A[3],

@@ -78,6 +78,10 @@ struct tdks_system {
   size_t state_bytes = 0, term_bytes = 0;
   bool have_orbitals = false, dens_valid = false;
   long long steps = 0;
+  // propagator (tdks_set_propagator); CFM4 keeps v_x of the last four sub-step starts
+  int prop = TDKS_PROP_TAYLOR4;
+  double *vx_hist[4] = {nullptr, nullptr, nullptr, nullptr};  // [0] the newest
+  int n_hist = 0;
   // clock used by batched propagation: state time, step length, sub-steps per step
   double clock_t = 0.0, clock_dt = 0.0;
   int clock_substeps = 1;

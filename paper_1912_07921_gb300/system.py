@@ -152,6 +152,10 @@ class System:
         """dev_in / dev_out: device pointers (e.g. torch tensor .data_ptr()) in the packed layout."""
         _lib.check(self.lib.tdks_apply_H(self.h, t, ctypes.c_void_p(dev_in), ctypes.c_void_p(dev_out)))
 
+    def set_propagator(self, propagator: int):
+        """0: Taylor-4 (default); 1: CFM4 (two exponentials per sub-step)."""
+        _lib.check(self.lib.tdks_set_propagator(self.h, propagator))
+
     def propagate(self, t0: float, dt: float, n_steps: int, substeps: int = 0):
         _lib.check(self.lib.tdks_propagate_n(self.h, t0, dt, n_steps, substeps))
 

@@ -245,6 +245,47 @@ def test_upload_issued_during_a_propagation_is_ordered(prec):
     b.close()
 
 
+@pytest.mark.parametrize("case", ["tiny_c128", "ragged_c128", "tiny_c64"])
+def test_cfm4_matches_oracle(case):
+    """CFM4 on the GPU (two Taylor-4 exponentials of dt/2 per sub-step with effective fields,
+    the exchange potential extrapolated from the last four sub-steps) against the oracle's
+    CFM4: the LDA history fills during the run; with projectors and two sub-steps per step."""
+    if case == "ragged_c128":
+        spec = ragged_molecule(I.PREC_C128)
+        n_steps, subs, dt = 4, 2, 0.03
+    else:
+        spec = I.tiny_molecule(prec=I.PREC_C128 if case == "tiny_c128" else I.PREC_C64)
+        n_steps, subs, dt = 12, 1, spec.dt
+    inp = I.make_inputs(spec)
+    sysm = _system(spec, inp)
+    sysm.set_propagator(1)
+    sysm.propagate(0.0, dt, n_steps, subs)
+    psi, rec = sysm.get_orbitals(), sysm.reductions(0, n_steps)
+    sysm.close()
+    psi_o, rec_o = oracle.System(spec, inp).propagate_cfm4(inp.psi0, 0.0, dt, n_steps, subs)
+    tol = 1e-12 if spec.prec == I.PREC_C128 else 2e-5
+    assert rel_err(psi, psi_o) < tol
+    assert _rec_err(rec, rec_o) < tol
+
+
+def test_cfm4_refuses_the_velocity_gauge_and_batches():
+    from paper_1912_07921_gb300 import _lib
+    from paper_1912_07921_gb300.system import Batch
+    spec = bloch_cell(I.PREC_C64)
+    sysm = _system(spec, bloch_inputs(spec))
+    sysm.set_propagator(1)
+    with pytest.raises(_lib.TdksError):
+        sysm.propagate(0.0, 0.01, 1, 1)
+    sysm.close()
+    spec = I.tiny_molecule(prec=I.PREC_C64)
+    a = _system(spec, I.make_inputs(spec))
+    a.set_propagator(1)
+    a.set_clock(0.0, spec.dt, 1)
+    with pytest.raises(_lib.TdksError):
+        Batch([a], stream=torch.cuda.current_stream().cuda_stream)
+    a.close()
+
+
 def _propagate_both(spec, inp, n_steps, substeps, dt=None):
     dt = spec.dt if dt is None else dt
     sysm = _system(spec, inp)
