@@ -461,6 +461,52 @@ def run_periodic_side(args):
             "autotune_ms_per_launch": None if tune is None else [[round(float(x), 4) for x in r] for r in tune]}
 
 
+def run_propagator_study(args):
+    """Cost against error of the two propagators (the comparison of the paper's EMR/CFM4
+    figure, on a synthetic molecule): a 48^3 molecule (h = 0.25, order 8, 16 orbitals in
+    complex128, 6 atoms with projectors, LDA exchange, laser E0 = 0.02, omega = 0.5) over
+    T = 1 (20 steps of dt = 0.05), with Taylor-4 at 4, 8, 16 and CFM4 at 2, 4, 8 sub-steps per
+    step; error = ||psi - psi_ref|| / ||psi_ref||, psi_ref from CFM4 at 64 sub-steps; time from
+    CUDA events around each propagation."""
+    import dataclasses as dc
+    import torch
+    from paper_1912_07921_gb300 import inputs as I
+    from paper_1912_07921_gb300.system import System
+    spec = dc.replace(I.medium_molecule(prec=I.PREC_C128), nx=48, ny=48, nz=48, n_orb=16, n_atoms=6, amp=0.02,
+                      omega=0.5, envelope=I.ENV_NONE)
+    inp = I.make_inputs(spec)
+    stream = torch.cuda.Stream()
+    T, n_steps = 1.0, 20
+    dt = T / n_steps
+
+    def run(prop, subs):
+        s = System(spec, inp, stream=stream.cuda_stream)
+        s.set_propagator(prop)
+        s.propagate(0.0, dt, 1, subs)  # warm-up (then restart from the same state)
+        s.set_orbitals(inp.psi0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.propagate(0.0, dt, n_steps, subs)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        psi = s.get_orbitals()
+        s.close()
+        return psi, e0.elapsed_time(e1)
+
+    ref, _ = run(1, 64)
+    nref = np.linalg.norm(ref)
+    pts = []
+    for prop, name, subs_list in ((0, "taylor4", (4, 8, 16)), (1, "cfm4", (2, 4, 8))):
+        for subs in subs_list:
+            psi, ms = run(prop, subs)
+            pts.append({"propagator": name, "substeps": subs, "ms": round(ms, 2),
+                        "err": float(np.linalg.norm(psi - ref) / nref)})
+    return {"workload": "48^3 molecule h=0.25 order-8, 16 orbitals c128, 6 atoms x 4 KB, LDA exchange, "
+                        "laser E0=0.02 omega=0.5, T=1 as 20 steps of dt=0.05",
+            "reference": "CFM4 at 64 sub-steps per step", "points": pts}
+
+
 def run_serving(args):
     """A scaled serving trace (Poisson arrivals) through the continuous-batching server.
     Each request carries its inputs (built before the server starts, as a client would
@@ -552,6 +598,7 @@ def main():
     ap.add_argument("--n-orb", type=int, default=0,
                     help="orbital count override (profiling on a smaller case); 0 = the workload's 64")
     ap.add_argument("--no-tune", action="store_true", help="keep the default sweep tile shape (no autotuner)")
+    ap.add_argument("--no-study", action="store_true", help="skip the propagator cost-against-error study")
     ap.add_argument("--shape", type=int, default=-1, help="force one sweep tile shape for all Taylor terms")
     ap.add_argument("--sweep-path", type=int, default=0,
                     help="stencil sweep variant: 0 warp-specialised TMA (default), 1 general, 2 lockstep TMA")
@@ -587,6 +634,8 @@ def main():
             out["periodic"] = run_periodic_side(args)
         if args.serving and world == 1:
             out["serving"] = run_serving(args)
+        if not args.no_study and world == 1:
+            out["propagators"] = run_propagator_study(args)
         if not args.no_cpu and world == 1:
             out["cpu_baseline"] = cpu_baseline(32)
         print(json.dumps(out))
