@@ -430,11 +430,15 @@ def run_periodic_side(args):
     import torch
     from paper_1912_07921_gb300 import inputs as I
     from paper_1912_07921_gb300.system import System
-    spec = I.periodic_cell()
+    spec = I.periodic_cell(n_k=args.periodic_k)
     inp = I.make_inputs(spec)
     stream = torch.cuda.Stream()
     sysm = System(spec, inp, stream=stream.cuda_stream)
-    tune = None if args.no_tune else sysm.autotune(reps=3)
+    tune = None
+    if args.shape >= 0:
+        sysm.set_sweep_shape(-1, args.shape)
+    elif not args.no_tune:
+        tune = sysm.autotune(reps=3)
     sysm.propagate(0.0, spec.dt, 2, spec.substeps)
     torch.cuda.synchronize()
     k = max(2, args.steps // 20)
@@ -454,7 +458,7 @@ def run_periodic_side(args):
     # algorithmic bytes per sweep launch: 104 B per value per sub-step (as the medium molecule's
     # complex64 path) over four sweeps, plus the 16-byte point records per orbital block
     per_launch = (spec.n_points * states * 104 + spec.n_points * 16 * 4 * (states // 8)) / 4
-    return {"workload": "periodic cell 64^3 L=10.2 order-4 FD, 32 k x 16 bands c64, 8 atoms x 4 KB, "
+    return {"workload": f"periodic cell 64^3 L=10.2 order-4 FD, {spec.n_k} k x 16 bands c64, 8 atoms x 4 KB, "
                         "velocity gauge A0=0.2, dt=0.04 as 6 Taylor-4 sub-steps",
             "value": spec.n_points * states * k / (ms / 1e3), "unit": UNIT, "steps": k, "ms_per_step": ms / k,
             "sweep_gbs": per_launch / ((sweep_ms / 1e3) / max(sweep_n, 1)) / 1e9, "sweep_shapes": shapes,
@@ -593,6 +597,8 @@ def main():
     ap.add_argument("--batched", type=int, default=256,
                     help="also measure the batched workload with this many systems (0: skip)")
     ap.add_argument("--no-periodic", action="store_true", help="skip the periodic-cell side measurement")
+    ap.add_argument("--periodic-k", type=int, default=32,
+                    help="k-points of the periodic cell (profiling on a smaller case); 32 = the workload")
     ap.add_argument("--serving", type=int, default=48,
                     help="also run a serving trace with this many jobs")
     ap.add_argument("--n-orb", type=int, default=0,
