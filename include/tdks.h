@@ -179,6 +179,32 @@ int tdks_propagate_n(tdks_sys sys, double t0, double dt, int n_steps, int subste
 #define TDKS_PROP_CFM4 1
 int tdks_set_propagator(tdks_sys sys, int propagator);
 
+/*
+ * State-parallel propagation (one molecule over several GPUs, each holding a slice of the
+ * orbitals).  The Hamiltonian couples the orbitals only through the density
+ * n(r) = sum_i f_i |phi_i(r)|^2 in v_x[n] (Sec. "New propagators for real-time TDDFT":
+ * H[n(t), t]); everything else in a Taylor sub-step acts on each orbital alone.  A system
+ * created with its slice's n_orb becomes one rank of such a run once an exchange hook is
+ * set: wherever the library needs n (every sub-step of tdks_propagate_n, tdks_observe,
+ * tdks_apply_H) it sums its own states' density into a device buffer of N doubles
+ * (N = nx ny nz; the k-points' weights already applied) and calls
+ *     fn(dev_buf, N, stream, ctx),
+ * which must replace dev_buf, in place, with the sum of all ranks' buffers (an allreduce)
+ * before work later enqueued on `stream` (the system's cudaStream_t) reads it; v_x and the
+ * density terms of the record are then built from that sum.  For each observable record
+ * it calls fn once more with n = 4 (this rank's band energy sum_i f_i <phi_i|H|phi_i> and
+ * its three current sums) to get the whole system's.  Every rank must make the same calls
+ * in the same order with the same arguments (times, fields, steps), and every rank's
+ * record is then the whole system's.  fn returns 0 on success; any other value stops the
+ * call with TDKS_EDEVICE.  fn runs on the calling thread, while earlier work may still run
+ * on the stream.  Every rank holds the same k-points, grid, potentials, projectors and
+ * field.  Taylor-4 only: TDKS_EINVAL from tdks_set_propagator(CFM4) while a hook is set and
+ * from this call on a CFM4 system.  fn = NULL detaches the hook.  ctx is passed through
+ * untouched.
+ */
+typedef int (*tdks_exchange_fn)(double *dev_buf, long long n, void *stream, void *ctx);
+int tdks_set_exchange(tdks_sys sys, tdks_exchange_fn fn, void *ctx);
+
 /* Sub-step count the automatic policy of tdks_propagate_n picks for step dt. */
 int tdks_auto_substeps(tdks_sys sys, double dt, int *substeps);
 

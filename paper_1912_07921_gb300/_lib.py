@@ -28,6 +28,7 @@ SIGNATURES = {
     "tdks_apply_H": ([P, D, P, P], I),
     "tdks_propagate_n": ([P, D, D, I, I], I),
     "tdks_set_propagator": ([P, I], I),
+    "tdks_set_exchange": ([P, P, P], I),
     "tdks_auto_substeps": ([P, D, PI], I),
     "tdks_reductions": ([P, LL, I, P], I),
     "tdks_step_count": ([P, PLL], I),
@@ -53,6 +54,9 @@ SIGNATURES = {
     "tdks_apply_H_noalloc": ([I, I, I, D, I, I, I, P, P, P, P], I),
     "tdks_last_error": ([], ctypes.c_char_p),
 }
+
+# C type of the exchange hook of tdks_set_exchange: (dev_buf, n, stream, ctx) -> status
+EXCHANGE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p)
 
 _lib = None
 

@@ -390,7 +390,8 @@ template <typename R>
 __device__ __forceinline__ void lda_body(long N, int nx, int ny, int nz, double h, int bloch, int n_kb,
                                          int n_batches, const double *wocc, const double *dens_part,
                                          const double *vloc, int xc, double Ex, double Ey, double Ez,
-                                         double half_A2, PointAux *aux, double *lda_part, int blk, int nblk) {
+                                         double half_A2, PointAux *aux, double *lda_part, int blk, int nblk,
+                                         const double *n_in = nullptr) {
   constexpr bool F32 = sizeof(R) == 4;
   const int n_k = n_kb / n_batches;
   __shared__ float2 s_w[LDA_MAXK];  // complex64: w_k f = hi + lo
@@ -410,7 +411,12 @@ __device__ __forceinline__ void lda_body(long N, int nx, int ny, int nz, double 
   for (long p = blk * (long)blockDim.x + threadIdx.x; p < N; p += (long)nblk * blockDim.x) {
     double n = 0.0;
     float nh = 0.f, nl = 0.f;  // complex64: n = nh + nl
-    if constexpr (F32) {
+    if (n_in) {
+      // the density summed over every rank's states (state-parallel propagation)
+      n = n_in[p];
+      nh = (float)n;
+      nl = (float)(n - (double)nh);
+    } else if constexpr (F32) {
       const float2 *d2 = reinterpret_cast<const float2 *>(dens_part);
       for (int k = 0; k < n_k; k++) {
         float sh = 0.f, sl = 0.f;  // sum over the k-point's batches of sum |psi|^2
@@ -482,9 +488,50 @@ template <typename R>
 __global__ void __launch_bounds__(LDA_THREADS)
 lda_kernel(long N, int nx, int ny, int nz, double h, int bloch, int n_kb, int n_batches, const double *wocc,
            const double *dens_part, const double *vloc, int xc, double Ex, double Ey, double Ez, double half_A2,
-           PointAux *aux, double *lda_part) {
+           PointAux *aux, double *lda_part, const double *n_in) {
   lda_body<R>(N, nx, ny, nz, h, bloch, n_kb, n_batches, wocc, dens_part, vloc, xc, Ex, Ey, Ez, half_A2, aux,
-              lda_part, blockIdx.x, gridDim.x);
+              lda_part, blockIdx.x, gridDim.x, n_in);
+}
+
+// The density of this system's states at every point, n(r) = sum_k w_k f sum_i |psi|^2, as
+// FP64 (the LDA kernel's sum: in order over the batches, complex64 partials as double-float),
+// for a state-parallel run to sum over ranks before the LDA kernel reads it back.
+template <typename R>
+__global__ void __launch_bounds__(LDA_THREADS)
+density_sum_kernel(long N, int n_kb, int n_batches, const double *wocc, const double *dens_part, double *n_out) {
+  constexpr bool F32 = sizeof(R) == 4;
+  const int n_k = n_kb / n_batches;
+  for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < N; p += (long)gridDim.x * blockDim.x) {
+    if constexpr (F32) {
+      const float2 *d2 = reinterpret_cast<const float2 *>(dens_part);
+      float nh = 0.f, nl = 0.f;
+      for (int k = 0; k < n_k; k++) {
+        float sh = 0.f, sl = 0.f;
+        for (int b = 0; b < n_batches; b++) {
+          const float2 d = d2[(long)(k * n_batches + b) * N + p];
+          df_add_df(sh, sl, d.x, d.y);
+        }
+        const float wh = (float)wocc[k], wl = (float)(wocc[k] - (double)wh);
+        const float ph = sh * wh;
+        const float pl = fmaf(sh, wh, -ph) + (sh * wl + sl * wh);
+        df_add_df(nh, nl, ph, pl);
+      }
+      n_out[p] = (double)nh + (double)nl;
+    } else {
+      double n = 0.0;
+      for (int kb = 0; kb < n_kb; kb++) n += dens_part[(long)kb * N + p];
+      n_out[p] = n;
+    }
+  }
+}
+
+cudaError_t launch_density_sum(int prec, long N, int n_kb, int n_batches, const double *wocc,
+                               const double *dens_part, double *n_out, cudaStream_t s) {
+  if (prec == P_C64)
+    density_sum_kernel<float><<<lda_blocks(N), LDA_THREADS, 0, s>>>(N, n_kb, n_batches, wocc, dens_part, n_out);
+  else
+    density_sum_kernel<double><<<lda_blocks(N), LDA_THREADS, 0, s>>>(N, n_kb, n_batches, wocc, dens_part, n_out);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------------
@@ -604,13 +651,14 @@ cudaError_t launch_lda_batch(int prec, const BatchAux *aux, const BatchClock *cl
 
 cudaError_t launch_lda(int prec, int bloch, long N, int nx, int ny, int nz, double h, int n_kb, int n_batches,
                        const double *wocc, const double *dens_part, const double *vloc, int xc, const double E[3],
-                       double half_A2, PointAux *aux, double *lda_part, int n_blocks, cudaStream_t s) {
+                       double half_A2, PointAux *aux, double *lda_part, int n_blocks, cudaStream_t s,
+                       const double *n_in) {
   if (prec == P_C64)
     lda_kernel<float><<<n_blocks, LDA_THREADS, 0, s>>>(N, nx, ny, nz, h, bloch, n_kb, n_batches, wocc, dens_part,
-                                                       vloc, xc, E[0], E[1], E[2], half_A2, aux, lda_part);
+                                                       vloc, xc, E[0], E[1], E[2], half_A2, aux, lda_part, n_in);
   else
     lda_kernel<double><<<n_blocks, LDA_THREADS, 0, s>>>(N, nx, ny, nz, h, bloch, n_kb, n_batches, wocc, dens_part,
-                                                        vloc, xc, E[0], E[1], E[2], half_A2, aux, lda_part);
+                                                        vloc, xc, E[0], E[1], E[2], half_A2, aux, lda_part, n_in);
   return cudaGetLastError();
 }
 
@@ -741,12 +789,47 @@ cudaError_t launch_batch_tail(const BatchAux *aux, BatchClock *clk, int n_sys, i
   return cudaGetLastError();
 }
 
+__global__ void __launch_bounds__(32) finalize_sums_kernel(const double *fin_part, int nb, double *sums) {
+  const int t = threadIdx.x;
+  if (t < 10) {
+    double x = 0.0;
+    for (int b = 0; b < nb; b++) x += fin_part[b * 10 + t];
+    sums[t] = x;
+  }
+}
+
+__global__ void __launch_bounds__(32)
+record_from_sums_kernel(const double *sums, double *rec, double t_state, double h3, double occ, int bloch,
+                        double omega_cell, double Ax, double Ay, double Az, double field_val) {
+  if (threadIdx.x == 0) write_record(sums, sums + 4, rec, t_state, h3, occ, bloch, omega_cell, Ax, Ay, Az, field_val);
+}
+
+static int finalize_blocks(long n_items, int n_lda) {
+  const long want = (n_items + n_lda + 4L * FIN_THREADS - 1) / (4L * FIN_THREADS);
+  return (int)(want < 1 ? 1 : (want > FIN_BLOCKS ? FIN_BLOCKS : want));
+}
+
+cudaError_t launch_finalize_sums(const double *obs_part, long n_items, const double *lda_part, int n_lda,
+                                 double *fin_part, double *sums, cudaStream_t s) {
+  const int nb = finalize_blocks(n_items, n_lda);
+  finalize_stage1_kernel<<<nb, FIN_THREADS, 0, s>>>(obs_part, n_items, lda_part, n_lda, fin_part);
+  finalize_sums_kernel<<<1, 32, 0, s>>>(fin_part, nb, sums);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_record_from_sums(const double *sums, double *record, double t_state, double h3, double occ,
+                                    int bloch, double omega_cell, const double A[3], double field_val,
+                                    cudaStream_t s) {
+  record_from_sums_kernel<<<1, 32, 0, s>>>(sums, record, t_state, h3, occ, bloch, omega_cell, A[0], A[1], A[2],
+                                           field_val);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_finalize(const double *obs_part, long n_items, const double *lda_part, int n_lda,
                             double *record, double t_state, double h3, double occ, int bloch,
                             double omega_cell, const double A[3], double field_val, double *fin_part,
                             cudaStream_t s) {
-  const long want = (n_items + n_lda + 4L * FIN_THREADS - 1) / (4L * FIN_THREADS);
-  const int nb = (int)(want < 1 ? 1 : (want > FIN_BLOCKS ? FIN_BLOCKS : want));
+  const int nb = finalize_blocks(n_items, n_lda);
   finalize_stage1_kernel<<<nb, FIN_THREADS, 0, s>>>(obs_part, n_items, lda_part, n_lda, fin_part);
   finalize_stage2_kernel<<<1, 32, 0, s>>>(fin_part, nb, record, t_state, h3, occ, bloch, omega_cell, A[0], A[1],
                                           A[2], field_val);

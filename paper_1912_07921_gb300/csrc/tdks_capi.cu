@@ -21,17 +21,16 @@ namespace tdks_host {
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn lookup_encode_fn() {
+  void *f = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+      q == cudaDriverEntryPointSuccess)
+    return reinterpret_cast<EncodeTiledFn>(f);
+  return nullptr;
+}
 EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
-    void *f = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(f);
-  }
+  static const EncodeTiledFn fn = lookup_encode_fn();  // initialised once, thread-safe
   return fn;
 }
 
@@ -352,10 +351,18 @@ int run_lda(tdks_system *s, const double E[3], const double A[3]) {
   const double half_A2 = s->gauge == TDKS_GAUGE_VELOCITY ? 0.5 * (A[0] * A[0] + A[1] * A[1] + A[2] * A[2]) : 0.0;
   const double El[3] = {s->gauge == TDKS_GAUGE_LENGTH ? E[0] : 0.0, s->gauge == TDKS_GAUGE_LENGTH ? E[1] : 0.0,
                         s->gauge == TDKS_GAUGE_LENGTH ? E[2] : 0.0};
+  if (s->xfn) {  // state-parallel: the density of every rank's states
+    cudaError_t e = launch_density_sum(s->prec, s->N, s->n_kb, s->n_batches, s->d_wocc, s->dens_part, s->n_total,
+                                       s->stream);
+    s->launches++;
+    if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("density sum: ") + cudaGetErrorString(e));
+    if (int r = s->xfn(s->n_total, (long long)s->N, (void *)s->stream, s->xctx))
+      return fail(TDKS_EDEVICE, "exchange hook failed on the density (" + std::to_string(r) + ")");
+  }
   Timed tm(s, 2);
   cudaError_t e = launch_lda(s->prec, s->bc == TDKS_BC_BLOCH, s->N, s->nx, s->ny, s->nz, s->h, s->n_kb,
                              s->n_batches, s->d_wocc, s->dens_part, s->vloc, s->xc, El, half_A2, s->aux,
-                             s->lda_part, lda_blocks(s->N), s->stream);
+                             s->lda_part, lda_blocks(s->N), s->stream, s->xfn ? s->n_total : nullptr);
   s->launches++;
   if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("lda: ") + cudaGetErrorString(e));
   return TDKS_OK;
@@ -367,6 +374,19 @@ int run_finalize(tdks_system *s, double *rec, double t_state, const double E[3],
   double fv = 0.0;
   for (int a = 0; a < 3; a++) fv += (s->gauge == TDKS_GAUGE_VELOCITY ? A[a] : E[a]) * s->pol[a];
   const double Az[3] = {0, 0, 0};
+  if (s->xfn) {  // state-parallel: band energy and currents summed over the ranks
+    cudaError_t e = launch_finalize_sums(s->obs_part, s->obs_count, s->lda_part, lda_blocks(s->N), s->fin_part,
+                                         s->fin_sum, s->stream);
+    s->launches += 2;
+    if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("finalize: ") + cudaGetErrorString(e));
+    if (int r = s->xfn(s->fin_sum, 4, (void *)s->stream, s->xctx))
+      return fail(TDKS_EDEVICE, "exchange hook failed on the record sums (" + std::to_string(r) + ")");
+    e = launch_record_from_sums(s->fin_sum, rec, t_state, h3, s->occ, s->bc == TDKS_BC_BLOCH, omega_cell,
+                                s->gauge == TDKS_GAUGE_VELOCITY ? A : Az, fv, s->stream);
+    s->launches++;
+    if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("record: ") + cudaGetErrorString(e));
+    return TDKS_OK;
+  }
   Timed tm(s, 2);
   cudaError_t e = launch_finalize(s->obs_part, s->obs_count, s->lda_part, lda_blocks(s->N), rec, t_state, h3,
                                   s->occ, s->bc == TDKS_BC_BLOCH, omega_cell,
@@ -549,7 +569,9 @@ int tdks_destroy(tdks_sys s) {
   for (int i = 0; i < 3; i++) cudaFree(s->term[i]);
   cudaFree(s->vloc); cudaFree(s->aux); cudaFree(s->dens_part); cudaFree(s->lda_part);
   cudaFree(s->obs_part); cudaFree(s->ring); cudaFree(s->fin_part);
-  for (int j = 0; j < 4; j++) cudaFree(s->vx_hist[j]); cudaFree(s->obs_rec); cudaFree(s->d_kvec); cudaFree(s->d_wocc);
+  for (int j = 0; j < 4; j++) cudaFree(s->vx_hist[j]);
+  cudaFree(s->n_total); cudaFree(s->fin_sum);
+  cudaFree(s->obs_rec); cudaFree(s->d_kvec); cudaFree(s->d_wocc);
   cudaFree(s->staging);
   if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
   if (s->ev_staging_free) cudaEventDestroy(s->ev_staging_free);
@@ -1070,11 +1092,26 @@ int tdks_set_propagator(tdks_sys s, int propagator) {
   if (!s) return fail(TDKS_EINVAL, "NULL system");
   if (propagator != TDKS_PROP_TAYLOR4 && propagator != TDKS_PROP_CFM4)
     return fail(TDKS_EINVAL, "propagator must be TDKS_PROP_TAYLOR4 or TDKS_PROP_CFM4");
+  if (propagator == TDKS_PROP_CFM4 && s->xfn)
+    return fail(TDKS_EINVAL, "state-parallel propagation (tdks_set_exchange) is Taylor-4 only");
   CU(cudaStreamSynchronize(s->stream));
   if (propagator == TDKS_PROP_CFM4 && !s->vx_hist[0])
     for (int j = 0; j < 4; j++) CU(cudaMalloc((void **)&s->vx_hist[j], (size_t)s->N * sizeof(double)));
   s->prop = propagator;
   s->n_hist = 0;
+  return TDKS_OK;
+}
+
+int tdks_set_exchange(tdks_sys s, tdks_exchange_fn fn, void *ctx) {
+  if (!s) return fail(TDKS_EINVAL, "NULL system");
+  if (fn && s->prop != TDKS_PROP_TAYLOR4)
+    return fail(TDKS_EINVAL, "state-parallel propagation is Taylor-4 only");
+  if (fn && !s->n_total) {
+    CU(cudaMalloc((void **)&s->n_total, (size_t)s->N * sizeof(double)));
+    CU(cudaMalloc((void **)&s->fin_sum, 10 * sizeof(double)));
+  }
+  s->xfn = fn;
+  s->xctx = fn ? ctx : nullptr;
   return TDKS_OK;
 }
 

@@ -19,7 +19,23 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 namespace tdks {
+
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) once per device for kernel k; `done`
+// (one per kernel instantiation) records the devices already set, safely across host
+// threads that drive systems at the same time.
+template <typename K>
+inline cudaError_t ensure_smem_attr(K k, size_t smem, std::atomic<unsigned> &done) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const unsigned bit = dev < 32 ? 1u << dev : 0u;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
+  return e;
+}
 
 constexpr int OVC = 4;        // 16-byte vectors per (point, batch)
 constexpr int MAXM = 4;       // largest FD half-width (8th order)
@@ -183,7 +199,10 @@ cudaError_t launch_lda(int prec, int bloch, long N, int nx, int ny, int nz, doub
                        int n_kb, int n_batches, const double *wocc, const double *dens_part,
                        const double *vloc, int xc,
                        const double E[3], double half_A2, PointAux *aux, double *lda_part,
-                       int n_blocks, cudaStream_t s);
+                       int n_blocks, cudaStream_t s, const double *n_in = nullptr);
+// n_out[r] = sum over this system's states of w_k f |psi_ik(r)|^2 (FP64), from dens_part
+cudaError_t launch_density_sum(int prec, long N, int n_kb, int n_batches, const double *wocc,
+                               const double *dens_part, double *n_out, cudaStream_t s);
 // fin_part: device scratch of FIN_BLOCKS * 10 doubles for the first of the two stages
 constexpr int FIN_BLOCKS = 64;
 // CFM4 exchange history: v[j] is v_x at the start of the j-th latest sub-step (v[0] the
@@ -200,6 +219,14 @@ cudaError_t launch_finalize(const double *obs_part, long n_items, const double *
                             int n_lda_blocks, double *record, double t_state, double h3,
                             double occ, int bloch, double omega_cell, const double A[3],
                             double field_val, double *fin_part, cudaStream_t s);
+// The same record in two parts, for state-parallel runs: the 10 sums into sums[0..9]
+// (sums[0..3]: this rank's band energy and current; sums[4..9]: from the summed density),
+// then, once the caller has summed sums[0..3] over the ranks, the record from sums.
+cudaError_t launch_finalize_sums(const double *obs_part, long n_items, const double *lda_part, int n_lda_blocks,
+                                 double *fin_part, double *sums, cudaStream_t s);
+cudaError_t launch_record_from_sums(const double *sums, double *record, double t_state, double h3, double occ,
+                                    int bloch, double omega_cell, const double A[3], double field_val,
+                                    cudaStream_t s);
 // host layout -> internal layout and density partials, points [pt0, pt0 + npts) of k-point k
 cudaError_t launch_pack_in(int prec, long N, int k, long pt0, long npts, int n_orb, int n_batches,
                            const double *plain, void *internal, void *internal_lo, const double *wocc,

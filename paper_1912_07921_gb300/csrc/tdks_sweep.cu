@@ -195,12 +195,8 @@ template <int M, int P, int MODE, int BLOCH, int TX, int TY>
 static cudaError_t launch_t(const SweepParams &p, int grid, cudaStream_t s) {
   const size_t smem = sweep_smem(M, TX, TY);
   auto k = sweep_kernel<M, P, MODE, BLOCH, TX, TY>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static std::atomic<unsigned> attr_done{0};
+  if (cudaError_t e = ensure_smem_attr(k, smem, attr_done)) return e;
   if (grid <= 0) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);

@@ -240,12 +240,8 @@ template <int M, int P, int MODE, int U>
 static cudaError_t launch_lockstep_t(const SweepMaps &maps, const SweepParams &p, int grid, cudaStream_t s) {
   typedef TmaGeom<M, 16, 8, U, MODE == MODE_LAST> G;
   auto k = tma_sweep_kernel<M, P, MODE, 16, 8, U>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static std::atomic<unsigned> attr_done{0};
+  if (cudaError_t e = ensure_smem_attr(k, G::SMEM, attr_done)) return e;
   if (grid <= 0) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);

@@ -82,6 +82,11 @@ struct tdks_system {
   int prop = TDKS_PROP_TAYLOR4;
   double *vx_hist[4] = {nullptr, nullptr, nullptr, nullptr};  // [0] the newest
   int n_hist = 0;
+  // state-parallel runs (tdks_set_exchange): hook, its context, the summed density
+  // (N doubles) and the record's 10 sums
+  tdks_exchange_fn xfn = nullptr;
+  void *xctx = nullptr;
+  double *n_total = nullptr, *fin_sum = nullptr;
   // clock used by batched propagation: state time, step length, sub-steps per step
   double clock_t = 0.0, clock_dt = 0.0;
   int clock_substeps = 1;

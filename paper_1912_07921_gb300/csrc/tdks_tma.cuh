@@ -876,12 +876,8 @@ static cudaError_t launch_ws_t(const SweepMaps &maps, const SweepParams &p, int 
   constexpr int TX = WsShape<SHAPE>::TX, TY = WsShape<SHAPE>::TY, R = WsShape<SHAPE>::R;
   typedef TmaGeom<M, TX, TY, 1, MODE == MODE_LAST, BLOCH != 0> G;
   auto k = ws_sweep_kernel<M, P, MODE, TX, TY, R, 1, BLOCH>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static std::atomic<unsigned> attr_done{0};
+  if (cudaError_t e = ensure_smem_attr(k, G::SMEM, attr_done)) return e;
   if (grid <= 0) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -899,12 +895,8 @@ static cudaError_t launch_ws_batch_t(const BatchSweepArgs &a, cudaStream_t s) {
   constexpr int TX = WsShape<SHAPE>::TX, TY = WsShape<SHAPE>::TY, R = WsShape<SHAPE>::R;
   typedef TmaGeom<M, TX, TY, 1, MODE == MODE_LAST> G;
   auto k = ws_sweep_batch_kernel<M, P, MODE, TX, TY, R, 1>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static std::atomic<unsigned> attr_done{0};
+  if (cudaError_t e = ensure_smem_attr(k, G::SMEM, attr_done)) return e;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

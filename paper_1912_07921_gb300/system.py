@@ -150,14 +150,48 @@ class System:
 
     def apply_H(self, t: float, dev_in: int, dev_out: int):
         """dev_in / dev_out: device pointers (e.g. torch tensor .data_ptr()) in the packed layout."""
-        _lib.check(self.lib.tdks_apply_H(self.h, t, ctypes.c_void_p(dev_in), ctypes.c_void_p(dev_out)))
+        self._xcheck(self.lib.tdks_apply_H(self.h, t, ctypes.c_void_p(dev_in), ctypes.c_void_p(dev_out)))
 
     def set_propagator(self, propagator: int):
         """0: Taylor-4 (default); 1: CFM4 (two exponentials per sub-step)."""
         _lib.check(self.lib.tdks_set_propagator(self.h, propagator))
 
+    def set_exchange(self, fn):
+        """Make this system one rank of a state-parallel run (tdks_set_exchange).
+
+        ``fn(ptr, n, stream) -> None`` must replace the n doubles at device address ``ptr``
+        with their sum over all ranks, ordered after the work already on the CUDA stream
+        handle ``stream`` and before what is enqueued there later (see
+        ``sharding.allreduce_exchange``).  ``None`` detaches the hook.  An exception in ``fn``
+        makes the library call that invoked it fail with TDKS_EDEVICE.
+        """
+        if fn is None:
+            _lib.check(self.lib.tdks_set_exchange(self.h, None, None))
+            self._xcb = None
+            return
+
+        def hook(ptr, n, stream, ctx):
+            try:
+                fn(ptr, n, stream)
+                return 0
+            except BaseException as exc:  # reported through the library's status code
+                self._x_error = exc
+                return 1
+
+        cb = _lib.EXCHANGE_FN(hook)
+        _lib.check(self.lib.tdks_set_exchange(self.h, ctypes.cast(cb, ctypes.c_void_p), None))
+        self._xcb = cb  # the C side keeps only the pointer
+        self._x_error = None
+
+    def _xcheck(self, code: int):
+        """check() that chains the exchange hook's exception when the hook failed."""
+        exc, self._x_error = getattr(self, "_x_error", None), None
+        if code != 0 and exc is not None:
+            raise _lib.TdksError(code, _lib.load().tdks_last_error().decode()) from exc
+        _lib.check(code)
+
     def propagate(self, t0: float, dt: float, n_steps: int, substeps: int = 0):
-        _lib.check(self.lib.tdks_propagate_n(self.h, t0, dt, n_steps, substeps))
+        self._xcheck(self.lib.tdks_propagate_n(self.h, t0, dt, n_steps, substeps))
 
     def auto_substeps(self, dt: float) -> int:
         s = ctypes.c_int()
@@ -178,7 +212,7 @@ class System:
 
     def observe(self, t_state: float, t_field: float) -> np.ndarray:
         out = np.empty(RECORD)
-        _lib.check(self.lib.tdks_observe(self.h, t_state, t_field, _dp(out)))
+        self._xcheck(self.lib.tdks_observe(self.h, t_state, t_field, _dp(out)))
         return out
 
     def set_profiling(self, on: bool):
