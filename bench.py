@@ -164,6 +164,13 @@ def max_over_ranks(x: float, dist, device) -> float:
     return float(t.item())
 
 
+def _free_port() -> int:
+    import socket
+    with socket.socket() as so:
+        so.bind(("127.0.0.1", 0))
+        return so.getsockname()[1]
+
+
 def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
     """Replicas: every rank advances its own copy of the workload, so the job's rate is the
     units all ranks processed over the slowest rank's time."""
@@ -178,16 +185,28 @@ def run_ours(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dist = None
-    if world > 1:
+    shard = args.shard == "states"
+    if world > 1 or shard:
         import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+        if world > 1:
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+        else:  # one-rank group: the state-parallel path with its exchange on one GPU
+            dist.init_process_group("nccl", init_method=f"tcp://127.0.0.1:{_free_port()}", rank=0,
+                                    world_size=1, device_id=torch.device("cuda", local_rank))
     prec = I.PREC_C64 if args.prec == "c64" else I.PREC_C128
     spec = I.medium_molecule(prec=prec)
     if args.n_orb:
         spec = dataclasses.replace(spec, n_orb=args.n_orb)
     inp = I.make_inputs(spec)
     stream = torch.cuda.Stream()
-    sysm = System(spec, inp, stream=stream.cuda_stream)
+    if shard:
+        # one molecule over the ranks: each holds its slice of the orbitals; the density and
+        # the record's band sums are allreduced (NCCL) on the library's stream
+        from paper_1912_07921_gb300.sharding import shard_system
+        sysm, (o_lo, o_hi) = shard_system(spec, inp, rank, world, stream=stream.cuda_stream)
+    else:
+        sysm = System(spec, inp, stream=stream.cuda_stream)
+        o_lo, o_hi = 0, spec.n_orb
     if args.sweep_path:
         sysm.set_sweep_path(args.sweep_path)
     tune = None
@@ -199,7 +218,9 @@ def run_ours(args, rank, world, local_rank):
         tune = sysm.autotune(reps=5)
     subs = spec.substeps
     dt = spec.dt
-    upd_per_step = spec.n_points * spec.n_orb
+    upd_per_step = spec.n_points * (o_hi - o_lo)  # this rank's orbital updates per step
+    # the whole job's units per step: every replica's, or the one sharded molecule's
+    job_per_step = spec.n_points * spec.n_orb if shard else upd_per_step * world
 
     def barrier():
         torch.cuda.synchronize()
@@ -235,7 +256,8 @@ def run_ours(args, rank, world, local_rank):
     # observable record back.  The upload of step i+1's inputs is issued right after step i
     # is enqueued, so its copy overlaps step i on the GPU (the library orders the state
     # update after step i); step 0's upload is not overlapped.
-    psi_host = torch.from_numpy(np.ascontiguousarray(inp.psi0).view(np.float64).reshape(-1)).pin_memory()
+    psi_host = torch.from_numpy(np.ascontiguousarray(inp.psi0[..., o_lo:o_hi]).view(np.float64)
+                                .reshape(-1)).pin_memory()
     h2d = psi_host.numel() * 8
     e2e_steps = max(3, min(args.steps, 20))
     # the host link's upload rate on this machine, for context (one upload with its packing)
@@ -260,26 +282,29 @@ def run_ours(args, rank, world, local_rank):
     out = None
     if rank == 0:
         peak, peak_kind = _peaks()
-        bytes_sub = _sweep_bytes(spec, sysm)
+        bytes_sub = _sweep_bytes(sysm.spec, sysm)
         per_launch_bytes = bytes_sub / 4.0
         avg_launch_s = (sweep_ms / 1e3) / max(sweep_n, 1)
         achieved = per_launch_bytes / avg_launch_s / 1e9
-        value = whole_job_rate(upd_per_step * args.steps, world, ms / 1e3)
+        value = (job_per_step * args.steps / (ms / 1e3) if shard
+                 else whole_job_rate(upd_per_step * args.steps, world, ms / 1e3))
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
+            "scaling": "strong" if shard else "weak", "vs_baseline": None,
             "dtype": "c64 terms + f64 state/reductions" if prec == I.PREC_C64 else "c128 (f64)",
             "data": "synthetic (seeded molecule: Gaussian orbitals, wells, KB projectors)",
             "config": {"workload": "medium molecule 96^3 h=0.25 order-8 FD, 64 orbitals, 16 atoms x 4 KB "
                                    "projectors, sin^2 pulse, LDA exchange, dt=0.05 as 4 Taylor-4 sub-steps",
                        "grid": [spec.nx, spec.ny, spec.nz], "n_orb": spec.n_orb, "substeps": subs,
                        "precision": args.prec, "l2": "working set > L2 (state 906 MB + terms), no flush",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"states x{world} (density allreduce per sub-step)" if shard
+                       else f"replicas x{world}"},
             "roofline": {"bound": "hbm", "kernel": "taylor stencil sweep (4 per sub-step)",
                          "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": achieved / peak,
-                         "traffic": _traffic_per_launch() if spec.n_orb == 64 and prec == I.PREC_C64 else None,
+                         "traffic": _traffic_per_launch() if sysm.spec.n_orb == 64 and prec == I.PREC_C64
+                         else None,
                          "sweep_source_hash": sweep_source_hash(),
                          "bytes_per_launch": per_launch_bytes, "avg_launch_us": avg_launch_s * 1e6},
             "kernel_ms": {"sweep": sweep_ms, "sweep_launches": sweep_n, "projector": gath_ms,
@@ -292,8 +317,9 @@ def run_ours(args, rank, world, local_rank):
                                        "ms[shape][sweep], sweeps t1..t4"},
             "gpu_launches": launches,
             "clocks": clk.summary(),
-            "e2e": {"value": whole_job_rate(upd_per_step * e2e_steps, world, e2e_s), "unit": UNIT,
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8 * 8,
+            "e2e": {"value": (job_per_step * e2e_steps / e2e_s if shard
+                              else whole_job_rate(upd_per_step * e2e_steps, world, e2e_s)), "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8 * 8, "bytes_scope": "per rank",
                     "upload_gbs": upload_gbs,
                     "how": "per step: host orbitals (complex128, pinned) uploaded through tdks_set_orbitals, "
                            "one configured step, its record read back; step i+1's upload overlaps step i"},
@@ -606,10 +632,16 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="keep the default sweep tile shape (no autotuner)")
     ap.add_argument("--no-study", action="store_true", help="skip the propagator cost-against-error study")
     ap.add_argument("--shape", type=int, default=-1, help="force one sweep tile shape for all Taylor terms")
+    ap.add_argument("--shard", default="replicas", choices=["replicas", "states"],
+                    help="ranks run replicas of the molecule (default), or split one molecule's orbitals "
+                         "with a density allreduce per sub-step (strong scaling; also at --gpus 1)")
     ap.add_argument("--sweep-path", type=int, default=0,
                     help="stencil sweep variant: 0 warp-specialised TMA (default), 1 general, 2 lockstep TMA")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    # NCCL's own log lines (its version banner, when NCCL_DEBUG asks for it) go to stderr, so
+    # that rank 0's stdout holds the one JSON line
+    os.environ.setdefault("NCCL_DEBUG_FILE", "/dev/stderr")
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
