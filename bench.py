@@ -492,11 +492,11 @@ def run_periodic_side(args):
 
 
 def run_propagator_study(args):
-    """Cost against error of the two propagators (the comparison of the paper's EMR/CFM4
-    figure, on a synthetic molecule): a 48^3 molecule (h = 0.25, order 8, 16 orbitals in
-    complex128, 6 atoms with projectors, LDA exchange, laser E0 = 0.02, omega = 0.5) over
-    T = 1 (20 steps of dt = 0.05), with Taylor-4 at 4, 8, 16 and CFM4 at 2, 4, 8 sub-steps per
-    step; error = ||psi - psi_ref|| / ||psi_ref||, psi_ref from CFM4 at 64 sub-steps; time from
+    """Cost against error of the propagators (the comparison of the paper's EMR/CFM4 figure,
+    on a synthetic molecule): a 48^3 molecule (h = 0.25, order 8, 16 orbitals in complex128,
+    6 atoms with projectors, LDA exchange, laser E0 = 0.02, omega = 0.5) over T = 1 (20 steps
+    of dt = 0.05), with Taylor-4 and EMR (one exponential per sub-step) at 4, 8, 16 and AETRS
+    and CFM4 (two half exponentials) at 2, 4, 8 sub-steps per step; error = ||psi - psi_ref|| / ||psi_ref||, psi_ref from CFM4 at 64 sub-steps; time from
     CUDA events around each propagation."""
     import dataclasses as dc
     import torch
@@ -527,7 +527,8 @@ def run_propagator_study(args):
     ref, _ = run(1, 64)
     nref = np.linalg.norm(ref)
     pts = []
-    for prop, name, subs_list in ((0, "taylor4", (4, 8, 16)), (1, "cfm4", (2, 4, 8))):
+    for prop, name, subs_list in ((0, "taylor4", (4, 8, 16)), (2, "emr", (4, 8, 16)), (3, "aetrs", (2, 4, 8)),
+                                  (1, "cfm4", (2, 4, 8))):
         for subs in subs_list:
             psi, ms = run(prop, subs)
             pts.append({"propagator": name, "substeps": subs, "ms": round(ms, 2),

@@ -170,13 +170,22 @@ int tdks_propagate_n(tdks_sys sys, double t0, double dt, int n_steps, int subste
  * exponential of ds/2 of H with the field 2 (a2 E(t1) + a1 E(t2)) (first factor; a1 and
  * a2 swapped in the second) and the exchange potential extrapolated the same way to t1 and
  * t2 from its values at the starts of the last four sub-steps (Lagrange, order four; fewer
- * points while the history fills).  The history is cleared by tdks_set_orbitals and by
- * this call.  Length gauge or no field (TDKS_EINVAL with the velocity gauge at
- * propagation); the stability limit applies to ds/2.  Records as for Taylor-4.  Batches
- * propagate with Taylor-4.
+ * points while the history fills).  The paper also names the exponential midpoint rule and
+ * the enforced time-reversal symmetry scheme among the propagators in use (same section)
+ * without stating them; their usual forms, with the exchange potential extrapolated the
+ * same way (the explicit variant of the time-reversal scheme, "approximate ETRS"):
+ *   TDKS_PROP_EMR:   phi(t + ds) = exp(-i ds H[t + ds/2]) phi(t),
+ *   TDKS_PROP_AETRS: phi(t + ds) = exp(-i ds/2 H[t + ds]) exp(-i ds/2 H[t]) phi(t),
+ * where H[t] uses v_x of the current state exactly.  Each exponential is a Taylor-4 series.
+ * The history is cleared by tdks_set_orbitals and by this call.  Length gauge or no field
+ * (TDKS_EINVAL with the velocity gauge at propagation); the stability limit applies to each
+ * exponential's length (ds/2, or ds for EMR).  Records as for Taylor-4.  Batches propagate
+ * with Taylor-4.
  */
 #define TDKS_PROP_TAYLOR4 0
 #define TDKS_PROP_CFM4 1
+#define TDKS_PROP_EMR 2
+#define TDKS_PROP_AETRS 3
 int tdks_set_propagator(tdks_sys sys, int propagator);
 
 /*
@@ -198,8 +207,9 @@ int tdks_set_propagator(tdks_sys sys, int propagator);
  * record is then the whole system's.  fn returns 0 on success; any other value stops the
  * call with TDKS_EDEVICE.  fn runs on the calling thread, while earlier work may still run
  * on the stream.  Every rank holds the same k-points, grid, potentials, projectors and
- * field.  Taylor-4 only: TDKS_EINVAL from tdks_set_propagator(CFM4) while a hook is set and
- * from this call on a CFM4 system.  fn = NULL detaches the hook.  ctx is passed through
+ * field.  Taylor-4 only: TDKS_EINVAL from tdks_set_propagator with another propagator while
+ * a hook is set, and from this call on a system with another propagator.  fn = NULL detaches
+ * the hook.  ctx is passed through
  * untouched.
  */
 typedef int (*tdks_exchange_fn)(double *dev_buf, long long n, void *stream, void *ctx);

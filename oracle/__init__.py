@@ -66,6 +66,8 @@ def _load():
         _lib.oracle_propagate_cfm4.argtypes = [S, D, D, I, I, P, P]
         _lib.oracle_cfm4_weights.argtypes = [I, P, P]
         _lib.oracle_cfm4_constants.argtypes = [P, P]
+        _lib.oracle_propagate_emr.argtypes = [S, D, D, I, I, P, P]
+        _lib.oracle_propagate_aetrs.argtypes = [S, D, D, I, I, P, P]
     return _lib
 
 
@@ -171,6 +173,24 @@ class System:
         obs = np.empty((n_steps, 8)) if record else None
         self.lib.oracle_propagate_cfm4(self.ref, t0, dt, n_steps, substeps, _ptr(psi),
                                        _ptr(obs) if record else None)
+        return psi, obs
+
+    def propagate_emr(self, psi, t0, dt, n_steps, substeps, record=True):
+        """Exponential midpoint rule, v_x extrapolated to the sub-step midpoint; length gauge
+        or no field."""
+        psi = self._psi(psi).copy()
+        obs = np.empty((n_steps, 8)) if record else None
+        self.lib.oracle_propagate_emr(self.ref, t0, dt, n_steps, substeps, _ptr(psi),
+                                      _ptr(obs) if record else None)
+        return psi, obs
+
+    def propagate_aetrs(self, psi, t0, dt, n_steps, substeps, record=True):
+        """Approximate enforced time-reversal symmetry: half exponentials with H at t and at
+        t + ds (v_x extrapolated there); length gauge or no field."""
+        psi = self._psi(psi).copy()
+        obs = np.empty((n_steps, 8)) if record else None
+        self.lib.oracle_propagate_aetrs(self.ref, t0, dt, n_steps, substeps, _ptr(psi),
+                                        _ptr(obs) if record else None)
         return psi, obs
 
     def sphere_count(self, a: int) -> int:

@@ -603,3 +603,81 @@ void oracle_propagate_cfm4(const oracle_sys *s, double t0, double dt, int n_step
   for (int j = 0; j < 4; j++) free(hist[j]);
   free(n); free(vf); free(vs);
 }
+
+/* --------------------------------------------------------------------------------
+ * Exponential midpoint rule and approximate enforced time-reversal symmetry.  The paper
+ * lists both among the propagators in use (Sec. "New propagators for real-time TDDFT"; the
+ * time-reversal scheme also in the hydrogen-fluoride dimer run of Sec. "vdW-TS" and in the
+ * first GPU port of Sec. "GPUs") without writing them out.  Their usual forms, per sub-step ds:
+ *   EMR:   phi(t + ds) = exp(-i ds H[t + ds/2]) phi(t)
+ *   AETRS: phi(t + ds) = exp(-i ds/2 H[t + ds]) exp(-i ds/2 H[t]) phi(t)
+ * with H[t] = H0 + v_x(t) + E(t).r.  v_x(t) is that of the current state; v_x at t + ds/2
+ * and t + ds is not known, and, as for CFM4, it is extrapolated from the values at the
+ * starts of the last nh <= 4 sub-steps (Lagrange, offsets 0, -1, .., -(nh-1)).  Each
+ * exponential is the Taylor-4 series.  Records and history as oracle_propagate_cfm4.
+ * ------------------------------------------------------------------------------ */
+
+/* Push v_x of psi into the history (hist[0] the newest) and return the new count. */
+static int push_vx(const oracle_sys *s, const cplx *psi, double **hist, int nh, double *n) {
+  double *oldest = hist[3];
+  for (int q = 3; q > 0; q--) hist[q] = hist[q - 1];
+  hist[0] = oldest;
+  oracle_density(s, psi, n);
+  oracle_lda_x(s, n, hist[0]);
+  return nh < 4 ? nh + 1 : 4;
+}
+
+/* v(p) = sum_j L_j(x) hist[j][p]: the history extrapolated to offset x (in sub-steps). */
+static void extrapolate_vx(const oracle_sys *s, double **hist, int nh, double x, double *v) {
+  double L[4];
+  lagrange_weights(nh, x, L);
+  for (long p = 0; p < npts(s); p++) {
+    double acc = 0.0;
+    for (int j = 0; j < nh; j++) acc += L[j] * hist[j][p];
+    v[p] = acc;
+  }
+}
+
+static void propagate_two_point(const oracle_sys *s, int aetrs, double t0, double dt, int n_steps, int substeps,
+                                cplx *psi, double *obs) {
+  if (s->gauge == 2) return;  /* the field must enter H linearly */
+  const long N = npts(s);
+  const double ds = dt / (double)substeps;
+  double *hist[4];
+  int nh = 0;
+  double *n = (double *)malloc(sizeof(double) * (size_t)N);
+  double *v = (double *)malloc(sizeof(double) * (size_t)N);
+  for (int j = 0; j < 4; j++) hist[j] = (double *)malloc(sizeof(double) * (size_t)N);
+  for (int st = 0; st < n_steps; st++) {
+    double t = t0 + (double)st * dt;
+    if (obs) oracle_observables(s, t, t + 0.5 * ds, psi, obs + 8 * st);
+    for (int j = 0; j < substeps; j++) {
+      const double tj = t + (double)j * ds;
+      double E[3], A[3];
+      if (s->xc == 1) nh = push_vx(s, psi, hist, nh, n);
+      if (!aetrs) {
+        if (s->xc == 1) extrapolate_vx(s, hist, nh, 0.5, v);
+        oracle_field(s, tj + 0.5 * ds, E, A);
+        taylor_exp_field(s, E, s->xc == 1 ? v : NULL, ds, psi);
+      } else {
+        oracle_field(s, tj, E, A);
+        taylor_exp_field(s, E, s->xc == 1 ? hist[0] : NULL, 0.5 * ds, psi);
+        if (s->xc == 1) extrapolate_vx(s, hist, nh, 1.0, v);
+        oracle_field(s, tj + ds, E, A);
+        taylor_exp_field(s, E, s->xc == 1 ? v : NULL, 0.5 * ds, psi);
+      }
+    }
+  }
+  for (int j = 0; j < 4; j++) free(hist[j]);
+  free(n); free(v);
+}
+
+void oracle_propagate_emr(const oracle_sys *s, double t0, double dt, int n_steps, int substeps, cplx *psi,
+                          double *obs) {
+  propagate_two_point(s, 0, t0, dt, n_steps, substeps, psi, obs);
+}
+
+void oracle_propagate_aetrs(const oracle_sys *s, double t0, double dt, int n_steps, int substeps, cplx *psi,
+                            double *obs) {
+  propagate_two_point(s, 1, t0, dt, n_steps, substeps, psi, obs);
+}

@@ -970,21 +970,62 @@ static void cfm4_constants(double a[2], double theta[2]) {
   theta[1] = 0.5 + r3 / 6.0;
 }
 
-// Extrapolation of the exchange history (values at offsets 0, -1, .., -(nh-1) sub-steps)
-// to the Gauss points, folded with the a's: weights of the first (wf) and second (ws)
-// exponential's effective potential.
-static void cfm4_history_weights(int nh, double wf[4], double ws[4]) {
-  double a[2], th[2];
-  cfm4_constants(a, th);
+// One exponential factor of a sub-step ds of an exponential propagator: exp(-i tau H_eff)
+// with tau = frac * ds and H_eff = H0 + v_eff + E_eff.r, where
+//   E_eff = sum_i c[i] E(t + th[i] ds),  v_eff = sum_i c[i] v_x(t + th[i] ds),
+// v_x at t + th ds extrapolated from its values at the starts of the last sub-steps.
+struct ExpFactor {
+  double frac;
+  int n;
+  double th[2], c[2];
+};
+struct ExpScheme {
+  int n_exp;
+  ExpFactor f[2];
+  const char *name;
+};
+
+// CFM4: exp(-i ds (a1 H[t1] + a2 H[t2])) exp(-i ds (a2 H[t1] + a1 H[t2])), a1 + a2 = 1/2, so
+// each factor is an exponential of ds/2 of 2 (a H[t1] + a' H[t2]).  EMR: exp(-i ds H[t + ds/2]).
+// AETRS: exp(-i ds/2 H[t + ds]) exp(-i ds/2 H[t]).  (Factors listed in the order applied.)
+static ExpScheme exp_scheme(int prop) {
+  ExpScheme e{};
+  if (prop == TDKS_PROP_CFM4) {
+    double a[2], th[2];
+    cfm4_constants(a, th);
+    e.n_exp = 2;
+    e.f[0] = ExpFactor{0.5, 2, {th[0], th[1]}, {2.0 * a[1], 2.0 * a[0]}};
+    e.f[1] = ExpFactor{0.5, 2, {th[0], th[1]}, {2.0 * a[0], 2.0 * a[1]}};
+    e.name = "CFM4";
+  } else if (prop == TDKS_PROP_EMR) {
+    e.n_exp = 1;
+    e.f[0] = ExpFactor{1.0, 1, {0.5, 0.0}, {1.0, 0.0}};
+    e.name = "EMR";
+  } else {
+    e.n_exp = 2;
+    e.f[0] = ExpFactor{0.5, 1, {0.0, 0.0}, {1.0, 0.0}};
+    e.f[1] = ExpFactor{0.5, 1, {1.0, 0.0}, {1.0, 0.0}};
+    e.name = "AETRS";
+  }
+  return e;
+}
+
+// Weights of the exchange history (v_x at offsets 0, -1, .., -(nh-1) sub-steps, [0] the
+// newest) in a factor's v_eff: sum_i c[i] times the Lagrange basis polynomials through the
+// nh offsets, evaluated at th[i].
+static void factor_history_weights(const ExpFactor &f, int nh, double w[4]) {
+  for (int j = 0; j < 4; j++) w[j] = 0.0;
   for (int j = 0; j < nh; j++) {
-    double l1 = 1.0, l2 = 1.0;  // Lagrange basis polynomial j at theta_1, theta_2
-    for (int i = 0; i < nh; i++) {
-      if (i == j) continue;
-      l1 *= (th[0] + i) / (double)(i - j);
-      l2 *= (th[1] + i) / (double)(i - j);
+    double acc = 0.0;
+    for (int q = 0; q < f.n; q++) {
+      double l = 1.0;
+      for (int i = 0; i < nh; i++) {
+        if (i == j) continue;
+        l *= (f.th[q] + i) / (double)(i - j);
+      }
+      acc += f.c[q] * l;
     }
-    wf[j] = 2.0 * (a[1] * l1 + a[0] * l2);
-    ws[j] = 2.0 * (a[0] * l1 + a[1] * l2);
+    w[j] = acc;
   }
 }
 
@@ -1031,18 +1072,23 @@ static int run_cfm_veff(tdks_system *s, bool push, const double w[4], const doub
   return TDKS_OK;
 }
 
-// CFM4 steps (see tdks_set_propagator).
-static int propagate_cfm4(tdks_system *s, double t0, double dt, int n_steps, int substeps) {
+// Steps of an exponential propagator other than Taylor-4 (CFM4, EMR, AETRS; see
+// tdks_set_propagator): per sub-step, v_x of the current state is pushed into the history,
+// then each factor sets its effective potential and applies a Taylor-4 exponential.
+static int propagate_exp(tdks_system *s, double t0, double dt, int n_steps, int substeps) {
+  const ExpScheme sc = exp_scheme(s->prop);
   if (s->gauge == TDKS_GAUGE_VELOCITY)
-    return fail(TDKS_EINVAL, "CFM4 needs a field that enters H linearly (length gauge or no field)");
+    return fail(TDKS_EINVAL, std::string(sc.name) + " needs a field that enters H linearly (length gauge or no field)");
   const double ds = dt / substeps;
-  if (std::fabs(0.5 * ds) * kinetic_max(s) > 2.0 * std::sqrt(2.0))
-    return fail(TDKS_EUNSTABLE, "CFM4 half sub-step beyond the Taylor-4 stability limit (dt_sub/2 * K_max > 2 sqrt 2)");
+  double fmax = 0.0;
+  for (int f = 0; f < sc.n_exp; f++) fmax = std::max(fmax, sc.f[f].frac);
+  if (std::fabs(fmax * ds) * kinetic_max(s) > 2.0 * std::sqrt(2.0))
+    return fail(TDKS_EUNSTABLE, std::string(sc.name) +
+                                    " exponential beyond the Taylor-4 stability limit (tau * K_max > 2 sqrt 2)");
   int rc = ensure_density(s);
   if (rc) return rc;
-  double a[2], th[2];
-  cfm4_constants(a, th);
   const double A0[3] = {0.0, 0.0, 0.0};
+  const bool xc = s->xc == TDKS_XC_LDA_X;
   for (int st = 0; st < n_steps; st++) {
     const double t = t0 + st * dt;
     for (int j = 0; j < substeps; j++) {
@@ -1056,28 +1102,26 @@ static int propagate_cfm4(tdks_system *s, double t0, double dt, int n_steps, int
         double *slot = s->ring + (s->steps % tdks_system::RING) * TDKS_RECORD;
         if ((rc = run_finalize(s, slot, t, E, A))) return rc;
       }
-      double E1[3], E2[3], Af[3], Ef[3], Es[3];
-      field_at(s, tj + th[0] * ds, E1, Af);
-      field_at(s, tj + th[1] * ds, E2, Af);
-      for (int ax = 0; ax < 3; ax++) {
-        Ef[ax] = 2.0 * (a[1] * E1[ax] + a[0] * E2[ax]);
-        Es[ax] = 2.0 * (a[0] * E1[ax] + a[1] * E2[ax]);
-      }
-      const bool xc = s->xc == TDKS_XC_LDA_X;
       if (xc) {  // the oldest history slot becomes the newest
         double *oldest = s->vx_hist[3];
         for (int q = 3; q > 0; q--) s->vx_hist[q] = s->vx_hist[q - 1];
         s->vx_hist[0] = oldest;
         s->n_hist = std::min(s->n_hist + 1, 4);
       }
-      double wf[4] = {0, 0, 0, 0}, ws[4] = {0, 0, 0, 0};
-      if (xc) cfm4_history_weights(s->n_hist, wf, ws);
-      if ((rc = run_cfm_veff(s, xc, wf, Ef))) return rc;
-      if ((rc = first_sweep(s, 0.0, -0.5 * ds, A0, false))) return rc;
-      if ((rc = taylor_tail(s, 0.5 * ds, A0))) return rc;
-      if ((rc = run_cfm_veff(s, false, ws, Es))) return rc;
-      if ((rc = first_sweep(s, 0.0, -0.5 * ds, A0, false))) return rc;
-      if ((rc = taylor_tail(s, 0.5 * ds, A0))) return rc;
+      for (int f = 0; f < sc.n_exp; f++) {
+        const ExpFactor &fa = sc.f[f];
+        double Ef[3] = {0.0, 0.0, 0.0}, w[4] = {0, 0, 0, 0};
+        for (int q = 0; q < fa.n; q++) {
+          double Eq[3], Aq[3];
+          field_at(s, tj + fa.th[q] * ds, Eq, Aq);
+          for (int ax = 0; ax < 3; ax++) Ef[ax] += fa.c[q] * Eq[ax];
+        }
+        if (xc) factor_history_weights(fa, s->n_hist, w);
+        if ((rc = run_cfm_veff(s, xc && f == 0, w, Ef))) return rc;
+        const double tau = fa.frac * ds;
+        if ((rc = first_sweep(s, 0.0, -tau, A0, false))) return rc;
+        if ((rc = taylor_tail(s, tau, A0))) return rc;
+      }
       s->dens_valid = true;  // the last sweep wrote the density of the new state
     }
     s->steps++;
@@ -1090,12 +1134,12 @@ static int propagate_cfm4(tdks_system *s, double t0, double dt, int n_steps, int
 
 int tdks_set_propagator(tdks_sys s, int propagator) {
   if (!s) return fail(TDKS_EINVAL, "NULL system");
-  if (propagator != TDKS_PROP_TAYLOR4 && propagator != TDKS_PROP_CFM4)
-    return fail(TDKS_EINVAL, "propagator must be TDKS_PROP_TAYLOR4 or TDKS_PROP_CFM4");
-  if (propagator == TDKS_PROP_CFM4 && s->xfn)
+  if (propagator < TDKS_PROP_TAYLOR4 || propagator > TDKS_PROP_AETRS)
+    return fail(TDKS_EINVAL, "propagator must be TDKS_PROP_TAYLOR4, _CFM4, _EMR or _AETRS");
+  if (propagator != TDKS_PROP_TAYLOR4 && s->xfn)
     return fail(TDKS_EINVAL, "state-parallel propagation (tdks_set_exchange) is Taylor-4 only");
   CU(cudaStreamSynchronize(s->stream));
-  if (propagator == TDKS_PROP_CFM4 && !s->vx_hist[0])
+  if (propagator != TDKS_PROP_TAYLOR4 && !s->vx_hist[0])
     for (int j = 0; j < 4; j++) CU(cudaMalloc((void **)&s->vx_hist[j], (size_t)s->N * sizeof(double)));
   s->prop = propagator;
   s->n_hist = 0;
@@ -1120,7 +1164,7 @@ int tdks_propagate_n(tdks_sys s, double t0, double dt, int n_steps, int substeps
   if (n_steps < 0 || substeps < 0) return fail(TDKS_EINVAL, "negative count");
   if (!s->have_orbitals) return fail(TDKS_ESTATE, "orbitals not set");
   if (substeps == 0) tdks_auto_substeps(s, dt, &substeps);
-  if (s->prop == TDKS_PROP_CFM4) return propagate_cfm4(s, t0, dt, n_steps, substeps);
+  if (s->prop != TDKS_PROP_TAYLOR4) return propagate_exp(s, t0, dt, n_steps, substeps);
   const double dts = dt / substeps;
   if (std::fabs(dts) * kinetic_max(s) > 2.0 * std::sqrt(2.0))
     return fail(TDKS_EUNSTABLE, "sub-step beyond the Taylor-4 stability limit (dt_sub * K_max > 2 sqrt 2)");

@@ -153,7 +153,8 @@ class System:
         self._xcheck(self.lib.tdks_apply_H(self.h, t, ctypes.c_void_p(dev_in), ctypes.c_void_p(dev_out)))
 
     def set_propagator(self, propagator: int):
-        """0: Taylor-4 (default); 1: CFM4 (two exponentials per sub-step)."""
+        """0: Taylor-4 (default); 1: CFM4 (two exponentials per sub-step); 2: exponential
+        midpoint rule; 3: approximate enforced time-reversal symmetry (two half exponentials)."""
         _lib.check(self.lib.tdks_set_propagator(self.h, propagator))
 
     def set_exchange(self, fn):

@@ -268,14 +268,42 @@ def test_cfm4_matches_oracle(case):
     assert _rec_err(rec, rec_o) < tol
 
 
+@pytest.mark.parametrize("prop", ["emr", "aetrs"])
+@pytest.mark.parametrize("case", ["tiny_c128", "ragged_c128", "tiny_c64"])
+def test_emr_and_aetrs_match_oracle(prop, case):
+    """EMR (one Taylor-4 exponential per sub-step, v_x extrapolated to the midpoint) and AETRS
+    (exponentials of dt/2 with H at t, then at t + dt with v_x extrapolated there) on the GPU
+    against the oracle's, as for CFM4."""
+    if case == "ragged_c128":
+        spec = ragged_molecule(I.PREC_C128)
+        n_steps, subs, dt = 4, 2, 0.03
+    else:
+        spec = I.tiny_molecule(prec=I.PREC_C128 if case == "tiny_c128" else I.PREC_C64)
+        n_steps, subs, dt = 12, 1, spec.dt
+    inp = I.make_inputs(spec)
+    sysm = _system(spec, inp)
+    sysm.set_propagator({"emr": 2, "aetrs": 3}[prop])
+    sysm.propagate(0.0, dt, n_steps, subs)
+    psi, rec = sysm.get_orbitals(), sysm.reductions(0, n_steps)
+    sysm.close()
+    o = oracle.System(spec, inp)
+    psi_o, rec_o = getattr(o, "propagate_" + prop)(inp.psi0, 0.0, dt, n_steps, subs)
+    tol = 1e-12 if spec.prec == I.PREC_C128 else 2e-5
+    assert rel_err(psi, psi_o) < tol
+    assert _rec_err(rec, rec_o) < tol
+
+
 def test_cfm4_refuses_the_velocity_gauge_and_batches():
     from paper_1912_07921_gb300 import _lib
     from paper_1912_07921_gb300.system import Batch
     spec = bloch_cell(I.PREC_C64)
     sysm = _system(spec, bloch_inputs(spec))
-    sysm.set_propagator(1)
+    for prop in (1, 2, 3):
+        sysm.set_propagator(prop)
+        with pytest.raises(_lib.TdksError):
+            sysm.propagate(0.0, 0.01, 1, 1)
     with pytest.raises(_lib.TdksError):
-        sysm.propagate(0.0, 0.01, 1, 1)
+        sysm.set_propagator(4)
     sysm.close()
     spec = I.tiny_molecule(prec=I.PREC_C64)
     a = _system(spec, I.make_inputs(spec))

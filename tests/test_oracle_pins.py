@@ -601,3 +601,51 @@ def test_cfm4_with_exchange_converges_faster_than_taylor():
         assert a / b > 6.0
     for a, b in zip(et, et[1:]):
         assert 1.7 < a / b < 2.3
+
+
+# ---------------------------------------------------------------------------------------
+# Exponential midpoint rule and approximate enforced time-reversal symmetry (named among the
+# propagators in use, Sec. "New propagators for real-time TDDFT"; forms as the oracle states)
+# ---------------------------------------------------------------------------------------
+def test_emr_and_aetrs_reduce_to_taylor_steps_without_exchange():
+    """H time-independent (no field, no exchange): an EMR step is one Taylor-4 step of dt and
+    an AETRS step two of dt/2.  With the field but no exchange, EMR is the Taylor-4 step with
+    the field at the midpoint: the plain propagator."""
+    spec, inp, o = _cfm_case(0)
+    o0 = oracle.System(spec, inp, xc=0, gauge=I.GAUGE_NONE)
+    e, obs_e = o0.propagate_emr(inp.psi0, 0.0, 0.04, 5, 1)
+    t1, obs_t1 = o0.propagate(inp.psi0, 0.0, 0.04, 5, 1)
+    a, obs_a = o0.propagate_aetrs(inp.psi0, 0.0, 0.04, 5, 1)
+    t2, obs_t2 = o0.propagate(inp.psi0, 0.0, 0.04, 5, 2)
+    assert np.max(np.abs(e - t1)) < 1e-14 and np.max(np.abs(a - t2)) < 1e-14
+    np.testing.assert_allclose(obs_e, obs_t1, rtol=1e-13, atol=1e-14)
+    np.testing.assert_allclose(obs_a, obs_t2, rtol=1e-13, atol=1e-14)
+    ef, _ = o.propagate_emr(inp.psi0, 0.0, 0.04, 5, 1)
+    tf, _ = o.propagate(inp.psi0, 0.0, 0.04, 5, 1)
+    assert np.max(np.abs(ef - tf)) < 1e-14
+    af, _ = o.propagate_aetrs(inp.psi0, 0.0, 0.04, 5, 1)
+    assert np.max(np.abs(af - tf)) > 1e-6  # the field enters at t and t + dt instead
+
+
+def _orders(o, inp, fn, T, ns):
+    ref, _ = o.propagate_cfm4(inp.psi0, 0.0, T / 256, 256, 1, record=False)
+    e = [np.linalg.norm(fn(inp.psi0, 0.0, T / n, n, 1, record=False)[0] - ref) for n in ns]
+    return [a / b for a, b in zip(e, e[1:])]
+
+
+def test_aetrs_is_second_order_for_a_driven_linear_problem():
+    """Fast laser, no exchange: halving dt divides the AETRS error by 4 (order two of the
+    trapezoid-like split); reference: CFM4 at dt/32."""
+    spec, inp, o = _cfm_case(0)
+    for r in _orders(o, inp, o.propagate_aetrs, 0.64, (8, 16, 32)):
+        assert 3.5 < r < 4.6, r
+
+
+@pytest.mark.parametrize("name", ["emr", "aetrs"])
+def test_emr_and_aetrs_with_exchange_are_second_order(name):
+    """With LDA exchange, v_x at t + dt/2 (EMR) or t + dt (AETRS) comes from the extrapolated
+    history: both stay order two (error ratio ~4 per halving), where Taylor-4 with the density
+    frozen over the step is order one (ratio ~2)."""
+    spec, inp, o = _cfm_case(1)
+    for r in _orders(o, inp, getattr(o, "propagate_" + name), 0.64, (16, 32, 64)):
+        assert 3.4 < r < 4.8, (name, r)
