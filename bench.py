@@ -209,7 +209,6 @@ def run_ours(args, rank, world, local_rank):
         o_lo, o_hi = 0, spec.n_orb
     if args.sweep_path:
         sysm.set_sweep_path(args.sweep_path)
-    sysm.set_upload_streams(args.upload_streams)
     tune = None
     if args.shape >= 0:
         sysm.set_sweep_shape(-1, args.shape)
@@ -321,7 +320,7 @@ def run_ours(args, rank, world, local_rank):
             "e2e": {"value": (job_per_step * e2e_steps / e2e_s if shard
                               else whole_job_rate(upd_per_step * e2e_steps, world, e2e_s)), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8 * 8, "bytes_scope": "per rank",
-                    "upload_gbs": upload_gbs, "upload_streams": args.upload_streams,
+                    "upload_gbs": upload_gbs,
                     "how": "per step: host orbitals (complex128, pinned) uploaded through tdks_set_orbitals, "
                            "one configured step, its record read back; step i+1's upload overlaps step i"},
             "last_record": {"t": rec[0], "norm": rec[1], "energy": rec[2], "dipole": list(rec[4:7])},
@@ -637,8 +636,6 @@ def main():
     ap.add_argument("--shard", default="replicas", choices=["replicas", "states"],
                     help="ranks run replicas of the molecule (default), or split one molecule's orbitals "
                          "with a density allreduce per sub-step (strong scaling; also at --gpus 1)")
-    ap.add_argument("--upload-streams", type=int, default=4,
-                    help="copy streams of an orbital upload (1..4) in the end-to-end steps")
     ap.add_argument("--sweep-path", type=int, default=0,
                     help="stencil sweep variant: 0 warp-specialised TMA (default), 1 general, 2 lockstep TMA")
     args = ap.parse_args()

@@ -104,11 +104,6 @@ int tdks_set_local_potential(tdks_sys sys, const double *v);
  * upload's packing, so an upload issued while a propagation runs overlaps it. */
 int tdks_set_orbitals(tdks_sys sys, const double *psi);
 
-/* Copy streams over which tdks_set_orbitals spreads its chunks, round-robin (1..4; default
- * 4): the driver may serve each with its own copy engine, which raises the host-to-device
- * rate of one upload.  Takes effect at the next upload. */
-int tdks_set_upload_streams(tdks_sys sys, int n);
-
 /* Copy the current orbitals out into the host layout.  Synchronises. */
 int tdks_get_orbitals(tdks_sys sys, double *psi_out);
 

@@ -573,8 +573,7 @@ int tdks_destroy(tdks_sys s) {
   cudaFree(s->n_total); cudaFree(s->fin_sum);
   cudaFree(s->obs_rec); cudaFree(s->d_kvec); cudaFree(s->d_wocc);
   cudaFree(s->staging);
-  for (auto cs : s->copy_stream)
-    if (cs) cudaStreamDestroy(cs);
+  if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
   if (s->ev_staging_free) cudaEventDestroy(s->ev_staging_free);
   for (auto e : s->ev_chunk) cudaEventDestroy(e);
   for (auto &u : s->ev_used) { cudaEventDestroy(u.second.first); cudaEventDestroy(u.second.second); }
@@ -610,11 +609,10 @@ int tdks_set_orbitals(tdks_sys s, const double *psi) {
   if (rc) return rc;
   const int per_k = std::max(1, (UPLOAD_CHUNKS + s->n_k - 1) / s->n_k);
   const int n_chunks = per_k * s->n_k;
-  if (!s->copy_stream[0]) {
-    for (auto &cs : s->copy_stream) CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  if (!s->copy_stream) {
+    CU(cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking));
     CU(cudaEventCreateWithFlags(&s->ev_staging_free, cudaEventDisableTiming));
   }
-  const int ncs = std::max(1, std::min(s->n_copy_streams, (int)tdks_system::COPY_STREAMS));
   while ((int)s->ev_chunk.size() < n_chunks) {
     cudaEvent_t e;
     CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -624,17 +622,16 @@ int tdks_set_orbitals(tdks_sys s, const double *psi) {
   // upload's packing) are done; they do not wait for other work of the system, so an upload
   // issued right after tdks_propagate_n overlaps that propagation (the packing, which writes
   // the state, still runs after it on the system's stream)
-  if (s->staging_pending)
-    for (int q = 0; q < ncs; q++) CU(cudaStreamWaitEvent(s->copy_stream[q], s->ev_staging_free, 0));
+  if (s->staging_pending) CU(cudaStreamWaitEvent(s->copy_stream, s->ev_staging_free, 0));
   const long len = (s->N + per_k - 1) / per_k;
   int c = 0;
   for (int k = 0; k < s->n_k; k++)
     for (long pt0 = 0; pt0 < s->N; pt0 += len, c++) {
       const long npts = std::min(len, s->N - pt0);
       const size_t off = ((size_t)k * s->N + pt0) * s->n_orb * 2;  // doubles
-      cudaStream_t cs = s->copy_stream[c % ncs];
-      CU(cudaMemcpyAsync(s->staging + off, psi + off, (size_t)npts * s->n_orb * 16, cudaMemcpyHostToDevice, cs));
-      CU(cudaEventRecord(s->ev_chunk[c], cs));
+      CU(cudaMemcpyAsync(s->staging + off, psi + off, (size_t)npts * s->n_orb * 16, cudaMemcpyHostToDevice,
+                         s->copy_stream));
+      CU(cudaEventRecord(s->ev_chunk[c], s->copy_stream));
       CU(cudaStreamWaitEvent(s->stream, s->ev_chunk[c], 0));
       CU(launch_pack_in(s->prec, s->N, k, pt0, npts, s->n_orb, s->n_batches, s->staging, s->psi, s->psi_lo,
                         s->d_wocc, s->dens_part, s->stream));
@@ -643,7 +640,7 @@ int tdks_set_orbitals(tdks_sys s, const double *psi) {
   CU(cudaEventRecord(s->ev_staging_free, s->stream));
   s->staging_pending = true;
   // the host buffer has been read once the copies are done ("copied")
-  for (int q = 0; q < ncs; q++) CU(cudaStreamSynchronize(s->copy_stream[q]));
+  CU(cudaStreamSynchronize(s->copy_stream));
   s->have_orbitals = true;
   s->dens_valid = true;
   s->n_hist = 0;  // a new state starts a new CFM4 exchange history
@@ -827,14 +824,6 @@ int tdks_set_tile(tdks_sys s, int tx, int ty, int zc) {
   CU(cudaStreamSynchronize(s->stream));
   s->tx = tx; s->ty = ty; s->zc = zc;
   build_tmaps(s);
-  return TDKS_OK;
-}
-
-int tdks_set_upload_streams(tdks_sys s, int n) {
-  if (!s) return fail(TDKS_EINVAL, "NULL system");
-  if (n < 1 || n > tdks_system::COPY_STREAMS)
-    return fail(TDKS_EINVAL, "upload streams must be 1.." + std::to_string(tdks_system::COPY_STREAMS));
-  s->n_copy_streams = n;
   return TDKS_OK;
 }
 

@@ -65,11 +65,7 @@ struct tdks_system {
   double2 *d_qpart = nullptr;   // gather partial sums, gchunks per (atom, k-batch)
   int gchunks = 1;
   double *staging = nullptr;
-  // host uploads, chunked so that packing overlaps them; the chunks go round-robin over
-  // several copy streams, which the driver may serve with separate copy engines
-  static constexpr int COPY_STREAMS = 4;
-  cudaStream_t copy_stream[COPY_STREAMS] = {nullptr, nullptr, nullptr, nullptr};
-  int n_copy_streams = COPY_STREAMS;
+  cudaStream_t copy_stream = nullptr;  // host uploads, chunked so that packing overlaps them
   cudaEvent_t ev_staging_free = nullptr;  // recorded after the last kernel that reads the staging buffer
   bool staging_pending = false;            // ev_staging_free has been recorded
   std::vector<cudaEvent_t> ev_chunk;

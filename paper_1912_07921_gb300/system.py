@@ -90,10 +90,6 @@ class System:
         """Orbitals from a host buffer (e.g. pinned memory) in the host layout."""
         _lib.check(self.lib.tdks_set_orbitals(self.h, ctypes.c_void_p(host_ptr)))
 
-    def set_upload_streams(self, n: int):
-        """Copy streams (1..4) over which an orbital upload spreads its chunks."""
-        _lib.check(self.lib.tdks_set_upload_streams(self.h, n))
-
     def set_tile(self, tx, ty, zc=0):
         _lib.check(self.lib.tdks_set_tile(self.h, tx, ty, zc))
 
