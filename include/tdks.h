@@ -215,6 +215,23 @@ int tdks_set_propagator(tdks_sys sys, int propagator);
 typedef int (*tdks_exchange_fn)(double *dev_buf, long long n, void *stream, void *ctx);
 int tdks_set_exchange(tdks_sys sys, tdks_exchange_fn fn, void *ctx);
 
+/*
+ * Checkpoint and resume.  tdks_save writes everything a propagation continues from: grid,
+ * precision, k-points, potential, projectors, field, exchange settings, propagator (with its
+ * exchange history), tile and sweep-shape choices, the device state exactly as stored (the
+ * hi and lo parts of a complex64 state), the density of that state, the step count, the
+ * clock of tdks_set_clock and the stored records (the last min(steps, 65536)).  It waits for
+ * the system's stream, writes `path` + ".tmp" and renames it to `path` once complete (an
+ * existing file is replaced only by a whole checkpoint).  The exchange hook is not saved.
+ * tdks_load creates a new system on `stream` (a cudaStream_t, or NULL) from such a file; it
+ * continues bit for bit as the saved system would have, with the same records and step
+ * count.  TDKS_EINVAL for a file that cannot be opened or written, is not a checkpoint, is
+ * truncated, or fails its checksum; the other codes as for the calls that set each part.
+ * The file is little-endian and holds doubles as stored in memory.
+ */
+int tdks_save(tdks_sys sys, const char *path);
+int tdks_load(const char *path, void *stream, tdks_sys *out);
+
 /* Sub-step count the automatic policy of tdks_propagate_n picks for step dt. */
 int tdks_auto_substeps(tdks_sys sys, double dt, int *substeps);
 

@@ -29,6 +29,8 @@ SIGNATURES = {
     "tdks_propagate_n": ([P, D, D, I, I], I),
     "tdks_set_propagator": ([P, I], I),
     "tdks_set_exchange": ([P, P, P], I),
+    "tdks_save": ([P, ctypes.c_char_p], I),
+    "tdks_load": ([ctypes.c_char_p, P, ctypes.POINTER(P)], I),
     "tdks_auto_substeps": ([P, D, PI], I),
     "tdks_reductions": ([P, LL, I, P], I),
     "tdks_step_count": ([P, PLL], I),

@@ -773,6 +773,8 @@ int tdks_set_atoms_projectors(tdks_sys s, int n_atoms, const double *pos, const 
   s->n_atoms = n_atoms;
   s->pos.assign(pos, pos + 3 * n_atoms);
   s->D.assign(D, D + 4 * n_atoms);
+  s->r_c = r_c;
+  s->r_cut = r_cut;
   s->vnl_bound = vnl;
   return TDKS_OK;
 }

@@ -39,6 +39,7 @@ struct tdks_system {
   double pol[3] = {0, 0, 1}, amp = 0, omega = 0, t_total = 0;
   int n_atoms = 0;
   std::vector<double> pos, D;
+  double r_c = 0.0, r_cut = 0.0;  // projector width and support radius (tdks_set_atoms_projectors)
   double vloc_absmax = 0.0, vnl_bound = 0.0;
   // device buffers
   void *psi = nullptr;          // packed state: complex128, or the hi part (complex64) of a

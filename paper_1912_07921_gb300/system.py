@@ -6,6 +6,7 @@ propagation runs in the library's kernels.
 from __future__ import annotations
 
 import ctypes
+import os
 from typing import Optional
 
 import numpy as np
@@ -236,6 +237,34 @@ class System:
         t, n = ctypes.c_double(), ctypes.c_longlong()
         _lib.check(self.lib.tdks_get_clock(self.h, ctypes.byref(t), ctypes.byref(n)))
         return t.value, n.value
+
+    # -- checkpoint / resume ----------------------------------------------------------
+    def save(self, path: str):
+        """Write a checkpoint (tdks_save): the loaded system continues bit for bit."""
+        _lib.check(self.lib.tdks_save(self.h, os.fsencode(path)))
+
+    @classmethod
+    def load(cls, path: str, stream: Optional[int] = None) -> "System":
+        """A system restored from a checkpoint of tdks_save (tdks_load), on `stream`.  The
+        spec reflects the file's grid, precision and counts (header fields 0..7 and 11 are
+        nx, ny, nz, FD order, bc, precision, orbitals, k-points and atoms; double 0 is h)."""
+        with open(path, "rb") as f:
+            head = f.read(8 + 32 * 8 + 16 * 8)
+        if len(head) < 8 + 32 * 8 + 16 * 8:
+            raise _lib.TdksError(1, f"{path}: not a checkpoint file")
+        ints = np.frombuffer(head, dtype="<i8", count=32, offset=8)
+        dbl = np.frombuffer(head, dtype="<f8", count=16, offset=8 + 32 * 8)
+        self = cls.__new__(cls)
+        self.lib = _lib.load()
+        h = ctypes.c_void_p()
+        _lib.check(self.lib.tdks_load(os.fsencode(path), ctypes.c_void_p(stream or 0), ctypes.byref(h)))
+        self.h = h
+        nx, ny, nz, order, bc, prec, n_orb, n_k = (int(v) for v in ints[:8])
+        self.spec = SystemSpec(nx=nx, ny=ny, nz=nz, h=float(dbl[0]), fd_order=order, bc=bc, prec=prec,
+                               n_orb=n_orb, n_k=n_k, n_atoms=int(ints[11]))
+        self.n_k = n_k
+        self.shape = (n_k, nz, ny, nx, n_orb)
+        return self
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:

@@ -41,3 +41,24 @@ def test_binding_fails_loudly_without_library(tmp_path):
             _lib.load(str(tmp_path / "missing.so"))
         finally:
             _lib._lib = old
+
+
+def test_checkpoint_load_rejects_bad_files_without_touching_the_device(tmp_path):
+    """tdks_load refuses a missing file, a file that is not a checkpoint and a truncated
+    header with TDKS_EINVAL before any CUDA call (so this runs without a GPU)."""
+    import ctypes
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1912_07921_gb300 import _lib
+    lib = _lib.load()
+    out = ctypes.c_void_p()
+    bad = tmp_path / "bad.ckpt"
+    bad.write_bytes(b"NOTACKPT" + bytes(400))
+    short = tmp_path / "short.ckpt"
+    short.write_bytes(b"TDKSCKP1" + bytes(40))
+    for path in (tmp_path / "missing.ckpt", bad, short):
+        assert lib.tdks_load(str(path).encode(), None, ctypes.byref(out)) == 1
+        assert out.value is None
+    assert lib.tdks_load(str(bad).encode(), None, ctypes.byref(out)) == 1
+    assert b"not a checkpoint" in lib.tdks_last_error()
+    assert lib.tdks_save(None, str(tmp_path / "x").encode()) == 1
