@@ -58,7 +58,7 @@ def test_resume_is_bit_identical_molecule(prec, tmp_path):
 def test_resume_keeps_the_exchange_history(prop, tmp_path):
     """CFM4, EMR and AETRS extrapolate v_x from the last sub-steps: the history is saved."""
     spec = ragged_molecule(I.PREC_C64)
-    _resume_case(spec, I.make_inputs(spec), tmp_path, prop=prop, n1=2, n2=3, subs=1)
+    _resume_case(spec, I.make_inputs(spec), tmp_path, prop=prop, n1=2, n2=3, subs=2)
 
 
 def test_resume_periodic_cell_with_chosen_shapes(tmp_path):
