@@ -73,7 +73,7 @@ def test_damaged_or_partial_checkpoints_are_refused(tmp_path):
     from paper_1912_07921_gb300.system import System
     spec = ragged_molecule(I.PREC_C128, n_orb=3)
     a = System(spec, I.make_inputs(spec), stream=_stream())
-    a.propagate(0.0, 0.03, 1, 1)
+    a.propagate(0.0, 0.03, 1, 2)
     path = tmp_path / "a.ckpt"
     a.save(str(path))
     data = bytearray(path.read_bytes())
@@ -104,7 +104,7 @@ def test_save_before_orbitals_then_resume(tmp_path):
     b = System.load(path, stream=_stream())
     for s in (a, b):
         s.set_orbitals(inp.psi0)
-        s.propagate(0.0, 0.03, 2, 1)
+        s.propagate(0.0, 0.03, 2, 2)
     assert np.array_equal(a.get_orbitals(), b.get_orbitals())
     a.close()
     b.close()
