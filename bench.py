@@ -495,8 +495,10 @@ def run_propagator_study(args):
     """Cost against error of the propagators (the comparison of the paper's EMR/CFM4 figure,
     on a synthetic molecule): a 48^3 molecule (h = 0.25, order 8, 16 orbitals in complex128,
     6 atoms with projectors, LDA exchange, laser E0 = 0.02, omega = 0.5) over T = 1 (20 steps
-    of dt = 0.05), with Taylor-4 and EMR (one exponential per sub-step) at 4, 8, 16 and AETRS
-    and CFM4 (two half exponentials) at 2, 4, 8 sub-steps per step; error = ||psi - psi_ref|| / ||psi_ref||, psi_ref from CFM4 at 64 sub-steps; time from
+    of dt = 0.05), with Taylor-4 and EMR (one exponential per sub-step) and RK4 (four stages)
+    at 4, 8, 16 and AETRS and CFM4 (two half exponentials) at 2, 4, 8 sub-steps per step;
+    error = ||psi - psi_ref|| / ||psi_ref||, psi_ref from RK4 at 64 sub-steps per step (the
+    density rebuilt at every stage, fourth order in the whole non-linear problem); time from
     CUDA events around each propagation."""
     import dataclasses as dc
     import torch

@@ -186,6 +186,15 @@ int tdks_propagate_n(tdks_sys sys, double t0, double dt, int n_steps, int subste
 #define TDKS_PROP_CFM4 1
 #define TDKS_PROP_EMR 2
 #define TDKS_PROP_AETRS 3
+/*
+ * TDKS_PROP_RK4: the classical fourth-order Runge-Kutta method (the same section's list of
+ * propagators names Runge-Kutta) on d phi/dt = -i H[n(phi), t] phi, with the density rebuilt at every
+ * stage from the stage vector and the field at the stage times t, t + ds/2, t + ds/2, t + ds;
+ * the slope weights 1/6, 1/3, 1/3, 1/6.  Fourth order also in the density coupling, at four
+ * H applications per sub-step: a reference integrator.  Complex128 systems only (TDKS_EINVAL
+ * for complex64); any gauge; its stability limit on the imaginary axis is the Taylor-4 one.
+ */
+#define TDKS_PROP_RK4 4
 int tdks_set_propagator(tdks_sys sys, int propagator);
 
 /*

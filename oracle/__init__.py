@@ -68,6 +68,7 @@ def _load():
         _lib.oracle_cfm4_constants.argtypes = [P, P]
         _lib.oracle_propagate_emr.argtypes = [S, D, D, I, I, P, P]
         _lib.oracle_propagate_aetrs.argtypes = [S, D, D, I, I, P, P]
+        _lib.oracle_propagate_rk4.argtypes = [S, D, D, I, I, P, P]
     return _lib
 
 
@@ -191,6 +192,14 @@ class System:
         obs = np.empty((n_steps, 8)) if record else None
         self.lib.oracle_propagate_aetrs(self.ref, t0, dt, n_steps, substeps, _ptr(psi),
                                         _ptr(obs) if record else None)
+        return psi, obs
+
+    def propagate_rk4(self, psi, t0, dt, n_steps, substeps, record=True):
+        """Classical Runge-Kutta 4 with the density rebuilt at every stage; any gauge."""
+        psi = self._psi(psi).copy()
+        obs = np.empty((n_steps, 8)) if record else None
+        self.lib.oracle_propagate_rk4(self.ref, t0, dt, n_steps, substeps, _ptr(psi),
+                                      _ptr(obs) if record else None)
         return psi, obs
 
     def sphere_count(self, a: int) -> int:

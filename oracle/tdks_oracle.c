@@ -681,3 +681,61 @@ void oracle_propagate_aetrs(const oracle_sys *s, double t0, double dt, int n_ste
                             double *obs) {
   propagate_two_point(s, 1, t0, dt, n_steps, substeps, psi, obs);
 }
+
+/* --------------------------------------------------------------------------------
+ * Classical fourth-order Runge-Kutta on the TDKS system d phi/dt = -i H[n(phi), t] phi
+ * (Sec. "New propagators for real-time TDDFT" lists Runge-Kutta among the propagators in
+ * use).  Per sub-step ds, with every stage's Hamiltonian built from that stage's own density:
+ *   k1 = -i H[n(phi), t] phi,                      k2 = -i H[n(p2), t + ds/2] p2, p2 = phi + ds/2 k1,
+ *   k3 = -i H[n(p3), t + ds/2] p3, p3 = phi + ds/2 k2,  k4 = -i H[n(p4), t + ds] p4, p4 = phi + ds k3,
+ *   phi(t + ds) = phi + ds/6 (k1 + 2 k2 + 2 k3 + k4).
+ * Records as oracle_propagate.
+ * ------------------------------------------------------------------------------ */
+/* k = -i H[n(v), t] v */
+static void rk4_slope(const oracle_sys *s, double t, const cplx *v, double *n, double *vx, cplx *k) {
+  const long tot = (long)s->n_k * npts(s) * s->n_orb;
+  double E[3], A[3];
+  oracle_field(s, t, E, A);
+  if (s->xc == 1) {
+    oracle_density(s, v, n);
+    oracle_lda_x(s, n, vx);
+  }
+  apply_H_field(s, E, A, s->xc == 1 ? vx : NULL, v, k);
+  for (long i = 0; i < tot; i++) k[i] *= -I;
+}
+
+void oracle_propagate_rk4(const oracle_sys *s, double t0, double dt, int n_steps, int substeps, cplx *psi,
+                          double *obs) {
+  const long N = npts(s), tot = (long)s->n_k * N * s->n_orb;
+  const double ds = dt / (double)substeps;
+  double *n = (double *)malloc(sizeof(double) * (size_t)N);
+  double *vx = (double *)malloc(sizeof(double) * (size_t)N);
+  cplx *k = (cplx *)malloc(sizeof(cplx) * (size_t)tot);
+  cplx *stage = (cplx *)malloc(sizeof(cplx) * (size_t)tot);
+  cplx *sum = (cplx *)malloc(sizeof(cplx) * (size_t)tot);
+  for (int st = 0; st < n_steps; st++) {
+    double t = t0 + (double)st * dt;
+    if (obs) oracle_observables(s, t, t + 0.5 * ds, psi, obs + 8 * st);
+    for (int j = 0; j < substeps; j++) {
+      const double tj = t + (double)j * ds;
+      rk4_slope(s, tj, psi, n, vx, k);
+      for (long i = 0; i < tot; i++) {
+        sum[i] = k[i];
+        stage[i] = psi[i] + 0.5 * ds * k[i];
+      }
+      rk4_slope(s, tj + 0.5 * ds, stage, n, vx, k);
+      for (long i = 0; i < tot; i++) {
+        sum[i] += 2.0 * k[i];
+        stage[i] = psi[i] + 0.5 * ds * k[i];
+      }
+      rk4_slope(s, tj + 0.5 * ds, stage, n, vx, k);
+      for (long i = 0; i < tot; i++) {
+        sum[i] += 2.0 * k[i];
+        stage[i] = psi[i] + ds * k[i];
+      }
+      rk4_slope(s, tj + ds, stage, n, vx, k);
+      for (long i = 0; i < tot; i++) psi[i] += ds / 6.0 * (sum[i] + k[i]);
+    }
+  }
+  free(n); free(vx); free(k); free(stage); free(sum);
+}

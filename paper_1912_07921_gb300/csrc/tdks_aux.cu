@@ -525,6 +525,43 @@ density_sum_kernel(long N, int n_kb, int n_batches, const double *wocc, const do
   }
 }
 
+// Runge-Kutta stage updates: element-wise over the packed state, one double2 per thread
+// and grid-stride loop (HBM-bound: 48 or 64 bytes per value).
+__global__ void rk4_stage_kernel(long n, const double2 *psi, const double2 *k, double a, double2 *stage, double2 *acc,
+                                 double b, int init) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const double2 kv = k[i], pv = psi[i];
+    stage[i] = make_double2(pv.x + a * kv.x, pv.y + a * kv.y);
+    const double2 av = init ? make_double2(0.0, 0.0) : acc[i];
+    acc[i] = make_double2(av.x + b * kv.x, av.y + b * kv.y);
+  }
+}
+
+__global__ void rk4_finish_kernel(long n, double2 *psi, const double2 *acc, const double2 *k, double b) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const double2 kv = k[i], av = acc[i], pv = psi[i];
+    psi[i] = make_double2(pv.x + (av.x + b * kv.x), pv.y + (av.y + b * kv.y));
+  }
+}
+
+static int elementwise_blocks(long n) {
+  const long want = (n + 255) / 256;
+  return (int)(want < 1 ? 1 : (want > 152L * 16 ? 152L * 16 : want));
+}
+
+cudaError_t launch_rk4_stage(long n, const void *psi, const void *k, double a, void *stage, void *acc, double b,
+                             int init, cudaStream_t s) {
+  rk4_stage_kernel<<<elementwise_blocks(n), 256, 0, s>>>(n, (const double2 *)psi, (const double2 *)k, a,
+                                                         (double2 *)stage, (double2 *)acc, b, init);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rk4_finish(long n, void *psi, const void *acc, const void *k, double b, cudaStream_t s) {
+  rk4_finish_kernel<<<elementwise_blocks(n), 256, 0, s>>>(n, (double2 *)psi, (const double2 *)acc,
+                                                          (const double2 *)k, b);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_density_sum(int prec, long N, int n_kb, int n_batches, const double *wocc,
                                const double *dens_part, double *n_out, cudaStream_t s) {
   if (prec == P_C64)

@@ -1134,14 +1134,88 @@ static int propagate_exp(tdks_system *s, double t0, double dt, int n_steps, int 
   return TDKS_OK;
 }
 
+// (cr + i ci) H[n, t] in -> out, with n the density now in dens_part: LDA, projector step
+// and a middle-term sweep (the shape of Taylor term 2).
+static int apply_scaled(tdks_system *s, const void *in, void *out, double cr, double ci, double t) {
+  double E[3], A[3];
+  field_at(s, t, E, A);
+  int rc;
+  if ((rc = run_lda(s, E, A))) return rc;
+  if ((rc = run_gather(s, in, A))) return rc;
+  SweepParams p{};
+  sweep_common(s, p, A, 1);
+  set_coef(p, cr, ci);
+  p.in = in;
+  p.out = out;
+  SweepMaps tm;
+  const bool have_tm = tma_path(s) && encode_sweep_maps(s, in, MODE_MID, &tm, s->path == 2, 1);
+  return run_sweep(s, MODE_MID, p, have_tm ? &tm : nullptr, 1);
+}
+
+// Classical fourth-order Runge-Kutta on d psi/dt = -i H[n(psi), t] psi (complex128 systems):
+// every stage rebuilds the density of its own stage vector, so H follows the state within the
+// sub-step.  term[0] accumulates the weighted slopes, term[1] holds the stage vector, term[2]
+// the slope k = -i H psi_stage.
+static int propagate_rk4(tdks_system *s, double t0, double dt, int n_steps, int substeps) {
+  const double ds = dt / substeps;
+  if (std::fabs(ds) * kinetic_max(s) > 2.0 * std::sqrt(2.0))
+    return fail(TDKS_EUNSTABLE, "RK4 sub-step beyond its stability limit on the imaginary axis (dt_sub * K_max > 2 sqrt 2)");
+  const long n = (long)(s->state_bytes / 16);
+  void *acc = s->term[0], *stage = s->term[1], *k = s->term[2];
+  int rc;
+  auto stage_density = [&](const void *v) -> int {
+    cudaError_t e = launch_density(s->prec, s->N, s->n_kb, s->n_batches, v, nullptr, s->d_wocc, s->dens_part,
+                                   s->stream);
+    s->launches++;
+    s->dens_valid = false;  // dens_part now holds a stage vector's density
+    return e == cudaSuccess ? TDKS_OK : fail(TDKS_EDEVICE, std::string("density: ") + cudaGetErrorString(e));
+  };
+  auto check = [&](cudaError_t e) {
+    s->launches++;
+    return e == cudaSuccess ? TDKS_OK : fail(TDKS_EDEVICE, std::string("rk4 update: ") + cudaGetErrorString(e));
+  };
+  for (int st = 0; st < n_steps; st++) {
+    const double t = t0 + st * dt;
+    for (int j = 0; j < substeps; j++) {
+      const double tj = t + j * ds;
+      if ((rc = ensure_density(s))) return rc;
+      if (j == 0) {
+        // record of the state at t: the Hamiltonian of t + ds/2 with v_x of this state
+        double E[3], A[3];
+        field_at(s, tj + 0.5 * ds, E, A);
+        if ((rc = run_lda(s, E, A))) return rc;
+        if ((rc = first_sweep(s, 1.0, 0.0, A, true))) return rc;
+        double *slot = s->ring + (s->steps % tdks_system::RING) * TDKS_RECORD;
+        if ((rc = run_finalize(s, slot, t, E, A))) return rc;
+      }
+      if ((rc = apply_scaled(s, s->psi, k, 0.0, -1.0, tj))) return rc;  // k1
+      if ((rc = check(launch_rk4_stage(n, s->psi, k, 0.5 * ds, stage, acc, ds / 6.0, 1, s->stream)))) return rc;
+      if ((rc = stage_density(stage)) || (rc = apply_scaled(s, stage, k, 0.0, -1.0, tj + 0.5 * ds))) return rc;  // k2
+      if ((rc = check(launch_rk4_stage(n, s->psi, k, 0.5 * ds, stage, acc, ds / 3.0, 0, s->stream)))) return rc;
+      if ((rc = stage_density(stage)) || (rc = apply_scaled(s, stage, k, 0.0, -1.0, tj + 0.5 * ds))) return rc;  // k3
+      if ((rc = check(launch_rk4_stage(n, s->psi, k, ds, stage, acc, ds / 3.0, 0, s->stream)))) return rc;
+      if ((rc = stage_density(stage)) || (rc = apply_scaled(s, stage, k, 0.0, -1.0, tj + ds))) return rc;  // k4
+      if ((rc = check(launch_rk4_finish(n, s->psi, acc, k, ds / 6.0, s->stream)))) return rc;
+      s->dens_valid = false;
+    }
+    s->steps++;
+  }
+  s->clock_t = t0 + n_steps * dt;
+  s->clock_dt = dt;
+  s->clock_substeps = substeps;
+  return TDKS_OK;
+}
+
 int tdks_set_propagator(tdks_sys s, int propagator) {
   if (!s) return fail(TDKS_EINVAL, "NULL system");
-  if (propagator < TDKS_PROP_TAYLOR4 || propagator > TDKS_PROP_AETRS)
-    return fail(TDKS_EINVAL, "propagator must be TDKS_PROP_TAYLOR4, _CFM4, _EMR or _AETRS");
+  if (propagator < TDKS_PROP_TAYLOR4 || propagator > TDKS_PROP_RK4)
+    return fail(TDKS_EINVAL, "propagator must be TDKS_PROP_TAYLOR4, _CFM4, _EMR, _AETRS or _RK4");
   if (propagator != TDKS_PROP_TAYLOR4 && s->xfn)
     return fail(TDKS_EINVAL, "state-parallel propagation (tdks_set_exchange) is Taylor-4 only");
+  if (propagator == TDKS_PROP_RK4 && s->prec != TDKS_C128)
+    return fail(TDKS_EINVAL, "RK4 runs on complex128 systems");
   CU(cudaStreamSynchronize(s->stream));
-  if (propagator != TDKS_PROP_TAYLOR4 && !s->vx_hist[0])
+  if (propagator != TDKS_PROP_TAYLOR4 && propagator != TDKS_PROP_RK4 && !s->vx_hist[0])
     for (int j = 0; j < 4; j++) CU(cudaMalloc((void **)&s->vx_hist[j], (size_t)s->N * sizeof(double)));
   s->prop = propagator;
   s->n_hist = 0;
@@ -1166,6 +1240,7 @@ int tdks_propagate_n(tdks_sys s, double t0, double dt, int n_steps, int substeps
   if (n_steps < 0 || substeps < 0) return fail(TDKS_EINVAL, "negative count");
   if (!s->have_orbitals) return fail(TDKS_ESTATE, "orbitals not set");
   if (substeps == 0) tdks_auto_substeps(s, dt, &substeps);
+  if (s->prop == TDKS_PROP_RK4) return propagate_rk4(s, t0, dt, n_steps, substeps);
   if (s->prop != TDKS_PROP_TAYLOR4) return propagate_exp(s, t0, dt, n_steps, substeps);
   const double dts = dt / substeps;
   if (std::fabs(dts) * kinetic_max(s) > 2.0 * std::sqrt(2.0))

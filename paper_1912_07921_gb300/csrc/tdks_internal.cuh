@@ -200,6 +200,12 @@ cudaError_t launch_lda(int prec, int bloch, long N, int nx, int ny, int nz, doub
                        const double *vloc, int xc,
                        const double E[3], double half_A2, PointAux *aux, double *lda_part,
                        int n_blocks, cudaStream_t s, const double *n_in = nullptr);
+// Classical Runge-Kutta stage update over n complex128 values (complex128 systems):
+//   stage = psi + a k,  acc = (init ? 0 : acc) + b k,
+// and the last stage's psi <- psi + acc + b k (rk4_finish).
+cudaError_t launch_rk4_stage(long n, const void *psi, const void *k, double a, void *stage, void *acc, double b,
+                             int init, cudaStream_t s);
+cudaError_t launch_rk4_finish(long n, void *psi, const void *acc, const void *k, double b, cudaStream_t s);
 // n_out[r] = sum over this system's states of w_k f |psi_ik(r)|^2 (FP64), from dens_part
 cudaError_t launch_density_sum(int prec, long N, int n_kb, int n_batches, const double *wocc,
                                const double *dens_part, double *n_out, cudaStream_t s);

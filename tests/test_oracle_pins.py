@@ -649,3 +649,47 @@ def test_emr_and_aetrs_with_exchange_are_second_order(name):
     spec, inp, o = _cfm_case(1)
     for r in _orders(o, inp, getattr(o, "propagate_" + name), 0.64, (16, 32, 64)):
         assert 3.4 < r < 4.8, (name, r)
+
+
+# ---------------------------------------------------------------------------------------
+# Classical Runge-Kutta 4 (Runge-Kutta is in the same section's list of propagators)
+# ---------------------------------------------------------------------------------------
+def test_rk4_without_field_or_exchange_is_the_taylor_step():
+    """For a time-independent linear H the RK4 update is exactly the degree-4 Taylor polynomial
+    of exp(-i dt H): one RK4 step equals one Taylor-4 step up to rounding."""
+    spec, inp, o = _cfm_case(0)
+    o0 = oracle.System(spec, inp, xc=0, gauge=I.GAUGE_NONE)
+    r, obs_r = o0.propagate_rk4(inp.psi0, 0.0, 0.04, 5, 1)
+    t, obs_t = o0.propagate(inp.psi0, 0.0, 0.04, 5, 1)
+    assert np.max(np.abs(r - t)) < 1e-13
+    np.testing.assert_allclose(obs_r, obs_t, rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("xc", [0, 1])
+def test_rk4_is_fourth_order_with_field_and_exchange(xc):
+    """Driven problem, with and without LDA exchange: the stages rebuild the density, so the
+    error falls 16x per halving of dt in both cases (reference: RK4 at dt/32)."""
+    spec, inp, o = _cfm_case(xc)
+    T = 0.64
+    ref, _ = o.propagate_rk4(inp.psi0, 0.0, T / 256, 256, 1, record=False)
+    e = [np.linalg.norm(o.propagate_rk4(inp.psi0, 0.0, T / n, n, 1, record=False)[0] - ref) for n in (8, 16, 32)]
+    for a, b in zip(e, e[1:]):
+        assert 14.0 < a / b < 18.0, e
+
+
+def test_rk4_velocity_gauge_agrees_with_taylor_at_small_steps():
+    """Periodic cell in the velocity gauge (H depends on A(t) non-linearly): RK4 and Taylor-4
+    (exchange off, so Taylor-4 is order two through the midpoint field) converge to the same
+    state; their difference falls ~4x per halving of dt."""
+    from tests._util import bloch_cell, bloch_inputs
+    spec = bloch_cell(I.PREC_C128)
+    inp = bloch_inputs(spec)
+    o = oracle.System(spec, inp, xc=0)
+    T = 0.16
+    d = []
+    for n in (4, 8, 16):
+        a, _ = o.propagate_rk4(inp.psi0, 0.0, T / n, n, 1, record=False)
+        b, _ = o.propagate(inp.psi0, 0.0, T / n, n, 1, record=False)
+        d.append(np.linalg.norm(a - b))
+    for x, y in zip(d, d[1:]):
+        assert 3.3 < x / y < 4.8, d
