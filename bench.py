@@ -40,6 +40,7 @@ UNIT = "updates/s"
 
 SWEEP_SOURCES = ["tdks_sweep_tma.cu", "tdks_tma.cuh", "tdks_sweep_ws1.cu", "tdks_sweep_ws2.cu", "tdks_sweep_ws3.cu",
                  "tdks_sweep_ws4.cu", "tdks_sweep_common.cuh", "tdks_vec.cuh", "tdks_internal.cuh"]
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e data-sheet bandwidth, for context beside the measured peak
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "tma_sweep_medium_molecule.md")
 
 
@@ -303,6 +304,7 @@ def run_ours(args, rank, world, local_rank):
             "roofline": {"bound": "hbm", "kernel": "taylor stencil sweep (4 per sub-step)",
                          "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": achieved / peak,
+                         "frac_of_nominal": achieved / NOMINAL_HBM_GBS, "nominal_peak": NOMINAL_HBM_GBS,
                          "traffic": _traffic_per_launch() if sysm.spec.n_orb == 64 and prec == I.PREC_C64
                          else None,
                          "sweep_source_hash": sweep_source_hash(),

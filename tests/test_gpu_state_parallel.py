@@ -137,6 +137,31 @@ def test_two_thread_ranks_match_one_system_and_the_oracle(prec):
     assert rel_err(psi_sh, ref_psi) < tol_o
 
 
+def test_two_thread_ranks_periodic_cell_currents():
+    """A periodic cell in the velocity gauge with k-points: the record's current is the sum of
+    the ranks' current partials (exchanged with the band energy), so a sharded run must give
+    the whole system's current and energy.  complex128 against one system and the oracle."""
+    from tests._util import bloch_cell, bloch_inputs
+    from paper_1912_07921_gb300.system import System
+
+    spec = bloch_cell(I.PREC_C128, n_orb=7)
+    inp = bloch_inputs(spec)
+    steps, substeps = 3, 2
+    psi_sh, recs, calls = _run_sharded(spec, inp, 2, steps, substeps, 4)
+    assert calls == [steps * substeps + steps] * 2
+    whole = System(spec, inp, stream=torch.cuda.current_stream().cuda_stream)
+    whole.propagate(0.0, spec.dt, steps, substeps)
+    psi_w, rec_w = whole.get_orbitals(), whole.reductions(0, steps)
+    whole.close()
+    ref_psi, ref_rec = oracle.System(spec, inp).propagate(inp.psi0, 0.0, spec.dt, steps, substeps)
+    assert np.max(np.abs(rec_w[:, 4:7])) > 0  # the current is recorded
+    for rec in recs:
+        assert _rec_err(rec, rec_w) < 1e-12
+        assert _rec_err(rec, ref_rec) < 1e-12
+    assert rel_err(psi_sh, psi_w) < 1e-12
+    assert rel_err(psi_sh, ref_psi) < 1e-12
+
+
 def _free_port():
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
