@@ -41,6 +41,19 @@ def _apply_gpu(sysm, psi, t):
     return sysm.unpack(out)
 
 
+def _minimal_box(prec):
+    """5^3 finite box at order 8 (M + 1 points per axis), one orbital, one atom whose
+    projector sphere covers the whole box."""
+    return I.SystemSpec(nx=5, ny=5, nz=5, h=0.4, fd_order=8, prec=prec, n_orb=1, n_atoms=1, projectors=True,
+                        gauge=I.GAUGE_LENGTH, amp=0.05, omega=0.3, dt=0.005, seed=12)
+
+
+def _minimal_cell(prec):
+    """2^3 periodic cell at order 4 (M points per axis): every halo point is a periodic image
+    of the cell itself, with its Bloch phase."""
+    return bloch_cell(prec, nx=2, ny=2, nz=2, n_orb=2, n_k=2)
+
+
 APPLY_CASES = {
     "tiny_c128": (lambda: I.tiny_molecule(), None),
     "ragged_c128_order8": (lambda: ragged_molecule(I.PREC_C128), None),
@@ -49,6 +62,11 @@ APPLY_CASES = {
     "bloch_c128_order4": (lambda: bloch_cell(I.PREC_C128), bloch_inputs),
     "bloch_c128_order8": (lambda: bloch_cell(I.PREC_C128, fd_order=8, n_k=2), bloch_inputs),
     "bloch_c64_order4": (lambda: bloch_cell(I.PREC_C64, n_orb=5), bloch_inputs),
+    # degenerate sizes: the smallest grids the stencils allow, one orbital in a padded batch
+    "minimal_box_c128_order8": (lambda: _minimal_box(I.PREC_C128), None),
+    "minimal_box_c64_order8": (lambda: _minimal_box(I.PREC_C64), None),
+    "minimal_cell_c128_order4": (lambda: _minimal_cell(I.PREC_C128), bloch_inputs),
+    "minimal_cell_c64_order4": (lambda: _minimal_cell(I.PREC_C64), bloch_inputs),
 }
 
 
@@ -323,6 +341,23 @@ def test_rk4_refuses_complex64():
     with pytest.raises(_lib.TdksError):
         sysm.set_propagator(4)
     sysm.close()
+
+
+@pytest.mark.parametrize("kind", ["box", "cell"])
+@pytest.mark.parametrize("prec", [I.PREC_C128, I.PREC_C64])
+def test_minimal_grids_propagate_like_the_oracle(kind, prec):
+    """Propagation with records on the smallest grids (see APPLY_CASES)."""
+    spec = _minimal_box(prec) if kind == "box" else _minimal_cell(prec)
+    inp = I.make_inputs(spec) if kind == "box" else bloch_inputs(spec)
+    n_steps, subs = 3, 2
+    sysm = _system(spec, inp)
+    sysm.propagate(0.0, spec.dt, n_steps, subs)
+    psi, rec = sysm.get_orbitals(), sysm.reductions(0, n_steps)
+    sysm.close()
+    psi_o, rec_o = oracle.System(spec, inp).propagate(inp.psi0, 0.0, spec.dt, n_steps, subs)
+    tol = 1e-12 if prec == I.PREC_C128 else 2e-5
+    assert rel_err(psi, psi_o) < tol
+    assert _rec_err(rec, rec_o) < tol
 
 
 def test_cfm4_refuses_the_velocity_gauge_and_batches():
