@@ -55,6 +55,12 @@ void batch_free(tdks_batch *b) {
   if (b->work) cudaStreamDestroy(b->work);
 }
 
+// CTAs of one system in the batched LDA launch: a sixteenth of the single-system count (whose
+// partial buffer it fills), i.e. ~16 points per thread, so that the launch over all systems pays
+// each CTA's setup (system lookup, field, weight staging) a few times per SM rather than once per
+// CTA-sized run of points.
+static int lda_batch_blocks(long N) { return std::max(1, (lda_blocks(N) + 15) / 16); }
+
 // Kernels one sub-step launches: the LDA/V_eff kernel, per Taylor term the projector step
 // (gather stages 1 and 2 and the non-local term, where any system has atoms) and the sweep,
 // and the record and clock kernels.
@@ -229,7 +235,7 @@ int tdks_batch_create(const tdks_sys *systems, int n, void *stream, tdks_batch_t
     gather_begin[i + 1] = gather_begin[i] + (long)s->n_atoms * s->n_kb * (s->n_atoms > 0 ? s->gchunks : 0);
     unit_begin[i + 1] = unit_begin[i] + (long)s->n_atoms * s->n_kb;
     nl_begin[i + 1] = nl_begin[i] + (s->n_atoms > 0 ? nl_blocks(s->n_sp, s->n_kb) : 0);
-    const int nl = lda_blocks(s->N);
+    const int nl = lda_batch_blocks(s->N);
     lda_begin[i + 1] = lda_begin[i] + nl;
     BatchAux &a = aux[i];
     a.N = s->N; a.nx = s->nx; a.ny = s->ny; a.nz = s->nz; a.n_kb = s->n_kb; a.xc = s->xc;
