@@ -40,6 +40,8 @@ UNIT = "updates/s"
 
 SWEEP_SOURCES = ["tdks_sweep_tma.cu", "tdks_tma.cuh", "tdks_sweep_ws1.cu", "tdks_sweep_ws2.cu", "tdks_sweep_ws3.cu",
                  "tdks_sweep_ws4.cu", "tdks_sweep_common.cuh", "tdks_vec.cuh", "tdks_internal.cuh"]
+WORKLOAD = ("medium molecule 96^3 h=0.25 order-8 FD, 64 orbitals, 16 atoms x 4 KB projectors, sin^2 pulse, "
+            "LDA exchange, dt=0.05 as 4 Taylor-4 sub-steps")
 NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e data-sheet bandwidth, for context beside the measured peak
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "tma_sweep_medium_molecule.md")
 
@@ -295,8 +297,7 @@ def run_ours(args, rank, world, local_rank):
             "scaling": "strong" if shard else "weak", "vs_baseline": None,
             "dtype": "c64 terms + f64 state/reductions" if prec == I.PREC_C64 else "c128 (f64)",
             "data": "synthetic (seeded molecule: Gaussian orbitals, wells, KB projectors)",
-            "config": {"workload": "medium molecule 96^3 h=0.25 order-8 FD, 64 orbitals, 16 atoms x 4 KB "
-                                   "projectors, sin^2 pulse, LDA exchange, dt=0.05 as 4 Taylor-4 sub-steps",
+            "config": {"workload": WORKLOAD,
                        "grid": [spec.nx, spec.ny, spec.nz], "n_orb": spec.n_orb, "substeps": subs,
                        "precision": args.prec, "l2": "working set > L2 (state 906 MB + terms), no flush",
                        "parallelism": f"states x{world} (density allreduce per sub-step)" if shard
@@ -609,8 +610,9 @@ def run_reference(args, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": s / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded molecule)",
-            "config": {"workload": "medium molecule 96^3 h=0.25 order-8 FD, 16 atoms x 4 KB projectors, "
-                                   "dt=0.05 as 4 Taylor-4 sub-steps", "precision": "c128 oracle"},
+            "config": {"workload": WORKLOAD, "grid": [spec.nx, spec.ny, spec.nz], "n_orb": spec.n_orb,
+                       "substeps": spec.substeps, "precision": "c128 oracle",
+                       "sample": f"{n_s} of {spec.n_orb} orbitals advanced per step"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{n_s} of 64 orbitals per step, {args.steps} steps"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
