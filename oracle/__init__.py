@@ -69,6 +69,10 @@ def _load():
         _lib.oracle_propagate_emr.argtypes = [S, D, D, I, I, P, P]
         _lib.oracle_propagate_aetrs.argtypes = [S, D, D, I, I, P, P]
         _lib.oracle_propagate_rk4.argtypes = [S, D, D, I, I, P, P]
+        _lib.oracle_hartree.argtypes = [S, P, P]
+        _lib.oracle_hartree.restype = D
+        _lib.oracle_hartree_self_cell.argtypes = []
+        _lib.oracle_hartree_self_cell.restype = D
     return _lib
 
 
@@ -131,6 +135,14 @@ class System:
         vx = np.empty_like(n)
         ex = self.lib.oracle_lda_x(self.ref, _ptr(n), _ptr(vx))
         return ex, vx
+
+    def hartree(self, n):
+        """(E_H, v_H) of the density n: a direct sum over grid cells in a finite box, the
+        exact plane-wave Poisson solve with a neutralising background in a periodic cell."""
+        n = np.ascontiguousarray(n, dtype=np.float64)
+        vh = np.empty_like(n)
+        eh = self.lib.oracle_hartree(self.ref, _ptr(n), _ptr(vh))
+        return eh, vh
 
     def apply_H(self, psi, t=0.0, vx=None) -> np.ndarray:
         """H[vx, t] psi.  vx=None applies no exchange term; pass vx explicitly (e.g. from
@@ -204,6 +216,11 @@ class System:
 
     def sphere_count(self, a: int) -> int:
         return self.lib.oracle_sphere_count(self.ref, a)
+
+
+def hartree_self_cell() -> float:
+    """c0 = integral of 1/|r| over the unit cube centred at 0 (a cell's own Coulomb term)."""
+    return _load().oracle_hartree_self_cell()
 
 
 def fd_weights(M: int):

@@ -739,3 +739,82 @@ void oracle_propagate_rk4(const oracle_sys *s, double t0, double dt, int n_steps
   }
   free(n); free(vx); free(k); free(stage); free(sum);
 }
+
+/* --------------------------------------------------------------------------------
+ * Hartree potential v_H(r) = int n(r') / |r - r'| dr' (atomic units), with the energy
+ * E_H = 1/2 int n v_H.  The paper's TDDFT Hamiltonian carries the Hartree term among the
+ * density-dependent potentials it extrapolates for CFM4 (Sec. "New propagators for
+ * real-time TDDFT"); the propagation path built here takes exchange only, and these
+ * functions are the definition a Hartree kernel is checked against.
+ *
+ * Finite box: the integral as a sum over grid cells, n taken constant over each cell:
+ *   v_H(r_i) = h^3 sum_j n_j G(r_i - r_j),  G(d) = 1/|d| for d != 0,
+ *   G(0) = (1/h^3) int over the cell centred at 0 of 1/|r| = c0 / h,
+ *   c0 = int over the unit cube [-1/2, 1/2]^3 of 1/|r| = 3 ln(2 + sqrt 3) - pi/2
+ * (the cell's own contribution; the other cells by their centre value).
+ * Periodic cell: the Poisson equation -Lap v_H = 4 pi (n - <n>) solved exactly on the
+ * grid's plane waves, v_H = sum_(G != 0) 4 pi n(G) / |G|^2 e^(i G.r), with the neutralising
+ * background removing G = 0 and each G the shortest of its aliases.
+ * Returns E_H = 1/2 h^3 sum_i n_i v_H(r_i).
+ * ------------------------------------------------------------------------------ */
+double oracle_hartree_self_cell(void) { return 3.0 * log(2.0 + sqrt(3.0)) - 0.5 * M_PI; }
+
+/* wavenumber of index k on an n-point periodic axis of length L: the alias nearest zero */
+static double grid_wavenumber(int k, int n, double L) {
+  const int kk = (k <= n / 2) ? k : k - n;
+  return 2.0 * M_PI * (double)kk / L;
+}
+
+double oracle_hartree(const oracle_sys *s, const double *n, double *vh) {
+  const long N = npts(s);
+  const double h = s->h, h3 = h * h * h;
+  if (s->bc == 0) {
+    const double g0 = oracle_hartree_self_cell() / h;
+#pragma omp parallel for
+    for (long i = 0; i < N; i++) {
+      const int ix = (int)(i % s->nx), iy = (int)((i / s->nx) % s->ny), iz = (int)(i / ((long)s->nx * s->ny));
+      double acc = 0.0;
+      for (long j = 0; j < N; j++) {
+        const int jx = (int)(j % s->nx), jy = (int)((j / s->nx) % s->ny), jz = (int)(j / ((long)s->nx * s->ny));
+        const double dx = (ix - jx) * h, dy = (iy - jy) * h, dz = (iz - jz) * h;
+        const double d = sqrt(dx * dx + dy * dy + dz * dz);
+        acc += n[j] * (j == i ? g0 : 1.0 / d);
+      }
+      vh[i] = h3 * acc;
+    }
+  } else {
+    /* plain discrete Fourier transform over all grid points (small cells only) */
+    const double L[3] = {s->nx * h, s->ny * h, s->nz * h};
+    const long NG = N;
+    cplx *nG = (cplx *)malloc(sizeof(cplx) * (size_t)NG);
+#pragma omp parallel for
+    for (long g = 0; g < NG; g++) {
+      const int kx = (int)(g % s->nx), ky = (int)((g / s->nx) % s->ny), kz = (int)(g / ((long)s->nx * s->ny));
+      cplx acc = 0.0;
+      for (long j = 0; j < N; j++) {
+        const int jx = (int)(j % s->nx), jy = (int)((j / s->nx) % s->ny), jz = (int)(j / ((long)s->nx * s->ny));
+        const double ph = 2.0 * M_PI * ((double)kx * jx / s->nx + (double)ky * jy / s->ny + (double)kz * jz / s->nz);
+        acc += n[j] * cexp(-I * ph);
+      }
+      nG[g] = acc;
+    }
+#pragma omp parallel for
+    for (long i = 0; i < N; i++) {
+      const int ix = (int)(i % s->nx), iy = (int)((i / s->nx) % s->ny), iz = (int)(i / ((long)s->nx * s->ny));
+      cplx acc = 0.0;
+      for (long g = 1; g < NG; g++) { /* g = 0 is the background */
+        const int kx = (int)(g % s->nx), ky = (int)((g / s->nx) % s->ny), kz = (int)(g / ((long)s->nx * s->ny));
+        const double Gx = grid_wavenumber(kx, s->nx, L[0]), Gy = grid_wavenumber(ky, s->ny, L[1]),
+                     Gz = grid_wavenumber(kz, s->nz, L[2]);
+        const double G2 = Gx * Gx + Gy * Gy + Gz * Gz;
+        const double ph = 2.0 * M_PI * ((double)kx * ix / s->nx + (double)ky * iy / s->ny + (double)kz * iz / s->nz);
+        acc += 4.0 * M_PI / G2 * nG[g] * cexp(I * ph);
+      }
+      vh[i] = creal(acc) / (double)N;
+    }
+    free(nG);
+  }
+  ksum e = {0.0, 0.0};
+  for (long i = 0; i < N; i++) kadd(&e, 0.5 * n[i] * vh[i] * h3);
+  return e.s;
+}

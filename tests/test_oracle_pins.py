@@ -693,3 +693,82 @@ def test_rk4_velocity_gauge_agrees_with_taylor_at_small_steps():
         d.append(np.linalg.norm(a - b))
     for x, y in zip(d, d[1:]):
         assert 3.3 < x / y < 4.8, d
+
+
+# ---------------------------------------------------------------------------------------
+# Hartree potential (the density-dependent potential beside exchange in the TDDFT
+# Hamiltonian): a direct sum over grid cells in a box, the plane-wave Poisson solve in a cell
+# ---------------------------------------------------------------------------------------
+def test_hartree_self_cell_constant_by_quadrature():
+    """c0 = int over the unit cube of 1/|r|: adaptive cubature over one octant, times 8."""
+    from scipy import integrate
+    val, err = integrate.nquad(lambda x, y, z: 1.0 / math.sqrt(x * x + y * y + z * z), [[0.0, 0.5]] * 3,
+                               opts={"epsabs": 1e-11, "epsrel": 1e-11, "limit": 100})
+    assert oracle.hartree_self_cell() == pytest.approx(8.0 * val, abs=1e-9)
+
+
+def _gaussian_box(n, h, sigma, xc=0):
+    spec = _spec(nx=n, ny=n, nz=n, h=h, n_orb=1, xc=xc)
+    o = oracle.System(spec, I.make_inputs(spec, with_orbitals=False))
+    x = (np.arange(n) - (n - 1) / 2) * h
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    r = np.sqrt(X * X + Y * Y + Z * Z)
+    dens = np.exp(-r * r / (2 * sigma ** 2)) / (2 * math.pi * sigma ** 2) ** 1.5
+    return o, r, dens
+
+
+def test_hartree_of_a_gaussian_converges_to_the_closed_form():
+    """n = normalised Gaussian of width sigma: v_H = erf(r / (sqrt2 sigma)) / r and
+    E_H = 1 / (2 sqrt(pi) sigma).  The cell sum is second order in h: halving h cuts the
+    error of both by more than 3 (the box edge at 4 sigma limits the ratio slightly)."""
+    from scipy import special
+    errs, eerrs = [], []
+    for n, h in ((16, 0.5), (32, 0.25)):
+        o, r, dens = _gaussian_box(n, h, 1.0)
+        eh, vh = o.hartree(dens.ravel())
+        exact = np.where(r > 0, special.erf(r / math.sqrt(2.0)) / np.maximum(r, 1e-300), math.sqrt(2 / math.pi))
+        errs.append(np.abs(vh.reshape(r.shape) - exact).max())
+        eerrs.append(abs(eh - 1 / (2 * math.sqrt(math.pi))))
+    assert errs[0] < 7e-3 and errs[1] < 2e-3 and errs[0] > 3.0 * errs[1], errs
+    assert eerrs[0] < 1.5e-3 and eerrs[0] > 3.0 * eerrs[1], eerrs
+
+
+def test_hartree_far_field_is_the_total_charge_over_r():
+    """Far from a compact, cubically symmetric charge the potential is Q/r (the quadrupole
+    vanishes by symmetry; the next term is (sigma/r)^4 ~ 1e-4 here)."""
+    o, r, dens = _gaussian_box(21, 0.4, 0.6)
+    _, vh = o.hartree(dens.ravel())
+    q = dens.sum() * 0.4 ** 3
+    corner = np.unravel_index(np.argmax(r), r.shape)
+    assert vh.reshape(r.shape)[corner] == pytest.approx(q / r[corner], rel=1e-3)
+
+
+def test_hartree_kernel_is_symmetric_and_linear():
+    """<n1, v_H[n2]> = <n2, v_H[n1]> and v_H[a n1 + n2] = a v_H[n1] + v_H[n2], in a box and in a
+    cell (a transposed or offset kernel breaks the first)."""
+    rng = np.random.default_rng(8)
+    for bc in (I.BC_ZERO, I.BC_BLOCH):
+        spec = _spec(nx=7, ny=6, nz=5, h=0.4, n_orb=1, bc=bc, xc=0)
+        o = oracle.System(spec, I.make_inputs(spec, with_orbitals=False))
+        n1, n2 = rng.random(spec.n_points), rng.random(spec.n_points)
+        v1, v2 = o.hartree(n1)[1], o.hartree(n2)[1]
+        assert n1 @ v2 == pytest.approx(n2 @ v1, rel=1e-12)
+        v12 = o.hartree(2.5 * n1 + n2)[1]
+        np.testing.assert_allclose(v12, 2.5 * v1 + v2, rtol=1e-12, atol=1e-12 * np.abs(v12).max())
+
+
+def test_hartree_of_plane_waves_in_a_cell_is_exact():
+    """Periodic cell: n = cos(G.r) gives v_H = 4 pi / |G|^2 cos(G.r) (the background removes
+    the mean); checked for three waves at once, one at the Nyquist index of an even axis."""
+    spec = _spec(nx=6, ny=5, nz=4, h=0.4, n_orb=1, bc=I.BC_BLOCH, xc=0)
+    o = oracle.System(spec, I.make_inputs(spec, with_orbitals=False))
+    L = np.array([6, 5, 4]) * 0.4
+    z, y, x = np.meshgrid(np.arange(4) * 0.4, np.arange(5) * 0.4, np.arange(6) * 0.4, indexing="ij")
+    waves = [((2 * math.pi / L[0], 0, 0), 1.0), ((0, 4 * math.pi / L[1], 2 * math.pi / L[2]), 0.5),
+             ((math.pi / 0.4, 0, 0), 0.25)]
+    n = 3.0 + sum(a * np.cos(g[0] * x + g[1] * y + g[2] * z) for g, a in waves)
+    want = sum(a * 4 * math.pi / (g[0] ** 2 + g[1] ** 2 + g[2] ** 2) * np.cos(g[0] * x + g[1] * y + g[2] * z)
+               for g, a in waves)
+    eh, vh = o.hartree(n.ravel())
+    np.testing.assert_allclose(vh, want.ravel(), atol=1e-11)
+    assert eh == pytest.approx(0.5 * float(n.ravel() @ vh) * 0.4 ** 3, rel=1e-12)
