@@ -576,12 +576,25 @@ def cpu_baseline(n_orb_sample: int):
     sspec = dataclasses.replace(spec, n_orb=n_orb_sample)
     o = oracle.System(sspec, inp)
     cores = len(os.sched_getaffinity(0))
+    prev = oracle.set_threads(cores)
     t0 = time.perf_counter()
     o.propagate(inp.psi0, 0.0, spec.dt, 1, spec.substeps)
     s = time.perf_counter() - t0
+    # the same oracle on one host thread, on a smaller sample of the same step
+    n1 = 2
+    inp1 = I.make_inputs(spec)
+    inp1.psi0 = np.ascontiguousarray(inp1.psi0[..., :n1])
+    o1 = oracle.System(dataclasses.replace(spec, n_orb=n1), inp1)
+    oracle.set_threads(1)
+    t1 = time.perf_counter()
+    o1.propagate(inp1.psi0, 0.0, spec.dt, 1, spec.substeps)
+    s1 = time.perf_counter() - t1
+    oracle.set_threads(prev)
     return {"value": spec.n_points * n_orb_sample / s, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"1 configured step (4 sub-steps + record) of the medium molecule with "
-                      f"{n_orb_sample} of 64 orbitals, {s:.1f} s"}
+                      f"{n_orb_sample} of 64 orbitals, {s:.1f} s",
+            "single_thread": {"value": spec.n_points * n1 / s1, "unit": UNIT, "cores": 1,
+                              "sample": f"the same step with {n1} of 64 orbitals, {s1:.1f} s"}}
 
 
 def run_reference(args, rank):

@@ -72,6 +72,8 @@ def _load():
         _lib.oracle_hartree.argtypes = [S, P, P]
         _lib.oracle_hartree.restype = D
         _lib.oracle_hartree_self_cell.argtypes = []
+        _lib.oracle_set_threads.argtypes = [I]
+        _lib.oracle_set_threads.restype = I
         _lib.oracle_hartree_self_cell.restype = D
     return _lib
 
@@ -216,6 +218,11 @@ class System:
 
     def sphere_count(self, a: int) -> int:
         return self.lib.oracle_sphere_count(self.ref, a)
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's parallel loops from now on; returns the previous count."""
+    return _load().oracle_set_threads(n)
 
 
 def hartree_self_cell() -> float:

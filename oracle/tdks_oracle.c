@@ -29,6 +29,7 @@
  */
 #include <complex.h>
 #include <math.h>
+#include <omp.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -817,4 +818,12 @@ double oracle_hartree(const oracle_sys *s, const double *n, double *vh) {
   ksum e = {0.0, 0.0};
   for (long i = 0; i < N; i++) kadd(&e, 0.5 * n[i] * vh[i] * h3);
   return e.s;
+}
+
+/* Host threads of the oracle's parallel loops (for timing it on one core and on all);
+ * returns the count in use before the call. */
+int oracle_set_threads(int n) {
+  const int old = omp_get_max_threads();
+  if (n > 0) omp_set_num_threads(n);
+  return old;
 }
