@@ -536,13 +536,25 @@ def test_energy_conservation_at_zero_field():
 # CFM4 (Sec. "New propagators for real-time TDDFT": two exponentials with the Hamiltonian
 # at the Gauss points t1,2 = t + (1/2 -+ sqrt3/6) dt, weights a1,2 = (3 -+ 2 sqrt3)/12)
 # ---------------------------------------------------------------------------------------
+def _golden_cfm4():
+    """The paper's printed CFM4 constants (tests/golden/cfm4_constants.txt)."""
+    out = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "cfm4_constants.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                name, expr = (x.strip() for x in line.split("=", 1))
+                out[name] = eval(expr, {"__builtins__": {}}, {"sqrt": math.sqrt})
+    return out
+
+
 def test_cfm4_constants_and_exchange_extrapolation():
     """The constants are the printed ones; the history weights are Lagrange extrapolation
     (exact on polynomials of degree nh - 1, summing to one), combined with the a's."""
     (a1, a2), (th1, th2) = oracle.cfm4_constants()
-    r3 = math.sqrt(3.0)
-    assert a1 == pytest.approx((3 - 2 * r3) / 12, abs=1e-16) and a2 == pytest.approx((3 + 2 * r3) / 12, abs=1e-16)
-    assert th1 == pytest.approx(0.5 - r3 / 6, abs=1e-16) and th2 == pytest.approx(0.5 + r3 / 6, abs=1e-16)
+    g = _golden_cfm4()
+    assert a1 == pytest.approx(g["alpha1"], abs=1e-16) and a2 == pytest.approx(g["alpha2"], abs=1e-16)
+    assert th1 == pytest.approx(g["theta1"], abs=1e-16) and th2 == pytest.approx(g["theta2"], abs=1e-16)
     assert a1 + a2 == pytest.approx(0.5, abs=1e-15)
     rng = np.random.default_rng(3)
     for nh in range(1, 5):
