@@ -357,6 +357,18 @@ def run_c128_side(args):
             "ms_per_step": ms / k}
 
 
+def _batched_sweep_roofline(specs, systems, tune, shapes):
+    """The four batched sweeps of a sub-step: the algorithmic bytes of every system over the
+    autotuner's CUDA-event time of each Taylor term's chosen shape."""
+    sub_bytes = sum(_sweep_bytes(sp, s) for sp, s in zip(specs, systems))
+    sweep_s = sum(float(tune[sh][term]) for term, sh in enumerate(shapes)) / 1e3
+    peak, peak_kind = _peaks()
+    achieved = sub_bytes / sweep_s / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+            "frac": achieved / peak, "bytes_per_substep": sub_bytes,
+            "basis": "autotuner CUDA-event times of the chosen shape per Taylor term"}
+
+
 def run_batched(args, n_sample=16):
     """The batched workload: n independent molecules (edges U[32,80], 4..32 orbitals,
     0..12 atoms with projectors, complex64, 4th-order FD, h = 0.25, dt = 0.015), advanced
@@ -391,6 +403,8 @@ def run_batched(args, n_sample=16):
            "ms_per_step": ms / k, "values_per_step": upd, "launches": b.launch_count() - l0,
            "graph": True, "sweep_shapes": b.shapes(),
            "autotune_ms_per_launch": None if tune is None else [[round(float(x), 4) for x in r] for r in tune]}
+    if tune is not None:
+        out["sweep_roofline"] = _batched_sweep_roofline(specs, systems, tune, b.shapes())
     records = [systems[i].reductions(0, 2 + k) for i in range(min(n_sample, len(systems)))]
     b.close()
     for s in systems:

@@ -62,3 +62,28 @@ def test_reference_arm_runs_on_rank_zero_only():
     import bench
     args = argparse.Namespace(gpus=2, steps=1, warmup=3)
     assert bench.run_reference(args, rank=1) is None
+
+
+def test_batched_sweep_roofline_uses_the_chosen_shape_of_each_term():
+    """The batched roofline divides the systems' algorithmic sweep bytes by the sum of the
+    autotuner's times of the shape chosen for each Taylor term."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    from paper_1912_07921_gb300 import inputs as I
+
+    class Layout:  # what System.layout reports for a complex64 system
+        def __init__(self, sp):
+            self.sp, self.n_k = sp, 1
+
+        def layout(self):
+            return 8, -(-self.sp.n_orb // 8), 8, 0
+
+    specs = I.batched_systems(4)
+    systems = [Layout(sp) for sp in specs]
+    tune = np.full((5, 4), 9.0)
+    tune[2] = [0.5, 9.0, 9.0, 0.9]
+    tune[1] = [9.0, 0.3, 0.3, 9.0]
+    r = bench._batched_sweep_roofline(specs, systems, tune, [2, 1, 1, 2])
+    want = sum(bench._sweep_bytes(sp, s) for sp, s in zip(specs, systems)) / 2.0e-3 / 1e9
+    assert r["achieved"] == pytest.approx(want) and r["frac"] == pytest.approx(want / r["peak"])
