@@ -159,9 +159,12 @@ class System:
         return out
 
     def vx_of(self, psi):
-        if self._s.xc != 1:
+        """The density-dependent potential of psi's density: v_x (xc 1), v_x + v_H (xc 2)."""
+        if self._s.xc not in (1, 2):
             return None
-        return self.lda_x(self.density(psi))[1]
+        n = self.density(psi)
+        v = self.lda_x(n)[1]
+        return v + self.hartree(n.ravel())[1].reshape(v.shape) if self._s.xc == 2 else v
 
     def taylor_substep(self, psi, t, dt) -> np.ndarray:
         psi = self._psi(psi).copy()

@@ -45,7 +45,7 @@ typedef struct {
   const double *kpts; /* [n_k][3] */
   const double *kw;   /* [n_k] */
   const double *vloc; /* [nz][ny][nx] */
-  int xc;             /* 0: none; 1: LDA exchange */
+  int xc;             /* 0: none; 1: LDA exchange; 2: LDA exchange and Hartree */
   double occ;         /* occupation of every orbital */
   int gauge;          /* 0: no field; 1: length gauge E(t).r; 2: velocity gauge A(t) */
   double pol[3];
@@ -186,6 +186,26 @@ double oracle_lda_x(const oracle_sys *s, const double *n, double *vx) {
     kadd(&ex, n[p] * (-0.75 * c) * h3);
   }
   return ex.s;
+}
+
+double oracle_hartree(const oracle_sys *s, const double *n, double *vh); /* defined below */
+
+/* The density-dependent potential of the xc setting: v = v_x (xc 1, exchange) or
+ * v = v_x + v_H (xc 2, exchange and Hartree); returns E_x and puts E_H (0 without
+ * Hartree) in *eh when eh is not NULL. */
+static int has_density_potential(const oracle_sys *s) { return s->xc == 1 || s->xc == 2; }
+static double density_potential(const oracle_sys *s, const double *n, double *v, double *eh) {
+  const double ex = oracle_lda_x(s, n, v);
+  double e = 0.0;
+  if (s->xc == 2) {
+    const long N = npts(s);
+    double *vh = (double *)malloc(sizeof(double) * (size_t)N);
+    e = oracle_hartree(s, n, vh);
+    for (long p = 0; p < N; p++) v[p] += vh[p];
+    free(vh);
+  }
+  if (eh) *eh = e;
+  return ex;
 }
 
 /* --------------------------------------------------------------------------------
@@ -357,11 +377,11 @@ static void apply_H_field(const oracle_sys *s, const double *E, const double *A,
 void oracle_taylor_substep(const oracle_sys *s, double t, double dt, cplx *psi) {
   long tot = (long)s->n_k * npts(s) * s->n_orb;
   double *n = NULL, *vx = NULL;
-  if (s->xc == 1) {
+  if (has_density_potential(s)) {
     n = (double *)malloc(sizeof(double) * (size_t)npts(s));
     vx = (double *)malloc(sizeof(double) * (size_t)npts(s));
     oracle_density(s, psi, n);
-    oracle_lda_x(s, n, vx);
+    density_potential(s, n, vx, NULL);
   }
   cplx *term = (cplx *)malloc(sizeof(cplx) * (size_t)tot);
   cplx *next = (cplx *)malloc(sizeof(cplx) * (size_t)tot);
@@ -385,6 +405,7 @@ void oracle_taylor_substep(const oracle_sys *s, double t, double dt, cplx *psi) 
  * Hamiltonian taken at t_field.  obs = [t_state, norm, E, E_x, o_x, o_y, o_z, f] with
  *   norm = sum_k w_k sum_i ||phi_ik||^2 h^3,
  *   E    = sum_k w_k f_i <phi|H(t_field)|phi> - int n v_x + E_x,
+ *          with Hartree (xc 2): v_x -> v_x + v_H and + E_H,
  *   o    = dipole int r n (finite systems) or the current
  *          J = -(1/Omega) sum_k w_k f_i <phi|(-i grad_h + A)|phi> (periodic cells),
  *   f    = field component along pol at t_field (E in length gauge, A in velocity gauge).
@@ -397,14 +418,14 @@ void oracle_observables(const oracle_sys *s, double t_state, double t_field, con
   double *n = (double *)malloc(sizeof(double) * (size_t)N);
   double *vx = (double *)malloc(sizeof(double) * (size_t)N);
   oracle_density(s, psi, n);
-  double ex = 0.0;
+  double ex = 0.0, eh = 0.0;
   ksum nvx = {0.0, 0.0};
-  if (s->xc == 1) {
-    ex = oracle_lda_x(s, n, vx);
+  if (has_density_potential(s)) {
+    ex = density_potential(s, n, vx, &eh);
     for (long p = 0; p < N; p++) kadd(&nvx, n[p] * vx[p] * h3);
   }
   cplx *hp = (cplx *)malloc(sizeof(cplx) * (size_t)tot);
-  oracle_apply_H(s, t_field, s->xc == 1 ? vx : NULL, psi, hp);
+  oracle_apply_H(s, t_field, has_density_potential(s) ? vx : NULL, psi, hp);
   ksum norm = {0.0, 0.0}, eband = {0.0, 0.0};
   for (int k = 0; k < s->n_k; k++)
     for (long p = 0; p < N; p++)
@@ -453,7 +474,7 @@ void oracle_observables(const oracle_sys *s, double t_state, double t_field, con
   }
   obs[0] = t_state;
   obs[1] = norm.s;
-  obs[2] = eband.s - nvx.s + ex;
+  obs[2] = eband.s - nvx.s + ex + eh;
   obs[3] = ex;
   obs[4] = o3[0];
   obs[5] = o3[1];
@@ -568,13 +589,13 @@ void oracle_propagate_cfm4(const oracle_sys *s, double t0, double dt, int n_step
     for (int j = 0; j < substeps; j++) {
       const double tj = t + (double)j * ds;
       const double *pf = NULL, *ps = NULL;
-      if (s->xc == 1) {
-        /* push v_x of the current state as the newest history entry */
+      if (has_density_potential(s)) {
+        /* push v_x (and v_H) of the current state as the newest history entry */
         double *oldest = hist[3];
         for (int q = 3; q > 0; q--) hist[q] = hist[q - 1];
         hist[0] = oldest;
         oracle_density(s, psi, n);
-        oracle_lda_x(s, n, hist[0]);
+        density_potential(s, n, hist[0], NULL);
         if (nh < 4) nh++;
         double wf[4], wsw[4];
         oracle_cfm4_weights(nh, wf, wsw);
@@ -624,7 +645,7 @@ static int push_vx(const oracle_sys *s, const cplx *psi, double **hist, int nh, 
   for (int q = 3; q > 0; q--) hist[q] = hist[q - 1];
   hist[0] = oldest;
   oracle_density(s, psi, n);
-  oracle_lda_x(s, n, hist[0]);
+  density_potential(s, n, hist[0], NULL);
   return nh < 4 ? nh + 1 : 4;
 }
 
@@ -655,17 +676,17 @@ static void propagate_two_point(const oracle_sys *s, int aetrs, double t0, doubl
     for (int j = 0; j < substeps; j++) {
       const double tj = t + (double)j * ds;
       double E[3], A[3];
-      if (s->xc == 1) nh = push_vx(s, psi, hist, nh, n);
+      if (has_density_potential(s)) nh = push_vx(s, psi, hist, nh, n);
       if (!aetrs) {
-        if (s->xc == 1) extrapolate_vx(s, hist, nh, 0.5, v);
+        if (has_density_potential(s)) extrapolate_vx(s, hist, nh, 0.5, v);
         oracle_field(s, tj + 0.5 * ds, E, A);
-        taylor_exp_field(s, E, s->xc == 1 ? v : NULL, ds, psi);
+        taylor_exp_field(s, E, has_density_potential(s) ? v : NULL, ds, psi);
       } else {
         oracle_field(s, tj, E, A);
-        taylor_exp_field(s, E, s->xc == 1 ? hist[0] : NULL, 0.5 * ds, psi);
-        if (s->xc == 1) extrapolate_vx(s, hist, nh, 1.0, v);
+        taylor_exp_field(s, E, has_density_potential(s) ? hist[0] : NULL, 0.5 * ds, psi);
+        if (has_density_potential(s)) extrapolate_vx(s, hist, nh, 1.0, v);
         oracle_field(s, tj + ds, E, A);
-        taylor_exp_field(s, E, s->xc == 1 ? v : NULL, 0.5 * ds, psi);
+        taylor_exp_field(s, E, has_density_potential(s) ? v : NULL, 0.5 * ds, psi);
       }
     }
   }
@@ -697,11 +718,11 @@ static void rk4_slope(const oracle_sys *s, double t, const cplx *v, double *n, d
   const long tot = (long)s->n_k * npts(s) * s->n_orb;
   double E[3], A[3];
   oracle_field(s, t, E, A);
-  if (s->xc == 1) {
+  if (has_density_potential(s)) {
     oracle_density(s, v, n);
-    oracle_lda_x(s, n, vx);
+    density_potential(s, n, vx, NULL);
   }
-  apply_H_field(s, E, A, s->xc == 1 ? vx : NULL, v, k);
+  apply_H_field(s, E, A, has_density_potential(s) ? vx : NULL, v, k);
   for (long i = 0; i < tot; i++) k[i] *= -I;
 }
 

@@ -784,3 +784,49 @@ def test_hartree_of_plane_waves_in_a_cell_is_exact():
     eh, vh = o.hartree(n.ravel())
     np.testing.assert_allclose(vh, want.ravel(), atol=1e-11)
     assert eh == pytest.approx(0.5 * float(n.ravel() @ vh) * 0.4 ** 3, rel=1e-12)
+
+
+# Exchange and Hartree together (xc 2): the density-dependent potential v_x + v_H wherever
+# the propagators rebuild or extrapolate it, and E_H in the recorded energy.
+def test_hartree_enters_the_energy_as_exactly_e_h():
+    """For one state, the recorded energy with Hartree minus the one without is E_H: the band
+    term gains int n v_H, the double-counting correction removes it, and E_H = 1/2 int n v_H is
+    added (a dropped or doubled piece breaks the equality)."""
+    spec, inp, _ = _cfm_case(1)
+    o1 = oracle.System(spec, inp, xc=1)
+    o2 = oracle.System(spec, inp, xc=2)
+    e1 = o1.observables(inp.psi0, 0.0, 0.1)
+    e2 = o2.observables(inp.psi0, 0.0, 0.1)
+    eh, _ = o2.hartree(o2.density(inp.psi0).ravel())
+    assert eh > 0
+    assert e2[2] - e1[2] == pytest.approx(eh, rel=1e-11)
+    assert e2[3] == e1[3] and e2[1] == e1[1]  # E_x and the norm are unchanged
+
+
+def test_hartree_energy_conservation_is_first_order_with_the_frozen_density():
+    """Zero field, exchange and Hartree: Taylor-4 freezes both over a step, so the energy drift
+    over a fixed time falls ~2x when dt halves, as with exchange alone."""
+    spec = _spec(nx=12, ny=12, nz=12, h=0.4, fd_order=4, n_orb=2, n_atoms=2, wells=True, xc=2, seed=6)
+    inp = I.make_inputs(spec)
+    o = oracle.System(spec, inp, xc=2)
+    drifts = []
+    for dt, nst in ((0.02, 20), (0.01, 40)):
+        psi_end, obs = o.propagate(inp.psi0, 0.0, dt, nst, 1)
+        drifts.append(abs(o.observables(psi_end, dt * nst, dt * nst)[2] - obs[0, 2]))
+    assert drifts[0] < 2e-3 * abs(obs[0, 2])
+    assert 1.7 * drifts[1] < drifts[0] < 2.4 * drifts[1], drifts
+
+
+def test_rk4_and_cfm4_with_hartree_keep_their_order():
+    """Driven problem with exchange and Hartree: RK4 (every stage rebuilds v_x + v_H) stays
+    fourth order (ratio ~16 per halving); CFM4 (v_x + v_H extrapolated from the history)
+    converges faster than second order (ratio > 6)."""
+    spec, inp, o = _cfm_case(2)
+    T = 0.64
+    ref, _ = o.propagate_rk4(inp.psi0, 0.0, T / 256, 256, 1, record=False)
+    er = [np.linalg.norm(o.propagate_rk4(inp.psi0, 0.0, T / n, n, 1, record=False)[0] - ref) for n in (8, 16, 32)]
+    ec = [np.linalg.norm(o.propagate_cfm4(inp.psi0, 0.0, T / n, n, 1, record=False)[0] - ref) for n in (16, 32, 64)]
+    for a, b in zip(er, er[1:]):
+        assert 14.0 < a / b < 18.0, er
+    for a, b in zip(ec, ec[1:]):
+        assert a / b > 6.0, ec
