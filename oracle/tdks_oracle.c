@@ -13,6 +13,9 @@
  *   - the high-order finite-difference Laplacian and gradient on the real-space grid
  *     (Sec. "Maxwell ... coupling", discretisation paragraph; Sec. "Periodic systems");
  *   - the LDA exchange energy E_x = int n e_x(n) (Sec. "Local domains", LDA equation);
+ *   - the Hartree potential of the density, for an exchange-plus-Hartree mode (the
+ *     density-dependent potentials that CFM4 extrapolates, Sec. "New propagators for
+ *     real-time TDDFT");
  *   - the time-dependent dipole d(t) = int r n(r,t) dr (Sec. "Local domains");
  *   - the macroscopic current J = -(i/Omega) int sum_i phi_i [H, r] phi_i
  *     (Sec. "Conductivities", eqn. current_density), local part;
