@@ -73,6 +73,9 @@ def _load():
         _lib.oracle_hartree.restype = D
         _lib.oracle_hartree_self_cell.argtypes = []
         _lib.oracle_set_threads.argtypes = [I]
+        _lib.oracle_band_energy.argtypes = [S, P, P]
+        _lib.oracle_band_energy.restype = D
+        _lib.oracle_velocity_expectation.argtypes = [S, P, P, I, P]
         _lib.oracle_set_threads.restype = I
         _lib.oracle_hartree_self_cell.restype = D
     return _lib
@@ -145,6 +148,19 @@ class System:
         vh = np.empty_like(n)
         eh = self.lib.oracle_hartree(self.ref, _ptr(n), _ptr(vh))
         return eh, vh
+
+    def band_energy(self, A, psi) -> float:
+        """sum_k w_k f <phi|H(A)|phi> h^3 at an explicit vector potential A (no exchange)."""
+        A = np.ascontiguousarray(A, dtype=np.float64)
+        return self.lib.oracle_band_energy(self.ref, _ptr(A), _ptr(self._psi(psi)))
+
+    def velocity(self, A, psi, with_nonlocal=True) -> np.ndarray:
+        """sum_k w_k f <phi| i[H, r] |phi> h^3 per axis at vector potential A; the projector
+        commutator included when `with_nonlocal` is set."""
+        A = np.ascontiguousarray(A, dtype=np.float64)
+        out = np.empty(3)
+        self.lib.oracle_velocity_expectation(self.ref, _ptr(A), _ptr(self._psi(psi)), int(with_nonlocal), _ptr(out))
+        return out
 
     def apply_H(self, psi, t=0.0, vx=None) -> np.ndarray:
         """H[vx, t] psi.  vx=None applies no exchange term; pass vx explicitly (e.g. from

@@ -851,3 +851,85 @@ int oracle_set_threads(int n) {
   if (n > 0) omp_set_num_threads(n);
   return old;
 }
+
+/* --------------------------------------------------------------------------------
+ * Velocity expectation and band energy at an explicit vector potential (periodic cells,
+ * velocity gauge).  The macroscopic current of Sec. "Conductivities" is
+ * J = -(1/Omega) sum_k w_k f_i <phi| v |phi> with the velocity operator v = i[H, r]:
+ *   local part     (-i grad_h + A),
+ *   non-local part i[V_NL, r], with r inside a projector sphere the unwrapped position of
+ *                  the sphere point (its atom's position cancels in the commutator):
+ *                  <phi| i[V_NL, r] |phi> = sum_aj D_aj i (<phi|b_aj><b_aj| d phi> - <phi| d b_aj><b_aj|phi>)
+ *                  with b_aj the dressed projector (Bloch and gauge phases) and d = r - R_a.
+ * The observable record carries the local part; oracle_velocity_expectation returns
+ * sum_k w_k f_i <phi|v|phi> h^3 per axis, with the non-local part when `nonlocal` is set.
+ * oracle_band_energy returns sum_k w_k f_i <phi|H(A)|phi> h^3 (no exchange, no other field).
+ * ------------------------------------------------------------------------------ */
+double oracle_band_energy(const oracle_sys *s, const double *A, const cplx *psi) {
+  const long N = npts(s), tot = (long)s->n_k * N * s->n_orb;
+  const double h3 = s->h * s->h * s->h, E0[3] = {0.0, 0.0, 0.0};
+  cplx *hp = (cplx *)malloc(sizeof(cplx) * (size_t)tot);
+  apply_H_field(s, E0, A, NULL, psi, hp);
+  ksum e = {0.0, 0.0};
+  for (int k = 0; k < s->n_k; k++)
+    for (long i = (long)k * N * s->n_orb; i < (long)(k + 1) * N * s->n_orb; i++)
+      kadd(&e, s->kw[k] * s->occ * creal(conj(psi[i]) * hp[i]) * h3);
+  free(hp);
+  return e.s;
+}
+
+void oracle_velocity_expectation(const oracle_sys *s, const double *A, const cplx *psi, int nonlocal, double *out) {
+  const long N = npts(s);
+  const int M = s->fd_order / 2, B = s->n_orb;
+  const double h = s->h, h3 = h * h * h;
+  double d[5];
+  oracle_fd_gradient_weights(M, d);
+  ksum acc[3] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
+  for (int k = 0; k < s->n_k; k++)
+    for (int iz = 0; iz < s->nz; iz++)
+      for (int iy = 0; iy < s->ny; iy++)
+        for (int ix = 0; ix < s->nx; ix++)
+          for (int o = 0; o < B; o++) {
+            const cplx v = fetch(s, psi, k, o, ix, iy, iz);
+            cplx g[3] = {0.0, 0.0, 0.0};
+            for (int m = 1; m <= M; m++) {
+              g[0] += d[m] * (fetch(s, psi, k, o, ix + m, iy, iz) - fetch(s, psi, k, o, ix - m, iy, iz));
+              g[1] += d[m] * (fetch(s, psi, k, o, ix, iy + m, iz) - fetch(s, psi, k, o, ix, iy - m, iz));
+              g[2] += d[m] * (fetch(s, psi, k, o, ix, iy, iz + m) - fetch(s, psi, k, o, ix, iy, iz - m));
+            }
+            for (int ax = 0; ax < 3; ax++)
+              kadd(&acc[ax], s->kw[k] * s->occ * creal(conj(v) * (-I * g[ax] / h + A[ax] * v)) * h3);
+          }
+  if (nonlocal && s->n_atoms > 0 && s->D != NULL) {
+    for (int a = 0; a < s->n_atoms; a++) {
+      sphere_pt *pts;
+      const int np = sphere_points(s, a, &pts);
+      for (int k = 0; k < s->n_k; k++) {
+        const double *kk = s->kpts + 3 * k;
+        for (int o = 0; o < B; o++) {
+          /* p_j = <b_j|phi>, q_jx = <d_x b_j|phi> */
+          cplx p[4] = {0.0, 0.0, 0.0, 0.0}, q[4][3];
+          for (int j = 0; j < 4; j++) q[j][0] = q[j][1] = q[j][2] = 0.0;
+          for (int t = 0; t < np; t++) {
+            double b[4];
+            beta_values(s, pts[t].d, b);
+            double ph = 0.0;
+            for (int ax = 0; ax < 3; ax++) ph += kk[ax] * pts[t].T[ax] + A[ax] * pts[t].d[ax];
+            const cplx val = h3 * cexp(I * ph) * psi[((long)k * N + pts[t].cell) * B + o];
+            for (int j = 0; j < 4; j++) {
+              p[j] += b[j] * val;
+              for (int ax = 0; ax < 3; ax++) q[j][ax] += pts[t].d[ax] * b[j] * val;
+            }
+          }
+          for (int j = 0; j < 4; j++)
+            for (int ax = 0; ax < 3; ax++) {
+              const cplx c = I * (conj(p[j]) * q[j][ax] - conj(q[j][ax]) * p[j]);
+              kadd(&acc[ax], s->kw[k] * s->occ * s->D[4 * a + j] * creal(c));
+            }
+        }
+      }
+      free(pts);
+    }
+  }
+  for (int ax = 0; ax < 3; ax++) out[ax] = acc[ax].s;
+}

@@ -830,3 +830,40 @@ def test_rk4_and_cfm4_with_hartree_keep_their_order():
         assert 14.0 < a / b < 18.0, er
     for a, b in zip(ec, ec[1:]):
         assert a / b > 6.0, ec
+
+
+# Current of a periodic cell with the projectors' commutator (Sec. "Conductivities": the
+# velocity operator i[H, r] includes i[V_NL, r]); the record carries the local part.
+def test_current_is_minus_the_energy_derivative_in_a():
+    """J = -(1/Omega) dE/dA on the discrete level, because H(A) depends on A only through
+    -i A.grad_h + |A|^2/2 and the projectors' gauge phases: the velocity expectation with the
+    projector commutator equals the central difference of the band energy in each component of
+    A (error ~delta^2), while the local part alone misses by the projectors' share."""
+    from tests._util import bloch_cell, bloch_inputs
+    spec = bloch_cell(I.PREC_C128, n_k=2)
+    inp = bloch_inputs(spec)
+    o = oracle.System(spec, inp, xc=0)
+    A = np.array([0.07, -0.05, 0.11])
+    d = 1e-4
+    fd = np.array([(o.band_energy(A + d * e, inp.psi0) - o.band_energy(A - d * e, inp.psi0)) / (2 * d)
+                   for e in np.eye(3)])
+    full, local = o.velocity(A, inp.psi0), o.velocity(A, inp.psi0, with_nonlocal=False)
+    scale = np.abs(full).max()
+    assert np.abs(fd - full).max() < 1e-8 * scale
+    assert np.abs(fd - local).max() > 1e-2 * scale
+    # without projectors the commutator vanishes
+    o0 = oracle.System(spec, inp, xc=0, projectors=False)
+    np.testing.assert_array_equal(o0.velocity(A, inp.psi0), o0.velocity(A, inp.psi0, with_nonlocal=False))
+
+
+def test_recorded_current_is_the_local_velocity():
+    """The record's current is -(1/Omega) times the local velocity expectation at A(t_field)."""
+    from tests._util import bloch_cell, bloch_inputs
+    spec = bloch_cell(I.PREC_C128, n_k=2)
+    inp = bloch_inputs(spec)
+    o = oracle.System(spec, inp, xc=0)
+    obs = o.observables(inp.psi0, 0.0, 0.3)
+    _, A = o.field(0.3)
+    omega = spec.nx * spec.ny * spec.nz * spec.h ** 3
+    np.testing.assert_allclose(obs[4:7], -o.velocity(A, inp.psi0, with_nonlocal=False) / omega, rtol=1e-12,
+                               atol=1e-14)
