@@ -32,7 +32,6 @@
  */
 #include <complex.h>
 #include <math.h>
-#include <omp.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -843,6 +842,10 @@ double oracle_hartree(const oracle_sys *s, const double *n, double *vh) {
   for (long i = 0; i < N; i++) kadd(&e, 0.5 * n[i] * vh[i] * h3);
   return e.s;
 }
+
+/* OpenMP runtime calls (libgomp, linked by -fopenmp) */
+int omp_get_max_threads(void);
+void omp_set_num_threads(int n);
 
 /* Host threads of the oracle's parallel loops (for timing it on one core and on all);
  * returns the count in use before the call. */
