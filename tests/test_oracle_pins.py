@@ -867,3 +867,28 @@ def test_recorded_current_is_the_local_velocity():
     omega = spec.nx * spec.ny * spec.nz * spec.h ** 3
     np.testing.assert_allclose(obs[4:7], -o.velocity(A, inp.psi0, with_nonlocal=False) / omega, rtol=1e-12,
                                atol=1e-14)
+
+
+def test_hartree_cell_sum_equals_a_zero_padded_fft_convolution():
+    """The box's cell sum is a linear convolution with the sampled kernel (1/|d|, c0/h at
+    d = 0), so a zero-padded FFT convolution (Hockney) reproduces it to rounding: the method a
+    GPU kernel can use, checked here with numpy's FFT on a random density."""
+    spec = _spec(nx=9, ny=8, nz=7, h=0.3, n_orb=1, xc=0)
+    o = oracle.System(spec, I.make_inputs(spec, with_orbitals=False))
+    rng = np.random.default_rng(21)
+    n = rng.random((spec.nz, spec.ny, spec.nx))
+    shape = (2 * spec.nz, 2 * spec.ny, 2 * spec.nx)
+    idx = [np.where(np.arange(m) < m // 2, np.arange(m), np.arange(m) - m) for m in shape]
+    dz, dy, dx = np.meshgrid(*idx, indexing="ij")
+    dist = spec.h * np.sqrt(dx * dx + dy * dy + dz * dz)
+    kern = np.where(dist > 0, 1.0 / np.where(dist > 0, dist, 1.0), oracle.hartree_self_cell() / spec.h)
+    # offsets of magnitude n along an axis never occur inside the box; keep them out of the wrap
+    for ax, m in enumerate(shape):
+        sl = [slice(None)] * 3
+        sl[ax] = m // 2
+        kern[tuple(sl)] = 0.0
+    pad = np.zeros(shape)
+    pad[:spec.nz, :spec.ny, :spec.nx] = n
+    conv = np.fft.irfftn(np.fft.rfftn(pad) * np.fft.rfftn(kern), s=shape, axes=(0, 1, 2))[:spec.nz, :spec.ny, :spec.nx]
+    _, vh = o.hartree(n.ravel())
+    np.testing.assert_allclose(vh, conv.ravel() * spec.h ** 3, rtol=1e-12, atol=1e-12 * np.abs(vh).max())
