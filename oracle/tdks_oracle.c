@@ -27,8 +27,10 @@
  * outermost independent loop.
  *
  * Layout: orbitals are complex doubles, index [k][z][y][x][orb] (state index innermost,
- * Sec. "Memory layout").  Parity with the paper itself is unpinned: the paper prints no
- * number for this path.
+ * Sec. "Memory layout").  Every function is pinned, in tests/test_oracle_pins.py, by closed
+ * forms, invariants, brute force or library routines.  The paper prints no worked-example
+ * numbers for this path; the printed values used as pins are the CFM4 constants and (through
+ * the cited literature) the finite-difference weights, both under tests/golden/.
  */
 #include <complex.h>
 #include <math.h>
