@@ -45,20 +45,20 @@ def _host_doubles(ptr: int, n: int) -> np.ndarray:
     return np.ctypeslib.as_array((ctypes.c_double * n).from_address(ptr))
 
 
-def allreduce_exchange(group=None, device: Optional[str] = None):
+def allreduce_exchange(group=None, device: str = "cuda"):
     """Exchange hook for ``System.set_exchange``: the sum over the ranks of ``group``
     (torch.distributed; default group if None), in place.
 
-    device: "cuda" (default when CUDA is available) for the library's device buffers: the
-    allreduce is issued with the library's stream as the current stream, so it starts after
-    the kernels that wrote the buffer and the library's later kernels wait for it.  "cpu" for
-    buffers in host memory (a host-side hook, e.g. over gloo).
+    device: "cuda" (the library's buffers, which are device memory): the allreduce is issued
+    with the library's stream as the current stream, so it starts after the kernels that wrote
+    the buffer and the library's later kernels wait for it.  "cpu": buffers in host memory, for
+    a hook driven from host code (e.g. over gloo); never for the library's own buffers.
     """
     import torch
     import torch.distributed as dist
 
-    if device is None:
-        device = "cuda" if torch.cuda.is_available() else "cpu"
+    if device not in ("cuda", "cpu"):
+        raise ValueError("device must be 'cuda' or 'cpu'")
 
     def fn(ptr: int, n: int, stream: Optional[int]) -> None:
         if device == "cpu":
