@@ -283,6 +283,20 @@ int tdks_launch_count(tdks_sys sys, long long *count);
  * the energy and current sums. */
 int tdks_set_tile(tdks_sys sys, int tx, int ty, int zc);
 
+/*
+ * Bound of every wait in the warp-specialised TMA sweeps, in GPU clock cycles (clock64);
+ * 0 restores the default of 4e9 cycles (~2 s).  A wait that runs out (a copy that does not
+ * land, a ring slot that is not released, a claimed work item that does not arrive) makes
+ * its CTA give up: the CTA's other warps stop at their next wait, the producer waits (for
+ * at most ~0.1 s each) for its copies in flight, the error word is set, and the next
+ * synchronising call (tdks_reductions, tdks_get_orbitals, tdks_observe, tdks_autotune)
+ * returns TDKS_ETIMEOUT and clears it; the orbitals are then undefined until set again.
+ * No passage of the paper defines this: it is the library's failure detection, and a
+ * small limit makes the failure path run without any fault (tests).  Synchronises the
+ * system's stream; applies to launches made after the call (batches: created after it).
+ */
+int tdks_set_wait_limit(tdks_sys sys, long long cycles);
+
 /* Stencil sweep implementation: 0 (default) streams the input planes with TMA bulk
  * tensor copies where that applies (finite boxes, 16x8 tiles) into a warp-specialised
  * kernel (one producer warp, eight consumer warps); 1 always uses the general sweep (loads
@@ -383,6 +397,16 @@ int tdks_batch_destroy(tdks_batch_t batch);
  */
 int tdks_apply_H_noalloc(int nx, int ny, int nz, double h, int fd_order, int prec, int n_orb,
                          const double *dev_vloc, const void *dev_in, void *dev_out, void *stream);
+
+/*
+ * Fused multiply-add throughput of the current device, measured by the library's own probe
+ * kernel: prec = TDKS_C128 for FP64 FMAs, TDKS_C64 for FP32 ones; *fma_per_s receives FMA
+ * instructions (thread-level) per second, 2 FLOP each.  The paper has no counterpart: it
+ * gives the denominator of the complex128 path's roofline, whose stencil sweeps are bound
+ * by the FP64 pipe rather than by HBM on GPUs with a low FP64 rate.  Allocates a small
+ * buffer, runs on the legacy default stream and synchronises.
+ */
+int tdks_fma_rate(int prec, double *fma_per_s);
 
 const char *tdks_last_error(void);
 

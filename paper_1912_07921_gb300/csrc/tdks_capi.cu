@@ -198,6 +198,9 @@ void sweep_common(const tdks_system *s, SweepParams &p, const double A[3], int s
   set_coef(p, 1.0, 0.0);
   p.aux = s->aux;
   p.has_proj = s->n_atoms > 0;
+  p.pbox = s->d_pbox;
+  p.n_pbox = s->d_pbox ? s->n_atoms : 0;
+  p.wait_limit = s->wait_limit;
   p.nl = s->d_nl;
   p.n_ent = s->n_ent;
   p.kvec = s->d_kvec;
@@ -445,7 +448,8 @@ void free_proj(tdks_system *s) {
   cudaFree(s->d_ent); cudaFree(s->d_q); cudaFree(s->d_D); cudaFree(s->d_qpart);
   cudaFree(s->d_ent_beta); cudaFree(s->d_ent_ca);
   s->d_ent_beta = nullptr; s->d_ent_ca = nullptr;
-  cudaFree(s->d_sp); cudaFree(s->d_nl);
+  cudaFree(s->d_sp); cudaFree(s->d_nl); cudaFree(s->d_pbox);
+  s->d_pbox = nullptr;
   s->d_rowent = s->d_atom_begin = nullptr;
   s->d_sp = nullptr; s->d_nl = nullptr;
   s->n_sp = s->n_ent = 0;
@@ -670,6 +674,7 @@ int tdks_set_atoms_projectors(tdks_sys s, int n_atoms, const double *pos, const 
   const int n[3] = {s->nx, s->ny, s->nz};
   std::vector<ProjEntry> ent;
   std::vector<int> atom_begin(n_atoms + 1, 0);
+  std::vector<int> pbox(6 * (size_t)n_atoms);  // sphere bounding boxes, for the sweeps' item test
   double vnl = 0.0;
   const double h3 = s->h * s->h * s->h;
   for (int a = 0; a < n_atoms; a++) {
@@ -685,6 +690,21 @@ int tdks_set_atoms_projectors(tdks_sys s, int n_atoms, const double *pos, const 
         lo[ax] = (int)std::floor((R[ax] - r_cut) / s->h) - 1;
         hi[ax] = (int)std::ceil((R[ax] + r_cut) / s->h) + 1;
       }
+      // the box the sweeps test work items against: clipped to a finite box; in a periodic
+      // cell its start taken into [0, n) (the whole axis when it spans the cell)
+      int blo = lo[ax], bhi = hi[ax];
+      if (s->bc != TDKS_BC_ZERO) {
+        if (bhi - blo + 1 >= n[ax]) {
+          blo = 0;
+          bhi = n[ax] - 1;
+        } else {
+          const int w = ((blo % n[ax]) + n[ax]) % n[ax];
+          bhi += w - blo;
+          blo = w;
+        }
+      }
+      pbox[6 * a + 2 * ax] = blo;
+      pbox[6 * a + 2 * ax + 1] = bhi;
     }
     double nb[4] = {0, 0, 0, 0};
     for (int iz = lo[2]; iz <= hi[2]; iz++)
@@ -770,6 +790,8 @@ int tdks_set_atoms_projectors(tdks_sys s, int n_atoms, const double *pos, const 
     CU(cudaMemcpy(s->d_ent_ca, eca.data(), ent.size() * sizeof(int2), cudaMemcpyHostToDevice));
   }
   CU(cudaMemcpy(s->d_D, D, (size_t)n_atoms * 4 * sizeof(double), cudaMemcpyHostToDevice));
+  CU(cudaMalloc((void **)&s->d_pbox, pbox.size() * sizeof(int)));
+  CU(cudaMemcpy(s->d_pbox, pbox.data(), pbox.size() * sizeof(int), cudaMemcpyHostToDevice));
   s->n_atoms = n_atoms;
   s->pos.assign(pos, pos + 3 * n_atoms);
   s->D.assign(D, D + 4 * n_atoms);
@@ -826,6 +848,14 @@ int tdks_set_tile(tdks_sys s, int tx, int ty, int zc) {
   CU(cudaStreamSynchronize(s->stream));
   s->tx = tx; s->ty = ty; s->zc = zc;
   build_tmaps(s);
+  return TDKS_OK;
+}
+
+int tdks_set_wait_limit(tdks_sys s, long long cycles) {
+  if (!s) return fail(TDKS_EINVAL, "NULL system");
+  if (cycles < 0) return fail(TDKS_EINVAL, "cycles < 0");
+  CU(cudaStreamSynchronize(s->stream));
+  s->wait_limit = cycles > 0 ? cycles : DEFAULT_WAIT_LIMIT_CYCLES;
   return TDKS_OK;
 }
 

@@ -69,6 +69,24 @@ struct Reader {
 constexpr size_t CHUNK = 64u << 20;  // device <-> host staging per copy
 
 // Device array -> file, through a host buffer of at most CHUNK bytes.
+// The ring positions of `count` consecutive records starting at step `from`: at most two
+// contiguous spans (the second where the ring wraps); `first` is the span's offset among
+// the records.
+struct RingSpan {
+  long long first, slot, count;
+};
+std::vector<RingSpan> ring_spans(long long from, long long count) {
+  std::vector<RingSpan> out;
+  long long done = 0;
+  while (done < count) {
+    const long long slot = (from + done) % tdks_system::RING;
+    const long long n = std::min(count - done, tdks_system::RING - slot);
+    out.push_back(RingSpan{done, slot, n});
+    done += n;
+  }
+  return out;
+}
+
 int put_device(Writer &w, const void *dev, size_t bytes, cudaStream_t st, std::vector<unsigned char> &buf) {
   buf.resize(std::min(bytes, CHUNK));
   for (size_t off = 0; off < bytes; off += CHUNK) {
@@ -132,11 +150,10 @@ int tdks_save(tdks_sys s, const char *path) {
     w.put(s->kpts.data(), s->kpts.size() * sizeof(double));
     w.put(s->kw.data(), s->kw.size() * sizeof(double));
     CU(cudaMemcpyAsync(vloc.data(), s->vloc, s->N * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
-    for (long long i = 0; i < n_rec; i++) {  // records of steps [steps - n_rec, steps), in order
-      const long long slot = (s->steps - n_rec + i) % tdks_system::RING;
-      CU(cudaMemcpyAsync(recs.data() + i * TDKS_RECORD, s->ring + slot * TDKS_RECORD, TDKS_RECORD * sizeof(double),
-                         cudaMemcpyDeviceToHost, s->stream));
-    }
+    // records of steps [steps - n_rec, steps), in order: at most two contiguous spans of the ring
+    for (const RingSpan &sp : ring_spans(s->steps - n_rec, n_rec))
+      CU(cudaMemcpyAsync(recs.data() + sp.first * TDKS_RECORD, s->ring + sp.slot * TDKS_RECORD,
+                         sp.count * TDKS_RECORD * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     CU(cudaStreamSynchronize(s->stream));
     w.put(vloc.data(), vloc.size() * sizeof(double));
     w.put(s->pos.data(), s->pos.size() * sizeof(double));
@@ -214,11 +231,9 @@ int tdks_load(const char *path, void *stream, tdks_sys *out) {
     if (r.ok) r.ok = std::fread(&want, sizeof want, 1, r.f) == 1;
     if (!r.ok) return fail(TDKS_EINVAL, "checkpoint file is truncated");
     if (want != got) return fail(TDKS_EINVAL, "checkpoint checksum mismatch (corrupt file)");
-    for (long long i = 0; i < nrec; i++) {
-      const long long slot = (hi[H_STEPS] - nrec + i) % tdks_system::RING;
-      CU(cudaMemcpyAsync(s->ring + slot * TDKS_RECORD, recs.data() + i * TDKS_RECORD, TDKS_RECORD * sizeof(double),
-                         cudaMemcpyHostToDevice, s->stream));
-    }
+    for (const RingSpan &sp : ring_spans(hi[H_STEPS] - nrec, nrec))
+      CU(cudaMemcpyAsync(s->ring + sp.slot * TDKS_RECORD, recs.data() + sp.first * TDKS_RECORD,
+                         sp.count * TDKS_RECORD * sizeof(double), cudaMemcpyHostToDevice, s->stream));
     CU(cudaStreamSynchronize(s->stream));
     s->n_hist = (int)nh;
     s->steps = hi[H_STEPS];

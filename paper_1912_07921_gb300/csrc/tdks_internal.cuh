@@ -38,6 +38,9 @@ inline cudaError_t ensure_smem_attr(K k, size_t smem, std::atomic<unsigned> &don
 }
 
 constexpr int OVC = 4;        // 16-byte vectors per (point, batch)
+// Default bound of every wait in the TMA sweeps (clock64 cycles, ~2 s at 2 GHz): a wait that
+// runs out makes the CTA give up and the host report TDKS_ETIMEOUT.
+constexpr long long DEFAULT_WAIT_LIMIT_CYCLES = 4000000000LL;
 constexpr int MAXM = 4;       // largest FD half-width (8th order)
 
 enum Mode { MODE_FIRST = 0, MODE_MID = 1, MODE_LAST = 2 };
@@ -81,6 +84,10 @@ struct SweepParams {
   const PointAux *aux;        // [N] V_eff and projector entry ranges
   // projectors
   int has_proj;               // the system has projector entries
+  const int *pbox;            // [n_pbox][6] per-atom sphere bounding boxes in grid indices (lo, hi
+                              // per axis; periodic cells: lo in [0, n), taken modulo the cell), or
+                              // NULL; a work item that meets none of them has no non-local term
+  int n_pbox;
   const void *nl;             // [kb][n_ent + 1][OVC] vectors: sum_aj beta_aj(r) phase q_aj at the
                               // sphere point whose entries start at r0; row n_ent is zero
   int n_ent;                  // projector entries
@@ -97,6 +104,7 @@ struct SweepParams {
   double *dens_part;          // [n_kb][N] (MODE_LAST): w_k f sum |psi|^2 (complex128); for
                               // complex64, the unweighted sum as a (float hi, float lo) pair
   int *err;                   // device error word (bounded waits that ran out set it)
+  long long wait_limit;       // bound of each wait of the TMA sweeps (clock64 cycles)
   unsigned int *work;         // work-item counter of the warp-specialised TMA sweep (zero
                               // between launches: the launch's last claim resets it)
 };

@@ -119,10 +119,11 @@ extern "C" int tdks_apply_H_noalloc(int nx, int ny, int nz, double h, int fd_ord
   else
     e = launch_sweep(M, prec, MODE_MID, 0, s.tx, s.ty, p, 0, st);
   if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("stencil sweep: ") + cudaGetErrorString(e));
-  // wait for the result and report a sweep that gave up waiting for its copies
-  CU(cudaStreamSynchronize(st));
+  // wait for the result and report a sweep that gave up waiting for its copies; the error
+  // word is read on the caller's stream, so no other stream of the device is waited for
   int h_err = 0;
-  CU(cudaMemcpy(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost));
+  CU(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
   if (h_err) return fail(TDKS_ETIMEOUT, "the sweep gave up waiting for its TMA copies");
   return TDKS_OK;
 }

@@ -92,6 +92,30 @@ __device__ __forceinline__ const typename VT<P>::V *nl_column(const SweepParams 
   return reinterpret_cast<const typename VT<P>::V *>(p.nl) + (long)kb * (p.n_ent + 1) * OVC + v;
 }
 
+// Whether the grid interval [t0, t1) meets [lo, hi] (periodic cells: also its image one
+// cell to the left, as lo lies in [0, n)).
+__device__ __forceinline__ bool span_meets(int lo, int hi, int t0, int t1, int n, bool wrap) {
+  return (lo < t1 && hi >= t0) || (wrap && lo - n < t1 && hi - n >= t0);
+}
+
+// Whether a work item's points [x0, x0 + tx) x [y0, y0 + ty) x [z0, z1) can lie in a
+// projector sphere: the non-local term is read only for such items (for all the others it
+// is zero, so skipping its loads changes no value).  One thread tests the atoms' bounding
+// boxes.
+__device__ __forceinline__ bool item_meets_spheres(const SweepParams &p, int x0, int tx, int y0, int ty, int z0,
+                                                   int z1) {
+  if (!p.has_proj) return false;
+  if (!p.pbox) return true;
+  const bool wrap = p.bloch != 0;
+  for (int a = 0; a < p.n_pbox; a++) {
+    const int *b = p.pbox + 6 * a;
+    if (span_meets(b[0], b[1], x0, x0 + tx, p.nx, wrap) && span_meets(b[2], b[3], y0, y0 + ty, p.ny, wrap) &&
+        span_meets(b[4], b[5], z0, z1, p.nz, wrap))
+      return true;
+  }
+  return false;
+}
+
 // Own-point operands of the last sweep (state parts and earlier terms).
 template <int P> struct LastOperands {
   typename VT<P>::V hi, lo, t1, t2;

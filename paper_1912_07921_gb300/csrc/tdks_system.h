@@ -57,6 +57,7 @@ struct tdks_system {
   int *d_rowent = nullptr, *d_atom_begin = nullptr;
   int2 *d_sp = nullptr;       // entry ranges of the points inside a sphere
   void *d_nl = nullptr;       // non-local term per sphere point, [n_kb][n_ent + 1][OVC]
+  int *d_pbox = nullptr;      // [n_atoms][6] bounding boxes of the spheres (grid indices)
   int n_sp = 0, n_ent = 0;
   tdks::ProjEntry *d_ent = nullptr;
   float4 *d_ent_beta = nullptr;  // compact copies of the entries' FP32 beta and (cell, atom)
@@ -71,6 +72,7 @@ struct tdks_system {
   bool staging_pending = false;            // ev_staging_free has been recorded
   std::vector<cudaEvent_t> ev_chunk;
   int *d_err = nullptr;       // [0]: error word of the bounded waits; [1]: sweep work counter
+  long long wait_limit = tdks::DEFAULT_WAIT_LIMIT_CYCLES;  // bound of each TMA-sweep wait (cycles)
   long obs_count = 0;         // energy/current partial records written by the last first sweep
   // TMA tensor maps over the four sweep inputs (state, t1, t2, t3) for the current tile
   tdks::SweepMaps smaps[4];   // TMA maps of the four Taylor-term sweeps

@@ -61,15 +61,18 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
-// Consumer wait: bounded, and gives up at once when another warp has given up.
-__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *bar, uint32_t parity, const volatile int *abort) {
+// Consumer wait: bounded by `limit` cycles, and gives up soon after another warp has given
+// up.  The abort flag and the clock are read once every 16 failed polls (each try_wait
+// already suspends the thread for a while), so a waiting warp adds almost no shared-memory
+// loads to those of the warps that compute.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *bar, uint32_t parity, const volatile int *abort,
+                                                   const long long *limit) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
-    if (*abort) return false;
-    if (clock64() - t0 > WAIT_LIMIT_CYCLES) return false;
+  for (unsigned i = 1;; i++) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 15u) == 0u && (*abort || clock64() - t0 > *limit)) return false;
   }
-  return true;
 }
 __device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *tmap, uint64_t *bar, int c0, int c1,
                                             int c2, int c3, int c4) {
@@ -166,6 +169,7 @@ struct SingleSrc {
   __device__ __forceinline__ int sys_of(long) const { return 0; }
   __device__ __forceinline__ const SweepMaps *maps_of(int) const { return maps; }
   __device__ __forceinline__ int *err0() const { return p->err; }
+  __device__ __forceinline__ long long wait_limit() const { return p->wait_limit; }
 };
 
 __device__ __forceinline__ int find_item_sys(const long *begin, int n, long u) {
@@ -189,6 +193,7 @@ struct BatchSrc {
   __device__ __forceinline__ int sys_of(long it) const { return find_item_sys(a->item_begin, a->n_sys, it); }
   __device__ __forceinline__ const SweepMaps *maps_of(int s) const { return a->maps + 4 * s + a->which; }
   __device__ __forceinline__ int *err0() const { return a->params[0].err; }
+  __device__ __forceinline__ long long wait_limit() const { return a->params[0].wait_limit; }
 };
 
 // Sequential cursor over one kind of load of the CTA's items (thread 0 only).  The item's
@@ -478,8 +483,11 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
   __shared__ __align__(8) uint64_t ofull[SO], oempty[SO];
   __shared__ __align__(8) uint64_t ibar[IR];  // completes when s_item[seq % IR] is written
   __shared__ long s_item[IR];                 // item of the CTA's seq-th claim (-1: no more)
+  __shared__ int s_nl[IR];                    // whether that item can meet a projector sphere
   __shared__ int s_abort;
+  __shared__ long long s_wlim;  // cycles any one wait may take before the CTA gives up
   volatile int *abort_flag = &s_abort;
+  const long long *wlim = &s_wlim;
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
@@ -493,6 +501,7 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
     for (int s = 0; s < SO; s++) { mbar_init(&ofull[s], 1); mbar_init(&oempty[s], CW); }
     for (int s = 0; s < IR; s++) mbar_init(&ibar[s], 1);
     s_abort = 0;
+    s_wlim = src.wait_limit();
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();  // the only CTA-wide barrier: from here on the warps run decoupled
@@ -517,6 +526,16 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
             // returns the counter to zero for the next launch
             if ((long)t == n_items_all + (long)gridDim.x - 1) atomicExch(work, 0u);
             s_item[claimed % IR] = (long)t < n_items_all ? (long)t : -1;
+            if ((long)t < n_items_all) {
+              // the consumers read the non-local term only in items that can meet a sphere
+              const SweepParams *qp = nullptr;
+              const SweepMaps *mq = nullptr;
+              long local = 0;
+              src.item((long)t, qp, mq, local);
+              int tx0, ty0, kb0, za, zb;
+              item_geom(*qp, local, tx0, ty0, kb0, za, zb);
+              s_nl[claimed % IR] = item_meets_spheres(*qp, tx0 * TX, TX, ty0 * TY, TY, za, zb);
+            }
             mbar_arrive(&ibar[claimed % IR]);
             claimed++;
           }
@@ -563,7 +582,7 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
         if (progressed) {
           idle_since = clock64();
         } else {
-          if (*abort_flag || clock64() - idle_since > WAIT_LIMIT_CYCLES) {
+          if (*abort_flag || clock64() - idle_since > *wlim) {
             *abort_flag = 1;
             break;
           }
@@ -590,7 +609,7 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
     // slot to the consumers -----------------------------------------------------------------
     RingPos rp;
     for (long seq = 0;; seq++) {
-      if (!mbar_wait_or_abort(&ibar[seq % IR], (uint32_t)((seq / IR) & 1), abort_flag)) {
+      if (!mbar_wait_or_abort(&ibar[seq % IR], (uint32_t)((seq / IR) & 1), abort_flag, wlim)) {
         *abort_flag = 1;
         break;
       }
@@ -616,7 +635,7 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
       bool gave_up = false;
       for (int z = z0; z < z1; z++) {
         const int hs = rp.slot;
-        if (!mbar_wait_or_abort(&hfull[hs], rp.phase, abort_flag)) {
+        if (!mbar_wait_or_abort(&hfull[hs], rp.phase, abort_flag, wlim)) {
           gave_up = true;
           break;
         }
@@ -672,12 +691,13 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
   bool aborted = false;
   int *errp = src.err0();  // then the current item's system's
   for (long seq = 0;; seq++) {
-    if (!mbar_wait_or_abort(&ibar[seq % IR], (uint32_t)((seq / IR) & 1), abort_flag)) {
+    if (!mbar_wait_or_abort(&ibar[seq % IR], (uint32_t)((seq / IR) & 1), abort_flag, wlim)) {
       aborted = true;
       break;
     }
     const long item = s_item[seq % IR];
     if (item < 0) break;
+    const bool has_proj = s_nl[seq % IR] != 0;
     const SweepParams *pp;
     const SweepMaps *mp_unused;
     long local;
@@ -696,7 +716,7 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
     item_geom(p, local, tx, ty, kb, z0, z1);
     const int kidx = kb / p.n_batches;
     const Epi epi = make_epi(p, kidx);
-    const bool has_proj = p.has_proj != 0, do_obs = p.do_obs != 0;
+    const bool do_obs = p.do_obs != 0;
     const V *nlk = nl_column<P>(p, kb, v);
     const int n_ent = p.n_ent;
     const int gx = tx * TX + lx, gy0 = ty * TY + ly0;
@@ -726,7 +746,7 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
     auto iteration = [&](auto rq) {
       constexpr int RQ = decltype(rq)::value;
       const int cs = rc.slot;
-      if (!mbar_wait_or_abort(&cfull[cs], rc.phase, abort_flag)) {
+      if (!mbar_wait_or_abort(&cfull[cs], rc.phase, abort_flag, wlim)) {
         aborted = true;
         return;
       }
@@ -752,7 +772,7 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
         const int zf = z0 + U * (l - LP);
         const int hs = rh.slot;
         // periodic cells: the slot is ready once the patcher warp has written the face images
-        if (!mbar_wait_or_abort(BLOCH ? &hready[hs] : &hfull[hs], rh.phase, abort_flag)) {
+        if (!mbar_wait_or_abort(BLOCH ? &hready[hs] : &hfull[hs], rh.phase, abort_flag, wlim)) {
           aborted = true;
           return;
         }
@@ -763,7 +783,7 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
         int os = 0;
         if constexpr (OPS) {
           os = ro.slot;
-          if (!mbar_wait_or_abort(&ofull[os], ro.phase, abort_flag)) {
+          if (!mbar_wait_or_abort(&ofull[os], ro.phase, abort_flag, wlim)) {
             aborted = true;
             return;
           }

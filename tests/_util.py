@@ -48,3 +48,29 @@ def small_uneven_batch(prec, n=5, seed=7):
                                 amp=0.01 * (i + 1), omega=0.2, envelope=I.ENV_SIN2 if i % 2 else I.ENV_NONE,
                                 t_total=0.5, dt=0.015, substeps=1, seed=(seed << 8) + i))
     return out
+
+
+def horizon_molecule(prec):
+    """The medium molecule's physics on a smaller grid, for the 1000-step FP32 check: order-8
+    FD at h = 0.25 on 32^3, 8 orbitals, 16 atoms with Gaussian wells and 4 Kleinman-Bylander
+    projectors each, LDA exchange, the sin^2 pulse E0 = 0.005, omega = 0.057 over T = 1000 dt,
+    dt = 0.05 as 4 Taylor-4 sub-steps."""
+    return I.medium_molecule(prec=prec, nx=32, ny=32, nz=32, n_orb=8, n_steps=1000)
+
+
+def horizon_cell(prec):
+    """The periodic cell's physics on a smaller grid, for the 1000-step FP32 check: side
+    10.2 bohr on 32^3 (h = 0.319), order-4 FD, 8 diamond atoms with wells and projectors,
+    2 seeded k-points x 8 bands, velocity gauge A0 = 0.2, omega = 0.03, dt = 0.04 as 2
+    Taylor-4 sub-steps (the automatic count at this spacing)."""
+    return I.periodic_cell(n_k=2, prec=prec, nx=32, ny=32, nz=32, h=10.2 / 32, n_orb=8, n_steps=1000,
+                           substeps=2)
+
+
+HORIZON_CASES = {"molecule": horizon_molecule, "cell": horizon_cell}
+
+
+def read_horizon_golden(path):
+    """Records [n_steps, 8] of a stored oracle trajectory (see make_fp32_horizon.py)."""
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    return np.array([[float(x) for x in r[1:]] for r in rows])

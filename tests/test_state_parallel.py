@@ -127,3 +127,60 @@ def test_two_gloo_ranks_reproduce_the_whole_system():
         assert g["band"] == pytest.approx(band_full, rel=1e-12)
         ref = stepped[..., g["lo"]:g["hi"]]
         assert np.max(np.abs(g["psi"] - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def _leaving_rank_main(rank, world, port, out):
+    """Rank 1 leaves between two exchanges (no collective in flight); rank 0 keeps going."""
+    import datetime
+    import time
+    sys.path.insert(0, ROOT)
+    import oracle
+    from paper_1912_07921_gb300 import _lib, inputs as I
+    from paper_1912_07921_gb300.sharding import allreduce_exchange
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=5))
+    spec = _spec()
+    inp = I.make_inputs(spec)
+    lo, hi = state_slice(spec.n_orb, rank, world, 2)
+    mine = oracle.System(dataclasses.replace(spec, n_orb=hi - lo), inp)
+    psi = np.ascontiguousarray(inp.psi0[..., lo:hi])
+    fn = allreduce_exchange(device="cpu")
+
+    def hook(ptr, n, stream, ctx):  # as System.set_exchange wraps it: an exception is a status
+        try:
+            fn(ptr, n, stream)
+            return 0
+        except Exception:
+            return 1
+
+    cb = _lib.EXCHANGE_FN(hook)
+    call = ctypes.cast(cb, _lib.EXCHANGE_FN)
+    log = []
+    for step in range(3):
+        if rank == 1 and step == 1:
+            os._exit(0)  # leaves between steps
+        n = np.ascontiguousarray(mine.density(psi).ravel())
+        t0 = time.time()
+        st = call(n.ctypes.data, n.size, None, None)
+        log.append((st, time.time() - t0))
+    out[rank] = log
+    try:
+        dist.destroy_process_group()
+    except Exception:
+        pass
+
+
+def test_rank_that_leaves_makes_the_survivor_fail_not_hang():
+    """The exchange of the survivor's next step fails (status 1, which the library turns into
+    TDKS_EDEVICE) within the process group's timeout, and so does every later one."""
+    world = 2
+    port = _free_port()
+    with mp.get_context("spawn").Manager() as m:
+        out = m.dict()
+        mp.spawn(_leaving_rank_main, args=(world, port, out), nprocs=world, join=True)
+        got = dict(out)
+    assert set(got) == {0}
+    statuses = [st for st, _ in got[0]]
+    assert statuses == [0, 1, 1], got[0]
+    assert all(sec < 30.0 for _, sec in got[0])
