@@ -284,18 +284,20 @@ int tdks_launch_count(tdks_sys sys, long long *count);
 int tdks_set_tile(tdks_sys sys, int tx, int ty, int zc);
 
 /*
- * Bound of every wait in the warp-specialised TMA sweeps, in GPU clock cycles (clock64);
- * 0 restores the default of 4e9 cycles (~2 s).  A wait that runs out (a copy that does not
- * land, a ring slot that is not released, a claimed work item that does not arrive) makes
- * its CTA give up: the CTA's other warps stop at their next wait, the producer waits (for
- * at most ~0.1 s each) for its copies in flight, the error word is set, and the next
- * synchronising call (tdks_reductions, tdks_get_orbitals, tdks_observe, tdks_autotune)
- * returns TDKS_ETIMEOUT and clears it; the orbitals are then undefined until set again.
- * No passage of the paper defines this: it is the library's failure detection, and a
- * small limit makes the failure path run without any fault (tests).  Synchronises the
- * system's stream; applies to launches made after the call (batches: created after it).
+ * Failure detection of the warp-specialised TMA sweeps.  Every wait in them is bounded by
+ * `cycles` GPU clock cycles (clock64; 0 restores the default of 4e9, ~2 s).  A wait that runs
+ * out (a copy that does not land, a ring slot that is not released, a claimed work item that
+ * does not arrive) makes its CTA give up: its other warps stop at their next wait, its
+ * producer waits (at most ~0.1 s each) for the copies it has in flight, the error word is
+ * set, and the next synchronising call (tdks_reductions, tdks_get_orbitals, tdks_observe,
+ * tdks_autotune) returns TDKS_ETIMEOUT and clears it; the orbitals are then undefined until
+ * set again.  withhold = 1 injects that failure for tests: the sweeps' producer warps make no
+ * claim and issue no copy, so every consumer's first wait runs out after `cycles` (nothing is
+ * read or written by those sweeps).  No passage of the paper defines this: it is the
+ * library's own failure handling.  Synchronises the system's stream; applies to launches
+ * made after the call (batches: to batches created after it).
  */
-int tdks_set_wait_limit(tdks_sys sys, long long cycles);
+int tdks_set_wait_limit(tdks_sys sys, long long cycles, int withhold);
 
 /* Stencil sweep implementation: 0 (default) streams the input planes with TMA bulk
  * tensor copies where that applies (finite boxes, 16x8 tiles) into a warp-specialised

@@ -77,6 +77,9 @@ def _load():
         _lib.oracle_band_energy.restype = D
         _lib.oracle_velocity_expectation.argtypes = [S, P, P, I, P]
         _lib.oracle_set_threads.restype = I
+        _lib.oracle_tsurff_flux.argtypes = [S, P, I, P, P, P, D, D, P, P]
+        _lib.oracle_volkov_step.argtypes = [S, D, D, P]
+        _lib.oracle_tsurff_propagate.argtypes = [S, P, I, P, D, D, I, I, P, P, P, P, P]
         _lib.oracle_hartree_self_cell.restype = D
     return _lib
 
@@ -234,6 +237,43 @@ class System:
         self.lib.oracle_propagate_rk4(self.ref, t0, dt, n_steps, substeps, _ptr(psi),
                                       _ptr(obs) if record else None)
         return psi, obs
+
+    def tsurff_flux(self, psi, box, p, a=(0.0, 0.0, 0.0), alpha=(0.0, 0.0, 0.0), beta=0.0, t_rel=0.0):
+        """t-SURFF flux F[i, p] = oint_S n . <chi_p| j |phi_i> ds of the orbitals psi through the
+        box surface `box` = (i0, i1, j0, j1, k0, k1) (grid planes), for momenta p [n_p, 3], with
+        the Volkov parameters a(t), alpha(t), beta(t) and the time t_rel since the accumulation
+        started.  Finite boxes, one k-point."""
+        psi = self._psi(psi)
+        box = np.ascontiguousarray(box, dtype=np.int32)
+        p = np.ascontiguousarray(p, dtype=np.float64).reshape(-1, 3)
+        a, alpha = np.ascontiguousarray(a, dtype=np.float64), np.ascontiguousarray(alpha, dtype=np.float64)
+        F = np.zeros((self.spec.n_orb, p.shape[0]), dtype=np.complex128)
+        self.lib.oracle_tsurff_flux(self.ref, _ptr(box), p.shape[0], _ptr(p), _ptr(a), _ptr(alpha), float(beta),
+                                    float(t_rel), _ptr(psi), _ptr(F))
+        return F
+
+    def volkov_step(self, vol, t, dt):
+        """(a, alpha, beta) = vol[0:3], vol[3:6], vol[6] advanced from t to t + dt (RK4)."""
+        vol = np.ascontiguousarray(vol, dtype=np.float64).copy()
+        self.lib.oracle_volkov_step(self.ref, t, dt, _ptr(vol))
+        return vol
+
+    def propagate_tsurff(self, psi, t0, dt, n_steps, substeps, box, p, vol=None, t_rel=0.0, b=None, record=True):
+        """Taylor-4 propagation with the t-SURFF amplitudes b[i, p] accumulated by the trapezoid
+        rule over the configured steps.  Returns (psi, records, b, vol, t_rel); pass vol, t_rel
+        and b back in to continue an accumulation."""
+        psi = self._psi(psi).copy()
+        box = np.ascontiguousarray(box, dtype=np.int32)
+        p = np.ascontiguousarray(p, dtype=np.float64).reshape(-1, 3)
+        vol = np.zeros(7) if vol is None else np.ascontiguousarray(vol, dtype=np.float64).copy()
+        b = (np.zeros((self.spec.n_orb, p.shape[0]), dtype=np.complex128) if b is None
+             else np.ascontiguousarray(b, dtype=np.complex128).copy())
+        tr = ctypes.c_double(t_rel)
+        obs = np.empty((n_steps, 8)) if record else None
+        self.lib.oracle_tsurff_propagate(self.ref, _ptr(box), p.shape[0], _ptr(p), t0, dt, n_steps, substeps,
+                                         _ptr(psi), _ptr(obs) if record else None, _ptr(vol), ctypes.byref(tr),
+                                         _ptr(b))
+        return psi, obs, b, vol, tr.value
 
     def sphere_count(self, a: int) -> int:
         return self.lib.oracle_sphere_count(self.ref, a)

@@ -20,7 +20,9 @@
  *   - the macroscopic current J = -(i/Omega) int sum_i phi_i [H, r] phi_i
  *     (Sec. "Conductivities", eqn. current_density), local part;
  *   - the velocity-gauge field E = -dA/dt (same section);
- *   - closed-shell occupations f_i = 2 (Sec. "t-SURFF", closed shells).
+ *   - closed-shell occupations f_i = 2 (Sec. "t-SURFF", closed shells);
+ *   - the t-SURFF photoelectron amplitudes: the time integral of the Volkov-state
+ *     current through a surface (Sec. "t-SURFF", eqns. for chi_p, b_i and the current).
  * The exponential is a 4th-order Taylor series with H frozen over a (sub-)step; the
  * paper does not print this propagator, so the oracle takes the readings listed at each
  * function.  Everything is plain loops in double precision; OpenMP only splits the
@@ -937,4 +939,126 @@ void oracle_velocity_expectation(const oracle_sys *s, const double *A, const cpl
     }
   }
   for (int ax = 0; ax < 3; ax++) out[ax] = acc[ax].s;
+}
+
+/* --------------------------------------------------------------------------------
+ * t-SURFF flux (Sec. "t-SURFF": the photoelectron amplitude b_i(p, t) as the time
+ * integral of the current of the Volkov state chi_p and the orbital through a surface S
+ * that separates the inner region from the outer one).
+ *
+ * Readings (the section prints the velocity-gauge forms; finite systems here couple the
+ * field in the length gauge, +E(t).r):
+ *   - S is the surface of a box of grid planes x = x_i0, x_i1, y = y_j0, y_j1, z = z_k0,
+ *     z_k1 (the section leaves the shape of S free; planes of the grid need no
+ *     interpolation).  Each face is integrated with the two-dimensional trapezoid rule over
+ *     its grid points (weight h^2, halved on its edges, quartered at its corners) and
+ *     carries the outward unit normal n.
+ *   - Volkov states of the free length-gauge Hamiltonian -1/2 Lap + E(t).r:
+ *       chi_p(r, t) = (2 pi)^(-3/2) exp(i k_p(t).r - i Phi_p(t)),  k_p(t) = p + a(t),
+ *       a(t) = -int_0^t E,  Phi_p(t) = 1/2 int_0^t |k_p|^2 = 1/2 (|p|^2 t + 2 p.alpha(t) + beta(t)),
+ *       alpha(t) = int_0^t a,  beta(t) = int_0^t |a|^2;
+ *     (the printed phase lacks the 1/2 and has the opposite sign; only this form solves the
+ *     Volkov equation), with times counted from the start of the accumulation.
+ *   - the current matrix element is the length-gauge one (no vector-potential term):
+ *       <chi_p| j |phi> = 1/2 (i phi grad chi_p^* - i chi_p^* grad phi) = 1/2 chi_p^* (k_p phi - i grad_h phi),
+ *     with grad_h the central difference of order 2M (psi = 0 outside the box);
+ *   - b_i(p, T) = int_0^T F_i(p, t) dt, F_i = oint_S n . <chi_p| j |phi_i> ds with the outward
+ *     normal (the projection of phi_i on chi_p in the outer region, from the continuity
+ *     equation; the printed minus sign belongs to the inward normal).
+ * F_i(p) is returned as F[i * n_p + pidx]; one k-point (finite systems).
+ * ------------------------------------------------------------------------------ */
+void oracle_tsurff_flux(const oracle_sys *s, const int *box, int n_p, const double *p, const double *a,
+                        const double *alpha, double beta, double t_rel, const cplx *psi, cplx *F) {
+  const int M = s->fd_order / 2, B = s->n_orb;
+  const double h = s->h;
+  double d[5];
+  oracle_fd_gradient_weights(M, d);
+  const double pref = 0.5 * pow(2.0 * M_PI, -1.5);
+  for (long i = 0; i < (long)B * n_p; i++) F[i] = 0.0;
+  for (int face = 0; face < 6; face++) {
+    const int ax = face / 2;                 /* normal axis */
+    const double sgn = (face % 2) ? 1.0 : -1.0;
+    const int c = box[2 * ax + (face % 2)];  /* the face's plane index along ax */
+    const int ua = (ax + 1) % 3, va = (ax + 2) % 3;
+    for (int u = box[2 * ua]; u <= box[2 * ua + 1]; u++)
+      for (int v = box[2 * va]; v <= box[2 * va + 1]; v++) {
+        double w = h * h;
+        if (u == box[2 * ua] || u == box[2 * ua + 1]) w *= 0.5;
+        if (v == box[2 * va] || v == box[2 * va + 1]) w *= 0.5;
+        int ii[3];
+        ii[ax] = c;
+        ii[ua] = u;
+        ii[va] = v;
+        double r[3];
+        for (int q = 0; q < 3; q++) r[q] = coord(s, q, ii[q]);
+        for (int o = 0; o < B; o++) {
+          const cplx phi = fetch(s, psi, 0, o, ii[0], ii[1], ii[2]);
+          cplx g = 0.0;
+          for (int m = 1; m <= M; m++) {
+            int ip[3] = {ii[0], ii[1], ii[2]}, im[3] = {ii[0], ii[1], ii[2]};
+            ip[ax] += m;
+            im[ax] -= m;
+            g += d[m] * (fetch(s, psi, 0, o, ip[0], ip[1], ip[2]) - fetch(s, psi, 0, o, im[0], im[1], im[2]));
+          }
+          g /= h;
+          for (int q = 0; q < n_p; q++) {
+            const double *pp = p + 3 * q;
+            double kr = 0.0, phase = 0.5 * (pp[0] * pp[0] + pp[1] * pp[1] + pp[2] * pp[2]) * t_rel + 0.5 * beta;
+            for (int x = 0; x < 3; x++) {
+              kr += (pp[x] + a[x]) * r[x];
+              phase += pp[x] * alpha[x];
+            }
+            const cplx chi_conj = cexp(I * (phase - kr));
+            const double kn = pp[ax] + a[ax];
+            F[(long)o * n_p + q] += w * sgn * pref * chi_conj * (kn * phi - I * g);
+          }
+        }
+      }
+  }
+}
+
+/* a(t), alpha(t), beta(t) advanced over one step dt by the classical Runge-Kutta method on
+ * a' = -E(t), alpha' = a, beta' = |a|^2 (y = a[3], alpha[3], beta). */
+static void volkov_rhs(const oracle_sys *s, double t, const double *y, double *f) {
+  double E[3], A[3];
+  oracle_field(s, t, E, A);
+  for (int x = 0; x < 3; x++) {
+    f[x] = s->gauge == 1 ? -E[x] : 0.0;
+    f[3 + x] = y[x];
+  }
+  f[6] = y[0] * y[0] + y[1] * y[1] + y[2] * y[2];
+}
+void oracle_volkov_step(const oracle_sys *s, double t, double dt, double *y) {
+  double k1[7], k2[7], k3[7], k4[7], tmp[7];
+  volkov_rhs(s, t, y, k1);
+  for (int i = 0; i < 7; i++) tmp[i] = y[i] + 0.5 * dt * k1[i];
+  volkov_rhs(s, t + 0.5 * dt, tmp, k2);
+  for (int i = 0; i < 7; i++) tmp[i] = y[i] + 0.5 * dt * k2[i];
+  volkov_rhs(s, t + 0.5 * dt, tmp, k3);
+  for (int i = 0; i < 7; i++) tmp[i] = y[i] + dt * k3[i];
+  volkov_rhs(s, t + dt, tmp, k4);
+  for (int i = 0; i < 7; i++) y[i] += dt / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+}
+
+/* Taylor-4 propagation (as oracle_propagate) with the t-SURFF amplitudes accumulated by the
+ * trapezoid rule in time over the configured steps: b += dt (F(t0)/2 + F(t1) + ... +
+ * F(t_(n-1)) + F(t_n)/2), so that consecutive calls add up to one trapezoid sum.  vol
+ * (a, alpha, beta) and t_rel (time since the accumulation started) are read and advanced. */
+void oracle_tsurff_propagate(const oracle_sys *s, const int *box, int n_p, const double *p, double t0, double dt,
+                             int n_steps, int substeps, cplx *psi, double *obs, double *vol, double *t_rel, cplx *b) {
+  const int B = s->n_orb;
+  cplx *F = (cplx *)malloc(sizeof(cplx) * (size_t)B * (size_t)n_p);
+  const double dts = dt / (double)substeps;
+  for (int st = 0; st <= n_steps; st++) {
+    const double t = t0 + (double)st * dt;
+    oracle_tsurff_flux(s, box, n_p, p, vol, vol + 3, vol[6], *t_rel, psi, F);
+    const double w = (st == 0 || st == n_steps) ? 0.5 * dt : dt;
+    for (long i = 0; i < (long)B * n_p; i++) b[i] += w * F[i];
+    if (st == n_steps) break;
+    if (obs) oracle_observables(s, t, t + 0.5 * dts, psi, obs + 8 * st);
+    for (int j = 0; j < substeps; j++) oracle_taylor_substep(s, t + (double)j * dts, dts, psi);
+    oracle_volkov_step(s, t, dt, vol);
+    *t_rel += dt;
+  }
+  free(F);
 }

@@ -40,7 +40,7 @@ SIGNATURES = {
     "tdks_launch_count": ([P, PLL], I),
     "tdks_set_tile": ([P, I, I, I], I),
     "tdks_set_sweep_path": ([P, I], I),
-    "tdks_set_wait_limit": ([P, LL], I),
+    "tdks_set_wait_limit": ([P, LL, I], I),
     "tdks_sweep_shape_info": ([I, PI, PI, PI, PI, PI], I),
     "tdks_set_sweep_shape": ([P, I, I], I),
     "tdks_get_sweep_shape": ([P, I, PI], I),

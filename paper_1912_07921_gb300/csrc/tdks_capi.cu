@@ -201,6 +201,7 @@ void sweep_common(const tdks_system *s, SweepParams &p, const double A[3], int s
   p.pbox = s->d_pbox;
   p.n_pbox = s->d_pbox ? s->n_atoms : 0;
   p.wait_limit = s->wait_limit;
+  p.withhold = s->withhold;
   p.nl = s->d_nl;
   p.n_ent = s->n_ent;
   p.kvec = s->d_kvec;
@@ -851,11 +852,12 @@ int tdks_set_tile(tdks_sys s, int tx, int ty, int zc) {
   return TDKS_OK;
 }
 
-int tdks_set_wait_limit(tdks_sys s, long long cycles) {
+int tdks_set_wait_limit(tdks_sys s, long long cycles, int withhold) {
   if (!s) return fail(TDKS_EINVAL, "NULL system");
   if (cycles < 0) return fail(TDKS_EINVAL, "cycles < 0");
   CU(cudaStreamSynchronize(s->stream));
   s->wait_limit = cycles > 0 ? cycles : DEFAULT_WAIT_LIMIT_CYCLES;
+  s->withhold = withhold ? 1 : 0;
   return TDKS_OK;
 }
 

@@ -105,6 +105,8 @@ struct SweepParams {
                               // complex64, the unweighted sum as a (float hi, float lo) pair
   int *err;                   // device error word (bounded waits that ran out set it)
   long long wait_limit;       // bound of each wait of the TMA sweeps (clock64 cycles)
+  int withhold;               // failure injection (tests): the producer makes no claim and no
+                              // copy, so every other warp's first wait runs out
   unsigned int *work;         // work-item counter of the warp-specialised TMA sweep (zero
                               // between launches: the launch's last claim resets it)
 };

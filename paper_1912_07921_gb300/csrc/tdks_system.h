@@ -73,6 +73,7 @@ struct tdks_system {
   std::vector<cudaEvent_t> ev_chunk;
   int *d_err = nullptr;       // [0]: error word of the bounded waits; [1]: sweep work counter
   long long wait_limit = tdks::DEFAULT_WAIT_LIMIT_CYCLES;  // bound of each TMA-sweep wait (cycles)
+  int withhold = 0;           // failure injection: the sweeps' producers withhold their copies
   long obs_count = 0;         // energy/current partial records written by the last first sweep
   // TMA tensor maps over the four sweep inputs (state, t1, t2, t3) for the current tile
   tdks::SweepMaps smaps[4];   // TMA maps of the four Taylor-term sweeps

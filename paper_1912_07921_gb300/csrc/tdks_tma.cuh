@@ -170,6 +170,7 @@ struct SingleSrc {
   __device__ __forceinline__ const SweepMaps *maps_of(int) const { return maps; }
   __device__ __forceinline__ int *err0() const { return p->err; }
   __device__ __forceinline__ long long wait_limit() const { return p->wait_limit; }
+  __device__ __forceinline__ bool withhold() const { return p->withhold != 0; }
 };
 
 __device__ __forceinline__ int find_item_sys(const long *begin, int n, long u) {
@@ -194,6 +195,7 @@ struct BatchSrc {
   __device__ __forceinline__ const SweepMaps *maps_of(int s) const { return a->maps + 4 * s + a->which; }
   __device__ __forceinline__ int *err0() const { return a->params[0].err; }
   __device__ __forceinline__ long long wait_limit() const { return a->params[0].wait_limit; }
+  __device__ __forceinline__ bool withhold() const { return a->params[0].withhold != 0; }
 };
 
 // Sequential cursor over one kind of load of the CTA's items (thread 0 only).  The item's
@@ -508,7 +510,9 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
 
   if (warp == CW) {
     // ---- producer: claim items, and issue every ring's loads as soon as a slot is free ----
-    if (lane == 0) {
+    // (failure injection: a withholding producer does nothing, so the other warps' waits
+    // run out; no copy is in flight and nothing needs draining)
+    if (lane == 0 && !src.withhold()) {
       const Loader<M, TX, TY, U, G, SC, SH, SO, Src> ld{src, 0, cbase, hbase, obase, cfull, hfull, ofull};
       LoadCursor c[3];
       bool done[3] = {false, false, !OPS};

@@ -94,10 +94,11 @@ class System:
     def set_tile(self, tx, ty, zc=0):
         _lib.check(self.lib.tdks_set_tile(self.h, tx, ty, zc))
 
-    def set_wait_limit(self, cycles: int):
+    def set_wait_limit(self, cycles: int, withhold: bool = False):
         """Bound (GPU clock cycles) of every wait in the TMA sweeps; 0 restores the default
-        (~2 s).  A wait that runs out makes the next synchronising call raise TDKS_ETIMEOUT."""
-        _lib.check(self.lib.tdks_set_wait_limit(self.h, int(cycles)))
+        (~2 s).  A wait that runs out makes the next synchronising call raise TDKS_ETIMEOUT.
+        withhold=True injects that failure (tests): the sweeps' producers issue no copy."""
+        _lib.check(self.lib.tdks_set_wait_limit(self.h, int(cycles), int(bool(withhold))))
 
     def set_sweep_path(self, path: int):
         """0: TMA-fed warp-specialised sweep where it applies (finite boxes, 16x8 tiles);

@@ -2,12 +2,12 @@
 
 Every wait in the warp-specialised sweep is bounded; a wait that runs out makes the CTA
 give up, the producer drains its copies in flight, and the host reports TDKS_ETIMEOUT at
-the next synchronising call.  tdks_set_wait_limit lowers the bound to one clock cycle:
-the producer then gives up as soon as its rings are full and no slot has been released,
-which every CTA meets on its first work item (nothing releases a slot within a cycle).
-No copy is cancelled and no memory is touched out of bounds: the copies in flight land
-as usual.  The test checks the status, and that the same system then propagates exactly
-like the oracle once the limit is restored and the orbitals are set again.
+the next synchronising call.  tdks_set_wait_limit(cycles, withhold=1) injects the failure:
+the sweeps' producer warps claim no work item and issue no copy, so every consumer warp's
+first wait (for a claim that nothing makes) runs out after ~1 ms.  Nothing is read or
+written by those sweeps and no copy is in flight.  The test checks the status, and that the
+same system then propagates exactly like the oracle once the injection is off and the
+orbitals are set again.
 """
 import numpy as np
 import pytest
@@ -34,13 +34,13 @@ def test_wait_that_runs_out_is_reported_and_the_system_recovers(prec):
     spec = ragged_molecule(prec)
     inp = I.make_inputs(spec)
     s = System(spec, inp, stream=torch.cuda.current_stream().cuda_stream)
-    s.set_wait_limit(1)
+    s.set_wait_limit(2_000_000, withhold=True)  # ~1 ms per wait
     s.propagate(0.0, 0.02, 2, 1)
     with pytest.raises(TdksError) as e:
         s.reductions(0, 2)
     assert e.value.code == 4 and "gave up" in str(e.value)
     # the error word was cleared: restore the bound and the state, then a normal run
-    s.set_wait_limit(0)
+    s.set_wait_limit(0, withhold=False)
     s.set_orbitals(inp.psi0)
     n0 = s.step_count()
     s.propagate(0.0, 0.02, 3, 1)
