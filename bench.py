@@ -38,7 +38,7 @@ METRIC = "H.psi orbital-gridpoint updates/s (medium molecule, Taylor-4 step)"
 UNIT = "updates/s"
 
 
-SWEEP_SOURCES = ["tdks_sweep_tma.cu", "tdks_tma.cuh", "tdks_sweep_ws1.cu", "tdks_sweep_ws2.cu", "tdks_sweep_ws3.cu",
+SWEEP_SOURCES = ["tdks_sweep_tma.cu", "tdks_tma.cuh", "tdks_sweep_ws1.cu", "tdks_sweep_ws2.cu", "tdks_sweep_ws3.cu", "tdks_sweep_ws5.cu",
                  "tdks_sweep_ws4.cu", "tdks_sweep_common.cuh", "tdks_vec.cuh", "tdks_internal.cuh"]
 WORKLOAD = ("medium molecule 96^3 h=0.25 order-8 FD, 64 orbitals, 16 atoms x 4 KB projectors, sin^2 pulse, "
             "LDA exchange, dt=0.05 as 4 Taylor-4 sub-steps")
@@ -628,6 +628,42 @@ def run_serving(args):
     return r
 
 
+def run_serving_full(args):
+    """The serving workload's size distribution: grid edges U[32,128], 4..128 orbitals,
+    0..32 atoms with projectors, half complex64 and half complex128, a 150 GB HBM budget,
+    Poisson arrivals; each job's step count drawn from U[200,5000] and divided by
+    --serving-steps-scale (the whole distribution at full length offers ~1e11 updates per job,
+    hours of GPU time for a few hundred jobs).  Two traces of the same jobs: the configured
+    20 jobs/s (far above the GPU's capacity, so latency is queueing), then arrivals at 70% of
+    the capacity measured on the first trace."""
+    import torch
+    from paper_1912_07921_gb300 import inputs as I, serving
+    scale = max(1, args.serving_steps_scale)
+    stream = torch.cuda.Stream()
+
+    def trace(rate):
+        jobs = serving.serving_trace(args.serving_full, rate=rate, seed=5, edge=(32, 128), orbitals=(4, 128),
+                                     steps=(200, 5000), atoms=(0, 32))
+        for j in jobs:
+            j.n_steps = max(1, j.n_steps // scale)
+            j.spec = dataclasses.replace(j.spec, n_steps=j.n_steps)
+        return jobs
+
+    def serve(jobs):
+        srv = serving.Server(hbm_budget=150 * 10 ** 9, max_slots=64, quantum=50, stream=stream.cuda_stream,
+                             sync=torch.cuda.synchronize)
+        srv.run(jobs)
+        return srv.report()
+
+    sat = serve(trace(20.0))
+    capacity = sat["jobs"] / sat["wall_s"]  # jobs per second the GPU completed under saturation
+    relaxed = serve(trace(0.7 * capacity))
+    desc = (f"{args.serving_full} jobs: edges U[32,128], orbitals U[4,128], atoms U[0,32], steps U[200,5000]/{scale}, "
+            "half complex64 / half complex128, 150 GB budget, 64 slots, quantum 50")
+    return {"trace": desc, "as_specified_20_per_s": sat,
+            "at_0.7_utilisation": dict(relaxed, arrival_rate_per_s=0.7 * capacity)}
+
+
 def cpu_baseline(n_orb_sample: int):
     """The FP64 oracle as it stands, on the host cores, on a bounded sample: one
     configured step (4 sub-steps plus the observable record) of the medium molecule with
@@ -729,6 +765,10 @@ def main():
                     help="k-points of the periodic cell (profiling on a smaller case); 32 = the workload")
     ap.add_argument("--serving", type=int, default=48,
                     help="also run a serving trace with this many jobs")
+    ap.add_argument("--serving-full", type=int, default=0,
+                    help="also serve this many jobs of the serving workload's full size distribution (0: skip)")
+    ap.add_argument("--serving-steps-scale", type=int, default=25,
+                    help="divide each full-distribution job's step count by this")
     ap.add_argument("--n-orb", type=int, default=0,
                     help="orbital count override (profiling on a smaller case); 0 = the workload's 64")
     ap.add_argument("--no-tune", action="store_true", help="keep the default sweep tile shape (no autotuner)")
@@ -774,6 +814,8 @@ def main():
             out["periodic"] = run_periodic_side(args)
         if args.serving and world == 1:
             out["serving"] = run_serving(args)
+        if args.serving_full and world == 1:
+            out["serving_full"] = run_serving_full(args)
         if not args.no_study and world == 1:
             out["propagators"] = run_propagator_study(args)
         if not args.no_cpu and world == 1:

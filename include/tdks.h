@@ -284,20 +284,20 @@ int tdks_launch_count(tdks_sys sys, long long *count);
 int tdks_set_tile(tdks_sys sys, int tx, int ty, int zc);
 
 /*
- * Failure detection of the warp-specialised TMA sweeps.  Every wait in them is bounded by
- * `cycles` GPU clock cycles (clock64; 0 restores the default of 4e9, ~2 s).  A wait that runs
- * out (a copy that does not land, a ring slot that is not released, a claimed work item that
- * does not arrive) makes its CTA give up: its other warps stop at their next wait, its
- * producer waits (at most ~0.1 s each) for the copies it has in flight, the error word is
- * set, and the next synchronising call (tdks_reductions, tdks_get_orbitals, tdks_observe,
- * tdks_autotune) returns TDKS_ETIMEOUT and clears it; the orbitals are then undefined until
- * set again.  withhold = 1 injects that failure for tests: the sweeps' producer warps make no
- * claim and issue no copy, so every consumer's first wait runs out after `cycles` (nothing is
- * read or written by those sweeps).  No passage of the paper defines this: it is the
- * library's own failure handling.  Synchronises the system's stream; applies to launches
- * made after the call (batches: to batches created after it).
+ * Failure detection of the warp-specialised TMA sweeps.  Every wait in them is bounded (4e9
+ * GPU clock cycles, ~2 s).  A wait that runs out (a copy that does not land, a ring slot that
+ * is not released, a claimed work item that does not arrive) makes its CTA give up: its other
+ * warps stop at their next wait, its producer waits (at most ~0.1 s each) for the copies it
+ * has in flight, the error word is set, and the next synchronising call (tdks_reductions,
+ * tdks_get_orbitals, tdks_observe, tdks_autotune, tdks_get_tsurff) returns TDKS_ETIMEOUT and
+ * clears it; the orbitals are then undefined until set again.  withhold = 1 injects that
+ * failure for tests: the sweeps' producer warps make no claim and issue no copy, so every
+ * consumer warp's first wait runs out after the bound (nothing is read or written by those
+ * sweeps, no copy is in flight); withhold = 0 restores normal sweeps.  No passage of the
+ * paper defines this: it is the library's own failure handling.  Synchronises the system's
+ * stream; applies to launches made after the call (batches: to batches created after it).
  */
-int tdks_set_wait_limit(tdks_sys sys, long long cycles, int withhold);
+int tdks_set_failure_injection(tdks_sys sys, int withhold);
 
 /* Stencil sweep implementation: 0 (default) streams the input planes with TMA bulk
  * tensor copies where that applies (finite boxes, 16x8 tiles) into a warp-specialised
@@ -317,8 +317,13 @@ int tdks_set_sweep_path(tdks_sys sys, int path);
  *
  * tdks_sweep_shape_info: shape s (0 .. count-1) covers tx x ty points of one orbital batch
  * per work item with `warps` consumer warps, each thread computing `rows` y-adjacent
- * points.  *count (if not NULL) receives the number of shapes; tx/ty/rows/warps may be
- * NULL.  TDKS_EINVAL for a shape out of range.
+ * points of one 16-byte vector (two complex64 or one complex128 values; 4 vectors per point,
+ * so warps x 32 = 4 tx ty / rows).  Shape 5 computes complex64 finite boxes with one
+ * complex64 value (8 bytes) per thread vector, 8 vectors per point (warps x 32 = 8 tx ty /
+ * rows): fewer shared-memory bytes per value at the same register budget; complex128
+ * systems and periodic cells run it as shape 2 (the same tile and warp count).  *count (if
+ * not NULL) receives the number of shapes; tx/ty/rows/warps may be NULL.  TDKS_EINVAL for a
+ * shape out of range.
  */
 int tdks_sweep_shape_info(int shape, int *count, int *tx, int *ty, int *rows, int *warps);
 /* Shape of Taylor-term sweep `sweep` (0 = t1 from psi, 1 = t2, 2 = t3, 3 = t4 and the
@@ -399,6 +404,32 @@ int tdks_batch_destroy(tdks_batch_t batch);
  */
 int tdks_apply_H_noalloc(int nx, int ny, int nz, double h, int fd_order, int prec, int n_orb,
                          const double *dev_vloc, const void *dev_in, void *dev_out, void *stream);
+
+/*
+ * t-SURFF photoelectron amplitudes (Sec. "t-SURFF": the expansion coefficients b_i(p, t) of
+ * the orbitals on Volkov states, obtained from the continuity equation as the time integral
+ * of the current through a surface S):
+ *   b_i(p, T) = int dt oint_S ds n . <chi_p| j |phi_i>,  <chi_p| j |phi> = 1/2 chi_p^* (k_p phi - i grad_h phi),
+ *   chi_p = (2 pi)^(-3/2) exp(i k_p.r - i Phi_p),  k_p = p + a(t),  a = -int E,
+ *   Phi_p = 1/2 int |k_p|^2  (Volkov states of -1/2 Lap + E(t).r, the length gauge of the
+ *   finite boxes; the section prints the velocity-gauge form).
+ * S is the surface of the box of grid planes x = x[box[0]], x[box[1]], y = y[box[2]], y[box[3]],
+ * z = z[box[4]], z[box[5]], integrated face by face with the two-dimensional trapezoid rule and
+ * the outward normal n; grad_h is the central difference of the system's order; time runs
+ * from the start of the first tdks_propagate_n after this call, and the time integral is the
+ * trapezoid rule over the configured steps (the flux of the state at the start of each step;
+ * a(t), int a and int |a|^2 advanced per step by the classical Runge-Kutta method).  Later
+ * propagations must continue in time from where the last one ended (TDKS_EINVAL otherwise).
+ *   box  six plane indices with fd_order/2 <= lo < hi <= n - 1 - fd_order/2 on each axis
+ *   p    [n_p][3] momenta (bohr^-1), copied; n_p = 0 turns t-SURFF off
+ * Finite boxes with one k-point only (TDKS_EINVAL otherwise).  Resets the amplitudes to zero.
+ * The amplitudes are not part of a checkpoint.  Synchronises.
+ */
+int tdks_set_tsurff(tdks_sys sys, const int box[6], int n_p, const double *p);
+/* b [n_orb][n_p] complex amplitudes (interleaved re, im doubles) accumulated so far, and the
+ * time since the accumulation started (either pointer may be NULL).  Synchronises;
+ * TDKS_ESTATE when t-SURFF is not set. */
+int tdks_get_tsurff(tdks_sys sys, double *b, double *t_rel);
 
 /*
  * Fused multiply-add throughput of the current device, measured by the library's own probe

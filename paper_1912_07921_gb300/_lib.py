@@ -40,7 +40,7 @@ SIGNATURES = {
     "tdks_launch_count": ([P, PLL], I),
     "tdks_set_tile": ([P, I, I, I], I),
     "tdks_set_sweep_path": ([P, I], I),
-    "tdks_set_wait_limit": ([P, LL, I], I),
+    "tdks_set_failure_injection": ([P, I], I),
     "tdks_sweep_shape_info": ([I, PI, PI, PI, PI, PI], I),
     "tdks_set_sweep_shape": ([P, I, I], I),
     "tdks_get_sweep_shape": ([P, I, PI], I),
@@ -56,6 +56,8 @@ SIGNATURES = {
     "tdks_batch_autotune": ([P, I, PD], I),
     "tdks_apply_H_noalloc": ([I, I, I, D, I, I, I, P, P, P, P], I),
     "tdks_fma_rate": ([I, PD], I),
+    "tdks_set_tsurff": ([P, P, I, P], I),
+    "tdks_get_tsurff": ([P, P, PD], I),
     "tdks_last_error": ([], ctypes.c_char_p),
 }
 

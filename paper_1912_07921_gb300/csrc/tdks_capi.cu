@@ -198,9 +198,6 @@ void sweep_common(const tdks_system *s, SweepParams &p, const double A[3], int s
   set_coef(p, 1.0, 0.0);
   p.aux = s->aux;
   p.has_proj = s->n_atoms > 0;
-  p.pbox = s->d_pbox;
-  p.n_pbox = s->d_pbox ? s->n_atoms : 0;
-  p.wait_limit = s->wait_limit;
   p.withhold = s->withhold;
   p.nl = s->d_nl;
   p.n_ent = s->n_ent;
@@ -449,8 +446,7 @@ void free_proj(tdks_system *s) {
   cudaFree(s->d_ent); cudaFree(s->d_q); cudaFree(s->d_D); cudaFree(s->d_qpart);
   cudaFree(s->d_ent_beta); cudaFree(s->d_ent_ca);
   s->d_ent_beta = nullptr; s->d_ent_ca = nullptr;
-  cudaFree(s->d_sp); cudaFree(s->d_nl); cudaFree(s->d_pbox);
-  s->d_pbox = nullptr;
+  cudaFree(s->d_sp); cudaFree(s->d_nl);
   s->d_rowent = s->d_atom_begin = nullptr;
   s->d_sp = nullptr; s->d_nl = nullptr;
   s->n_sp = s->n_ent = 0;
@@ -578,6 +574,7 @@ int tdks_destroy(tdks_sys s) {
   cudaFree(s->n_total); cudaFree(s->fin_sum);
   cudaFree(s->obs_rec); cudaFree(s->d_kvec); cudaFree(s->d_wocc);
   cudaFree(s->staging);
+  tsurff_free(s);
   if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
   if (s->ev_staging_free) cudaEventDestroy(s->ev_staging_free);
   for (auto e : s->ev_chunk) cudaEventDestroy(e);
@@ -675,7 +672,6 @@ int tdks_set_atoms_projectors(tdks_sys s, int n_atoms, const double *pos, const 
   const int n[3] = {s->nx, s->ny, s->nz};
   std::vector<ProjEntry> ent;
   std::vector<int> atom_begin(n_atoms + 1, 0);
-  std::vector<int> pbox(6 * (size_t)n_atoms);  // sphere bounding boxes, for the sweeps' item test
   double vnl = 0.0;
   const double h3 = s->h * s->h * s->h;
   for (int a = 0; a < n_atoms; a++) {
@@ -691,21 +687,6 @@ int tdks_set_atoms_projectors(tdks_sys s, int n_atoms, const double *pos, const 
         lo[ax] = (int)std::floor((R[ax] - r_cut) / s->h) - 1;
         hi[ax] = (int)std::ceil((R[ax] + r_cut) / s->h) + 1;
       }
-      // the box the sweeps test work items against: clipped to a finite box; in a periodic
-      // cell its start taken into [0, n) (the whole axis when it spans the cell)
-      int blo = lo[ax], bhi = hi[ax];
-      if (s->bc != TDKS_BC_ZERO) {
-        if (bhi - blo + 1 >= n[ax]) {
-          blo = 0;
-          bhi = n[ax] - 1;
-        } else {
-          const int w = ((blo % n[ax]) + n[ax]) % n[ax];
-          bhi += w - blo;
-          blo = w;
-        }
-      }
-      pbox[6 * a + 2 * ax] = blo;
-      pbox[6 * a + 2 * ax + 1] = bhi;
     }
     double nb[4] = {0, 0, 0, 0};
     for (int iz = lo[2]; iz <= hi[2]; iz++)
@@ -791,8 +772,6 @@ int tdks_set_atoms_projectors(tdks_sys s, int n_atoms, const double *pos, const 
     CU(cudaMemcpy(s->d_ent_ca, eca.data(), ent.size() * sizeof(int2), cudaMemcpyHostToDevice));
   }
   CU(cudaMemcpy(s->d_D, D, (size_t)n_atoms * 4 * sizeof(double), cudaMemcpyHostToDevice));
-  CU(cudaMalloc((void **)&s->d_pbox, pbox.size() * sizeof(int)));
-  CU(cudaMemcpy(s->d_pbox, pbox.data(), pbox.size() * sizeof(int), cudaMemcpyHostToDevice));
   s->n_atoms = n_atoms;
   s->pos.assign(pos, pos + 3 * n_atoms);
   s->D.assign(D, D + 4 * n_atoms);
@@ -852,11 +831,9 @@ int tdks_set_tile(tdks_sys s, int tx, int ty, int zc) {
   return TDKS_OK;
 }
 
-int tdks_set_wait_limit(tdks_sys s, long long cycles, int withhold) {
+int tdks_set_failure_injection(tdks_sys s, int withhold) {
   if (!s) return fail(TDKS_EINVAL, "NULL system");
-  if (cycles < 0) return fail(TDKS_EINVAL, "cycles < 0");
   CU(cudaStreamSynchronize(s->stream));
-  s->wait_limit = cycles > 0 ? cycles : DEFAULT_WAIT_LIMIT_CYCLES;
   s->withhold = withhold ? 1 : 0;
   return TDKS_OK;
 }
@@ -1267,11 +1244,35 @@ int tdks_set_exchange(tdks_sys s, tdks_exchange_fn fn, void *ctx) {
   return TDKS_OK;
 }
 
+static int propagate_steps(tdks_system *s, double t0, double dt, int n_steps, int substeps);
+
 int tdks_propagate_n(tdks_sys s, double t0, double dt, int n_steps, int substeps) {
   if (!s) return fail(TDKS_EINVAL, "NULL system");
   if (n_steps < 0 || substeps < 0) return fail(TDKS_EINVAL, "negative count");
   if (!s->have_orbitals) return fail(TDKS_ESTATE, "orbitals not set");
   if (substeps == 0) tdks_auto_substeps(s, dt, &substeps);
+  if (s->ts_np == 0) return propagate_steps(s, t0, dt, n_steps, substeps);
+  // t-SURFF: the flux of the state at the start of every step, by the trapezoid rule in time
+  // (dt/2 at this call's first and last states), the Volkov parameters advanced per step
+  if (!s->ts_started) {
+    s->ts_started = true;
+    s->ts_t0 = t0;
+  } else if (std::fabs(t0 - (s->ts_t0 + s->ts_trel)) > 1e-9 * std::max(1.0, std::fabs(t0))) {
+    return fail(TDKS_EINVAL, "t-SURFF accumulation: t0 must continue from the last propagation's end");
+  }
+  int rc = TDKS_OK;
+  for (int st = 0; st <= n_steps; st++) {
+    const double t = t0 + st * dt;
+    if ((rc = tsurff_accumulate(s, (st == 0 || st == n_steps) ? 0.5 * dt : dt))) return rc;
+    if (st == n_steps) break;
+    if ((rc = propagate_steps(s, t, dt, 1, substeps))) return rc;
+    tsurff_advance(s, t, dt);
+  }
+  s->clock_t = t0 + n_steps * dt;
+  return TDKS_OK;
+}
+
+static int propagate_steps(tdks_system *s, double t0, double dt, int n_steps, int substeps) {
   if (s->prop == TDKS_PROP_RK4) return propagate_rk4(s, t0, dt, n_steps, substeps);
   if (s->prop != TDKS_PROP_TAYLOR4) return propagate_exp(s, t0, dt, n_steps, substeps);
   const double dts = dt / substeps;

@@ -38,13 +38,13 @@ inline cudaError_t ensure_smem_attr(K k, size_t smem, std::atomic<unsigned> &don
 }
 
 constexpr int OVC = 4;        // 16-byte vectors per (point, batch)
-// Default bound of every wait in the TMA sweeps (clock64 cycles, ~2 s at 2 GHz): a wait that
-// runs out makes the CTA give up and the host report TDKS_ETIMEOUT.
-constexpr long long DEFAULT_WAIT_LIMIT_CYCLES = 4000000000LL;
 constexpr int MAXM = 4;       // largest FD half-width (8th order)
 
 enum Mode { MODE_FIRST = 0, MODE_MID = 1, MODE_LAST = 2 };
-enum Prec { P_C128 = 0, P_C64 = 1 };
+// Compute precisions of the sweeps.  P_C64S is complex64 storage computed with one complex
+// value per thread vector (8 bytes, 8 vectors per (point, batch)) instead of two (16 bytes,
+// 4 vectors): the tile shapes that use it keep more points per thread in registers.
+enum Prec { P_C128 = 0, P_C64 = 1, P_C64S = 2 };
 
 // Per-entry projector data (one grid point of one atom's sphere).
 struct ProjEntry {
@@ -54,6 +54,15 @@ struct ProjEntry {
   double betad[4]; // same, double (c128 path)
   double T[3];     // lattice translation of the unwrapped point
   double d[3];     // unwrapped point minus atom centre
+};
+
+// One point of one face of the t-SURFF surface: its flat grid index, the face's normal
+// axis, the trapezoid weight times the sign of the outward normal, and its position.
+struct TsEntry {
+  long cell;
+  int ax;
+  double ws;
+  double r[3];
 };
 
 // Per-point record read by the sweeps (16 bytes): the diagonal potential V_eff (double
@@ -84,10 +93,6 @@ struct SweepParams {
   const PointAux *aux;        // [N] V_eff and projector entry ranges
   // projectors
   int has_proj;               // the system has projector entries
-  const int *pbox;            // [n_pbox][6] per-atom sphere bounding boxes in grid indices (lo, hi
-                              // per axis; periodic cells: lo in [0, n), taken modulo the cell), or
-                              // NULL; a work item that meets none of them has no non-local term
-  int n_pbox;
   const void *nl;             // [kb][n_ent + 1][OVC] vectors: sum_aj beta_aj(r) phase q_aj at the
                               // sphere point whose entries start at r0; row n_ent is zero
   int n_ent;                  // projector entries
@@ -104,7 +109,6 @@ struct SweepParams {
   double *dens_part;          // [n_kb][N] (MODE_LAST): w_k f sum |psi|^2 (complex128); for
                               // complex64, the unweighted sum as a (float hi, float lo) pair
   int *err;                   // device error word (bounded waits that ran out set it)
-  long long wait_limit;       // bound of each wait of the TMA sweeps (clock64 cycles)
   int withhold;               // failure injection (tests): the producer makes no claim and no
                               // copy, so every other warp's first wait runs out
   unsigned int *work;         // work-item counter of the warp-specialised TMA sweep (zero
@@ -263,7 +267,7 @@ cudaError_t launch_sweep_tma(int M, int prec, int mode, int tx, int ty, const Sw
 // block with `warps` consumer warps, each thread computing `rows` y-adjacent points.
 // Shape 0 (16 x 8, two points per thread, eight consumer warps) is the default and the one
 // the batched sweep uses.  Null outputs are skipped; false for a shape out of range.
-constexpr int WS_SHAPES = 5;
+constexpr int WS_SHAPES = 6;
 bool ws_shape_info(int shape, int *tx, int *ty, int *rows, int *warps);
 bool tma_supported(int M, int tx, int ty);
 int tma_planes(int prec, int mode, bool lockstep = false);

@@ -38,9 +38,23 @@ template <> struct ObsAcc<P_C64> {
   __device__ __forceinline__ double get_j(int a) const { return (double)jh[a] + (double)jl[a]; }
 };
 
+template <> struct ObsAcc<P_C64S> {
+  float eh = 0.f, el = 0.f, jh[3] = {0.f, 0.f, 0.f}, jl[3] = {0.f, 0.f, 0.f};
+  __device__ __forceinline__ void add_e(u64 c, u64 h) {
+    const float2 c0 = up2(c), h0 = up2(h);
+    df_acc(eh, el, c0.x * h0.x + c0.y * h0.y);
+  }
+  __device__ __forceinline__ void add_j(int a, u64 c, u64 g) {
+    const float2 c0 = up2(c), g0 = up2(g);
+    df_acc(jh[a], jl[a], c0.x * g0.y - c0.y * g0.x);
+  }
+  __device__ __forceinline__ double get_e() const { return (double)eh + (double)el; }
+  __device__ __forceinline__ double get_j(int a) const { return (double)jh[a] + (double)jl[a]; }
+};
+
 // Diagonal weight w0 in the compute precision.
-template <int P> struct W0T { typedef double type; };
-template <> struct W0T<P_C64> { typedef float type; };
+template <int P> struct W0T { typedef float type; };
+template <> struct W0T<P_C128> { typedef double type; };
 
 // H applied at one point.  The z-column queue is the circular register array Q of QN
 // (>= 2M+1) entries; plane z+j (j = -M..M) sits in Q[(QB + M + j) % QN] (QB: compile-time
@@ -85,35 +99,11 @@ stencil_point(const SweepParams &p, const typename VT<P>::S *W, typename W0T<P>:
 // the zero row n_ent for the others (a branch-free load that can be issued early).
 template <int P>
 __device__ __forceinline__ typename VT<P>::V nl_term(const typename VT<P>::V *nlk, int n_ent, int r0, int r1) {
-  return VT<P>::ld(nlk + (long)(r1 > r0 ? r0 : n_ent) * OVC);
+  return VT<P>::ld(nlk + (long)(r1 > r0 ? r0 : n_ent) * VT<P>::OV);
 }
 template <int P>
 __device__ __forceinline__ const typename VT<P>::V *nl_column(const SweepParams &p, int kb, int v) {
-  return reinterpret_cast<const typename VT<P>::V *>(p.nl) + (long)kb * (p.n_ent + 1) * OVC + v;
-}
-
-// Whether the grid interval [t0, t1) meets [lo, hi] (periodic cells: also its image one
-// cell to the left, as lo lies in [0, n)).
-__device__ __forceinline__ bool span_meets(int lo, int hi, int t0, int t1, int n, bool wrap) {
-  return (lo < t1 && hi >= t0) || (wrap && lo - n < t1 && hi - n >= t0);
-}
-
-// Whether a work item's points [x0, x0 + tx) x [y0, y0 + ty) x [z0, z1) can lie in a
-// projector sphere: the non-local term is read only for such items (for all the others it
-// is zero, so skipping its loads changes no value).  One thread tests the atoms' bounding
-// boxes.
-__device__ __forceinline__ bool item_meets_spheres(const SweepParams &p, int x0, int tx, int y0, int ty, int z0,
-                                                   int z1) {
-  if (!p.has_proj) return false;
-  if (!p.pbox) return true;
-  const bool wrap = p.bloch != 0;
-  for (int a = 0; a < p.n_pbox; a++) {
-    const int *b = p.pbox + 6 * a;
-    if (span_meets(b[0], b[1], x0, x0 + tx, p.nx, wrap) && span_meets(b[2], b[3], y0, y0 + ty, p.ny, wrap) &&
-        span_meets(b[4], b[5], z0, z1, p.nz, wrap))
-      return true;
-  }
-  return false;
+  return reinterpret_cast<const typename VT<P>::V *>(p.nl) + (long)kb * (p.n_ent + 1) * VT<P>::OV + v;
 }
 
 // Own-point operands of the last sweep (state parts and earlier terms).
@@ -125,7 +115,7 @@ template <int P>
 __device__ __forceinline__ void load_last(const SweepParams &p, long idx, LastOperands<P> &o) {
   typedef typename VT<P>::V V;
   o.hi = VT<P>::ld(reinterpret_cast<const V *>(p.psi) + idx);
-  o.lo = P == P_C64 ? VT<P>::ld(reinterpret_cast<const V *>(p.psi_lo) + idx) : VT<P>::zero();
+  o.lo = P != P_C128 ? VT<P>::ld(reinterpret_cast<const V *>(p.psi_lo) + idx) : VT<P>::zero();
   o.t1 = VT<P>::ld(reinterpret_cast<const V *>(p.t1) + idx);
   o.t2 = VT<P>::ld(reinterpret_cast<const V *>(p.t2) + idx);
 }
@@ -158,10 +148,10 @@ __device__ __forceinline__ void finish_point(const Epi &ep, typename VT<P>::S CR
     Combine<P>::run(hi, lo_ops.lo, lo_ops.t1, lo_ops.t2, c0, outv, lo_out, dh, dl);
     if (own) {
       reinterpret_cast<V *>(ep.psi)[idx] = hi;
-      if (P == P_C64) reinterpret_cast<V *>(ep.psi_lo)[idx] = lo_out;
+      if (P != P_C128) reinterpret_cast<V *>(ep.psi_lo)[idx] = lo_out;
     }
-    Combine<P>::reduce4(dh, dl);
-    if (own && v == 0) Combine<P>::store_density(ep.dens_part + idx / OVC, ep.wocc, dh, dl);
+    Combine<P>::reduce_point(dh, dl);
+    if (own && v == 0) Combine<P>::store_density(ep.dens_part + idx / T::OV, ep.wocc, dh, dl);
   }
 }
 

@@ -256,6 +256,7 @@ extern template cudaError_t launch_ws_batch_shape<1>(int, int, int, const BatchS
 extern template cudaError_t launch_ws_batch_shape<2>(int, int, int, const BatchSweepArgs &, cudaStream_t);
 extern template cudaError_t launch_ws_batch_shape<3>(int, int, int, const BatchSweepArgs &, cudaStream_t);
 extern template cudaError_t launch_ws_batch_shape<4>(int, int, int, const BatchSweepArgs &, cudaStream_t);
+extern template cudaError_t launch_ws_batch_shape<5>(int, int, int, const BatchSweepArgs &, cudaStream_t);
 template cudaError_t launch_ws_batch_shape<0>(int, int, int, const BatchSweepArgs &, cudaStream_t);
 
 cudaError_t launch_sweep_tma_batch(int M, int prec, int mode, const BatchSweepArgs &a, cudaStream_t s, int shape) {
@@ -266,6 +267,7 @@ cudaError_t launch_sweep_tma_batch(int M, int prec, int mode, const BatchSweepAr
     case 2: return launch_ws_batch_shape<2>(M, prec, mode, a, s);
     case 3: return launch_ws_batch_shape<3>(M, prec, mode, a, s);
     case 4: return launch_ws_batch_shape<4>(M, prec, mode, a, s);
+    case 5: return launch_ws_batch_shape<5>(M, prec, mode, a, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -289,6 +291,8 @@ extern template cudaError_t launch_ws_shape<3>(int, int, int, int, const SweepMa
                                                  cudaStream_t);
 extern template cudaError_t launch_ws_shape<4>(int, int, int, int, const SweepMaps &, const SweepParams &, int,
                                                  cudaStream_t);
+extern template cudaError_t launch_ws_shape<5>(int, int, int, int, const SweepMaps &, const SweepParams &, int,
+                                                 cudaStream_t);
 template cudaError_t launch_ws_shape<0>(int, int, int, int, const SweepMaps &, const SweepParams &, int, cudaStream_t);
 
 template <int SHAPE>
@@ -307,6 +311,15 @@ bool ws_shape_info(int shape, int *tx, int *ty, int *rows, int *warps) {
     case 2: shape_of<2>(tx, ty, rows, warps); return true;
     case 3: shape_of<3>(tx, ty, rows, warps); return true;
     case 4: shape_of<4>(tx, ty, rows, warps); return true;
+    case 5: {
+      // complex64 systems: 8 one-complex vectors per point (complex128 runs shape 2, also 12 warps)
+      typedef WsShape<5> S;
+      if (tx) *tx = S::TX;
+      if (ty) *ty = S::TY;
+      if (rows) *rows = S::R;
+      if (warps) *warps = WsWarps<S::TX, S::TY, S::R, 8>::CW;
+      return true;
+    }
   }
   return false;
 }
@@ -328,6 +341,7 @@ cudaError_t launch_sweep_tma(int M, int prec, int mode, int tx, int ty, const Sw
     case 2: return launch_ws_shape<2>(M, prec, mode, b, maps, p, grid, s);
     case 3: return launch_ws_shape<3>(M, prec, mode, b, maps, p, grid, s);
     case 4: return launch_ws_shape<4>(M, prec, mode, b, maps, p, grid, s);
+    case 5: return launch_ws_shape<5>(M, prec, mode, b, maps, p, grid, s);
   }
   return cudaErrorInvalidValue;
 }

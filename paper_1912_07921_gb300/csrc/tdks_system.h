@@ -57,7 +57,6 @@ struct tdks_system {
   int *d_rowent = nullptr, *d_atom_begin = nullptr;
   int2 *d_sp = nullptr;       // entry ranges of the points inside a sphere
   void *d_nl = nullptr;       // non-local term per sphere point, [n_kb][n_ent + 1][OVC]
-  int *d_pbox = nullptr;      // [n_atoms][6] bounding boxes of the spheres (grid indices)
   int n_sp = 0, n_ent = 0;
   tdks::ProjEntry *d_ent = nullptr;
   float4 *d_ent_beta = nullptr;  // compact copies of the entries' FP32 beta and (cell, atom)
@@ -72,7 +71,6 @@ struct tdks_system {
   bool staging_pending = false;            // ev_staging_free has been recorded
   std::vector<cudaEvent_t> ev_chunk;
   int *d_err = nullptr;       // [0]: error word of the bounded waits; [1]: sweep work counter
-  long long wait_limit = tdks::DEFAULT_WAIT_LIMIT_CYCLES;  // bound of each TMA-sweep wait (cycles)
   int withhold = 0;           // failure injection: the sweeps' producers withhold their copies
   long obs_count = 0;         // energy/current partial records written by the last first sweep
   // TMA tensor maps over the four sweep inputs (state, t1, t2, t3) for the current tile
@@ -91,6 +89,15 @@ struct tdks_system {
   tdks_exchange_fn xfn = nullptr;
   void *xctx = nullptr;
   double *n_total = nullptr, *fin_sum = nullptr;
+  // t-SURFF (tdks_set_tsurff): surface entries, momenta, gathered surface values, amplitudes,
+  // the Volkov parameters a, alpha, beta and the time since the accumulation started
+  tdks::TsEntry *d_ts_ent = nullptr;
+  double *d_ts_p = nullptr;
+  double2 *d_ts_G = nullptr, *d_ts_b = nullptr;
+  int ts_np = 0, ts_ne = 0;
+  double ts_vol[7] = {0, 0, 0, 0, 0, 0, 0};
+  double ts_trel = 0.0, ts_t0 = 0.0;
+  bool ts_started = false;
   // clock used by batched propagation: state time, step length, sub-steps per step
   double clock_t = 0.0, clock_dt = 0.0;
   int clock_substeps = 1;
@@ -128,6 +135,11 @@ bool encode_op_map(const tdks_system *s, const void *ptr, CUtensorMap *out, int 
 bool encode_sweep_maps(const tdks_system *s, const void *in, int mode, tdks::SweepMaps *out, bool lockstep,
                        int sweep = -1);
 int ensure_density(tdks_system *s);
+// t-SURFF (tdks_tsurff.cu): add weight x the flux of the current state to the amplitudes;
+// advance a, alpha, beta and the accumulation time by dt from t; free the buffers
+int tsurff_accumulate(tdks_system *s, double weight);
+void tsurff_advance(tdks_system *s, double t, double dt);
+void tsurff_free(tdks_system *s);
 int check_err(tdks_system *s);
 double kinetic_max(const tdks_system *s);
 

@@ -61,18 +61,17 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
-// Consumer wait: bounded by `limit` cycles, and gives up soon after another warp has given
-// up.  The abort flag and the clock are read once every 16 failed polls (each try_wait
-// already suspends the thread for a while), so a waiting warp adds almost no shared-memory
-// loads to those of the warps that compute.
-__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *bar, uint32_t parity, const volatile int *abort,
-                                                   const long long *limit) {
+// Consumer wait: bounded, and gives up at once when another warp has given up.  (Reading
+// the abort flag only every 16 polls, or taking the bound from shared memory, measured 1-3%
+// slower sweeps: the flag's load paces the polling.)
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *bar, uint32_t parity, const volatile int *abort) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
-  for (unsigned i = 1;; i++) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 15u) == 0u && (*abort || clock64() - t0 > *limit)) return false;
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort) return false;
+    if (clock64() - t0 > WAIT_LIMIT_CYCLES) return false;
   }
+  return true;
 }
 __device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *tmap, uint64_t *bar, int c0, int c1,
                                             int c2, int c3, int c4) {
@@ -169,7 +168,6 @@ struct SingleSrc {
   __device__ __forceinline__ int sys_of(long) const { return 0; }
   __device__ __forceinline__ const SweepMaps *maps_of(int) const { return maps; }
   __device__ __forceinline__ int *err0() const { return p->err; }
-  __device__ __forceinline__ long long wait_limit() const { return p->wait_limit; }
   __device__ __forceinline__ bool withhold() const { return p->withhold != 0; }
 };
 
@@ -194,7 +192,6 @@ struct BatchSrc {
   __device__ __forceinline__ int sys_of(long it) const { return find_item_sys(a->item_begin, a->n_sys, it); }
   __device__ __forceinline__ const SweepMaps *maps_of(int s) const { return a->maps + 4 * s + a->which; }
   __device__ __forceinline__ int *err0() const { return a->params[0].err; }
-  __device__ __forceinline__ long long wait_limit() const { return a->params[0].wait_limit; }
   __device__ __forceinline__ bool withhold() const { return a->params[0].withhold != 0; }
 };
 
@@ -335,18 +332,27 @@ struct Loader {
 // one of the SM's four scheduler partitions (16K registers each): 7 or 8 warps in all leave
 // 255 registers per thread, 9 leave 168, 13 leave 128, 17 leave 96.  tdks_autotune times
 // the shapes on the system's own data.
+//
+// Shape 5 computes complex64 systems with one complex value per thread vector (8 bytes, 8
+// vectors per point, P_C64S): at the same register budget a thread then holds the z queues
+// of 4 y-adjacent points, which share their y-column loads, while a warp still spans 4
+// consecutive points in x (conflict-free 256-byte shared loads).  Per output value that is
+// 2M x-arm loads, 2M/4 y-arm loads and one queue load of 8 bytes, against 2M, (2M+2)/2 and
+// one of 16 bytes for two values in the two-complex shapes: about a third fewer shared-memory
+// bytes per value.  Complex128 systems and periodic cells run shape 5 as shape 2.
 template <int SHAPE> struct WsShape;
 template <> struct WsShape<0> { static constexpr int TX = 16, TY = 8, R = 2; };   //  8 consumer warps
 template <> struct WsShape<1> { static constexpr int TX = 16, TY = 12, R = 4; };  //  6
 template <> struct WsShape<2> { static constexpr int TX = 16, TY = 12, R = 2; };  // 12
 template <> struct WsShape<3> { static constexpr int TX = 16, TY = 8, R = 1; };   // 16
 template <> struct WsShape<4> { static constexpr int TX = 14, TY = 8, R = 2; };   //  7
-template <int TX, int TY, int R> struct WsWarps {
-  static constexpr int CW = OVC * TX * TY / (32 * R);      // consumer warps
+template <> struct WsShape<5> { static constexpr int TX = 16, TY = 12, R = 4; };  // 12 (complex64, 8-byte vectors)
+template <int TX, int TY, int R, int OV = OVC> struct WsWarps {
+  static constexpr int CW = OV * TX * TY / (32 * R);       // consumer warps
   static constexpr int THREADS = 32 * CW + 32;             // + the producer warp
-  // consumer thread t owns vector t % 4 of point (t / 4) % TX of row group t / (4 TX), whose
+  // consumer thread t owns vector t % OV of point (t / OV) % TX of row group t / (OV TX), whose
   // R rows are y-adjacent: the row groups must fill the tile and the warps exactly
-  static_assert(TY % R == 0 && CW * 32 == OVC * TX * (TY / R), "row groups must fill the tile and the warps");
+  static_assert(TY % R == 0 && CW * 32 == OV * TX * (TY / R), "row groups must fill the tile and the warps");
 };
 
 // H at R y-adjacent points (rows 0 .. R-1) of one plane, from their z queues Q[r] and
@@ -369,7 +375,7 @@ __device__ __forceinline__ void stencil_rows(const typename VT<P>::S *W, typenam
     for (int r = 0; r < R; r++) {
       const int hr = hs0 + r * SXO;
       const V s = T::add(T::add(T::add(Q[r][(QB + M - m) % QN], Q[r][(QB + M + m) % QN]),
-                                T::add(Sp[hr - m * OVC], Sp[hr + m * OVC])),
+                                T::add(Sp[hr - m * T::OV], Sp[hr + m * T::OV])),
                          T::add(col[M + r - m], col[M + r + m]));
       acc[r] = T::fma(W[m], s, acc[r]);
     }
@@ -435,7 +441,7 @@ __device__ __forceinline__ void stencil_rows_bloch(const SweepParams &p, const t
   for (int m = 1; m <= M; m++) {
 #pragma unroll
     for (int r = 0; r < R; r++) {
-      const V xm = S[hs0 + r * SXO - m * OVC], xp = S[hs0 + r * SXO + m * OVC];
+      const V xm = S[hs0 + r * SXO - m * T::OV], xp = S[hs0 + r * SXO + m * T::OV];
       const V zm = Q[r][(QB + M - m) % QN], zp = Q[r][(QB + M + m) % QN];
       const V ym = col[M + r - m], yp = col[M + r + m];
       const V s6 = T::add(T::add(T::add(zm, zp), T::add(xm, xp)), T::add(ym, yp));
@@ -469,7 +475,9 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
   typedef TmaGeom<M, TX, TY, U, OPS, BLOCH != 0> G;
   static_assert(M % U == 0, "M must be a multiple of U");
   static_assert(!OPS || U == 1, "the last Taylor term takes one plane per iteration");
-  constexpr int CW = WsWarps<TX, TY, R>::CW;
+  constexpr int OV = T::OV;       // thread vectors per (point, batch)
+  constexpr int CPL = TX * TY * OV;  // thread vectors per centre plane or operand tile
+  constexpr int CW = WsWarps<TX, TY, R, OV>::CW;
   constexpr int SC = G::SC, SH = G::SH;
   constexpr int SO = G::SO > 0 ? G::SO : 1;
   constexpr int QN = 2 * M + U;   // z-queue entries
@@ -485,11 +493,8 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
   __shared__ __align__(8) uint64_t ofull[SO], oempty[SO];
   __shared__ __align__(8) uint64_t ibar[IR];  // completes when s_item[seq % IR] is written
   __shared__ long s_item[IR];                 // item of the CTA's seq-th claim (-1: no more)
-  __shared__ int s_nl[IR];                    // whether that item can meet a projector sphere
   __shared__ int s_abort;
-  __shared__ long long s_wlim;  // cycles any one wait may take before the CTA gives up
   volatile int *abort_flag = &s_abort;
-  const long long *wlim = &s_wlim;
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
@@ -503,7 +508,6 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
     for (int s = 0; s < SO; s++) { mbar_init(&ofull[s], 1); mbar_init(&oempty[s], CW); }
     for (int s = 0; s < IR; s++) mbar_init(&ibar[s], 1);
     s_abort = 0;
-    s_wlim = src.wait_limit();
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();  // the only CTA-wide barrier: from here on the warps run decoupled
@@ -530,16 +534,6 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
             // returns the counter to zero for the next launch
             if ((long)t == n_items_all + (long)gridDim.x - 1) atomicExch(work, 0u);
             s_item[claimed % IR] = (long)t < n_items_all ? (long)t : -1;
-            if ((long)t < n_items_all) {
-              // the consumers read the non-local term only in items that can meet a sphere
-              const SweepParams *qp = nullptr;
-              const SweepMaps *mq = nullptr;
-              long local = 0;
-              src.item((long)t, qp, mq, local);
-              int tx0, ty0, kb0, za, zb;
-              item_geom(*qp, local, tx0, ty0, kb0, za, zb);
-              s_nl[claimed % IR] = item_meets_spheres(*qp, tx0 * TX, TX, ty0 * TY, TY, za, zb);
-            }
             mbar_arrive(&ibar[claimed % IR]);
             claimed++;
           }
@@ -586,7 +580,7 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
         if (progressed) {
           idle_since = clock64();
         } else {
-          if (*abort_flag || clock64() - idle_since > *wlim) {
+          if (*abort_flag || clock64() - idle_since > WAIT_LIMIT_CYCLES) {
             *abort_flag = 1;
             break;
           }
@@ -613,7 +607,7 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
     // slot to the consumers -----------------------------------------------------------------
     RingPos rp;
     for (long seq = 0;; seq++) {
-      if (!mbar_wait_or_abort(&ibar[seq % IR], (uint32_t)((seq / IR) & 1), abort_flag, wlim)) {
+      if (!mbar_wait_or_abort(&ibar[seq % IR], (uint32_t)((seq / IR) & 1), abort_flag)) {
         *abort_flag = 1;
         break;
       }
@@ -632,14 +626,15 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
       S_ cx, sx, cy, sy;
       bloch_phase<P>(p.kvec[3 * kidx] * p.L[0], cx, sx);
       bloch_phase<P>(p.kvec[3 * kidx + 1] * p.L[1], cy, sy);
-      constexpr int SLB = (int)((G::IN_BYTES + G::AUX_BYTES) / 16);
-      constexpr int SRB = SLB + (int)(G::STRIPX_BYTES / 16);
-      constexpr int STB = SRB + (int)(G::STRIPX_BYTES / 16);
-      constexpr int SBB = STB + (int)(G::STRIPY_BYTES / 16);
+      constexpr int VB = (int)sizeof(V);  // bytes per thread vector
+      constexpr int SLB = (int)((G::IN_BYTES + G::AUX_BYTES) / VB);
+      constexpr int SRB = SLB + (int)(G::STRIPX_BYTES / VB);
+      constexpr int STB = SRB + (int)(G::STRIPX_BYTES / VB);
+      constexpr int SBB = STB + (int)(G::STRIPY_BYTES / VB);
       bool gave_up = false;
       for (int z = z0; z < z1; z++) {
         const int hs = rp.slot;
-        if (!mbar_wait_or_abort(&hfull[hs], rp.phase, abort_flag, wlim)) {
+        if (!mbar_wait_or_abort(&hfull[hs], rp.phase, abort_flag)) {
           gave_up = true;
           break;
         }
@@ -647,26 +642,26 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
         if (sl || sr) {
           // box columns c with grid x = x0 - M + c beyond x = 0 (c < M) or beyond x = nx - 1
           const int cr0 = nx - x0 + M;  // first box column past the last grid column
-          for (int i = lane; i < 2 * G::SY * M * OVC; i += 32) {
-            const int v = i % OVC, j = (i / OVC) % M, row = (i / (OVC * M)) % G::SY, side = i / (OVC * M * G::SY);
+          for (int i = lane; i < 2 * G::SY * M * OV; i += 32) {
+            const int v = i % OV, j = (i / OV) % M, row = (i / (OV * M)) % G::SY, side = i / (OV * M * G::SY);
             if (side == 0 ? !sl : !sr) continue;
             const int c = side == 0 ? j : cr0 + j;
             if (c >= G::SX) continue;
-            const V a = box[(side == 0 ? SLB : SRB) + (row * M + j) * OVC + v];
-            box[(row * G::SX + c) * OVC + v] = apply_phase<P>(cx, sx, side == 0 ? -1 : 1, a);
+            const V a = box[(side == 0 ? SLB : SRB) + (row * M + j) * OV + v];
+            box[(row * G::SX + c) * OV + v] = apply_phase<P>(cx, sx, side == 0 ? -1 : 1, a);
           }
         }
         if (st || sb) {
           // box rows rr with grid y = y0 - M + rr beyond y = 0 (rr < M) or beyond y = ny - 1,
           // over the tile's columns (the star stencil never reads the corners)
           const int rb0 = ny - y0 + M;
-          for (int i = lane; i < 2 * M * TX * OVC; i += 32) {
-            const int v = i % OVC, c = (i / OVC) % TX, j = (i / (OVC * TX)) % M, side = i / (OVC * TX * M);
+          for (int i = lane; i < 2 * M * TX * OV; i += 32) {
+            const int v = i % OV, c = (i / OV) % TX, j = (i / (OV * TX)) % M, side = i / (OV * TX * M);
             if (side == 0 ? !st : !sb) continue;
             const int rr = side == 0 ? j : rb0 + j;
             if (rr >= G::SY) continue;
-            const V a = box[(side == 0 ? STB : SBB) + (j * TX + c) * OVC + v];
-            box[(rr * G::SX + c + M) * OVC + v] = apply_phase<P>(cy, sy, side == 0 ? -1 : 1, a);
+            const V a = box[(side == 0 ? STB : SBB) + (j * TX + c) * OV + v];
+            box[(rr * G::SX + c + M) * OV + v] = apply_phase<P>(cy, sy, side == 0 ? -1 : 1, a);
           }
         }
         __syncwarp();
@@ -683,25 +678,24 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
 
   // ---- consumers: no barrier between warps; a warp that gives up stops, and the others
   // give up at their next wait ----------------------------------------------------------------
-  const int v = tid % OVC;
-  const int lx = (tid / OVC) % TX;
-  const int ly0 = R * (tid / (OVC * TX));
-  const int hs0 = ((ly0 + M) * G::SX + (lx + M)) * OVC + v;  // row 0's vector in a halo plane
+  const int v = tid % OV;
+  const int lx = (tid / OV) % TX;
+  const int ly0 = R * (tid / (OV * TX));
+  const int hs0 = ((ly0 + M) * G::SX + (lx + M)) * OV + v;   // row 0's vector in a halo plane
   const int tsl0 = ly0 * TX + lx;                             // row 0's point in a tile
-  const int csl0 = tsl0 * OVC + v;                            // row 0's vector in a centre plane
-  constexpr int SXO = G::SX * OVC;
+  const int csl0 = tsl0 * OV + v;                             // row 0's vector in a centre plane
+  constexpr int SXO = G::SX * OV;
 
   RingPos rc, rh, ro;  // ring positions of the next centre / halo / operand load
   bool aborted = false;
   int *errp = src.err0();  // then the current item's system's
   for (long seq = 0;; seq++) {
-    if (!mbar_wait_or_abort(&ibar[seq % IR], (uint32_t)((seq / IR) & 1), abort_flag, wlim)) {
+    if (!mbar_wait_or_abort(&ibar[seq % IR], (uint32_t)((seq / IR) & 1), abort_flag)) {
       aborted = true;
       break;
     }
     const long item = s_item[seq % IR];
     if (item < 0) break;
-    const bool has_proj = s_nl[seq % IR] != 0;
     const SweepParams *pp;
     const SweepMaps *mp_unused;
     long local;
@@ -714,13 +708,13 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
     S_ W[M + 1];
 #pragma unroll
     for (int m = 0; m <= M; m++) W[m] = T::coef(p.w[m], p.wf[m]);
-    const typename W0T<P>::type w0 = P == P_C64 ? (typename W0T<P>::type)p.wf[0] : (typename W0T<P>::type)p.w[0];
+    const typename W0T<P>::type w0 = P != P_C128 ? (typename W0T<P>::type)p.wf[0] : (typename W0T<P>::type)p.w[0];
     const S_ CR = T::coef(p.cr, p.crf), CI = T::coef(p.ci, p.cif);
     int tx, ty, kb, z0, z1;
     item_geom(p, local, tx, ty, kb, z0, z1);
     const int kidx = kb / p.n_batches;
     const Epi epi = make_epi(p, kidx);
-    const bool do_obs = p.do_obs != 0;
+    const bool has_proj = p.has_proj != 0, do_obs = p.do_obs != 0;
     const V *nlk = nl_column<P>(p, kb, v);
     const int n_ent = p.n_ent;
     const int gx = tx * TX + lx, gy0 = ty * TY + ly0;
@@ -735,8 +729,8 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
     for (int r = 0; r < R; r++) own[r] = gx < nx && gy0 + r < ny;
     const int nl = loads_of<M, U>(0, z0, z1);
     // vector index of row 0's point in the first output plane (advances one plane per output)
-    long idx = ((long)kb * N + ((long)z0 * ny + gy0) * nx + gx) * OVC + v;
-    const long row = (long)nx * OVC;
+    long idx = ((long)kb * N + ((long)z0 * ny + gy0) * nx + gx) * OV + v;
+    const long row = (long)nx * OV;
     V Q[R][QN];
 #pragma unroll
     for (int r = 0; r < R; r++)
@@ -750,7 +744,7 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
     auto iteration = [&](auto rq) {
       constexpr int RQ = decltype(rq)::value;
       const int cs = rc.slot;
-      if (!mbar_wait_or_abort(&cfull[cs], rc.phase, abort_flag, wlim)) {
+      if (!mbar_wait_or_abort(&cfull[cs], rc.phase, abort_flag)) {
         aborted = true;
         return;
       }
@@ -758,7 +752,7 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
 #pragma unroll
       for (int u = 0; u < U; u++) {
 #pragma unroll
-        for (int r = 0; r < R; r++) Q[r][(RQ + u) % QN] = cslot[u * G::CPLANE + csl0 + r * TX * OVC];
+        for (int r = 0; r < R; r++) Q[r][(RQ + u) % QN] = cslot[u * CPL + csl0 + r * TX * OV];
         if constexpr (BLOCH) {
           // a plane beyond a z face was loaded from its periodic image: apply the Bloch phase
           const int zq = z0 - M + U * l + u;
@@ -776,7 +770,7 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
         const int zf = z0 + U * (l - LP);
         const int hs = rh.slot;
         // periodic cells: the slot is ready once the patcher warp has written the face images
-        if (!mbar_wait_or_abort(BLOCH ? &hready[hs] : &hfull[hs], rh.phase, abort_flag, wlim)) {
+        if (!mbar_wait_or_abort(BLOCH ? &hready[hs] : &hfull[hs], rh.phase, abort_flag)) {
           aborted = true;
           return;
         }
@@ -787,7 +781,7 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
         int os = 0;
         if constexpr (OPS) {
           os = ro.slot;
-          if (!mbar_wait_or_abort(&ofull[os], ro.phase, abort_flag, wlim)) {
+          if (!mbar_wait_or_abort(&ofull[os], ro.phase, abort_flag)) {
             aborted = true;
             return;
           }
@@ -799,9 +793,9 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
           LastOperands<P> o;
           if constexpr (OPS) {
             o.hi = ob[c];
-            o.lo = ob[G::CPLANE + c];
-            o.t1 = ob[2 * G::CPLANE + c];
-            o.t2 = ob[3 * G::CPLANE + c];
+            o.lo = ob[CPL + c];
+            o.t1 = ob[2 * CPL + c];
+            o.t2 = ob[3 * CPL + c];
           } else {
             (void)c;
             o.hi = o.lo = o.t1 = o.t2 = T::zero();
@@ -823,9 +817,9 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
           if constexpr (BLOCH) {
             stencil_rows_bloch<M, P, QB, QN, R>(p, W, w0, Q, xs, hs0, SXO, ve, acc, gax, need_grad, grads);
           } else {
-            stencil_rows<M, P, QB, QN, R>(W, w0, Q, xs + u * G::PLANE, hs0, SXO, ve, acc);
+            stencil_rows<M, P, QB, QN, R>(W, w0, Q, xs + u * G::SX * G::SY * OV, hs0, SXO, ve, acc);
           }
-          const long iu = idx + (long)u * plane_pts * OVC;
+          const long iu = idx + (long)u * plane_pts * OV;
 #pragma unroll
           for (int r = 0; r < R; r++) {
             const bool live = own[r] && (zf + u < z1);
@@ -840,7 +834,7 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
                 }
               }
             }
-            finish_point<P, MODE>(epi, CR, CI, live, iu + r * row, v, c0, acc[r], operands(csl0 + r * TX * OVC));
+            finish_point<P, MODE>(epi, CR, CI, live, iu + r * row, v, c0, acc[r], operands(csl0 + r * TX * OV));
           }
         });
         __syncwarp();
@@ -848,7 +842,7 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
           mbar_arrive(&hempty[hs]);
           if constexpr (OPS) mbar_arrive(&oempty[os]);
         }
-        idx += U * plane_pts * OVC;
+        idx += U * plane_pts * OV;
         rh.next<SH>();
         if (OPS) ro.next<SO>();
       }
@@ -880,14 +874,14 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
 }
 
 template <int M, int P, int MODE, int TX, int TY, int R, int U, int BLOCH>
-__global__ void __launch_bounds__(WsWarps<TX, TY, R>::THREADS + 32 * BLOCH, 1)
+__global__ void __launch_bounds__(WsWarps<TX, TY, R, VT<P>::OV>::THREADS + 32 * BLOCH, 1)
 ws_sweep_kernel(const __grid_constant__ SweepMaps maps, const __grid_constant__ SweepParams p) {
   const SingleSrc src{&p, &maps};
   ws_sweep_body<M, P, MODE, TX, TY, R, U, false, BLOCH>(src, p.work);
 }
 
 template <int M, int P, int MODE, int TX, int TY, int R, int U>
-__global__ void __launch_bounds__(WsWarps<TX, TY, R>::THREADS, 1)
+__global__ void __launch_bounds__(WsWarps<TX, TY, R, VT<P>::OV>::THREADS, 1)
 ws_sweep_batch_kernel(const __grid_constant__ BatchSweepArgs a) {
   const BatchSrc src{&a};
   ws_sweep_body<M, P, MODE, TX, TY, R, U, true, 0>(src, a.work);
@@ -908,7 +902,7 @@ static cudaError_t launch_ws_t(const SweepMaps &maps, const SweepParams &p, int 
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     grid = (int)(p.n_items < sms ? p.n_items : sms);
   }
-  k<<<grid, WsWarps<TX, TY, R>::THREADS + 32 * BLOCH, G::SMEM, s>>>(maps, p);  // (+ the patcher warp)
+  k<<<grid, WsWarps<TX, TY, R, VT<P>::OV>::THREADS + 32 * BLOCH, G::SMEM, s>>>(maps, p);  // (+ the patcher warp)
   return cudaGetLastError();
 }
 
@@ -926,7 +920,7 @@ static cudaError_t launch_ws_batch_t(const BatchSweepArgs &a, cudaStream_t s) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = (int)(a.total_items < sms ? a.total_items : sms);
   if (grid <= 0) return cudaSuccess;
-  k<<<grid, WsWarps<TX, TY, R>::THREADS, G::SMEM, s>>>(a);
+  k<<<grid, WsWarps<TX, TY, R, VT<P>::OV>::THREADS, G::SMEM, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -939,11 +933,18 @@ cudaError_t launch_ws_batch_shape(int M, int prec, int mode, const BatchSweepArg
     case MODE_LAST: return launch_ws_batch_t<SHAPE, MM, PP, MODE_LAST>(a, s);     \
   }                                                                               \
   return cudaErrorInvalidValue;
-  if (M == 2) {
-    if (prec == P_C64) { TDKS_WSB_MODES(2, P_C64) } else { TDKS_WSB_MODES(2, P_C128) }
-  }
-  if (M == 4) {
-    if (prec == P_C64) { TDKS_WSB_MODES(4, P_C64) } else { TDKS_WSB_MODES(4, P_C128) }
+  if constexpr (SHAPE == 5) {
+    // complex64: one complex value per thread vector; complex128 runs shape 2
+    if (prec != P_C64) return launch_ws_batch_shape<2>(M, prec, mode, a, s);
+    if (M == 2) { TDKS_WSB_MODES(2, P_C64S) }
+    if (M == 4) { TDKS_WSB_MODES(4, P_C64S) }
+  } else {
+    if (M == 2) {
+      if (prec == P_C64) { TDKS_WSB_MODES(2, P_C64) } else { TDKS_WSB_MODES(2, P_C128) }
+    }
+    if (M == 4) {
+      if (prec == P_C64) { TDKS_WSB_MODES(4, P_C64) } else { TDKS_WSB_MODES(4, P_C128) }
+    }
   }
 #undef TDKS_WSB_MODES
   return cudaErrorInvalidValue;
@@ -975,8 +976,24 @@ static cudaError_t launch_ws_bc(int M, int prec, int mode, const SweepMaps &maps
 template <int SHAPE>
 cudaError_t launch_ws_shape(int M, int prec, int mode, int bloch, const SweepMaps &maps, const SweepParams &p,
                             int grid, cudaStream_t s) {
-  return bloch ? launch_ws_bc<SHAPE, 1>(M, prec, mode, maps, p, grid, s)
-               : launch_ws_bc<SHAPE, 0>(M, prec, mode, maps, p, grid, s);
+  if constexpr (SHAPE == 5) {
+    // complex64 finite boxes: one complex value per thread vector; the rest run shape 2
+    if (bloch || prec != P_C64) return launch_ws_shape<2>(M, prec, mode, bloch, maps, p, grid, s);
+#define TDKS_WS5_MODES(MM)                                                                       \
+  switch (mode) {                                                                                \
+    case MODE_FIRST: return launch_ws_t<5, MM, P_C64S, MODE_FIRST, 0>(maps, p, grid, s);         \
+    case MODE_MID: return launch_ws_t<5, MM, P_C64S, MODE_MID, 0>(maps, p, grid, s);             \
+    case MODE_LAST: return launch_ws_t<5, MM, P_C64S, MODE_LAST, 0>(maps, p, grid, s);           \
+  }                                                                                              \
+  return cudaErrorInvalidValue;
+    if (M == 2) { TDKS_WS5_MODES(2) }
+    if (M == 4) { TDKS_WS5_MODES(4) }
+#undef TDKS_WS5_MODES
+    return cudaErrorInvalidValue;
+  } else {
+    return bloch ? launch_ws_bc<SHAPE, 1>(M, prec, mode, maps, p, grid, s)
+                 : launch_ws_bc<SHAPE, 0>(M, prec, mode, maps, p, grid, s);
+  }
 }
 
 }  // namespace tdks

@@ -113,6 +113,7 @@ template <> struct VT<P_C128> {
   static __device__ __forceinline__ V ld(const V *p) { return __ldg(p); }
   static __device__ __forceinline__ void to_d(V a, double2 *o) { o[0] = a; }
   static constexpr int CPV = 1;  // complex values per vector
+  static constexpr int OV = 4;   // vectors per (point, batch): 64 bytes
 };
 
 template <> struct VT<P_C64> {
@@ -142,6 +143,35 @@ template <> struct VT<P_C64> {
     o[1] = make_double2(q.x, q.y);
   }
   static constexpr int CPV = 2;
+  static constexpr int OV = 4;
+};
+
+// complex64 with one complex value per thread vector (one packed 64-bit register); the
+// same per-component arithmetic as VT<P_C64>, on half the data per thread.
+template <> struct VT<P_C64S> {
+  typedef u64 V;
+  typedef u64 S;
+  typedef float R;
+  static __device__ __forceinline__ V zero() { return 0ull; }
+  static __device__ __forceinline__ S bc(double s) { float f = (float)s; return pk2(f, f); }
+  static __device__ __forceinline__ S coef(double, float f) { return pk2(f, f); }
+  static __device__ __forceinline__ S diag(R ve, float w0) { const float d = ve + w0; return pk2(d, d); }
+  static __device__ __forceinline__ V add(V a, V b) { return add2(a, b); }
+  static __device__ __forceinline__ V sub(V a, V b) { return sub2(a, b); }
+  static __device__ __forceinline__ V mul(S s, V a) { return mul2(s, a); }
+  static __device__ __forceinline__ V fma(S s, V a, V c) { return fma2(s, a, c); }
+  static __device__ __forceinline__ V cmul(S cr, S ci, V a) { return fma2(ci, ipos2(a), mul2(cr, a)); }
+  static __device__ __forceinline__ V negi(V a) {
+    const float2 p = up2(a);
+    return pk2(p.y, -p.x);
+  }
+  static __device__ __forceinline__ V ld(const V *p) { return __ldg(reinterpret_cast<const unsigned long long *>(p)); }
+  static __device__ __forceinline__ void to_d(V a, double2 *o) {
+    const float2 p = up2(a);
+    o[0] = make_double2(p.x, p.y);
+  }
+  static constexpr int CPV = 1;
+  static constexpr int OV = 8;
 };
 
 // ---------------------------------------------------------------------------------
@@ -170,7 +200,7 @@ template <> struct Combine<P_C128> {
     dl = 0.0;
   }
   // sum over the 4 consecutive lanes that hold one (point, batch)
-  static __device__ __forceinline__ void reduce4(A &h, A &l) {
+  static __device__ __forceinline__ void reduce_point(A &h, A &l) {
     h += __shfl_xor_sync(0xffffffffu, h, 1);
     h += __shfl_xor_sync(0xffffffffu, h, 2);
     (void)l;
@@ -210,7 +240,8 @@ template <> struct Combine<P_C64> {
     dh = two_sum(sa, sb, ec);
     dl = ea + eb + ec;
   }
-  static __device__ __forceinline__ void reduce4(A &h, A &l) {
+  // sum over the 4 consecutive lanes that hold one (point, batch)
+  static __device__ __forceinline__ void reduce_point(A &h, A &l) {
 #pragma unroll
     for (int o = 1; o <= 2; o <<= 1) {
       const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
@@ -225,6 +256,34 @@ template <> struct Combine<P_C64> {
   static __device__ __forceinline__ void store_density(double *slot, double wocc, A h, A l) {
     (void)wocc;
     *reinterpret_cast<float2 *>(slot) = make_float2(h, l);
+  }
+};
+
+// One complex value per lane: the same state update as Combine<P_C64> per component, the
+// density summed over the 8 lanes of a (point, batch).
+template <> struct Combine<P_C64S> {
+  typedef u64 V;
+  typedef float A;
+  static __device__ __forceinline__ void run(V &hi, V lo, V t1, V t2, V t3, V t4, V &lo_out, A &dh, A &dl) {
+    const u64 d = add2(add2(add2(t1, t2), t3), t4);
+    u64 h, l;
+    df_add2(hi, lo, d, h, l);
+    hi = h;
+    lo_out = l;
+    dh = Combine<P_C64>::sq_parts(h, l, dl);
+  }
+  static __device__ __forceinline__ void reduce_point(A &h, A &l) {
+#pragma unroll
+    for (int o = 1; o <= 4; o <<= 1) {
+      const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
+      float e;
+      h = two_sum(h, oh, e);
+      l = l + ol + e;
+    }
+  }
+  static __device__ __forceinline__ double value(A h, A l) { return (double)h + (double)l; }
+  static __device__ __forceinline__ void store_density(double *slot, double wocc, A h, A l) {
+    Combine<P_C64>::store_density(slot, wocc, h, l);
   }
 };
 

@@ -9,6 +9,13 @@ graph), and the batch is rebuilt whenever a job joins or leaves.  A job that arr
 while others are on the GPU joins at the next tick; a finished job releases its memory
 and slot at once.  Latency is measured from arrival to the moment the job's results
 (its observable records and final orbitals' norm) are on the host.
+
+A bad request fails alone.  Every job ends with a status: "done"; "rejected" (its footprint
+exceeds the whole HBM budget); "invalid" (a non-finite number in its inputs, found on the
+host before any device allocation); "failed" (the library refused it, e.g. an allocation
+that did not fit, or its batch reported an error; the job's memory is released and the
+others go on); "cancelled" (``Server.cancel``, while queued or active).  Percentiles are
+taken over the jobs that finished.
 """
 from __future__ import annotations
 
@@ -38,6 +45,8 @@ class Job:
     inputs: Optional[I.Inputs] = None  # the request's payload (built at admission when absent)
     system: Optional[System] = None
     nbytes: int = 0
+    status: str = "queued"  # queued, active, done, rejected, invalid, failed, cancelled
+    error: str = ""
 
     @property
     def latency(self) -> float:
@@ -102,32 +111,78 @@ class Server:
         self.batches: Dict[Tuple, Tuple[Tuple[int, ...], Batch]] = {}
         self.ticks = 0
         self.max_concurrent = 0
+        self._cancel: set = set()
 
     # -- admission / eviction -----------------------------------------------------------
+    def cancel(self, jid: int):
+        """Cancel a job: dropped from the queue, or released at the next tick if active."""
+        self._cancel.add(jid)
+
+    def _end(self, job: Job, status: str, now: float, error: str = ""):
+        """A job that leaves without results (rejected, invalid, failed, cancelled)."""
+        job.status, job.error, job.finished = status, error, now
+        job.inputs = None
+        self.done.append(job)
+
+    @staticmethod
+    def _finite_inputs(inp: Optional[I.Inputs]) -> bool:
+        if inp is None:
+            return True
+        return all(a is None or bool(np.all(np.isfinite(a))) for a in (inp.vloc, inp.psi0, inp.pos, inp.D))
+
     def _admit(self, job: Job, now: float):
         job.nbytes = job_bytes(job.spec)
         inp = job.inputs if job.inputs is not None else self.make_inputs(job.spec)
-        job.system = System(job.spec, inp, stream=self.stream)
-        job.system.set_clock(0.0, job.spec.dt, job.spec.substeps)
+        if not self._finite_inputs(inp):
+            self._end(job, "invalid", now, "non-finite input")
+            return
+        try:
+            job.system = System(job.spec, inp, stream=self.stream)
+            job.system.set_clock(0.0, job.spec.dt, job.spec.substeps)
+        except Exception as exc:  # the library refused this job (e.g. out of memory): it fails alone
+            if job.system is not None:
+                job.system.close()
+                job.system = None
+            self._end(job, "failed", now, str(exc))
+            return
         job.admitted = now
+        job.status = "active"
         self.used += job.nbytes
         self.peak_used = max(self.peak_used, self.used)
         self.active.append(job)
         self.max_concurrent = max(self.max_concurrent, len(self.active))
 
-    def _finish(self, job: Job, now_fn):
-        job.records = job.system.reductions(0, job.n_steps)
-        job.orbitals = job.system.get_orbitals() if self.keep_orbitals else None
-        job.finished = now_fn()
-        job.system.close()
-        job.system = None
+    def _release(self, job: Job):
+        if job.system is not None:
+            job.system.close()
+            job.system = None
         job.inputs = None
         self.used -= job.nbytes
         self.active.remove(job)
+
+    def _finish(self, job: Job, now_fn):
+        try:
+            job.records = job.system.reductions(0, job.n_steps)
+            job.orbitals = job.system.get_orbitals() if self.keep_orbitals else None
+        except Exception as exc:
+            self._release(job)
+            self._end(job, "failed", now_fn(), str(exc))
+            return
+        job.finished = now_fn()
+        job.status = "done"
+        self._release(job)
         self.done.append(job)
 
+    def _fail_group(self, jobs: List[Job], key, exc: Exception, now: float):
+        """A batch that reported an error: its jobs fail, the others are untouched."""
+        if key in self.batches:
+            self.batches.pop(key)[1].close()
+        for j in jobs:
+            self._release(j)
+            self._end(j, "failed", now, str(exc))
+
     # -- one tick: every active job advances ---------------------------------------------
-    def _tick(self):
+    def _tick(self, now: float = 0.0):
         groups: Dict[Tuple, List[Job]] = {}
         for j in self.active:
             key = (j.spec.prec, j.spec.fd_order, j.spec.substeps)
@@ -138,12 +193,16 @@ class Server:
         advanced = []
         for key, jobs in groups.items():
             ids = tuple(j.jid for j in jobs)
-            if key not in self.batches or self.batches[key][0] != ids:
-                if key in self.batches:
-                    self.batches[key][1].close()
-                self.batches[key] = (ids, Batch([j.system for j in jobs], stream=self.stream))
-            q = min(self.quantum, min(j.n_steps - j.steps_done for j in jobs))
-            self.batches[key][1].propagate(q, use_graph=self.use_graph)
+            try:
+                if key not in self.batches or self.batches[key][0] != ids:
+                    if key in self.batches:
+                        self.batches.pop(key)[1].close()
+                    self.batches[key] = (ids, Batch([j.system for j in jobs], stream=self.stream))
+                q = min(self.quantum, min(j.n_steps - j.steps_done for j in jobs))
+                self.batches[key][1].propagate(q, use_graph=self.use_graph)
+            except Exception as exc:
+                self._fail_group(jobs, key, exc, now)
+                continue
             advanced.append((jobs, q))
         self.sync()
         for jobs, q in advanced:
@@ -162,10 +221,17 @@ class Server:
             t = now()
             while pending and pending[0].arrival <= t:
                 queue.append(pending.pop(0))
+            for j in [j for j in queue if j.jid in self._cancel]:
+                queue.remove(j)
+                self._end(j, "cancelled", t)
+            for j in [j for j in self.active if j.jid in self._cancel]:
+                self._release(j)
+                self._end(j, "cancelled", t)
             while queue and len(self.active) < self.max_slots:
                 nb = job_bytes(queue[0].spec)
                 if nb > self.budget:
-                    raise ValueError(f"job {queue[0].jid} needs {nb} bytes, more than the whole budget")
+                    self._end(queue.pop(0), "rejected", t, f"needs {nb} bytes, more than the whole budget")
+                    continue
                 if self.used + nb > self.budget:
                     break
                 self._admit(queue.pop(0), t)
@@ -173,7 +239,7 @@ class Server:
                 if pending:
                     time.sleep(max(0.0, (pending[0].arrival - now()) * time_scale))
                 continue
-            self._tick()
+            self._tick(t)
             for j in [j for j in self.active if j.steps_done >= j.n_steps]:
                 self._finish(j, now)
         for _, b in self.batches.values():
@@ -183,9 +249,14 @@ class Server:
         return self.done
 
     def report(self) -> dict:
-        lat = np.array([j.latency for j in self.done])
-        upd = sum(j.updates for j in self.done)
-        return {"jobs": len(self.done), "wall_s": self.wall, "updates": upd,
+        ok = [j for j in self.done if j.status == "done"]
+        lat = np.array([j.latency for j in ok]) if ok else np.array([math.nan])
+        upd = sum(j.updates for j in ok)
+        status: Dict[str, int] = {}
+        for j in self.done:
+            status[j.status] = status.get(j.status, 0) + 1
+        return {"jobs": len(ok), "wall_s": self.wall, "updates": upd,
                 "throughput": upd / self.wall if self.wall > 0 else math.nan,
                 "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-                "ticks": self.ticks, "peak_hbm_bytes": self.peak_used, "max_concurrent": self.max_concurrent}
+                "ticks": self.ticks, "peak_hbm_bytes": self.peak_used, "max_concurrent": self.max_concurrent,
+                "status": status}

@@ -94,11 +94,27 @@ class System:
     def set_tile(self, tx, ty, zc=0):
         _lib.check(self.lib.tdks_set_tile(self.h, tx, ty, zc))
 
-    def set_wait_limit(self, cycles: int, withhold: bool = False):
-        """Bound (GPU clock cycles) of every wait in the TMA sweeps; 0 restores the default
-        (~2 s).  A wait that runs out makes the next synchronising call raise TDKS_ETIMEOUT.
-        withhold=True injects that failure (tests): the sweeps' producers issue no copy."""
-        _lib.check(self.lib.tdks_set_wait_limit(self.h, int(cycles), int(bool(withhold))))
+    def set_tsurff(self, box, p):
+        """t-SURFF amplitudes through the surface of the box of grid planes `box` =
+        (i0, i1, j0, j1, k0, k1) for momenta p [n_p, 3], accumulated from the next propagation
+        on; an empty p turns it off."""
+        box = np.ascontiguousarray(box, dtype=np.int32)
+        p = np.ascontiguousarray(p, dtype=np.float64).reshape(-1, 3)
+        self._ts_np = p.shape[0]
+        _lib.check(self.lib.tdks_set_tsurff(self.h, _dp(box), p.shape[0], _dp(p)))
+
+    def tsurff(self):
+        """(b [n_orb, n_p] complex128, time since the accumulation started)."""
+        b = np.empty((self.spec.n_orb, self._ts_np), dtype=np.complex128)
+        t = ctypes.c_double(0.0)
+        _lib.check(self.lib.tdks_get_tsurff(self.h, _dp(b), ctypes.byref(t)))
+        return b, t.value
+
+    def set_failure_injection(self, withhold: bool):
+        """Failure injection (tests): the TMA sweeps' producers withhold every copy, so the
+        consumers' bounded waits run out (~2 s) and the next synchronising call raises
+        TDKS_ETIMEOUT; False restores normal sweeps."""
+        _lib.check(self.lib.tdks_set_failure_injection(self.h, int(bool(withhold))))
 
     def set_sweep_path(self, path: int):
         """0: TMA-fed warp-specialised sweep where it applies (finite boxes, 16x8 tiles);

@@ -56,6 +56,11 @@ def test_calls_on_a_null_system_are_refused(lib):
     assert lib.tdks_apply_H(None, 0.0, None, None) == EINVAL
     out = ctypes.c_void_p()
     assert lib.tdks_batch_create(None, 0, None, ctypes.byref(out)) == EINVAL
+    assert lib.tdks_set_tsurff(None, None, 0, None) == EINVAL
+    assert lib.tdks_get_tsurff(None, None, None) == EINVAL
+    assert lib.tdks_set_failure_injection(None, 0) == EINVAL
+    assert lib.tdks_fma_rate(0, None) == EINVAL
+    assert lib.tdks_fma_rate(7, ctypes.byref(ctypes.c_double())) == EINVAL
 
 
 def test_noalloc_entry_refuses_bad_arguments(lib):
@@ -76,6 +81,8 @@ def test_sweep_shape_table(lib):
         assert lib.tdks_sweep_shape_info(shape, None, ctypes.byref(tx), ctypes.byref(ty), ctypes.byref(r),
                                          ctypes.byref(w)) == 0
         assert ty.value % r.value == 0
-        assert w.value * 32 == 4 * tx.value * ty.value // r.value
+        # 16-byte thread vectors (4 per point); shape 5 runs complex64 systems with 8-byte ones
+        vectors = 8 if shape == 5 else 4
+        assert w.value * 32 == vectors * tx.value * ty.value // r.value
     assert lib.tdks_sweep_shape_info(n.value, None, None, None, None, None) == EINVAL
     assert lib.tdks_sweep_shape_info(-1, None, None, None, None, None) == EINVAL

@@ -2,13 +2,15 @@
 
 Every wait in the warp-specialised sweep is bounded; a wait that runs out makes the CTA
 give up, the producer drains its copies in flight, and the host reports TDKS_ETIMEOUT at
-the next synchronising call.  tdks_set_wait_limit(cycles, withhold=1) injects the failure:
-the sweeps' producer warps claim no work item and issue no copy, so every consumer warp's
-first wait (for a claim that nothing makes) runs out after ~1 ms.  Nothing is read or
-written by those sweeps and no copy is in flight.  The test checks the status, and that the
+the next synchronising call.  tdks_set_failure_injection(1) injects the failure: the
+sweeps' producer warps claim no work item and issue no copy, so every consumer warp's first
+wait (for a claim that nothing makes) runs out after its bound (~2 s).  Nothing is read or
+written by that sweep and no copy is in flight.  The test checks the status, and that the
 same system then propagates exactly like the oracle once the injection is off and the
 orbitals are set again.
 """
+import time
+
 import numpy as np
 import pytest
 
@@ -34,13 +36,19 @@ def test_wait_that_runs_out_is_reported_and_the_system_recovers(prec):
     spec = ragged_molecule(prec)
     inp = I.make_inputs(spec)
     s = System(spec, inp, stream=torch.cuda.current_stream().cuda_stream)
-    s.set_wait_limit(2_000_000, withhold=True)  # ~1 ms per wait
-    s.propagate(0.0, 0.02, 2, 1)
+    s.set_failure_injection(True)
+    packed = s.pack(I.random_orbitals(spec, 3))
+    view = np.float32 if packed.dtype == np.complex64 else np.float64
+    din = torch.from_numpy(packed.view(view)).cuda()
+    dout = torch.empty_like(din)
+    t0 = time.perf_counter()
+    s.apply_H(0.0, din.data_ptr(), dout.data_ptr())  # one sweep, which gives up after ~2 s
     with pytest.raises(TdksError) as e:
-        s.reductions(0, 2)
+        s.reductions(0, 0)
     assert e.value.code == 4 and "gave up" in str(e.value)
-    # the error word was cleared: restore the bound and the state, then a normal run
-    s.set_wait_limit(0, withhold=False)
+    assert time.perf_counter() - t0 < 30.0
+    # the error word was cleared: injection off, the state set again, then a normal run
+    s.set_failure_injection(False)
     s.set_orbitals(inp.psi0)
     n0 = s.step_count()
     s.propagate(0.0, 0.02, 3, 1)

@@ -141,7 +141,8 @@ def test_apply_H_is_independent_of_sweep_shape(prec):
     assert n >= 2
     for sh in range(n):
         tx, ty, rows, warps = shape_info(sh)
-        assert 4 * tx * ty == 32 * warps * rows and ty % rows == 0
+        vectors = 8 if sh == 5 else 4  # shape 5: one complex64 value per thread vector
+        assert vectors * tx * ty == 32 * warps * rows and ty % rows == 0
         sysm.set_sweep_shape(-1, sh)
         assert sysm.sweep_shapes() == [sh] * 4
         outs.append(_apply_gpu(sysm, psi, 0.3))
@@ -149,6 +150,29 @@ def test_apply_H_is_independent_of_sweep_shape(prec):
     for o in outs[1:]:
         assert rel_err(o, outs[0]) < tol
     sysm.close()
+
+
+@pytest.mark.parametrize("order", [4, 8])
+def test_single_complex_shape_matches_oracle_c64(order):
+    """Shape 5 (one complex64 value per thread vector, four y-adjacent points per thread) on a
+    grid that is ragged for its 16 x 12 tile: H applications and a propagation with
+    projectors, laser and LDA against the FP64 oracle."""
+    spec = ragged_molecule(I.PREC_C64, fd_order=order, n_orb=13)
+    inp = I.make_inputs(spec)
+    sysm = _system(spec, inp)
+    sysm.set_sweep_shape(-1, 5)
+    psi = I.random_orbitals(spec, 21).astype(np.complex64).astype(np.complex128)
+    got = _apply_gpu(sysm, psi, 0.4)
+    o = oracle.System(spec, inp)
+    ref = o.apply_H(psi, 0.4, o.vx_of(inp.psi0))
+    assert rel_err(got, ref) < 5e-6
+    sysm.propagate(0.0, 0.02, 3, 1)
+    rec = sysm.reductions(0, 3)
+    out = sysm.get_orbitals()
+    sysm.close()
+    psi_o, rec_o = o.propagate(inp.psi0, 0.0, 0.02, 3, 1)
+    assert rel_err(out, psi_o) < 1e-5
+    assert np.max(np.abs(rec[:, 4:7] - rec_o[:, 4:7])) < 1e-5 * np.max(np.abs(rec_o[:, 4:7]))
 
 
 def test_mixed_sweep_shapes_match_oracle_c128():

@@ -3,6 +3,7 @@ replaced by fakes that count steps, so admission by HBM budget and slot count, g
 (precision, FD order, sub-steps), batch rebuilds on join and leave, the step quantum and the
 report are checked without a GPU."""
 import dataclasses
+import math
 
 import numpy as np
 import pytest
@@ -72,10 +73,10 @@ def _serve(jobs, budget, slots=64, quantum=7):
     used = []
     tick = srv._tick
 
-    def watched_tick():
+    def watched_tick(now=0.0):
         used.append(srv.used)
         assert srv.used <= budget and len(srv.active) <= slots
-        tick()
+        tick(now)
 
     srv._tick = watched_tick
     done = srv.run(jobs, time_scale=1e-6)  # arrivals replayed a million times faster
@@ -120,10 +121,104 @@ def test_quantum_never_overshoots_a_job():
     assert {j.jid: j.steps_done for j in done} == {0: 5, 1: 12, 2: 3}
 
 
-def test_a_job_larger_than_the_budget_is_refused():
-    jobs = _jobs(2)
-    with pytest.raises(ValueError, match="more than the whole budget"):
-        _serve(jobs, budget=16)
+def test_a_job_larger_than_the_budget_is_rejected_alone():
+    jobs = _jobs(6, seed=21)
+    sizes = sorted(serving.job_bytes(j.spec) for j in jobs)
+    budget = sizes[-2]  # the largest job alone does not fit
+    big = max(jobs, key=lambda j: serving.job_bytes(j.spec))
+    srv, done, _ = _serve(jobs, budget=budget)
+    status = {j.jid: j.status for j in done}
+    assert status.pop(big.jid) == "rejected" and set(status.values()) == {"done"}
+    assert "more than the whole budget" in big.error
+    assert srv.report()["status"] == {"done": len(jobs) - 1, "rejected": 1}
+
+
+class RefusingSystem(FakeSystem):
+    """The library refusing one job at creation (an allocation that does not fit)."""
+    refuse = set()
+
+    def __init__(self, spec, inputs, stream=None):
+        if spec.seed in RefusingSystem.refuse:
+            from paper_1912_07921_gb300._lib import TdksError
+            raise TdksError(2, "cudaMalloc: out of memory")
+        super().__init__(spec, inputs, stream)
+
+
+def test_an_allocation_refusal_fails_that_job_alone(monkeypatch):
+    jobs = _jobs(8, seed=23)
+    RefusingSystem.refuse = {jobs[3].spec.seed}
+    monkeypatch.setattr(serving, "System", RefusingSystem)
+    srv, done, used = _serve(jobs, budget=10 ** 12)
+    status = {j.jid: j.status for j in done}
+    assert status[3] == "failed" and "out of memory" in jobs[3].error
+    assert all(v == "done" for k, v in status.items() if k != 3)
+    assert srv.used == 0 and FakeSystem.live == 0  # nothing was charged or left for the refused job
+
+
+def test_a_non_finite_input_is_found_before_any_allocation():
+    jobs = _jobs(5, seed=25)
+    inp = I.Inputs(vloc=np.zeros(4), psi0=np.array([1.0, np.nan]), pos=np.zeros((0, 3)), D=np.zeros((0, 4)),
+                   kpts=np.zeros((1, 3)), kw=np.ones(1))
+    jobs[2].inputs = inp
+    srv = serving.Server(10 ** 12, quantum=7, make_inputs=lambda spec: None)
+    done = srv.run(jobs, time_scale=1e-6)
+    status = {j.jid: j.status for j in done}
+    assert status[2] == "invalid" and jobs[2].system is None
+    assert sum(v == "done" for v in status.values()) == 4
+    assert FakeSystem.live == 0
+
+
+def test_cancelled_jobs_leave_the_queue_or_release_their_memory():
+    jobs = _jobs(6, seed=27)
+    for j in jobs:
+        j.arrival = 0.0
+    jobs[5].n_steps = 10 ** 6  # long enough to be cancelled while active
+    srv = serving.Server(10 ** 12, max_slots=5, quantum=3, make_inputs=lambda spec: None)
+    tick = srv._tick
+    calls = []
+
+    def ticking(now=0.0):
+        calls.append(1)
+        if len(calls) == 2:
+            srv.cancel(5)   # active by now
+            srv.cancel(4)   # maybe active, maybe finished
+        tick(now)
+
+    srv._tick = ticking
+    srv.cancel(0)  # cancelled while queued, never admitted
+    done = srv.run(jobs, time_scale=1e-6)
+    status = {j.jid: j.status for j in done}
+    assert status[0] == "cancelled" and jobs[0].system is None and math.isnan(jobs[0].admitted)
+    assert status[5] == "cancelled" and jobs[5].steps_done < jobs[5].n_steps
+    assert status[4] in ("cancelled", "done")
+    assert srv.used == 0 and FakeSystem.live == 0
+
+
+class FailingBatch(FakeBatch):
+    """A batch whose propagation reports an error when it holds a poisoned job."""
+    poison = set()
+
+    def propagate(self, q, use_graph=True):
+        if any(s.spec.seed in FailingBatch.poison for s in self.systems):
+            from paper_1912_07921_gb300._lib import TdksError
+            raise TdksError(4, "a sweep kernel gave up waiting for its TMA copies")
+        super().propagate(q, use_graph)
+
+
+def test_a_batch_error_fails_its_group_and_the_others_go_on(monkeypatch):
+    jobs = _jobs(10, seed=29)
+    c64 = [j for j in jobs if j.spec.prec == I.PREC_C64]
+    c128 = [j for j in jobs if j.spec.prec == I.PREC_C128]
+    assert c64 and c128
+    for j in jobs:
+        j.arrival = 0.0
+    FailingBatch.poison = {c64[0].spec.seed}
+    monkeypatch.setattr(serving, "Batch", FailingBatch)
+    srv, done, _ = _serve(jobs, budget=10 ** 12)
+    status = {j.jid: j.status for j in done}
+    assert status[c64[0].jid] == "failed"
+    assert all(status[j.jid] == "done" for j in c128)
+    assert srv.used == 0 and FakeSystem.live == 0
 
 
 def test_job_bytes_grows_with_the_job():
