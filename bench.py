@@ -11,8 +11,10 @@ point advanced by one configured step.
 
 Timing: W warm-up steps, then K steps between CUDA events on the system's stream, with
 a device synchronise (and a barrier across ranks) on both sides; the working set
-(~2.3 GB) is far larger than L2, so no flush is needed.  Multi-GPU runs are independent
-replicas (weak scaling); the time is the maximum over ranks.
+(~2.3 GB) is far larger than L2, so no flush is needed.  Multi-GPU runs split the
+molecule's orbitals over the ranks with an FP64 density allreduce per sub-step (strong
+scaling; --shard replicas runs independent copies instead); the time is the maximum over
+ranks.
 
 ``--impl reference`` times the FP64 CPU oracle on the host cores on a bounded sample of
 the same workload (a subset of the orbitals) and reports the same metric.
@@ -774,9 +776,10 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="keep the default sweep tile shape (no autotuner)")
     ap.add_argument("--no-study", action="store_true", help="skip the propagator cost-against-error study")
     ap.add_argument("--shape", type=int, default=-1, help="force one sweep tile shape for all Taylor terms")
-    ap.add_argument("--shard", default="replicas", choices=["replicas", "states"],
-                    help="ranks run replicas of the molecule (default), or split one molecule's orbitals "
-                         "with a density allreduce per sub-step (strong scaling; also at --gpus 1)")
+    ap.add_argument("--shard", default="auto", choices=["auto", "replicas", "states"],
+                    help="states: split one molecule's orbitals over the ranks with a density allreduce per "
+                         "sub-step (strong scaling; also at --gpus 1); replicas: every rank runs its own copy; "
+                         "auto (default): states on several GPUs, the single system on one")
     ap.add_argument("--sweep-path", type=int, default=0,
                     help="stencil sweep variant: 0 warp-specialised TMA (default), 1 general, 2 lockstep TMA")
     args = ap.parse_args()
@@ -787,6 +790,9 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.shard == "auto":
+        # one molecule over several GPUs is the paper's multi-GPU mode (states distributed)
+        args.shard = "states" if world > 1 else "replicas"
     if args.impl == "reference":
         out = run_reference(args, rank)
         if out is not None:

@@ -18,7 +18,7 @@
  *     real-time TDDFT");
  *   - the time-dependent dipole d(t) = int r n(r,t) dr (Sec. "Local domains");
  *   - the macroscopic current J = -(i/Omega) int sum_i phi_i [H, r] phi_i
- *     (Sec. "Conductivities", eqn. current_density), local part;
+ *     (Sec. "Conductivities", eqn. current_density), with the projectors' commutator;
  *   - the velocity-gauge field E = -dA/dt (same section);
  *   - closed-shell occupations f_i = 2 (Sec. "t-SURFF", closed shells);
  *   - the t-SURFF photoelectron amplitudes: the time integral of the Volkov-state
@@ -406,6 +406,45 @@ void oracle_taylor_substep(const oracle_sys *s, double t, double dt, cplx *psi) 
   free(term); free(next); free(acc); free(n); free(vx);
 }
 
+/* The projectors' part of sum_k w_k f <phi| i[V_NL, r] |phi> h^3 per axis, added to acc:
+ * per atom, k-point and orbital, p_j = <b_j|phi> and q_jx = <d_x b_j|phi> (sphere points
+ * unwrapped, r - R_a = d, with the Bloch and gauge phases), and
+ * <phi| i[V_NL, r_x] |phi> = sum_j D_j i (p_j^* q_jx - q_jx^* p_j)  (the atom's position cancels). */
+static void nonlocal_velocity(const oracle_sys *s, const double *A, const cplx *psi, ksum *acc) {
+  if (s->n_atoms <= 0 || s->D == NULL) return;
+  const long N = npts(s);
+  const int B = s->n_orb;
+  const double h3 = s->h * s->h * s->h;
+  for (int a = 0; a < s->n_atoms; a++) {
+    sphere_pt *pts;
+    const int np = sphere_points(s, a, &pts);
+    for (int k = 0; k < s->n_k; k++) {
+      const double *kk = s->kpts + 3 * k;
+      for (int o = 0; o < B; o++) {
+        cplx p[4] = {0.0, 0.0, 0.0, 0.0}, q[4][3];
+        for (int j = 0; j < 4; j++) q[j][0] = q[j][1] = q[j][2] = 0.0;
+        for (int t = 0; t < np; t++) {
+          double b[4];
+          beta_values(s, pts[t].d, b);
+          double ph = 0.0;
+          for (int ax = 0; ax < 3; ax++) ph += kk[ax] * pts[t].T[ax] + A[ax] * pts[t].d[ax];
+          const cplx val = h3 * cexp(I * ph) * psi[((long)k * N + pts[t].cell) * B + o];
+          for (int j = 0; j < 4; j++) {
+            p[j] += b[j] * val;
+            for (int ax = 0; ax < 3; ax++) q[j][ax] += pts[t].d[ax] * b[j] * val;
+          }
+        }
+        for (int j = 0; j < 4; j++)
+          for (int ax = 0; ax < 3; ax++) {
+            const cplx c = I * (conj(p[j]) * q[j][ax] - conj(q[j][ax]) * p[j]);
+            kadd(&acc[ax], s->kw[k] * s->occ * s->D[4 * a + j] * creal(c));
+          }
+      }
+    }
+    free(pts);
+  }
+}
+
 /* --------------------------------------------------------------------------------
  * Observables of the state psi (recorded at state time t_state) with the field of the
  * Hamiltonian taken at t_field.  obs = [t_state, norm, E, E_x, o_x, o_y, o_z, f] with
@@ -413,7 +452,8 @@ void oracle_taylor_substep(const oracle_sys *s, double t, double dt, cplx *psi) 
  *   E    = sum_k w_k f_i <phi|H(t_field)|phi> - int n v_x + E_x,
  *          with Hartree (xc 2): v_x -> v_x + v_H and + E_H,
  *   o    = dipole int r n (finite systems) or the current
- *          J = -(1/Omega) sum_k w_k f_i <phi|(-i grad_h + A)|phi> (periodic cells),
+ *          J = -(1/Omega) sum_k w_k f_i <phi| i[H, r] |phi> (periodic cells): the local part
+ *          <phi|(-i grad_h + A)|phi> and the projectors' commutator <phi| i[V_NL, r] |phi>,
  *   f    = field component along pol at t_field (E in length gauge, A in velocity gauge).
  * ------------------------------------------------------------------------------ */
 void oracle_observables(const oracle_sys *s, double t_state, double t_field, const cplx *psi,
@@ -476,6 +516,7 @@ void oracle_observables(const oracle_sys *s, double t_state, double t_field, con
                 kadd(&pexp[ax], s->kw[k] * s->occ * creal(conj(v) * (-I) * g[ax] / h) * h3);
               kadd(&nel, s->kw[k] * s->occ * creal(conj(v) * v) * h3);
             }
+    nonlocal_velocity(s, A, psi, pexp);
     for (int ax = 0; ax < 3; ax++) o3[ax] = -(pexp[ax].s + A[ax] * nel.s) / omega_cell;
   }
   obs[0] = t_state;
@@ -868,7 +909,7 @@ int oracle_set_threads(int n) {
  *                  the sphere point (its atom's position cancels in the commutator):
  *                  <phi| i[V_NL, r] |phi> = sum_aj D_aj i (<phi|b_aj><b_aj| d phi> - <phi| d b_aj><b_aj|phi>)
  *                  with b_aj the dressed projector (Bloch and gauge phases) and d = r - R_a.
- * The observable record carries the local part; oracle_velocity_expectation returns
+ * The observable record carries both parts; oracle_velocity_expectation returns
  * sum_k w_k f_i <phi|v|phi> h^3 per axis, with the non-local part when `nonlocal` is set.
  * oracle_band_energy returns sum_k w_k f_i <phi|H(A)|phi> h^3 (no exchange, no other field).
  * ------------------------------------------------------------------------------ */
@@ -907,37 +948,7 @@ void oracle_velocity_expectation(const oracle_sys *s, const double *A, const cpl
             for (int ax = 0; ax < 3; ax++)
               kadd(&acc[ax], s->kw[k] * s->occ * creal(conj(v) * (-I * g[ax] / h + A[ax] * v)) * h3);
           }
-  if (nonlocal && s->n_atoms > 0 && s->D != NULL) {
-    for (int a = 0; a < s->n_atoms; a++) {
-      sphere_pt *pts;
-      const int np = sphere_points(s, a, &pts);
-      for (int k = 0; k < s->n_k; k++) {
-        const double *kk = s->kpts + 3 * k;
-        for (int o = 0; o < B; o++) {
-          /* p_j = <b_j|phi>, q_jx = <d_x b_j|phi> */
-          cplx p[4] = {0.0, 0.0, 0.0, 0.0}, q[4][3];
-          for (int j = 0; j < 4; j++) q[j][0] = q[j][1] = q[j][2] = 0.0;
-          for (int t = 0; t < np; t++) {
-            double b[4];
-            beta_values(s, pts[t].d, b);
-            double ph = 0.0;
-            for (int ax = 0; ax < 3; ax++) ph += kk[ax] * pts[t].T[ax] + A[ax] * pts[t].d[ax];
-            const cplx val = h3 * cexp(I * ph) * psi[((long)k * N + pts[t].cell) * B + o];
-            for (int j = 0; j < 4; j++) {
-              p[j] += b[j] * val;
-              for (int ax = 0; ax < 3; ax++) q[j][ax] += pts[t].d[ax] * b[j] * val;
-            }
-          }
-          for (int j = 0; j < 4; j++)
-            for (int ax = 0; ax < 3; ax++) {
-              const cplx c = I * (conj(p[j]) * q[j][ax] - conj(q[j][ax]) * p[j]);
-              kadd(&acc[ax], s->kw[k] * s->occ * s->D[4 * a + j] * creal(c));
-            }
-        }
-      }
-      free(pts);
-    }
-  }
+  if (nonlocal) nonlocal_velocity(s, A, psi, acc);
   for (int ax = 0; ax < 3; ax++) out[ax] = acc[ax].s;
 }
 

@@ -273,6 +273,92 @@ cudaError_t launch_gather_batch(int prec, const GatherParams *gp, const long *be
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------------
+// Projectors' share of the periodic cell's current (Sec. "Conductivities", eqn.
+// current_density: the velocity operator i[H, r] includes i[V_NL, r]).  For one atom, one
+// k-batch and the BS orbitals of the batch, with d = (sphere point, unwrapped) - R_a and the
+// Bloch and gauge phase e^{i(k.T + A.d)} of each entry,
+//   p_j = sum beta_j(d) e^{i..} phi,   q_jx = sum d_x beta_j(d) e^{i..} phi   (times h^3 each),
+//   <phi| i[V_NL, r_x] |phi> = sum_j D_j i (p_j^* q_jx - q_jx^* p_j) = sum_j D_j (-2 Im(p_j^* q_jx)).
+// Written as extra partial records (energy 0, three current sums in the units of the sweep's
+// partials: w_k f times the velocity, over h^3) that the record's finalise adds in order.
+// FP64 throughout (complex64 systems: the state hi + lo), once per record.
+// ---------------------------------------------------------------------------------
+constexpr int NLC_THREADS = 128;
+
+__global__ void __launch_bounds__(NLC_THREADS) nl_current_kernel(const NlCurrentParams p) {
+  const int a = blockIdx.x, kb = blockIdx.y, t = threadIdx.x;
+  const int o = t % p.BS, lane = t / p.BS, lanes = NLC_THREADS / p.BS;
+  const int kidx = kb / p.n_batches;
+  const double kx = p.kvec[3 * kidx], ky = p.kvec[3 * kidx + 1], kz = p.kvec[3 * kidx + 2];
+  double pr[4] = {}, pi[4] = {}, qr[4][3] = {}, qi[4][3] = {};
+  for (int e = p.atom_begin[a] + lane; e < p.atom_begin[a + 1]; e += lanes) {
+    const ProjEntry &E = p.ent[e];
+    const long i = ((long)kb * p.N + E.cell) * p.BS + o;
+    double xr, xi;
+    if (p.prec == P_C128) {
+      const double2 v = reinterpret_cast<const double2 *>(p.psi)[i];
+      xr = v.x;
+      xi = v.y;
+    } else {
+      const float2 hi = reinterpret_cast<const float2 *>(p.psi)[i], lo = reinterpret_cast<const float2 *>(p.psi_lo)[i];
+      xr = (double)hi.x + (double)lo.x;
+      xi = (double)hi.y + (double)lo.y;
+    }
+    double sn, cs;
+    sincos(kx * E.T[0] + ky * E.T[1] + kz * E.T[2] + p.A[0] * E.d[0] + p.A[1] * E.d[1] + p.A[2] * E.d[2], &sn, &cs);
+    const double vr = cs * xr - sn * xi, vi = cs * xi + sn * xr;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      pr[j] += E.betad[j] * vr;
+      pi[j] += E.betad[j] * vi;
+#pragma unroll
+      for (int x = 0; x < 3; x++) {
+        qr[j][x] += E.d[x] * E.betad[j] * vr;
+        qi[j][x] += E.d[x] * E.betad[j] * vi;
+      }
+    }
+  }
+  // sum over the lanes of each orbital in a fixed order
+  __shared__ double red[NLC_THREADS][32];
+  double *r = red[t];
+#pragma unroll
+  for (int j = 0; j < 4; j++) {
+    r[8 * j] = pr[j];
+    r[8 * j + 1] = pi[j];
+#pragma unroll
+    for (int x = 0; x < 3; x++) {
+      r[8 * j + 2 + 2 * x] = qr[j][x];
+      r[8 * j + 3 + 2 * x] = qi[j][x];
+    }
+  }
+  __syncthreads();
+  if (t < p.BS) {
+    double sum[32];
+    for (int c = 0; c < 32; c++) sum[c] = 0.0;
+    for (int l = 0; l < lanes; l++)
+      for (int c = 0; c < 32; c++) sum[c] += red[l * p.BS + t][c];
+    double vel[3] = {0.0, 0.0, 0.0};
+    for (int j = 0; j < 4; j++)
+      for (int x = 0; x < 3; x++) {
+        // Im(p^* q) = p_r q_i - p_i q_r
+        const double im = sum[8 * j] * sum[8 * j + 3 + 2 * x] - sum[8 * j + 1] * sum[8 * j + 2 + 2 * x];
+        vel[x] += p.D[4 * a + j] * (-2.0 * im);
+      }
+    double *out = p.out + ((long)kb * p.n_atoms * p.BS + (long)a * p.BS + t) * 4;
+    const double f = p.wocc[kidx] * p.h3;  // (h^3)^2 of p and q, over the h^3 the finalise applies
+    out[0] = 0.0;
+    out[1] = f * vel[0];
+    out[2] = f * vel[1];
+    out[3] = f * vel[2];
+  }
+}
+
+cudaError_t launch_nl_current(const NlCurrentParams &p, cudaStream_t s) {
+  nl_current_kernel<<<dim3(p.n_atoms, p.n_kb), NLC_THREADS, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gather(int prec, int bloch, const GatherParams &p, cudaStream_t s) {
   if (p.n_atoms <= 0) return cudaSuccess;
   dim3 grid(p.n_atoms * p.n_chunks, p.n_kb);

@@ -372,11 +372,27 @@ int run_lda(tdks_system *s, const double E[3], const double A[3]) {
 int run_finalize(tdks_system *s, double *rec, double t_state, const double E[3], const double A[3]) {
   const double h3 = s->h * s->h * s->h;
   const double omega_cell = (double)s->N * h3;
+  long n_part = s->obs_count;
+  if (s->bc == TDKS_BC_BLOCH && s->n_atoms > 0) {
+    // the projectors' commutator in the current: partial records after the sweep's
+    const long extra = (long)s->n_atoms * s->n_kb * s->BS;
+    if (n_part + extra > s->obs_cap) return fail(TDKS_EDEVICE, "observable partials exceed their buffer");
+    NlCurrentParams q{};
+    q.prec = s->prec; q.BS = s->BS; q.n_batches = s->n_batches; q.n_kb = s->n_kb; q.n_atoms = s->n_atoms;
+    q.N = s->N; q.psi = s->psi; q.psi_lo = s->psi_lo; q.atom_begin = s->d_atom_begin; q.ent = s->d_ent;
+    q.D = s->d_D; q.kvec = s->d_kvec; q.wocc = s->d_wocc; q.h3 = h3;
+    for (int a = 0; a < 3; a++) q.A[a] = s->gauge == TDKS_GAUGE_VELOCITY ? A[a] : 0.0;
+    q.out = s->obs_part + n_part * 4;
+    cudaError_t e = launch_nl_current(q, s->stream);
+    s->launches++;
+    if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("non-local current: ") + cudaGetErrorString(e));
+    n_part += extra;
+  }
   double fv = 0.0;
   for (int a = 0; a < 3; a++) fv += (s->gauge == TDKS_GAUGE_VELOCITY ? A[a] : E[a]) * s->pol[a];
   const double Az[3] = {0, 0, 0};
   if (s->xfn) {  // state-parallel: band energy and currents summed over the ranks
-    cudaError_t e = launch_finalize_sums(s->obs_part, s->obs_count, s->lda_part, lda_blocks(s->N), s->fin_part,
+    cudaError_t e = launch_finalize_sums(s->obs_part, n_part, s->lda_part, lda_blocks(s->N), s->fin_part,
                                          s->fin_sum, s->stream);
     s->launches += 2;
     if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("finalize: ") + cudaGetErrorString(e));
@@ -389,7 +405,7 @@ int run_finalize(tdks_system *s, double *rec, double t_state, const double E[3],
     return TDKS_OK;
   }
   Timed tm(s, 2);
-  cudaError_t e = launch_finalize(s->obs_part, s->obs_count, s->lda_part, lda_blocks(s->N), rec, t_state, h3,
+  cudaError_t e = launch_finalize(s->obs_part, n_part, s->lda_part, lda_blocks(s->N), rec, t_state, h3,
                                   s->occ, s->bc == TDKS_BC_BLOCH, omega_cell,
                                   s->gauge == TDKS_GAUGE_VELOCITY ? A : Az, fv, s->fin_part, s->stream);
   s->launches += 2;
@@ -536,7 +552,8 @@ int tdks_create_grid(int nx, int ny, int nz, double h, int fd_order, int bc, int
       ws_shape_info(sh, &tx, &ty, nullptr, &warps);
       items_ws = std::max(items_ws, (long)((nx + tx - 1) / tx) * ((ny + ty - 1) / ty) * s->n_kb * nz * warps);
     }
-    ALLOC(s->obs_part, (size_t)std::max(items_gen, items_ws) * 4 * sizeof(double));
+    s->obs_cap = s->obs_base = std::max(items_gen, items_ws);
+    ALLOC(s->obs_part, (size_t)s->obs_cap * 4 * sizeof(double));
   }
   ALLOC(s->ring, (size_t)tdks_system::RING * TDKS_RECORD * sizeof(double));
   ALLOC(s->fin_part, (size_t)FIN_BLOCKS * 10 * sizeof(double));
@@ -772,6 +789,15 @@ int tdks_set_atoms_projectors(tdks_sys s, int n_atoms, const double *pos, const 
     CU(cudaMemcpy(s->d_ent_ca, eca.data(), ent.size() * sizeof(int2), cudaMemcpyHostToDevice));
   }
   CU(cudaMemcpy(s->d_D, D, (size_t)n_atoms * 4 * sizeof(double), cudaMemcpyHostToDevice));
+  if (s->bc == TDKS_BC_BLOCH) {
+    // room for the projectors' current records after the sweep partials
+    const long need = s->obs_base + (long)n_atoms * s->n_kb * s->BS;
+    double *grown = nullptr;
+    CU(cudaMalloc((void **)&grown, (size_t)need * 4 * sizeof(double)));
+    cudaFree(s->obs_part);
+    s->obs_part = grown;
+    s->obs_cap = need;
+  }
   s->n_atoms = n_atoms;
   s->pos.assign(pos, pos + 3 * n_atoms);
   s->D.assign(D, D + 4 * n_atoms);

@@ -146,6 +146,22 @@ struct GatherParams {
   void *nl;                   // [kb][n_ent + 1][OVC] vectors, row r0 of each sphere point
 };
 
+// The projectors' share of a periodic cell's current (record time): partial records
+// out[(kb * n_atoms + a) * BS + o][4] for every atom, k-batch and orbital of the batch.
+struct NlCurrentParams {
+  int prec, BS, n_batches, n_kb, n_atoms;
+  long N;
+  const void *psi, *psi_lo;   // the state (complex64: hi and lo parts)
+  const int *atom_begin;      // [n_atoms + 1] entry ranges
+  const ProjEntry *ent;
+  const double *D;            // [n_atoms][4]
+  const double *kvec;         // [n_k][3]
+  const double *wocc;         // [n_k] k-weight times occupation
+  double A[3], h3;
+  double *out;
+};
+cudaError_t launch_nl_current(const NlCurrentParams &p, cudaStream_t s);
+
 // Per-system data of a batch (device copies), for the batched LDA and finalise kernels.
 struct BatchAux {
   long N;

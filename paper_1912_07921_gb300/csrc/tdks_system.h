@@ -51,6 +51,8 @@ struct tdks_system {
   double *dens_part = nullptr;
   double *lda_part = nullptr;
   double *obs_part = nullptr;
+  long obs_cap = 0;            // records obs_part holds (sweep partials, then the projectors' current)
+  long obs_base = 0;           // of which the sweep partials
   double *ring = nullptr;
   double *obs_rec = nullptr;    // single record for tdks_observe
   double *d_kvec = nullptr, *d_wocc = nullptr, *d_D = nullptr;

@@ -57,17 +57,40 @@ class Job:
         return self.spec.n_points * self.spec.n_orb * self.n_steps
 
 
+_PAGE = 2 << 20  # device allocations are made in 2 MiB pages
+
+
+def _pages(nbytes: float) -> int:
+    return int(-(-int(math.ceil(nbytes)) // _PAGE)) * _PAGE if nbytes > 0 else 0
+
+
 def job_bytes(spec: I.SystemSpec) -> int:
-    """Device memory a job holds while resident (the library's allocation for it)."""
+    """Device memory a job holds while resident: the library's buffers for it, each rounded
+    up to the 2 MiB pages it occupies (state and Taylor terms, potentials and per-point
+    records, density partials, observable partials, record ring, upload staging, projector
+    tables).  A GPU test checks it against the device's free memory around a system."""
     bs = 8 if spec.prec == I.PREC_C64 else 4
     nb = -(-spec.n_orb // bs)
-    vals = spec.n_points * nb * bs * spec.n_k
-    term = 8 if spec.prec == I.PREC_C64 else 16
-    state = 16
-    per_point = 8 + (4 if spec.prec == I.PREC_C64 else 8) + 8 * nb * spec.n_k + 4
-    staging = spec.n_points * spec.n_orb * spec.n_k * 16
-    ring = 65536 * 8 * 8
-    return vals * (state + 3 * term) + spec.n_points * per_point + staging + ring + (1 << 20)
+    n_kb = nb * spec.n_k
+    N = spec.n_points
+    packed = n_kb * N * 64  # one packed array: 64 bytes per (point, batch)
+    total = _pages(packed) * (5 if spec.prec == I.PREC_C64 else 4)  # state (hi, lo) and 3 terms
+    total += _pages(N * 8) + _pages(N * 16) + _pages(n_kb * N * 8)  # V_loc, records, density
+    # observable partials: the most records a first sweep can write over the tile shapes
+    items_gen = -(-spec.nx // 8) * -(-spec.ny // 4) * n_kb * spec.nz
+    shapes = ((16, 8, 8), (16, 12, 6), (16, 12, 12), (16, 8, 16), (14, 8, 7), (16, 12, 12))
+    items_ws = max(-(-spec.nx // tx) * -(-spec.ny // ty) * n_kb * spec.nz * w for tx, ty, w in shapes)
+    total += _pages(max(items_gen, items_ws) * 32)
+    total += _pages(65536 * 8 * 8) + 6 * _PAGE  # record ring; error word, LDA/finalise partials, k-points
+    total += _pages(spec.n_k * N * spec.n_orb * 16)  # upload staging
+    if spec.projectors and spec.n_atoms > 0:
+        pts = 1.15 * 4.0 / 3.0 * math.pi * (spec.r_cut / spec.h + 1.0) ** 3  # points in a sphere (bound)
+        ent = spec.n_atoms * pts * (8 if spec.bc == I.BC_BLOCH else 1)     # periodic: the images
+        total += _pages(ent * 120) + _pages(ent * 16) + _pages(ent * 8) + _pages(ent * 4) + _pages(ent * 8)
+        total += _pages(n_kb * (ent + 1) * 64)  # non-local term per sphere point
+        total += _pages(n_kb * spec.n_atoms * 4 * 64) + _pages(n_kb * spec.n_atoms * 64 * 4 * 4 * 32)
+        total += 3 * _PAGE  # atom ranges, strengths, sphere-point ranges
+    return total
 
 
 def serving_trace(n_jobs: int, rate: float, seed: int, edge=(32, 128), orbitals=(4, 128),

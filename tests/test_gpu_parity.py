@@ -538,3 +538,27 @@ def test_periodic_cell_full_grid_one_step(prec):
         # down to ~0.45 Ha per orbital, so the relative error is ~eps32 * K_max / e ~ 4e-5
         assert abs(rec[0, 2] - rec_o[0, 2]) < 2e-4 * abs(rec_o[0, 2])
         assert np.max(np.abs(rec[0, 4:7] - rec_o[0, 4:7])) < 1e-4 * np.max(np.abs(rec_o[0, 4:7]))
+
+
+@pytest.mark.parametrize("prec", [I.PREC_C128, I.PREC_C64])
+def test_periodic_current_includes_the_projectors_commutator(prec):
+    """The periodic cell's recorded current is the full -(1/Omega) <i[H, r]> (Sec.
+    "Conductivities", eqn. current_density): the local part and the projectors' commutator,
+    against the oracle's velocity expectation; without the commutator it would differ."""
+    spec = bloch_cell(prec, n_orb=5 if prec == I.PREC_C64 else 3)
+    inp = bloch_inputs(spec)
+    psi = inp.psi0
+    if prec == I.PREC_C64:
+        inp.psi0 = psi.astype(np.complex64).astype(np.complex128)
+    sysm = _system(spec, inp)
+    got = sysm.observe(0.0, 0.45)
+    sysm.close()
+    o = oracle.System(spec, inp)
+    _, A = o.field(0.45)
+    omega = spec.nx * spec.ny * spec.nz * spec.h ** 3
+    full = -o.velocity(A, inp.psi0) / omega
+    local = -o.velocity(A, inp.psi0, with_nonlocal=False) / omega
+    scale = np.abs(full).max()
+    assert np.abs(full - local).max() > 1e-3 * scale
+    tol = 1e-12 if prec == I.PREC_C128 else 1e-4
+    assert np.abs(got[4:7] - full).max() < tol * scale

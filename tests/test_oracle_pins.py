@@ -833,7 +833,7 @@ def test_rk4_and_cfm4_with_hartree_keep_their_order():
 
 
 # Current of a periodic cell with the projectors' commutator (Sec. "Conductivities": the
-# velocity operator i[H, r] includes i[V_NL, r]); the record carries the local part.
+# velocity operator i[H, r] includes i[V_NL, r]); the record carries both parts.
 def test_current_is_minus_the_energy_derivative_in_a():
     """J = -(1/Omega) dE/dA on the discrete level, because H(A) depends on A only through
     -i A.grad_h + |A|^2/2 and the projectors' gauge phases: the velocity expectation with the
@@ -856,8 +856,9 @@ def test_current_is_minus_the_energy_derivative_in_a():
     np.testing.assert_array_equal(o0.velocity(A, inp.psi0), o0.velocity(A, inp.psi0, with_nonlocal=False))
 
 
-def test_recorded_current_is_the_local_velocity():
-    """The record's current is -(1/Omega) times the local velocity expectation at A(t_field)."""
+def test_recorded_current_is_minus_the_energy_derivative():
+    """The record's current is -(1/Omega) times the full velocity expectation at A(t_field),
+    projectors' commutator included, so it equals -(1/Omega) dE/dA by central differences."""
     from tests._util import bloch_cell, bloch_inputs
     spec = bloch_cell(I.PREC_C128, n_k=2)
     inp = bloch_inputs(spec)
@@ -865,8 +866,11 @@ def test_recorded_current_is_the_local_velocity():
     obs = o.observables(inp.psi0, 0.0, 0.3)
     _, A = o.field(0.3)
     omega = spec.nx * spec.ny * spec.nz * spec.h ** 3
-    np.testing.assert_allclose(obs[4:7], -o.velocity(A, inp.psi0, with_nonlocal=False) / omega, rtol=1e-12,
-                               atol=1e-14)
+    np.testing.assert_allclose(obs[4:7], -o.velocity(A, inp.psi0) / omega, rtol=1e-12, atol=1e-14)
+    d = 1e-4
+    fd = np.array([(o.band_energy(A + d * e, inp.psi0) - o.band_energy(A - d * e, inp.psi0)) / (2 * d)
+                   for e in np.eye(3)])
+    assert np.abs(obs[4:7] + fd / omega).max() < 1e-8 * np.abs(fd / omega).max()
 
 
 def test_hartree_cell_sum_equals_a_zero_padded_fft_convolution():
@@ -892,3 +896,41 @@ def test_hartree_cell_sum_equals_a_zero_padded_fft_convolution():
     conv = np.fft.irfftn(np.fft.rfftn(pad) * np.fft.rfftn(kern), s=shape, axes=(0, 1, 2))[:spec.nz, :spec.ny, :spec.nx]
     _, vh = o.hartree(n.ravel())
     np.testing.assert_allclose(vh, conv.ravel() * spec.h ** 3, rtol=1e-12, atol=1e-12 * np.abs(vh).max())
+
+
+def test_energy_with_projectors_and_length_gauge_field_is_the_dense_expectation():
+    """The recorded energy of a finite box with projectors, wells, LDA exchange and a
+    length-gauge field, against sum_i f <phi_i|H0|phi_i> h^3 + E_x built here densely: the
+    kinetic matrix from the golden FD weights, the wells, +E(t).r with E written out, and the
+    brute-force projector matrix (the exchange terms of the record cancel except E_x, which
+    is the Dirac expression of the density formed here)."""
+    spec = _spec(nx=8, ny=8, nz=8, h=0.45, fd_order=4, n_orb=2, n_atoms=2, projectors=True, wells=True,
+                 xc=I.XC_LDA_X, gauge=I.GAUGE_LENGTH, amp=0.3, omega=0.7, pol=(0.3, -0.5, 0.8), seed=5)
+    inp = I.make_inputs(spec)
+    o = oracle.System(spec, inp)
+    psi = I.random_orbitals(spec, 31) * 0.3
+    t_field = 1.1
+    rec = o.observables(psi, 0.0, t_field)
+    n = spec.n_points
+    h = spec.h
+    c = [float(v) for v in _read_golden()[("lap", 4)]]
+    x = _axis(spec, spec.nx)
+    D1 = np.zeros((spec.nx, spec.nx))
+    for i in range(spec.nx):
+        D1[i, i] = c[0]
+        for m in (1, 2):
+            if i + m < spec.nx:
+                D1[i, i + m] = D1[i + m, i] = c[m]
+    I1 = np.eye(spec.nx)
+    lap = (np.kron(np.kron(D1, I1), I1) + np.kron(np.kron(I1, D1), I1) + np.kron(np.kron(I1, I1), D1)) / h ** 2
+    E = spec.amp * math.sin(spec.omega * t_field) * np.array(spec.pol)
+    X, Y, Z = _grids(spec)
+    er = (E[0] * X + E[1] * Y + E[2] * Z).reshape(-1)
+    H0 = -0.5 * lap + np.diag(inp.vloc.reshape(-1) + er) + _dense_vnl(spec, inp, np.zeros(3), np.zeros(3))
+    band = sum(spec.occ * np.vdot(psi[0, ..., j].reshape(-1), H0 @ psi[0, ..., j].reshape(-1)).real * h ** 3
+               for j in range(spec.n_orb))
+    dens = spec.occ * np.sum(np.abs(psi[0]) ** 2, axis=-1)
+    ex = -0.75 * (3.0 / math.pi) ** (1.0 / 3.0) * np.sum(dens ** (4.0 / 3.0)) * h ** 3
+    assert rec[3] == pytest.approx(ex, rel=1e-12)
+    assert rec[2] == pytest.approx(band + ex, rel=1e-12)
+    assert rec[7] == pytest.approx(E @ np.array(spec.pol), rel=1e-12)

@@ -222,10 +222,11 @@ def test_a_batch_error_fails_its_group_and_the_others_go_on(monkeypatch):
 
 
 def test_job_bytes_grows_with_the_job():
-    base = I.SystemSpec(nx=20, ny=20, nz=20, h=0.25, n_orb=8, prec=I.PREC_C64)
+    base = I.SystemSpec(nx=48, ny=48, nz=48, h=0.25, n_orb=16, prec=I.PREC_C64)
     b = serving.job_bytes(base)
     assert serving.job_bytes(dataclasses.replace(base, prec=I.PREC_C128)) > b
-    assert serving.job_bytes(dataclasses.replace(base, n_orb=16)) > b
-    assert serving.job_bytes(dataclasses.replace(base, nx=40)) > b
+    assert serving.job_bytes(dataclasses.replace(base, n_orb=32)) > b
+    assert serving.job_bytes(dataclasses.replace(base, nx=96)) > b
+    assert serving.job_bytes(dataclasses.replace(base, n_atoms=4, projectors=True)) > b
     # at least the state, the three Taylor terms and the host-layout staging buffer
-    assert b >= base.n_points * 8 * (16 + 3 * 8) + base.n_points * 8 * 16
+    assert b >= base.n_points * 16 * (16 + 3 * 8) + base.n_points * 16 * 16

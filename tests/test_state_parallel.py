@@ -100,11 +100,12 @@ def _rank_main(rank, world, port, out):
         dist.destroy_process_group()
 
 
-def test_two_gloo_ranks_reproduce_the_whole_system():
+@pytest.mark.parametrize("world", [2, 3])
+def test_gloo_ranks_reproduce_the_whole_system(world):
+    """Two ranks (slices of 4 and 1 orbitals), or three (2, 2 and 1: an uneven last slice)."""
     import oracle
     from paper_1912_07921_gb300 import inputs as I
 
-    world = 2
     port = _free_port()
     with mp.get_context("spawn").Manager() as m:
         out = m.dict()
@@ -118,7 +119,8 @@ def test_two_gloo_ranks_reproduce_the_whole_system():
     hpsi = full.apply_H(inp.psi0, 0.3, vx_full)
     band_full = spec.occ * np.vdot(inp.psi0, hpsi).real * spec.h ** 3
     stepped = full.taylor_substep(inp.psi0, 0.3, spec.dt)
-    assert (got[0]["lo"], got[0]["hi"], got[1]["lo"], got[1]["hi"]) == (0, 4, 4, 5)
+    slices = [(got[r]["lo"], got[r]["hi"]) for r in range(world)]
+    assert slices == ([(0, 4), (4, 5)] if world == 2 else [(0, 2), (2, 4), (4, 5)])
     for r in range(world):
         g = got[r]
         # every rank holds the whole system's density and band energy after the exchange
