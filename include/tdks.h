@@ -62,7 +62,7 @@ enum { TDKS_BC_ZERO = 0, TDKS_BC_BLOCH = 1 };
 enum { TDKS_C128 = 0, TDKS_C64 = 1 };
 enum { TDKS_GAUGE_NONE = 0, TDKS_GAUGE_LENGTH = 1, TDKS_GAUGE_VELOCITY = 2 };
 enum { TDKS_ENV_NONE = 0, TDKS_ENV_SIN2 = 1 };
-enum { TDKS_XC_NONE = 0, TDKS_XC_LDA_X = 1 };
+enum { TDKS_XC_NONE = 0, TDKS_XC_LDA_X = 1, TDKS_XC_LDA_X_HARTREE = 2 };
 
 /* Number of doubles in one observable record. */
 #define TDKS_RECORD 8
@@ -132,7 +132,17 @@ int tdks_set_field(tdks_sys sys, int gauge, const double pol[3], double amp, dou
                    double t_total);
 
 /* Exchange-correlation term: TDKS_XC_NONE or TDKS_XC_LDA_X (spin-unpolarised LDA
- * exchange, v_x = -(3n/pi)^(1/3)); occupation f > 0 of every orbital (2 for closed shells). */
+ * exchange, v_x = -(3n/pi)^(1/3)); occupation f > 0 of every orbital (2 for closed shells).
+ * TDKS_XC_LDA_X_HARTREE adds the Hartree potential of the density (the other density-dependent
+ * part of the Kohn-Sham potential, which CFM4 of Sec. "New propagators for real-time TDDFT"
+ * extrapolates with exchange): finite box, the Coulomb sum over grid cells
+ * v_H(r_i) = h^3 sum_j n_j / |r_i - r_j| with a cell's own term n_i h^2 c0,
+ * c0 = 3 ln(2 + sqrt 3) - pi/2, computed exactly by a zero-padded FFT; periodic cell,
+ * v_H(G) = 4 pi n(G) / |G|^2 on the grid's plane waves (G = 0 dropped, neutralising
+ * background).  The record's energy then adds E_H = 1/2 int n v_H.  Taylor-4 only (TDKS_EINVAL
+ * with another propagator and from tdks_batch_create); grid edges with prime factors <= 13
+ * (periodic cells) and transforms of at most 1024 points per axis (TDKS_EINVAL otherwise).
+ * Allocates the transform workspace (two complex arrays of the padded grid) once. */
 int tdks_set_xc(tdks_sys sys, int xc, double occupation);
 
 /*

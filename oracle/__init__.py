@@ -78,6 +78,7 @@ def _load():
         _lib.oracle_velocity_expectation.argtypes = [S, P, P, I, P]
         _lib.oracle_set_threads.restype = I
         _lib.oracle_tsurff_flux.argtypes = [S, P, I, P, P, P, D, D, P, P]
+        _lib.oracle_heat_current.argtypes = [S, P, P, P]
         _lib.oracle_volkov_step.argtypes = [S, D, D, P]
         _lib.oracle_tsurff_propagate.argtypes = [S, P, I, P, D, D, I, I, P, P, P, P, P]
         _lib.oracle_hartree_self_cell.restype = D
@@ -274,6 +275,14 @@ class System:
                                          _ptr(psi), _ptr(obs) if record else None, _ptr(vol), ctypes.byref(tr),
                                          _ptr(b))
         return psi, obs, b, vol, tr.value
+
+    def heat_current(self, A, psi) -> np.ndarray:
+        """Macroscopic kinetic heat current (1/Omega) sum_k w_k f int J_t at vector potential A
+        (the printed kinetic term with its last pair antisymmetric; covariant derivatives)."""
+        A = np.ascontiguousarray(A, dtype=np.float64)
+        out = np.empty(3)
+        self.lib.oracle_heat_current(self.ref, _ptr(A), _ptr(self._psi(psi)), _ptr(out))
+        return out
 
     def sphere_count(self, a: int) -> int:
         return self.lib.oracle_sphere_count(self.ref, a)

@@ -22,7 +22,8 @@
  *   - the velocity-gauge field E = -dA/dt (same section);
  *   - closed-shell occupations f_i = 2 (Sec. "t-SURFF", closed shells);
  *   - the t-SURFF photoelectron amplitudes: the time integral of the Volkov-state
- *     current through a surface (Sec. "t-SURFF", eqns. for chi_p, b_i and the current).
+ *     current through a surface (Sec. "t-SURFF", eqns. for chi_p, b_i and the current);
+ *   - the kinetic heat current (Sec. "Conductivities", eqn. KEcurrent).
  * The exponential is a 4th-order Taylor series with H frozen over a (sub-)step; the
  * paper does not print this propagator, so the oracle takes the readings listed at each
  * function.  Everything is plain loops in double precision; OpenMP only splits the
@@ -1072,4 +1073,92 @@ void oracle_tsurff_propagate(const oracle_sys *s, const int *box, int n_p, const
     *t_rel += dt;
   }
   free(F);
+}
+
+/* --------------------------------------------------------------------------------
+ * Kinetic heat current (Sec. "Conductivities", eqn. KEcurrent): the macroscopic (cell-averaged)
+ *   J_t = (1/Omega) sum_k w_k f int [J_t(r)] dr,
+ *   [J_t(r)]_i = (i/8) ( [d_i phi^*][Lap phi] - [Lap phi^*][d_i phi] - [d_i grad phi^*].[grad phi]
+ *                        + [grad phi^*].[d_i grad phi] ).
+ * Reading: the printed last pair has equal signs, which makes its (i/8) multiple imaginary; with
+ * the pair antisymmetric, as the first one, J_t is real, and a plane wave gives
+ * -(1/2)|k|^2 k: minus its kinetic energy times its velocity, the sign convention of the charge
+ * current J of eqn. current_density (electron charge -1).  Derivatives as in H: covariant in the
+ * velocity gauge, d_j -> d_j + i A_j with d_j the central difference of order 2M (Bloch images in a
+ * periodic cell, zeros outside a box); Lap -> Lap_h + 2 i A.grad_h - |A|^2 with Lap_h the star
+ * Laplacian; d_i grad phi -> the covariant first differences composed.  Plain loops, every
+ * neighbour fetched.
+ * ------------------------------------------------------------------------------ */
+static void cov_grad(const oracle_sys *s, const double *d, const double *A, const cplx *psi, int k, int o, int ix,
+                     int iy, int iz, cplx *g) {
+  const int M = s->fd_order / 2;
+  const cplx v = fetch(s, psi, k, o, ix, iy, iz);
+  for (int j = 0; j < 3; j++) {
+    cplx acc = 0.0;
+    for (int m = 1; m <= M; m++) {
+      int p[3] = {ix, iy, iz}, q[3] = {ix, iy, iz};
+      p[j] += m;
+      q[j] -= m;
+      acc += d[m] * (fetch(s, psi, k, o, p[0], p[1], p[2]) - fetch(s, psi, k, o, q[0], q[1], q[2]));
+    }
+    g[j] = acc / s->h + I * A[j] * v;
+  }
+}
+
+void oracle_heat_current(const oracle_sys *s, const double *A, const cplx *psi, double *out) {
+  const int M = s->fd_order / 2, B = s->n_orb;
+  const double h = s->h, h2 = h * h, h3 = h * h * h;
+  double c[5], d[5];
+  oracle_fd_laplacian_weights(M, c);
+  oracle_fd_gradient_weights(M, d);
+  const double A2 = A[0] * A[0] + A[1] * A[1] + A[2] * A[2];
+  const double omega_cell = (double)s->nx * s->ny * s->nz * h3;
+  ksum acc[3] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
+  for (int k = 0; k < s->n_k; k++)
+    for (int iz = 0; iz < s->nz; iz++)
+      for (int iy = 0; iy < s->ny; iy++)
+        for (int ix = 0; ix < s->nx; ix++)
+          for (int o = 0; o < B; o++) {
+            const cplx v = fetch(s, psi, k, o, ix, iy, iz);
+            cplx g[3];
+            cov_grad(s, d, A, psi, k, o, ix, iy, iz, g);
+            /* covariant Laplacian: the star Laplacian, 2 i A.grad_h, -|A|^2 */
+            cplx lap = 3.0 * c[0] * v, adg = 0.0;
+            for (int j = 0; j < 3; j++)
+              for (int m = 1; m <= M; m++) {
+                int p[3] = {ix, iy, iz}, q[3] = {ix, iy, iz};
+                p[j] += m;
+                q[j] -= m;
+                const cplx a = fetch(s, psi, k, o, p[0], p[1], p[2]), b = fetch(s, psi, k, o, q[0], q[1], q[2]);
+                lap += c[m] * (a + b);
+                adg += A[j] * d[m] * (a - b);
+              }
+            lap = lap / h2 + 2.0 * I * adg / h - A2 * v;
+            /* G[i][j] = (d_i + i A_i)(d_j + i A_j) phi: the covariant gradient at the neighbours along i */
+            cplx G[3][3];
+            for (int i = 0; i < 3; i++) {
+              cplx gi[3] = {0.0, 0.0, 0.0};
+              for (int m = 1; m <= M; m++) {
+                int p[3] = {ix, iy, iz}, q[3] = {ix, iy, iz};
+                p[i] += m;
+                q[i] -= m;
+                cplx gp[3], gq[3];
+                cov_grad(s, d, A, psi, k, o, p[0], p[1], p[2], gp);
+                cov_grad(s, d, A, psi, k, o, q[0], q[1], q[2], gq);
+                for (int j = 0; j < 3; j++) gi[j] += d[m] * (gp[j] - gq[j]);
+              }
+              for (int j = 0; j < 3; j++) G[i][j] = gi[j] / h + I * A[i] * g[j];
+            }
+            for (int i = 0; i < 3; i++) {
+              const cplx t1 = conj(g[i]) * lap, t2 = conj(lap) * g[i];
+              cplx t3 = 0.0, t4 = 0.0;
+              for (int j = 0; j < 3; j++) {
+                t3 += conj(G[i][j]) * g[j];
+                t4 += conj(g[j]) * G[i][j];
+              }
+              const cplx jt = (I / 8.0) * (t1 - t2 - t3 + t4);
+              kadd(&acc[i], s->kw[k] * s->occ * creal(jt) * h3);
+            }
+          }
+  for (int i = 0; i < 3; i++) out[i] = acc[i].s / omega_cell;
 }

@@ -282,46 +282,52 @@ cudaError_t launch_gather_batch(int prec, const GatherParams *gp, const long *be
 //   <phi| i[V_NL, r_x] |phi> = sum_j D_j i (p_j^* q_jx - q_jx^* p_j) = sum_j D_j (-2 Im(p_j^* q_jx)).
 // Written as extra partial records (energy 0, three current sums in the units of the sweep's
 // partials: w_k f times the velocity, over h^3) that the record's finalise adds in order.
-// FP64 throughout (complex64 systems: the state hi + lo), once per record.
+// Once per record; complex128 systems in FP64, complex64 systems with FP32 lane sums.
 // ---------------------------------------------------------------------------------
 constexpr int NLC_THREADS = 128;
 
-__global__ void __launch_bounds__(NLC_THREADS) nl_current_kernel(const NlCurrentParams p) {
-  const int a = blockIdx.x, kb = blockIdx.y, t = threadIdx.x;
-  const int o = t % p.BS, lane = t / p.BS, lanes = NLC_THREADS / p.BS;
+// per-lane sums of one orbital over a strided share of the atom's entries: FP64 for complex128
+// systems; FP32 products and sums for complex64 systems (the FP64 pipe of GB300 is a small
+// fraction of its FP32 one; the lane sums meet in FP64)
+template <typename F>
+__device__ __forceinline__ void nl_current_lane(const NlCurrentParams &p, int a, int kb, int o, int lane, int lanes,
+                                                double *r) {
   const int kidx = kb / p.n_batches;
   const double kx = p.kvec[3 * kidx], ky = p.kvec[3 * kidx + 1], kz = p.kvec[3 * kidx + 2];
-  double pr[4] = {}, pi[4] = {}, qr[4][3] = {}, qi[4][3] = {};
+  F pr[4] = {}, pi[4] = {}, qr[4][3] = {}, qi[4][3] = {};
   for (int e = p.atom_begin[a] + lane; e < p.atom_begin[a + 1]; e += lanes) {
     const ProjEntry &E = p.ent[e];
     const long i = ((long)kb * p.N + E.cell) * p.BS + o;
-    double xr, xi;
-    if (p.prec == P_C128) {
+    F xr, xi;
+    if constexpr (sizeof(F) == 8) {
       const double2 v = reinterpret_cast<const double2 *>(p.psi)[i];
       xr = v.x;
       xi = v.y;
     } else {
       const float2 hi = reinterpret_cast<const float2 *>(p.psi)[i], lo = reinterpret_cast<const float2 *>(p.psi_lo)[i];
-      xr = (double)hi.x + (double)lo.x;
-      xi = (double)hi.y + (double)lo.y;
+      xr = hi.x + lo.x;
+      xi = hi.y + lo.y;
     }
-    double sn, cs;
-    sincos(kx * E.T[0] + ky * E.T[1] + kz * E.T[2] + p.A[0] * E.d[0] + p.A[1] * E.d[1] + p.A[2] * E.d[2], &sn, &cs);
-    const double vr = cs * xr - sn * xi, vi = cs * xi + sn * xr;
+    const double ang = kx * E.T[0] + ky * E.T[1] + kz * E.T[2] + p.A[0] * E.d[0] + p.A[1] * E.d[1] + p.A[2] * E.d[2];
+    F sn, cs;
+    if constexpr (sizeof(F) == 8) sincos(ang, &sn, &cs); else sincosf((float)ang, &sn, &cs);
+    const F vr = cs * xr - sn * xi, vi = cs * xi + sn * xr;
+    F b[4], d[3];
+#pragma unroll
+    for (int j = 0; j < 4; j++) b[j] = sizeof(F) == 8 ? (F)E.betad[j] : (F)E.beta[j];
+#pragma unroll
+    for (int x = 0; x < 3; x++) d[x] = (F)E.d[x];
 #pragma unroll
     for (int j = 0; j < 4; j++) {
-      pr[j] += E.betad[j] * vr;
-      pi[j] += E.betad[j] * vi;
+      pr[j] += b[j] * vr;
+      pi[j] += b[j] * vi;
 #pragma unroll
       for (int x = 0; x < 3; x++) {
-        qr[j][x] += E.d[x] * E.betad[j] * vr;
-        qi[j][x] += E.d[x] * E.betad[j] * vi;
+        qr[j][x] += d[x] * b[j] * vr;
+        qi[j][x] += d[x] * b[j] * vi;
       }
     }
   }
-  // sum over the lanes of each orbital in a fixed order
-  __shared__ double red[NLC_THREADS][32];
-  double *r = red[t];
 #pragma unroll
   for (int j = 0; j < 4; j++) {
     r[8 * j] = pr[j];
@@ -332,6 +338,16 @@ __global__ void __launch_bounds__(NLC_THREADS) nl_current_kernel(const NlCurrent
       r[8 * j + 3 + 2 * x] = qi[j][x];
     }
   }
+}
+
+__global__ void __launch_bounds__(NLC_THREADS) nl_current_kernel(const NlCurrentParams p) {
+  const int a = blockIdx.x, kb = blockIdx.y, t = threadIdx.x;
+  const int o = t % p.BS, lane = t / p.BS, lanes = NLC_THREADS / p.BS;
+  const int kidx = kb / p.n_batches;
+  // sum over the lanes of each orbital in a fixed order
+  __shared__ double red[NLC_THREADS][32];
+  if (p.prec == P_C128) nl_current_lane<double>(p, a, kb, o, lane, lanes, red[t]);
+  else nl_current_lane<float>(p, a, kb, o, lane, lanes, red[t]);
   __syncthreads();
   if (t < p.BS) {
     double sum[32];
@@ -477,7 +493,7 @@ __device__ __forceinline__ void lda_body(long N, int nx, int ny, int nz, double 
                                          int n_batches, const double *wocc, const double *dens_part,
                                          const double *vloc, int xc, double Ex, double Ey, double Ez,
                                          double half_A2, PointAux *aux, double *lda_part, int blk, int nblk,
-                                         const double *n_in = nullptr) {
+                                         const double *n_in = nullptr, const double *vh = nullptr) {
   constexpr bool F32 = sizeof(R) == 4;
   const int n_k = n_kb / n_batches;
   __shared__ float2 s_w[LDA_MAXK];  // complex64: w_k f = hi + lo
@@ -530,10 +546,13 @@ __device__ __forceinline__ void lda_body(long N, int nx, int ny, int nz, double 
       const float nf = nh;
       const float x = (ix - cxf) * hf, y = (iy - cyf) * hf, z = (iz - czf) * hf;
       const float vx = xc ? -cbrtf(3.0f * nf * 0.318309886f) : 0.0f;
-      float v = (float)vloc[p] + vx + hA2f;
+      const float vhf = vh ? (float)vh[p] : 0.0f;
+      float v = (float)vloc[p] + vx + vhf + hA2f;
       if (!bloch) v += Exf * x + Eyf * y + Ezf * z;
       *reinterpret_cast<float *>(&aux[p].veff) = v;
-      const float t[6] = {nf, nf * 0.75f * vx, nf * vx, x * nf, y * nf, z * nf};
+      // (with the Hartree potential the record subtracts int n (v_x + v_H) and adds E_H =
+      // 1/2 int n v_H: the third sum is int n (v_x + v_H / 2))
+      const float t[6] = {nf, nf * 0.75f * vx, nf * (vx + 0.5f * vhf), x * nf, y * nf, z * nf};
 #pragma unroll
       for (int c = 0; c < 6; c++) df_acc(fh[c], fl[c], t[c]);
       fl[0] += nl;  // the electron count keeps the double-float density in full
@@ -541,12 +560,13 @@ __device__ __forceinline__ void lda_body(long N, int nx, int ny, int nz, double 
       const double x = (ix - cx) * h, y = (iy - cy) * h, z = (iz - cz) * h;
       double vx = 0.0;
       if (xc) vx = -cbrt(3.0 * n * 0.31830988618379067154);  // 1/pi
-      double v = vloc[p] + vx + half_A2;
+      const double vhd = vh ? vh[p] : 0.0;
+      double v = vloc[p] + vx + vhd + half_A2;
       if (!bloch) v += Ex * x + Ey * y + Ez * z;
       *reinterpret_cast<double *>(&aux[p].veff) = v;
       acc[0] += n;
       acc[1] += n * 0.75 * vx;
-      acc[2] += n * vx;
+      acc[2] += n * (vx + 0.5 * vhd);
       acc[3] += x * n;
       acc[4] += y * n;
       acc[5] += z * n;
@@ -574,9 +594,9 @@ template <typename R>
 __global__ void __launch_bounds__(LDA_THREADS)
 lda_kernel(long N, int nx, int ny, int nz, double h, int bloch, int n_kb, int n_batches, const double *wocc,
            const double *dens_part, const double *vloc, int xc, double Ex, double Ey, double Ez, double half_A2,
-           PointAux *aux, double *lda_part, const double *n_in) {
+           PointAux *aux, double *lda_part, const double *n_in, const double *vh) {
   lda_body<R>(N, nx, ny, nz, h, bloch, n_kb, n_batches, wocc, dens_part, vloc, xc, Ex, Ey, Ez, half_A2, aux,
-              lda_part, blockIdx.x, gridDim.x, n_in);
+              lda_part, blockIdx.x, gridDim.x, n_in, vh);
 }
 
 // The density of this system's states at every point, n(r) = sum_k w_k f sum_i |psi|^2, as
@@ -775,13 +795,13 @@ cudaError_t launch_lda_batch(int prec, const BatchAux *aux, const BatchClock *cl
 cudaError_t launch_lda(int prec, int bloch, long N, int nx, int ny, int nz, double h, int n_kb, int n_batches,
                        const double *wocc, const double *dens_part, const double *vloc, int xc, const double E[3],
                        double half_A2, PointAux *aux, double *lda_part, int n_blocks, cudaStream_t s,
-                       const double *n_in) {
+                       const double *n_in, const double *vh) {
   if (prec == P_C64)
     lda_kernel<float><<<n_blocks, LDA_THREADS, 0, s>>>(N, nx, ny, nz, h, bloch, n_kb, n_batches, wocc, dens_part,
-                                                       vloc, xc, E[0], E[1], E[2], half_A2, aux, lda_part, n_in);
+                                                       vloc, xc, E[0], E[1], E[2], half_A2, aux, lda_part, n_in, vh);
   else
     lda_kernel<double><<<n_blocks, LDA_THREADS, 0, s>>>(N, nx, ny, nz, h, bloch, n_kb, n_batches, wocc, dens_part,
-                                                        vloc, xc, E[0], E[1], E[2], half_A2, aux, lda_part, n_in);
+                                                        vloc, xc, E[0], E[1], E[2], half_A2, aux, lda_part, n_in, vh);
   return cudaGetLastError();
 }
 

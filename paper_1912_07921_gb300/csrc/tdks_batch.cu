@@ -212,6 +212,7 @@ int tdks_batch_create(const tdks_sys *systems, int n, void *stream, tdks_batch_t
     if (!tma_supported(s->M, 16, 8)) return bad("no TMA sweep for this FD order");
     if (s->prop != TDKS_PROP_TAYLOR4) return bad("batched propagation uses the Taylor-4 propagator");
     if (s->xfn) return bad("a state-parallel system (exchange hook set) cannot join a batch");
+    if (s->xc == TDKS_XC_LDA_X_HARTREE) return bad("a system with the Hartree term cannot join a batch");
   }
   std::vector<GatherParams> gp[4];
   std::vector<long> gather_begin(n + 1, 0), unit_begin(n + 1, 0), lda_begin(n + 1, 0);

@@ -352,18 +352,23 @@ int run_lda(tdks_system *s, const double E[3], const double A[3]) {
   const double half_A2 = s->gauge == TDKS_GAUGE_VELOCITY ? 0.5 * (A[0] * A[0] + A[1] * A[1] + A[2] * A[2]) : 0.0;
   const double El[3] = {s->gauge == TDKS_GAUGE_LENGTH ? E[0] : 0.0, s->gauge == TDKS_GAUGE_LENGTH ? E[1] : 0.0,
                         s->gauge == TDKS_GAUGE_LENGTH ? E[2] : 0.0};
-  if (s->xfn) {  // state-parallel: the density of every rank's states
+  const bool hartree = s->xc == TDKS_XC_LDA_X_HARTREE;
+  if (s->xfn || hartree) {  // the density as one FP64 array: every rank's states, or the Hartree source
     cudaError_t e = launch_density_sum(s->prec, s->N, s->n_kb, s->n_batches, s->d_wocc, s->dens_part, s->n_total,
                                        s->stream);
     s->launches++;
     if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("density sum: ") + cudaGetErrorString(e));
-    if (int r = s->xfn(s->n_total, (long long)s->N, (void *)s->stream, s->xctx))
-      return fail(TDKS_EDEVICE, "exchange hook failed on the density (" + std::to_string(r) + ")");
+    if (s->xfn)
+      if (int r = s->xfn(s->n_total, (long long)s->N, (void *)s->stream, s->xctx))
+        return fail(TDKS_EDEVICE, "exchange hook failed on the density (" + std::to_string(r) + ")");
   }
+  if (hartree)
+    if (int rc = hartree_solve(s)) return rc;
   Timed tm(s, 2);
   cudaError_t e = launch_lda(s->prec, s->bc == TDKS_BC_BLOCH, s->N, s->nx, s->ny, s->nz, s->h, s->n_kb,
-                             s->n_batches, s->d_wocc, s->dens_part, s->vloc, s->xc, El, half_A2, s->aux,
-                             s->lda_part, lda_blocks(s->N), s->stream, s->xfn ? s->n_total : nullptr);
+                             s->n_batches, s->d_wocc, s->dens_part, s->vloc, s->xc != TDKS_XC_NONE, El, half_A2,
+                             s->aux, s->lda_part, lda_blocks(s->N), s->stream,
+                             (s->xfn || hartree) ? s->n_total : nullptr, hartree ? s->d_vh : nullptr);
   s->launches++;
   if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("lda: ") + cudaGetErrorString(e));
   return TDKS_OK;
@@ -592,6 +597,7 @@ int tdks_destroy(tdks_sys s) {
   cudaFree(s->obs_rec); cudaFree(s->d_kvec); cudaFree(s->d_wocc);
   cudaFree(s->staging);
   tsurff_free(s);
+  hartree_free(s);
   if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
   if (s->ev_staging_free) cudaEventDestroy(s->ev_staging_free);
   for (auto e : s->ev_chunk) cudaEventDestroy(e);
@@ -825,8 +831,13 @@ int tdks_set_field(tdks_sys s, int gauge, const double pol[3], double amp, doubl
 
 int tdks_set_xc(tdks_sys s, int xc, double occupation) {
   if (!s) return fail(TDKS_EINVAL, "NULL system");
-  if (xc != TDKS_XC_NONE && xc != TDKS_XC_LDA_X) return fail(TDKS_EINVAL, "bad xc");
+  if (xc != TDKS_XC_NONE && xc != TDKS_XC_LDA_X && xc != TDKS_XC_LDA_X_HARTREE) return fail(TDKS_EINVAL, "bad xc");
   if (!(occupation > 0.0)) return fail(TDKS_EINVAL, "occupation must be > 0");
+  if (xc == TDKS_XC_LDA_X_HARTREE) {
+    if (s->prop != TDKS_PROP_TAYLOR4)
+      return fail(TDKS_EINVAL, "the Hartree term is built for the Taylor-4 propagator only");
+    if (int rc = hartree_setup(s)) return rc;
+  }
   s->xc = xc;
   s->occ = occupation;
   std::vector<double> wocc(s->n_k);
@@ -1249,6 +1260,8 @@ int tdks_set_propagator(tdks_sys s, int propagator) {
     return fail(TDKS_EINVAL, "state-parallel propagation (tdks_set_exchange) is Taylor-4 only");
   if (propagator == TDKS_PROP_RK4 && s->prec != TDKS_C128)
     return fail(TDKS_EINVAL, "RK4 runs on complex128 systems");
+  if (propagator != TDKS_PROP_TAYLOR4 && s->xc == TDKS_XC_LDA_X_HARTREE)
+    return fail(TDKS_EINVAL, "the Hartree term is built for the Taylor-4 propagator only");
   CU(cudaStreamSynchronize(s->stream));
   if (propagator != TDKS_PROP_TAYLOR4 && propagator != TDKS_PROP_RK4 && !s->vx_hist[0])
     for (int j = 0; j < 4; j++) CU(cudaMalloc((void **)&s->vx_hist[j], (size_t)s->N * sizeof(double)));

@@ -100,6 +100,11 @@ struct tdks_system {
   double ts_vol[7] = {0, 0, 0, 0, 0, 0, 0};
   double ts_trel = 0.0, ts_t0 = 0.0;
   bool ts_started = false;
+  // Hartree term (xc = TDKS_XC_LDA_X_HARTREE): padded transform buffer and transformed kernel
+  // (hp[] points per axis), the potential v_H (N doubles); the density goes through n_total
+  double2 *d_hbuf = nullptr, *d_hkern = nullptr;
+  double *d_vh = nullptr;
+  int hp[3] = {0, 0, 0};
   // clock used by batched propagation: state time, step length, sub-steps per step
   double clock_t = 0.0, clock_dt = 0.0;
   int clock_substeps = 1;
@@ -142,6 +147,10 @@ int ensure_density(tdks_system *s);
 int tsurff_accumulate(tdks_system *s, double weight);
 void tsurff_advance(tdks_system *s, double t, double dt);
 void tsurff_free(tdks_system *s);
+// Hartree potential (tdks_hartree.cu): workspace and transformed kernel; v_H of n_total into d_vh
+int hartree_setup(tdks_system *s);
+int hartree_solve(tdks_system *s);
+void hartree_free(tdks_system *s);
 int check_err(tdks_system *s);
 double kinetic_max(const tdks_system *s);
 

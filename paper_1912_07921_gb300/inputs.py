@@ -63,7 +63,7 @@ GAUGE_NONE, GAUGE_LENGTH, GAUGE_VELOCITY = 0, 1, 2
 ENV_NONE, ENV_SIN2 = 0, 1
 BC_ZERO, BC_BLOCH = 0, 1
 PREC_C128, PREC_C64 = 0, 1
-XC_NONE, XC_LDA_X = 0, 1
+XC_NONE, XC_LDA_X, XC_LDA_X_HARTREE = 0, 1, 2
 
 
 @dataclasses.dataclass

@@ -934,3 +934,61 @@ def test_energy_with_projectors_and_length_gauge_field_is_the_dense_expectation(
     assert rec[3] == pytest.approx(ex, rel=1e-12)
     assert rec[2] == pytest.approx(band + ex, rel=1e-12)
     assert rec[7] == pytest.approx(E @ np.array(spec.pol), rel=1e-12)
+
+
+# Kinetic heat current (Sec. "Conductivities", eqn. KEcurrent; the reading with the last pair
+# antisymmetric, covariant derivatives).  On a periodic grid every discrete operator in it is
+# diagonal in the grid's plane waves q = k + 2 pi n / L: the covariant gradient has the symbol
+# i kappa = i (qd + A) (qd the central difference's symbol), the covariant Laplacian -Lambda =
+# -(lambda + 2 A.qd + |A|^2) (lambda the star Laplacian's), the composed second differences
+# -kappa_i kappa_j.  So J_t = sum_k w_k f sum_q |a_q|^2 (-1/4) kappa_q (Lambda_q + |kappa_q|^2), with
+# a_q the state's plane-wave amplitudes (numpy's FFT), and for a plane wave in the continuum limit
+# -(1/2)|k|^2 k: minus its kinetic energy times its velocity.
+def _heat_symbols(spec, q, A):
+    M = spec.fd_order // 2
+    c, d = oracle.fd_weights(M)
+    h = spec.h
+    qd = np.array([2.0 / h * sum(d[m] * math.sin(m * qa * h) for m in range(1, M + 1)) for qa in q])
+    lam = sum((-c[0] - 2 * sum(c[m] * math.cos(m * qa * h) for m in range(1, M + 1))) / (h * h) for qa in q)
+    kappa = qd + A
+    Lam = lam + 2.0 * A @ qd + A @ A
+    return -0.25 * kappa * (Lam + kappa @ kappa)
+
+
+@pytest.mark.parametrize("fd_order", [4, 8])
+def test_heat_current_of_plane_waves(fd_order):
+    spec, inp, psi, qs = _plane_wave_case(fd_order, I.GAUGE_VELOCITY)
+    o = oracle.System(spec, inp)
+    A = np.array([0.07, -0.12, 0.2])
+    got = o.heat_current(A, psi)
+    want = sum(inp.kw[ik] * spec.occ * _heat_symbols(spec, qs[ik, j], A) for ik in range(2) for j in range(3))
+    np.testing.assert_allclose(got, want, rtol=1e-11, atol=1e-13 * np.abs(want).max())
+    # continuum limit of one plane wave: minus its kinetic energy times its velocity
+    spec1 = dataclasses.replace(spec, h=0.01)
+    q = np.array([0.3, -0.2, 0.5])
+    np.testing.assert_allclose(_heat_symbols(spec1, q, np.zeros(3)), -0.5 * (q @ q) * q, rtol=1e-4)
+
+
+def test_heat_current_of_random_bloch_states_is_diagonal_in_plane_waves():
+    spec = _spec(nx=8, ny=6, nz=5, h=0.4, fd_order=4, bc=I.BC_BLOCH, n_orb=2, n_k=2, seed=9)
+    inp = _inputs(spec)
+    o = oracle.System(spec, inp)
+    L = np.array([spec.nx, spec.ny, spec.nz]) * spec.h
+    X, Y, Z = _grids(spec)
+    rng = np.random.Generator(np.random.PCG64(7))
+    A = np.array([0.15, 0.05, -0.1])
+    psi = np.empty((2, spec.nz, spec.ny, spec.nx, 2), dtype=np.complex128)
+    want = np.zeros(3)
+    for ik in range(2):
+        k = inp.kpts[ik]
+        for j in range(2):
+            u = rng.standard_normal((spec.nz, spec.ny, spec.nx)) + 1j * rng.standard_normal((spec.nz, spec.ny, spec.nx))
+            psi[ik, ..., j] = np.exp(1j * (k[0] * X + k[1] * Y + k[2] * Z)) * u
+            a = np.fft.fftn(u) / u.size  # u = sum_n a_n exp(2 pi i n.r / L)
+            for (nz_, ny_, nx_), amp in np.ndenumerate(a):
+                n = np.array([nx_ if nx_ <= spec.nx // 2 else nx_ - spec.nx,
+                              ny_ if ny_ <= spec.ny // 2 else ny_ - spec.ny,
+                              nz_ if nz_ <= spec.nz // 2 else nz_ - spec.nz])
+                want += inp.kw[ik] * spec.occ * abs(amp) ** 2 * _heat_symbols(spec, k + 2 * np.pi * n / L, A)
+    got = o.heat_current(A, psi)
+    np.testing.assert_allclose(got, want, rtol=1e-11, atol=1e-12 * np.abs(want).max())
