@@ -416,6 +416,19 @@ int tdks_apply_H_noalloc(int nx, int ny, int nz, double h, int fd_order, int pre
                          const double *dev_vloc, const void *dev_in, void *dev_out, void *stream);
 
 /*
+ * Kinetic heat current of a periodic cell (Sec. "Conductivities", eqn. KEcurrent), cell-averaged:
+ *   J_t = (1/Omega) sum_k w_k f int [J_t(r)] dr,
+ *   [J_t]_i = (i/8) ([d_i phi^*][Lap phi] - [Lap phi^*][d_i phi] - [d_i grad phi^*].[grad phi]
+ *              + [grad phi^*].[d_i grad phi]),
+ * the printed last pair taken with the sign that makes J_t real (a plane wave then carries minus
+ * its kinetic energy times its velocity, the sign convention of the charge current J of the
+ * record); derivatives as in H (central differences of the system's order with Bloch images,
+ * covariant d + i A with the vector potential at t_field in the velocity gauge).  out[3]
+ * receives J_t of the current state.  Periodic cells only (TDKS_EINVAL otherwise).  Synchronises.
+ */
+int tdks_heat_current(tdks_sys sys, double t_field, double *out);
+
+/*
  * t-SURFF photoelectron amplitudes (Sec. "t-SURFF": the expansion coefficients b_i(p, t) of
  * the orbitals on Volkov states, obtained from the continuity equation as the time integral
  * of the current through a surface S):

@@ -57,6 +57,7 @@ SIGNATURES = {
     "tdks_apply_H_noalloc": ([I, I, I, D, I, I, I, P, P, P, P], I),
     "tdks_fma_rate": ([I, PD], I),
     "tdks_set_tsurff": ([P, P, I, P], I),
+    "tdks_heat_current": ([P, D, PD], I),
     "tdks_get_tsurff": ([P, P, PD], I),
     "tdks_last_error": ([], ctypes.c_char_p),
 }

@@ -15,7 +15,7 @@ SOURCES = ["tdks_sweep.cu", "tdks_sweep_tma.cu", "tdks_sweep_ws1.cu", "tdks_swee
            "tdks_sweep_ws4.cu", "tdks_sweep_ws5.cu",
            "tdks_aux.cu", "tdks_capi.cu", "tdks_batch.cu", "tdks_noalloc.cu",
            "tdks_checkpoint.cu", "tdks_probe.cu",
-           "tdks_tsurff.cu", "tdks_hartree.cu"]
+           "tdks_tsurff.cu", "tdks_hartree.cu", "tdks_heat.cu"]
 HEADERS = ["tdks_internal.cuh", "tdks_vec.cuh", "tdks_sweep_common.cuh", "tdks_tma.cuh", "tdks_system.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

@@ -94,6 +94,13 @@ class System:
     def set_tile(self, tx, ty, zc=0):
         _lib.check(self.lib.tdks_set_tile(self.h, tx, ty, zc))
 
+    def heat_current(self, t_field: float) -> np.ndarray:
+        """Macroscopic kinetic heat current of the current state (periodic cells), with the
+        vector potential at t_field."""
+        out = np.empty(3)
+        _lib.check(self.lib.tdks_heat_current(self.h, t_field, _dp(out)))
+        return out
+
     def set_tsurff(self, box, p):
         """t-SURFF amplitudes through the surface of the box of grid planes `box` =
         (i0, i1, j0, j1, k0, k1) for momenta p [n_p, 3], accumulated from the next propagation

@@ -562,3 +562,36 @@ def test_periodic_current_includes_the_projectors_commutator(prec):
     assert np.abs(full - local).max() > 1e-3 * scale
     tol = 1e-12 if prec == I.PREC_C128 else 1e-4
     assert np.abs(got[4:7] - full).max() < tol * scale
+
+
+@pytest.mark.parametrize("prec,order", [(I.PREC_C128, 4), (I.PREC_C128, 8), (I.PREC_C64, 4)])
+def test_heat_current_matches_oracle(prec, order):
+    """The kinetic heat current of Sec. "Conductivities" (eqn. KEcurrent; the reading with the
+    last pair antisymmetric, covariant derivatives) of a periodic cell in the velocity gauge: the
+    GPU's cell integral (composed second differences, no mixed derivatives) against the oracle's
+    pointwise formula."""
+    spec = bloch_cell(prec, fd_order=order, n_k=2)
+    inp = bloch_inputs(spec)
+    psi = I.random_orbitals(spec, 17) * 0.2 + inp.psi0
+    if prec == I.PREC_C64:
+        psi = psi.astype(np.complex64).astype(np.complex128)
+    inp.psi0 = psi
+    sysm = _system(spec, inp)
+    got = sysm.heat_current(0.6)
+    sysm.close()
+    o = oracle.System(spec, inp)
+    _, A = o.field(0.6)
+    assert np.abs(A).max() > 0
+    ref = o.heat_current(A, psi)
+    tol = 1e-11 if prec == I.PREC_C128 else 1e-6
+    assert np.abs(got - ref).max() <= tol * np.abs(ref).max(), (got, ref)
+
+
+def test_heat_current_refuses_finite_boxes():
+    from paper_1912_07921_gb300._lib import TdksError
+    spec = ragged_molecule(I.PREC_C128)
+    sysm = _system(spec, I.make_inputs(spec))
+    with pytest.raises(TdksError) as e:
+        sysm.heat_current(0.0)
+    assert e.value.code == 1
+    sysm.close()
