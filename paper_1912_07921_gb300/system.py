@@ -98,7 +98,7 @@ class System:
         """Macroscopic kinetic heat current of the current state (periodic cells), with the
         vector potential at t_field."""
         out = np.empty(3)
-        _lib.check(self.lib.tdks_heat_current(self.h, t_field, _dp(out)))
+        _lib.check(self.lib.tdks_heat_current(self.h, t_field, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return out
 
     def set_tsurff(self, box, p):

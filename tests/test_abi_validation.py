@@ -5,6 +5,8 @@ with the shapes' own constraints (every consumer thread owns R y-adjacent points
 16-byte vector: CW warps x 32 = 4 vectors x TX x TY / R)."""
 import ctypes
 
+import numpy as np
+
 import pytest
 
 EINVAL = 1
@@ -59,6 +61,8 @@ def test_calls_on_a_null_system_are_refused(lib):
     assert lib.tdks_set_tsurff(None, None, 0, None) == EINVAL
     assert lib.tdks_get_tsurff(None, None, None) == EINVAL
     assert lib.tdks_set_failure_injection(None, 0) == EINVAL
+    out3 = np.empty(3)
+    assert lib.tdks_heat_current(None, 0.0, out3.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) == EINVAL
     assert lib.tdks_fma_rate(0, None) == EINVAL
     assert lib.tdks_fma_rate(7, ctypes.byref(ctypes.c_double())) == EINVAL
 
