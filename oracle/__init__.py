@@ -68,6 +68,7 @@ def _load():
         _lib.oracle_cfm4_constants.argtypes = [P, P]
         _lib.oracle_propagate_emr.argtypes = [S, D, D, I, I, P, P]
         _lib.oracle_propagate_aetrs.argtypes = [S, D, D, I, I, P, P]
+        _lib.oracle_propagate_etrs.argtypes = [S, D, D, I, I, P, P]
         _lib.oracle_propagate_rk4.argtypes = [S, D, D, I, I, P, P]
         _lib.oracle_hartree.argtypes = [S, P, P]
         _lib.oracle_hartree.restype = D
@@ -229,6 +230,16 @@ class System:
         obs = np.empty((n_steps, 8)) if record else None
         self.lib.oracle_propagate_aetrs(self.ref, t0, dt, n_steps, substeps, _ptr(psi),
                                         _ptr(obs) if record else None)
+        return psi, obs
+
+    def propagate_etrs(self, psi, t0, dt, n_steps, substeps, record=True):
+        """Enforced time-reversal symmetry: H at t + ds from the density of the trial state
+        exp(-i ds H[t]) psi; half exponentials with H at t and at t + ds; length gauge or no
+        field."""
+        psi = self._psi(psi).copy()
+        obs = np.empty((n_steps, 8)) if record else None
+        self.lib.oracle_propagate_etrs(self.ref, t0, dt, n_steps, substeps, _ptr(psi),
+                                       _ptr(obs) if record else None)
         return psi, obs
 
     def propagate_rk4(self, psi, t0, dt, n_steps, substeps, record=True):

@@ -742,6 +742,50 @@ static void propagate_two_point(const oracle_sys *s, int aetrs, double t0, doubl
   free(n); free(v);
 }
 
+/* --------------------------------------------------------------------------------
+ * Enforced time-reversal symmetry with its trial state (the scheme of the propagator review
+ * the paper cites in Sec. "New propagators for real-time TDDFT"; used in the hydrogen-fluoride
+ * dimer run of Sec. "vdW-TS" and the first GPU port of Sec. "GPUs").  Per sub-step ds:
+ *   trial:  phi~ = exp(-i ds H[t]) phi(t)                     (H[t] frozen over the step)
+ *   step:   phi(t + ds) = exp(-i ds/2 H[t + ds]) exp(-i ds/2 H[t]) phi(t)
+ * with H[t] = H0 + v_x(n(phi(t))) + E(t).r and H[t + ds] = H0 + v_x(n(phi~)) + E(t + ds).r.
+ * Each exponential is the Taylor-4 series.  Without a density-dependent potential the trial
+ * changes nothing and the step is the AETRS step.  Records as oracle_propagate.
+ * ------------------------------------------------------------------------------ */
+void oracle_propagate_etrs(const oracle_sys *s, double t0, double dt, int n_steps, int substeps, cplx *psi,
+                           double *obs) {
+  if (s->gauge == 2) return;  /* the field must enter H linearly */
+  const long N = npts(s);
+  const long tot = (long)s->n_k * N * s->n_orb;
+  const double ds = dt / (double)substeps;
+  const int dp = has_density_potential(s);
+  double *n = (double *)malloc(sizeof(double) * (size_t)N);
+  double *v_t = (double *)malloc(sizeof(double) * (size_t)N);
+  double *v_next = (double *)malloc(sizeof(double) * (size_t)N);
+  cplx *trial = (cplx *)malloc(sizeof(cplx) * (size_t)tot);
+  for (int st = 0; st < n_steps; st++) {
+    double t = t0 + (double)st * dt;
+    if (obs) oracle_observables(s, t, t + 0.5 * ds, psi, obs + 8 * st);
+    for (int j = 0; j < substeps; j++) {
+      const double tj = t + (double)j * ds;
+      double E[3], A[3];
+      oracle_field(s, tj, E, A);
+      if (dp) {
+        oracle_density(s, psi, n);
+        density_potential(s, n, v_t, NULL);
+        memcpy(trial, psi, sizeof(cplx) * (size_t)tot);
+        taylor_exp_field(s, E, v_t, ds, trial);
+        oracle_density(s, trial, n);
+        density_potential(s, n, v_next, NULL);
+      }
+      taylor_exp_field(s, E, dp ? v_t : NULL, 0.5 * ds, psi);
+      oracle_field(s, tj + ds, E, A);
+      taylor_exp_field(s, E, dp ? v_next : NULL, 0.5 * ds, psi);
+    }
+  }
+  free(n); free(v_t); free(v_next); free(trial);
+}
+
 void oracle_propagate_emr(const oracle_sys *s, double t0, double dt, int n_steps, int substeps, cplx *psi,
                           double *obs) {
   propagate_two_point(s, 0, t0, dt, n_steps, substeps, psi, obs);

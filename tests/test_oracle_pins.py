@@ -664,6 +664,65 @@ def test_emr_and_aetrs_with_exchange_are_second_order(name):
 
 
 # ---------------------------------------------------------------------------------------
+# Enforced time-reversal symmetry with its trial state (the scheme of the propagator review
+# the paper cites beside EMR; forms as the oracle states)
+# ---------------------------------------------------------------------------------------
+def test_etrs_without_exchange_is_the_aetrs_step():
+    """Without a density-dependent potential the trial state changes nothing: the ETRS step is
+    exp(-i dt/2 H[t + dt]) exp(-i dt/2 H[t]), the AETRS step, with the field at t and t + dt."""
+    spec, inp, o = _cfm_case(0)
+    e, obs_e = o.propagate_etrs(inp.psi0, 0.0, 0.04, 5, 2)
+    a, obs_a = o.propagate_aetrs(inp.psi0, 0.0, 0.04, 5, 2)
+    assert np.max(np.abs(e - a)) == 0.0
+    np.testing.assert_array_equal(obs_e, obs_a)
+
+
+def _taylor4(z):
+    return 1 + z + z * z / 2 + z ** 3 / 6 + z ** 4 / 24
+
+
+def test_etrs_on_plane_waves_with_exchange_is_closed_form():
+    """Plane waves in a cell keep a uniform density, so H acts on each as the number
+    lam_j = kappa_j + v_x(n) and every exponential is the scalar Taylor polynomial R(-i tau lam).
+    One ETRS sub-step: the trial multiplies plane wave j by R(-i dt lam_j) (uniform density
+    n~ = sum f |amplitude|^2 / V), then phi_j <- R(-i dt/2 (kappa_j + v_x(n~))) R(-i dt/2 lam_j)
+    phi_j.  A trial of dt/2, or v_x of the old density in the second half, misses by >1e-8."""
+    spec, inp, psi, qs = _plane_wave_case(4, I.GAUGE_NONE)
+    spec = dataclasses.replace(spec, xc=I.XC_LDA_X, amp=0.0)
+    o = oracle.System(spec, inp)
+    vol = spec.n_points * spec.h ** 3
+    psi = psi / math.sqrt(vol)
+    kap = np.array([[_pw_eigen(spec, qs[ik, j], np.zeros(3))[0] for j in range(3)] for ik in range(2)])
+    dt, n_steps = 0.8 / np.max(np.abs(kap)), 3
+    vx = lambda n: -(3 * n / math.pi) ** (1 / 3)
+    dens = lambda amp: spec.occ * float(np.sum(inp.kw[:, None] * np.abs(amp) ** 2)) / vol
+
+    def closed(trial_frac, use_trial):
+        amp = np.ones((2, 3), dtype=complex)
+        for _ in range(n_steps):
+            lam1 = kap + vx(dens(amp))
+            lam2 = kap + vx(dens(amp * _taylor4(-1j * trial_frac * dt * lam1))) if use_trial else lam1
+            amp = amp * _taylor4(-0.5j * dt * lam1) * _taylor4(-0.5j * dt * lam2)
+        return amp
+
+    got, _ = o.propagate_etrs(psi, 0.0, dt, n_steps, 1, record=False)
+    want = closed(1.0, True)
+    for ik in range(2):
+        for j in range(3):
+            np.testing.assert_allclose(got[ik, ..., j], want[ik, j] * psi[ik, ..., j], rtol=0, atol=1e-13 / math.sqrt(vol))
+    for wrong in (closed(0.5, True), closed(1.0, False)):
+        assert np.max(np.abs(wrong - want)) > 1e-8
+
+
+def test_etrs_with_exchange_is_second_order():
+    """With LDA exchange the trial state supplies v_x at t + dt: ETRS stays order two (error
+    ratio ~4 per halving; reference: CFM4 at dt/256)."""
+    spec, inp, o = _cfm_case(1)
+    for r in _orders(o, inp, o.propagate_etrs, 0.64, (16, 32, 64)):
+        assert 3.4 < r < 4.8, r
+
+
+# ---------------------------------------------------------------------------------------
 # Classical Runge-Kutta 4 (Runge-Kutta is in the same section's list of propagators)
 # ---------------------------------------------------------------------------------------
 def test_rk4_without_field_or_exchange_is_the_taylor_step():
