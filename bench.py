@@ -566,7 +566,8 @@ def run_propagator_study(args):
     on a synthetic molecule): a 48^3 molecule (h = 0.25, order 8, 16 orbitals in complex128,
     6 atoms with projectors, LDA exchange, laser E0 = 0.02, omega = 0.5) over T = 1 (20 steps
     of dt = 0.05), with Taylor-4 and EMR (one exponential per sub-step) and RK4 (four stages)
-    at 4, 8, 16 and AETRS and CFM4 (two half exponentials) at 2, 4, 8 sub-steps per step;
+    and ETRS (a trial exponential of the sub-step and two halves) at 4, 8, 16, AETRS and CFM4
+    (two half exponentials) at 2, 4, 8 sub-steps per step;
     error = ||psi - psi_ref|| / ||psi_ref||, psi_ref from RK4 at 64 sub-steps per step (the
     density rebuilt at every stage, fourth order in the whole non-linear problem); time from
     CUDA events around each propagation."""
@@ -600,7 +601,7 @@ def run_propagator_study(args):
     nref = np.linalg.norm(ref)
     pts = []
     for prop, name, subs_list in ((0, "taylor4", (4, 8, 16)), (2, "emr", (4, 8, 16)), (3, "aetrs", (2, 4, 8)),
-                                  (1, "cfm4", (2, 4, 8)), (4, "rk4", (4, 8, 16))):
+                                  (5, "etrs", (4, 8, 16)), (1, "cfm4", (2, 4, 8)), (4, "rk4", (4, 8, 16))):
         for subs in subs_list:
             psi, ms = run(prop, subs)
             pts.append({"propagator": name, "substeps": subs, "ms": round(ms, 2),

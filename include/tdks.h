@@ -205,6 +205,18 @@ int tdks_propagate_n(tdks_sys sys, double t0, double dt, int n_steps, int subste
  * for complex64); any gauge; its stability limit on the imaginary axis is the Taylor-4 one.
  */
 #define TDKS_PROP_RK4 4
+/*
+ * TDKS_PROP_ETRS: enforced time-reversal symmetry with its trial state, as the propagator
+ * review that the same section cites defines it (the scheme of the hydrogen-fluoride dimer run
+ * of Sec. "vdW-TS" and of the first GPU port of Sec. "GPUs"):
+ *   trial:  phi~ = exp(-i ds H[t]) phi(t),
+ *   step:   phi(t + ds) = exp(-i ds/2 H[t + ds]) exp(-i ds/2 H[t]) phi(t),
+ * H[t] with v_x of phi(t) and E(t), H[t + ds] with v_x of the trial's density and E(t + ds).
+ * Three Taylor-4 exponentials per sub-step (lengths ds, ds/2, ds/2; the stability limit
+ * applies to ds); without exchange the trial is skipped and the step is the AETRS step.  One
+ * extra state-sized buffer (allocated here).  Length gauge or no field, as AETRS.
+ */
+#define TDKS_PROP_ETRS 5
 int tdks_set_propagator(tdks_sys sys, int propagator);
 
 /*

@@ -593,6 +593,7 @@ int tdks_destroy(tdks_sys s) {
   cudaFree(s->vloc); cudaFree(s->aux); cudaFree(s->dens_part); cudaFree(s->lda_part);
   cudaFree(s->obs_part); cudaFree(s->ring); cudaFree(s->fin_part);
   for (int j = 0; j < 4; j++) cudaFree(s->vx_hist[j]);
+  cudaFree(s->etrs_save); cudaFree(s->etrs_save_lo);
   cudaFree(s->n_total); cudaFree(s->fin_sum);
   cudaFree(s->obs_rec); cudaFree(s->d_kvec); cudaFree(s->d_wocc);
   cudaFree(s->staging);
@@ -1104,10 +1105,10 @@ static int taylor_tail(tdks_system *s, double dts, const double A[3]) {
 
 // V_eff of one CFM4 exponential (push: first store v_x of the current density as the newest
 // history entry).
-static int run_cfm_veff(tdks_system *s, bool push, const double w[4], const double E[3]) {
+static int run_cfm_veff(tdks_system *s, bool push, int nh, const double w[4], const double E[3]) {
   CfmHist h{};
   for (int j = 0; j < 4; j++) h.v[j] = s->vx_hist[j];
-  h.nh = s->xc == TDKS_XC_LDA_X ? s->n_hist : 0;
+  h.nh = s->xc == TDKS_XC_LDA_X ? nh : 0;
   for (int j = 0; j < 4; j++) h.w[j] = j < h.nh ? w[j] : 0.0;
   const double El[3] = {s->gauge == TDKS_GAUGE_LENGTH ? E[0] : 0.0, s->gauge == TDKS_GAUGE_LENGTH ? E[1] : 0.0,
                         s->gauge == TDKS_GAUGE_LENGTH ? E[2] : 0.0};
@@ -1165,11 +1166,75 @@ static int propagate_exp(tdks_system *s, double t0, double dt, int n_steps, int 
           for (int ax = 0; ax < 3; ax++) Ef[ax] += fa.c[q] * Eq[ax];
         }
         if (xc) factor_history_weights(fa, s->n_hist, w);
-        if ((rc = run_cfm_veff(s, xc && f == 0, w, Ef))) return rc;
+        if ((rc = run_cfm_veff(s, xc && f == 0, s->n_hist, w, Ef))) return rc;
         const double tau = fa.frac * ds;
         if ((rc = first_sweep(s, 0.0, -tau, A0, false))) return rc;
         if ((rc = taylor_tail(s, tau, A0))) return rc;
       }
+      s->dens_valid = true;  // the last sweep wrote the density of the new state
+    }
+    s->steps++;
+  }
+  s->clock_t = t0 + n_steps * dt;
+  s->clock_dt = dt;
+  s->clock_substeps = substeps;
+  return TDKS_OK;
+}
+
+// Enforced time-reversal symmetry with its trial state (see tdks_set_propagator): per sub-step
+// ds, H[t] takes v_x of the current state; the trial exp(-i ds H[t]) phi runs on the state
+// itself (saved first), and its density gives v_x at t + ds; then the saved state takes
+// exp(-i ds/2 H[t]) and exp(-i ds/2 H[t + ds]).  History slots: [0] the newest v_x, [1] v_x(t)
+// while the trial's is computed.
+static int propagate_etrs(tdks_system *s, double t0, double dt, int n_steps, int substeps) {
+  if (s->gauge == TDKS_GAUGE_VELOCITY)
+    return fail(TDKS_EINVAL, "ETRS needs a field that enters H linearly (length gauge or no field)");
+  const double ds = dt / substeps;
+  if (std::fabs(ds) * kinetic_max(s) > 2.0 * std::sqrt(2.0))
+    return fail(TDKS_EUNSTABLE, "ETRS trial exponential beyond the Taylor-4 stability limit (tau * K_max > 2 sqrt 2)");
+  int rc = ensure_density(s);
+  if (rc) return rc;
+  const double A0[3] = {0.0, 0.0, 0.0};
+  const bool xc = s->xc == TDKS_XC_LDA_X;
+  const double w_new[4] = {1.0, 0.0, 0.0, 0.0}, w_old[4] = {0.0, 1.0, 0.0, 0.0};
+  auto exponential = [&](double tau) -> int {
+    int r;
+    if ((r = first_sweep(s, 0.0, -tau, A0, false))) return r;
+    return taylor_tail(s, tau, A0);
+  };
+  auto copy_state = [&](void *dst, void *dst_lo, const void *src, const void *src_lo) -> int {
+    CU(cudaMemcpyAsync(dst, src, s->state_bytes, cudaMemcpyDeviceToDevice, s->stream));
+    if (src_lo) CU(cudaMemcpyAsync(dst_lo, src_lo, s->state_bytes, cudaMemcpyDeviceToDevice, s->stream));
+    return TDKS_OK;
+  };
+  for (int st = 0; st < n_steps; st++) {
+    const double t = t0 + st * dt;
+    for (int j = 0; j < substeps; j++) {
+      const double tj = t + j * ds;
+      double E[3], A[3];
+      if (j == 0) {
+        // record of the state at t: the Hamiltonian of t + ds/2 with v_x of this state
+        field_at(s, tj + 0.5 * ds, E, A);
+        if ((rc = run_lda(s, E, A))) return rc;
+        if ((rc = first_sweep(s, 1.0, 0.0, A, true))) return rc;
+        double *slot = s->ring + (s->steps % tdks_system::RING) * TDKS_RECORD;
+        if ((rc = run_finalize(s, slot, t, E, A))) return rc;
+      }
+      field_at(s, tj, E, A);
+      // H[t]: v_x of the current state into slot 0
+      if ((rc = run_cfm_veff(s, xc, 1, w_new, E))) return rc;
+      if (xc) {
+        if ((rc = copy_state(s->etrs_save, s->etrs_save_lo, s->psi, s->psi_lo))) return rc;
+        if ((rc = exponential(ds))) return rc;  // the trial; its density now in dens_part
+        std::swap(s->vx_hist[0], s->vx_hist[1]);
+        // v_x of the trial into slot 0; V_eff stays H[t] (slot 1)
+        if ((rc = run_cfm_veff(s, true, 2, w_old, E))) return rc;
+        if ((rc = copy_state(s->psi, s->psi_lo, s->etrs_save, s->etrs_save_lo))) return rc;
+      }
+      if ((rc = exponential(0.5 * ds))) return rc;
+      field_at(s, tj + ds, E, A);
+      if ((rc = run_cfm_veff(s, false, 1, w_new, E))) return rc;  // H[t + ds]
+      if ((rc = exponential(0.5 * ds))) return rc;
       s->dens_valid = true;  // the last sweep wrote the density of the new state
     }
     s->steps++;
@@ -1254,8 +1319,8 @@ static int propagate_rk4(tdks_system *s, double t0, double dt, int n_steps, int 
 
 int tdks_set_propagator(tdks_sys s, int propagator) {
   if (!s) return fail(TDKS_EINVAL, "NULL system");
-  if (propagator < TDKS_PROP_TAYLOR4 || propagator > TDKS_PROP_RK4)
-    return fail(TDKS_EINVAL, "propagator must be TDKS_PROP_TAYLOR4, _CFM4, _EMR, _AETRS or _RK4");
+  if (propagator < TDKS_PROP_TAYLOR4 || propagator > TDKS_PROP_ETRS)
+    return fail(TDKS_EINVAL, "propagator must be TDKS_PROP_TAYLOR4, _CFM4, _EMR, _AETRS, _RK4 or _ETRS");
   if (propagator != TDKS_PROP_TAYLOR4 && s->xfn)
     return fail(TDKS_EINVAL, "state-parallel propagation (tdks_set_exchange) is Taylor-4 only");
   if (propagator == TDKS_PROP_RK4 && s->prec != TDKS_C128)
@@ -1265,6 +1330,10 @@ int tdks_set_propagator(tdks_sys s, int propagator) {
   CU(cudaStreamSynchronize(s->stream));
   if (propagator != TDKS_PROP_TAYLOR4 && propagator != TDKS_PROP_RK4 && !s->vx_hist[0])
     for (int j = 0; j < 4; j++) CU(cudaMalloc((void **)&s->vx_hist[j], (size_t)s->N * sizeof(double)));
+  if (propagator == TDKS_PROP_ETRS && !s->etrs_save) {
+    CU(cudaMalloc(&s->etrs_save, s->state_bytes));
+    if (s->psi_lo) CU(cudaMalloc(&s->etrs_save_lo, s->state_bytes));
+  }
   s->prop = propagator;
   s->n_hist = 0;
   return TDKS_OK;
@@ -1313,6 +1382,7 @@ int tdks_propagate_n(tdks_sys s, double t0, double dt, int n_steps, int substeps
 
 static int propagate_steps(tdks_system *s, double t0, double dt, int n_steps, int substeps) {
   if (s->prop == TDKS_PROP_RK4) return propagate_rk4(s, t0, dt, n_steps, substeps);
+  if (s->prop == TDKS_PROP_ETRS) return propagate_etrs(s, t0, dt, n_steps, substeps);
   if (s->prop != TDKS_PROP_TAYLOR4) return propagate_exp(s, t0, dt, n_steps, substeps);
   const double dts = dt / substeps;
   if (std::fabs(dts) * kinetic_max(s) > 2.0 * std::sqrt(2.0))

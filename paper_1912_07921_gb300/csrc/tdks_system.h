@@ -85,6 +85,7 @@ struct tdks_system {
   // propagator (tdks_set_propagator); CFM4 keeps v_x of the last four sub-step starts
   int prop = TDKS_PROP_TAYLOR4;
   double *vx_hist[4] = {nullptr, nullptr, nullptr, nullptr};  // [0] the newest
+  void *etrs_save = nullptr, *etrs_save_lo = nullptr;         // ETRS: the state during the trial
   int n_hist = 0;
   // state-parallel runs (tdks_set_exchange): hook, its context, the summed density
   // (N doubles) and the record's 10 sums

@@ -184,7 +184,9 @@ class System:
 
     def set_propagator(self, propagator: int):
         """0: Taylor-4 (default); 1: CFM4 (two exponentials per sub-step); 2: exponential
-        midpoint rule; 3: approximate enforced time-reversal symmetry (two half exponentials)."""
+        midpoint rule; 3: approximate enforced time-reversal symmetry (two half exponentials);
+        4: classical Runge-Kutta 4 (complex128); 5: enforced time-reversal symmetry with its
+        trial state (three exponentials per sub-step)."""
         _lib.check(self.lib.tdks_set_propagator(self.h, propagator))
 
     def set_exchange(self, fn):

@@ -54,9 +54,10 @@ def test_resume_is_bit_identical_molecule(prec, tmp_path):
     _resume_case(spec, I.make_inputs(spec), tmp_path)
 
 
-@pytest.mark.parametrize("prop", [1, 2, 3])
+@pytest.mark.parametrize("prop", [1, 2, 3, 5])
 def test_resume_keeps_the_exchange_history(prop, tmp_path):
-    """CFM4, EMR and AETRS extrapolate v_x from the last sub-steps: the history is saved."""
+    """CFM4, EMR and AETRS extrapolate v_x from the last sub-steps: the history is saved.
+    (ETRS keeps none across sub-steps; it resumes as well.)"""
     spec = ragged_molecule(I.PREC_C64)
     _resume_case(spec, I.make_inputs(spec), tmp_path, prop=prop, n1=2, n2=3, subs=2)
 

@@ -335,6 +335,31 @@ def test_emr_and_aetrs_match_oracle(prop, case):
     assert _rec_err(rec, rec_o) < tol
 
 
+@pytest.mark.parametrize("case", ["tiny_c128", "ragged_c128", "tiny_c64", "ragged_c128_no_xc"])
+def test_etrs_matches_oracle(case):
+    """ETRS with its trial state (three Taylor-4 exponentials per sub-step, v_x at t + dt from
+    the trial's density) on the GPU against the oracle's; without exchange it is the AETRS step."""
+    if case.startswith("ragged"):
+        spec = ragged_molecule(I.PREC_C128)
+        n_steps, subs, dt = 4, 2, 0.03
+    else:
+        spec = I.tiny_molecule(prec=I.PREC_C128 if case == "tiny_c128" else I.PREC_C64)
+        n_steps, subs, dt = 12, 1, spec.dt
+    if case.endswith("no_xc"):
+        spec = dataclasses.replace(spec, xc=I.XC_NONE)
+    inp = I.make_inputs(spec)
+    sysm = _system(spec, inp)
+    sysm.set_propagator(5)
+    sysm.propagate(0.0, dt, n_steps, subs)
+    psi, rec = sysm.get_orbitals(), sysm.reductions(0, n_steps)
+    sysm.close()
+    o = oracle.System(spec, inp)
+    psi_o, rec_o = o.propagate_etrs(inp.psi0, 0.0, dt, n_steps, subs)
+    tol = 1e-12 if spec.prec == I.PREC_C128 else 2e-5
+    assert rel_err(psi, psi_o) < tol
+    assert _rec_err(rec, rec_o) < tol
+
+
 @pytest.mark.parametrize("case", ["ragged", "bloch"])
 def test_rk4_matches_oracle(case):
     """Classical RK4 on the GPU (density rebuilt at every stage, field at the stage times)
@@ -389,12 +414,12 @@ def test_cfm4_refuses_the_velocity_gauge_and_batches():
     from paper_1912_07921_gb300.system import Batch
     spec = bloch_cell(I.PREC_C64)
     sysm = _system(spec, bloch_inputs(spec))
-    for prop in (1, 2, 3):
+    for prop in (1, 2, 3, 5):
         sysm.set_propagator(prop)
         with pytest.raises(_lib.TdksError):
             sysm.propagate(0.0, 0.01, 1, 1)
     with pytest.raises(_lib.TdksError):
-        sysm.set_propagator(5)
+        sysm.set_propagator(6)
     sysm.close()
     spec = I.tiny_molecule(prec=I.PREC_C64)
     a = _system(spec, I.make_inputs(spec))
