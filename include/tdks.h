@@ -139,8 +139,9 @@ int tdks_set_field(tdks_sys sys, int gauge, const double pol[3], double amp, dou
  * v_H(r_i) = h^3 sum_j n_j / |r_i - r_j| with a cell's own term n_i h^2 c0,
  * c0 = 3 ln(2 + sqrt 3) - pi/2, computed exactly by a zero-padded FFT; periodic cell,
  * v_H(G) = 4 pi n(G) / |G|^2 on the grid's plane waves (G = 0 dropped, neutralising
- * background).  The record's energy then adds E_H = 1/2 int n v_H.  Taylor-4 only (TDKS_EINVAL
- * with another propagator and from tdks_batch_create); grid edges with prime factors <= 13
+ * background).  The record's energy then adds E_H = 1/2 int n v_H.  Every propagator takes v_H
+ * with v_x (CFM4, EMR and AETRS extrapolate their sum, ETRS takes both from the trial's density,
+ * RK4 rebuilds both at every stage); TDKS_EINVAL from tdks_batch_create; grid edges with prime factors <= 13
  * (periodic cells) and transforms of at most 1024 points per axis (TDKS_EINVAL otherwise).
  * Allocates the transform workspace (two complex arrays of the padded grid) once. */
 int tdks_set_xc(tdks_sys sys, int xc, double occupation);

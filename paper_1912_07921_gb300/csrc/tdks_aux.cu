@@ -690,7 +690,7 @@ template <typename R>
 __global__ void __launch_bounds__(LDA_THREADS)
 cfm_veff_kernel(long N, int nx, int ny, int nz, double h, int bloch, int n_kb, int n_batches, const double *wocc,
                 const double *dens_part, const double *vloc, int xc, int push, CfmHist hist, double Ex, double Ey,
-                double Ez, PointAux *aux) {
+                double Ez, PointAux *aux, const double *vh) {
   constexpr bool F32 = sizeof(R) == 4;
   const int n_k = n_kb / n_batches;
   __shared__ float2 s_w[LDA_MAXK];
@@ -731,6 +731,7 @@ cfm_veff_kernel(long N, int nx, int ny, int nz, double h, int bloch, int n_kb, i
         for (int kb = 0; kb < n_kb; kb++) n += dens_part[(long)kb * N + p];
         vx = -cbrt(3.0 * n * 0.31830988618379067154);
       }
+      if (vh) vx += vh[p];  // the Hartree potential of the same density
       hist.v[0][p] = vx;
     }
     const int ix = (int)(p % nx), iy = (int)((p / nx) % ny), iz = (int)(p / ((long)nx * ny));
@@ -743,14 +744,15 @@ cfm_veff_kernel(long N, int nx, int ny, int nz, double h, int bloch, int n_kb, i
 
 cudaError_t launch_cfm_veff(int prec, int bloch, long N, int nx, int ny, int nz, double h, int n_kb, int n_batches,
                             const double *wocc, const double *dens_part, const double *vloc, int xc, int push,
-                            const CfmHist &hist, const double E[3], PointAux *aux, cudaStream_t s) {
+                            const CfmHist &hist, const double E[3], PointAux *aux, cudaStream_t s,
+                            const double *vh) {
   const int blocks = lda_blocks(N);
   if (prec == P_C64)
     cfm_veff_kernel<float><<<blocks, LDA_THREADS, 0, s>>>(N, nx, ny, nz, h, bloch, n_kb, n_batches, wocc, dens_part,
-                                                          vloc, xc, push, hist, E[0], E[1], E[2], aux);
+                                                          vloc, xc, push, hist, E[0], E[1], E[2], aux, vh);
   else
     cfm_veff_kernel<double><<<blocks, LDA_THREADS, 0, s>>>(N, nx, ny, nz, h, bloch, n_kb, n_batches, wocc, dens_part,
-                                                           vloc, xc, push, hist, E[0], E[1], E[2], aux);
+                                                           vloc, xc, push, hist, E[0], E[1], E[2], aux, vh);
   return cudaGetLastError();
 }
 

@@ -834,11 +834,8 @@ int tdks_set_xc(tdks_sys s, int xc, double occupation) {
   if (!s) return fail(TDKS_EINVAL, "NULL system");
   if (xc != TDKS_XC_NONE && xc != TDKS_XC_LDA_X && xc != TDKS_XC_LDA_X_HARTREE) return fail(TDKS_EINVAL, "bad xc");
   if (!(occupation > 0.0)) return fail(TDKS_EINVAL, "occupation must be > 0");
-  if (xc == TDKS_XC_LDA_X_HARTREE) {
-    if (s->prop != TDKS_PROP_TAYLOR4)
-      return fail(TDKS_EINVAL, "the Hartree term is built for the Taylor-4 propagator only");
+  if (xc == TDKS_XC_LDA_X_HARTREE)
     if (int rc = hartree_setup(s)) return rc;
-  }
   s->xc = xc;
   s->occ = occupation;
   std::vector<double> wocc(s->n_k);
@@ -1106,16 +1103,24 @@ static int taylor_tail(tdks_system *s, double dts, const double A[3]) {
 // V_eff of one CFM4 exponential (push: first store v_x of the current density as the newest
 // history entry).
 static int run_cfm_veff(tdks_system *s, bool push, int nh, const double w[4], const double E[3]) {
+  const bool hartree = s->xc == TDKS_XC_LDA_X_HARTREE;
+  if (push && hartree) {  // v_H of the same density joins the pushed v_x
+    cudaError_t e = launch_density_sum(s->prec, s->N, s->n_kb, s->n_batches, s->d_wocc, s->dens_part, s->n_total,
+                                       s->stream);
+    s->launches++;
+    if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("density sum: ") + cudaGetErrorString(e));
+    if (int rc = hartree_solve(s)) return rc;
+  }
   CfmHist h{};
   for (int j = 0; j < 4; j++) h.v[j] = s->vx_hist[j];
-  h.nh = s->xc == TDKS_XC_LDA_X ? nh : 0;
+  h.nh = s->xc != TDKS_XC_NONE ? nh : 0;
   for (int j = 0; j < 4; j++) h.w[j] = j < h.nh ? w[j] : 0.0;
   const double El[3] = {s->gauge == TDKS_GAUGE_LENGTH ? E[0] : 0.0, s->gauge == TDKS_GAUGE_LENGTH ? E[1] : 0.0,
                         s->gauge == TDKS_GAUGE_LENGTH ? E[2] : 0.0};
   Timed tm(s, 2);
   cudaError_t e = launch_cfm_veff(s->prec, s->bc == TDKS_BC_BLOCH, s->N, s->nx, s->ny, s->nz, s->h, s->n_kb,
-                                  s->n_batches, s->d_wocc, s->dens_part, s->vloc, s->xc == TDKS_XC_LDA_X,
-                                  push ? 1 : 0, h, El, s->aux, s->stream);
+                                  s->n_batches, s->d_wocc, s->dens_part, s->vloc, s->xc != TDKS_XC_NONE,
+                                  push ? 1 : 0, h, El, s->aux, s->stream, hartree ? s->d_vh : nullptr);
   s->launches++;
   if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("cfm4 potential: ") + cudaGetErrorString(e));
   return TDKS_OK;
@@ -1137,7 +1142,7 @@ static int propagate_exp(tdks_system *s, double t0, double dt, int n_steps, int 
   int rc = ensure_density(s);
   if (rc) return rc;
   const double A0[3] = {0.0, 0.0, 0.0};
-  const bool xc = s->xc == TDKS_XC_LDA_X;
+  const bool xc = s->xc != TDKS_XC_NONE;  // a density-dependent potential (v_x, v_x + v_H)
   for (int st = 0; st < n_steps; st++) {
     const double t = t0 + st * dt;
     for (int j = 0; j < substeps; j++) {
@@ -1195,7 +1200,7 @@ static int propagate_etrs(tdks_system *s, double t0, double dt, int n_steps, int
   int rc = ensure_density(s);
   if (rc) return rc;
   const double A0[3] = {0.0, 0.0, 0.0};
-  const bool xc = s->xc == TDKS_XC_LDA_X;
+  const bool xc = s->xc != TDKS_XC_NONE;  // a density-dependent potential (v_x, v_x + v_H)
   const double w_new[4] = {1.0, 0.0, 0.0, 0.0}, w_old[4] = {0.0, 1.0, 0.0, 0.0};
   auto exponential = [&](double tau) -> int {
     int r;
@@ -1325,8 +1330,6 @@ int tdks_set_propagator(tdks_sys s, int propagator) {
     return fail(TDKS_EINVAL, "state-parallel propagation (tdks_set_exchange) is Taylor-4 only");
   if (propagator == TDKS_PROP_RK4 && s->prec != TDKS_C128)
     return fail(TDKS_EINVAL, "RK4 runs on complex128 systems");
-  if (propagator != TDKS_PROP_TAYLOR4 && s->xc == TDKS_XC_LDA_X_HARTREE)
-    return fail(TDKS_EINVAL, "the Hartree term is built for the Taylor-4 propagator only");
   CU(cudaStreamSynchronize(s->stream));
   if (propagator != TDKS_PROP_TAYLOR4 && propagator != TDKS_PROP_RK4 && !s->vx_hist[0])
     for (int j = 0; j < 4; j++) CU(cudaMalloc((void **)&s->vx_hist[j], (size_t)s->N * sizeof(double)));

@@ -1,7 +1,8 @@
 """The Hartree potential on the GPU (xc = TDKS_XC_LDA_X_HARTREE) against the oracle's exchange-
 plus-Hartree mode: the box's Coulomb cell sum computed by the library's own zero-padded FFTs,
 and the periodic cell's plane-wave Poisson solve, inside H applications, records (E_H in the
-energy) and Taylor-4 propagations.  complex128 to 1e-12, complex64 to the FP32 tolerances."""
+energy) and propagations with every propagator.  complex128 to 1e-12, complex64 to the FP32
+tolerances."""
 import dataclasses
 
 import numpy as np
@@ -74,14 +75,35 @@ def test_propagation_with_hartree_matches_oracle(kind, prec):
     assert abs(no_h[2] - rec_o[0, 2]) > 1e3 * tol * abs(rec_o[0, 2])
 
 
-def test_hartree_refuses_other_propagators_and_batches():
+@pytest.mark.parametrize("prop,name", [(1, "cfm4"), (2, "emr"), (3, "aetrs"), (5, "etrs"), (4, "rk4")])
+@pytest.mark.parametrize("prec", [I.PREC_C128, I.PREC_C64])
+def test_other_propagators_with_hartree_match_oracle(prop, name, prec):
+    """v_x + v_H together: pushed into the extrapolation history (CFM4, EMR, AETRS), taken from
+    the trial's density (ETRS), or rebuilt at every stage (RK4, complex128 only)."""
+    if prop == 4 and prec != I.PREC_C128:
+        pytest.skip("RK4 runs on complex128 systems")
+    spec, inp = _case("box", prec)
+    s = _system(spec, inp)
+    s.set_propagator(prop)
+    n, dt, subs = 4, 0.02, 2
+    s.propagate(0.0, dt, n, subs)
+    rec = s.reductions(0, n)
+    psi = s.get_orbitals()
+    s.close()
+    psi_o, rec_o = getattr(oracle.System(spec, inp), "propagate_" + name)(inp.psi0, 0.0, dt, n, subs)
+    tol = 1e-12 if prec == I.PREC_C128 else 2e-5
+    assert rel_err(psi, psi_o) < tol
+    for c in range(1, 8):
+        scale = np.abs(rec_o[:, c]).max()
+        if scale > 0:
+            assert np.abs(rec[:, c] - rec_o[:, c]).max() <= tol * scale, c
+
+
+def test_hartree_refuses_batches():
     from paper_1912_07921_gb300._lib import TdksError
     from paper_1912_07921_gb300.system import Batch
     spec, inp = _case("box", I.PREC_C128)
     s = _system(spec, inp)
-    with pytest.raises(TdksError) as e:
-        s.set_propagator(1)
-    assert e.value.code == 1
     s.set_clock(0.0, spec.dt, 1)
     with pytest.raises(TdksError) as e:
         Batch([s], stream=torch.cuda.current_stream().cuda_stream)

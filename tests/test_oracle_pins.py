@@ -891,6 +891,15 @@ def test_rk4_and_cfm4_with_hartree_keep_their_order():
         assert a / b > 6.0, ec
 
 
+@pytest.mark.parametrize("name", ["emr", "aetrs", "etrs"])
+def test_two_point_propagators_with_hartree_stay_second_order(name):
+    """Exchange and Hartree: EMR and AETRS (v_x + v_H extrapolated from the history) and ETRS
+    (v_x + v_H of the trial's density) stay order two (error ratio ~4 per halving)."""
+    spec, inp, o = _cfm_case(2)
+    for r in _orders(o, inp, getattr(o, "propagate_" + name), 0.64, (16, 32, 64)):
+        assert 3.4 < r < 4.8, (name, r)
+
+
 # Current of a periodic cell with the projectors' commutator (Sec. "Conductivities": the
 # velocity operator i[H, r] includes i[V_NL, r]); the record carries both parts.
 def test_current_is_minus_the_energy_derivative_in_a():
