@@ -554,10 +554,17 @@ def run_periodic_side(args):
     # algorithmic bytes per sweep launch: 104 B per value per sub-step (as the medium molecule's
     # complex64 path) over four sweeps, plus the 16-byte point records per orbital block
     per_launch = (spec.n_points * states * 104 + spec.n_points * 16 * 4 * (states // 8)) / 4
+    sweep_gbs = per_launch / ((sweep_ms / 1e3) / max(sweep_n, 1)) / 1e9
+    peak, peak_kind = _peaks()
     return {"workload": f"periodic cell 64^3 L=10.2 order-4 FD, {spec.n_k} k x 16 bands c64, 8 atoms x 4 KB, "
                         "velocity gauge A0=0.2, dt=0.04 as 6 Taylor-4 sub-steps",
             "value": spec.n_points * states * k / (ms / 1e3), "unit": UNIT, "steps": k, "ms_per_step": ms / k,
-            "sweep_gbs": per_launch / ((sweep_ms / 1e3) / max(sweep_n, 1)) / 1e9, "sweep_shapes": shapes,
+            "sweep_gbs": sweep_gbs, "sweep_shapes": shapes,
+            "roofline": {"bound": "hbm", "achieved": sweep_gbs, "peak": peak, "unit": "GB/s",
+                         "frac": sweep_gbs / peak, "frac_of_nominal_7900": sweep_gbs / 7900.0,
+                         "peak_kind": peak_kind, "traffic": None,
+                         "bytes_per_launch": per_launch, "launches": sweep_n,
+                         "avg_launch_us": 1e3 * sweep_ms / max(sweep_n, 1)},
             "autotune_ms_per_launch": None if tune is None else [[round(float(x), 4) for x in r] for r in tune]}
 
 

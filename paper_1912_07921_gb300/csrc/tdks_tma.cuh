@@ -61,6 +61,16 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
+// 16-byte asynchronous global -> shared copy (L2 only), and an arrive on an mbarrier that
+// fires once every cp.async this thread has issued so far has landed (the barrier's pending
+// count is raised by one at issue, so its expected count stays as initialised).
+__device__ __forceinline__ void cp_async_16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_arrive(uint64_t *bar) {
+  asm volatile("cp.async.mbarrier.arrive.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 // Consumer wait: bounded, and gives up at once when another warp has given up.  (Reading
 // the abort flag only every 16 polls, or taking the bound from shared memory, measured 1-3%
 // slower sweeps: the flag's load paces the polling.)
@@ -126,8 +136,11 @@ struct RingPos {
 // ahead of the plane being computed.
 //   periodic cells (BL): each halo slot also holds the four periodic-image strips a boundary
 //     tile needs (the M columns beyond each x face over the slot's SY rows, the M rows beyond
-//     each y face over the tile's TX columns), loaded by TMA from the opposite faces.
-template <int M, int TX, int TY, int U, bool OPS, bool BL = false>
+//     each y face over the tile's TX columns), loaded by TMA from the opposite faces, and (first
+//     Taylor term) the non-local rows of the plane's sphere points (one per point, in tile
+//     order), which the patcher warp copies in with cp.async so that no consumer waits on a
+//     global load.
+template <int M, int TX, int TY, int U, bool OPS, bool BL = false, bool NLG = false>
 struct TmaGeom {
   static constexpr int SX = TX + 2 * M, SY = TY + 2 * M;
   static constexpr int PLANE = SX * SY * OVC;                        // vectors per halo plane
@@ -138,16 +151,23 @@ struct TmaGeom {
   static constexpr uint32_t STRIPX_BYTES = (uint32_t)M * SY * OVC * 16;   // beyond x = 0 or x = nx - 1
   static constexpr uint32_t STRIPY_BYTES = (uint32_t)TX * M * OVC * 16;   // beyond y = 0 or y = ny - 1
   static constexpr uint32_t STRIP_BYTES = BL ? 2 * (STRIPX_BYTES + STRIPY_BYTES) : 0;
-  static constexpr uint32_t HSLOT_BYTES = IN_BYTES + AUX_BYTES + STRIP_BYTES;
-  static_assert(!BL || U == 1, "periodic cells take one plane per iteration");
   static constexpr uint32_t OPT_BYTES = (uint32_t)CPLANE * 16;       // one operand tile
   static constexpr uint32_t OP_BYTES = 4 * OPT_BYTES;
   static constexpr int SO = OPS ? 2 : 0;
   // (the last term's 4 operand tiles leave taller tiles room for few centre slots)
   static constexpr int SC = U == 1 ? (OPS ? (TX * TY > 128 ? 2 : 4) : 6) : 4;
   static constexpr size_t BUDGET = 227 * 1024 - 2048;                // dynamic smem available
-  static constexpr int SH_FIT =
-      (int)((BUDGET - 128 - (size_t)SO * OP_BYTES - (size_t)SC * CSLOT_BYTES) / HSLOT_BYTES);
+  static constexpr size_t HALO_ROOM = BUDGET - 128 - (size_t)SO * OP_BYTES - (size_t)SC * CSLOT_BYTES;
+  // periodic cells, first Taylor term (NLG): the non-local rows of the plane's sphere points,
+  // gathered into the slot by the patcher warp, where two slots still fit (else the consumers
+  // load them).  (The larger slot leaves fewer halo slots: the faster middle and last sweeps
+  // measured slower with it, the first sweep, with its current gradients, faster.)
+  static constexpr uint32_t NL_STAGE = (uint32_t)TX * TY * OVC * 16;
+  static constexpr bool NLS = BL && NLG && HALO_ROOM / (IN_BYTES + AUX_BYTES + STRIP_BYTES + NL_STAGE) >= 2;
+  static constexpr uint32_t NL_BYTES = NLS ? NL_STAGE : 0;
+  static constexpr uint32_t HSLOT_BYTES = IN_BYTES + AUX_BYTES + STRIP_BYTES + NL_BYTES;
+  static_assert(!BL || U == 1, "periodic cells take one plane per iteration");
+  static constexpr int SH_FIT = (int)(HALO_ROOM / HSLOT_BYTES);
   static constexpr int SH = SH_FIT < 8 ? SH_FIT : 8;
   static constexpr size_t SMEM = (size_t)SC * CSLOT_BYTES + (size_t)SH * HSLOT_BYTES + (size_t)SO * OP_BYTES + 128;
   static_assert(SH >= 2, "halo ring too small");
@@ -472,7 +492,7 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
   typedef typename T::S S_;
   typedef typename T::R Rv;
   constexpr bool OPS = MODE == MODE_LAST;
-  typedef TmaGeom<M, TX, TY, U, OPS, BLOCH != 0> G;
+  typedef TmaGeom<M, TX, TY, U, OPS, BLOCH != 0, MODE == MODE_FIRST> G;
   static_assert(M % U == 0, "M must be a multiple of U");
   static_assert(!OPS || U == 1, "the last Taylor term takes one plane per iteration");
   constexpr int OV = T::OV;       // thread vectors per (point, batch)
@@ -664,6 +684,18 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
             box[(rr * G::SX + c + M) * OV + v] = apply_phase<P>(cy, sy, side == 0 ? -1 : 1, a);
           }
         }
+        if (G::NLS && p.has_proj) {
+          // the plane's non-local rows: row r0 of each sphere point (points outside every
+          // sphere are never read from here)
+          const PointAux *ax = reinterpret_cast<const PointAux *>(hbase + (size_t)hs * G::HSLOT_BYTES + G::IN_BYTES);
+          V *nla = box + (G::IN_BYTES + G::AUX_BYTES + G::STRIP_BYTES) / VB;
+          const V *nlk = reinterpret_cast<const V *>(p.nl) + (long)kb * (p.n_ent + 1) * OV;
+          for (int i = lane; i < TX * TY * OV; i += 32) {
+            const PointAux a = ax[i / OV];
+            if (a.r1 > a.r0) cp_async_16(nla + i, nlk + (long)a.r0 * OV + i % OV);
+          }
+          cp_async_arrive(&hready[hs]);
+        }
         __syncwarp();
         if (lane == 0) mbar_arrive(&hready[hs]);
         rp.next<SH>();
@@ -673,6 +705,7 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
         break;
       }
     }
+    cp_async_wait_all();  // no copy may land after the CTA's shared memory is gone
     return;
   }
 
@@ -811,7 +844,13 @@ __device__ __forceinline__ void ws_sweep_body(const Src &src, unsigned int *work
           for (int r = 0; r < R; r++) {
             const PointAux a = ax[u * TX * TY + tsl0 + r * TX];
             ve[r] = *reinterpret_cast<const Rv *>(&a.veff);
-            nlv[r] = has_proj ? nl_term<P>(nlk, n_ent, a.r0, a.r1) : T::zero();
+            if constexpr (G::NLS) {
+              // (gathered into the slot by the patcher warp)
+              const V *nla = reinterpret_cast<const V *>(hslot + G::IN_BYTES + G::AUX_BYTES + G::STRIP_BYTES);
+              nlv[r] = has_proj && a.r1 > a.r0 ? nla[(tsl0 + r * TX) * OV + v] : T::zero();
+            } else {
+              nlv[r] = has_proj ? nl_term<P>(nlk, n_ent, a.r0, a.r1) : T::zero();
+            }
           }
           V gax[BLOCH ? R : 1][3];
           if constexpr (BLOCH) {
@@ -892,7 +931,7 @@ ws_sweep_batch_kernel(const __grid_constant__ BatchSweepArgs a) {
 template <int SHAPE, int M, int P, int MODE, int BLOCH>
 static cudaError_t launch_ws_t(const SweepMaps &maps, const SweepParams &p, int grid, cudaStream_t s) {
   constexpr int TX = WsShape<SHAPE>::TX, TY = WsShape<SHAPE>::TY, R = WsShape<SHAPE>::R;
-  typedef TmaGeom<M, TX, TY, 1, MODE == MODE_LAST, BLOCH != 0> G;
+  typedef TmaGeom<M, TX, TY, 1, MODE == MODE_LAST, BLOCH != 0, MODE == MODE_FIRST> G;
   auto k = ws_sweep_kernel<M, P, MODE, TX, TY, R, 1, BLOCH>;
   static std::atomic<unsigned> attr_done{0};
   if (cudaError_t e = ensure_smem_attr(k, G::SMEM, attr_done)) return e;
