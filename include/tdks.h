@@ -239,10 +239,10 @@ int tdks_set_propagator(tdks_sys sys, int propagator);
  * record is then the whole system's.  fn returns 0 on success; any other value stops the
  * call with TDKS_EDEVICE.  fn runs on the calling thread, while earlier work may still run
  * on the stream.  Every rank holds the same k-points, grid, potentials, projectors and
- * field.  Taylor-4 only: TDKS_EINVAL from tdks_set_propagator with another propagator while
- * a hook is set, and from this call on a system with another propagator.  fn = NULL detaches
- * the hook.  ctx is passed through
- * untouched.
+ * field.  Every propagator: the density behind each potential it builds (the pushed v_x of
+ * CFM4, EMR and AETRS, the state's and the trial's in ETRS, each RK4 stage's) is exchanged
+ * first, so a sub-step calls fn once per such density.  fn = NULL detaches the hook.  ctx is
+ * passed through untouched.
  */
 typedef int (*tdks_exchange_fn)(double *dev_buf, long long n, void *stream, void *ctx);
 int tdks_set_exchange(tdks_sys sys, tdks_exchange_fn fn, void *ctx);

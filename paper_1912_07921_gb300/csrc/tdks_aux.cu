@@ -690,7 +690,7 @@ template <typename R>
 __global__ void __launch_bounds__(LDA_THREADS)
 cfm_veff_kernel(long N, int nx, int ny, int nz, double h, int bloch, int n_kb, int n_batches, const double *wocc,
                 const double *dens_part, const double *vloc, int xc, int push, CfmHist hist, double Ex, double Ey,
-                double Ez, PointAux *aux, const double *vh) {
+                double Ez, PointAux *aux, const double *vh, const double *n_in) {
   constexpr bool F32 = sizeof(R) == 4;
   const int n_k = n_kb / n_batches;
   __shared__ float2 s_w[LDA_MAXK];
@@ -705,7 +705,14 @@ cfm_veff_kernel(long N, int nx, int ny, int nz, double h, int bloch, int n_kb, i
   for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < N; p += (long)gridDim.x * blockDim.x) {
     if (push && xc) {
       double vx;
-      if constexpr (F32) {
+      if (n_in) {
+        // the density summed in FP64 (every rank's states, or the Hartree source)
+        if constexpr (F32) {
+          vx = (double)(-cbrtf(3.0f * (float)n_in[p] * 0.318309886f));
+        } else {
+          vx = -cbrt(3.0 * n_in[p] * 0.31830988618379067154);
+        }
+      } else if constexpr (F32) {
         const float2 *d2 = reinterpret_cast<const float2 *>(dens_part);
         float nh = 0.f, nl = 0.f;
         for (int k = 0; k < n_k; k++) {
@@ -745,14 +752,14 @@ cfm_veff_kernel(long N, int nx, int ny, int nz, double h, int bloch, int n_kb, i
 cudaError_t launch_cfm_veff(int prec, int bloch, long N, int nx, int ny, int nz, double h, int n_kb, int n_batches,
                             const double *wocc, const double *dens_part, const double *vloc, int xc, int push,
                             const CfmHist &hist, const double E[3], PointAux *aux, cudaStream_t s,
-                            const double *vh) {
+                            const double *vh, const double *n_in) {
   const int blocks = lda_blocks(N);
   if (prec == P_C64)
     cfm_veff_kernel<float><<<blocks, LDA_THREADS, 0, s>>>(N, nx, ny, nz, h, bloch, n_kb, n_batches, wocc, dens_part,
-                                                          vloc, xc, push, hist, E[0], E[1], E[2], aux, vh);
+                                                          vloc, xc, push, hist, E[0], E[1], E[2], aux, vh, n_in);
   else
     cfm_veff_kernel<double><<<blocks, LDA_THREADS, 0, s>>>(N, nx, ny, nz, h, bloch, n_kb, n_batches, wocc, dens_part,
-                                                           vloc, xc, push, hist, E[0], E[1], E[2], aux, vh);
+                                                           vloc, xc, push, hist, E[0], E[1], E[2], aux, vh, n_in);
   return cudaGetLastError();
 }
 

@@ -1104,12 +1104,19 @@ static int taylor_tail(tdks_system *s, double dts, const double A[3]) {
 // history entry).
 static int run_cfm_veff(tdks_system *s, bool push, int nh, const double w[4], const double E[3]) {
   const bool hartree = s->xc == TDKS_XC_LDA_X_HARTREE;
-  if (push && hartree) {  // v_H of the same density joins the pushed v_x
+  // the pushed potential from the density as one FP64 array: every rank's states
+  // (state-parallel propagation), and the source of v_H, which joins the pushed v_x
+  const bool total = push && s->xc != TDKS_XC_NONE && (s->xfn || hartree);
+  if (total) {
     cudaError_t e = launch_density_sum(s->prec, s->N, s->n_kb, s->n_batches, s->d_wocc, s->dens_part, s->n_total,
                                        s->stream);
     s->launches++;
     if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("density sum: ") + cudaGetErrorString(e));
-    if (int rc = hartree_solve(s)) return rc;
+    if (s->xfn)
+      if (int r = s->xfn(s->n_total, (long long)s->N, (void *)s->stream, s->xctx))
+        return fail(TDKS_EDEVICE, "exchange hook failed on the density (" + std::to_string(r) + ")");
+    if (hartree)
+      if (int rc = hartree_solve(s)) return rc;
   }
   CfmHist h{};
   for (int j = 0; j < 4; j++) h.v[j] = s->vx_hist[j];
@@ -1120,7 +1127,8 @@ static int run_cfm_veff(tdks_system *s, bool push, int nh, const double w[4], co
   Timed tm(s, 2);
   cudaError_t e = launch_cfm_veff(s->prec, s->bc == TDKS_BC_BLOCH, s->N, s->nx, s->ny, s->nz, s->h, s->n_kb,
                                   s->n_batches, s->d_wocc, s->dens_part, s->vloc, s->xc != TDKS_XC_NONE,
-                                  push ? 1 : 0, h, El, s->aux, s->stream, hartree ? s->d_vh : nullptr);
+                                  push ? 1 : 0, h, El, s->aux, s->stream, total && hartree ? s->d_vh : nullptr,
+                                  total ? s->n_total : nullptr);
   s->launches++;
   if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("cfm4 potential: ") + cudaGetErrorString(e));
   return TDKS_OK;
@@ -1326,8 +1334,6 @@ int tdks_set_propagator(tdks_sys s, int propagator) {
   if (!s) return fail(TDKS_EINVAL, "NULL system");
   if (propagator < TDKS_PROP_TAYLOR4 || propagator > TDKS_PROP_ETRS)
     return fail(TDKS_EINVAL, "propagator must be TDKS_PROP_TAYLOR4, _CFM4, _EMR, _AETRS, _RK4 or _ETRS");
-  if (propagator != TDKS_PROP_TAYLOR4 && s->xfn)
-    return fail(TDKS_EINVAL, "state-parallel propagation (tdks_set_exchange) is Taylor-4 only");
   if (propagator == TDKS_PROP_RK4 && s->prec != TDKS_C128)
     return fail(TDKS_EINVAL, "RK4 runs on complex128 systems");
   CU(cudaStreamSynchronize(s->stream));
@@ -1344,8 +1350,6 @@ int tdks_set_propagator(tdks_sys s, int propagator) {
 
 int tdks_set_exchange(tdks_sys s, tdks_exchange_fn fn, void *ctx) {
   if (!s) return fail(TDKS_EINVAL, "NULL system");
-  if (fn && s->prop != TDKS_PROP_TAYLOR4)
-    return fail(TDKS_EINVAL, "state-parallel propagation is Taylor-4 only");
   if (fn && !s->n_total) {
     CU(cudaMalloc((void **)&s->n_total, (size_t)s->N * sizeof(double)));
     CU(cudaMalloc((void **)&s->fin_sum, 10 * sizeof(double)));

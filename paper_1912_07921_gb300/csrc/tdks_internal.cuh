@@ -251,7 +251,7 @@ struct CfmHist {
 cudaError_t launch_cfm_veff(int prec, int bloch, long N, int nx, int ny, int nz, double h, int n_kb, int n_batches,
                             const double *wocc, const double *dens_part, const double *vloc, int xc, int push,
                             const CfmHist &hist, const double E[3], PointAux *aux, cudaStream_t s,
-                            const double *vh = nullptr);
+                            const double *vh = nullptr, const double *n_in = nullptr);
 cudaError_t launch_finalize(const double *obs_part, long n_items, const double *lda_part,
                             int n_lda_blocks, double *record, double t_state, double h3,
                             double occ, int bloch, double omega_cell, const double A[3],

@@ -6,9 +6,10 @@ given H, every orbital advances alone.  The paper's multi-GPU runs distribute th
 only and keep the grid whole on every GPU (Sec. "GPUs"), because a distributed grid needs
 far more frequent communication.  Here each rank holds a contiguous slice of the orbitals
 (``state_slice``) in its own library system, and the library calls an exchange hook
-(``tdks_set_exchange``) where the whole system's density is needed: once per Taylor
-sub-step with this rank's density (N doubles), and once per observable record with this
-rank's band energy and current sums (4 doubles).  ``allreduce_exchange`` is that hook over
+(``tdks_set_exchange``) where the whole system's density is needed: once per density a
+sub-step builds a potential from (one per Taylor-4 sub-step; two for ETRS; four for RK4)
+with this rank's density (N doubles), and once per observable record with this rank's band
+energy and current sums (4 doubles).  ``allreduce_exchange`` is that hook over
 ``torch.distributed`` (NCCL on GPUs), enqueued on the library's own CUDA stream.
 """
 from __future__ import annotations

@@ -70,7 +70,7 @@ def _rec_err(rec, rec_o):
                for c in range(rec.shape[1]) if np.max(np.abs(rec_o[:, c])) > 0)
 
 
-def _run_sharded(spec, inp, world, steps, substeps, block):
+def _run_sharded(spec, inp, world, steps, substeps, block, prop=0):
     from paper_1912_07921_gb300.sharding import state_slice
     from paper_1912_07921_gb300.system import System
 
@@ -82,6 +82,7 @@ def _run_sharded(spec, inp, world, steps, substeps, block):
         s = System(dataclasses.replace(spec, n_orb=hi - lo), inp, stream=st.cuda_stream,
                    orbitals=inp.psi0[..., lo:hi])
         s.set_exchange(grp.hook(r))
+        s.set_propagator(prop)
         systems.append(s)
         slices.append((lo, hi))
         streams.append(st)
@@ -162,6 +163,34 @@ def test_two_thread_ranks_periodic_cell_currents():
     assert rel_err(psi_sh, ref_psi) < 1e-12
 
 
+@pytest.mark.parametrize("prop,name,per_sub", [(1, "cfm4", 1), (2, "emr", 1), (3, "aetrs", 1), (5, "etrs", 2),
+                                               (4, "rk4", 4)])
+def test_two_thread_ranks_with_every_propagator(prop, name, per_sub):
+    """Every propagator state-parallel: the density each one builds its potential from (the
+    pushed v_x of CFM4, EMR and AETRS, ETRS's state and trial, every RK4 stage) is summed over
+    the ranks first.  complex128 against one system and the oracle."""
+    from paper_1912_07921_gb300.system import System
+
+    spec = ragged_molecule(I.PREC_C128, n_orb=7)
+    inp = I.make_inputs(spec)
+    steps, substeps = 2, 2
+    psi_sh, recs, calls = _run_sharded(spec, inp, 2, steps, substeps, 4, prop=prop)
+    # per sub-step: the densities of its potentials; per step: the record's density and sums
+    assert calls == [steps * (per_sub * substeps + 2)] * 2
+    whole = System(spec, inp, stream=torch.cuda.current_stream().cuda_stream)
+    whole.set_propagator(prop)
+    whole.propagate(0.0, spec.dt, steps, substeps)
+    psi_w, rec_w = whole.get_orbitals(), whole.reductions(0, steps)
+    whole.close()
+    ref_psi, ref_rec = getattr(oracle.System(spec, inp), "propagate_" + name)(inp.psi0, 0.0, spec.dt, steps,
+                                                                                substeps)
+    for rec in recs:
+        assert _rec_err(rec, rec_w) < 1e-12
+        assert _rec_err(rec, ref_rec) < 1e-12
+    assert rel_err(psi_sh, psi_w) < 1e-12
+    assert rel_err(psi_sh, ref_psi) < 1e-12
+
+
 def _free_port():
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
@@ -203,10 +232,6 @@ def test_exchange_hook_refusals_and_errors():
     spec = ragged_molecule(I.PREC_C128, n_orb=3)
     inp = I.make_inputs(spec)
     s = System(spec, inp, stream=torch.cuda.current_stream().cuda_stream)
-    s.set_exchange(lambda ptr, n, stream: None)
-    with pytest.raises(_lib.TdksError):  # CFM4 is not state-parallel
-        s.set_propagator(1)
-
     def broken(ptr, n, stream):
         raise RuntimeError("peer lost")
 
@@ -215,5 +240,5 @@ def test_exchange_hook_refusals_and_errors():
         s.propagate(0.0, spec.dt, 1, 1)
     assert isinstance(ei.value.__cause__, RuntimeError)
     s.set_exchange(None)  # detached: a plain system again
-    s.set_propagator(1)
+    s.propagate(0.0, spec.dt, 1, 1)
     s.close()
