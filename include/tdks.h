@@ -99,9 +99,13 @@ int tdks_set_local_potential(tdks_sys sys, const double *v);
 /* Orbitals: host array in the host layout (2 * n_k * N * n_orb doubles), copied (the call
  * returns once the buffer has been read; pinned memory gives the fastest upload) and packed
  * on the device in chunks that overlap the copy, together with the density of the new
- * state.  The packing is asynchronous on the system's stream and replaces the state after
- * all work enqueued there before the call; the copy itself waits only for the previous
- * upload's packing, so an upload issued while a propagation runs overlaps it. */
+ * state.  The new state replaces the old one for all work enqueued on the system's stream
+ * after the call; work enqueued before it still sees the old state.  The copy waits only for
+ * the previous upload's packing, so an upload issued while a propagation runs overlaps it.
+ * The first upload packs in place on the system's stream (after the work enqueued there);
+ * later uploads of a system that is in no batch pack into a second state buffer (allocated
+ * at the second upload: one more state and density array) on a stream of their own, so that
+ * the packing overlaps that work too, and the system then switches buffers. */
 int tdks_set_orbitals(tdks_sys sys, const double *psi);
 
 /* Copy the current orbitals out into the host layout.  Synchronises. */

@@ -270,6 +270,7 @@ int tdks_batch_create(const tdks_sys *systems, int n, void *stream, tdks_batch_t
     delete b;
     return rc;
   }
+  for (tdks_system *s : b->sys) s->batch_refs++;  // (their buffers stay in place while batched)
   *out = b;
   return TDKS_OK;
 }
@@ -278,6 +279,7 @@ int tdks_batch_destroy(tdks_batch_t b) {
   if (!b) return TDKS_OK;
   cudaStreamSynchronize(b->stream);
   if (b->work) cudaStreamSynchronize(b->work);
+  for (tdks_system *s : b->sys) s->batch_refs--;
   batch_free(b);
   delete b;
   return TDKS_OK;

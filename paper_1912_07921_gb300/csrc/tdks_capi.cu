@@ -599,6 +599,11 @@ int tdks_destroy(tdks_sys s) {
   cudaFree(s->staging);
   tsurff_free(s);
   hartree_free(s);
+  if (s->pack_stream) cudaStreamSynchronize(s->pack_stream);
+  cudaFree(s->psi_b); cudaFree(s->psi_lo_b); cudaFree(s->dens_b);
+  if (s->pack_stream) cudaStreamDestroy(s->pack_stream);
+  if (s->ev_spare_free) cudaEventDestroy(s->ev_spare_free);
+  if (s->ev_packed) cudaEventDestroy(s->ev_packed);
   if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
   if (s->ev_staging_free) cudaEventDestroy(s->ev_staging_free);
   for (auto e : s->ev_chunk) cudaEventDestroy(e);
@@ -644,10 +649,27 @@ int tdks_set_orbitals(tdks_sys s, const double *psi) {
     CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     s->ev_chunk.push_back(e);
   }
+  // A repeated upload of a system in no batch packs into spare buffers on its own stream, so
+  // that the packing too overlaps the work enqueued before this call; the system then switches
+  // to them for the work enqueued after it.  (A first upload packs in place on the system's
+  // stream: a system that is uploaded once never holds the spares.)
+  const bool twin = s->uploads > 0 && s->batch_refs == 0;
+  if (twin && !s->psi_b) {
+    CU(cudaMalloc(&s->psi_b, s->state_bytes));
+    if (s->psi_lo) CU(cudaMalloc(&s->psi_lo_b, s->state_bytes));
+    CU(cudaMalloc((void **)&s->dens_b, (size_t)s->n_kb * s->N * sizeof(double)));
+    CU(cudaStreamCreateWithFlags(&s->pack_stream, cudaStreamNonBlocking));
+    CU(cudaEventCreateWithFlags(&s->ev_spare_free, cudaEventDisableTiming));
+    CU(cudaEventCreateWithFlags(&s->ev_packed, cudaEventDisableTiming));
+  }
+  cudaStream_t ps = twin ? s->pack_stream : s->stream;
+  void *dst = twin ? s->psi_b : s->psi, *dst_lo = twin ? s->psi_lo_b : s->psi_lo;
+  double *dst_dens = twin ? s->dens_b : s->dens_part;
+  // the spares are written only once the work that used them as the state is done
+  if (twin && s->spare_pending) CU(cudaStreamWaitEvent(ps, s->ev_spare_free, 0));
   // the copies overwrite the staging buffer only once the kernels that read it (the previous
   // upload's packing) are done; they do not wait for other work of the system, so an upload
-  // issued right after tdks_propagate_n overlaps that propagation (the packing, which writes
-  // the state, still runs after it on the system's stream)
+  // issued right after tdks_propagate_n overlaps that propagation
   if (s->staging_pending) CU(cudaStreamWaitEvent(s->copy_stream, s->ev_staging_free, 0));
   const long len = (s->N + per_k - 1) / per_k;
   int c = 0;
@@ -658,13 +680,26 @@ int tdks_set_orbitals(tdks_sys s, const double *psi) {
       CU(cudaMemcpyAsync(s->staging + off, psi + off, (size_t)npts * s->n_orb * 16, cudaMemcpyHostToDevice,
                          s->copy_stream));
       CU(cudaEventRecord(s->ev_chunk[c], s->copy_stream));
-      CU(cudaStreamWaitEvent(s->stream, s->ev_chunk[c], 0));
-      CU(launch_pack_in(s->prec, s->N, k, pt0, npts, s->n_orb, s->n_batches, s->staging, s->psi, s->psi_lo,
-                        s->d_wocc, s->dens_part, s->stream));
+      CU(cudaStreamWaitEvent(ps, s->ev_chunk[c], 0));
+      CU(launch_pack_in(s->prec, s->N, k, pt0, npts, s->n_orb, s->n_batches, s->staging, dst, dst_lo, s->d_wocc,
+                        dst_dens, ps));
       s->launches++;
     }
-  CU(cudaEventRecord(s->ev_staging_free, s->stream));
+  CU(cudaEventRecord(s->ev_staging_free, ps));
   s->staging_pending = true;
+  if (twin) {
+    // work enqueued from now on reads the new state once it is packed; the old state becomes
+    // the spare once the work enqueued so far is done
+    CU(cudaEventRecord(s->ev_packed, ps));
+    CU(cudaStreamWaitEvent(s->stream, s->ev_packed, 0));
+    std::swap(s->psi, s->psi_b);
+    std::swap(s->psi_lo, s->psi_lo_b);
+    std::swap(s->dens_part, s->dens_b);
+    CU(cudaEventRecord(s->ev_spare_free, s->stream));
+    s->spare_pending = true;
+    build_tmaps(s);
+  }
+  s->uploads++;
   // the host buffer has been read once the copies are done ("copied")
   CU(cudaStreamSynchronize(s->copy_stream));
   s->have_orbitals = true;
