@@ -102,11 +102,17 @@ int tdks_set_local_potential(tdks_sys sys, const double *v);
  * state.  The new state replaces the old one for all work enqueued on the system's stream
  * after the call; work enqueued before it still sees the old state.  The copy waits only for
  * the previous upload's packing, so an upload issued while a propagation runs overlaps it.
- * The first upload packs in place on the system's stream (after the work enqueued there);
- * later uploads of a system that is in no batch pack into a second state buffer (allocated
- * at the second upload: one more state and density array) on a stream of their own, so that
- * the packing overlaps that work too, and the system then switches buffers. */
+ * The packing runs on the system's stream, after the work enqueued there, unless the system
+ * has two upload buffers (tdks_set_upload_buffers). */
 int tdks_set_orbitals(tdks_sys sys, const double *psi);
+
+/* Upload buffers of a system: 1 (default), or 2 for a stream of uploads (one per step, say):
+ * each tdks_set_orbitals then packs the new state into a second state buffer (one more state
+ * and density array, allocated here) on a stream of its own, so that the packing overlaps
+ * the work enqueued before the call too, and the system switches buffers for the work
+ * enqueued after it.  A system with two buffers cannot join a batch (TDKS_EINVAL from
+ * tdks_batch_create).  n = 1 frees the second buffer.  Synchronises the system's stream. */
+int tdks_set_upload_buffers(tdks_sys sys, int n);
 
 /* Copy the current orbitals out into the host layout.  Synchronises. */
 int tdks_get_orbitals(tdks_sys sys, double *psi_out);

@@ -20,6 +20,7 @@ SIGNATURES = {
     "tdks_destroy": ([P], I),
     "tdks_set_local_potential": ([P, P], I),
     "tdks_set_orbitals": ([P, P], I),
+    "tdks_set_upload_buffers": ([P, I], I),
     "tdks_get_orbitals": ([P, P], I),
     "tdks_set_atoms_projectors": ([P, I, P, P, D, D], I),
     "tdks_set_field": ([P, I, P, D, D, I, D], I),

@@ -211,22 +211,12 @@ __global__ void __launch_bounds__(NL_THREADS) nl_kernel(const GatherParams p) {
   nl_body<P, BLOCH>(p, (long)blockIdx.x * NL_THREADS + threadIdx.x, blockIdx.y);
 }
 
-// index of the system that owns unit u: begin[s] <= u < begin[s+1]
-__device__ __forceinline__ int find_sys(const long *begin, int n, long u) {
-  int lo = 0, hi = n - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (begin[mid] <= u) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
 // Batched gather: stage 1 over every system's (atom, kb, chunk) CTAs, stage 2 over every
-// system's (atom, kb) units.
+// system's (atom, kb) units.  The system of a CTA (or unit) comes from a table.
 template <int P>
 __global__ void __launch_bounds__(GATHER_THREADS)
-gather_batch_kernel(const GatherParams *gp, const long *begin, int n_sys) {
-  const int s = find_sys(begin, n_sys, blockIdx.x);
+gather_batch_kernel(const GatherParams *gp, const long *begin, const int *sys_of) {
+  const int s = sys_of[blockIdx.x];
   const GatherParams &p = gp[s];
   const long u = blockIdx.x - begin[s];
   const long unit = u / p.n_chunks;
@@ -235,10 +225,10 @@ gather_batch_kernel(const GatherParams *gp, const long *begin, int n_sys) {
 
 template <int P>
 __global__ void __launch_bounds__(128)
-gather_finish_batch_kernel(const GatherParams *gp, const long *ubegin, int n_sys, long total_units) {
+gather_finish_batch_kernel(const GatherParams *gp, const long *ubegin, const int *sys_of, long total_units) {
   const long u = blockIdx.x * 8L + threadIdx.x / 16;
   if (u >= total_units) return;
-  const int s = find_sys(ubegin, n_sys, u);
+  const int s = sys_of[u];
   const GatherParams &p = gp[s];
   const long local = u - ubegin[s];
   gather_finish<P>(p, (int)(local % p.n_atoms), (int)(local / p.n_atoms), threadIdx.x % 16);
@@ -248,27 +238,31 @@ gather_finish_batch_kernel(const GatherParams *gp, const long *ubegin, int n_sys
 // it, kb = local / chunks, chunk = local % chunks.
 template <int P>
 __global__ void __launch_bounds__(NL_THREADS)
-nl_batch_kernel(const GatherParams *gp, const long *nbegin, int n_sys) {
-  const int s = find_sys(nbegin, n_sys, blockIdx.x);
+nl_batch_kernel(const GatherParams *gp, const long *nbegin, const int *sys_of) {
+  const int s = sys_of[blockIdx.x];
   const GatherParams &p = gp[s];
   const long local = blockIdx.x - nbegin[s];
-  const long chunks = ((long)p.n_sp * OVC + NL_THREADS - 1) / NL_THREADS;
-  nl_body<P, 0>(p, (local % chunks) * NL_THREADS + threadIdx.x, (int)(local / chunks));
+  constexpr long RUN = (long)NL_THREADS * NL_BATCH_RUNS;
+  const long chunks = ((long)p.n_sp * OVC + RUN - 1) / RUN;
+  const int kb = (int)(local / chunks);
+  const long t0 = (local % chunks) * RUN + threadIdx.x;
+#pragma unroll 2
+  for (int i = 0; i < NL_BATCH_RUNS; i++) nl_body<P, 0>(p, t0 + (long)i * NL_THREADS, kb);
 }
 
 cudaError_t launch_gather_batch(int prec, const GatherParams *gp, const long *begin, const long *ubegin,
-                                const long *nbegin, int n_sys, long total, long total_units, long total_nl,
-                                cudaStream_t s) {
+                                const long *nbegin, const int *gsys, const int *usys, const int *nsys,
+                                long total, long total_units, long total_nl, cudaStream_t s) {
   if (total <= 0) return cudaSuccess;
   const unsigned fgrid = (unsigned)((total_units + 7) / 8);
   if (prec == P_C64) {
-    gather_batch_kernel<P_C64><<<(unsigned)total, GATHER_THREADS, 0, s>>>(gp, begin, n_sys);
-    gather_finish_batch_kernel<P_C64><<<fgrid, 128, 0, s>>>(gp, ubegin, n_sys, total_units);
-    if (total_nl > 0) nl_batch_kernel<P_C64><<<(unsigned)total_nl, NL_THREADS, 0, s>>>(gp, nbegin, n_sys);
+    gather_batch_kernel<P_C64><<<(unsigned)total, GATHER_THREADS, 0, s>>>(gp, begin, gsys);
+    gather_finish_batch_kernel<P_C64><<<fgrid, 128, 0, s>>>(gp, ubegin, usys, total_units);
+    if (total_nl > 0) nl_batch_kernel<P_C64><<<(unsigned)total_nl, NL_THREADS, 0, s>>>(gp, nbegin, nsys);
   } else {
-    gather_batch_kernel<P_C128><<<(unsigned)total, GATHER_THREADS, 0, s>>>(gp, begin, n_sys);
-    gather_finish_batch_kernel<P_C128><<<fgrid, 128, 0, s>>>(gp, ubegin, n_sys, total_units);
-    if (total_nl > 0) nl_batch_kernel<P_C128><<<(unsigned)total_nl, NL_THREADS, 0, s>>>(gp, nbegin, n_sys);
+    gather_batch_kernel<P_C128><<<(unsigned)total, GATHER_THREADS, 0, s>>>(gp, begin, gsys);
+    gather_finish_batch_kernel<P_C128><<<fgrid, 128, 0, s>>>(gp, ubegin, usys, total_units);
+    if (total_nl > 0) nl_batch_kernel<P_C128><<<(unsigned)total_nl, NL_THREADS, 0, s>>>(gp, nbegin, nsys);
   }
   return cudaGetLastError();
 }
@@ -779,9 +773,9 @@ __device__ __forceinline__ double batch_field(const BatchAux &a, double t) {
 // system's current sub-step midpoint from its device clock.
 template <typename R>
 __global__ void __launch_bounds__(LDA_THREADS)
-lda_batch_kernel(const BatchAux *aux, const BatchClock *clk, const long *begin, int n_sys) {
+lda_batch_kernel(const BatchAux *aux, const BatchClock *clk, const long *begin, const int *sys_of) {
   __shared__ double f;
-  const int s = find_sys(begin, n_sys, blockIdx.x);
+  const int s = sys_of[blockIdx.x];
   const BatchAux &a = aux[s];
   if (threadIdx.x == 0) {
     const BatchClock c = clk[s];
@@ -794,10 +788,10 @@ lda_batch_kernel(const BatchAux *aux, const BatchClock *clk, const long *begin, 
               a.n_lda);
 }
 
-cudaError_t launch_lda_batch(int prec, const BatchAux *aux, const BatchClock *clk, const long *begin, int n_sys,
-                             long total, cudaStream_t s) {
-  if (prec == P_C64) lda_batch_kernel<float><<<(unsigned)total, LDA_THREADS, 0, s>>>(aux, clk, begin, n_sys);
-  else lda_batch_kernel<double><<<(unsigned)total, LDA_THREADS, 0, s>>>(aux, clk, begin, n_sys);
+cudaError_t launch_lda_batch(int prec, const BatchAux *aux, const BatchClock *clk, const long *begin,
+                             const int *lsys, long total, cudaStream_t s) {
+  if (prec == P_C64) lda_batch_kernel<float><<<(unsigned)total, LDA_THREADS, 0, s>>>(aux, clk, begin, lsys);
+  else lda_batch_kernel<double><<<(unsigned)total, LDA_THREADS, 0, s>>>(aux, clk, begin, lsys);
   return cudaGetLastError();
 }
 

@@ -27,8 +27,10 @@ struct tdks_batch {
   GatherParams *d_gather[4] = {nullptr, nullptr, nullptr, nullptr};
   SweepMaps *d_maps = nullptr;                                      // 4 per system
   long *d_item_begin[4] = {nullptr, nullptr, nullptr, nullptr};     // per Taylor term
+  int *d_item_sys[4] = {nullptr, nullptr, nullptr, nullptr};        // the system of every item
   long *d_gather_begin = nullptr, *d_unit_begin = nullptr, *d_lda_begin = nullptr;
   long *d_nl_begin = nullptr;
+  int *d_gather_sys = nullptr, *d_unit_sys = nullptr, *d_nl_sys = nullptr, *d_lda_sys = nullptr;
   unsigned int *d_work = nullptr;  // work-item counter of the batched sweep (zero between launches)
   BatchAux *d_aux = nullptr;
   std::vector<BatchAux> aux_h;     // host copy (the record count follows the first term's shape)
@@ -43,10 +45,13 @@ struct tdks_batch {
 namespace {
 
 void batch_free(tdks_batch *b) {
-  for (int k = 0; k < 4; k++) { cudaFree(b->d_sweep[k]); cudaFree(b->d_gather[k]); cudaFree(b->d_item_begin[k]); }
+  for (int k = 0; k < 4; k++) {
+    cudaFree(b->d_sweep[k]); cudaFree(b->d_gather[k]); cudaFree(b->d_item_begin[k]); cudaFree(b->d_item_sys[k]);
+  }
   cudaFree(b->d_maps); cudaFree(b->d_gather_begin); cudaFree(b->d_lda_begin);
   cudaFree(b->d_nl_begin); cudaFree(b->d_work);
   cudaFree(b->d_unit_begin);
+  cudaFree(b->d_gather_sys); cudaFree(b->d_unit_sys); cudaFree(b->d_nl_sys); cudaFree(b->d_lda_sys);
   cudaFree(b->d_aux); cudaFree(b->d_clock);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
@@ -72,13 +77,16 @@ long long substep_launches(const tdks_batch *b) {
 // Enqueue one sub-step of every system of the batch.
 int enqueue_substep(tdks_batch *b) {
   const int n = (int)b->sys.size();
-  cudaError_t e = launch_lda_batch(b->prec, b->d_aux, b->d_clock, b->d_lda_begin, n, b->total_lda, b->work);
+  cudaError_t e = launch_lda_batch(b->prec, b->d_aux, b->d_clock, b->d_lda_begin, b->d_lda_sys, b->total_lda,
+                                   b->work);
   if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("batched lda: ") + cudaGetErrorString(e));
   for (int k = 0; k < 4; k++) {
-    e = launch_gather_batch(b->prec, b->d_gather[k], b->d_gather_begin, b->d_unit_begin, b->d_nl_begin, n,
-                            b->total_gather, b->total_units, b->total_nl, b->work);
+    e = launch_gather_batch(b->prec, b->d_gather[k], b->d_gather_begin, b->d_unit_begin, b->d_nl_begin,
+                            b->d_gather_sys, b->d_unit_sys, b->d_nl_sys, b->total_gather, b->total_units,
+                            b->total_nl, b->work);
     if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("batched gather: ") + cudaGetErrorString(e));
-    BatchSweepArgs a{b->d_sweep[k], b->d_maps, k, b->d_item_begin[k], n, b->total_items[k], b->d_work};
+    BatchSweepArgs a{b->d_sweep[k], b->d_maps, k, b->d_item_begin[k],
+                      n, b->total_items[k], b->d_work, b->d_item_sys[k]};
     const int mode = k == 0 ? MODE_FIRST : (k == 3 ? MODE_LAST : MODE_MID);
     e = launch_sweep_tma_batch(b->M, b->prec, mode, a, b->work, b->shape[k]);
     if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("batched sweep: ") + cudaGetErrorString(e));
@@ -153,6 +161,7 @@ int build_sweep_tables(tdks_batch *b, bool tune) {
   for (int k = 0; k < 4; k++) {
     cudaFree(b->d_sweep[k]); b->d_sweep[k] = nullptr;
     cudaFree(b->d_item_begin[k]); b->d_item_begin[k] = nullptr;
+    cudaFree(b->d_item_sys[k]); b->d_item_sys[k] = nullptr;
   }
   cudaFree(b->d_maps); b->d_maps = nullptr;
   int rc = TDKS_OK;
@@ -160,6 +169,10 @@ int build_sweep_tables(tdks_batch *b, bool tune) {
     rc = upload(&b->d_sweep[k], sp[k]);
     if (!rc) rc = upload(&b->d_item_begin[k], ib[k]);
     b->total_items[k] = ib[k][n];
+    std::vector<int> owner((size_t)ib[k][n]);
+    for (int i = 0; i < n; i++)
+      for (long it = ib[k][i]; it < ib[k][i + 1]; it++) owner[(size_t)it] = i;
+    if (!rc) rc = upload(&b->d_item_sys[k], owner);
   }
   if (!rc) rc = upload(&b->d_maps, maps);
   if (!rc && b->d_aux) CU(cudaMemcpy(b->d_aux, b->aux_h.data(), n * sizeof(BatchAux), cudaMemcpyHostToDevice));
@@ -213,6 +226,7 @@ int tdks_batch_create(const tdks_sys *systems, int n, void *stream, tdks_batch_t
     if (s->prop != TDKS_PROP_TAYLOR4) return bad("batched propagation uses the Taylor-4 propagator");
     if (s->xfn) return bad("a state-parallel system (exchange hook set) cannot join a batch");
     if (s->xc == TDKS_XC_LDA_X_HARTREE) return bad("a system with the Hartree term cannot join a batch");
+    if (s->upload_buffers != 1) return bad("a system with two upload buffers cannot join a batch");
   }
   std::vector<GatherParams> gp[4];
   std::vector<long> gather_begin(n + 1, 0), unit_begin(n + 1, 0), lda_begin(n + 1, 0);
@@ -220,22 +234,30 @@ int tdks_batch_create(const tdks_sys *systems, int n, void *stream, tdks_batch_t
   std::vector<BatchAux> &aux = b->aux_h;
   aux.assign(n, BatchAux{});
   std::vector<BatchClock> clk(n);
+  // the projector gather's chunks per (atom, k-batch) unit are sized for the whole batch's
+  // units (a system alone splits each unit into up to 16 chunks to fill the GPU; a batch has
+  // the units to fill it without the per-chunk reductions); never more than the system's
+  // partial-sum buffer holds
+  long batch_units = 0;
+  for (tdks_system *s : b->sys) batch_units += (long)s->n_atoms * s->n_kb;
+  const int bchunks = gather_chunks(std::max(batch_units, 1L));
   for (int i = 0; i < n; i++) {
     tdks_system *s = b->sys[i];
     const void *ins[4] = {s->psi, s->term[0], s->term[1], s->term[2]};
+    const int nch = std::min(s->gchunks, bchunks);
     for (int k = 0; k < 4; k++) {
       GatherParams g{};
       g.n_kb = s->n_kb; g.n_batches = s->n_batches; g.n_atoms = s->n_atoms; g.N = s->N;
       g.in = ins[k]; g.atom_begin = s->d_atom_begin; g.ent = s->d_ent; g.D = s->d_D;
       g.ent_beta = s->d_ent_beta; g.ent_ca = s->d_ent_ca;
       g.h3 = s->h * s->h * s->h; g.kvec = s->d_kvec; g.q = s->d_q;
-      g.n_chunks = s->gchunks; g.qpart = s->d_qpart;
+      g.n_chunks = nch; g.qpart = s->d_qpart;
       g.sp = s->d_sp; g.n_sp = s->n_sp; g.rowent = s->d_rowent; g.n_ent = s->n_ent; g.nl = s->d_nl;
       gp[k].push_back(g);
     }
-    gather_begin[i + 1] = gather_begin[i] + (long)s->n_atoms * s->n_kb * (s->n_atoms > 0 ? s->gchunks : 0);
+    gather_begin[i + 1] = gather_begin[i] + (long)s->n_atoms * s->n_kb * (s->n_atoms > 0 ? nch : 0);
     unit_begin[i + 1] = unit_begin[i] + (long)s->n_atoms * s->n_kb;
-    nl_begin[i + 1] = nl_begin[i] + (s->n_atoms > 0 ? nl_blocks(s->n_sp, s->n_kb) : 0);
+    nl_begin[i + 1] = nl_begin[i] + (s->n_atoms > 0 ? nl_batch_blocks(s->n_sp, s->n_kb) : 0);
     const int nl = lda_batch_blocks(s->N);
     lda_begin[i + 1] = lda_begin[i] + nl;
     BatchAux &a = aux[i];
@@ -258,6 +280,17 @@ int tdks_batch_create(const tdks_sys *systems, int n, void *stream, tdks_batch_t
   if (!rc) rc = upload(&b->d_unit_begin, unit_begin);
   if (!rc) rc = upload(&b->d_lda_begin, lda_begin);
   if (!rc) rc = upload(&b->d_nl_begin, nl_begin);
+  // the system of every CTA (or unit) of the batched projector and LDA launches
+  auto owners = [&](const std::vector<long> &beg) {
+    std::vector<int> o((size_t)beg[n]);
+    for (int i = 0; i < n; i++)
+      for (long c = beg[i]; c < beg[i + 1]; c++) o[(size_t)c] = i;
+    return o;
+  };
+  if (!rc) rc = upload(&b->d_gather_sys, owners(gather_begin));
+  if (!rc) rc = upload(&b->d_unit_sys, owners(unit_begin));
+  if (!rc) rc = upload(&b->d_nl_sys, owners(nl_begin));
+  if (!rc) rc = upload(&b->d_lda_sys, owners(lda_begin));
   if (!rc) rc = upload(&b->d_work, std::vector<unsigned int>(1, 0u));
   if (!rc) rc = upload(&b->d_aux, aux);
   if (!rc) rc = upload(&b->d_clock, clk);
@@ -270,7 +303,6 @@ int tdks_batch_create(const tdks_sys *systems, int n, void *stream, tdks_batch_t
     delete b;
     return rc;
   }
-  for (tdks_system *s : b->sys) s->batch_refs++;  // (their buffers stay in place while batched)
   *out = b;
   return TDKS_OK;
 }
@@ -279,7 +311,6 @@ int tdks_batch_destroy(tdks_batch_t b) {
   if (!b) return TDKS_OK;
   cudaStreamSynchronize(b->stream);
   if (b->work) cudaStreamSynchronize(b->work);
-  for (tdks_system *s : b->sys) s->batch_refs--;
   batch_free(b);
   delete b;
   return TDKS_OK;
@@ -373,7 +404,8 @@ int tdks_batch_autotune(tdks_batch_t b, int reps, double *ms) {
     for (int k = 0; k < 4; k++) b->shape[k] = sh;
     if ((rc = build_sweep_tables(b, true))) break;
     for (int k = 0; k < 4 && !rc; k++) {
-      BatchSweepArgs a{b->d_sweep[k], b->d_maps, k, b->d_item_begin[k], n, b->total_items[k], b->d_work};
+      BatchSweepArgs a{b->d_sweep[k], b->d_maps, k, b->d_item_begin[k],
+                      n, b->total_items[k], b->d_work, b->d_item_sys[k]};
       cudaError_t e = launch_sweep_tma_batch(b->M, b->prec, modes[k], a, b->work, sh);  // warm-up
       cudaEventRecord(e0, b->work);
       for (int r = 0; r < reps && e == cudaSuccess; r++)

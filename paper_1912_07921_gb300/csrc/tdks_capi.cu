@@ -649,19 +649,10 @@ int tdks_set_orbitals(tdks_sys s, const double *psi) {
     CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     s->ev_chunk.push_back(e);
   }
-  // A repeated upload of a system in no batch packs into spare buffers on its own stream, so
-  // that the packing too overlaps the work enqueued before this call; the system then switches
-  // to them for the work enqueued after it.  (A first upload packs in place on the system's
-  // stream: a system that is uploaded once never holds the spares.)
-  const bool twin = s->uploads > 0 && s->batch_refs == 0;
-  if (twin && !s->psi_b) {
-    CU(cudaMalloc(&s->psi_b, s->state_bytes));
-    if (s->psi_lo) CU(cudaMalloc(&s->psi_lo_b, s->state_bytes));
-    CU(cudaMalloc((void **)&s->dens_b, (size_t)s->n_kb * s->N * sizeof(double)));
-    CU(cudaStreamCreateWithFlags(&s->pack_stream, cudaStreamNonBlocking));
-    CU(cudaEventCreateWithFlags(&s->ev_spare_free, cudaEventDisableTiming));
-    CU(cudaEventCreateWithFlags(&s->ev_packed, cudaEventDisableTiming));
-  }
+  // With two upload buffers the upload packs into the spares on their own stream, so that the
+  // packing too overlaps the work enqueued before this call; the system then switches to them
+  // for the work enqueued after it.  With one, it packs in place on the system's stream.
+  const bool twin = s->upload_buffers == 2;
   cudaStream_t ps = twin ? s->pack_stream : s->stream;
   void *dst = twin ? s->psi_b : s->psi, *dst_lo = twin ? s->psi_lo_b : s->psi_lo;
   double *dst_dens = twin ? s->dens_b : s->dens_part;
@@ -699,12 +690,36 @@ int tdks_set_orbitals(tdks_sys s, const double *psi) {
     s->spare_pending = true;
     build_tmaps(s);
   }
-  s->uploads++;
   // the host buffer has been read once the copies are done ("copied")
   CU(cudaStreamSynchronize(s->copy_stream));
   s->have_orbitals = true;
   s->dens_valid = true;
   s->n_hist = 0;  // a new state starts a new CFM4 exchange history
+  return TDKS_OK;
+}
+
+int tdks_set_upload_buffers(tdks_sys s, int n) {
+  if (!s) return fail(TDKS_EINVAL, "NULL system");
+  if (n != 1 && n != 2) return fail(TDKS_EINVAL, "upload buffers must be 1 or 2");
+  if (n == s->upload_buffers) return TDKS_OK;
+  CU(cudaStreamSynchronize(s->stream));
+  if (s->pack_stream) CU(cudaStreamSynchronize(s->pack_stream));
+  if (n == 2) {
+    CU(cudaMalloc(&s->psi_b, s->state_bytes));
+    if (s->psi_lo) CU(cudaMalloc(&s->psi_lo_b, s->state_bytes));
+    CU(cudaMalloc((void **)&s->dens_b, (size_t)s->n_kb * s->N * sizeof(double)));
+    if (!s->pack_stream) {
+      CU(cudaStreamCreateWithFlags(&s->pack_stream, cudaStreamNonBlocking));
+      CU(cudaEventCreateWithFlags(&s->ev_spare_free, cudaEventDisableTiming));
+      CU(cudaEventCreateWithFlags(&s->ev_packed, cudaEventDisableTiming));
+    }
+  } else {
+    cudaFree(s->psi_b); cudaFree(s->psi_lo_b); cudaFree(s->dens_b);
+    s->psi_b = s->psi_lo_b = nullptr;
+    s->dens_b = nullptr;
+  }
+  s->spare_pending = false;
+  s->upload_buffers = n;
   return TDKS_OK;
 }
 

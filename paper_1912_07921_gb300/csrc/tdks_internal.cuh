@@ -208,6 +208,7 @@ struct BatchSweepArgs {
   int n_sys;
   long total_items;
   unsigned int *work;     // work-item counter (zero between launches)
+  const int *item_sys;    // the system of every work item
 };
 
 
@@ -292,14 +293,21 @@ int lda_blocks(long N);
 cudaError_t launch_sweep_tma_batch(int M, int prec, int mode, const BatchSweepArgs &a, cudaStream_t s,
                                    int shape = 0);
 // begin: prefix sums of n_atoms * n_kb * n_chunks (stage 1 CTAs); ubegin: of n_atoms * n_kb;
-// nbegin: of the non-local kernel's CTAs, n_kb * ceil(n_sp * OVC / NL_THREADS)
+// nbegin: of the non-local kernel's CTAs, n_kb * ceil(n_sp * OVC / NL_THREADS).  gsys, usys,
+// nsys: the system of each stage-1 CTA, unit and non-local CTA (one table load instead of a
+// binary search over the prefix sums in every CTA).
 cudaError_t launch_gather_batch(int prec, const GatherParams *gp, const long *begin, const long *ubegin,
-                                const long *nbegin, int n_sys, long total, long total_units, long total_nl,
-                                cudaStream_t s);
-// CTAs of the non-local kernel of one system
+                                const long *nbegin, const int *gsys, const int *usys, const int *nsys,
+                                long total, long total_units, long total_nl, cudaStream_t s);
+// CTAs of the non-local kernel of one system; in a batch each CTA covers NL_BATCH_RUNS runs of
+// NL_THREADS (sphere point, vector) pairs, so that its setup is paid once per several runs
 inline long nl_blocks(int n_sp, int n_kb) { return (long)n_kb * (((long)n_sp * OVC + NL_THREADS - 1) / NL_THREADS); }
-cudaError_t launch_lda_batch(int prec, const BatchAux *aux, const BatchClock *clk, const long *begin, int n_sys,
-                             long total, cudaStream_t s);
+constexpr int NL_BATCH_RUNS = 8;
+inline long nl_batch_blocks(int n_sp, int n_kb) {
+  return (long)n_kb * (((long)n_sp * OVC + NL_THREADS * NL_BATCH_RUNS - 1) / (NL_THREADS * NL_BATCH_RUNS));
+}
+cudaError_t launch_lda_batch(int prec, const BatchAux *aux, const BatchClock *clk, const long *begin,
+                             const int *lsys, long total, cudaStream_t s);
 // which = 0: observable records (first sub-step of a step); 1: advance the clocks
 cudaError_t launch_batch_tail(const BatchAux *aux, BatchClock *clk, int n_sys, int which, cudaStream_t s);
 

@@ -72,17 +72,15 @@ struct tdks_system {
   cudaEvent_t ev_staging_free = nullptr;  // recorded after the last kernel that reads the staging buffer
   bool staging_pending = false;            // ev_staging_free has been recorded
   std::vector<cudaEvent_t> ev_chunk;
-  // repeated uploads (the second and later tdks_set_orbitals of a system in no batch): the next
-  // state is packed into these spare buffers on pack_stream while earlier work runs, and then
-  // they swap with psi / psi_lo / dens_part
+  // two upload buffers (tdks_set_upload_buffers): each upload packs the next state into these
+  // spares on pack_stream while earlier work runs, and then they swap with psi / psi_lo / dens_part
+  int upload_buffers = 1;
   void *psi_b = nullptr, *psi_lo_b = nullptr;
   double *dens_b = nullptr;
   cudaStream_t pack_stream = nullptr;
   cudaEvent_t ev_spare_free = nullptr;  // recorded on the stream when the spares were swapped out
   cudaEvent_t ev_packed = nullptr;      // recorded on pack_stream after an upload's packing
   bool spare_pending = false;
-  int uploads = 0;                      // tdks_set_orbitals calls so far
-  int batch_refs = 0;                   // batches that hold this system's buffers
   int *d_err = nullptr;       // [0]: error word of the bounded waits; [1]: sweep work counter
   int withhold = 0;           // failure injection: the sweeps' producers withhold their copies
   long obs_count = 0;         // energy/current partial records written by the last first sweep

@@ -191,25 +191,18 @@ struct SingleSrc {
   __device__ __forceinline__ bool withhold() const { return p->withhold != 0; }
 };
 
-__device__ __forceinline__ int find_item_sys(const long *begin, int n, long u) {
-  int lo = 0, hi = n - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (begin[mid] <= u) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
+// (the system of an item comes from a table: one load where a binary search over the systems'
+// item ranges took a chain of them at the start of every item, in every warp)
 struct BatchSrc {
   const BatchSweepArgs *a;
   __device__ __forceinline__ long n_items() const { return a->total_items; }
   __device__ __forceinline__ void item(long it, const SweepParams *&pp, const SweepMaps *&mp, long &local) const {
-    const int s = find_item_sys(a->item_begin, a->n_sys, it);
+    const int s = a->item_sys[it];
     pp = a->params + s;
     mp = a->maps + 4 * s + a->which;
     local = it - a->item_begin[s];
   }
-  __device__ __forceinline__ int sys_of(long it) const { return find_item_sys(a->item_begin, a->n_sys, it); }
+  __device__ __forceinline__ int sys_of(long it) const { return a->item_sys[it]; }
   __device__ __forceinline__ const SweepMaps *maps_of(int s) const { return a->maps + 4 * s + a->which; }
   __device__ __forceinline__ int *err0() const { return a->params[0].err; }
   __device__ __forceinline__ bool withhold() const { return a->params[0].withhold != 0; }

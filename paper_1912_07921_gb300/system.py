@@ -91,6 +91,11 @@ class System:
         """Orbitals from a host buffer (e.g. pinned memory) in the host layout."""
         _lib.check(self.lib.tdks_set_orbitals(self.h, ctypes.c_void_p(host_ptr)))
 
+    def set_upload_buffers(self, n: int):
+        """1 (default) or 2: with two, each upload packs into a second state buffer while
+        the work enqueued before it runs (a stream of uploads); such a system joins no batch."""
+        _lib.check(self.lib.tdks_set_upload_buffers(self.h, n))
+
     def set_tile(self, tx, ty, zc=0):
         _lib.check(self.lib.tdks_set_tile(self.h, tx, ty, zc))
 

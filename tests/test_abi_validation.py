@@ -61,6 +61,7 @@ def test_calls_on_a_null_system_are_refused(lib):
     assert lib.tdks_set_tsurff(None, None, 0, None) == EINVAL
     assert lib.tdks_get_tsurff(None, None, None) == EINVAL
     assert lib.tdks_set_failure_injection(None, 0) == EINVAL
+    assert lib.tdks_set_upload_buffers(None, 2) == EINVAL
     out3 = np.empty(3)
     assert lib.tdks_heat_current(None, 0.0, out3.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) == EINVAL
     assert lib.tdks_fma_rate(0, None) == EINVAL

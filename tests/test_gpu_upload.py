@@ -1,7 +1,7 @@
 """Orbital uploads through the C interface while a propagation is in flight.
 
-The second and later uploads of a system pack into a spare state buffer on a stream of their
-own and the system then switches buffers: work enqueued before the upload must still see the
+With two upload buffers, each upload packs into the spare state buffer on a stream of its own
+and the system then switches buffers: work enqueued before the upload must still see the
 old state, work enqueued after it the new one, and the spare may only be overwritten once the
 work that used it is done.  Each case compares with systems that never overlap anything (one
 upload each, propagated alone): complex128 bit for bit."""
@@ -50,6 +50,7 @@ def test_uploads_overlapping_propagations_keep_stream_order(prec):
     n = 2
     want = [_alone(spec, inp, psi, 0.0, n) for psi in states]
     s = System(spec, inp, stream=_stream(), orbitals=states[0])
+    s.set_upload_buffers(2)
     try:
         for i in range(len(states)):
             s.propagate(0.0, spec.dt, n, 2)  # enqueued; the next upload overlaps it
@@ -62,19 +63,28 @@ def test_uploads_overlapping_propagations_keep_stream_order(prec):
         got = s.get_orbitals()
         tol = 0.0 if prec == I.PREC_C128 else 1e-13
         assert np.max(np.abs(got - states[1])) <= tol * np.max(np.abs(states[1]))
+        s.set_upload_buffers(1)  # back to one buffer: the current state stays
+        assert np.array_equal(s.get_orbitals(), got)
+        s.propagate(0.0, spec.dt, n, 2)
+        np.testing.assert_array_equal(s.get_orbitals(), want[1][0])
     finally:
         s.close()
 
 
 def test_batched_system_uploads_in_place():
-    """A system held by a batch keeps its buffers: a repeated upload packs in place, and the
-    batch propagates the uploaded state."""
+    """A system in a batch has one upload buffer: an upload packs in place, and the batch
+    propagates the uploaded state.  A system with two buffers is refused by a batch."""
+    from paper_1912_07921_gb300._lib import TdksError
     from paper_1912_07921_gb300.system import Batch, System
     spec = ragged_molecule(I.PREC_C64, n_orb=4)
     inp = I.make_inputs(spec)
     psi1 = _orbitals(spec, 7)
     a = System(spec, inp, stream=_stream())
     a.set_clock(0.0, spec.dt, 1)
+    a.set_upload_buffers(2)
+    with pytest.raises(TdksError):
+        Batch([a], stream=_stream())
+    a.set_upload_buffers(1)
     b = Batch([a], stream=_stream())
     try:
         a.set_orbitals(psi1)
