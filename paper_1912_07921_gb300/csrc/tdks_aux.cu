@@ -45,10 +45,16 @@ __device__ __forceinline__ void gather_body(const GatherParams &p, int a, int kb
       const V x = T::ld(reinterpret_cast<const V *>(p.in) + ((long)kb * p.N + ca.x) * OVC + v);
       float c = 1.f, s = 0.f;
       if (phase) {
-        const ProjEntry &E = p.ent[e];
-        double ang = p.A[0] * E.d[0] + p.A[1] * E.d[1] + p.A[2] * E.d[2];
-        if (BLOCH) ang += p.kvec[3 * kidx] * E.T[0] + p.kvec[3 * kidx + 1] * E.T[1] + p.kvec[3 * kidx + 2] * E.T[2];
-        sincosf((float)ang, &s, &c);
+        if (p.phase) {
+          const float2 ph = p.phase[(long)kidx * p.n_ent + e];
+          c = ph.x;
+          s = ph.y;
+        } else {
+          const ProjEntry &E = p.ent[e];
+          double ang = p.A[0] * E.d[0] + p.A[1] * E.d[1] + p.A[2] * E.d[2];
+          if (BLOCH) ang += p.kvec[3 * kidx] * E.T[0] + p.kvec[3 * kidx + 1] * E.T[1] + p.kvec[3 * kidx + 2] * E.T[2];
+          sincosf((float)ang, &s, &c);
+        }
       }
       const float2 x0 = up2(x.x), x1 = up2(x.y);
       const float2 y0 = make_float2(c * x0.x - s * x0.y, c * x0.y + s * x0.x);
@@ -180,11 +186,17 @@ __device__ __forceinline__ void nl_body(const GatherParams &p, long t, int kb) {
       x = T::fma(T::coef(0.0, b4.z), T::ld(qa + 2 * OVC), x);
       x = T::fma(T::coef(0.0, b4.w), T::ld(qa + 3 * OVC), x);
       if (phase) {
-        const ProjEntry &E = p.ent[ei];
-        double ang = p.A[0] * E.d[0] + p.A[1] * E.d[1] + p.A[2] * E.d[2];
-        if (BLOCH) ang += p.kvec[3 * kidx] * E.T[0] + p.kvec[3 * kidx + 1] * E.T[1] + p.kvec[3 * kidx + 2] * E.T[2];
         float sn, cs;
-        sincosf((float)ang, &sn, &cs);
+        if (p.phase) {
+          const float2 ph = p.phase[(long)kidx * p.n_ent + ei];
+          cs = ph.x;
+          sn = ph.y;
+        } else {
+          const ProjEntry &E = p.ent[ei];
+          double ang = p.A[0] * E.d[0] + p.A[1] * E.d[1] + p.A[2] * E.d[2];
+          if (BLOCH) ang += p.kvec[3 * kidx] * E.T[0] + p.kvec[3 * kidx + 1] * E.T[1] + p.kvec[3 * kidx + 2] * E.T[2];
+          sincosf((float)ang, &sn, &cs);
+        }
         x = T::cmul(pk2(cs, cs), pk2(-sn, -sn), x);
       }
     } else {
@@ -366,6 +378,28 @@ __global__ void __launch_bounds__(NLC_THREADS) nl_current_kernel(const NlCurrent
 
 cudaError_t launch_nl_current(const NlCurrentParams &p, cudaStream_t s) {
   nl_current_kernel<<<dim3(p.n_atoms, p.n_kb), NLC_THREADS, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+__global__ void phase_table_kernel(const ProjEntry *ent, int n_ent, int n_k, const double *kvec, double Ax,
+                                   double Ay, double Az, int bloch, float2 *out) {
+  const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i >= (long)n_ent * n_k) return;
+  const int e = (int)(i % n_ent), k = (int)(i / n_ent);
+  const ProjEntry &E = ent[e];
+  double ang = Ax * E.d[0] + Ay * E.d[1] + Az * E.d[2];
+  if (bloch) ang += kvec[3 * k] * E.T[0] + kvec[3 * k + 1] * E.T[1] + kvec[3 * k + 2] * E.T[2];
+  float sn, cs;
+  sincosf((float)ang, &sn, &cs);
+  out[i] = make_float2(cs, sn);
+}
+
+cudaError_t launch_phase_table(const ProjEntry *ent, int n_ent, int n_k, const double *kvec, const double A[3],
+                               int bloch, float2 *out, cudaStream_t s) {
+  const long n = (long)n_ent * n_k;
+  if (n <= 0) return cudaSuccess;
+  phase_table_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ent, n_ent, n_k, kvec, A[0], A[1], A[2], bloch,
+                                                                 out);
   return cudaGetLastError();
 }
 

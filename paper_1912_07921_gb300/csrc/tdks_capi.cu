@@ -329,8 +329,21 @@ int run_gather(tdks_system *s, const void *in, const double A[3]) {
   g.sp = s->d_sp; g.n_sp = s->n_sp;
   g.rowent = s->d_rowent; g.n_ent = s->n_ent;
   g.nl = s->d_nl;
+  g.phase = nullptr;
+  const bool bloch = s->bc == TDKS_BC_BLOCH;
+  if (s->prec == TDKS_C64 && (bloch || g.A[0] != 0.0 || g.A[1] != 0.0 || g.A[2] != 0.0)) {
+    // the entries' phases for this vector potential, once for the Taylor terms that share it
+    if (!s->d_phase) CU(cudaMalloc((void **)&s->d_phase, (size_t)s->n_ent * s->n_k * sizeof(float2)));
+    if (!s->phase_ok || g.A[0] != s->phase_A[0] || g.A[1] != s->phase_A[1] || g.A[2] != s->phase_A[2]) {
+      CU(launch_phase_table(s->d_ent, s->n_ent, s->n_k, s->d_kvec, g.A, bloch, s->d_phase, s->stream));
+      s->launches++;
+      for (int a = 0; a < 3; a++) s->phase_A[a] = g.A[a];
+      s->phase_ok = true;
+    }
+    g.phase = s->d_phase;
+  }
   Timed tm(s, 1);
-  cudaError_t e = launch_gather(s->prec, s->bc == TDKS_BC_BLOCH, g, s->stream);
+  cudaError_t e = launch_gather(s->prec, bloch, g, s->stream);
   s->launches += s->n_sp > 0 ? 3 : 2;  // gather stages 1 and 2, the non-local term
   if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("projector gather: ") + cudaGetErrorString(e));
   return TDKS_OK;
@@ -465,8 +478,9 @@ double kinetic_max(const tdks_system *s) {
 void free_proj(tdks_system *s) {
   cudaFree(s->d_rowent); cudaFree(s->d_atom_begin);
   cudaFree(s->d_ent); cudaFree(s->d_q); cudaFree(s->d_D); cudaFree(s->d_qpart);
-  cudaFree(s->d_ent_beta); cudaFree(s->d_ent_ca);
-  s->d_ent_beta = nullptr; s->d_ent_ca = nullptr;
+  cudaFree(s->d_ent_beta); cudaFree(s->d_ent_ca); cudaFree(s->d_phase);
+  s->d_ent_beta = nullptr; s->d_ent_ca = nullptr; s->d_phase = nullptr;
+  s->phase_ok = false;
   cudaFree(s->d_sp); cudaFree(s->d_nl);
   s->d_rowent = s->d_atom_begin = nullptr;
   s->d_sp = nullptr; s->d_nl = nullptr;

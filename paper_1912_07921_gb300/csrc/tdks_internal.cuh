@@ -144,6 +144,7 @@ struct GatherParams {
   const int *rowent;          // entry indices, point-major
   int n_ent;
   void *nl;                   // [kb][n_ent + 1][OVC] vectors, row r0 of each sphere point
+  const float2 *phase;        // complex64: [k][n_ent] (cos, sin) of k.T + A.d, or null
 };
 
 // The projectors' share of a periodic cell's current (record time): partial records
@@ -222,6 +223,10 @@ size_t sweep_smem(int M, int tx, int ty);
 // and 2) and the non-local term at every sphere point (skipped when no point is in a sphere).
 constexpr int NL_THREADS = 256;
 cudaError_t launch_gather(int prec, int bloch, const GatherParams &p, cudaStream_t s);
+// out[k * n_ent + e] = (cos, sin) of A.d_e (+ k.T_e in a periodic cell), as the complex64
+// projector kernels would form it per entry
+cudaError_t launch_phase_table(const ProjEntry *ent, int n_ent, int n_k, const double *kvec, const double A[3],
+                               int bloch, float2 *out, cudaStream_t s);
 // chunks per (atom, k-batch) that fill the GPU for n_atoms * n_kb units
 int gather_chunks(long units);
 cudaError_t launch_density(int prec, long N, int n_kb, int n_batches, const void *psi, const void *psi_lo,

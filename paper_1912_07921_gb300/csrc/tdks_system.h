@@ -63,6 +63,11 @@ struct tdks_system {
   tdks::ProjEntry *d_ent = nullptr;
   float4 *d_ent_beta = nullptr;  // compact copies of the entries' FP32 beta and (cell, atom)
   int2 *d_ent_ca = nullptr;
+  // complex64 projector phases e^{i (k.T + A.d)} of every entry and k-point, built once per
+  // vector potential (a sub-step's Taylor terms share one)
+  float2 *d_phase = nullptr;
+  double phase_A[3] = {0.0, 0.0, 0.0};
+  bool phase_ok = false;
   double *fin_part = nullptr;    // first-stage partials of the observable record
   void *d_q = nullptr;
   double2 *d_qpart = nullptr;   // gather partial sums, gchunks per (atom, k-batch)
