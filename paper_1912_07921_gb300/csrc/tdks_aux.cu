@@ -218,13 +218,20 @@ __device__ __forceinline__ void nl_body(const GatherParams &p, long t, int kb) {
   reinterpret_cast<V *>(p.nl)[((long)kb * (p.n_ent + 1) + r.x) * OVC + v] = acc;
 }
 
-// (each thread takes its (sphere point, vector) through NL_KB_RUN k-batches: the point's entry
-// data stays in L1 across them, and a periodic cell's 64 k-batches need 8x fewer CTAs)
+// (with many k-batches each thread takes its (sphere point, vector) through a run of them: the
+// point's entry data stays in L1 across the run, and a periodic cell's 64 k-batches need 8x
+// fewer CTAs; a molecule's few k-batches keep one per CTA row, for parallelism)
 constexpr int NL_KB_RUN = 8;
+inline unsigned nl_kb_rows(int n_kb) { return n_kb >= 4 * NL_KB_RUN ? (n_kb + NL_KB_RUN - 1) / NL_KB_RUN : n_kb; }
 template <int P, int BLOCH>
 __global__ void __launch_bounds__(NL_THREADS) nl_kernel(const GatherParams p) {
   const long t = (long)blockIdx.x * NL_THREADS + threadIdx.x;
-  const int kb0 = blockIdx.y * NL_KB_RUN, kb1 = min(p.n_kb, kb0 + NL_KB_RUN);
+  if ((int)gridDim.y == p.n_kb) {
+    nl_body<P, BLOCH>(p, t, blockIdx.y);
+    return;
+  }
+  const int run = (p.n_kb + gridDim.y - 1) / gridDim.y;
+  const int kb0 = blockIdx.y * run, kb1 = min(p.n_kb, kb0 + run);
   for (int kb = kb0; kb < kb1; kb++) nl_body<P, BLOCH>(p, t, kb);
 }
 
@@ -412,8 +419,7 @@ cudaError_t launch_gather(int prec, int bloch, const GatherParams &p, cudaStream
   if (p.n_atoms <= 0) return cudaSuccess;
   dim3 grid(p.n_atoms * p.n_chunks, p.n_kb);
   const unsigned fgrid = (unsigned)(((long)p.n_atoms * p.n_kb + 7) / 8);
-  const dim3 ngrid((unsigned)(((long)p.n_sp * OVC + NL_THREADS - 1) / NL_THREADS),
-                   (unsigned)((p.n_kb + NL_KB_RUN - 1) / NL_KB_RUN));
+  const dim3 ngrid((unsigned)(((long)p.n_sp * OVC + NL_THREADS - 1) / NL_THREADS), nl_kb_rows(p.n_kb));
   if (prec == P_C64) {
     if (bloch) gather_kernel<P_C64, 1><<<grid, GATHER_THREADS, 0, s>>>(p);
     else gather_kernel<P_C64, 0><<<grid, GATHER_THREADS, 0, s>>>(p);
@@ -527,7 +533,8 @@ __device__ __forceinline__ void lda_body(long N, int nx, int ny, int nz, double 
                                          int n_batches, const double *wocc, const double *dens_part,
                                          const double *vloc, int xc, double Ex, double Ey, double Ez,
                                          double half_A2, PointAux *aux, double *lda_part, int blk, int nblk,
-                                         const double *n_in = nullptr, const double *vh = nullptr) {
+                                         const double *n_in = nullptr, const double *vh = nullptr,
+                                         bool sums = true) {
   constexpr bool F32 = sizeof(R) == 4;
   const int n_k = n_kb / n_batches;
   __shared__ float2 s_w[LDA_MAXK];  // complex64: w_k f = hi + lo
@@ -584,12 +591,14 @@ __device__ __forceinline__ void lda_body(long N, int nx, int ny, int nz, double 
       float v = (float)vloc[p] + vx + vhf + hA2f;
       if (!bloch) v += Exf * x + Eyf * y + Ezf * z;
       *reinterpret_cast<float *>(&aux[p].veff) = v;
-      // (with the Hartree potential the record subtracts int n (v_x + v_H) and adds E_H =
-      // 1/2 int n v_H: the third sum is int n (v_x + v_H / 2))
-      const float t[6] = {nf, nf * 0.75f * vx, nf * (vx + 0.5f * vhf), x * nf, y * nf, z * nf};
+      if (sums) {
+        // (with the Hartree potential the record subtracts int n (v_x + v_H) and adds E_H =
+        // 1/2 int n v_H: the third sum is int n (v_x + v_H / 2))
+        const float t[6] = {nf, nf * 0.75f * vx, nf * (vx + 0.5f * vhf), x * nf, y * nf, z * nf};
 #pragma unroll
-      for (int c = 0; c < 6; c++) df_acc(fh[c], fl[c], t[c]);
-      fl[0] += nl;  // the electron count keeps the double-float density in full
+        for (int c = 0; c < 6; c++) df_acc(fh[c], fl[c], t[c]);
+        fl[0] += nl;  // the electron count keeps the double-float density in full
+      }
     } else {
       const double x = (ix - cx) * h, y = (iy - cy) * h, z = (iz - cz) * h;
       double vx = 0.0;
@@ -598,14 +607,17 @@ __device__ __forceinline__ void lda_body(long N, int nx, int ny, int nz, double 
       double v = vloc[p] + vx + vhd + half_A2;
       if (!bloch) v += Ex * x + Ey * y + Ez * z;
       *reinterpret_cast<double *>(&aux[p].veff) = v;
-      acc[0] += n;
-      acc[1] += n * 0.75 * vx;
-      acc[2] += n * (vx + 0.5 * vhd);
-      acc[3] += x * n;
-      acc[4] += y * n;
-      acc[5] += z * n;
+      if (sums) {
+        acc[0] += n;
+        acc[1] += n * 0.75 * vx;
+        acc[2] += n * (vx + 0.5 * vhd);
+        acc[3] += x * n;
+        acc[4] += y * n;
+        acc[5] += z * n;
+      }
     }
   }
+  if (!sums) return;  // (uniform over the grid: V_eff only, no record follows)
   if constexpr (F32) {
 #pragma unroll
     for (int c = 0; c < 6; c++) acc[c] = (double)fh[c] + (double)fl[c];
@@ -628,9 +640,9 @@ template <typename R>
 __global__ void __launch_bounds__(LDA_THREADS)
 lda_kernel(long N, int nx, int ny, int nz, double h, int bloch, int n_kb, int n_batches, const double *wocc,
            const double *dens_part, const double *vloc, int xc, double Ex, double Ey, double Ez, double half_A2,
-           PointAux *aux, double *lda_part, const double *n_in, const double *vh) {
+           PointAux *aux, double *lda_part, const double *n_in, const double *vh, int sums) {
   lda_body<R>(N, nx, ny, nz, h, bloch, n_kb, n_batches, wocc, dens_part, vloc, xc, Ex, Ey, Ez, half_A2, aux,
-              lda_part, blockIdx.x, gridDim.x, n_in, vh);
+              lda_part, blockIdx.x, gridDim.x, n_in, vh, sums != 0);
 }
 
 // The density of this system's states at every point, n(r) = sum_k w_k f sum_i |psi|^2, as
@@ -838,13 +850,15 @@ cudaError_t launch_lda_batch(int prec, const BatchAux *aux, const BatchClock *cl
 cudaError_t launch_lda(int prec, int bloch, long N, int nx, int ny, int nz, double h, int n_kb, int n_batches,
                        const double *wocc, const double *dens_part, const double *vloc, int xc, const double E[3],
                        double half_A2, PointAux *aux, double *lda_part, int n_blocks, cudaStream_t s,
-                       const double *n_in, const double *vh) {
+                       const double *n_in, const double *vh, int sums) {
   if (prec == P_C64)
     lda_kernel<float><<<n_blocks, LDA_THREADS, 0, s>>>(N, nx, ny, nz, h, bloch, n_kb, n_batches, wocc, dens_part,
-                                                       vloc, xc, E[0], E[1], E[2], half_A2, aux, lda_part, n_in, vh);
+                                                       vloc, xc, E[0], E[1], E[2], half_A2, aux, lda_part, n_in, vh,
+                                                       sums);
   else
     lda_kernel<double><<<n_blocks, LDA_THREADS, 0, s>>>(N, nx, ny, nz, h, bloch, n_kb, n_batches, wocc, dens_part,
-                                                        vloc, xc, E[0], E[1], E[2], half_A2, aux, lda_part, n_in, vh);
+                                                        vloc, xc, E[0], E[1], E[2], half_A2, aux, lda_part, n_in, vh,
+                                                        sums);
   return cudaGetLastError();
 }
 

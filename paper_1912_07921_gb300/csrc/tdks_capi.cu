@@ -361,7 +361,7 @@ int ensure_density(tdks_system *s) {
   return TDKS_OK;
 }
 
-int run_lda(tdks_system *s, const double E[3], const double A[3]) {
+int run_lda(tdks_system *s, const double E[3], const double A[3], bool sums = true) {
   const double half_A2 = s->gauge == TDKS_GAUGE_VELOCITY ? 0.5 * (A[0] * A[0] + A[1] * A[1] + A[2] * A[2]) : 0.0;
   const double El[3] = {s->gauge == TDKS_GAUGE_LENGTH ? E[0] : 0.0, s->gauge == TDKS_GAUGE_LENGTH ? E[1] : 0.0,
                         s->gauge == TDKS_GAUGE_LENGTH ? E[2] : 0.0};
@@ -381,7 +381,7 @@ int run_lda(tdks_system *s, const double E[3], const double A[3]) {
   cudaError_t e = launch_lda(s->prec, s->bc == TDKS_BC_BLOCH, s->N, s->nx, s->ny, s->nz, s->h, s->n_kb,
                              s->n_batches, s->d_wocc, s->dens_part, s->vloc, s->xc != TDKS_XC_NONE, El, half_A2,
                              s->aux, s->lda_part, lda_blocks(s->N), s->stream,
-                             (s->xfn || hartree) ? s->n_total : nullptr, hartree ? s->d_vh : nullptr);
+                             (s->xfn || hartree) ? s->n_total : nullptr, hartree ? s->d_vh : nullptr, sums ? 1 : 0);
   s->launches++;
   if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("lda: ") + cudaGetErrorString(e));
   return TDKS_OK;
@@ -1467,7 +1467,7 @@ static int propagate_steps(tdks_system *s, double t0, double dt, int n_steps, in
       double E[3], A[3];
       field_at(s, tm, E, A);
       const bool rec = (j == 0);
-      if ((rc = run_lda(s, E, A))) return rc;
+      if ((rc = run_lda(s, E, A, rec))) return rc;  // (the record's sums on record sub-steps only)
       if ((rc = first_sweep(s, 0.0, -dts, A, rec))) return rc;
       if (rec) {
         double *slot = s->ring + (s->steps % tdks_system::RING) * TDKS_RECORD;

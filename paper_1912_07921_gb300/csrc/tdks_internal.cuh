@@ -235,7 +235,8 @@ cudaError_t launch_lda(int prec, int bloch, long N, int nx, int ny, int nz, doub
                        int n_kb, int n_batches, const double *wocc, const double *dens_part,
                        const double *vloc, int xc,
                        const double E[3], double half_A2, PointAux *aux, double *lda_part,
-                       int n_blocks, cudaStream_t s, const double *n_in = nullptr, const double *vh = nullptr);
+                       int n_blocks, cudaStream_t s, const double *n_in = nullptr, const double *vh = nullptr,
+                       int sums = 1);
 // Classical Runge-Kutta stage update over n complex128 values (complex128 systems):
 //   stage = psi + a k,  acc = (init ? 0 : acc) + b k,
 // and the last stage's psi <- psi + acc + b k (rk4_finish).
