@@ -432,8 +432,8 @@ int tdks_batch_destroy(tdks_batch_t batch);
  * the process exits; grids above 2^20 = 1,048,576 points are rejected with TDKS_EINVAL.
  * All calls on a device share that array and each call overwrites it, so calls whose work
  * overlaps on the GPU (several streams or host threads) race: serialise them.  The first
- * call on a device looks up the array's device address on that device (make it before
- * any stream capture).  Returns TDKS_ETIMEOUT if a sweep gave up waiting for its copies.
+ * call on a device looks up the array's device address on that device.  Returns
+ * TDKS_ETIMEOUT if a sweep gave up waiting for its copies.
  */
 int tdks_apply_H_noalloc(int nx, int ny, int nz, double h, int fd_order, int prec, int n_orb,
                          const double *dev_vloc, const void *dev_in, void *dev_out, void *stream);

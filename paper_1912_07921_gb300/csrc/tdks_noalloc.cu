@@ -13,8 +13,7 @@
 // The scratch array is shared by all calls on a device and keeps the last call's
 // contents.  Calls whose work overlaps on the GPU (several streams, or several host
 // threads) race on it; serialise them.  The first call on a device looks up the array's
-// device address (cudaGetSymbolAddress) with that device current; make that first call
-// before any stream capture.
+// device address (cudaGetSymbolAddress) with that device current.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
