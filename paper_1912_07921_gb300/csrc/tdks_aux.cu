@@ -825,9 +825,16 @@ __device__ __forceinline__ double batch_field(const BatchAux &a, double t) {
 // system's current sub-step midpoint from its device clock.
 template <typename R>
 __global__ void __launch_bounds__(LDA_THREADS)
-lda_batch_kernel(const BatchAux *aux, const BatchClock *clk, const long *begin, const int *sys_of) {
+lda_batch_kernel(const BatchAux *aux, const BatchClock *clk, const long *begin, int n_sys) {
   __shared__ double f;
-  const int s = sys_of[blockIdx.x];
+  // the CTA's system: a binary search over the systems' CTA ranges (a table lookup, as the
+  // projector kernels use, measured 1.3% slower on the batched step here)
+  int lo = 0, hi = n_sys - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (begin[mid] <= (long)blockIdx.x) lo = mid; else hi = mid - 1;
+  }
+  const int s = lo;
   const BatchAux &a = aux[s];
   if (threadIdx.x == 0) {
     const BatchClock c = clk[s];
@@ -840,10 +847,10 @@ lda_batch_kernel(const BatchAux *aux, const BatchClock *clk, const long *begin, 
               a.n_lda);
 }
 
-cudaError_t launch_lda_batch(int prec, const BatchAux *aux, const BatchClock *clk, const long *begin,
-                             const int *lsys, long total, cudaStream_t s) {
-  if (prec == P_C64) lda_batch_kernel<float><<<(unsigned)total, LDA_THREADS, 0, s>>>(aux, clk, begin, lsys);
-  else lda_batch_kernel<double><<<(unsigned)total, LDA_THREADS, 0, s>>>(aux, clk, begin, lsys);
+cudaError_t launch_lda_batch(int prec, const BatchAux *aux, const BatchClock *clk, const long *begin, int n_sys,
+                             long total, cudaStream_t s) {
+  if (prec == P_C64) lda_batch_kernel<float><<<(unsigned)total, LDA_THREADS, 0, s>>>(aux, clk, begin, n_sys);
+  else lda_batch_kernel<double><<<(unsigned)total, LDA_THREADS, 0, s>>>(aux, clk, begin, n_sys);
   return cudaGetLastError();
 }
 

@@ -30,7 +30,7 @@ struct tdks_batch {
   int *d_item_sys[4] = {nullptr, nullptr, nullptr, nullptr};        // the system of every item
   long *d_gather_begin = nullptr, *d_unit_begin = nullptr, *d_lda_begin = nullptr;
   long *d_nl_begin = nullptr;
-  int *d_gather_sys = nullptr, *d_unit_sys = nullptr, *d_nl_sys = nullptr, *d_lda_sys = nullptr;
+  int *d_gather_sys = nullptr, *d_unit_sys = nullptr, *d_nl_sys = nullptr;
   unsigned int *d_work = nullptr;  // work-item counter of the batched sweep (zero between launches)
   BatchAux *d_aux = nullptr;
   std::vector<BatchAux> aux_h;     // host copy (the record count follows the first term's shape)
@@ -51,7 +51,7 @@ void batch_free(tdks_batch *b) {
   cudaFree(b->d_maps); cudaFree(b->d_gather_begin); cudaFree(b->d_lda_begin);
   cudaFree(b->d_nl_begin); cudaFree(b->d_work);
   cudaFree(b->d_unit_begin);
-  cudaFree(b->d_gather_sys); cudaFree(b->d_unit_sys); cudaFree(b->d_nl_sys); cudaFree(b->d_lda_sys);
+  cudaFree(b->d_gather_sys); cudaFree(b->d_unit_sys); cudaFree(b->d_nl_sys);
   cudaFree(b->d_aux); cudaFree(b->d_clock);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
@@ -77,8 +77,7 @@ long long substep_launches(const tdks_batch *b) {
 // Enqueue one sub-step of every system of the batch.
 int enqueue_substep(tdks_batch *b) {
   const int n = (int)b->sys.size();
-  cudaError_t e = launch_lda_batch(b->prec, b->d_aux, b->d_clock, b->d_lda_begin, b->d_lda_sys, b->total_lda,
-                                   b->work);
+  cudaError_t e = launch_lda_batch(b->prec, b->d_aux, b->d_clock, b->d_lda_begin, n, b->total_lda, b->work);
   if (e != cudaSuccess) return fail(TDKS_EDEVICE, std::string("batched lda: ") + cudaGetErrorString(e));
   for (int k = 0; k < 4; k++) {
     e = launch_gather_batch(b->prec, b->d_gather[k], b->d_gather_begin, b->d_unit_begin, b->d_nl_begin,
@@ -280,7 +279,7 @@ int tdks_batch_create(const tdks_sys *systems, int n, void *stream, tdks_batch_t
   if (!rc) rc = upload(&b->d_unit_begin, unit_begin);
   if (!rc) rc = upload(&b->d_lda_begin, lda_begin);
   if (!rc) rc = upload(&b->d_nl_begin, nl_begin);
-  // the system of every CTA (or unit) of the batched projector and LDA launches
+  // the system of every CTA (or unit) of the batched projector launches
   auto owners = [&](const std::vector<long> &beg) {
     std::vector<int> o((size_t)beg[n]);
     for (int i = 0; i < n; i++)
@@ -290,7 +289,6 @@ int tdks_batch_create(const tdks_sys *systems, int n, void *stream, tdks_batch_t
   if (!rc) rc = upload(&b->d_gather_sys, owners(gather_begin));
   if (!rc) rc = upload(&b->d_unit_sys, owners(unit_begin));
   if (!rc) rc = upload(&b->d_nl_sys, owners(nl_begin));
-  if (!rc) rc = upload(&b->d_lda_sys, owners(lda_begin));
   if (!rc) rc = upload(&b->d_work, std::vector<unsigned int>(1, 0u));
   if (!rc) rc = upload(&b->d_aux, aux);
   if (!rc) rc = upload(&b->d_clock, clk);

@@ -312,8 +312,8 @@ constexpr int NL_BATCH_RUNS = 8;
 inline long nl_batch_blocks(int n_sp, int n_kb) {
   return (long)n_kb * (((long)n_sp * OVC + NL_THREADS * NL_BATCH_RUNS - 1) / (NL_THREADS * NL_BATCH_RUNS));
 }
-cudaError_t launch_lda_batch(int prec, const BatchAux *aux, const BatchClock *clk, const long *begin,
-                             const int *lsys, long total, cudaStream_t s);
+cudaError_t launch_lda_batch(int prec, const BatchAux *aux, const BatchClock *clk, const long *begin, int n_sys,
+                             long total, cudaStream_t s);
 // which = 0: observable records (first sub-step of a step); 1: advance the clocks
 cudaError_t launch_batch_tail(const BatchAux *aux, BatchClock *clk, int n_sys, int which, cudaStream_t s);
 
