@@ -364,8 +364,9 @@ int tdks_sweep_shape_info(int shape, int *count, int *tx, int *ty, int *rows, in
 int tdks_set_sweep_shape(tdks_sys sys, int sweep, int shape);
 int tdks_get_sweep_shape(tdks_sys sys, int sweep, int *shape);
 /* Autotuner: times every shape on each of the four Taylor-term sweeps of this system, on
- * its own grid, orbitals and projectors (reps launches each after one warm-up launch, CUDA
- * events on the system's stream), and keeps the fastest shape per sweep.  The state psi is
+ * its own grid, orbitals and projectors (in the velocity gauge with a vector potential
+ * amp * pol, so that the gauge term is timed too; reps launches each after one warm-up
+ * launch, CUDA events on the system's stream), and keeps the fastest shape per sweep.  The state psi is
  * not changed; the Taylor-term buffers and the density partials are overwritten (the next
  * propagation or H application rebuilds them).  ms (if not NULL) receives the mean
  * milliseconds per launch as ms[shape * 4 + sweep] (count * 4 values).  Systems that do not

@@ -974,11 +974,15 @@ int tdks_get_sweep_shape(tdks_sys s, int sweep, int *shape) {
 // sweeps 1 and 2 read t(k-1) and write t(k); sweep 3 reads t3 and combines into t1/t2 in
 // place of the state (state hi <- t1, state lo <- t2), so the state itself is untouched.
 static int tune_launch(tdks_system *s, int sweep) {
-  const double A0[3] = {0.0, 0.0, 0.0};
+  // in the velocity gauge, a vector potential along the field's polarisation, so that the
+  // timed sweeps carry the gauge term the propagation's sweeps carry
+  double At[3] = {0.0, 0.0, 0.0};
+  if (s->gauge == TDKS_GAUGE_VELOCITY)
+    for (int a = 0; a < 3; a++) At[a] = s->amp * s->pol[a];
   const int modes[4] = {MODE_FIRST, MODE_MID, MODE_MID, MODE_LAST};
   const int mode = modes[sweep];
   SweepParams p{};
-  sweep_common(s, p, A0, sweep);
+  sweep_common(s, p, At, sweep);
   set_coef(p, 0.0, -0.01 / (sweep + 1));
   p.in = sweep == 0 ? s->psi : s->term[sweep - 1];
   SweepMaps tm;
