@@ -159,6 +159,30 @@ def _sweep_bytes(spec, sysm) -> float:
     return vals * per_val + veff + dens
 
 
+def _sweep_bytes_by_term(spec, sysm):
+    """_sweep_bytes split over the four Taylor-term sweeps (each reads the per-point V_eff
+    record; the last writes the density words)."""
+    bs, nb, eb, _ = sysm.layout()
+    vals = spec.n_points * nb * bs * sysm.n_k
+    st_first, st = (8.0, 16.0) if eb == 8 else (16.0, 16.0)
+    veff = spec.n_points * (4 if eb == 8 else 8)
+    dens = spec.n_points * nb * sysm.n_k * 8
+    return [vals * (st_first + eb) + veff, vals * 2 * eb + veff, vals * 2 * eb + veff,
+            vals * (eb + st + eb + eb + st) + veff + dens]
+
+
+def _by_term(term_bytes, term_ms, peak):
+    """Per Taylor-term sweep: average launch time (CUDA events in the timed region), the
+    algorithmic bytes of one launch, and the achieved GB/s and its fraction of the peak."""
+    out = []
+    for b, (ms, n) in zip(term_bytes, term_ms):
+        us = 1e3 * ms / max(n, 1)
+        gbs = b / (us * 1e-6) / 1e9 if n else 0.0
+        out.append({"avg_launch_us": us, "launches": n, "bytes_per_launch": b, "achieved": gbs,
+                    "frac": gbs / peak})
+    return out
+
+
 def max_over_ranks(x: float, dist, device) -> float:
     """The largest of every rank's x (the job's time is its slowest rank's); x itself at N = 1."""
     if dist is None:
@@ -252,6 +276,7 @@ def run_ours(args, rank, world, local_rank):
     sweep_ms, sweep_n = sysm.kernel_time(0)
     gath_ms, gath_n = sysm.kernel_time(1)
     aux_ms, aux_n = sysm.kernel_time(2)
+    term_ms = [sysm.kernel_time(3 + k) for k in range(4)]
     sysm.set_profiling(False)
     rec = sysm.reductions(sysm.step_count() - 1, 1)[0]
     ms = max_over_ranks(ms, dist, "cuda")
@@ -312,7 +337,8 @@ def run_ours(args, rank, world, local_rank):
                          "traffic": _traffic_per_launch() if sysm.spec.n_orb == 64 and prec == I.PREC_C64
                          else None,
                          "sweep_source_hash": sweep_source_hash(),
-                         "bytes_per_launch": per_launch_bytes, "avg_launch_us": avg_launch_s * 1e6},
+                         "bytes_per_launch": per_launch_bytes, "avg_launch_us": avg_launch_s * 1e6,
+                         "by_taylor_term": _by_term(_sweep_bytes_by_term(sysm.spec, sysm), term_ms, peak)},
             "kernel_ms": {"sweep": sweep_ms, "sweep_launches": sweep_n, "projector": gath_ms,
                           "projector_steps": gath_n, "density_lda_finalize": aux_ms, "aux_launches": aux_n},
             "sweep_shapes": {"chosen": sysm.sweep_shapes(),

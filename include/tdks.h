@@ -304,7 +304,8 @@ int tdks_observe(tdks_sys sys, double t_state, double t_field, double *out);
  * Kernel accounting.  tdks_set_profiling(sys, 1) brackets every stencil-sweep launch
  * with CUDA events on the system's stream; tdks_kernel_time(sys, kind, &ms, &n) then
  * returns the summed device time and launch count since the last call and resets them
- * (kind 0: stencil sweeps, 1: projector gathers, 2: density/LDA/finalise).  Synchronises.
+ * (kind 0: stencil sweeps, 1: projector gathers, 2: density/LDA/finalise; 3..6: the stencil
+ * sweeps of Taylor terms 1..4, which kind 0 counts too).  Synchronises.
  * tdks_launch_count returns the number of kernels this system has launched.
  */
 int tdks_set_profiling(tdks_sys sys, int on);

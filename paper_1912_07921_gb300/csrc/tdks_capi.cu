@@ -293,7 +293,7 @@ void build_tmaps(tdks_system *s) {
 // sweep: which Taylor-term sweep (0..3; its tile shape on the warp-specialised TMA path), or
 // -1 for the default shape
 int run_sweep(tdks_system *s, int mode, SweepParams &p, const SweepMaps *tm, int sweep = -1) {
-  Timed tmr(s, 0);
+  Timed tmr(s, sweep >= 0 && sweep < 4 ? 3 + sweep : 0);  // (kinds 3..6 also count as kind 0)
   p.err = s->d_err;
   cudaError_t e;
   const bool tma = tm && tma_path(s);
@@ -1531,13 +1531,17 @@ int tdks_set_profiling(tdks_sys s, int on) {
 }
 
 int tdks_kernel_time(tdks_sys s, int kind, double *ms, long long *launches) {
-  if (!s || kind < 0 || kind > 2) return fail(TDKS_EINVAL, "bad argument");
+  if (!s || kind < 0 || kind > 6) return fail(TDKS_EINVAL, "bad argument");
   CU(cudaStreamSynchronize(s->stream));
   for (auto &u : s->ev_used) {
     float t = 0.0f;
     if (cudaEventElapsedTime(&t, u.second.first, u.second.second) == cudaSuccess) {
       s->prof_ms[u.first] += t;
       s->prof_n[u.first]++;
+      if (u.first >= 3) {  // a Taylor term's sweep is also a stencil sweep
+        s->prof_ms[0] += t;
+        s->prof_n[0]++;
+      }
     }
     s->ev_free.push_back(u.second.first);
     s->ev_free.push_back(u.second.second);

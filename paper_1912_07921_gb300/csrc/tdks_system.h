@@ -132,8 +132,8 @@ struct tdks_system {
   bool profile = false;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
   std::vector<cudaEvent_t> ev_free;
-  double prof_ms[3] = {0, 0, 0};
-  long long prof_n[3] = {0, 0, 0};
+  double prof_ms[7] = {0, 0, 0, 0, 0, 0, 0};  // kinds of tdks_kernel_time
+  long long prof_n[7] = {0, 0, 0, 0, 0, 0, 0};
 };
 
 namespace tdks_host {
