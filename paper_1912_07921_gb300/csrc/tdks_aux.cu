@@ -582,7 +582,10 @@ __device__ __forceinline__ void lda_body(long N, int nx, int ny, int nz, double 
     } else {
       for (int kb = 0; kb < n_kb; kb++) n += dens_part[(long)kb * N + p];
     }
-    const int ix = (int)(p % nx), iy = (int)((p / nx) % ny), iz = (int)(p / ((long)nx * ny));
+    // (32-bit index arithmetic: a 64-bit division per coordinate cost more than the point's
+    // arithmetic; the grids here have far fewer than 2^32 points)
+    const unsigned up = (unsigned)p, unx = (unsigned)nx, uny = (unsigned)ny;
+    const int ix = (int)(up % unx), iy = (int)((up / unx) % uny), iz = (int)(up / (unx * uny));
     if constexpr (F32) {
       const float nf = nh;
       const float x = (ix - cxf) * hf, y = (iy - cyf) * hf, z = (iz - czf) * hf;
@@ -787,7 +790,10 @@ cfm_veff_kernel(long N, int nx, int ny, int nz, double h, int bloch, int n_kb, i
       if (vh) vx += vh[p];  // the Hartree potential of the same density
       hist.v[0][p] = vx;
     }
-    const int ix = (int)(p % nx), iy = (int)((p / nx) % ny), iz = (int)(p / ((long)nx * ny));
+    // (32-bit index arithmetic: a 64-bit division per coordinate cost more than the point's
+    // arithmetic; the grids here have far fewer than 2^32 points)
+    const unsigned up = (unsigned)p, unx = (unsigned)nx, uny = (unsigned)ny;
+    const int ix = (int)(up % unx), iy = (int)((up / unx) % uny), iz = (int)(up / (unx * uny));
     double v = vloc[p];
     for (int j = 0; j < hist.nh; j++) v += hist.w[j] * hist.v[j][p];
     v += Ex * ((ix - cx) * h) + Ey * ((iy - cy) * h) + Ez * ((iz - cz) * h);
